@@ -1,0 +1,96 @@
+/*
+ * Plain FP64 CPU oracle for the Cartesian cut-cell discrete-velocity method
+ * (Dechriste & Mieussens, arXiv:1503.04544).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library
+ * against the paper: only the tests, the smoke entry point and the CPU
+ * baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or helper with the GPU path.
+ *
+ * Every routine is written as plain loops in the order the paper states the
+ * method (Sec. 3.3.5 "Summary of the numerical scheme" for 2D, Sec. 5 for 3D,
+ * Appendix A for the geometry).  Compiled with -ffp-contract=off so that the
+ * geometry (a pure function of +,-,*,/,sqrt) is reproducible bit for bit.
+ *
+ * Layout of a distribution array: [cell][component][p], cell = j*nx + i
+ * (3D: (k*ny + j)*nx + i), p = p2*nvx + p1 (3D: (p3*nvy + p2)*nvx + p1), the
+ * velocity ordering of Sec. 3.1.  2D has two components (f, g) of the reduced
+ * model (Sec. 2.2); 3D has one (F).
+ */
+#ifndef DVM_ORACLE_H
+#define DVM_ORACLE_H
+#include <stdint.h>
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_CFL = 2, ORC_ERR_GEOMETRY = 3,
+       ORC_ERR_NONPHYSICAL = 4 };
+enum { ORC_GAS = 0, ORC_CUT = 1, ORC_SOLID = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_MAXWELLIAN = 1, ORC_BC_ZEROGRAD = 2 };
+enum { ORC_SHAPE_NONE = 0, ORC_SHAPE_CIRCLE = 1, ORC_SHAPE_ELLIPSE = 2,
+       ORC_SHAPE_SPHERE = 3 };
+enum { ORC_UPWIND = 0, ORC_MUSCL = 1 };
+
+/* Problem statement.  2D uses the x/y fields, 3D also the z ones. */
+typedef struct {
+    int dim;                       /* 2 or 3 */
+    int nx, ny, nz;                /* cells per axis */
+    double xmin, xmax, ymin, ymax, zmin, zmax;
+    int nvx, nvy, nvz;             /* velocity points per axis */
+    double vxmin, vxmax, vymin, vymax, vzmin, vzmax;
+    double Kn, Lref, cfl, dt;      /* dt > 0 overrides the CFL rule */
+    int scheme;                    /* ORC_UPWIND | ORC_MUSCL */
+    int bc[6];                     /* x-, x+, y-, y+, z-, z+ */
+    /* Maxwellian sides: (rho, ux, uy, uz, T) per boundary cell of that side,
+     * ordered like the cells of the side (2D: j or i; 3D: row-major of the
+     * two remaining axes). */
+    const double *bc_state[6];
+    /* obstacle */
+    int shape;
+    double cx, cy, cz, ra, rb;     /* circle/sphere radius ra; ellipse a=ra, b=rb */
+    double theta, omega;           /* body angle and angular velocity */
+    double vbx, vby;               /* translational velocity (kept fixed; the
+                                      configurations only rotate) */
+    double mass, inertia;
+    int movable;                   /* 1: free rotation about (cx, cy) */
+    double Tw;                     /* wall temperature */
+    int nseg;                      /* >0: per-sector wall temperatures */
+    const double *Tw_seg;          /* [nseg] */
+    const double *seg_dir;         /* [2*nseg] sector boundary directions */
+} orc_cfg;
+
+/* Geometry of one time level (2D): every array is caller-owned.          */
+typedef struct {
+    double *phi;      /* (nx+1)*(ny+1) nodal level set, node (a,b) at b*(nx+1)+a */
+    int8_t *type;     /* nx*ny: ORC_GAS / ORC_CUT / ORC_SOLID                   */
+    int8_t *cgas;     /* nx*ny: centre-in-gas test of Eq. (ii)                   */
+    double *lx;       /* (nx+1)*ny vertical edges, edge a of row j at j*(nx+1)+a */
+    double *ly;       /* nx*(ny+1) horizontal edges, edge b of column i at b*nx+i */
+    double *lw;       /* nx*ny wall edge length                                  */
+    double *nwx, *nwy;/* nx*ny wall normal (towards the solid)                   */
+    double *rwx, *rwy;/* nx*ny wall edge centre (absolute)                       */
+    double *sbar;     /* nx*ny virtual cell area                                 */
+} orc_geo2d;
+
+/* Diagnostics written by the runner, one entry per step (nullable).        */
+typedef struct {
+    double *Fx, *Fy, *Fz;   /* force on the body at t^n                     */
+    double *torque;         /* torque about the z axis at t^n               */
+    double *theta, *omega;  /* body state after the step                    */
+    double *mass;           /* total mass after the step                    */
+} orc_hist;
+
+double orc_tau0(const orc_cfg *c);
+double orc_dt(const orc_cfg *c);
+
+int orc_geometry2d(const orc_cfg *c, double cos_t, double sin_t, orc_geo2d *g);
+int orc_masters2d(const orc_cfg *c, const orc_geo2d *gn, const orc_geo2d *gnp1,
+                  int32_t *master);
+int orc_init_maxwellian(const orc_cfg *c, const double *rho, const double *ux,
+                        const double *uy, const double *uz, const double *T,
+                        double *F);
+int orc_moments(const orc_cfg *c, const double *F, double *rho, double *ux,
+                double *uy, double *uz, double *T);
+int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
+              double *theta_out, double *omega_out);
+double orc_mass2d(const orc_cfg *c, const double *F);
+
+#endif
