@@ -1,0 +1,301 @@
+#!/usr/bin/env python3
+"""Throughput of the cut-cell discrete-velocity step on GB300.
+
+Default workload: 2D fixed cylinder, 256x256 cells on [0,1]^2, cylinder
+r = 0.1, 32x32 velocities on [-8,8)^2, Mach-2 inflow, Kn 0.05, MUSCL-minmod,
+FP32 state.  One bench step is one time step of the whole method (wall
+density and stress, force/torque, fluxes, relaxation, cut-cell control
+volumes, moments).  Metric: (cell, velocity) pair updates per second over
+the non-solid cells.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+                  [--impl gb300|reference]
+
+For N > 1 each rank runs an independent replica (the path is not sharded
+here); value = pairs updated by all ranks / max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-velocity pair updates/s"
+UNIT = "pair-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(name: str):
+    from paper_1503_04544_gb300 import workloads as W
+    if name == "cylinder":
+        return W.cylinder_mach2(nx=256, nv=32, scheme=1)
+    if name == "ellipse":
+        return W.rotating_ellipse(nx=512, nv=40)
+    if name == "bump":
+        return W.periodic_bump()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def config_dict(cfg, prec, nsolid_free, extra=None):
+    d = {
+        "workload": cfg["name"],
+        "cells": [cfg["nx"], cfg["ny"]],
+        "velocities": [cfg["nvx"], cfg["nvy"]],
+        "scheme": "muscl-minmod" if cfg.get("scheme", 0) == 1 else "upwind",
+        "precision": prec,
+        "pairs_per_step": nsolid_free,
+        "l2": "inputs larger than L2 (state per copy > 129 MB)",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel_src: str):
+    """DRAM bytes per launch of the bulk kernel from the committed ncu summary,
+    or None if the kernel source changed since the capture."""
+    import hashlib
+    summ = os.path.join(ROOT, "profiles", "k_bulk_cylinder_fp32.md")
+    if not os.path.exists(summ):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    rec = {}
+    for line in open(summ):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel source sha256/16") != h:
+        return None
+    try:
+        return float(rec["dram bytes per launch (scaled)"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in region"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if "Active" in r[5 + q]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(cfg, budget_s: float = 20.0, max_steps: int = 4):
+    """Time the FP64 oracle as it stands on the host cores (bounded sample)."""
+    import numpy as np
+    import oracle
+    F = oracle.initial_state(cfg)
+    g = oracle.geometry2d(cfg)
+    nonsolid = int(np.sum(g["type"] != 2))
+    pairs = nonsolid * cfg["nvx"] * cfg["nvy"]
+    done = 0
+    t0 = time.perf_counter()
+    while done < max_steps:
+        oracle.run(cfg, F, 1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": pairs * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} FP64 oracle step(s) of {cfg['name']} from the initial state, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = workload(args.workload)
+    cb = cpu_baseline(cfg, budget_s=60.0, max_steps=max(1, min(args.steps, 8)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": config_dict(cfg, "fp64", None, {"sample": cb["sample"]}),
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--workload", default="cylinder")
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1503_04544_gb300 import dvm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cfg = workload(args.workload)
+    prec = dvm.FP32 if args.precision == "fp32" else dvm.FP64
+    stream = torch.cuda.current_stream()
+    s = dvm.Solver(cfg, prec, stream=stream.cuda_stream)
+    s.init_maxwellian()
+    s.step(max(args.warmup, 3))
+    counts = s.cell_counts()
+    pairs_per_step = counts["nonsolid"] * s.nv
+    bulk_pairs = counts["bulk"] * s.nv
+    bytes_per_pair = 2 * s.ncomp * s.elem      # one read and one write of each component
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    s.timing(True)
+    l0 = s.launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step_async(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = s.launches() - l0
+    s.check()
+    ms = e0.elapsed_time(e1)
+    bulk_ms, nb = s.kernel_time()
+    s.timing(False)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    barrier()
+
+    # end to end through the public API with pinned host buffers
+    host = torch.empty(s.state_size, dtype=torch.float32 if prec == dvm.FP32 else torch.float64,
+                       pin_memory=True)
+    s.get_state(host)
+    s.set_state(host)
+    s.step(1)
+    s.moments()
+    barrier()
+    t0 = time.perf_counter()
+    s.set_state(host)
+    s.step(args.steps)
+    m = s.moments()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    h2d = s.state_size * s.elem
+    d2h = 5 * 8 * s.ncell
+    e2e = {"value": world * pairs_per_step * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "note": "per run: state H2D from pinned host memory, K steps, moments D2H"}
+    assert np.isfinite(m["rho"]).all()
+
+    if rank == 0:
+        peak, peak_kind = read_peaks()
+        avg_bulk_s = bulk_ms / max(nb, 1) / 1e3
+        achieved = bulk_pairs * bytes_per_pair / avg_bulk_s / 1e9
+        traffic = recorded_traffic(os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step2d.cu"))
+        line = {
+            "metric": METRIC,
+            "value": world * pairs_per_step * args.steps / (ms_max / 1e3),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if prec == dvm.FP32 else "f64",
+            "data": "synthetic",
+            "config": config_dict(cfg, args.precision, pairs_per_step,
+                                  {"parallelism": f"replicas{world}" if world > 1 else "single",
+                                   "bulk_pairs_per_step": bulk_pairs,
+                                   "cut_cell_cvs": counts["cvs"], "wall_cells": counts["walls"]}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_bulk (fused stream + relax + moments)",
+                         "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "bytes_per_pair": bytes_per_pair,
+                         "bulk_ms_per_launch": avg_bulk_s * 1e3,
+                         "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)},
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": launches,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(cfg)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

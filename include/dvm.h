@@ -1,0 +1,209 @@
+/*
+ * libdvm - GB300 (sm_103a) CUDA library for the Cartesian cut-cell
+ * discrete-velocity method of Dechriste & Mieussens, "A Cartesian cut cell
+ * method for rarefied flow simulations around moving obstacles"
+ * (arXiv:1503.04544).
+ *
+ * One time step updates every (cell, discrete velocity) pair: the BGK
+ * relaxation toward the local Maxwellian (Sec. 2.1, Eq. BGKDD), upwind or
+ * limited fluxes across the Cartesian edges of each virtual cell and the
+ * diffuse-reflection flux across its wall edge (Eq. FluxDD, Eq.
+ * BoundaryDDv), the explicit update of each control volume (Eq. ExSchemeDD)
+ * and the wall stress, force, torque and rigid rotation (Sec. 3.3.4).  2D
+ * uses the reduced pair (f, g) (Sec. 2.2); 3D uses the full F (Sec. 5).
+ *
+ * Conventions
+ *  - Every call returns a dvm_status.  Nothing aborts or throws across this
+ *    boundary; dvm_last_error() gives a thread-local message.
+ *  - The caller owns every pointer it passes.  Inputs are copied; the
+ *    library never keeps a caller pointer.  The context owns its device
+ *    buffers (allocated in dvm_create, freed in dvm_destroy).
+ *  - Host arrays are plain C arrays; "on_device" pointers are CUDA device
+ *    addresses valid on the context's device.
+ *  - Work is enqueued on the context's stream.  Calls that return host data
+ *    synchronise that stream.
+ *  - Cell index: 2D k = j*nx + i; 3D k = (l*ny + j)*nx + i.
+ *    Velocity index (Sec. 3.1): p = p2*nvx + p1, 3D p = (p3*nvy + p2)*nvx + p1,
+ *    v = vmin + p*(vmax - vmin)/n per axis (vmax itself is not a grid point).
+ *  - State layout in memory: [cell][component][p], 2 components (f, g) in 2D,
+ *    1 (F) in 3D, FP32 or FP64 as chosen at creation.
+ */
+#ifndef DVM_H
+#define DVM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DVM_OK = 0,
+    DVM_ERR_ARG = 1,          /* invalid argument or size                       */
+    DVM_ERR_CFL = 2,          /* time step violates the positivity condition    */
+    DVM_ERR_GEOMETRY = 3,     /* saddle cell, merge walk out of bounds, ...      */
+    DVM_ERR_NONPHYSICAL = 4,  /* non-positive density or temperature            */
+    DVM_ERR_CUDA = 5,         /* a CUDA runtime call failed                      */
+    DVM_ERR_OOM = 6,          /* device allocation failed                        */
+    DVM_ERR_STATE = 7,        /* call out of order (e.g. step before a state)    */
+    DVM_ERR_UNSUPPORTED = 8   /* valid but not implemented combination           */
+} dvm_status;
+
+enum { DVM_FP32 = 32, DVM_FP64 = 64 };
+enum { DVM_UPWIND = 0, DVM_MUSCL = 1 };
+enum { DVM_BC_PERIODIC = 0, DVM_BC_MAXWELLIAN = 1, DVM_BC_ZEROGRAD = 2 };
+enum { DVM_SHAPE_NONE = 0, DVM_SHAPE_CIRCLE = 1, DVM_SHAPE_ELLIPSE = 2, DVM_SHAPE_SPHERE = 3 };
+enum { DVM_GAS = 0, DVM_CUT = 1, DVM_SOLID = 2 };
+
+/* Cartesian grid of Sec. 3.2.1: nx*ny (*nz) cells on the box. */
+typedef struct {
+    int dim;                  /* 2 or 3 */
+    int nx, ny, nz;           /* nz ignored in 2D */
+    double xmin, xmax, ymin, ymax, zmin, zmax;
+} dvm_grid;
+
+/* Discrete velocity grid of Sec. 3.1: n points per axis on [vmin, vmax). */
+typedef struct {
+    int nvx, nvy, nvz;
+    double vxmin, vxmax, vymin, vymax, vzmin, vzmax;
+} dvm_vgrid;
+
+/* Physical and numerical parameters.  R = T0 = rho0 = 1.  The relaxation time
+ * is tau = sqrt(pi)/2 * Kn * Lref / sqrt(2) / rho (Sec. 5).  The time step is
+ * dt if dt > 0, else cfl / sum_d max_p |v_{p,d}| / dx_d. */
+typedef struct {
+    double Kn, Lref, cfl, dt;
+} dvm_physics;
+
+/* Obstacle (Sec. 3.3.4, Appendix A).  Level set: circle/sphere |x-c| - ra;
+ * ellipse with semi-axes ra (along the body x axis) and rb, turned by theta,
+ * first-order distance g/|grad g|.  movable = 1: free rotation about the
+ * centre with moment of inertia `inertia` (Eq. motionDD_vit); the centre and
+ * (vbx, vby) stay fixed.  Wall temperature Tw, or per angular sector when
+ * nseg > 0: sector s spans from direction seg_dir[2s..2s+1] counter-
+ * clockwise to the next one, with temperature Tw_seg[s]. */
+typedef struct {
+    int shape;
+    double cx, cy, cz, ra, rb;
+    double theta, omega;
+    double vbx, vby;
+    double mass, inertia;
+    int movable;
+    double Tw;
+    int nseg;
+    const double *Tw_seg;     /* host, [nseg]   */
+    const double *seg_dir;    /* host, [2*nseg] */
+} dvm_body;
+
+typedef struct dvm_ctx dvm_ctx;
+
+/* Create a solver for one problem on the current CUDA device.
+ * precision: DVM_FP32 (state and transport in FP32; wall density, force,
+ * torque, rigid-body ODE and mass diagnostic in FP64) or DVM_FP64.
+ * scheme: DVM_UPWIND (Eq. FluxDD) or DVM_MUSCL (limited fluxes on full gas
+ * stencils).  stream: a cudaStream_t, or NULL for a stream the context
+ * creates.  All sides start periodic; no obstacle.
+ * Errors: DVM_ERR_ARG (bad sizes), DVM_ERR_OOM, DVM_ERR_CUDA. */
+int dvm_create(const dvm_grid *grid, const dvm_vgrid *vgrid, const dvm_physics *phys,
+               int precision, int scheme, void *stream, dvm_ctx **out);
+
+/* Release every device buffer of the context (NULL is a no-op). */
+void dvm_destroy(dvm_ctx *ctx);
+
+/* Domain boundary of one side (0..5 = x-, x+, y-, y+, z-, z+; Sec. 4 uses
+ * periodic, Maxwellian and zero-gradient sides).  For DVM_BC_MAXWELLIAN,
+ * `state` is a host array of (rho, ux, uy, uz, T) per boundary cell of the
+ * side, ordered by the remaining cell index (2D: j for x sides, i for y
+ * sides; 3D: row-major over the two remaining axes).  Opposite sides must
+ * both be periodic or both not.  Errors: DVM_ERR_ARG. */
+int dvm_set_bc(dvm_ctx *ctx, int side, int kind, const double *state);
+
+/* Place the obstacle and build the Appendix A geometry on the device (level
+ * set, cell types, edge lengths, wall edges, areas, control volumes).
+ * Errors: DVM_ERR_GEOMETRY, DVM_ERR_ARG. */
+int dvm_set_body(dvm_ctx *ctx, const dvm_body *body);
+
+/* Maxwellian initial state from host arrays of per-cell (rho, ux, uy, uz, T);
+ * a NULL array means 0 for velocities, 1 for rho and T.  Solid cells get 0.
+ * Errors: DVM_ERR_STATE (no geometry yet). */
+int dvm_init_maxwellian(dvm_ctx *ctx, const double *rho, const double *ux,
+                        const double *uy, const double *uz, const double *T);
+
+/* Copy a full state in or out.  bytes must equal ncell*ncomp*nv*elem.
+ * on_device = 0: host pointer; 1: device pointer.  Errors: DVM_ERR_ARG. */
+int dvm_set_state(dvm_ctx *ctx, const void *f, size_t bytes, int on_device);
+int dvm_get_state(dvm_ctx *ctx, void *f, size_t bytes, int on_device);
+
+/* Advance nsteps explicit steps (the 7 steps of Sec. 3.3.5), enqueued on
+ * the context's stream without host synchronisation inside the loop.  The
+ * call synchronises once at the end to check the device error flags.
+ * Errors: DVM_ERR_NONPHYSICAL, DVM_ERR_GEOMETRY, DVM_ERR_CUDA. */
+int dvm_step(dvm_ctx *ctx, int nsteps);
+
+/* Same as dvm_step but without the final synchronisation and flag check
+ * (for timing and graph capture); dvm_check() reads the flags later. */
+int dvm_step_async(dvm_ctx *ctx, int nsteps);
+int dvm_check(dvm_ctx *ctx);
+
+/* Per-cell moments of the current state (Eq. MacroscopicDDv): density,
+ * velocity and temperature into host arrays of ncell entries (uz may be NULL
+ * in 2D).  Solid cells give 0. */
+int dvm_moments(dvm_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *T);
+
+/* Force (F[0..2]) and torque about the z axis exerted by the gas on the body
+ * at the start of the last step (Eqs. eq-force, eq-torque), FP64. */
+int dvm_wall_force(dvm_ctx *ctx, double *F, double *torque);
+
+/* Per-step history of the last min(n, steps taken) steps, oldest first:
+ * Fx, Fy, Fz, torque at t^n and theta, omega after the step (any pointer may
+ * be NULL).  Returns the number of entries written through *count. */
+int dvm_history(dvm_ctx *ctx, double *Fx, double *Fy, double *Fz, double *torque,
+                double *theta, double *omega, int n, int *count);
+
+/* Body angle and angular velocity after the last step. */
+int dvm_body_state(dvm_ctx *ctx, double *theta, double *omega);
+
+/* Total mass sum_cells sbar * sum_p f dv (Eq. def-masse), FP64. */
+int dvm_mass(dvm_ctx *ctx, double *mass);
+
+/* Time step, relaxation scale tau0 (tau = tau0/rho), and sizes. */
+int dvm_info(dvm_ctx *ctx, double *dt, double *tau0, long long *ncell, int *nv,
+             int *ncomp, int *elem_bytes);
+
+/* 2D geometry of the current time level, copied to host arrays (any may be
+ * NULL): type/cgas [ncell], lx [(nx+1)*ny], ly [nx*(ny+1)], lw, nwx, nwy,
+ * rwx, rwy, sbar [ncell], master [ncell] (-1 for cells in no control
+ * volume).  Layouts as in Appendix A: vertical edge a of row j at
+ * j*(nx+1)+a, horizontal edge b of column i at b*nx+i. */
+int dvm_geometry2d(dvm_ctx *ctx, int8_t *type, int8_t *cgas, double *lx, double *ly,
+                   double *lw, double *nwx, double *nwy, double *rwx, double *rwy,
+                   double *sbar, int32_t *master);
+
+/* Rebuild the 2D geometry for an explicit (cos theta, sin theta) pair, for
+ * bit-exact comparisons with an independent implementation. */
+int dvm_geometry2d_at(dvm_ctx *ctx, double cos_t, double sin_t);
+
+/* Live timing of the dominant kernel (the fused bulk stream-and-relax
+ * kernel): when enabled, every step records a CUDA event pair around its
+ * launch on the context's stream.  dvm_kernel_time synchronises the stream,
+ * returns the summed duration in milliseconds and the number of timed
+ * launches, and clears the record. */
+int dvm_timing(dvm_ctx *ctx, int enable);
+int dvm_kernel_time(dvm_ctx *ctx, double *bulk_ms, long long *launches);
+
+/* Number of kernels this context has launched since creation. */
+int dvm_launches(dvm_ctx *ctx, long long *count);
+
+/* Cells by role at the current time level: non-solid cells, cells updated by
+ * the bulk kernel, control volumes handled by the cut-cell kernel, wall
+ * cells. */
+int dvm_cell_counts(dvm_ctx *ctx, long long *nonsolid, long long *bulk, long long *cvs,
+                    long long *walls);
+
+/* Thread-local description of the last error. */
+const char *dvm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

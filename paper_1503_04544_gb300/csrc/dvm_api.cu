@@ -1,0 +1,573 @@
+// C-ABI of libdvm: context management, set-up, stepping and read-back.
+// Every entry point returns a dvm_status and records a thread-local message.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dvm_internal.h"
+
+namespace dvm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? DVM_ERR_OOM : DVM_ERR_CUDA;
+}
+
+cudaError_t timing_mark(dvm_ctx *c, int which)
+{
+    if (!c->timing) return cudaSuccess;
+    auto *pool = static_cast<std::vector<cudaEvent_t> *>(c->ev_pool);
+    const size_t need = 2 * (size_t)(c->ev_used + 1);
+    while (pool->size() < need) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        pool->push_back(e);
+    }
+    cudaError_t err = cudaEventRecord((*pool)[2 * c->ev_used + which], c->stream);
+    if (which == 1) c->ev_used++;
+    return err;
+}
+
+Grid2D grid2d(const dvm_ctx *c)
+{
+    Grid2D g;
+    g.nx = c->nx; g.ny = c->ny; g.nvx = c->nvx; g.nvy = c->nvy; g.nv = c->nv;
+    g.xmin = c->xmin; g.ymin = c->ymin; g.dx = c->dx; g.dy = c->dy;
+    g.vxmin = c->vxmin; g.vymin = c->vymin; g.dvx = c->dvx; g.dvy = c->dvy;
+    g.dv = c->dvx * c->dvy;
+    g.dt = c->dt; g.tau0 = c->tau0;
+    for (int s = 0; s < 4; ++s) g.bc[s] = c->bc[s];
+    g.i0 = c->i0; g.i1 = c->i1; g.j0 = c->j0; g.j1 = c->j1;
+    return g;
+}
+
+BodyParams body_params(const dvm_ctx *c)
+{
+    BodyParams b;
+    b.shape = c->body.shape; b.movable = c->body.movable; b.nseg = c->body.nseg;
+    b.cx = c->body.cx; b.cy = c->body.cy; b.cz = c->body.cz; b.ra = c->body.ra; b.rb = c->body.rb;
+    b.vbx = c->body.vbx; b.vby = c->body.vby; b.mass = c->body.mass; b.inertia = c->body.inertia;
+    b.Tw = c->body.Tw; b.Tw_seg = c->d_Twseg; b.seg_dir = c->d_segdir;
+    return b;
+}
+
+}  // namespace dvm
+
+using namespace dvm;
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+static double axis_vmax(int n, double vmin, double vmax)
+{
+    double dv = (vmax - vmin) / n;
+    double a = std::fabs(vmin), b = std::fabs(vmin + (n - 1) * dv);
+    return a > b ? a : b;
+}
+
+static int side_cells(const dvm_ctx *c, int side)
+{
+    if (c->dim == 2) return side < 2 ? c->ny : c->nx;
+    if (side < 2) return c->ny * c->nz;
+    if (side < 4) return c->nx * c->nz;
+    return c->nx * c->ny;
+}
+
+template <typename P> static cudaError_t dalloc(P **p, size_t bytes)
+{
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void **)p, bytes > 0 ? bytes : 16);
+    return e;
+}
+
+static void free_geo(dvm::Geo2D &G)
+{
+    cudaFree(G.phi); cudaFree(G.type); cudaFree(G.cgas); cudaFree(G.lx); cudaFree(G.ly);
+    cudaFree(G.lw); cudaFree(G.nwx); cudaFree(G.nwy); cudaFree(G.rwx); cudaFree(G.rwy);
+    cudaFree(G.sbar);
+    std::memset(&G, 0, sizeof(G));
+}
+
+static int check_flags(dvm_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->h_err, c->d_err, kErrCount * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int rc = DVM_OK;
+    if (c->h_err[kErrGeometry]) { set_error("geometry: saddle cell or master search left its bounds"); rc = DVM_ERR_GEOMETRY; }
+    else if (c->h_err[kErrCapacity]) { set_error("geometry: control-volume list or member capacity exceeded"); rc = DVM_ERR_GEOMETRY; }
+    else if (c->h_err[kErrNonphys]) { set_error("non-positive density or temperature"); rc = DVM_ERR_NONPHYSICAL; }
+    if (rc != DVM_OK) {
+        // report once: the flags are cleared so that the context stays usable
+        CK(cudaMemsetAsync(c->d_err, 0, kErrCount * sizeof(int), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return rc;
+}
+
+extern "C" {
+
+const char *dvm_last_error(void) { return g_last_error.c_str(); }
+
+int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph, int precision,
+               int scheme, void *stream, dvm_ctx **out)
+{
+    if (!grid || !vg || !ph || !out) { set_error("null argument"); return DVM_ERR_ARG; }
+    *out = nullptr;
+    if (grid->dim != 2) { set_error("only dim = 2 is built in this library version"); return DVM_ERR_UNSUPPORTED; }
+    if (grid->nx < 2 || grid->ny < 1 || vg->nvx < 1 || vg->nvy < 1) { set_error("grid sizes"); return DVM_ERR_ARG; }
+    if (vg->nvx > kMaxAxisNv || vg->nvy > kMaxAxisNv) { set_error("at most 64 velocities per axis"); return DVM_ERR_ARG; }
+    if (precision != DVM_FP32 && precision != DVM_FP64) { set_error("precision must be 32 or 64"); return DVM_ERR_ARG; }
+    if (scheme != DVM_UPWIND && scheme != DVM_MUSCL) { set_error("scheme"); return DVM_ERR_ARG; }
+    if (!(grid->xmax > grid->xmin) || !(grid->ymax > grid->ymin) || !(vg->vxmax > vg->vxmin) ||
+        !(vg->vymax > vg->vymin) || !(ph->Kn > 0) || !(ph->Lref > 0)) {
+        set_error("empty box, velocity window or non-positive Kn/Lref"); return DVM_ERR_ARG;
+    }
+    dvm_ctx *c = new (std::nothrow) dvm_ctx();
+    if (!c) { set_error("host allocation"); return DVM_ERR_OOM; }
+    std::memset((void *)c, 0, sizeof(*c));
+    c->dim = 2; c->nx = grid->nx; c->ny = grid->ny; c->nz = 1;
+    c->xmin = grid->xmin; c->xmax = grid->xmax; c->ymin = grid->ymin; c->ymax = grid->ymax;
+    c->dx = (c->xmax - c->xmin) / c->nx;
+    c->dy = (c->ymax - c->ymin) / c->ny;
+    c->nvx = vg->nvx; c->nvy = vg->nvy; c->nvz = 1; c->nv = c->nvx * c->nvy;
+    c->vxmin = vg->vxmin; c->vxmax = vg->vxmax; c->vymin = vg->vymin; c->vymax = vg->vymax;
+    c->dvx = (c->vxmax - c->vxmin) / c->nvx;
+    c->dvy = (c->vymax - c->vymin) / c->nvy;
+    c->Kn = ph->Kn; c->Lref = ph->Lref; c->cfl = ph->cfl;
+    // tau = sqrt(pi)/2 (rho0/rho) Kn L / sqrt(2 R T0), Sec. 5, R = T0 = rho0 = 1
+    c->tau0 = std::sqrt(M_PI) / 2.0 * c->Kn * c->Lref / std::sqrt(2.0);
+    if (ph->dt > 0) c->dt = ph->dt;
+    else {
+        double s = axis_vmax(c->nvx, c->vxmin, c->vxmax) / c->dx + axis_vmax(c->nvy, c->vymin, c->vymax) / c->dy;
+        c->dt = c->cfl / s;
+    }
+    if (!(c->dt > 0)) { delete c; set_error("time step"); return DVM_ERR_CFL; }
+    c->prec = precision; c->scheme = scheme; c->ncomp = 2;
+    c->elem = precision == DVM_FP32 ? 4 : 8;
+    c->nc = (long long)c->nx * c->ny;
+    c->state_elems = (size_t)c->nc * c->ncomp * c->nv;
+    if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
+    else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreate"); }
+        c->own_stream = true;
+    }
+    for (int s = 0; s < 6; ++s) c->bc[s] = DVM_BC_PERIODIC;
+    c->body.shape = DVM_SHAPE_NONE;
+    c->i0 = c->i1 = c->j0 = c->j1 = 0;
+    const size_t nc = (size_t)c->nc;
+    cudaError_t e = cudaSuccess;
+#define AL(p, b) if (e == cudaSuccess) e = dalloc(&(p), (b))
+    AL(c->f[0], c->state_elems * c->elem);
+    AL(c->f[1], c->state_elems * c->elem);
+    AL(c->mom, nc * 8 * c->elem);
+    for (int l = 0; l < 2; ++l) {
+        dvm::Geo2D &G = c->geo[l];
+        AL(G.phi, sizeof(double) * (c->nx + 1) * (c->ny + 1));
+        AL(G.type, nc); AL(G.cgas, nc);
+        AL(G.lx, sizeof(double) * (c->nx + 1) * c->ny);
+        AL(G.ly, sizeof(double) * c->nx * (c->ny + 1));
+        AL(G.lw, sizeof(double) * nc); AL(G.nwx, sizeof(double) * nc); AL(G.nwy, sizeof(double) * nc);
+        AL(G.rwx, sizeof(double) * nc); AL(G.rwy, sizeof(double) * nc); AL(G.sbar, sizeof(double) * nc);
+    }
+    AL(c->master, sizeof(int32_t) * nc);
+    AL(c->flags, nc);
+    AL(c->hs, nc);
+    AL(c->wphi, sizeof(double) * nc); AL(c->wux, sizeof(double) * nc);
+    AL(c->wuy, sizeof(double) * nc); AL(c->wT, sizeof(double) * nc);
+    AL(c->counts, sizeof(int32_t) * 4);
+    AL(c->d_body, sizeof(dvm::BodyDev));
+    AL(c->d_hist, sizeof(double) * 6 * kHistCap);
+    AL(c->d_err, sizeof(int) * kErrCount);
+    AL(c->d_scratch, sizeof(double) * nc);
+    AL(c->d_out, sizeof(double) * nc * 5);
+#undef AL
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_err, sizeof(int) * kErrCount);
+    if (e != cudaSuccess) { int rc = cuda_fail(e, "dvm_create allocation"); dvm_destroy(c); return rc; }
+    cudaMemsetAsync(c->f[0], 0, c->state_elems * c->elem, c->stream);
+    cudaMemsetAsync(c->f[1], 0, c->state_elems * c->elem, c->stream);
+    cudaMemsetAsync(c->mom, 0, nc * 8 * c->elem, c->stream);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int) * kErrCount, c->stream);
+    cudaMemsetAsync(c->d_body, 0, sizeof(dvm::BodyDev), c->stream);
+    cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 6 * kHistCap, c->stream);
+    cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4, c->stream);
+    e = init_static_geometry2d(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { int rc = cuda_fail(e, "dvm_create init"); dvm_destroy(c); return rc; }
+    c->have_geo = true;
+    c->ev_pool = new (std::nothrow) std::vector<cudaEvent_t>();
+    if (!c->ev_pool) { dvm_destroy(c); set_error("host allocation"); return DVM_ERR_OOM; }
+    *out = c;
+    return DVM_OK;
+}
+
+void dvm_destroy(dvm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->mom);
+    for (int l = 0; l < 2; ++l) free_geo(c->geo[l]);
+    cudaFree(c->master); cudaFree(c->flags); cudaFree(c->hs);
+    cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->counts);
+    cudaFree(c->wphi); cudaFree(c->wux); cudaFree(c->wuy); cudaFree(c->wT); cudaFree(c->wcontrib);
+    cudaFree(c->d_body); cudaFree(c->d_hist); cudaFree(c->d_err);
+    cudaFree(c->d_scratch); cudaFree(c->d_out);
+    cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
+    for (int s = 0; s < 6; ++s) cudaFree(c->ghost[s]);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->ev_pool) {
+        auto *pool = static_cast<std::vector<cudaEvent_t> *>(c->ev_pool);
+        for (cudaEvent_t e : *pool) cudaEventDestroy(e);
+        delete pool;
+    }
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int dvm_set_bc(dvm_ctx *c, int side, int kind, const double *state)
+{
+    if (!c || side < 0 || side >= 2 * c->dim) { set_error("side"); return DVM_ERR_ARG; }
+    if (kind != DVM_BC_PERIODIC && kind != DVM_BC_MAXWELLIAN && kind != DVM_BC_ZEROGRAD) { set_error("kind"); return DVM_ERR_ARG; }
+    if (kind == DVM_BC_MAXWELLIAN && !state) { set_error("Maxwellian side needs a state"); return DVM_ERR_ARG; }
+    const int n = side_cells(c, side);
+    if (kind == DVM_BC_MAXWELLIAN) {
+        for (int q = 0; q < n; ++q)
+            if (!(state[5 * q] > 0) || !(state[5 * q + 4] > 0)) { set_error("Maxwellian side: rho and T must be > 0"); return DVM_ERR_ARG; }
+        if (!c->ghost[side]) CK(cudaMalloc(&c->ghost[side], (size_t)n * c->ncomp * c->nv * c->elem));
+        double *d = nullptr;
+        CK(cudaMalloc(&d, sizeof(double) * 5 * n));
+        cudaError_t e = cudaMemcpyAsync(d, state, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = ghost2d(c, side, d, n);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(d);
+        if (e != cudaSuccess) return cuda_fail(e, "dvm_set_bc");
+    }
+    c->bc[side] = kind;
+    // flags depend on the periodicity of the sides through the limiter masks
+    if (c->body.shape != DVM_SHAPE_NONE) {
+        cudaError_t e = masters_flags2d(c, false);
+        if (e != cudaSuccess) return cuda_fail(e, "dvm_set_bc flags");
+        return check_flags(c);
+    }
+    return DVM_OK;
+}
+
+int dvm_set_body(dvm_ctx *c, const dvm_body *b)
+{
+    if (!c || !b) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (b->shape != DVM_SHAPE_NONE && b->shape != DVM_SHAPE_CIRCLE && b->shape != DVM_SHAPE_ELLIPSE) {
+        set_error("2D shapes: none, circle, ellipse"); return DVM_ERR_UNSUPPORTED;
+    }
+    if (b->shape != DVM_SHAPE_NONE && (!(b->ra > 0) || (b->shape == DVM_SHAPE_ELLIPSE && !(b->rb > 0)))) {
+        set_error("body size"); return DVM_ERR_ARG;
+    }
+    if (b->movable && !(b->inertia > 0)) { set_error("movable body needs inertia > 0"); return DVM_ERR_ARG; }
+    if (b->nseg > 0 && (!b->Tw_seg || !b->seg_dir)) { set_error("nseg > 0 needs Tw_seg and seg_dir"); return DVM_ERR_ARG; }
+    c->body = *b;
+    c->body.Tw_seg = nullptr; c->body.seg_dir = nullptr;
+    cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
+    c->d_Twseg = c->d_segdir = nullptr;
+    if (b->nseg > 0) {
+        CK(cudaMalloc(&c->d_Twseg, sizeof(double) * b->nseg));
+        CK(cudaMalloc(&c->d_segdir, sizeof(double) * 2 * b->nseg));
+        CK(cudaMemcpy(c->d_Twseg, b->Tw_seg, sizeof(double) * b->nseg, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_segdir, b->seg_dir, sizeof(double) * 2 * b->nseg, cudaMemcpyHostToDevice));
+    }
+    c->moving = b->shape != DVM_SHAPE_NONE && b->movable;
+    // box of cells that can be non-gas or have a non-gas cell within reach
+    if (b->shape == DVM_SHAPE_NONE) {
+        c->i0 = c->i1 = c->j0 = c->j1 = 0;
+    } else {
+        const double R = b->shape == DVM_SHAPE_ELLIPSE ? std::fmax(b->ra, b->rb) : b->ra;
+        auto lo = [](double v, double h, int n) { int q = (int)std::floor(v / h) - kBoxMargin; return q < 0 ? 0 : (q > n ? n : q); };
+        auto hi = [](double v, double h, int n) { int q = (int)std::ceil(v / h) + kBoxMargin; return q < 0 ? 0 : (q > n ? n : q); };
+        c->i0 = lo(b->cx - R - c->xmin, c->dx, c->nx); c->i1 = hi(b->cx + R - c->xmin, c->dx, c->nx);
+        c->j0 = lo(b->cy - R - c->ymin, c->dy, c->ny); c->j1 = hi(b->cy + R - c->ymin, c->dy, c->ny);
+    }
+    const int nbox = (c->i1 - c->i0) * (c->j1 - c->j0);
+    cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->wcontrib);
+    c->list_cap = nbox > 0 ? nbox : 1;
+    CK(cudaMalloc(&c->spec_list, sizeof(int32_t) * c->list_cap));
+    CK(cudaMalloc(&c->wall_list, sizeof(int32_t) * c->list_cap));
+    CK(cudaMalloc(&c->wcontrib, sizeof(double) * 3 * c->list_cap));
+    CK(cudaMemsetAsync(c->wcontrib, 0, sizeof(double) * 3 * c->list_cap, c->stream));
+    dvm::BodyDev hb;
+    std::memset(&hb, 0, sizeof(hb));
+    hb.theta = b->theta; hb.omega = b->omega; hb.theta1 = b->theta;
+    hb.trig[0] = std::cos(b->theta); hb.trig[1] = std::sin(b->theta);
+    hb.trig[2] = hb.trig[0]; hb.trig[3] = hb.trig[1];
+    CK(cudaMemcpyAsync(c->d_body, &hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int) * kErrCount, c->stream));
+    c->gcur = 0;
+    CK(init_static_geometry2d(c));
+    if (b->shape != DVM_SHAPE_NONE) {
+        CK(geometry2d_level(c, 0, body_trig(c, 0)));
+        CK(geometry2d_level(c, 1, body_trig(c, 0)));
+        CK(masters_flags2d(c, false));
+    }
+    c->need_fusion = true;
+    c->steps_done = 0;
+    return check_flags(c);
+}
+
+int dvm_geometry2d_at(dvm_ctx *c, double cos_t, double sin_t)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (c->body.shape == DVM_SHAPE_NONE) return DVM_OK;
+    double t[2] = {cos_t, sin_t};
+    CK(cudaMemcpyAsync(body_trig(c, 0), t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
+    CK(geometry2d_level(c, c->gcur, body_trig(c, 0)));
+    CK(masters_flags2d(c, false));
+    c->need_fusion = true;
+    return check_flags(c);
+}
+
+int dvm_init_maxwellian(dvm_ctx *c, const double *rho, const double *ux, const double *uy,
+                        const double *uz, const double *T)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    const size_t nc = (size_t)c->nc;
+    std::vector<double> prim(5 * nc);
+    for (size_t k = 0; k < nc; ++k) {
+        prim[5 * k] = rho ? rho[k] : 1.0;
+        prim[5 * k + 1] = ux ? ux[k] : 0.0;
+        prim[5 * k + 2] = uy ? uy[k] : 0.0;
+        prim[5 * k + 3] = uz ? uz[k] : 0.0;
+        prim[5 * k + 4] = T ? T[k] : 1.0;
+        if (prim[5 * k] > 0 && !(prim[5 * k + 4] > 0)) { set_error("T must be > 0"); return DVM_ERR_ARG; }
+    }
+    double *d = c->d_out;      // nc*5 doubles
+    CK(cudaMemcpyAsync(d, prim.data(), sizeof(double) * 5 * nc, cudaMemcpyHostToDevice, c->stream));
+    CK(init_maxwellian2d(c, d));
+    CK(cudaMemsetAsync(c->f[1 - c->cur], 0, c->state_elems * c->elem, c->stream));
+    CK(moments2d(c));
+    c->have_state = true;
+    c->need_fusion = true;
+    return check_flags(c);
+}
+
+int dvm_set_state(dvm_ctx *c, const void *f, size_t bytes, int on_device)
+{
+    if (!c || !f) { set_error("null"); return DVM_ERR_ARG; }
+    if (bytes != c->state_elems * c->elem) { set_error("state size mismatch"); return DVM_ERR_ARG; }
+    CK(cudaMemcpyAsync(c->f[c->cur], f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->f[1 - c->cur], 0, bytes, c->stream));
+    CK(moments2d(c));
+    c->have_state = true;
+    c->need_fusion = true;
+    CK(cudaStreamSynchronize(c->stream));
+    return DVM_OK;
+}
+
+int dvm_get_state(dvm_ctx *c, void *f, size_t bytes, int on_device)
+{
+    if (!c || !f) { set_error("null"); return DVM_ERR_ARG; }
+    if (bytes != c->state_elems * c->elem) { set_error("state size mismatch"); return DVM_ERR_ARG; }
+    CK(cudaMemcpyAsync(f, c->f[c->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return DVM_OK;
+}
+
+int dvm_step_async(dvm_ctx *c, int nsteps)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
+    if (nsteps < 0) { set_error("nsteps < 0"); return DVM_ERR_ARG; }
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = step2d(c);
+        if (e != cudaSuccess) return cuda_fail(e, "dvm_step");
+    }
+    return DVM_OK;
+}
+
+int dvm_check(dvm_ctx *c)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    return check_flags(c);
+}
+
+int dvm_step(dvm_ctx *c, int nsteps)
+{
+    int rc = dvm_step_async(c, nsteps);
+    if (rc != DVM_OK) return rc;
+    return check_flags(c);
+}
+
+int dvm_moments(dvm_ctx *c, double *rho, double *ux, double *uy, double *uz, double *T)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    const size_t nc = (size_t)c->nc;
+    CK(moments_out2d(c, c->d_out));
+    std::vector<double> h(5 * nc);
+    CK(cudaMemcpyAsync(h.data(), c->d_out, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < nc; ++k) {
+        if (rho) rho[k] = h[5 * k];
+        if (ux) ux[k] = h[5 * k + 1];
+        if (uy) uy[k] = h[5 * k + 2];
+        if (uz) uz[k] = h[5 * k + 3];
+        if (T) T[k] = h[5 * k + 4];
+    }
+    return DVM_OK;
+}
+
+int dvm_wall_force(dvm_ctx *c, double *F, double *torque)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    dvm::BodyDev hb;
+    CK(cudaMemcpyAsync(&hb, c->d_body, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (F) { F[0] = hb.F[0]; F[1] = hb.F[1]; F[2] = hb.F[2]; }
+    if (torque) *torque = hb.torque;
+    return DVM_OK;
+}
+
+int dvm_body_state(dvm_ctx *c, double *theta, double *omega)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    dvm::BodyDev hb;
+    CK(cudaMemcpyAsync(&hb, c->d_body, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (theta) *theta = hb.theta;
+    if (omega) *omega = hb.omega;
+    return DVM_OK;
+}
+
+int dvm_history(dvm_ctx *c, double *Fx, double *Fy, double *Fz, double *torque, double *theta,
+                double *omega, int n, int *count)
+{
+    if (!c || n < 0) { set_error("bad argument"); return DVM_ERR_ARG; }
+    long long avail = c->steps_done < kHistCap ? c->steps_done : kHistCap;
+    long long m = n < avail ? n : avail;
+    std::vector<double> h(6 * (size_t)kHistCap);
+    CK(cudaMemcpyAsync(h.data(), c->d_hist, sizeof(double) * 6 * kHistCap, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (long long q = 0; q < m; ++q) {
+        long long step = c->steps_done - m + q;
+        const double *r = &h[6 * (size_t)(step % kHistCap)];
+        if (Fx) Fx[q] = r[0];
+        if (Fy) Fy[q] = r[1];
+        if (Fz) Fz[q] = r[2];
+        if (torque) torque[q] = r[3];
+        if (theta) theta[q] = r[4];
+        if (omega) omega[q] = r[5];
+    }
+    if (count) *count = (int)m;
+    return DVM_OK;
+}
+
+int dvm_mass(dvm_ctx *c, double *mass)
+{
+    if (!c || !mass) { set_error("null"); return DVM_ERR_ARG; }
+    double *d = c->d_out;
+    CK(mass2d(c, c->d_scratch, d));
+    CK(cudaMemcpyAsync(mass, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return DVM_OK;
+}
+
+int dvm_info(dvm_ctx *c, double *dt, double *tau0, long long *ncell, int *nv, int *ncomp, int *elem)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (dt) *dt = c->dt;
+    if (tau0) *tau0 = c->tau0;
+    if (ncell) *ncell = c->nc;
+    if (nv) *nv = c->nv;
+    if (ncomp) *ncomp = c->ncomp;
+    if (elem) *elem = c->elem;
+    return DVM_OK;
+}
+
+int dvm_geometry2d(dvm_ctx *c, int8_t *type, int8_t *cgas, double *lx, double *ly, double *lw,
+                   double *nwx, double *nwy, double *rwx, double *rwy, double *sbar, int32_t *master)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    const dvm::Geo2D &G = c->geo[c->gcur];
+    const size_t nc = (size_t)c->nc;
+    auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream) : cudaSuccess;
+    };
+    CK(cp(type, G.type, nc));
+    CK(cp(cgas, G.cgas, nc));
+    CK(cp(lx, G.lx, sizeof(double) * (c->nx + 1) * c->ny));
+    CK(cp(ly, G.ly, sizeof(double) * c->nx * (c->ny + 1)));
+    CK(cp(lw, G.lw, sizeof(double) * nc));
+    CK(cp(nwx, G.nwx, sizeof(double) * nc));
+    CK(cp(nwy, G.nwy, sizeof(double) * nc));
+    CK(cp(rwx, G.rwx, sizeof(double) * nc));
+    CK(cp(rwy, G.rwy, sizeof(double) * nc));
+    CK(cp(sbar, G.sbar, sizeof(double) * nc));
+    CK(cp(master, c->master, sizeof(int32_t) * nc));
+    CK(cudaStreamSynchronize(c->stream));
+    return DVM_OK;
+}
+
+int dvm_timing(dvm_ctx *c, int enable)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    c->timing = enable != 0;
+    c->ev_used = 0;
+    return DVM_OK;
+}
+
+int dvm_kernel_time(dvm_ctx *c, double *bulk_ms, long long *launches)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    CK(cudaStreamSynchronize(c->stream));
+    auto *pool = static_cast<std::vector<cudaEvent_t> *>(c->ev_pool);
+    double tot = 0;
+    for (int q = 0; q < c->ev_used; ++q) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, (*pool)[2 * q], (*pool)[2 * q + 1]));
+        tot += ms;
+    }
+    if (bulk_ms) *bulk_ms = tot;
+    if (launches) *launches = c->ev_used;
+    c->ev_used = 0;
+    return DVM_OK;
+}
+
+int dvm_launches(dvm_ctx *c, long long *count)
+{
+    if (!c || !count) { set_error("null"); return DVM_ERR_ARG; }
+    *count = c->launches;
+    return DVM_OK;
+}
+
+int dvm_cell_counts(dvm_ctx *c, long long *nonsolid, long long *bulk, long long *cvs, long long *walls)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    const size_t nc = (size_t)c->nc;
+    std::vector<uint8_t> fl(nc);
+    std::vector<int8_t> ty(nc);
+    int32_t cnt[2] = {0, 0};
+    CK(cudaMemcpyAsync(fl.data(), c->flags, nc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(ty.data(), c->geo[c->gcur].type, nc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(cnt, c->counts, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    long long ns = 0, nb = 0;
+    for (size_t k = 0; k < nc; ++k) {
+        ns += ty[k] != DVM_SOLID;
+        nb += (fl[k] & kPlain) != 0;
+    }
+    const bool body = c->body.shape != DVM_SHAPE_NONE;
+    if (nonsolid) *nonsolid = ns;
+    if (bulk) *bulk = nb;
+    if (cvs) *cvs = body ? cnt[0] : 0;
+    if (walls) *walls = body ? cnt[1] : 0;
+    return DVM_OK;
+}
+
+}  // extern "C"
