@@ -125,7 +125,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[q] for r in rows for q in range(4) if "Active" in r[5 + q]})
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
@@ -197,7 +197,10 @@ def main():
 
     cfg = workload(args.workload)
     prec = dvm.FP32 if args.precision == "fp32" else dvm.FP64
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library enqueues on it and the events below
+    # are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     s = dvm.Solver(cfg, prec, stream=stream.cuda_stream)
     s.init_maxwellian()
     s.step(max(args.warmup, 3))

@@ -41,6 +41,8 @@ Grid2D grid2d(const dvm_ctx *c)
 {
     Grid2D g;
     g.nx = c->nx; g.ny = c->ny; g.nvx = c->nvx; g.nvy = c->nvy; g.nv = c->nv;
+    g.W = c->W; g.nvp = c->nvp; g.ngrp = c->ngrp; g.slab = c->slab;
+    for (int s = 0; s < 4; ++s) g.gofs[s] = c->gofs[s];
     g.xmin = c->xmin; g.ymin = c->ymin; g.dx = c->dx; g.dy = c->dy;
     g.vxmin = c->vxmin; g.vymin = c->vymin; g.dvx = c->dvx; g.dvy = c->dvy;
     g.dv = c->dvx * c->dvy;
@@ -59,6 +61,8 @@ BodyParams body_params(const dvm_ctx *c)
     b.Tw = c->body.Tw; b.Tw_seg = c->d_Twseg; b.seg_dir = c->d_segdir;
     return b;
 }
+
+size_t vcoef_bytes(int prec);
 
 }  // namespace dvm
 
@@ -108,6 +112,7 @@ static int check_flags(dvm_ctx *c)
     if (c->h_err[kErrGeometry]) { set_error("geometry: saddle cell or master search left its bounds"); rc = DVM_ERR_GEOMETRY; }
     else if (c->h_err[kErrCapacity]) { set_error("geometry: control-volume list or member capacity exceeded"); rc = DVM_ERR_GEOMETRY; }
     else if (c->h_err[kErrNonphys]) { set_error("non-positive density or temperature"); rc = DVM_ERR_NONPHYSICAL; }
+    else if (c->h_err[kErrTimeout]) { set_error("a bounded wait on a TMA transfer timed out"); rc = DVM_ERR_CUDA; }
     if (rc != DVM_OK) {
         // report once: the flags are cleared so that the context stays usable
         CK(cudaMemsetAsync(c->d_err, 0, kErrCount * sizeof(int), c->stream));
@@ -158,6 +163,21 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     c->elem = precision == DVM_FP32 ? 4 : 8;
     c->nc = (long long)c->nx * c->ny;
     c->state_elems = (size_t)c->nc * c->ncomp * c->nv;
+    c->W = 16 / c->elem;
+    c->nvp = (c->nv + c->W - 1) / c->W * c->W;
+    c->ngrp = c->nvp / c->W;
+    c->gofs[0] = 0; c->gofs[1] = c->ny; c->gofs[2] = 2 * c->ny; c->gofs[3] = 2 * c->ny + c->nx;
+    c->slab = (long)c->nc + 2L * (c->nx + c->ny);
+    c->dev_elems = (size_t)c->ngrp * c->ncomp * c->slab * c->W;
+    {
+        // velocity splits: enough blocks for a few waves on 152 SMs
+        const long bxy = (long)((c->nx + 31) / 32) * ((c->ny + kRows - 1) / kRows);
+        int S = (int)((1200 + bxy - 1) / bxy);
+        if (S < 1) S = 1;
+        if (S > 16) S = 16;
+        if (S > c->ngrp) S = c->ngrp;
+        c->S = S;
+    }
     if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
     else {
         cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -170,9 +190,14 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     const size_t nc = (size_t)c->nc;
     cudaError_t e = cudaSuccess;
 #define AL(p, b) if (e == cudaSuccess) e = dalloc(&(p), (b))
-    AL(c->f[0], c->state_elems * c->elem);
-    AL(c->f[1], c->state_elems * c->elem);
-    AL(c->mom, nc * 8 * c->elem);
+    AL(c->f[0], c->dev_elems * c->elem);
+    AL(c->f[1], c->dev_elems * c->elem);
+    AL(c->part[0], (size_t)c->S * 4 * nc * c->elem);
+    AL(c->part[1], (size_t)c->S * 4 * nc * c->elem);
+    AL(c->vtab, (size_t)c->nvp * vcoef_bytes(c->prec));
+    AL(c->gsign, (size_t)2 * c->ngrp);
+    AL(c->wslot, sizeof(int32_t) * nc);
+    AL(c->ticket, sizeof(int));
     for (int l = 0; l < 2; ++l) {
         dvm::Geo2D &G = c->geo[l];
         AL(G.phi, sizeof(double) * (c->nx + 1) * (c->ny + 1));
@@ -185,8 +210,6 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     AL(c->master, sizeof(int32_t) * nc);
     AL(c->flags, nc);
     AL(c->hs, nc);
-    AL(c->wphi, sizeof(double) * nc); AL(c->wux, sizeof(double) * nc);
-    AL(c->wuy, sizeof(double) * nc); AL(c->wT, sizeof(double) * nc);
     AL(c->counts, sizeof(int32_t) * 4);
     AL(c->d_body, sizeof(dvm::BodyDev));
     AL(c->d_hist, sizeof(double) * 6 * kHistCap);
@@ -196,14 +219,21 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_err, sizeof(int) * kErrCount);
     if (e != cudaSuccess) { int rc = cuda_fail(e, "dvm_create allocation"); dvm_destroy(c); return rc; }
-    cudaMemsetAsync(c->f[0], 0, c->state_elems * c->elem, c->stream);
-    cudaMemsetAsync(c->f[1], 0, c->state_elems * c->elem, c->stream);
-    cudaMemsetAsync(c->mom, 0, nc * 8 * c->elem, c->stream);
+    cudaMemsetAsync(c->f[0], 0, c->dev_elems * c->elem, c->stream);
+    cudaMemsetAsync(c->f[1], 0, c->dev_elems * c->elem, c->stream);
+    cudaMemsetAsync(c->part[0], 0, (size_t)c->S * 4 * nc * c->elem, c->stream);
+    cudaMemsetAsync(c->part[1], 0, (size_t)c->S * 4 * nc * c->elem, c->stream);
+    cudaMemsetAsync(c->ticket, 0, sizeof(int), c->stream);
     cudaMemsetAsync(c->d_err, 0, sizeof(int) * kErrCount, c->stream);
     cudaMemsetAsync(c->d_body, 0, sizeof(dvm::BodyDev), c->stream);
     cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 6 * kHistCap, c->stream);
     cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4, c->stream);
+    {
+        int rc = make_tensor_maps2d(c);
+        if (rc != DVM_OK) { dvm_destroy(c); return rc; }
+    }
     e = init_static_geometry2d(c);
+    if (e == cudaSuccess) e = tables2d(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { int rc = cuda_fail(e, "dvm_create init"); dvm_destroy(c); return rc; }
     c->have_geo = true;
@@ -217,15 +247,16 @@ void dvm_destroy(dvm_ctx *c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->mom);
+    cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->part[0]); cudaFree(c->part[1]);
+    cudaFree(c->vtab); cudaFree(c->gsign); cudaFree(c->wslot); cudaFree(c->ticket);
+    cudaFree(c->wflux); cudaFree(c->d_pub);
     for (int l = 0; l < 2; ++l) free_geo(c->geo[l]);
     cudaFree(c->master); cudaFree(c->flags); cudaFree(c->hs);
     cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->counts);
-    cudaFree(c->wphi); cudaFree(c->wux); cudaFree(c->wuy); cudaFree(c->wT); cudaFree(c->wcontrib);
+    cudaFree(c->wphi); cudaFree(c->wcontrib);
     cudaFree(c->d_body); cudaFree(c->d_hist); cudaFree(c->d_err);
     cudaFree(c->d_scratch); cudaFree(c->d_out);
     cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
-    for (int s = 0; s < 6; ++s) cudaFree(c->ghost[s]);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->ev_pool) {
         auto *pool = static_cast<std::vector<cudaEvent_t> *>(c->ev_pool);
@@ -245,7 +276,6 @@ int dvm_set_bc(dvm_ctx *c, int side, int kind, const double *state)
     if (kind == DVM_BC_MAXWELLIAN) {
         for (int q = 0; q < n; ++q)
             if (!(state[5 * q] > 0) || !(state[5 * q + 4] > 0)) { set_error("Maxwellian side: rho and T must be > 0"); return DVM_ERR_ARG; }
-        if (!c->ghost[side]) CK(cudaMalloc(&c->ghost[side], (size_t)n * c->ncomp * c->nv * c->elem));
         double *d = nullptr;
         CK(cudaMalloc(&d, sizeof(double) * 5 * n));
         cudaError_t e = cudaMemcpyAsync(d, state, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, c->stream);
@@ -297,12 +327,17 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
         c->j0 = lo(b->cy - R - c->ymin, c->dy, c->ny); c->j1 = hi(b->cy + R - c->ymin, c->dy, c->ny);
     }
     const int nbox = (c->i1 - c->i0) * (c->j1 - c->j0);
-    cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->wcontrib);
+    cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->wcontrib); cudaFree(c->wphi);
+    cudaFree(c->wflux);
+    c->spec_list = c->wall_list = nullptr; c->wcontrib = c->wphi = nullptr; c->wflux = nullptr;
     c->list_cap = nbox > 0 ? nbox : 1;
     CK(cudaMalloc(&c->spec_list, sizeof(int32_t) * c->list_cap));
     CK(cudaMalloc(&c->wall_list, sizeof(int32_t) * c->list_cap));
     CK(cudaMalloc(&c->wcontrib, sizeof(double) * 3 * c->list_cap));
+    CK(cudaMalloc(&c->wphi, sizeof(double) * c->list_cap));
+    CK(cudaMalloc(&c->wflux, (size_t)c->list_cap * 2 * c->nv * c->elem));
     CK(cudaMemsetAsync(c->wcontrib, 0, sizeof(double) * 3 * c->list_cap, c->stream));
+    CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4, c->stream));
     dvm::BodyDev hb;
     std::memset(&hb, 0, sizeof(hb));
     hb.theta = b->theta; hb.omega = b->omega; hb.theta1 = b->theta;
@@ -351,20 +386,29 @@ int dvm_init_maxwellian(dvm_ctx *c, const double *rho, const double *ux, const d
     double *d = c->d_out;      // nc*5 doubles
     CK(cudaMemcpyAsync(d, prim.data(), sizeof(double) * 5 * nc, cudaMemcpyHostToDevice, c->stream));
     CK(init_maxwellian2d(c, d));
-    CK(cudaMemsetAsync(c->f[1 - c->cur], 0, c->state_elems * c->elem, c->stream));
-    CK(moments2d(c));
+    CK(zero_solid2d(c));
+    CK(partials_from_state2d(c));
     c->have_state = true;
     c->need_fusion = true;
     return check_flags(c);
+}
+
+static int ensure_pub(dvm_ctx *c)
+{
+    if (!c->d_pub) CK(cudaMalloc(&c->d_pub, c->state_elems * c->elem));
+    return DVM_OK;
 }
 
 int dvm_set_state(dvm_ctx *c, const void *f, size_t bytes, int on_device)
 {
     if (!c || !f) { set_error("null"); return DVM_ERR_ARG; }
     if (bytes != c->state_elems * c->elem) { set_error("state size mismatch"); return DVM_ERR_ARG; }
-    CK(cudaMemcpyAsync(c->f[c->cur], f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(c->f[1 - c->cur], 0, bytes, c->stream));
-    CK(moments2d(c));
+    int rc = ensure_pub(c);
+    if (rc != DVM_OK) return rc;
+    CK(cudaMemcpyAsync(c->d_pub, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CK(pack2d(c, c->d_pub, c->f[c->cur]));
+    CK(zero_solid2d(c));
+    CK(partials_from_state2d(c));
     c->have_state = true;
     c->need_fusion = true;
     CK(cudaStreamSynchronize(c->stream));
@@ -375,7 +419,10 @@ int dvm_get_state(dvm_ctx *c, void *f, size_t bytes, int on_device)
 {
     if (!c || !f) { set_error("null"); return DVM_ERR_ARG; }
     if (bytes != c->state_elems * c->elem) { set_error("state size mismatch"); return DVM_ERR_ARG; }
-    CK(cudaMemcpyAsync(f, c->f[c->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    int rc = ensure_pub(c);
+    if (rc != DVM_OK) return rc;
+    CK(unpack2d(c, c->f[c->cur], c->d_pub));
+    CK(cudaMemcpyAsync(f, c->d_pub, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return DVM_OK;
 }

@@ -183,15 +183,13 @@ __device__ __forceinline__ bool gas_at(const Grid2D &g, const int8_t *type, int 
 }
 
 __global__ void k_flags(Grid2D g, Geo2D Gn, Geo2D Gp, const int32_t *master, const uint8_t *hs,
-                        uint8_t *flags, int32_t *spec_list, int32_t *wall_list, int32_t *counts,
-                        int cap, double *wcontrib, bool moving, bool muscl, int *err)
+                        uint8_t *flags, bool moving, bool muscl)
 {
     int ni = g.i1 - g.i0, nj = g.j1 - g.j0;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ni * nj) return;
     int i = g.i0 + t % ni, j = g.j0 + t / ni;
     long k = (long)j * g.nx + i;
-    wcontrib[3 * t] = 0; wcontrib[3 * t + 1] = 0; wcontrib[3 * t + 2] = 0;
     uint8_t f = 0;
     int32_t m = master[k];
     if (m < 0) {
@@ -200,11 +198,6 @@ __global__ void k_flags(Grid2D g, Geo2D Gn, Geo2D Gp, const int32_t *master, con
         f = kPlain;
     } else {
         f = kSpecial;
-        if (m == k) {
-            int s = atomicAdd(&counts[0], 1);
-            if (s < cap) spec_list[s] = (int32_t)k;
-            else atomicExch(&err[kErrCapacity], 1);
-        }
     }
     if (muscl) {
         const int8_t *ty = Gn.type;
@@ -220,15 +213,74 @@ __global__ void k_flags(Grid2D g, Geo2D Gn, Geo2D Gp, const int32_t *master, con
         f |= mask << kMaskShift;
     }
     flags[k] = f;
-    if (Gn.type[k] == DVM_CUT && Gn.lw[k] > 0) {
-        int s = atomicAdd(&counts[1], 1);
-        if (s < cap) wall_list[s] = (int32_t)k;
-        else atomicExch(&err[kErrCapacity], 1);
+}
+
+// Exclusive block-wide prefix count of a predicate (1024 threads).
+__device__ int block_excl_scan(bool pred, int *wsum, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned b = __ballot_sync(0xffffffffu, pred);
+    int pre = __popc(b & ((1u << lane) - 1u));
+    if (lane == 0) wsum[warp] = __popc(b);
+    __syncthreads();
+    if (warp == 0) {
+        int v = wsum[lane];
+        int inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        wsum[lane] = inc - v;
+        if (lane == 31) *total = inc;
+    }
+    __syncthreads();
+    int r = wsum[warp] + pre;
+    __syncthreads();
+    return r;
+}
+
+// Control-volume masters and wall cells of the box, listed in cell order
+// (deterministic, so that the force and torque sums have a fixed order).
+__global__ void __launch_bounds__(1024) k_lists(Grid2D g, Geo2D Gn, const int32_t *master,
+                                                const uint8_t *flags, int32_t *spec_list,
+                                                int32_t *wall_list, int32_t *wslot,
+                                                int32_t *counts, int cap, int *err)
+{
+    __shared__ int wsum[32];
+    __shared__ int tot;
+    const int ni = g.i1 - g.i0, nbox = ni * (g.j1 - g.j0);
+    int nspec = 0, nwall = 0;
+    for (int base = 0; base < nbox; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        bool sp = false, wl = false;
+        long k = 0;
+        if (t < nbox) {
+            k = (long)(g.j0 + t / ni) * g.nx + g.i0 + t % ni;
+            sp = (flags[k] & kSpecial) && master[k] == (int32_t)k;
+            wl = Gn.type[k] == DVM_CUT && Gn.lw[k] > 0;
+        }
+        int ps = block_excl_scan(sp, wsum, &tot) + nspec;
+        __syncthreads();
+        nspec += tot;
+        __syncthreads();
+        int pw = block_excl_scan(wl, wsum, &tot) + nwall;
+        __syncthreads();
+        nwall += tot;
+        if (t < nbox) {
+            if (sp) { if (ps < cap) spec_list[ps] = (int32_t)k; else atomicExch(&err[kErrCapacity], 1); }
+            wslot[k] = wl && pw < cap ? pw : -1;
+            if (wl) { if (pw < cap) wall_list[pw] = (int32_t)k; else atomicExch(&err[kErrCapacity], 1); }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        counts[0] = nspec < cap ? nspec : cap;
+        counts[1] = nwall < cap ? nwall : cap;
     }
 }
 
 __global__ void k_static_fill(Grid2D g, Geo2D G, int32_t *master, uint8_t *flags, uint8_t *hs,
-                              bool muscl)
+                              int32_t *wslot, bool muscl)
 {
     long nc = (long)g.nx * g.ny;
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -238,6 +290,7 @@ __global__ void k_static_fill(Grid2D g, Geo2D G, int32_t *master, uint8_t *flags
         G.sbar[t] = g.dx * g.dy;
         master[t] = (int32_t)t;
         hs[t] = 0;
+        wslot[t] = -1;
         flags[t] = kPlain | (muscl ? (uint8_t)(0xF << kMaskShift) : 0);
     }
     long nvert = (long)(g.nx + 1) * g.ny;
@@ -258,7 +311,7 @@ cudaError_t init_static_geometry2d(dvm_ctx *c)
     long n = (long)(c->nx + 1) * (c->ny + 1);
     for (int l = 0; l < 2; ++l)
         k_static_fill<<<nblk(n, 256), 256, 0, c->stream>>>(g, c->geo[l], c->master, c->flags,
-                                                           c->hs, c->scheme == DVM_MUSCL);
+                                                           c->hs, c->wslot, c->scheme == DVM_MUSCL);
     return cudaGetLastError();
 }
 
@@ -286,11 +339,10 @@ cudaError_t masters_flags2d(dvm_ctx *c, bool moving)
     const Geo2D &Gp = moving ? c->geo[1 - c->gcur] : c->geo[c->gcur];
     k_clear_hs<<<nblk(ncell, 256), 256, 0, c->stream>>>(g, c->hs);
     k_masters<<<nblk(ncell, 256), 256, 0, c->stream>>>(g, Gn, Gp, c->master, c->hs, c->d_err);
-    cudaMemsetAsync(c->counts, 0, 2 * sizeof(int32_t), c->stream);
-    k_flags<<<nblk(ncell, 256), 256, 0, c->stream>>>(g, Gn, Gp, c->master, c->hs, c->flags,
-                                                     c->spec_list, c->wall_list, c->counts,
-                                                     c->list_cap, c->wcontrib, moving,
-                                                     c->scheme == DVM_MUSCL, c->d_err);
+    k_flags<<<nblk(ncell, 256), 256, 0, c->stream>>>(g, Gn, Gp, c->master, c->hs, c->flags, moving,
+                                                     c->scheme == DVM_MUSCL);
+    k_lists<<<1, 1024, 0, c->stream>>>(g, Gn, c->master, c->flags, c->spec_list, c->wall_list,
+                                       c->wslot, c->counts, c->list_cap, c->d_err);
     return cudaGetLastError();
 }
 

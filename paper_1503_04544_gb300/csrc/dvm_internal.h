@@ -1,5 +1,17 @@
 // Internal declarations of libdvm shared by its CUDA translation units.
+//
+// Device layout of a distribution (2D, reduced pair f, g):
+//   element (cell, comp, p) at ((p / W) * 2 + comp) * slab * W + cell * W + p % W
+// with W = 16 bytes / sizeof(T) velocities per group (4 in FP32, 2 in FP64),
+// the velocity count padded to a multiple of W with zero entries, and
+// slab = ncell + nghost cells: the ghost cells of the four sides follow the
+// interior cells.  For one velocity group the states of consecutive cells
+// are contiguous, so a warp of 32 consecutive cells in x reads 512 contiguous
+// bytes per load, its x neighbours come from the same cache lines, and the
+// velocity (hence the upwind direction) is uniform across the warp.  The
+// public layout of dvm.h ([cell][comp][p]) is converted on the way in and out.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <cstddef>
@@ -14,6 +26,11 @@ constexpr int kBoxMargin = 12;       // cells between the body and the edge of i
 constexpr int kHistCap = 1 << 15;    // steps kept in the force/angle history
 constexpr int kMaxMembers = 32;      // virtual cells per control volume
 constexpr int kMaxAxisNv = 64;       // velocity points per axis
+constexpr int kRows = 8;             // cell rows per block of the bulk kernel
+constexpr int kStages = 4;           // shared-memory stages of the bulk kernel's TMA ring
+constexpr int kTileX = 32 + 4;       // tile width with a two-cell halo on each side
+constexpr int kTileY = kRows + 4;    // tile height with a two-cell halo
+constexpr long kWaitLimit = 1L << 24; // bound of every mbarrier wait
 
 // cell flag bits
 constexpr uint8_t kPlain = 1;        // gas cell alone in its control volume at t^n and t^{n+1}
@@ -22,7 +39,7 @@ constexpr uint8_t kSpecial = 4;      // updated by the control-volume kernel
 constexpr uint8_t kMaskShift = 4;    // bits 4..7: limiter allowed on faces x-, x+, y-, y+
 
 // device error flag slots
-enum { kErrNonphys = 0, kErrGeometry = 1, kErrCapacity = 2, kErrCount = 4 };
+enum { kErrNonphys = 0, kErrGeometry = 1, kErrCapacity = 2, kErrTimeout = 3, kErrCount = 4 };
 
 // One time level of the 2D geometry (Appendix A), FP64.
 struct Geo2D {
@@ -40,11 +57,15 @@ struct BodyDev {
     double theta1;            // at t^{n+1}
     double trig[4];           // cos/sin of theta (t^n), cos/sin of theta1
     double F[3], torque;      // at t^n of the last step
+    long long step;           // steps completed
 };
 
 // Parameters shared by the 2D kernels, passed by value.
 struct Grid2D {
     int nx, ny, nvx, nvy, nv;
+    int W, nvp, ngrp;         // velocities per group, padded count, groups
+    long slab;                // cells per slab: interior + ghosts
+    int gofs[4];              // first ghost cell of each side in the slab
     double xmin, ymin, dx, dy;
     double vxmin, vymin, dvx, dvy, dv;
     double dt, tau0;
@@ -62,6 +83,7 @@ struct BodyParams {
 }  // namespace dvm
 
 struct dvm_ctx {
+    CUtensorMap tmap[2];          // TMA descriptors of the two state buffers
     int dim, nx, ny, nz;
     double xmin, xmax, ymin, ymax, zmin, zmax, dx, dy, dz;
     int nvx, nvy, nvz, nv;
@@ -69,25 +91,34 @@ struct dvm_ctx {
     double Kn, Lref, cfl, dt, tau0;
     int prec, scheme, ncomp, elem;
     long long nc;
-    size_t state_elems;
+    size_t state_elems;           // public layout: nc * ncomp * nv
+    int W, nvp, ngrp;
+    long slab;
+    int gofs[4];
+    size_t dev_elems;             // device layout: ngrp * ncomp * slab * W
+    int S;                        // velocity splits of the bulk kernel
     cudaStream_t stream;
     bool own_stream;
     int bc[6];
-    void *ghost[6];               // device, [side cell][comp][p], state precision
     dvm_body body;
     double *d_Twseg, *d_segdir;
     void *f[2];
     int cur;
-    void *mom;                    // [nc][8] state precision: rho ux uy uz T
+    void *part[2];                // [S][4][nc] partial moment sums, paired with f
+    void *vtab;                   // [nvp][8] per-velocity coefficients (state precision)
+    int8_t *gsign;                // [ngrp][2] sign of v_x, v_y in a group (0: mixed)
     dvm::Geo2D geo[2];
     int gcur;
     int32_t *master;
     uint8_t *flags;
     uint8_t *hs;                  // has-slaves marks
     int32_t *spec_list, *wall_list, *counts;   // counts[0] = specials, [1] = walls
+    int32_t *wslot;               // wall slot of each cell, -1 if none
     int list_cap;
-    double *wphi, *wux, *wuy, *wT;              // per cell, wall data of t^n
-    double *wcontrib;             // per box cell: Fx, Fy, torque
+    void *wflux;                  // [wall slot][comp][nvp] wall-edge flux of the step
+    double *wphi;                 // [wall slot] wall density
+    double *wcontrib;             // [wall slot][3] Fx, Fy, torque
+    int *ticket;                  // block counter of the wall kernel
     int i0, i1, j0, j1;
     dvm::BodyDev *d_body;
     double *d_hist;               // [kHistCap][6]
@@ -96,6 +127,7 @@ struct dvm_ctx {
     int *h_err;                   // pinned
     double *d_scratch;            // nc doubles (mass)
     double *d_out;                // nc*5 doubles (moments output)
+    void *d_pub;                  // staging buffer in the public layout
     bool have_state, have_geo, need_fusion, moving;
     bool timing;
     void *ev_pool;                // std::vector<cudaEvent_t> of start/stop pairs
@@ -117,13 +149,18 @@ cudaError_t masters_flags2d(dvm_ctx *c, bool moving);
 cudaError_t init_static_geometry2d(dvm_ctx *c);
 
 // step kernels (dvm_step2d.cu)
-cudaError_t moments2d(dvm_ctx *c);
+cudaError_t tables2d(dvm_ctx *c);
+cudaError_t partials_from_state2d(dvm_ctx *c);
 cudaError_t init_maxwellian2d(dvm_ctx *c, const double *d_prim);
 cudaError_t step2d(dvm_ctx *c);
 cudaError_t mass2d(dvm_ctx *c, double *d_scratch, double *d_out);
 cudaError_t moments_out2d(dvm_ctx *c, double *d_out);
 cudaError_t ghost2d(dvm_ctx *c, int side, const double *d_prim, int nside);
+cudaError_t pack2d(dvm_ctx *c, const void *pub, void *dev);      // public -> device layout
+cudaError_t unpack2d(dvm_ctx *c, const void *dev, void *pub);    // device -> public layout
+cudaError_t zero_solid2d(dvm_ctx *c);                            // both state buffers
 cudaError_t timing_mark(dvm_ctx *c, int which);   // 0: before, 1: after the bulk kernel
+int make_tensor_maps2d(dvm_ctx *c);                // TMA descriptors of f[0], f[1]
 
 inline double *body_trig(dvm_ctx *c, int which)
 {

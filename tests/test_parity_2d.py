@@ -16,6 +16,9 @@ from paper_1503_04544_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = {dvm.FP64: 1e-12, dvm.FP32: 1e-5}
+# Velocities are in units of sqrt(R T0) = 1: a velocity error is relative to
+# max(||u||_inf, 1), so that a flow near rest is not judged on the ratio of
+# two round-off-sized numbers.
 GEO_KEYS = ("type", "cgas", "lx", "ly", "lw", "nwx", "nwy", "rwx", "rwy", "sbar")
 
 
@@ -32,10 +35,10 @@ def moments_err(cfg, Fo, s):
     errs = {}
     for k in ("rho", "ux", "uy", "T"):
         ref = mo[k][live]
-        if np.abs(ref).max() == 0:
-            errs[k] = np.abs(mg[k][live]).max()
-        else:
-            errs[k] = rel_inf(mg[k][live], ref)
+        scale = np.abs(ref).max()
+        if k in ("ux", "uy"):
+            scale = max(scale, 1.0)
+        errs[k] = np.abs(mg[k][live] - ref).max() / scale
     return errs
 
 
@@ -153,7 +156,8 @@ def test_cylinder_small(prec, scheme):
     hg = s.history(steps)
     assert len(hg["Fx"]) == steps
     assert rel_inf(hg["Fx"], h["Fx"]) < TOL[prec]
-    assert rel_inf(hg["Fy"], h["Fy"]) < max(TOL[prec], 1e-12) * 10
+    # the lift is round-off noise around zero: compare on the drag scale
+    assert np.abs(hg["Fy"] - h["Fy"]).max() < TOL[prec] * np.abs(h["Fx"]).max()
     if prec == dvm.FP64:
         assert rel_inf(s.get_state(), Fo) < 1e-12
     assert s.get_state().min() >= 0
