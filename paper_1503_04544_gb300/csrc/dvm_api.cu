@@ -42,11 +42,13 @@ Grid2D grid2d(const dvm_ctx *c)
     Grid2D g;
     g.nx = c->nx; g.ny = c->ny; g.nvx = c->nvx; g.nvy = c->nvy; g.nv = c->nv;
     g.W = c->W; g.nvp = c->nvp; g.ngrp = c->ngrp; g.slab = c->slab;
-    for (int s = 0; s < 4; ++s) g.gofs[s] = c->gofs[s];
     g.xmin = c->xmin; g.ymin = c->ymin; g.dx = c->dx; g.dy = c->dy;
     g.vxmin = c->vxmin; g.vymin = c->vymin; g.dvx = c->dvx; g.dvy = c->dvy;
     g.dv = c->dvx * c->dvy;
     g.dt = c->dt; g.tau0 = c->tau0;
+    g.dt_tau0 = c->dt / c->tau0;
+    g.dv_f = (float)g.dv;
+    g.dt_tau0_f = (float)g.dt_tau0;
     for (int s = 0; s < 4; ++s) g.bc[s] = c->bc[s];
     g.i0 = c->i0; g.i1 = c->i1; g.j0 = c->j0; g.j1 = c->j1;
     return g;
@@ -63,6 +65,7 @@ BodyParams body_params(const dvm_ctx *c)
 }
 
 size_t vcoef_bytes(int prec);
+size_t cvinfo_bytes();
 
 }  // namespace dvm
 
@@ -131,7 +134,7 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     if (!grid || !vg || !ph || !out) { set_error("null argument"); return DVM_ERR_ARG; }
     *out = nullptr;
     if (grid->dim != 2) { set_error("only dim = 2 is built in this library version"); return DVM_ERR_UNSUPPORTED; }
-    if (grid->nx < 2 || grid->ny < 1 || vg->nvx < 1 || vg->nvy < 1) { set_error("grid sizes"); return DVM_ERR_ARG; }
+    if (grid->nx < 4 || grid->ny < 4 || vg->nvx < 1 || vg->nvy < 1) { set_error("grid sizes: at least 4 x 4 cells and one velocity"); return DVM_ERR_ARG; }
     if (vg->nvx > kMaxAxisNv || vg->nvy > kMaxAxisNv) { set_error("at most 64 velocities per axis"); return DVM_ERR_ARG; }
     if (precision != DVM_FP32 && precision != DVM_FP64) { set_error("precision must be 32 or 64"); return DVM_ERR_ARG; }
     if (scheme != DVM_UPWIND && scheme != DVM_MUSCL) { set_error("scheme"); return DVM_ERR_ARG; }
@@ -166,8 +169,7 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     c->W = 16 / c->elem;
     c->nvp = (c->nv + c->W - 1) / c->W * c->W;
     c->ngrp = c->nvp / c->W;
-    c->gofs[0] = 0; c->gofs[1] = c->ny; c->gofs[2] = 2 * c->ny; c->gofs[3] = 2 * c->ny + c->nx;
-    c->slab = (long)c->nc + 2L * (c->nx + c->ny);
+    c->slab = (long)(c->nx + 4) * (c->ny + 4);
     c->dev_elems = (size_t)c->ngrp * c->ncomp * c->slab * c->W;
     {
         // velocity splits: enough blocks for a few waves on 152 SMs
@@ -253,7 +255,7 @@ void dvm_destroy(dvm_ctx *c)
     for (int l = 0; l < 2; ++l) free_geo(c->geo[l]);
     cudaFree(c->master); cudaFree(c->flags); cudaFree(c->hs);
     cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->counts);
-    cudaFree(c->wphi); cudaFree(c->wcontrib);
+    cudaFree(c->wphi); cudaFree(c->wcontrib); cudaFree(c->cvinfo);
     cudaFree(c->d_body); cudaFree(c->d_hist); cudaFree(c->d_err);
     cudaFree(c->d_scratch); cudaFree(c->d_out);
     cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
@@ -285,6 +287,7 @@ int dvm_set_bc(dvm_ctx *c, int side, int kind, const double *state)
         if (e != cudaSuccess) return cuda_fail(e, "dvm_set_bc");
     }
     c->bc[side] = kind;
+    if (c->have_state) CK(halo2d(c, c->cur));
     // flags depend on the periodicity of the sides through the limiter masks
     if (c->body.shape != DVM_SHAPE_NONE) {
         cudaError_t e = masters_flags2d(c, false);
@@ -334,8 +337,10 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
     CK(cudaMalloc(&c->spec_list, sizeof(int32_t) * c->list_cap));
     CK(cudaMalloc(&c->wall_list, sizeof(int32_t) * c->list_cap));
     CK(cudaMalloc(&c->wcontrib, sizeof(double) * 3 * c->list_cap));
-    CK(cudaMalloc(&c->wphi, sizeof(double) * c->list_cap));
-    CK(cudaMalloc(&c->wflux, (size_t)c->list_cap * 2 * c->nv * c->elem));
+    CK(cudaMalloc(&c->wphi, sizeof(double) * 4 * c->list_cap));
+    cudaFree(c->cvinfo);
+    CK(cudaMalloc(&c->cvinfo, cvinfo_bytes() * (size_t)c->list_cap));
+    CK(cudaMalloc(&c->wflux, sizeof(double) * 8 * (size_t)c->list_cap * c->S));
     CK(cudaMemsetAsync(c->wcontrib, 0, sizeof(double) * 3 * c->list_cap, c->stream));
     CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4, c->stream));
     dvm::BodyDev hb;
@@ -387,6 +392,7 @@ int dvm_init_maxwellian(dvm_ctx *c, const double *rho, const double *ux, const d
     CK(cudaMemcpyAsync(d, prim.data(), sizeof(double) * 5 * nc, cudaMemcpyHostToDevice, c->stream));
     CK(init_maxwellian2d(c, d));
     CK(zero_solid2d(c));
+    CK(halo2d(c, c->cur));
     CK(partials_from_state2d(c));
     c->have_state = true;
     c->need_fusion = true;
@@ -408,6 +414,7 @@ int dvm_set_state(dvm_ctx *c, const void *f, size_t bytes, int on_device)
     CK(cudaMemcpyAsync(c->d_pub, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(pack2d(c, c->d_pub, c->f[c->cur]));
     CK(zero_solid2d(c));
+    CK(halo2d(c, c->cur));
     CK(partials_from_state2d(c));
     c->have_state = true;
     c->need_fusion = true;
@@ -430,6 +437,11 @@ int dvm_get_state(dvm_ctx *c, void *f, size_t bytes, int on_device)
 int dvm_step_async(dvm_ctx *c, int nsteps)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    for (int d = 0; d < c->dim; ++d)
+        if ((c->bc[2 * d] == DVM_BC_PERIODIC) != (c->bc[2 * d + 1] == DVM_BC_PERIODIC)) {
+            set_error("opposite sides must both be periodic or both not");
+            return DVM_ERR_ARG;
+        }
     if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return DVM_ERR_ARG; }
     for (int s = 0; s < nsteps; ++s) {

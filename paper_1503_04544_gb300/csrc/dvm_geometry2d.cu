@@ -343,6 +343,9 @@ cudaError_t masters_flags2d(dvm_ctx *c, bool moving)
                                                      c->scheme == DVM_MUSCL);
     k_lists<<<1, 1024, 0, c->stream>>>(g, Gn, c->master, c->flags, c->spec_list, c->wall_list,
                                        c->wslot, c->counts, c->list_cap, c->d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return members2d(c, moving);
     return cudaGetLastError();
 }
 

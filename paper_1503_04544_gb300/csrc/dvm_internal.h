@@ -1,15 +1,17 @@
 // Internal declarations of libdvm shared by its CUDA translation units.
 //
 // Device layout of a distribution (2D, reduced pair f, g):
-//   element (cell, comp, p) at ((p / W) * 2 + comp) * slab * W + cell * W + p % W
-// with W = 16 bytes / sizeof(T) velocities per group (4 in FP32, 2 in FP64),
-// the velocity count padded to a multiple of W with zero entries, and
-// slab = ncell + nghost cells: the ghost cells of the four sides follow the
-// interior cells.  For one velocity group the states of consecutive cells
-// are contiguous, so a warp of 32 consecutive cells in x reads 512 contiguous
-// bytes per load, its x neighbours come from the same cache lines, and the
-// velocity (hence the upwind direction) is uniform across the warp.  The
-// public layout of dvm.h ([cell][comp][p]) is converted on the way in and out.
+//   element (cell, comp, p) at ((p / W) * 2 + comp) * slab * W + P(cell) * W + p % W
+// with W = 16 bytes / sizeof(T) velocities per group (4 in FP32, 2 in FP64)
+// and the velocity count padded to a multiple of W with zero entries.  Each
+// (group, component) slab is the cell grid padded by two cells on every side,
+// P(i, j) = (j + 2) * (nx + 4) + i + 2; the padding holds the boundary
+// condition (Maxwellian ghost states, or periodic images / zero-gradient
+// copies that the kernels writing boundary cells keep up to date).  For one
+// velocity group the states of consecutive cells are contiguous, so a warp of
+// 32 consecutive cells in x reads 512 contiguous bytes, and the velocity
+// (hence the upwind direction) is uniform across the warp.  The public layout
+// of dvm.h ([cell][comp][p]) is converted on the way in and out.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -24,13 +26,13 @@ namespace dvm {
 constexpr int kMaxWalk = 8;          // bound of the master search (Appendix A.3)
 constexpr int kBoxMargin = 12;       // cells between the body and the edge of its box
 constexpr int kHistCap = 1 << 15;    // steps kept in the force/angle history
-constexpr int kMaxMembers = 32;      // virtual cells per control volume
+constexpr int kMaxMembers = 16;      // virtual cells per control volume
 constexpr int kMaxAxisNv = 64;       // velocity points per axis
 constexpr int kRows = 8;             // cell rows per block of the bulk kernel
 constexpr int kStages = 4;           // shared-memory stages of the bulk kernel's TMA ring
 constexpr int kTileX = 32 + 4;       // tile width with a two-cell halo on each side
 constexpr int kTileY = kRows + 4;    // tile height with a two-cell halo
-constexpr long kWaitLimit = 1L << 24; // bound of every mbarrier wait
+constexpr long kWaitLimit = 1L << 20; // bound of every mbarrier wait (polls)
 
 // cell flag bits
 constexpr uint8_t kPlain = 1;        // gas cell alone in its control volume at t^n and t^{n+1}
@@ -64,11 +66,12 @@ struct BodyDev {
 struct Grid2D {
     int nx, ny, nvx, nvy, nv;
     int W, nvp, ngrp;         // velocities per group, padded count, groups
-    long slab;                // cells per slab: interior + ghosts
-    int gofs[4];              // first ghost cell of each side in the slab
+    long slab;                // cells per slab: (nx + 4) * (ny + 4)
     double xmin, ymin, dx, dy;
     double vxmin, vymin, dvx, dvy, dv;
     double dt, tau0;
+    double dt_tau0;           // dt / tau0
+    float dv_f, dt_tau0_f;    // FP32 copies for the FP32 kernels
     int bc[4];
     int i0, i1, j0, j1;       // geometry box [i0, i1) x [j0, j1)
 };
@@ -94,7 +97,6 @@ struct dvm_ctx {
     size_t state_elems;           // public layout: nc * ncomp * nv
     int W, nvp, ngrp;
     long slab;
-    int gofs[4];
     size_t dev_elems;             // device layout: ngrp * ncomp * slab * W
     int S;                        // velocity splits of the bulk kernel
     cudaStream_t stream;
@@ -114,9 +116,10 @@ struct dvm_ctx {
     uint8_t *hs;                  // has-slaves marks
     int32_t *spec_list, *wall_list, *counts;   // counts[0] = specials, [1] = walls
     int32_t *wslot;               // wall slot of each cell, -1 if none
+    void *cvinfo;                 // [control volume] CvInfo records (dvm_step2d.cu)
     int list_cap;
-    void *wflux;                  // [wall slot][comp][nvp] wall-edge flux of the step
-    double *wphi;                 // [wall slot] wall density
+    void *wflux;                  // [wall slot][split][8] FP64 partial wall sums
+    double *wphi;                 // [wall slot][4] wall density, u_w (2), T_w
     double *wcontrib;             // [wall slot][3] Fx, Fy, torque
     int *ticket;                  // block counter of the wall kernel
     int i0, i1, j0, j1;
@@ -159,6 +162,8 @@ cudaError_t ghost2d(dvm_ctx *c, int side, const double *d_prim, int nside);
 cudaError_t pack2d(dvm_ctx *c, const void *pub, void *dev);      // public -> device layout
 cudaError_t unpack2d(dvm_ctx *c, const void *dev, void *pub);    // device -> public layout
 cudaError_t zero_solid2d(dvm_ctx *c);                            // both state buffers
+cudaError_t halo2d(dvm_ctx *c, int buf);                         // periodic / zero-gradient padding
+cudaError_t members2d(dvm_ctx *c, bool moving);                  // control-volume records
 cudaError_t timing_mark(dvm_ctx *c, int which);   // 0: before, 1: after the bulk kernel
 int make_tensor_maps2d(dvm_ctx *c);                // TMA descriptors of f[0], f[1]
 

@@ -102,47 +102,83 @@ template <typename T> struct Acc {
     __device__ __forceinline__ T value() const { return s - c; }
 };
 
-// Element (cell, comp, p) of the device layout.
-template <typename T>
-__device__ __forceinline__ long didx(const Grid2D &g, long cell, int comp, int p)
-{
-    constexpr int W = Vec<T>::W;
-    return ((long)(p / W) * 2 + comp) * g.slab * W + cell * W + (p % W);
-}
-
-// Slab index of cell (i, j) or of the ghost cell that replaces it beyond a
-// side: periodic wrap, Maxwellian ghost, zero-gradient copy of the boundary.
+// Slab index of cell (i, j), -2 <= i < nx + 2, -2 <= j < ny + 2: the slab is
+// the grid padded by two cells on every side, and the padding holds the
+// boundary-condition values (Maxwellian ghosts, periodic images or
+// zero-gradient copies), so a neighbour within two cells is a plain index.
 __device__ __forceinline__ long nbr(const Grid2D &g, int i, int j)
 {
-    const long nc = (long)g.nx * g.ny;
-    if (i < 0) {
-        if (g.bc[0] == DVM_BC_PERIODIC) i = ((i % g.nx) + g.nx) % g.nx;
-        else if (g.bc[0] == DVM_BC_MAXWELLIAN) return nc + g.gofs[0] + j;
-        else i = 0;
-    } else if (i >= g.nx) {
-        if (g.bc[1] == DVM_BC_PERIODIC) i = i % g.nx;
-        else if (g.bc[1] == DVM_BC_MAXWELLIAN) return nc + g.gofs[1] + j;
-        else i = g.nx - 1;
+    return (long)(j + 2) * (g.nx + 4) + (i + 2);
+}
+
+// Cell coordinates of interior cell k = j*nx + i (2D grids have fewer than
+// 2^31 cells, so 32-bit arithmetic suffices).
+__device__ __forceinline__ void cell_ij(const Grid2D &g, long k, int &i, int &j)
+{
+    const int kk = (int)k;
+    j = kk / g.nx;
+    i = kk - j * g.nx;
+}
+
+// Slab index of interior cell k.
+__device__ __forceinline__ long pcell(const Grid2D &g, long k)
+{
+    int i, j;
+    cell_ij(g, k, i, j);
+    return nbr(g, i, j);
+}
+
+// Offset of (comp, p) within the device layout; add slab index * W.
+template <typename T>
+__device__ __forceinline__ long ebase(const Grid2D &g, int comp, int p)
+{
+    constexpr int W = Vec<T>::W;
+    return ((long)(p / W) * 2 + comp) * g.slab * W + (p % W);
+}
+
+// Element (interior cell k, comp, p) of the device layout.
+template <typename T>
+__device__ __forceinline__ long didx(const Grid2D &g, long k, int comp, int p)
+{
+    return ebase<T>(g, comp, p) + pcell(g, k) * Vec<T>::W;
+}
+
+// Padding cells that mirror interior cell (i, j) on periodic and
+// zero-gradient sides (at most two along each axis); -1 where unused.
+__device__ __forceinline__ void mirrors(const Grid2D &g, int i, int j, long (&m)[4])
+{
+    m[0] = m[1] = m[2] = m[3] = -1;
+    if (g.bc[0] == DVM_BC_PERIODIC) {
+        if (i < 2) m[0] = nbr(g, i + g.nx, j);
+        else if (i >= g.nx - 2) m[0] = nbr(g, i - g.nx, j);
+    } else {
+        if (i == 0 && g.bc[0] == DVM_BC_ZEROGRAD) { m[0] = nbr(g, -1, j); m[1] = nbr(g, -2, j); }
+        if (i == g.nx - 1 && g.bc[1] == DVM_BC_ZEROGRAD) { m[0] = nbr(g, g.nx, j); m[1] = nbr(g, g.nx + 1, j); }
     }
-    if (j < 0) {
-        if (g.bc[2] == DVM_BC_PERIODIC) j = ((j % g.ny) + g.ny) % g.ny;
-        else if (g.bc[2] == DVM_BC_MAXWELLIAN) return nc + g.gofs[2] + i;
-        else j = 0;
-    } else if (j >= g.ny) {
-        if (g.bc[3] == DVM_BC_PERIODIC) j = j % g.ny;
-        else if (g.bc[3] == DVM_BC_MAXWELLIAN) return nc + g.gofs[3] + i;
-        else j = g.ny - 1;
+    if (g.bc[2] == DVM_BC_PERIODIC) {
+        if (j < 2) m[2] = nbr(g, i, j + g.ny);
+        else if (j >= g.ny - 2) m[2] = nbr(g, i, j - g.ny);
+    } else {
+        if (j == 0 && g.bc[2] == DVM_BC_ZEROGRAD) { m[2] = nbr(g, i, -1); m[3] = nbr(g, i, -2); }
+        if (j == g.ny - 1 && g.bc[3] == DVM_BC_ZEROGRAD) { m[2] = nbr(g, i, g.ny); m[3] = nbr(g, i, g.ny + 1); }
     }
-    return (long)j * g.nx + i;
 }
 
 // Primitive variables (Eq. MacroscopicDDv; T from E = rho|u|^2/2 + 3/2 rho T)
 // from the reduced sums s0 = sum f, s1 = sum vx f, s2 = sum vy f,
 // s3 = sum (|v|^2/2 f + g).
+// A scalar in the state precision without FP64 arithmetic in FP32 kernels.
 template <typename T>
-__device__ __forceinline__ bool primitives(double dv, T s0, T s1, T s2, T s3, T &rho, T &ux, T &uy, T &tmp)
+__device__ __forceinline__ T pick(float f, double d)
 {
-    rho = s0 * T(dv);
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
+}
+
+template <typename T>
+__device__ __forceinline__ bool primitives(T dv, T s0, T s1, T s2, T s3, T &rho, T &ux, T &uy, T &tmp)
+{
+    rho = s0 * dv;
     ux = s1 / s0;
     uy = s2 / s0;
     tmp = (T(2) * (s3 / s0) - (ux * ux + uy * uy)) / T(3);
@@ -263,11 +299,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
 
 constexpr int kStageBytes = 2 * kTileY * kTileX * 16;     // both components of one group
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Update of one component of one velocity group for the thread's cell from
 // the shared-memory tile (Eq. ExSchemeDD on a full gas cell, fluxes of Eq.
 // FluxDD in difference form with the limited reconstruction), moment sums.
-// c0 is the tile index of the cell; ox/oy the tile strides of one cell
-// step along x/y towards the upwind side (per element in the mixed case).
+// c0 is the tile index of the cell; ux1/uy1 the tile offsets of one cell step
+// towards the upwind side along x/y (sign-uniform groups), else per element.
 template <typename T, bool MUSCL, int COMP, bool UNIFORM>
 __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0, int ux1, int uy1,
                                           const T (&vx)[Vec<T>::W], const T (&vy)[Vec<T>::W],
@@ -279,7 +320,6 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
     T f[W];
     sld<T>(t + c0, f);
     if (UNIFORM) {
-        // ux1/uy1: tile offset of the upwind neighbour (+-1 or +-kTileX)
         T u1[W], w1[W], d1[W], u2[W], e1[W], w2[W];
         sld<T>(t + c0 - ux1, u1);
         sld<T>(t + c0 - uy1, w1);
@@ -340,13 +380,29 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
     }
 }
 
+// Store of one (group, component) vector of a cell and of its padding
+// mirrors (cells within two cells of a periodic or zero-gradient side).
+template <typename T>
+__device__ __forceinline__ void store_cell(typename Vec<T>::type *slab, long pc, const long (&mir)[4], bool anymir,
+                                           const T (&v)[Vec<T>::W])
+{
+    vst<T>(slab + pc, v);
+    if (anymir) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (mir[k] >= 0) vst<T>(slab + mir[k], v);
+    }
+}
+
 // Bulk update.  Block = 32 x kRows cells; the velocity groups of split
 // blockIdx.z stream through a kStages-deep ring of shared-memory tiles
 // (the block's cells plus a two-cell halo, both components of one group),
-// each filled by one TMA tensor load completing on an mbarrier.  Halo cells
-// beyond the domain are replaced by their boundary-condition values after
-// the load.  Every thread of the block takes part in the waits and barriers;
-// only threads of plain cells compute.
+// each filled by one TMA tensor load that completes on the stage's "full"
+// mbarrier; each warp releases a stage on its "empty" mbarrier once it has
+// read it, and thread 0 refills a stage only after all warps released it.
+// Every wait is bounded: on timeout the kernel records kErrTimeout and goes
+// on without blocking.  Threads of non-plain cells only take part in the
+// barriers.
 template <typename T, bool MUSCL>
 __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __grid_constant__ CUtensorMap tmap)
 {
@@ -354,7 +410,8 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     using V = typename Vec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     V *ring = reinterpret_cast<V *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint64_t *empty = full + kStages;
     const Grid2D &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kRows;
@@ -362,21 +419,24 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     const bool inside = i < g.nx && j < g.ny;
     const long nc = (long)g.nx * g.ny;
     const long cell = inside ? (long)j * g.nx + i : 0;
+    const long pc = nbr(g, i, j);
     const int split = blockIdx.z;
     const int gps = (g.ngrp + a.S - 1) / a.S;
     const int g0 = split * gps, g1 = min(g0 + gps, g.ngrp);
     const int ngr = max(g1 - g0, 0);
     const uint8_t fl = inside ? a.flags[cell] : 0;
     const bool plain = (fl & kPlain) != 0, zero = (fl & kZero) != 0;
-    const V *fin = reinterpret_cast<const V *>(a.fin);
     V *fout = reinterpret_cast<V *>(a.fout);
 
     if (tid == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], kRows);
+        }
         mbar_fence_init();
         for (int st = 0; st < kStages - 1 && st < ngr; ++st) {
-            mbar_expect_tx(&bars[st], kStageBytes);
-            tma_load_3d(ring + (long)st * (kStageBytes / 16), &tmap, &bars[st], (i0 - 2) * W, j0 - 2, (g0 + st) * 2);
+            mbar_expect_tx(&full[st], kStageBytes);
+            tma_load_3d(ring + (long)st * (kStageBytes / 16), &tmap, &full[st], i0 * W, j0, (g0 + st) * 2);
         }
     }
 
@@ -386,10 +446,11 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
         T s[4];
         gather_partials(a.pin, a.S, nc, cell, s);
         T rho, tmp;
-        if (!primitives<T>(g.dv, s[0], s[1], s[2], s[3], rho, ux, uy, tmp)) atomicExch(&a.err[kErrNonphys], 1);
+        if (!primitives<T>(pick<T>(g.dv_f, g.dv), s[0], s[1], s[2], s[3], rho, ux, uy, tmp))
+            atomicExch(&a.err[kErrNonphys], 1);
         A = rho / (T(2.0 * kPi) * tmp);
         c2 = T(kLog2e) / (T(2) * tmp);
-        r = T(g.dt / g.tau0) * rho;
+        r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
         gfac = tmp / T(2);
     }
     const int mask = fl >> kMaskShift;
@@ -398,7 +459,9 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     const T wxm = (mask & 1) ? T(0.5) : T(0), wxp = (mask & 2) ? T(0.5) : T(0);
     const T wym = (mask & 4) ? T(0.5) : T(0), wyp = (mask & 8) ? T(0.5) : T(0);
     const int c0 = (ty + 2) * kTileX + tx + 2;
-    const bool edge = i0 - 2 < 0 || i0 + 34 > g.nx || j0 - 2 < 0 || j0 + kRows + 2 > g.ny;
+    long mir[4];
+    mirrors(g, i, j, mir);
+    const bool anymir = __any_sync(0xffffffffu, inside && (mir[0] >= 0 || mir[2] >= 0));
     __syncthreads();
 
     Acc<T> m0, m1, m2, m3;
@@ -406,39 +469,16 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     int fold = 0;
     for (int it = 0; it < ngr; ++it) {
         const int q = g0 + it, st = it % kStages;
-        const uint32_t parity = (uint32_t)((it / kStages) & 1);
         if (tid == 0 && it + kStages - 1 < ngr) {
-            const int s2 = (it + kStages - 1) % kStages;
-            mbar_expect_tx(&bars[s2], kStageBytes);
-            tma_load_3d(ring + (long)s2 * (kStageBytes / 16), &tmap, &bars[s2], (i0 - 2) * W, j0 - 2,
-                        (g0 + it + kStages - 1) * 2);
-        }
-        const bool ok = mbar_wait(&bars[st], parity);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
+            const int k = it + kStages - 1, s2 = k % kStages;
+            if (k >= kStages && !mbar_wait(&empty[s2], (uint32_t)((k / kStages - 1) & 1)))
                 atomicExch(&a.err[kErrTimeout], 1);
-                // let the copies already issued land before the block exits
-                for (int k2 = it; k2 < it + kStages && k2 < ngr; ++k2)
-                    mbar_wait(&bars[k2 % kStages], (uint32_t)((k2 / kStages) & 1));
-            }
-            __syncthreads();
-            return;
+            mbar_expect_tx(&full[s2], kStageBytes);
+            tma_load_3d(ring + (long)s2 * (kStageBytes / 16), &tmap, &full[s2], i0 * W, j0, (g0 + k) * 2);
         }
-        V *tile = ring + (long)st * (kStageBytes / 16);
-        if (edge) {
-            // halo cells beyond the domain: boundary-condition values
-            for (int e = tid; e < 2 * kTileY * kTileX; e += 32 * kRows) {
-                const int comp = e / (kTileY * kTileX), rem = e % (kTileY * kTileX);
-                const int rr = rem / kTileX, cc = rem % kTileX;
-                const int gi = i0 - 2 + cc, gj = j0 - 2 + rr;
-                const bool inx = gi >= 0 && gi < g.nx, iny = gj >= 0 && gj < g.ny;
-                const bool cross = (cc >= 2 && cc < 34) || (rr >= 2 && rr < kRows + 2);
-                if ((inx && iny) || !cross) continue;
-                if (!inx && !iny) continue;
-                tile[e] = fin[((long)q * 2 + comp) * g.slab + nbr(g, gi, gj)];
-            }
-            __syncthreads();
-        }
+        if (!mbar_wait(&full[st], (uint32_t)((it / kStages) & 1))) atomicExch(&a.err[kErrTimeout], 1);
+        const V *tile = ring + (long)st * (kStageBytes / 16);
+        V *o0 = fout + (long)q * 2 * g.slab;
         if (plain) {
             const int sx = a.gsign[2 * q], sy = a.gsign[2 * q + 1];
             T vx[W], vy[W], nux[W], nuy[W], feq[W], out[W];
@@ -449,26 +489,25 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                 const T dx = vc.vx - ux, dy = vc.vy - uy;
                 feq[e] = A * dexp2(-(dx * dx + dy * dy) * c2);
             }
-            V *o0 = fout + (long)q * 2 * g.slab + cell;
             if (sx != 0 && sy != 0) {
                 const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
                 bulk_tile<T, MUSCL, 0, true>(tile, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
                                              out, q0, q1, q2, q3);
-                vst<T>(o0, out);
+                store_cell<T>(o0, pc, mir, anymir, out);
 #pragma unroll
                 for (int e = 0; e < W; ++e) feq[e] *= gfac;
                 bulk_tile<T, MUSCL, 1, true>(tile + kTileY * kTileX, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm,
                                              wxp, wym, wyp, r, out, q0, q1, q2, q3);
-                vst<T>(o0 + g.slab, out);
+                store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
             } else {
                 bulk_tile<T, MUSCL, 0, false>(tile, c0, 1, kTileX, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
                                               out, q0, q1, q2, q3);
-                vst<T>(o0, out);
+                store_cell<T>(o0, pc, mir, anymir, out);
 #pragma unroll
                 for (int e = 0; e < W; ++e) feq[e] *= gfac;
                 bulk_tile<T, MUSCL, 1, false>(tile + kTileY * kTileX, c0, 1, kTileX, vx, vy, nux, nuy, feq, wxm,
                                               wxp, wym, wyp, r, out, q0, q1, q2, q3);
-                vst<T>(o0 + g.slab, out);
+                store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
             }
             // fold the plain sums of 8 groups into the compensated sums
             if (++fold == 8) {
@@ -480,10 +519,16 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
             T z[W];
 #pragma unroll
             for (int e = 0; e < W; ++e) z[e] = 0;
-            vst<T>(fout + (long)q * 2 * g.slab + cell, z);
-            vst<T>(fout + ((long)q * 2 + 1) * g.slab + cell, z);
+            store_cell<T>(o0, pc, mir, anymir, z);
+            store_cell<T>(o0 + g.slab, pc, mir, anymir, z);
         }
-        __syncthreads();      // the stage is refilled at the next iteration
+        __syncwarp();
+        if (tx == 0) mbar_arrive(&empty[st]);
+    }
+    if (tid == 0) {
+        // every issued copy has landed before the block exits (normally
+        // already observed by the waits above)
+        for (int k = max(ngr - kStages, 0); k < ngr; ++k) mbar_wait(&full[k % kStages], (uint32_t)((k / kStages) & 1));
     }
     if (plain) {
         m0.add(q0); m1.add(q1); m2.add(q2); m3.add(q3);
@@ -509,8 +554,18 @@ struct CvArgs {
     const int32_t *counts;
     int cap;
     int S;
+    int gps;                  // velocity groups per split
+    const void *cvinfo;       // control-volume records
+    const void *vt;           // per-velocity coefficients (state precision)
     int *err;
 };
+
+// Velocity range [v0, v1) of split s.
+__device__ __forceinline__ void split_range(const CvArgs &c, int s, int W, int &v0, int &v1)
+{
+    v0 = s * c.gps * W;
+    v1 = min(c.g.nv, v0 + c.gps * W);
+}
 
 // Ordered list of the members of control volume m (cells whose master is m),
 // scanned in row-major order over the window reachable by the master search.
@@ -550,6 +605,96 @@ __device__ int gather_members(const CvArgs &c, long m, int32_t *mem)
         __syncthreads();
     }
     return total < kMaxMembers ? total : kMaxMembers;
+}
+
+// One member (virtual cell) of a control volume, as the update needs it.
+struct __align__(16) CvMember {
+    long pc;                  // slab index
+    long mir[4];              // padding mirrors (-1: none)
+    int i, j;
+    double L[4];              // Cartesian edge lengths at t^n: x-, x+, y-, y+
+    double lw, nwx, nwy;      // wall edge at t^n (lw = 0: no wall)
+    double sb;                // virtual-cell area at t^n
+    int wslot;                // wall slot, -1 if none
+    int mask;                 // limiter mask of the faces
+    int live, keep;           // non-solid at t^n / at t^{n+1}
+};
+
+// A control volume: members in cell order, the master's slab index and the
+// area ratios of Eq. ExSchemeDD, all fixed between geometry updates.
+struct __align__(16) CvInfo {
+    int nm;
+    int ok;                   // S^{n+1,*} > 0
+    long pcm;
+    double a;                 // S^n / S^{n+1,*}
+    double bco;               // dt / S^{n+1,*}
+    double Sn;
+    CvMember mem[kMaxMembers];
+};
+
+// Control-volume records of every control volume in the list (once per
+// geometry): members from the master search, their slab indices, padding
+// mirrors, edge lengths, wall edges and the area ratios.
+__global__ void __launch_bounds__(256) k_members(CvArgs c, CvInfo *info)
+{
+    __shared__ int32_t mem[kMaxMembers];
+    const Grid2D &g = c.g;
+    const int n = min(c.counts[0], c.cap);
+    const int W1 = g.nx + 1;
+    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
+        const long m = c.spec_list[idx];
+        const int nm = gather_members(c, m, mem);
+        CvInfo &I = info[idx];
+        if (threadIdx.x < nm) {
+            const long k = mem[threadIdx.x];
+            CvMember &M = I.mem[threadIdx.x];
+            int i, j;
+            cell_ij(g, k, i, j);
+            M.i = i; M.j = j;
+            M.pc = nbr(g, i, j);
+            mirrors(g, i, j, M.mir);
+            M.L[0] = c.Gn.lx[(long)j * W1 + i];
+            M.L[1] = c.Gn.lx[(long)j * W1 + i + 1];
+            M.L[2] = c.Gn.ly[(long)j * g.nx + i];
+            M.L[3] = c.Gn.ly[(long)(j + 1) * g.nx + i];
+            M.wslot = c.wslot[k];
+            const bool wall = M.wslot >= 0;
+            M.lw = wall ? c.Gn.lw[k] : 0.0;
+            M.nwx = c.Gn.nwx[k];
+            M.nwy = c.Gn.nwy[k];
+            M.sb = c.Gn.sbar[k];
+            M.mask = c.flags[k] >> kMaskShift;
+            M.live = c.Gn.type[k] != DVM_SOLID;
+            M.keep = c.Gp.type[k] != DVM_SOLID;
+            if (k == m) I.pcm = M.pc;
+        }
+        if (threadIdx.x == 0) {
+            double Sn = 0, Sp = 0;
+            for (int q = 0; q < nm; ++q) { Sn += c.Gn.sbar[mem[q]]; Sp += c.Gp.sbar[mem[q]]; }
+            I.nm = nm;
+            I.ok = Sp > 0;
+            I.Sn = Sn;
+            I.a = Sp > 0 ? Sn / Sp : 0.0;
+            I.bco = Sp > 0 ? g.dt / Sp : 0.0;
+            if (!(Sp > 0)) atomicExch(&c.err[kErrGeometry], 1);
+        }
+        __syncthreads();
+    }
+}
+
+// Compensated block sum (all threads return the total); red holds 2 values
+// per warp.
+template <typename T>
+__device__ __forceinline__ T block_acc(Acc<T> a, T *red)
+{
+    a.warp_reduce();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) { red[2 * warp] = a.s; red[2 * warp + 1] = a.c; }
+    __syncthreads();
+    Acc<T> t;
+    for (int w = 0; w < nw; ++w) t.merge(red[2 * w], red[2 * w + 1]);
+    return t.value();
 }
 
 template <typename T>
@@ -592,41 +737,64 @@ __device__ __forceinline__ void write_member_partials(T *part, int S, long nc, l
     }
 }
 
+// Write the moment sums of one velocity split to a member (zeros if the
+// member is solid).
+template <typename T>
+__device__ __forceinline__ void write_split_partials(T *part, int s, long nc, long k, bool keep,
+                                                     T s0, T s1, T s2, T s3)
+{
+    part[((long)s * 4 + 0) * nc + k] = keep ? s0 : T(0);
+    part[((long)s * 4 + 1) * nc + k] = keep ? s1 : T(0);
+    part[((long)s * 4 + 2) * nc + k] = keep ? s2 : T(0);
+    part[((long)s * 4 + 3) * nc + k] = keep ? s3 : T(0);
+}
+
 // Fusion (Eq. FusionDD): f_CV = sum sbar f / S over a merged control volume,
-// written back to every member, with the moment sums of the result.
+// written back to every member, with the moment sums of the result.  One
+// work item is one control volume and one velocity split.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fusion(CvArgs c, T *f, T *part)
 {
-    __shared__ int32_t mem[kMaxMembers];
-    __shared__ double sb[kMaxMembers];
-    __shared__ double red[8 * 4];
+    __shared__ T red[8 * 2];
     const Grid2D &g = c.g;
+    const CvInfo *info = reinterpret_cast<const CvInfo *>(c.cvinfo);
+    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(c.vt);
     const long nc = (long)g.nx * g.ny;
-    const int n = min(c.counts[0], c.cap);
-    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
-        const long m = c.spec_list[idx];
-        const int nm = gather_members(c, m, mem);
+    const int n = min(c.counts[0], c.cap) * c.S;
+    for (int item = blockIdx.x; item < n; item += gridDim.x) {
+        const CvInfo &I = info[item / c.S];
+        const int sp = item % c.S;
+        const int nm = I.nm;
         if (nm <= 1) continue;
-        double S = 0;
-        for (int q = 0; q < nm; ++q) S += c.Gn.sbar[mem[q]];
-        for (int q = threadIdx.x; q < nm; q += blockDim.x) sb[q] = c.Gn.sbar[mem[q]];
-        __syncthreads();
-        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int v0, v1;
+        split_range(c, sp, Vec<T>::W, v0, v1);
+        const double S = I.Sn;
+        Acc<T> a0, a1, a2, a3;
         for (int comp = 0; comp < 2; ++comp)
-            for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
-                double s = 0;
-                for (int q = 0; q < nm; ++q) s += sb[q] * (double)f[didx<T>(g, mem[q], comp, p)];
-                const T fcv = (T)(s / S);
-                for (int q = 0; q < nm; ++q) f[didx<T>(g, mem[q], comp, p)] = fcv;
-                const double vx = g.vxmin + (p % g.nvx) * g.dvx, vy = g.vymin + (p / g.nvx) * g.dvy;
-                if (comp == 0) { a0 += fcv; a1 += vx * fcv; a2 += vy * fcv; a3 += 0.5 * (vx * vx + vy * vy) * fcv; }
-                else a3 += fcv;
+            for (int p = v0 + threadIdx.x; p < v1; p += blockDim.x) {
+                const long base = ebase<T>(g, comp, p);
+                double acc = 0;
+                for (int q = 0; q < nm; ++q) acc += I.mem[q].sb * (double)f[base + I.mem[q].pc * Vec<T>::W];
+                const T fcv = (T)(acc / S);
+                for (int q = 0; q < nm; ++q) {
+                    f[base + I.mem[q].pc * Vec<T>::W] = fcv;
+                    for (int t = 0; t < 4; ++t)
+                        if (I.mem[q].mir[t] >= 0) f[base + I.mem[q].mir[t] * Vec<T>::W] = fcv;
+                }
+                const VCoef<T> vc = ld_coef(vt + p);
+                if (comp == 0) {
+                    a0.add(fcv); a1.add(vc.vx * fcv); a2.add(vc.vy * fcv);
+                    a3.add(T(0.5) * (vc.vx * vc.vx + vc.vy * vc.vy) * fcv);
+                } else {
+                    a3.add(fcv);
+                }
             }
-        a0 = block_sum(a0, red); a1 = block_sum(a1, red + 8);
-        a2 = block_sum(a2, red + 16); a3 = block_sum(a3, red + 24);
-        if (threadIdx.x < nm)
-            write_member_partials<T>(part, c.S, nc, mem[threadIdx.x], c.Gn.type[mem[threadIdx.x]] != DVM_SOLID,
-                                     (T)a0, (T)a1, (T)a2, (T)a3);
+        const T t0 = block_acc(a0, red), t1 = block_acc(a1, red), t2 = block_acc(a2, red), t3 = block_acc(a3, red);
+        if (threadIdx.x < nm) {
+            const CvMember &M = I.mem[threadIdx.x];
+            const long k = (long)M.j * g.nx + M.i;
+            write_split_partials<T>(part, sp, nc, k, M.live != 0, t0, t1, t2, t3);
+        }
         __syncthreads();
     }
 }
@@ -645,93 +813,115 @@ __device__ __forceinline__ double wall_temperature(const BodyParams &b, double r
     return b.Tw_seg[0];
 }
 
-// Wall density (Eq. BoundaryDDv), stress (Eq. StressTensorDD), the wall-edge
-// flux of every velocity (Eq. FluxDD) and the cell's force and torque
-// (Eqs. eq-force, eq-torque), in FP64.  The wall velocity is
-// u_w = u_c + (r - c)^perp omega (Eq. uwDD) at t^n.  The last block to finish
-// sums the force and torque over the wall list in list order, advances the
-// angular velocity (Eq. motionDD_vit) and records the history.
+// Wall density (Eq. BoundaryDDv), stress (Eq. StressTensorDD), force and
+// torque (Eqs. eq-force, eq-torque), in FP64.  The wall velocity is
+// u_w = u_c + (r - c)^perp omega (Eq. uwDD) at t^n.  A work item is one wall
+// cell and one velocity split: it writes the split's sums over outgoing
+// velocities (of f) and incoming ones (of M[1, u_w, T_w]).  The last block to
+// finish combines the splits of every wall cell in list order: wall density
+// phi, stress, force and torque, their sum over the body, the angular
+// velocity at t^{n+1} (Eq. motionDD_vit) and the history record.  It leaves
+// (phi, u_w, T_w) of each wall cell for the control-volume kernel.
+struct WallGeom {
+    double rx, ry, uwx, uwy, Tw, nwx, nwy, lw;
+};
+
+__device__ __forceinline__ WallGeom wall_geom(const CvArgs &c, const BodyParams &b, long k, double omega)
+{
+    WallGeom w;
+    w.rx = c.Gn.rwx[k] - b.cx;
+    w.ry = c.Gn.rwy[k] - b.cy;
+    w.uwx = b.vbx - w.ry * omega;
+    w.uwy = b.vby + w.rx * omega;
+    w.Tw = wall_temperature(b, w.rx, w.ry);
+    w.nwx = c.Gn.nwx[k];
+    w.nwy = c.Gn.nwy[k];
+    w.lw = c.Gn.lw[k];
+    return w;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_wall(CvArgs c, BodyParams b, BodyDev *body, const T *f,
-                                              T *wflux, double *wphi, double *wcontrib, int *ticket,
+                                              double *wdat, double *wcontrib, int *ticket,
                                               double *hist, int moving)
 {
     __shared__ double red[8 * 8];
-    __shared__ double ex[kMaxAxisNv], ey[kMaxAxisNv];
-    __shared__ double sphi;
+    __shared__ T ex[kMaxAxisNv], ey[kMaxAxisNv];
+    __shared__ T wsc[6];        // uwx, uwy, nwx, nwy, 1/(2 pi Tw), 2 Tw
+    __shared__ T wred[8 * 2];
     __shared__ bool last;
     const Grid2D &g = c.g;
-    const int n = min(c.counts[1], c.cap);
+    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(c.vt);
+    const int nw = min(c.counts[1], c.cap);
     const double omega = body->omega;
-    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
+    const int tid = threadIdx.x;
+    for (int idx = blockIdx.x; idx < nw; idx += gridDim.x) {
         const long k = c.wall_list[idx];
-        const double rx = c.Gn.rwx[k] - b.cx, ry = c.Gn.rwy[k] - b.cy;
-        const double uwx = b.vbx - ry * omega, uwy = b.vby + rx * omega;
-        const double Tw = wall_temperature(b, rx, ry);
-        const double nwx = c.Gn.nwx[k], nwy = c.Gn.nwy[k], lw = c.Gn.lw[k];
+        if (tid == 0) {
+            const WallGeom w = wall_geom(c, b, k, omega);
+            wsc[0] = (T)w.uwx; wsc[1] = (T)w.uwy; wsc[2] = (T)w.nwx; wsc[3] = (T)w.nwy;
+            wsc[4] = (T)(1.0 / (2.0 * kPi * w.Tw)); wsc[5] = (T)(2.0 * w.Tw);
+        }
+        __syncthreads();
+        const T uwx = wsc[0], uwy = wsc[1], nwx = wsc[2], nwy = wsc[3], cm = wsc[4], twoTw = wsc[5];
         // separable Maxwellian M[1, u_w, T_w] = ex[p1] ey[p2] / (2 pi T_w)
-        for (int q = threadIdx.x; q < g.nvx + g.nvy; q += blockDim.x) {
-            if (q < g.nvx) { double d = g.vxmin + q * g.dvx - uwx; ex[q] = exp(-(d * d) / (2.0 * Tw)); }
-            else { int qq = q - g.nvx; double d = g.vymin + qq * g.dvy - uwy; ey[qq] = exp(-(d * d) / (2.0 * Tw)); }
+        for (int q = tid; q < g.nvx + g.nvy; q += blockDim.x) {
+            if (q < g.nvx) { T d = vt[q].vx - uwx; ex[q] = dexp(-(d * d) / twoTw); }
+            else { int qq = q - g.nvx; T d = vt[qq * g.nvx].vy - uwy; ey[qq] = dexp(-(d * d) / twoTw); }
         }
         __syncthreads();
-        const double cm = 1.0 / (2.0 * kPi * Tw);
-        double num = 0, den = 0, ixx = 0, ixy = 0, iyy = 0, oxx = 0, oxy = 0, oyy = 0;
-        for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
-            const int p1 = p % g.nvx, p2 = p / g.nvx;
-            const double ax = g.vxmin + p1 * g.dvx - uwx, ay = g.vymin + p2 * g.dvy - uwy;
-            const double cp = ax * nwx + ay * nwy;
-            if (cp > 0) {
-                const double fv = (double)f[didx<T>(g, k, 0, p)];
-                num += cp * fv;
-                oxx += ax * ax * fv; oxy += ax * ay * fv; oyy += ay * ay * fv;
-            } else if (cp < 0) {
-                const double m1 = cm * ex[p1] * ey[p2];
-                den += cp * m1;
-                ixx += ax * ax * m1; ixy += ax * ay * m1; iyy += ay * ay * m1;
+        // products and compensated sums in the state precision; the wall
+        // density, stress and force are formed from them in FP64
+        const long pck = pcell(g, k) * Vec<T>::W;
+        Acc<T> a0, a1, a2, a3, a4, a5, a6, a7;
+        int p1 = tid % g.nvx, p2 = tid / g.nvx;
+        const int dp1 = blockDim.x % g.nvx, dp2 = blockDim.x / g.nvx;
+        for (int p = tid; p < g.nv; p += blockDim.x) {
+            const VCoef<T> vc = ld_coef(vt + p);
+            const T ax = vc.vx - uwx, ay = vc.vy - uwy;
+            const T cp = ax * nwx + ay * nwy;
+            if (cp > T(0)) {
+                const T fv = f[ebase<T>(g, 0, p) + pck];
+                a0.add(cp * fv);
+                a5.add(ax * ax * fv); a6.add(ax * ay * fv); a7.add(ay * ay * fv);
+            } else if (cp < T(0)) {
+                const T m1 = cm * ex[p1] * ey[p2];
+                a1.add(cp * m1);
+                a2.add(ax * ax * m1); a3.add(ax * ay * m1); a4.add(ay * ay * m1);
             }
+            p1 += dp1; p2 += dp2;
+            if (p1 >= g.nvx) { p1 -= g.nvx; p2 += 1; }
         }
-        num = block_sum(num, red); den = block_sum(den, red + 8);
-        ixx = block_sum(ixx, red + 16); ixy = block_sum(ixy, red + 24); iyy = block_sum(iyy, red + 32);
-        oxx = block_sum(oxx, red + 40); oxy = block_sum(oxy, red + 48); oyy = block_sum(oyy, red + 56);
-        if (threadIdx.x == 0) {
-            const double phi = -(num * g.dv) / (den * g.dv);
-            const double sxx = (phi * ixx + oxx) * g.dv, sxy = (phi * ixy + oxy) * g.dv;
-            const double syy = (phi * iyy + oyy) * g.dv;
-            const double fx = (sxx * nwx + sxy * nwy) * lw, fy = (sxy * nwx + syy * nwy) * lw;
-            wphi[idx] = phi;
-            wcontrib[3 * idx] = fx;
-            wcontrib[3 * idx + 1] = fy;
-            wcontrib[3 * idx + 2] = rx * fy - ry * fx;
-            sphi = phi;
+        const T r0 = block_acc(a0, wred), r1 = block_acc(a1, wred), r2 = block_acc(a2, wred);
+        const T r3 = block_acc(a3, wred), r4 = block_acc(a4, wred), r5 = block_acc(a5, wred);
+        const T r6 = block_acc(a6, wred), r7 = block_acc(a7, wred);
+        if (tid == 0) {
+            const WallGeom w = wall_geom(c, b, k, omega);
+            const double phi = -((double)r0 * g.dv) / ((double)r1 * g.dv);
+            const double sxx = (phi * (double)r2 + (double)r5) * g.dv, sxy = (phi * (double)r3 + (double)r6) * g.dv;
+            const double syy = (phi * (double)r4 + (double)r7) * g.dv;
+            const double fkx = (sxx * w.nwx + sxy * w.nwy) * w.lw, fky = (sxy * w.nwx + syy * w.nwy) * w.lw;
+            wcontrib[3 * idx] = fkx;
+            wcontrib[3 * idx + 1] = fky;
+            wcontrib[3 * idx + 2] = w.rx * fky - w.ry * fkx;
+            double *d = wdat + 4L * idx;
+            d[0] = phi; d[1] = w.uwx; d[2] = w.uwy; d[3] = w.Tw;
         }
-        __syncthreads();
-        const double phi = sphi;
-        for (int comp = 0; comp < 2; ++comp)
-            for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
-                const int p1 = p % g.nvx, p2 = p / g.nvx;
-                const double ax = g.vxmin + p1 * g.dvx - uwx, ay = g.vymin + p2 * g.dvy - uwy;
-                const double cp = ax * nwx + ay * nwy;
-                const double m1 = cm * ex[p1] * ey[p2];
-                const double fw = comp == 0 ? phi * m1 : phi * (Tw / 2.0 * m1);
-                const double fv = (double)f[didx<T>(g, k, comp, p)];
-                wflux[((long)idx * 2 + comp) * g.nv + p] = (T)(lw * (fmin(cp, 0.0) * fw + fmax(cp, 0.0) * fv));
-            }
         __syncthreads();
     }
     // the last block sums the contributions in list order
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    if (tid == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
     double fx = 0, fy = 0, tq = 0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    for (int t = tid; t < nw; t += blockDim.x) {
         fx += wcontrib[3 * t]; fy += wcontrib[3 * t + 1]; tq += wcontrib[3 * t + 2];
     }
     fx = block_sum(fx, red); fy = block_sum(fy, red + 8); tq = block_sum(tq, red + 16);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         body->F[0] = fx; body->F[1] = fy; body->F[2] = 0; body->torque = tq;
         const double om1 = moving ? body->omega + g.dt * tq / b.inertia : body->omega;
         body->theta = body->theta1;
@@ -750,90 +940,114 @@ __global__ void __launch_bounds__(256) k_wall(CvArgs c, BodyParams b, BodyDev *b
 template <typename T>
 __device__ __forceinline__ T fval(const Grid2D &g, const T *f, int i, int j, int comp, int p)
 {
-    return f[didx<T>(g, nbr(g, i, j), comp, p)];
+    constexpr int W = Vec<T>::W;
+    return f[((long)(p / W) * 2 + comp) * g.slab * W + nbr(g, i, j) * W + (p % W)];
 }
 
 // Explicit update of one control volume (Eq. ExSchemeDD): fluxes across the
-// Cartesian edges of every member (Eq. FluxDD) plus its wall-edge flux,
-// area ratio S^n / S^{n+1,*}, relaxation, then distribution to the members
-// (Eq. UpdateDD; members solid at t^{n+1} hold 0) and the moment sums.
+// Cartesian edges of every member (Eq. FluxDD) and across its wall edge with
+// the diffuse-reflection state f_w = phi M[1, u_w, T_w], g_w = T_w/2 f_w on
+// incoming velocities (Eq. BoundaryDDv; phi from the FP64 wall kernel), area
+// ratio S^n / S^{n+1,*}, relaxation, then distribution to the members (Eq.
+// UpdateDD; members solid at t^{n+1} hold 0) and the moment sums of the
+// velocity split.  One work item is one control volume and one split.
+// Copy of one control-volume record into shared memory (16-byte words).
+__device__ __forceinline__ void load_info(const CvInfo *src, CvInfo *dst)
+{
+    static_assert(sizeof(CvInfo) % 16 == 0, "CvInfo is copied in 16-byte words");
+    const int4 *s4 = reinterpret_cast<const int4 *>(src);
+    int4 *d4 = reinterpret_cast<int4 *>(dst);
+    for (int q = threadIdx.x; q < (int)(sizeof(CvInfo) / 16); q += blockDim.x) d4[q] = __ldg(s4 + q);
+    __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_special(CvArgs c, const T *fin, T *fout, const T *pin,
-                                                 T *pout, const T *wflux)
+                                                 T *pout, const double *wdat)
 {
-    __shared__ int32_t mem[kMaxMembers];
-    __shared__ T L[kMaxMembers][4];           // lx-, lx+, ly-, ly+
-    __shared__ int32_t ws[kMaxMembers];       // wall slot
-    __shared__ int8_t mk[kMaxMembers];        // limiter mask
-    __shared__ int8_t live[kMaxMembers];      // non-solid at t^n
-    __shared__ int8_t keep[kMaxMembers];      // non-solid at t^{n+1}
-    __shared__ double red[8 * 4];
+    __shared__ T red[8 * 2];
+    __shared__ __align__(16) CvInfo I;
     const Grid2D &g = c.g;
+    const CvInfo *info = reinterpret_cast<const CvInfo *>(c.cvinfo);
+    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(c.vt);
     const long nc = (long)g.nx * g.ny;
-    const int n = min(c.counts[0], c.cap);
-    const int W1 = g.nx + 1;
-    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
+    const int n = min(c.counts[0], c.cap) * c.S;
+    constexpr int W = Vec<T>::W;
+    for (int item = blockIdx.x; item < n; item += gridDim.x) {
+        const int idx = item / c.S, sp = item % c.S;
+        load_info(info + idx, &I);
+        if (!I.ok) { __syncthreads(); continue; }
+        const int nm = I.nm;
+        int v0, v1;
+        split_range(c, sp, W, v0, v1);
         const long m = c.spec_list[idx];
-        const int nm = gather_members(c, m, mem);
-        for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-            const long k = mem[q];
-            const int i = (int)(k % g.nx), j = (int)(k / g.nx);
-            L[q][0] = (T)c.Gn.lx[(long)j * W1 + i];
-            L[q][1] = (T)c.Gn.lx[(long)j * W1 + i + 1];
-            L[q][2] = (T)c.Gn.ly[(long)j * g.nx + i];
-            L[q][3] = (T)c.Gn.ly[(long)(j + 1) * g.nx + i];
-            ws[q] = c.wslot[k];
-            mk[q] = (int8_t)(c.flags[k] >> kMaskShift);
-            live[q] = c.Gn.type[k] != DVM_SOLID;
-            keep[q] = c.Gp.type[k] != DVM_SOLID;
-        }
-        __syncthreads();
-        double Sn = 0, Sp = 0;
-        for (int q = 0; q < nm; ++q) { Sn += c.Gn.sbar[mem[q]]; Sp += c.Gp.sbar[mem[q]]; }
-        if (!(Sp > 0)) {
-            if (threadIdx.x == 0) atomicExch(&c.err[kErrGeometry], 1);
-            __syncthreads();
-            continue;
-        }
         T s[4];
         gather_partials(pin, c.S, nc, m, s);
         T rho, ux, uy, tmp;
-        if (!primitives<T>(g.dv, s[0], s[1], s[2], s[3], rho, ux, uy, tmp) && threadIdx.x == 0)
+        if (!primitives<T>(pick<T>(g.dv_f, g.dv), s[0], s[1], s[2], s[3], rho, ux, uy, tmp) && threadIdx.x == 0 && sp == 0)
             atomicExch(&c.err[kErrNonphys], 1);
-        const T a = T(Sn / Sp), bco = T(g.dt / Sp), r = T(g.dt / g.tau0) * rho;
+        const T a = (T)I.a, bco = (T)I.bco, r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
         const T A = rho / (T(2.0 * kPi) * tmp);
+        const T i2T = T(1) / (T(2) * tmp);
         Acc<T> s0, s1, s2, s3;
-        for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
-            const int p1 = p % g.nvx, p2 = p / g.nvx;
-            const T vx = T(g.vxmin + p1 * g.dvx), vy = T(g.vymin + p2 * g.dvy);
-            const T nux = fabs(vx) * T(g.dt / g.dx), nuy = fabs(vy) * T(g.dt / g.dy);
+        for (int p = v0 + threadIdx.x; p < v1; p += blockDim.x) {
+            const VCoef<T> vc = ld_coef(vt + p);
+            const T vx = vc.vx, vy = vc.vy, nux = vc.nux, nuy = vc.nuy;
             const T dxu = vx - ux, dyu = vy - uy;
-            const T feq0 = A * dexp(-(dxu * dxu + dyu * dyu) / (T(2) * tmp));
-            for (int comp = 0; comp < 2; ++comp) {
-                T R = 0;
-                for (int q = 0; q < nm; ++q) {
-                    if (!live[q]) continue;
-                    const long k = mem[q];
-                    const int i = (int)(k % g.nx), j = (int)(k / g.nx);
-                    const T fc = fin[didx<T>(g, k, comp, p)];
-                    const T fxm1 = fval(g, fin, i - 1, j, comp, p), fxp1 = fval(g, fin, i + 1, j, comp, p);
-                    const T fym1 = fval(g, fin, i, j - 1, comp, p), fyp1 = fval(g, fin, i, j + 1, comp, p);
-                    T fxm2 = 0, fxp2 = 0, fym2 = 0, fyp2 = 0;
-                    if (mk[q]) {
-                        fxm2 = fval(g, fin, i - 2, j, comp, p); fxp2 = fval(g, fin, i + 2, j, comp, p);
-                        fym2 = fval(g, fin, i, j - 2, comp, p); fyp2 = fval(g, fin, i, j + 2, comp, p);
-                    }
-                    const T Fxp = face_flux<T>(L[q][1], vx, nux, fxm1, fc, fxp1, fxp2, mk[q] & 2);
-                    const T Fxm = face_flux<T>(L[q][0], vx, nux, fxm2, fxm1, fc, fxp1, mk[q] & 1);
-                    const T Fyp = face_flux<T>(L[q][3], vy, nuy, fym1, fc, fyp1, fyp2, mk[q] & 8);
-                    const T Fym = face_flux<T>(L[q][2], vy, nuy, fym2, fym1, fc, fyp1, mk[q] & 4);
-                    const T Fw = ws[q] >= 0 ? wflux[((long)ws[q] * 2 + comp) * g.nv + p] : T(0);
-                    R += (Fxp - Fxm) + (Fyp - Fym) + Fw;
+            const T feq0 = A * dexp(-(dxu * dxu + dyu * dyu) * i2T);
+            const long base0 = ebase<T>(g, 0, p), base1 = ebase<T>(g, 1, p);
+            T R0 = 0, R1 = 0;
+            for (int q = 0; q < nm; ++q) {
+                const CvMember &M = I.mem[q];
+                if (!M.live) continue;
+                const int i = M.i, j = M.j;
+                const bool mus = M.mask != 0;
+                T Fw0 = 0, Fw1 = 0;
+                const T f0 = fin[base0 + M.pc * W], f1 = fin[base1 + M.pc * W];
+                if (M.wslot >= 0) {
+                    // diffuse reflection: incoming state f_w and the flux
+                    // lw [min(c, 0) f_w + max(c, 0) f] across the wall edge
+                    const double *d = wdat + 4L * M.wslot;
+                    const T phi = (T)d[0], uwx = (T)d[1], uwy = (T)d[2], Tw = (T)d[3];
+                    const T ax = vx - uwx, ay = vy - uwy;
+                    const T cw = ax * (T)M.nwx + ay * (T)M.nwy;
+                    const T m1 = dexp(-(ax * ax + ay * ay) / (T(2) * Tw)) / (T(2.0 * kPi) * Tw);
+                    const T lw = (T)M.lw;
+                    Fw0 = lw * (fmin(cw, T(0)) * (phi * m1) + fmax(cw, T(0)) * f0);
+                    Fw1 = lw * (fmin(cw, T(0)) * (phi * (Tw / T(2) * m1)) + fmax(cw, T(0)) * f1);
                 }
-                const T fcv = fin[didx<T>(g, m, comp, p)];
+#pragma unroll
+                for (int comp = 0; comp < 2; ++comp) {
+                    const long base = comp == 0 ? base0 : base1;
+                    const T fc = comp == 0 ? f0 : f1;
+                    const T fxm1 = fin[base + nbr(g, i - 1, j) * W], fxp1 = fin[base + nbr(g, i + 1, j) * W];
+                    const T fym1 = fin[base + nbr(g, i, j - 1) * W], fyp1 = fin[base + nbr(g, i, j + 1) * W];
+                    T fxm2 = 0, fxp2 = 0, fym2 = 0, fyp2 = 0;
+                    if (mus) {
+                        fxm2 = fin[base + nbr(g, i - 2, j) * W]; fxp2 = fin[base + nbr(g, i + 2, j) * W];
+                        fym2 = fin[base + nbr(g, i, j - 2) * W]; fyp2 = fin[base + nbr(g, i, j + 2) * W];
+                    }
+                    const T Fxp = face_flux<T>((T)M.L[1], vx, nux, fxm1, fc, fxp1, fxp2, M.mask & 2);
+                    const T Fxm = face_flux<T>((T)M.L[0], vx, nux, fxm2, fxm1, fc, fxp1, M.mask & 1);
+                    const T Fyp = face_flux<T>((T)M.L[3], vy, nuy, fym1, fc, fyp1, fyp2, M.mask & 8);
+                    const T Fym = face_flux<T>((T)M.L[2], vy, nuy, fym2, fym1, fc, fyp1, M.mask & 4);
+                    const T Rq = (Fxp - Fxm) + (Fyp - Fym) + (comp == 0 ? Fw0 : Fw1);
+                    if (comp == 0) R0 += Rq; else R1 += Rq;
+                }
+            }
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                const long base = comp == 0 ? base0 : base1;
+                const T fcv = fin[base + I.pcm * W];
                 const T feq = comp == 0 ? feq0 : tmp / T(2) * feq0;
-                const T fn = a * fcv - bco * R + a * r * (feq - fcv);
-                for (int q = 0; q < nm; ++q) fout[didx<T>(g, mem[q], comp, p)] = keep[q] ? fn : T(0);
+                const T fn = a * fcv - bco * (comp == 0 ? R0 : R1) + a * r * (feq - fcv);
+                for (int q = 0; q < nm; ++q) {
+                    const CvMember &M = I.mem[q];
+                    const T v = M.keep ? fn : T(0);
+                    fout[base + M.pc * W] = v;
+                    for (int t = 0; t < 4; ++t)
+                        if (M.mir[t] >= 0) fout[base + M.mir[t] * W] = v;
+                }
                 if (comp == 0) {
                     s0.add(fn); s1.add(vx * fn); s2.add(vy * fn);
                     s3.add(T(0.5) * (vx * vx + vy * vy) * fn);
@@ -842,10 +1056,12 @@ __global__ void __launch_bounds__(256) k_special(CvArgs c, const T *fin, T *fout
                 }
             }
         }
-        const double t0 = block_sum((double)s0.value(), red), t1 = block_sum((double)s1.value(), red + 8);
-        const double t2 = block_sum((double)s2.value(), red + 16), t3 = block_sum((double)s3.value(), red + 24);
-        if (threadIdx.x < nm) write_member_partials<T>(pout, c.S, nc, mem[threadIdx.x], keep[threadIdx.x],
-                                                       (T)t0, (T)t1, (T)t2, (T)t3);
+        const T t0 = block_acc(s0, red), t1 = block_acc(s1, red);
+        const T t2 = block_acc(s2, red), t3 = block_acc(s3, red);
+        if (threadIdx.x < nm) {
+            const CvMember &M = I.mem[threadIdx.x];
+            write_split_partials<T>(pout, sp, nc, (long)M.j * g.nx + M.i, M.keep != 0, t0, t1, t2, t3);
+        }
         __syncthreads();
     }
 }
@@ -870,19 +1086,20 @@ __global__ void __launch_bounds__(256) k_partials(Grid2D g, int S, const T *f, T
     const long cell = (long)blockIdx.x * 8 + warp;
     if (cell >= nc) return;
     Acc<T> s0, s1, s2, s3;
+    const long pc = pcell(g, cell) * Vec<T>::W;
     for (int p = lane; p < g.nv; p += 32) {
         const T vx = T(g.vxmin + (p % g.nvx) * g.dvx), vy = T(g.vymin + (p / g.nvx) * g.dvy);
-        const T fv = f[didx<T>(g, cell, 0, p)];
+        const T fv = f[ebase<T>(g, 0, p) + pc];
         s0.add(fv); s1.add(vx * fv); s2.add(vy * fv);
         s3.add(T(0.5) * (vx * vx + vy * vy) * fv);
-        s3.add(f[didx<T>(g, cell, 1, p)]);
+        s3.add(f[ebase<T>(g, 1, p) + pc]);
     }
     s0.warp_reduce(); s1.warp_reduce(); s2.warp_reduce(); s3.warp_reduce();
     if (lane == 0) {
         const bool keep = type[cell] != DVM_SOLID;
         if (keep) {
             T rho, ux, uy, tmp;
-            if (!primitives<T>(g.dv, s0.value(), s1.value(), s2.value(), s3.value(), rho, ux, uy, tmp))
+            if (!primitives<T>(pick<T>(g.dv_f, g.dv), s0.value(), s1.value(), s2.value(), s3.value(), rho, ux, uy, tmp))
                 atomicExch(&err[kErrNonphys], 1);
         }
         write_member_partials<T>(part, S, nc, cell, keep, s0.value(), s1.value(), s2.value(), s3.value());
@@ -897,11 +1114,12 @@ __global__ void __launch_bounds__(256) k_moments_out(Grid2D g, const T *f, doubl
     const long cell = (long)blockIdx.x * 8 + warp;
     if (cell >= (long)g.nx * g.ny) return;
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    const long pc = pcell(g, cell) * Vec<T>::W;
     for (int p = lane; p < g.nv; p += 32) {
         const double vx = g.vxmin + (p % g.nvx) * g.dvx, vy = g.vymin + (p / g.nvx) * g.dvy;
-        const double fv = (double)f[didx<T>(g, cell, 0, p)];
+        const double fv = (double)f[ebase<T>(g, 0, p) + pc];
         s0 += fv; s1 += vx * fv; s2 += vy * fv;
-        s3 += 0.5 * (vx * vx + vy * vy) * fv + (double)f[didx<T>(g, cell, 1, p)];
+        s3 += 0.5 * (vx * vx + vy * vy) * fv + (double)f[ebase<T>(g, 1, p) + pc];
     }
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -922,11 +1140,10 @@ __global__ void __launch_bounds__(256) k_moments_out(Grid2D g, const T *f, doubl
 template <typename T>
 __global__ void k_init(Grid2D g, const double *prim, const int8_t *type, T *f)
 {
-    const long nc = (long)g.nx * g.ny;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nc * g.nv) return;
-    const long k = t / g.nv;
-    const int p = (int)(t % g.nv);
+    const long k = blockIdx.x;            // one block per cell, threads over velocities
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    if (p >= g.nv) return;
+    const long pc = pcell(g, k) * Vec<T>::W;
     const double *q = prim + 5 * k;
     double m = 0;
     if (type[k] != DVM_SOLID && q[0] > 0) {
@@ -934,8 +1151,8 @@ __global__ void k_init(Grid2D g, const double *prim, const int8_t *type, T *f)
         const double ay = g.vymin + (p / g.nvx) * g.dvy - q[2];
         m = q[0] / (2.0 * kPi * q[4]) * exp(-(ax * ax + ay * ay) / (2.0 * q[4]));
     }
-    f[didx<T>(g, k, 0, p)] = (T)m;
-    f[didx<T>(g, k, 1, p)] = (T)(q[4] / 2.0 * m);
+    f[ebase<T>(g, 0, p) + pc] = (T)m;
+    f[ebase<T>(g, 1, p) + pc] = (T)(q[4] / 2.0 * m);
 }
 
 // Ghost cells of a Maxwellian side from (rho, ux, uy, uz, T) per side cell,
@@ -951,23 +1168,62 @@ __global__ void k_ghost(Grid2D g, const double *prim, int side, int nside, T *f0
     const double ax = g.vxmin + (p % g.nvx) * g.dvx - s[1];
     const double ay = g.vymin + (p / g.nvx) * g.dvy - s[2];
     const double m = s[0] / (2.0 * kPi * s[4]) * exp(-(ax * ax + ay * ay) / (2.0 * s[4]));
-    const long cell = (long)g.nx * g.ny + g.gofs[side] + q;
-    f0[didx<T>(g, cell, 0, p)] = (T)m;
-    f0[didx<T>(g, cell, 1, p)] = (T)(s[4] / 2.0 * m);
-    f1[didx<T>(g, cell, 0, p)] = (T)m;
-    f1[didx<T>(g, cell, 1, p)] = (T)(s[4] / 2.0 * m);
+    constexpr int W = Vec<T>::W;
+    const long base0 = ((long)(p / W) * 2) * g.slab * W + (p % W);
+    const long base1 = base0 + g.slab * W;
+    for (int layer = 1; layer <= 2; ++layer) {
+        long pcg;
+        if (side == 0) pcg = nbr(g, -layer, (int)q);
+        else if (side == 1) pcg = nbr(g, g.nx - 1 + layer, (int)q);
+        else if (side == 2) pcg = nbr(g, (int)q, -layer);
+        else pcg = nbr(g, (int)q, g.ny - 1 + layer);
+        f0[base0 + pcg * W] = (T)m;
+        f0[base1 + pcg * W] = (T)(s[4] / 2.0 * m);
+        f1[base0 + pcg * W] = (T)m;
+        f1[base1 + pcg * W] = (T)(s[4] / 2.0 * m);
+    }
+}
+
+// Padding of periodic and zero-gradient sides from the interior of a state
+// buffer (both layers, every group and component).
+template <typename T>
+__global__ void k_halo(Grid2D g, T *f)
+{
+    constexpr int W = Vec<T>::W;
+    const long per = 2L * (g.nx + g.ny);      // padding cells of one layer (cross arms)
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * per * 2 * g.nvp) return;
+    const long hc = t % (2 * per);            // padding cell: layer, side, position
+    const long rest = t / (2 * per);
+    const int comp = (int)(rest % 2), p = (int)(rest / 2);
+    const int layer = (int)(hc / per) + 1;
+    long pos = hc % per;
+    int side, q;
+    if (pos < g.ny) { side = 0; q = (int)pos; }
+    else if (pos < 2L * g.ny) { side = 1; q = (int)(pos - g.ny); }
+    else if (pos < 2L * g.ny + g.nx) { side = 2; q = (int)(pos - 2L * g.ny); }
+    else { side = 3; q = (int)(pos - 2L * g.ny - g.nx); }
+    const int kind = g.bc[side];
+    if (kind == DVM_BC_MAXWELLIAN) return;
+    int di, dj, si, sj;
+    if (side == 0) { di = -layer; dj = q; si = kind == DVM_BC_PERIODIC ? g.nx - layer : 0; sj = q; }
+    else if (side == 1) { di = g.nx - 1 + layer; dj = q; si = kind == DVM_BC_PERIODIC ? layer - 1 : g.nx - 1; sj = q; }
+    else if (side == 2) { di = q; dj = -layer; si = q; sj = kind == DVM_BC_PERIODIC ? g.ny - layer : 0; }
+    else { di = q; dj = g.ny - 1 + layer; si = q; sj = kind == DVM_BC_PERIODIC ? layer - 1 : g.ny - 1; }
+    const long base = ((long)(p / W) * 2 + comp) * g.slab * W + (p % W);
+    f[base + nbr(g, di, dj) * W] = f[base + nbr(g, si, sj) * W];
 }
 
 // Conversion between the public layout [cell][comp][p] and the device layout.
 template <typename T>
 __global__ void k_pack(Grid2D g, const T *src, T *dst, int to_dev)
 {
-    const long nc = (long)g.nx * g.ny;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nc * 2 * g.nv) return;
-    const long k = t / (2L * g.nv);
-    const int comp = (int)((t / g.nv) % 2), p = (int)(t % g.nv);
-    const long d = didx<T>(g, k, comp, p);
+    const long k = blockIdx.x;            // one block per cell, threads over (comp, p)
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= 2 * g.nv) return;
+    const int comp = e >= g.nv, p = e - comp * g.nv;
+    const long t = k * 2L * g.nv + e;
+    const long d = ebase<T>(g, comp, p) + pcell(g, k) * Vec<T>::W;
     if (to_dev) dst[d] = src[t];
     else dst[t] = src[d];
 }
@@ -976,14 +1232,12 @@ __global__ void k_pack(Grid2D g, const T *src, T *dst, int to_dev)
 template <typename T>
 __global__ void k_zero_solid(Grid2D g, const int8_t *type, T *f)
 {
-    const long nc = (long)g.nx * g.ny;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nc * 2 * g.nvp) return;
-    const long k = t % nc;
+    const long k = blockIdx.x;            // one block per cell, threads over (comp, p)
     if (type[k] != DVM_SOLID) return;
-    const long rest = t / nc;
-    const int comp = (int)(rest % 2), p = (int)(rest / 2);
-    f[didx<T>(g, k, comp, p)] = T(0);
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= 2 * g.nvp) return;
+    const int comp = e >= g.nvp, p = e - comp * g.nvp;
+    f[ebase<T>(g, comp, p) + pcell(g, k) * Vec<T>::W] = T(0);
 }
 
 // Per-cell mass sbar * sum_p f dv (FP64), then a fixed-order sum.
@@ -994,7 +1248,8 @@ __global__ void __launch_bounds__(256) k_mass_cells(Grid2D g, const T *f, const 
     const long cell = (long)blockIdx.x * 8 + warp;
     if (cell >= (long)g.nx * g.ny) return;
     double s = 0;
-    for (int p = lane; p < g.nv; p += 32) s += (double)f[didx<T>(g, cell, 0, p)];
+    const long pc = pcell(g, cell) * Vec<T>::W;
+    for (int p = lane; p < g.nv; p += 32) s += (double)f[ebase<T>(g, 0, p) + pc];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) cm[cell] = sbar[cell] * (s * g.dv);
 }
@@ -1045,7 +1300,7 @@ inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 template <typename T, bool MUSCL>
 cudaError_t launch_bulk(dvm_ctx *c, const BulkArgs<T> &a)
 {
-    const size_t smem = (size_t)kStages * kStageBytes + kStages * sizeof(uint64_t);
+    const size_t smem = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_bulk<T, MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1071,7 +1326,7 @@ cudaError_t step2d_t(dvm_ctx *c)
         k_advance<<<1, 32, 0, c->stream>>>(c->d_body, c->dt, 1);
         if ((e = geometry2d_level(c, 1 - c->gcur, body_trig(c, 2))) != cudaSuccess) return e;
         if ((e = masters_flags2d(c, true)) != cudaSuccess) return e;
-        c->launches += 8;
+        c->launches += 9;
     }
     CvArgs cv;
     cv.g = g;
@@ -1080,15 +1335,17 @@ cudaError_t step2d_t(dvm_ctx *c)
     cv.master = c->master; cv.flags = c->flags;
     cv.spec_list = c->spec_list; cv.wall_list = c->wall_list; cv.wslot = c->wslot;
     cv.counts = c->counts; cv.cap = c->list_cap; cv.S = c->S;
+    cv.gps = (c->ngrp + c->S - 1) / c->S;
+    cv.cvinfo = c->cvinfo; cv.vt = c->vtab;
     cv.err = c->d_err;
-    const int cvgrid = 2 * 152;
+    const int cvgrid = 4 * 152;
     if (body) {
         if (moving || c->need_fusion) {
             k_fusion<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, pin);
             c->launches += 1;
         }
-        k_wall<T><<<cvgrid, 256, 0, c->stream>>>(cv, bp, c->d_body, fin, (T *)c->wflux, c->wphi,
-                                                  c->wcontrib, c->ticket, c->d_hist, moving ? 1 : 0);
+        k_wall<T><<<cvgrid, 256, 0, c->stream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
+                                                  c->d_hist, moving ? 1 : 0);
         c->launches += 1;
     }
     BulkArgs<T> a;
@@ -1100,7 +1357,7 @@ cudaError_t step2d_t(dvm_ctx *c)
     if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
     c->launches += 1;
     if (body) {
-        k_special<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, fout, pin, pout, (const T *)c->wflux);
+        k_special<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, fout, pin, pout, c->wphi);
         c->launches += 1;
     }
     c->cur = 1 - c->cur;
@@ -1112,9 +1369,9 @@ cudaError_t step2d_t(dvm_ctx *c)
 
 }  // namespace
 
-// TMA descriptors of the two state buffers: a 3D view (x: cells of a row
-// times the W velocities of a group, y: rows, z: group and component) of
-// the interior cells of each slab; the box is the bulk kernel's tile.
+// TMA descriptors of the two state buffers: a 3D view (x: padded cells of a
+// row times the W velocities of a group, y: padded rows, z: group and
+// component) of each slab; the box is the bulk kernel's tile with its halo.
 int make_tensor_maps2d(dvm_ctx *c)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -1129,8 +1386,8 @@ int make_tensor_maps2d(dvm_ctx *c)
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     const int W = c->W;
-    const cuuint64_t dims[3] = {(cuuint64_t)c->nx * W, (cuuint64_t)c->ny, (cuuint64_t)2 * c->ngrp};
-    const cuuint64_t strides[2] = {(cuuint64_t)c->nx * W * c->elem, (cuuint64_t)c->slab * W * c->elem};
+    const cuuint64_t dims[3] = {(cuuint64_t)(c->nx + 4) * W, (cuuint64_t)(c->ny + 4), (cuuint64_t)2 * c->ngrp};
+    const cuuint64_t strides[2] = {(cuuint64_t)(c->nx + 4) * W * c->elem, (cuuint64_t)c->slab * W * c->elem};
     const cuuint32_t box[3] = {(cuuint32_t)kTileX * W, (cuuint32_t)kTileY, 2};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = c->prec == DVM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
@@ -1147,6 +1404,21 @@ int make_tensor_maps2d(dvm_ctx *c)
 }
 
 size_t vcoef_bytes(int prec) { return prec == DVM_FP32 ? sizeof(VCoef<float>) : sizeof(VCoef<double>); }
+
+size_t cvinfo_bytes() { return sizeof(CvInfo); }
+
+cudaError_t members2d(dvm_ctx *c, bool moving)
+{
+    CvArgs cv;
+    cv.g = grid2d(c);
+    cv.Gn = c->geo[c->gcur];
+    cv.Gp = moving ? c->geo[1 - c->gcur] : c->geo[c->gcur];
+    cv.master = c->master; cv.flags = c->flags; cv.wslot = c->wslot;
+    cv.spec_list = c->spec_list; cv.counts = c->counts; cv.cap = c->list_cap;
+    cv.err = c->d_err;
+    k_members<<<4 * 152, 256, 0, c->stream>>>(cv, (CvInfo *)c->cvinfo);
+    return cudaGetLastError();
+}
 
 cudaError_t step2d(dvm_ctx *c)
 {
@@ -1191,11 +1463,11 @@ cudaError_t moments_out2d(dvm_ctx *c, double *d_out)
 cudaError_t init_maxwellian2d(dvm_ctx *c, const double *d_prim)
 {
     Grid2D g = grid2d(c);
-    const long n = (long)c->nx * c->ny * c->nv;
+    dim3 grid((unsigned)(c->nx * c->ny), nblk(c->nv, 256));
     if (c->prec == DVM_FP32)
-        k_init<float><<<nblk(n, 256), 256, 0, c->stream>>>(g, d_prim, c->geo[c->gcur].type, (float *)c->f[c->cur]);
+        k_init<float><<<grid, 256, 0, c->stream>>>(g, d_prim, c->geo[c->gcur].type, (float *)c->f[c->cur]);
     else
-        k_init<double><<<nblk(n, 256), 256, 0, c->stream>>>(g, d_prim, c->geo[c->gcur].type, (double *)c->f[c->cur]);
+        k_init<double><<<grid, 256, 0, c->stream>>>(g, d_prim, c->geo[c->gcur].type, (double *)c->f[c->cur]);
     return cudaGetLastError();
 }
 
@@ -1213,35 +1485,44 @@ cudaError_t ghost2d(dvm_ctx *c, int side, const double *d_prim, int nside)
 cudaError_t pack2d(dvm_ctx *c, const void *pub, void *dev)
 {
     Grid2D g = grid2d(c);
-    const long n = (long)c->nx * c->ny * 2 * c->nv;
+    dim3 grid((unsigned)(c->nx * c->ny), nblk(2 * c->nv, 256));
     if (c->prec == DVM_FP32)
-        k_pack<float><<<nblk(n, 256), 256, 0, c->stream>>>(g, (const float *)pub, (float *)dev, 1);
+        k_pack<float><<<grid, 256, 0, c->stream>>>(g, (const float *)pub, (float *)dev, 1);
     else
-        k_pack<double><<<nblk(n, 256), 256, 0, c->stream>>>(g, (const double *)pub, (double *)dev, 1);
+        k_pack<double><<<grid, 256, 0, c->stream>>>(g, (const double *)pub, (double *)dev, 1);
     return cudaGetLastError();
 }
 
 cudaError_t zero_solid2d(dvm_ctx *c)
 {
     Grid2D g = grid2d(c);
-    const long n = (long)c->nx * c->ny * 2 * c->nvp;
+    dim3 grid((unsigned)(c->nx * c->ny), nblk(2 * c->nvp, 256));
     for (int b = 0; b < 2; ++b) {
         if (c->prec == DVM_FP32)
-            k_zero_solid<float><<<nblk(n, 256), 256, 0, c->stream>>>(g, c->geo[c->gcur].type, (float *)c->f[b]);
+            k_zero_solid<float><<<grid, 256, 0, c->stream>>>(g, c->geo[c->gcur].type, (float *)c->f[b]);
         else
-            k_zero_solid<double><<<nblk(n, 256), 256, 0, c->stream>>>(g, c->geo[c->gcur].type, (double *)c->f[b]);
+            k_zero_solid<double><<<grid, 256, 0, c->stream>>>(g, c->geo[c->gcur].type, (double *)c->f[b]);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t halo2d(dvm_ctx *c, int buf)
+{
+    Grid2D g = grid2d(c);
+    const long n = 2 * 2L * (c->nx + c->ny) * 2 * c->nvp;
+    if (c->prec == DVM_FP32) k_halo<float><<<nblk(n, 256), 256, 0, c->stream>>>(g, (float *)c->f[buf]);
+    else k_halo<double><<<nblk(n, 256), 256, 0, c->stream>>>(g, (double *)c->f[buf]);
     return cudaGetLastError();
 }
 
 cudaError_t unpack2d(dvm_ctx *c, const void *dev, void *pub)
 {
     Grid2D g = grid2d(c);
-    const long n = (long)c->nx * c->ny * 2 * c->nv;
+    dim3 grid((unsigned)(c->nx * c->ny), nblk(2 * c->nv, 256));
     if (c->prec == DVM_FP32)
-        k_pack<float><<<nblk(n, 256), 256, 0, c->stream>>>(g, (const float *)dev, (float *)pub, 0);
+        k_pack<float><<<grid, 256, 0, c->stream>>>(g, (const float *)dev, (float *)pub, 0);
     else
-        k_pack<double><<<nblk(n, 256), 256, 0, c->stream>>>(g, (const double *)dev, (double *)pub, 0);
+        k_pack<double><<<grid, 256, 0, c->stream>>>(g, (const double *)dev, (double *)pub, 0);
     return cudaGetLastError();
 }
 
