@@ -200,6 +200,26 @@ int dvm_launches(dvm_ctx *ctx, long long *count);
 int dvm_cell_counts(dvm_ctx *ctx, long long *nonsolid, long long *bulk, long long *cvs,
                     long long *walls);
 
+/* Total mass of a state, allocating no device memory.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc,
+ * such as code running while a stream is captured into a CUDA graph or a hook
+ * inside a framework whose allocator owns all device memory.
+ *   f      device pointer, state in the public layout [cell][comp][p],
+ *          FP32 or FP64 as `precision` says; only component 0 is summed
+ *   sbar   device pointer, ncell cell areas (2D) or volumes (3D)
+ *   dv     velocity cell measure (product of the grid steps)
+ *   mass   device pointer, receives sum_cells sbar * sum_p f dv (FP64)
+ *   stream cudaStream_t or NULL (legacy default stream); asynchronous
+ * The scratch (one FP64 value per cell) is a static device array of 2^20
+ * cells held by every GPU that loads the library until exit; larger states
+ * are rejected with DVM_ERR_ARG.  The first call on a device looks up the
+ * array's address with that device current: make it before any stream
+ * capture.  All calls share the array, so calls whose work overlaps on the
+ * GPU (different streams, no ordering) race; order them.
+ * Errors: DVM_ERR_ARG, DVM_ERR_CUDA. */
+int dvm_mass_noalloc(const void *f, int precision, long long ncell, int ncomp, int nv,
+                     const double *sbar, double dv, double *mass, void *stream);
+
 /* Thread-local description of the last error. */
 const char *dvm_last_error(void);
 

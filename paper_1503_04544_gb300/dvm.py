@@ -89,6 +89,7 @@ SIGNATURES = {
     "dvm_launches": [_P, C.POINTER(C.c_longlong)],
     "dvm_cell_counts": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                         C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
+    "dvm_mass_noalloc": [_P, C.c_int, C.c_longlong, C.c_int, C.c_int, _P, C.c_double, _P, _P],
     "dvm_last_error": [],
 }
 
