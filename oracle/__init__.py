@@ -55,6 +55,7 @@ class _Cfg(C.Structure):
         ("vbx", C.c_double), ("vby", C.c_double), ("mass", C.c_double), ("inertia", C.c_double),
         ("movable", C.c_int), ("Tw", C.c_double), ("nseg", C.c_int),
         ("Tw_seg", C.POINTER(C.c_double)), ("seg_dir", C.POINTER(C.c_double)),
+        ("axis", C.c_int),
     ]
 
 
@@ -67,6 +68,16 @@ class _Geo2d(C.Structure):
     _fields_ = [("phi", _PD), ("type", _PI8), ("cgas", _PI8), ("lx", _PD), ("ly", _PD),
                 ("lw", _PD), ("nwx", _PD), ("nwy", _PD), ("rwx", _PD), ("rwy", _PD),
                 ("sbar", _PD)]
+
+
+class _Geo3d(C.Structure):
+    _fields_ = [("phi", _PD), ("type", _PI8), ("cgas", _PI8), ("ax", _PD), ("ay", _PD),
+                ("az", _PD), ("sw", _PD), ("nwx", _PD), ("nwy", _PD), ("nwz", _PD),
+                ("rwx", _PD), ("rwy", _PD), ("rwz", _PD), ("vol", _PD)]
+
+
+_GEO3D_KEYS = ("phi", "type", "cgas", "ax", "ay", "az", "sw", "nwx", "nwy", "nwz", "rwx",
+               "rwy", "rwz", "vol")
 
 
 class _Hist(C.Structure):
@@ -88,6 +99,10 @@ def _load():
             lib.orc_moments.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD]
             lib.orc_run2d.argtypes = [P, _PD, C.c_int, C.POINTER(_Hist), _PD, _PD]
             lib.orc_mass2d.argtypes = [P, _PD]; lib.orc_mass2d.restype = C.c_double
+            lib.orc_geometry3d.argtypes = [P, C.POINTER(_Geo3d)]
+            lib.orc_masters3d.argtypes = [P, C.POINTER(_Geo3d), _PI32]
+            lib.orc_run3d.argtypes = [P, _PD, C.c_int, C.POINTER(_Hist)]
+            lib.orc_mass3d.argtypes = [P, _PD]; lib.orc_mass3d.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -124,6 +139,7 @@ class _CfgHolder:
             self.keep += [tw, sd]
             s.Tw_seg = _ptr(tw)
             s.seg_dir = _ptr(sd)
+        s.axis = int(cfg.get("axis", 2))
         self.s = s
         self.cfg = cfg
 
@@ -233,9 +249,41 @@ def mass2d(cfg: dict, F: np.ndarray) -> float:
     return _load().orc_mass2d(_CfgHolder(cfg).ref, _ptr(np.ascontiguousarray(F)))
 
 
-def geometry3d(cfg: dict) -> dict:  # filled in with the 3D oracle
-    raise NotImplementedError
+def geometry3d(cfg: dict) -> dict:
+    """3D cut-cell geometry (faces from the 2D construction of Appendix A)."""
+    lib = _load()
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    nc = nx * ny * nz
+    out = dict(
+        phi=np.zeros((nx + 1) * (ny + 1) * (nz + 1)), type=np.zeros(nc, np.int8),
+        cgas=np.zeros(nc, np.int8), ax=np.zeros((nx + 1) * ny * nz),
+        ay=np.zeros(nx * (ny + 1) * nz), az=np.zeros(nx * ny * (nz + 1)))
+    for k in ("sw", "nwx", "nwy", "nwz", "rwx", "rwy", "rwz", "vol"):
+        out[k] = np.zeros(nc)
+    g = _Geo3d(*[_ptr(out[k], _PI8 if k in ("type", "cgas") else _PD) for k in _GEO3D_KEYS])
+    out["status"] = lib.orc_geometry3d(_CfgHolder(cfg).ref, C.byref(g))
+    out["_struct"] = g
+    return out
 
 
-def run3d(cfg: dict, F: np.ndarray, nsteps: int) -> dict:  # filled in with the 3D oracle
-    raise NotImplementedError
+def masters3d(cfg: dict, g: dict) -> tuple[np.ndarray, int]:
+    master = np.zeros(ncells(cfg), np.int32)
+    rc = _load().orc_masters3d(_CfgHolder(cfg).ref, C.byref(g["_struct"]), _ptr(master, _PI32))
+    return master, rc
+
+
+def run3d(cfg: dict, F: np.ndarray, nsteps: int) -> dict:
+    """Advance a 3D state ``F`` (modified in place) by ``nsteps`` steps (fixed body)."""
+    lib = _load()
+    hist = {k: np.zeros(max(nsteps, 1)) for k in ("Fx", "Fy", "Fz", "torque", "mass")}
+    h = _Hist(_ptr(hist["Fx"]), _ptr(hist["Fy"]), _ptr(hist["Fz"]), _ptr(hist["torque"]),
+              None, None, _ptr(hist["mass"]))
+    assert F.dtype == np.float64 and F.flags.c_contiguous
+    rc = lib.orc_run3d(_CfgHolder(cfg).ref, _ptr(F), int(nsteps), C.byref(h))
+    hist = {k: v[:nsteps] for k, v in hist.items()}
+    hist.update(status=rc)
+    return hist
+
+
+def mass3d(cfg: dict, F: np.ndarray) -> float:
+    return _load().orc_mass3d(_CfgHolder(cfg).ref, _ptr(np.ascontiguousarray(F)))

@@ -299,6 +299,14 @@ typedef struct {
     const orc_geo2d *g;       /* geometry at t^n                            */
 } orc_ctx2d;
 
+/* Periodic image of index a on an axis of n cells (any a, also when the
+ * stencil reaches further than n cells). */
+static int wrap(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
 /* Value of a virtual cell, extended by the domain boundary conditions.
  * reading: periodic wrap; Maxwellian sides hold the prescribed state in
  * every ghost layer; zero-gradient copies the boundary cell. */
@@ -306,20 +314,20 @@ static double fval2d(const orc_ctx2d *x, int i, int j, int comp, int p)
 {
     const orc_cfg *c = x->c;
     if (i < 0) {
-        if (c->bc[0] == ORC_BC_PERIODIC) i += x->nx;
+        if (c->bc[0] == ORC_BC_PERIODIC) i = wrap(i, x->nx);
         else if (c->bc[0] == ORC_BC_MAXWELLIAN) return x->ghost[0][((long)j * 2 + comp) * x->nv + p];
         else i = 0;
     } else if (i >= x->nx) {
-        if (c->bc[1] == ORC_BC_PERIODIC) i -= x->nx;
+        if (c->bc[1] == ORC_BC_PERIODIC) i = wrap(i, x->nx);
         else if (c->bc[1] == ORC_BC_MAXWELLIAN) return x->ghost[1][((long)j * 2 + comp) * x->nv + p];
         else i = x->nx - 1;
     }
     if (j < 0) {
-        if (c->bc[2] == ORC_BC_PERIODIC) j += x->ny;
+        if (c->bc[2] == ORC_BC_PERIODIC) j = wrap(j, x->ny);
         else if (c->bc[2] == ORC_BC_MAXWELLIAN) return x->ghost[2][((long)i * 2 + comp) * x->nv + p];
         else j = 0;
     } else if (j >= x->ny) {
-        if (c->bc[3] == ORC_BC_PERIODIC) j -= x->ny;
+        if (c->bc[3] == ORC_BC_PERIODIC) j = wrap(j, x->ny);
         else if (c->bc[3] == ORC_BC_MAXWELLIAN) return x->ghost[3][((long)i * 2 + comp) * x->nv + p];
         else j = x->ny - 1;
     }
@@ -330,10 +338,10 @@ static double fval2d(const orc_ctx2d *x, int i, int j, int comp, int p)
 static int isgas2d(const orc_ctx2d *x, int i, int j)
 {
     const orc_cfg *c = x->c;
-    if (i < 0) { if (c->bc[0] != ORC_BC_PERIODIC) return 1; i += x->nx; }
-    else if (i >= x->nx) { if (c->bc[1] != ORC_BC_PERIODIC) return 1; i -= x->nx; }
-    if (j < 0) { if (c->bc[2] != ORC_BC_PERIODIC) return 1; j += x->ny; }
-    else if (j >= x->ny) { if (c->bc[3] != ORC_BC_PERIODIC) return 1; j -= x->ny; }
+    if (i < 0) { if (c->bc[0] != ORC_BC_PERIODIC) return 1; i = wrap(i, x->nx); }
+    else if (i >= x->nx) { if (c->bc[1] != ORC_BC_PERIODIC) return 1; i = wrap(i, x->nx); }
+    if (j < 0) { if (c->bc[2] != ORC_BC_PERIODIC) return 1; j = wrap(j, x->ny); }
+    else if (j >= x->ny) { if (c->bc[3] != ORC_BC_PERIODIC) return 1; j = wrap(j, x->ny); }
     return x->g->type[j * x->nx + i] == ORC_GAS;
 }
 
@@ -667,5 +675,462 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
     free(mrho); free(mux); free(muy); free(mT);
     free(wphi); free(wux); free(wuy); free(wT); free(Fnew); free(vx); free(vy);
     for (int s = 0; s < 4; ++s) free(X.ghost[s]);
+    return err;
+}
+
+/* ================================================================ 3D
+ * Full-distribution BGK in 3D (Sec. 5): the same steps with seven-face
+ * virtual cells.  reading: the geometry that the paper leaves to the reader
+ * is built face by face from the 2D construction of Appendix A; the wall face
+ * closes the polyhedron, S_w n_w = -sum_faces A_f n_f; the volume follows
+ * from the divergence theorem in the cell frame, where the faces at the
+ * frame's origin contribute nothing and the wall plane passes through the
+ * centroid of the edge crossings.  Only fixed obstacles are handled in 3D. */
+
+static double levelset3d(const orc_cfg *c, double x, double y, double z)
+{
+    double ddx = x - c->cx, ddy = y - c->cy, ddz = z - c->cz;
+    if (c->shape == ORC_SHAPE_SPHERE) return sqrt(ddx * ddx + ddy * ddy + ddz * ddz) - c->ra;
+    if (c->shape == ORC_SHAPE_CIRCLE) {          /* infinite circular cylinder */
+        if (c->axis == 0) return sqrt(ddy * ddy + ddz * ddz) - c->ra;
+        if (c->axis == 1) return sqrt(ddx * ddx + ddz * ddz) - c->ra;
+        return sqrt(ddx * ddx + ddy * ddy) - c->ra;
+    }
+    return 1.0;
+}
+
+/* Gas area of a square face with nodal values p00 (u=0,w=0), p10 (u=h1,w=0),
+ * p11 (u=h1,w=h2), p01 (u=0,w=h2): the 2D virtual-cell area (Appendix A)
+ * evaluated in the plane of the face. */
+static double face_area(double p00, double p10, double p11, double p01, double h1, double h2, int *err)
+{
+    double m = fmin(fmin(p00, p10), fmin(p11, p01));
+    double M = fmax(fmax(p00, p10), fmax(p11, p01));
+    if (m > 0) return h1 * h2;
+    if (M < 0) return 0.0;
+    double lum = edge_gas_length(p00, p01, h2), lup = edge_gas_length(p10, p11, h2);
+    double lwm = edge_gas_length(p00, p10, h1), lwp = edge_gas_length(p01, p11, h1);
+    double pu[4], pw[4];
+    int n = 0;
+    if ((p00 > 0) != (p01 > 0)) { pu[n] = 0;  pw[n] = h2 * (p00 / (p00 - p01)); ++n; }
+    if ((p10 > 0) != (p11 > 0)) { pu[n] = h1; pw[n] = h2 * (p10 / (p10 - p11)); ++n; }
+    if ((p00 > 0) != (p10 > 0)) { pu[n] = h1 * (p00 / (p00 - p10)); pw[n] = 0;  ++n; }
+    if ((p01 > 0) != (p11 > 0)) { pu[n] = h1 * (p01 / (p01 - p11)); pw[n] = h2; ++n; }
+    if (n != 2) { *err = ORC_ERR_GEOMETRY; return 0.0; }
+    double eu = pu[1] - pu[0], ew = pw[1] - pw[0];
+    double lw = sqrt(eu * eu + ew * ew);
+    double ru = 0.5 * (pu[0] + pu[1]), rw = 0.5 * (pw[0] + pw[1]);
+    double nu = (lum - lup) / lw, nw = (lwm - lwp) / lw;
+    return 0.5 * (lup * h1 + lwp * h2 + lw * (ru * nu + rw * nw));
+}
+
+int orc_geometry3d(const orc_cfg *c, orc_geo3d *g)
+{
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    const double dx = (c->xmax - c->xmin) / nx, dy = (c->ymax - c->ymin) / ny, dz = (c->zmax - c->zmin) / nz;
+    int err = ORC_OK;
+#define N3(a, b, cc) g->phi[((long)(cc) * (ny + 1) + (b)) * (nx + 1) + (a)]
+    for (int cc = 0; cc <= nz; ++cc)
+        for (int b = 0; b <= ny; ++b)
+            for (int a = 0; a <= nx; ++a)
+                N3(a, b, cc) = clamp_phi(levelset3d(c, c->xmin + a * dx, c->ymin + b * dy, c->zmin + cc * dz), dx);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int a = 0; a <= nx; ++a)
+                g->ax[((long)k * ny + j) * (nx + 1) + a] =
+                    face_area(N3(a, j, k), N3(a, j + 1, k), N3(a, j + 1, k + 1), N3(a, j, k + 1), dy, dz, &err);
+    for (int k = 0; k < nz; ++k)
+        for (int b = 0; b <= ny; ++b)
+            for (int i = 0; i < nx; ++i)
+                g->ay[((long)k * (ny + 1) + b) * nx + i] =
+                    face_area(N3(i, b, k), N3(i + 1, b, k), N3(i + 1, b, k + 1), N3(i, b, k + 1), dx, dz, &err);
+    for (int cc = 0; cc <= nz; ++cc)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                g->az[((long)cc * ny + j) * nx + i] =
+                    face_area(N3(i, j, cc), N3(i + 1, j, cc), N3(i + 1, j + 1, cc), N3(i, j + 1, cc), dx, dy, &err);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                long q = ((long)k * ny + j) * nx + i;
+                double p[8] = {N3(i, j, k), N3(i + 1, j, k), N3(i + 1, j + 1, k), N3(i, j + 1, k),
+                               N3(i, j, k + 1), N3(i + 1, j, k + 1), N3(i + 1, j + 1, k + 1), N3(i, j + 1, k + 1)};
+                double m = p[0], M = p[0], s = p[0];
+                for (int t = 1; t < 8; ++t) { m = fmin(m, p[t]); M = fmax(M, p[t]); s = s + p[t]; }
+                g->cgas[q] = 0.125 * s > 0;     /* Eq. (ii) with the 8 nodes */
+                g->sw[q] = 0; g->nwx[q] = g->nwy[q] = g->nwz[q] = 0;
+                g->rwx[q] = g->rwy[q] = g->rwz[q] = 0;
+                if (m > 0) { g->type[q] = ORC_GAS; g->vol[q] = dx * dy * dz; continue; }
+                if (M < 0) { g->type[q] = ORC_SOLID; g->vol[q] = 0; continue; }
+                g->type[q] = ORC_CUT;
+                double axm = g->ax[((long)k * ny + j) * (nx + 1) + i], axp = g->ax[((long)k * ny + j) * (nx + 1) + i + 1];
+                double aym = g->ay[((long)k * (ny + 1) + j) * nx + i], ayp = g->ay[((long)k * (ny + 1) + j + 1) * nx + i];
+                double azm = g->az[((long)k * ny + j) * nx + i], azp = g->az[((long)(k + 1) * ny + j) * nx + i];
+                double wx = axm - axp, wy = aym - ayp, wz = azm - azp;
+                double sw = sqrt(wx * wx + wy * wy + wz * wz);
+                /* crossings of the 12 edges in the cell frame */
+                static const int E[12][2] = {{0, 1}, {3, 2}, {4, 5}, {7, 6},     /* along x */
+                                             {0, 3}, {1, 2}, {4, 7}, {5, 6},     /* along y */
+                                             {0, 4}, {1, 5}, {3, 7}, {2, 6}};    /* along z */
+                static const double O[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                                               {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+                double rx = 0, ry = 0, rz = 0;
+                int nc = 0;
+                for (int e = 0; e < 12; ++e) {
+                    double p0 = p[E[e][0]], p1 = p[E[e][1]];
+                    if ((p0 > 0) == (p1 > 0)) continue;
+                    double t = p0 / (p0 - p1);
+                    const double *o0 = O[E[e][0]], *o1 = O[E[e][1]];
+                    rx += dx * (o0[0] + t * (o1[0] - o0[0]));
+                    ry += dy * (o0[1] + t * (o1[1] - o0[1]));
+                    rz += dz * (o0[2] + t * (o1[2] - o0[2]));
+                    ++nc;
+                }
+                rx /= nc; ry /= nc; rz /= nc;
+                double nwx = sw > 0 ? wx / sw : 0, nwy = sw > 0 ? wy / sw : 0, nwz = sw > 0 ? wz / sw : 0;
+                g->sw[q] = sw; g->nwx[q] = nwx; g->nwy[q] = nwy; g->nwz[q] = nwz;
+                g->rwx[q] = (c->xmin + i * dx) + rx;
+                g->rwy[q] = (c->ymin + j * dy) + ry;
+                g->rwz[q] = (c->zmin + k * dz) + rz;
+                g->vol[q] = (axp * dx + ayp * dy + azp * dz + sw * (rx * nwx + ry * nwy + rz * nwz)) / 3.0;
+            }
+#undef N3
+    return err;
+}
+
+/* Master search with the six faces (ties: x+, x-, y+, y-, z+, z-). */
+int orc_masters3d(const orc_cfg *c, const orc_geo3d *g, int32_t *master)
+{
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    int err = ORC_OK;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                long q = ((long)k * ny + j) * nx + i;
+                master[q] = -1;
+                if (g->type[q] == ORC_SOLID) continue;
+                int ci = i, cj = j, ck = k, it = 0, ok = 0;
+                while (it <= ORC_MAXWALK) {
+                    long r = ((long)ck * ny + cj) * nx + ci;
+                    if (g->cgas[r]) { ok = 1; break; }
+                    double axm = g->ax[((long)ck * ny + cj) * (nx + 1) + ci], axp = g->ax[((long)ck * ny + cj) * (nx + 1) + ci + 1];
+                    double aym = g->ay[((long)ck * (ny + 1) + cj) * nx + ci], ayp = g->ay[((long)ck * (ny + 1) + cj + 1) * nx + ci];
+                    double azm = g->az[((long)ck * ny + cj) * nx + ci], azp = g->az[((long)(ck + 1) * ny + cj) * nx + ci];
+                    double M = fmax(fmax(fmax(axp, axm), fmax(ayp, aym)), fmax(azp, azm));
+                    if (!(M > 0)) break;
+                    if (axp == M) ci++;
+                    else if (axm == M) ci--;
+                    else if (ayp == M) cj++;
+                    else if (aym == M) cj--;
+                    else if (azp == M) ck++;
+                    else ck--;
+                    if (ci < 0 || ci >= nx || cj < 0 || cj >= ny || ck < 0 || ck >= nz) break;
+                    ++it;
+                }
+                if (!ok) { err = ORC_ERR_GEOMETRY; continue; }
+                master[q] = (int32_t)(((long)ck * ny + cj) * nx + ci);
+            }
+    return err;
+}
+
+typedef struct {
+    const orc_cfg *c;
+    int nx, ny, nz, nv, nv1, nv2, nv3;
+    double dx, dy, dz, dvx, dvy, dvz, dt;
+    double *ghost[6];
+    const double *F;
+    const orc_geo3d *g;
+} orc_ctx3d;
+
+/* Value of cell (i, j, k) with the domain boundary conditions (same readings
+ * as in 2D, per axis). */
+static double fval3d(const orc_ctx3d *x, int i, int j, int k, int p)
+{
+    const orc_cfg *c = x->c;
+    if (i < 0) {
+        if (c->bc[0] == ORC_BC_PERIODIC) i = wrap(i, x->nx);
+        else if (c->bc[0] == ORC_BC_MAXWELLIAN) return x->ghost[0][((long)k * x->ny + j) * x->nv + p];
+        else i = 0;
+    } else if (i >= x->nx) {
+        if (c->bc[1] == ORC_BC_PERIODIC) i = wrap(i, x->nx);
+        else if (c->bc[1] == ORC_BC_MAXWELLIAN) return x->ghost[1][((long)k * x->ny + j) * x->nv + p];
+        else i = x->nx - 1;
+    }
+    if (j < 0) {
+        if (c->bc[2] == ORC_BC_PERIODIC) j = wrap(j, x->ny);
+        else if (c->bc[2] == ORC_BC_MAXWELLIAN) return x->ghost[2][((long)k * x->nx + i) * x->nv + p];
+        else j = 0;
+    } else if (j >= x->ny) {
+        if (c->bc[3] == ORC_BC_PERIODIC) j = wrap(j, x->ny);
+        else if (c->bc[3] == ORC_BC_MAXWELLIAN) return x->ghost[3][((long)k * x->nx + i) * x->nv + p];
+        else j = x->ny - 1;
+    }
+    if (k < 0) {
+        if (c->bc[4] == ORC_BC_PERIODIC) k = wrap(k, x->nz);
+        else if (c->bc[4] == ORC_BC_MAXWELLIAN) return x->ghost[4][((long)j * x->nx + i) * x->nv + p];
+        else k = 0;
+    } else if (k >= x->nz) {
+        if (c->bc[5] == ORC_BC_PERIODIC) k = wrap(k, x->nz);
+        else if (c->bc[5] == ORC_BC_MAXWELLIAN) return x->ghost[5][((long)j * x->nx + i) * x->nv + p];
+        else k = x->nz - 1;
+    }
+    return x->F[(((long)k * x->ny + j) * x->nx + i) * x->nv + p];
+}
+
+static int isgas3d(const orc_ctx3d *x, int i, int j, int k)
+{
+    const orc_cfg *c = x->c;
+    if (i < 0) { if (c->bc[0] != ORC_BC_PERIODIC) return 1; i = wrap(i, x->nx); }
+    else if (i >= x->nx) { if (c->bc[1] != ORC_BC_PERIODIC) return 1; i = wrap(i, x->nx); }
+    if (j < 0) { if (c->bc[2] != ORC_BC_PERIODIC) return 1; j = wrap(j, x->ny); }
+    else if (j >= x->ny) { if (c->bc[3] != ORC_BC_PERIODIC) return 1; j = wrap(j, x->ny); }
+    if (k < 0) { if (c->bc[4] != ORC_BC_PERIODIC) return 1; k = wrap(k, x->nz); }
+    else if (k >= x->nz) { if (c->bc[5] != ORC_BC_PERIODIC) return 1; k = wrap(k, x->nz); }
+    return x->g->type[((long)k * x->ny + j) * x->nx + i] == ORC_GAS;
+}
+
+static void alloc_geo3d(orc_geo3d *g, int nx, int ny, int nz)
+{
+    long nc = (long)nx * ny * nz;
+    g->phi = malloc(sizeof(double) * (nx + 1) * (ny + 1) * (long)(nz + 1));
+    g->type = malloc(nc); g->cgas = malloc(nc);
+    g->ax = malloc(sizeof(double) * (nx + 1) * (long)ny * nz);
+    g->ay = malloc(sizeof(double) * nx * (long)(ny + 1) * nz);
+    g->az = malloc(sizeof(double) * nx * (long)ny * (nz + 1));
+    g->sw = malloc(sizeof(double) * nc);
+    g->nwx = malloc(sizeof(double) * nc); g->nwy = malloc(sizeof(double) * nc); g->nwz = malloc(sizeof(double) * nc);
+    g->rwx = malloc(sizeof(double) * nc); g->rwy = malloc(sizeof(double) * nc); g->rwz = malloc(sizeof(double) * nc);
+    g->vol = malloc(sizeof(double) * nc);
+}
+
+static void free_geo3d(orc_geo3d *g)
+{
+    free(g->phi); free(g->type); free(g->cgas); free(g->ax); free(g->ay); free(g->az); free(g->sw);
+    free(g->nwx); free(g->nwy); free(g->nwz); free(g->rwx); free(g->rwy); free(g->rwz); free(g->vol);
+}
+
+double orc_mass3d(const orc_cfg *c, const double *F)
+{
+    const int nv = c->nvx * c->nvy * c->nvz;
+    const double dv = (c->vxmax - c->vxmin) / c->nvx * ((c->vymax - c->vymin) / c->nvy) *
+                      ((c->vzmax - c->vzmin) / c->nvz);
+    orc_geo3d g;
+    alloc_geo3d(&g, c->nx, c->ny, c->nz);
+    orc_geometry3d(c, &g);
+    double M = 0;
+    const long nc = (long)c->nx * c->ny * c->nz;
+    for (long q = 0; q < nc; ++q) {
+        double s = 0;
+        for (int p = 0; p < nv; ++p) s += F[q * nv + p];
+        M += g.vol[q] * (s * dv);
+    }
+    free_geo3d(&g);
+    return M;
+}
+
+int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
+{
+    if (c->dim != 3 || c->movable) return ORC_ERR_ARG;
+    orc_ctx3d X;
+    X.c = c; X.nx = c->nx; X.ny = c->ny; X.nz = c->nz;
+    X.nv1 = c->nvx; X.nv2 = c->nvy; X.nv3 = c->nvz; X.nv = X.nv1 * X.nv2 * X.nv3;
+    X.dx = (c->xmax - c->xmin) / c->nx; X.dy = (c->ymax - c->ymin) / c->ny; X.dz = (c->zmax - c->zmin) / c->nz;
+    X.dvx = (c->vxmax - c->vxmin) / c->nvx; X.dvy = (c->vymax - c->vymin) / c->nvy;
+    X.dvz = (c->vzmax - c->vzmin) / c->nvz;
+    X.dt = orc_dt(c);
+    const int nx = X.nx, ny = X.ny, nz = X.nz, nv = X.nv;
+    const long nc = (long)nx * ny * nz;
+    const double dt = X.dt, dv = X.dvx * X.dvy * X.dvz, tau0 = orc_tau0(c);
+    /* ghosts of Maxwellian sides */
+    for (int s = 0; s < 6; ++s) {
+        X.ghost[s] = NULL;
+        if (c->bc[s] != ORC_BC_MAXWELLIAN) continue;
+        long n = s < 2 ? (long)ny * nz : (s < 4 ? (long)nx * nz : (long)nx * ny);
+        X.ghost[s] = malloc(sizeof(double) * n * nv);
+        for (long q = 0; q < n; ++q) {
+            const double *st = c->bc_state[s] + 5 * q;
+            for (int p3 = 0; p3 < X.nv3; ++p3)
+                for (int p2 = 0; p2 < X.nv2; ++p2)
+                    for (int p1 = 0; p1 < X.nv1; ++p1) {
+                        int p = (p3 * X.nv2 + p2) * X.nv1 + p1;
+                        X.ghost[s][q * nv + p] = maxw3d(st[0], st[1], st[2], st[3], st[4], c->vxmin + p1 * X.dvx,
+                                                        c->vymin + p2 * X.dvy, c->vzmin + p3 * X.dvz);
+                    }
+        }
+    }
+    orc_geo3d geo;
+    alloc_geo3d(&geo, nx, ny, nz);
+    int err = orc_geometry3d(c, &geo);
+    int32_t *master = malloc(sizeof(int32_t) * nc);
+    if (!err) err = orc_masters3d(c, &geo, master);
+    int32_t *mstart = malloc(sizeof(int32_t) * (nc + 1)), *mlist = malloc(sizeof(int32_t) * nc), *cnt = malloc(sizeof(int32_t) * nc);
+    double *S = malloc(sizeof(double) * nc);
+    double *mr = malloc(sizeof(double) * nc), *mu = malloc(sizeof(double) * 3 * nc), *mT = malloc(sizeof(double) * nc);
+    double *wphi = malloc(sizeof(double) * nc), *wu = malloc(sizeof(double) * 3 * nc), *wT = malloc(sizeof(double) * nc);
+    double *Fnew = malloc(sizeof(double) * nc * nv);
+    double *vx = malloc(sizeof(double) * X.nv1), *vy = malloc(sizeof(double) * X.nv2), *vz = malloc(sizeof(double) * X.nv3);
+    for (int q = 0; q < X.nv1; ++q) vx[q] = c->vxmin + q * X.dvx;
+    for (int q = 0; q < X.nv2; ++q) vy[q] = c->vymin + q * X.dvy;
+    for (int q = 0; q < X.nv3; ++q) vz[q] = c->vzmin + q * X.dvz;
+    if (!err) {
+        for (long q = 0; q < nc; ++q) { cnt[q] = 0; S[q] = 0; }
+        for (long q = 0; q < nc; ++q) if (master[q] >= 0) { cnt[master[q]]++; S[master[q]] += geo.vol[q]; }
+        mstart[0] = 0;
+        for (long q = 0; q < nc; ++q) mstart[q + 1] = mstart[q] + cnt[q];
+        for (long q = 0; q < nc; ++q) cnt[q] = 0;
+        for (long q = 0; q < nc; ++q) if (master[q] >= 0) { int m = master[q]; mlist[mstart[m] + cnt[m]++] = (int32_t)q; }
+    }
+    X.g = &geo;
+    for (int step = 0; step < nsteps && err == ORC_OK; ++step) {
+        /* fusion (3D form of Eq. FusionDD) */
+        #pragma omp parallel for schedule(dynamic, 64)
+        for (long m = 0; m < nc; ++m) {
+            if (mstart[m + 1] - mstart[m] <= 1) continue;
+            for (int p = 0; p < nv; ++p) {
+                double s = 0;
+                for (int q = mstart[m]; q < mstart[m + 1]; ++q) s += geo.vol[mlist[q]] * F[(long)mlist[q] * nv + p];
+                double fcv = s / S[m];
+                for (int q = mstart[m]; q < mstart[m + 1]; ++q) F[(long)mlist[q] * nv + p] = fcv;
+            }
+        }
+        X.F = F;
+        int nonphys = 0;
+        #pragma omp parallel for reduction(|:nonphys)
+        for (long m = 0; m < nc; ++m) {
+            if (mstart[m + 1] - mstart[m] == 0) continue;
+            double u[3], r, T;
+            if (cell_moments(c, F + m * nv, &r, u, &T)) nonphys = 1;
+            mr[m] = r; mu[3 * m] = u[0]; mu[3 * m + 1] = u[1]; mu[3 * m + 2] = u[2]; mT[m] = T;
+        }
+        if (nonphys) { err = ORC_ERR_NONPHYSICAL; break; }
+        /* wall density and stress (3D forms of Eqs. BoundaryTD, StressTensorDD) */
+        double Fx = 0, Fy = 0, Fz = 0, Tq = 0;
+        for (long q = 0; q < nc; ++q) {
+            if (geo.type[q] != ORC_CUT || !(geo.sw[q] > 0)) continue;
+            double rx = geo.rwx[q] - c->cx, ry = geo.rwy[q] - c->cy;
+            double uw[3] = {c->vbx - ry * c->omega, c->vby + rx * c->omega, 0.0};
+            double Tw = c->Tw, n[3] = {geo.nwx[q], geo.nwy[q], geo.nwz[q]};
+            const double *fk = F + q * nv;
+            double num = 0, den = 0;
+            for (int p3 = 0; p3 < X.nv3; ++p3)
+                for (int p2 = 0; p2 < X.nv2; ++p2)
+                    for (int p1 = 0; p1 < X.nv1; ++p1) {
+                        int p = (p3 * X.nv2 + p2) * X.nv1 + p1;
+                        double a[3] = {vx[p1] - uw[0], vy[p2] - uw[1], vz[p3] - uw[2]};
+                        double cp = a[0] * n[0] + a[1] * n[1] + a[2] * n[2];
+                        if (cp > 0) num += cp * fk[p] * dv;
+                        else if (cp < 0) den += cp * maxw3d(1.0, uw[0], uw[1], uw[2], Tw, vx[p1], vy[p2], vz[p3]) * dv;
+                    }
+            double phi = -num / den;
+            double Sg[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            for (int p3 = 0; p3 < X.nv3; ++p3)
+                for (int p2 = 0; p2 < X.nv2; ++p2)
+                    for (int p1 = 0; p1 < X.nv1; ++p1) {
+                        int p = (p3 * X.nv2 + p2) * X.nv1 + p1;
+                        double a[3] = {vx[p1] - uw[0], vy[p2] - uw[1], vz[p3] - uw[2]};
+                        double cp = a[0] * n[0] + a[1] * n[1] + a[2] * n[2];
+                        double fv;
+                        if (cp < 0) fv = phi * maxw3d(1.0, uw[0], uw[1], uw[2], Tw, vx[p1], vy[p2], vz[p3]);
+                        else if (cp > 0) fv = fk[p];
+                        else continue;
+                        for (int r1 = 0; r1 < 3; ++r1)
+                            for (int r2 = 0; r2 < 3; ++r2) Sg[r1][r2] += a[r1] * a[r2] * fv * dv;
+                    }
+            double fk3[3];
+            for (int r1 = 0; r1 < 3; ++r1) fk3[r1] = (Sg[r1][0] * n[0] + Sg[r1][1] * n[1] + Sg[r1][2] * n[2]) * geo.sw[q];
+            Fx += fk3[0]; Fy += fk3[1]; Fz += fk3[2];
+            Tq += rx * fk3[1] - ry * fk3[0];
+            wphi[q] = phi; wu[3 * q] = uw[0]; wu[3 * q + 1] = uw[1]; wu[3 * q + 2] = uw[2]; wT[q] = Tw;
+        }
+        /* explicit scheme (Eq. eq-schema3D) */
+        #pragma omp parallel
+        {
+            double *R = malloc(sizeof(double) * nv);
+            #pragma omp for schedule(dynamic, 16)
+            for (long m = 0; m < nc; ++m) {
+                if (mstart[m + 1] - mstart[m] == 0) continue;
+                for (int p = 0; p < nv; ++p) R[p] = 0;
+                for (int q = mstart[m]; q < mstart[m + 1]; ++q) {
+                    long kq = mlist[q];
+                    int i = (int)(kq % nx), j = (int)((kq / nx) % ny), k = (int)(kq / ((long)nx * ny));
+                    int mus = c->scheme == ORC_MUSCL;
+                    int mxp = mus && isgas3d(&X, i - 1, j, k) && isgas3d(&X, i, j, k) && isgas3d(&X, i + 1, j, k) && isgas3d(&X, i + 2, j, k);
+                    int mxm = mus && isgas3d(&X, i - 2, j, k) && isgas3d(&X, i - 1, j, k) && isgas3d(&X, i, j, k) && isgas3d(&X, i + 1, j, k);
+                    int myp = mus && isgas3d(&X, i, j - 1, k) && isgas3d(&X, i, j, k) && isgas3d(&X, i, j + 1, k) && isgas3d(&X, i, j + 2, k);
+                    int mym = mus && isgas3d(&X, i, j - 2, k) && isgas3d(&X, i, j - 1, k) && isgas3d(&X, i, j, k) && isgas3d(&X, i, j + 1, k);
+                    int mzp = mus && isgas3d(&X, i, j, k - 1) && isgas3d(&X, i, j, k) && isgas3d(&X, i, j, k + 1) && isgas3d(&X, i, j, k + 2);
+                    int mzm = mus && isgas3d(&X, i, j, k - 2) && isgas3d(&X, i, j, k - 1) && isgas3d(&X, i, j, k) && isgas3d(&X, i, j, k + 1);
+                    double axm = geo.ax[((long)k * ny + j) * (nx + 1) + i], axp = geo.ax[((long)k * ny + j) * (nx + 1) + i + 1];
+                    double aym = geo.ay[((long)k * (ny + 1) + j) * nx + i], ayp = geo.ay[((long)k * (ny + 1) + j + 1) * nx + i];
+                    double azm = geo.az[((long)k * ny + j) * nx + i], azp = geo.az[((long)(k + 1) * ny + j) * nx + i];
+                    int wall = geo.type[kq] == ORC_CUT && geo.sw[kq] > 0;
+                    for (int p3 = 0; p3 < X.nv3; ++p3)
+                        for (int p2 = 0; p2 < X.nv2; ++p2)
+                            for (int p1 = 0; p1 < X.nv1; ++p1) {
+                                int p = (p3 * X.nv2 + p2) * X.nv1 + p1;
+                                double v1 = vx[p1], v2 = vy[p2], v3 = vz[p3];
+                                double n1 = fabs(v1) * dt / X.dx, n2 = fabs(v2) * dt / X.dy, n3 = fabs(v3) * dt / X.dz;
+                                /* reading: each direction uses its own velocity component */
+                                double fxp = face_flux(axp, v1, n1, fval3d(&X, i - 1, j, k, p), fval3d(&X, i, j, k, p),
+                                                       fval3d(&X, i + 1, j, k, p), fval3d(&X, i + 2, j, k, p), mxp);
+                                double fxm = face_flux(axm, v1, n1, fval3d(&X, i - 2, j, k, p), fval3d(&X, i - 1, j, k, p),
+                                                       fval3d(&X, i, j, k, p), fval3d(&X, i + 1, j, k, p), mxm);
+                                double fyp = face_flux(ayp, v2, n2, fval3d(&X, i, j - 1, k, p), fval3d(&X, i, j, k, p),
+                                                       fval3d(&X, i, j + 1, k, p), fval3d(&X, i, j + 2, k, p), myp);
+                                double fym = face_flux(aym, v2, n2, fval3d(&X, i, j - 2, k, p), fval3d(&X, i, j - 1, k, p),
+                                                       fval3d(&X, i, j, k, p), fval3d(&X, i, j + 1, k, p), mym);
+                                double fzp = face_flux(azp, v3, n3, fval3d(&X, i, j, k - 1, p), fval3d(&X, i, j, k, p),
+                                                       fval3d(&X, i, j, k + 1, p), fval3d(&X, i, j, k + 2, p), mzp);
+                                double fzm = face_flux(azm, v3, n3, fval3d(&X, i, j, k - 2, p), fval3d(&X, i, j, k - 1, p),
+                                                       fval3d(&X, i, j, k, p), fval3d(&X, i, j, k + 1, p), mzm);
+                                double fw = 0;
+                                if (wall) {
+                                    double a0 = v1 - wu[3 * kq], a1 = v2 - wu[3 * kq + 1], a2 = v3 - wu[3 * kq + 2];
+                                    double cp = a0 * geo.nwx[kq] + a1 * geo.nwy[kq] + a2 * geo.nwz[kq];
+                                    double fwall = wphi[kq] * maxw3d(1.0, wu[3 * kq], wu[3 * kq + 1], wu[3 * kq + 2], wT[kq], v1, v2, v3);
+                                    fw = geo.sw[kq] * (fmin(cp, 0.0) * fwall + fmax(cp, 0.0) * F[kq * nv + p]);
+                                }
+                                R[p] += (fxp - fxm) + (fyp - fym) + (fzp - fzm) + fw;
+                            }
+                }
+                double tau = tau0 / mr[m];
+                double a = 1.0, b = dt / S[m], r = dt / tau;   /* fixed body: V^n = V^{n+1,*} */
+                for (int p3 = 0; p3 < X.nv3; ++p3)
+                    for (int p2 = 0; p2 < X.nv2; ++p2)
+                        for (int p1 = 0; p1 < X.nv1; ++p1) {
+                            int p = (p3 * X.nv2 + p2) * X.nv1 + p1;
+                            double fcv = F[m * nv + p];
+                            double feq = maxw3d(mr[m], mu[3 * m], mu[3 * m + 1], mu[3 * m + 2], mT[m], vx[p1], vy[p2], vz[p3]);
+                            Fnew[m * nv + p] = a * fcv - b * R[p] + a * r * (feq - fcv);
+                        }
+            }
+            free(R);
+        }
+        #pragma omp parallel for
+        for (long q = 0; q < nc; ++q) {
+            int m = master[q];
+            if (m < 0) { memset(F + q * nv, 0, sizeof(double) * nv); continue; }
+            memcpy(F + q * nv, Fnew + (long)m * nv, sizeof(double) * nv);
+        }
+        if (h) {
+            if (h->Fx) h->Fx[step] = Fx;
+            if (h->Fy) h->Fy[step] = Fy;
+            if (h->Fz) h->Fz[step] = Fz;
+            if (h->torque) h->torque[step] = Tq;
+            if (h->mass) {
+                double M = 0;
+                for (long q = 0; q < nc; ++q) {
+                    double s = 0;
+                    for (int p = 0; p < nv; ++p) s += F[q * nv + p];
+                    M += geo.vol[q] * (s * dv);
+                }
+                h->mass[step] = M;
+            }
+        }
+    }
+    free_geo3d(&geo);
+    free(master); free(mstart); free(mlist); free(cnt); free(S); free(mr); free(mu); free(mT);
+    free(wphi); free(wu); free(wT); free(Fnew); free(vx); free(vy); free(vz);
+    for (int s = 0; s < 6; ++s) free(X.ghost[s]);
     return err;
 }

@@ -55,6 +55,8 @@ typedef struct {
     int nseg;                      /* >0: per-sector wall temperatures */
     const double *Tw_seg;          /* [nseg] */
     const double *seg_dir;         /* [2*nseg] sector boundary directions */
+    int axis;                      /* 3D circle: axis of the infinite cylinder
+                                      (0 x, 1 y, 2 z) */
 } orc_cfg;
 
 /* Geometry of one time level (2D): every array is caller-owned.          */
@@ -92,5 +94,30 @@ int orc_moments(const orc_cfg *c, const double *F, double *rho, double *ux,
 int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
               double *theta_out, double *omega_out);
 double orc_mass2d(const orc_cfg *c, const double *F);
+
+
+/* ------------------------------------------------------------------ 3D */
+
+/* Geometry of the 3D cut cells (reading of the extension of Appendix A that
+ * the paper leaves to the reader, Sec. 5): faces carry the 2D virtual-cell
+ * area of their four nodes; the wall face closes the polyhedron.  Arrays are
+ * caller-owned. */
+typedef struct {
+    double *phi;      /* (nx+1)(ny+1)(nz+1) nodes, node (a,b,c) at (c*(ny+1)+b)*(nx+1)+a */
+    int8_t *type;     /* nx*ny*nz                                                    */
+    int8_t *cgas;     /* nx*ny*nz                                                    */
+    double *ax;       /* (nx+1)*ny*nz x-faces, face a of (j,k) at (k*ny+j)*(nx+1)+a   */
+    double *ay;       /* nx*(ny+1)*nz y-faces, face b of (i,k) at (k*(ny+1)+b)*nx+i   */
+    double *az;       /* nx*ny*(nz+1) z-faces, face c of (i,j) at (c*ny+j)*nx+i       */
+    double *sw;       /* wall face area                                              */
+    double *nwx, *nwy, *nwz;   /* wall normal (towards the solid)                    */
+    double *rwx, *rwy, *rwz;   /* wall centre (absolute)                             */
+    double *vol;      /* virtual-cell volume                                         */
+} orc_geo3d;
+
+int orc_geometry3d(const orc_cfg *c, orc_geo3d *g);
+int orc_masters3d(const orc_cfg *c, const orc_geo3d *g, int32_t *master);
+int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h);
+double orc_mass3d(const orc_cfg *c, const double *F);
 
 #endif

@@ -19,6 +19,8 @@ bc                  6 ints for the x-, x+, y-, y+, z-, z+ sides:
 bc_state            per side: None or an array (n_side_cells, 5) of
                     (rho, ux, uy, uz, T) for Maxwellian sides
 shape               0 none, 1 circle, 2 ellipse, 3 sphere
+                    (in 3D, 1 is an infinite circular cylinder along ``axis``)
+axis                3D cylinder axis: 0 x, 1 y, 2 z
 cx, cy, cz, ra, rb  obstacle centre, radius (ra) or semi-axes (ra, rb)
 theta, omega        body angle and angular velocity
 mass, inertia       rigid-body mass and moment of inertia
@@ -69,6 +71,13 @@ def base2d(nx, ny, nv, vwin, **kw) -> dict:
                bc_state=[None] * 6, shape=0, cx=0.5, cy=0.5, cz=0.5, ra=0.0, rb=0.0,
                theta=0.0, omega=0.0, vbx=0.0, vby=0.0, mass=1.0, inertia=1.0, movable=0,
                Tw=1.0, nseg=0, init=dict(rho=1.0, ux=0.0, uy=0.0, uz=0.0, T=1.0), steps=1)
+    cfg.update(kw)
+    return cfg
+
+
+def base3d(n, nv, vwin, **kw) -> dict:
+    """A 3D problem on the unit cube with n cells and nv velocities per axis."""
+    cfg = base2d(n, n, nv, vwin, dim=3, nz=n, nvz=nv, vzmin=-vwin, vzmax=vwin, axis=2)
     cfg.update(kw)
     return cfg
 
