@@ -97,7 +97,9 @@ typedef struct {
 
 typedef struct dvm_ctx dvm_ctx;
 
-/* Create a solver for one problem on the current CUDA device.
+/* Create a solver for one problem on the current CUDA device: dim 2 (reduced
+ * pair f, g; circle or ellipse, fixed or rotating) or dim 3 (full F; fixed
+ * sphere), at least 4 cells and at most 64 velocities per axis.
  * precision: DVM_FP32 (state and transport in FP32; wall density, force,
  * torque, rigid-body ODE and mass diagnostic in FP64) or DVM_FP64.
  * scheme: DVM_UPWIND (Eq. FluxDD) or DVM_MUSCL (limited fluxes on full gas
@@ -178,6 +180,18 @@ int dvm_info(dvm_ctx *ctx, double *dt, double *tau0, long long *ncell, int *nv,
 int dvm_geometry2d(dvm_ctx *ctx, int8_t *type, int8_t *cgas, double *lx, double *ly,
                    double *lw, double *nwx, double *nwy, double *rwx, double *rwy,
                    double *sbar, int32_t *master);
+
+/* 3D geometry (Sec. 5; faces from the Appendix A construction, the wall face
+ * closing the polyhedron), copied to host arrays (any may be NULL):
+ * type/cgas [ncell]; face areas ax [(nx+1)*ny*nz] (face a of row (j, k) at
+ * (k*ny + j)*(nx+1) + a), ay [nx*(ny+1)*nz] (face b of (i, k) at
+ * (k*(ny+1) + b)*nx + i), az [nx*ny*(nz+1)] (face c of (i, j) at
+ * (c*ny + j)*nx + i); wall area sw, unit normal (nwx, nwy, nwz) pointing into
+ * the solid, wall centre (rwx, rwy, rwz), virtual-cell volume vol and master
+ * [ncell].  Errors: DVM_ERR_ARG on a 2D context. */
+int dvm_geometry3d(dvm_ctx *ctx, int8_t *type, int8_t *cgas, double *ax, double *ay, double *az,
+                   double *sw, double *nwx, double *nwy, double *nwz, double *rwx, double *rwy,
+                   double *rwz, double *vol, int32_t *master);
 
 /* Rebuild the 2D geometry for an explicit (cos theta, sin theta) pair, for
  * bit-exact comparisons with an independent implementation. */

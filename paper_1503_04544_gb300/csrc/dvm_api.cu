@@ -54,6 +54,25 @@ Grid2D grid2d(const dvm_ctx *c)
     return g;
 }
 
+Grid3D grid3d(const dvm_ctx *c)
+{
+    Grid3D g;
+    g.nx = c->nx; g.ny = c->ny; g.nz = c->nz;
+    g.nvx = c->nvx; g.nvy = c->nvy; g.nvz = c->nvz; g.nv = c->nv;
+    g.W = c->W; g.nvxp = c->nvxp; g.nxg = c->nxg; g.nvp = c->nvp; g.ngrp = c->ngrp;
+    g.slab = c->slab;
+    g.xmin = c->xmin; g.ymin = c->ymin; g.zmin = c->zmin; g.dx = c->dx; g.dy = c->dy; g.dz = c->dz;
+    g.vxmin = c->vxmin; g.vymin = c->vymin; g.vzmin = c->vzmin;
+    g.dvx = c->dvx; g.dvy = c->dvy; g.dvz = c->dvz;
+    g.dv = c->dvx * c->dvy * c->dvz;
+    g.dt = c->dt; g.tau0 = c->tau0;
+    g.dt_tau0 = c->dt / c->tau0;
+    g.dv_f = (float)g.dv;
+    g.dt_tau0_f = (float)g.dt_tau0;
+    for (int s = 0; s < 6; ++s) g.bc[s] = c->bc[s];
+    return g;
+}
+
 BodyParams body_params(const dvm_ctx *c)
 {
     BodyParams b;
@@ -107,6 +126,14 @@ static void free_geo(dvm::Geo2D &G)
     std::memset(&G, 0, sizeof(G));
 }
 
+static void free_geo3(dvm::Geo3D &G)
+{
+    cudaFree(G.phi); cudaFree(G.type); cudaFree(G.cgas); cudaFree(G.ax); cudaFree(G.ay); cudaFree(G.az);
+    cudaFree(G.sw); cudaFree(G.nwx); cudaFree(G.nwy); cudaFree(G.nwz);
+    cudaFree(G.rwx); cudaFree(G.rwy); cudaFree(G.rwz); cudaFree(G.vol);
+    std::memset(&G, 0, sizeof(G));
+}
+
 static int check_flags(dvm_ctx *c)
 {
     CK(cudaMemcpyAsync(c->h_err, c->d_err, kErrCount * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -124,6 +151,20 @@ static int check_flags(dvm_ctx *c)
     return rc;
 }
 
+// Dimension dispatch of the state services.
+static cudaError_t st_ghost(dvm_ctx *c, int side, const double *d, int n)
+{ return c->dim == 2 ? ghost2d(c, side, d, n) : ghost3d(c, side, d, n); }
+static cudaError_t st_halo(dvm_ctx *c, int buf) { return c->dim == 2 ? halo2d(c, buf) : halo3d(c, buf); }
+static cudaError_t st_zero_solid(dvm_ctx *c) { return c->dim == 2 ? zero_solid2d(c) : zero_solid3d(c); }
+static cudaError_t st_partials(dvm_ctx *c) { return c->dim == 2 ? partials_from_state2d(c) : partials_from_state3d(c); }
+static cudaError_t st_pack(dvm_ctx *c, const void *pub, void *dev) { return c->dim == 2 ? pack2d(c, pub, dev) : pack3d(c, pub, dev); }
+static cudaError_t st_unpack(dvm_ctx *c, const void *dev, void *pub) { return c->dim == 2 ? unpack2d(c, dev, pub) : unpack3d(c, dev, pub); }
+static cudaError_t st_step(dvm_ctx *c) { return c->dim == 2 ? step2d(c) : step3d(c); }
+static cudaError_t st_moments(dvm_ctx *c, double *d) { return c->dim == 2 ? moments_out2d(c, d) : moments_out3d(c, d); }
+static cudaError_t st_mass(dvm_ctx *c, double *s, double *d) { return c->dim == 2 ? mass2d(c, s, d) : mass3d(c, s, d); }
+static cudaError_t st_init(dvm_ctx *c, const double *d) { return c->dim == 2 ? init_maxwellian2d(c, d) : init_maxwellian3d(c, d); }
+static cudaError_t st_flags(dvm_ctx *c) { return c->dim == 2 ? masters_flags2d(c, false) : masters_flags3d(c); }
+
 extern "C" {
 
 const char *dvm_last_error(void) { return g_last_error.c_str(); }
@@ -133,53 +174,79 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
 {
     if (!grid || !vg || !ph || !out) { set_error("null argument"); return DVM_ERR_ARG; }
     *out = nullptr;
-    if (grid->dim != 2) { set_error("only dim = 2 is built in this library version"); return DVM_ERR_UNSUPPORTED; }
-    if (grid->nx < 4 || grid->ny < 4 || vg->nvx < 1 || vg->nvy < 1) { set_error("grid sizes: at least 4 x 4 cells and one velocity"); return DVM_ERR_ARG; }
-    if (vg->nvx > kMaxAxisNv || vg->nvy > kMaxAxisNv) { set_error("at most 64 velocities per axis"); return DVM_ERR_ARG; }
+    const int dim = grid->dim;
+    if (dim != 2 && dim != 3) { set_error("dim must be 2 or 3"); return DVM_ERR_ARG; }
+    if (grid->nx < 4 || grid->ny < 4 || (dim == 3 && grid->nz < 4) || vg->nvx < 1 || vg->nvy < 1 ||
+        (dim == 3 && vg->nvz < 1)) {
+        set_error("grid sizes: at least 4 cells per axis and one velocity"); return DVM_ERR_ARG;
+    }
+    if (vg->nvx > kMaxAxisNv || vg->nvy > kMaxAxisNv || (dim == 3 && vg->nvz > kMaxAxisNv)) {
+        set_error("at most 64 velocities per axis"); return DVM_ERR_ARG;
+    }
     if (precision != DVM_FP32 && precision != DVM_FP64) { set_error("precision must be 32 or 64"); return DVM_ERR_ARG; }
     if (scheme != DVM_UPWIND && scheme != DVM_MUSCL) { set_error("scheme"); return DVM_ERR_ARG; }
     if (!(grid->xmax > grid->xmin) || !(grid->ymax > grid->ymin) || !(vg->vxmax > vg->vxmin) ||
-        !(vg->vymax > vg->vymin) || !(ph->Kn > 0) || !(ph->Lref > 0)) {
+        !(vg->vymax > vg->vymin) || !(ph->Kn > 0) || !(ph->Lref > 0) ||
+        (dim == 3 && (!(grid->zmax > grid->zmin) || !(vg->vzmax > vg->vzmin)))) {
         set_error("empty box, velocity window or non-positive Kn/Lref"); return DVM_ERR_ARG;
+    }
+    if (dim == 3 && (double)(grid->nx + 4) * (grid->ny + 4) * (grid->nz + 4) > 2.0e9) {
+        set_error("3D grid too large for 32-bit slab indices"); return DVM_ERR_ARG;
     }
     dvm_ctx *c = new (std::nothrow) dvm_ctx();
     if (!c) { set_error("host allocation"); return DVM_ERR_OOM; }
     std::memset((void *)c, 0, sizeof(*c));
-    c->dim = 2; c->nx = grid->nx; c->ny = grid->ny; c->nz = 1;
+    c->dim = dim; c->nx = grid->nx; c->ny = grid->ny; c->nz = dim == 3 ? grid->nz : 1;
     c->xmin = grid->xmin; c->xmax = grid->xmax; c->ymin = grid->ymin; c->ymax = grid->ymax;
+    c->zmin = grid->zmin; c->zmax = grid->zmax;
     c->dx = (c->xmax - c->xmin) / c->nx;
     c->dy = (c->ymax - c->ymin) / c->ny;
-    c->nvx = vg->nvx; c->nvy = vg->nvy; c->nvz = 1; c->nv = c->nvx * c->nvy;
+    c->dz = dim == 3 ? (c->zmax - c->zmin) / c->nz : 1.0;
+    c->nvx = vg->nvx; c->nvy = vg->nvy; c->nvz = dim == 3 ? vg->nvz : 1;
+    c->nv = c->nvx * c->nvy * c->nvz;
     c->vxmin = vg->vxmin; c->vxmax = vg->vxmax; c->vymin = vg->vymin; c->vymax = vg->vymax;
+    c->vzmin = vg->vzmin; c->vzmax = vg->vzmax;
     c->dvx = (c->vxmax - c->vxmin) / c->nvx;
     c->dvy = (c->vymax - c->vymin) / c->nvy;
+    c->dvz = dim == 3 ? (c->vzmax - c->vzmin) / c->nvz : 1.0;
     c->Kn = ph->Kn; c->Lref = ph->Lref; c->cfl = ph->cfl;
     // tau = sqrt(pi)/2 (rho0/rho) Kn L / sqrt(2 R T0), Sec. 5, R = T0 = rho0 = 1
     c->tau0 = std::sqrt(M_PI) / 2.0 * c->Kn * c->Lref / std::sqrt(2.0);
     if (ph->dt > 0) c->dt = ph->dt;
     else {
         double s = axis_vmax(c->nvx, c->vxmin, c->vxmax) / c->dx + axis_vmax(c->nvy, c->vymin, c->vymax) / c->dy;
+        if (dim == 3) s += axis_vmax(c->nvz, c->vzmin, c->vzmax) / c->dz;
         c->dt = c->cfl / s;
     }
     if (!(c->dt > 0)) { delete c; set_error("time step"); return DVM_ERR_CFL; }
-    c->prec = precision; c->scheme = scheme; c->ncomp = 2;
+    c->prec = precision; c->scheme = scheme; c->ncomp = dim == 2 ? 2 : 1;
     c->elem = precision == DVM_FP32 ? 4 : 8;
-    c->nc = (long long)c->nx * c->ny;
+    c->nc = (long long)c->nx * c->ny * c->nz;
     c->state_elems = (size_t)c->nc * c->ncomp * c->nv;
     c->W = 16 / c->elem;
-    c->nvp = (c->nv + c->W - 1) / c->W * c->W;
-    c->ngrp = c->nvp / c->W;
-    c->slab = (long)(c->nx + 4) * (c->ny + 4);
+    if (dim == 2) {
+        c->nvp = (c->nv + c->W - 1) / c->W * c->W;
+        c->ngrp = c->nvp / c->W;
+        c->slab = (long)(c->nx + 4) * (c->ny + 4);
+    } else {
+        c->nvxp = (c->nvx + c->W - 1) / c->W * c->W;
+        c->nxg = c->nvxp / c->W;
+        c->nvp = c->nvxp * c->nvy * c->nvz;
+        c->ngrp = c->nvp / c->W;
+        c->slab = (long)(c->nx + 4) * (c->ny + 4) * (c->nz + 4);
+    }
     c->dev_elems = (size_t)c->ngrp * c->ncomp * c->slab * c->W;
     {
         // velocity splits: enough blocks for a few waves on 152 SMs
-        const long bxy = (long)((c->nx + 31) / 32) * ((c->ny + kRows - 1) / kRows);
-        int S = (int)((1200 + bxy - 1) / bxy);
+        long blocks = (long)((c->nx + 31) / 32) * ((c->ny + kRows - 1) / kRows);
+        if (dim == 3) blocks *= (c->nz + kZc3 - 1) / kZc3;
+        int S = (int)((1200 + blocks - 1) / blocks);
         if (S < 1) S = 1;
         if (S > 16) S = 16;
         if (S > c->ngrp) S = c->ngrp;
         c->S = S;
     }
+    const int nmom = dim == 2 ? 4 : 5;
     if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
     else {
         cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -194,23 +261,37 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
 #define AL(p, b) if (e == cudaSuccess) e = dalloc(&(p), (b))
     AL(c->f[0], c->dev_elems * c->elem);
     AL(c->f[1], c->dev_elems * c->elem);
-    AL(c->part[0], (size_t)c->S * 4 * nc * c->elem);
-    AL(c->part[1], (size_t)c->S * 4 * nc * c->elem);
-    AL(c->vtab, (size_t)c->nvp * vcoef_bytes(c->prec));
-    AL(c->gsign, (size_t)2 * c->ngrp);
+    AL(c->part[0], (size_t)c->S * nmom * nc * c->elem);
+    AL(c->part[1], (size_t)c->S * nmom * nc * c->elem);
     AL(c->wslot, sizeof(int32_t) * nc);
     AL(c->ticket, sizeof(int));
-    for (int l = 0; l < 2; ++l) {
-        dvm::Geo2D &G = c->geo[l];
-        AL(G.phi, sizeof(double) * (c->nx + 1) * (c->ny + 1));
+    if (dim == 2) {
+        AL(c->vtab, (size_t)c->nvp * vcoef_bytes(c->prec));
+        AL(c->gsign, (size_t)2 * c->ngrp);
+        for (int l = 0; l < 2; ++l) {
+            dvm::Geo2D &G = c->geo[l];
+            AL(G.phi, sizeof(double) * (c->nx + 1) * (c->ny + 1));
+            AL(G.type, nc); AL(G.cgas, nc);
+            AL(G.lx, sizeof(double) * (c->nx + 1) * c->ny);
+            AL(G.ly, sizeof(double) * c->nx * (c->ny + 1));
+            AL(G.lw, sizeof(double) * nc); AL(G.nwx, sizeof(double) * nc); AL(G.nwy, sizeof(double) * nc);
+            AL(G.rwx, sizeof(double) * nc); AL(G.rwy, sizeof(double) * nc); AL(G.sbar, sizeof(double) * nc);
+        }
+        AL(c->flags, nc);
+    } else {
+        AL(c->vtab, vtab3_bytes(c));
+        dvm::Geo3D &G = c->geo3;
+        AL(G.phi, sizeof(double) * (c->nx + 1) * (c->ny + 1) * (size_t)(c->nz + 1));
         AL(G.type, nc); AL(G.cgas, nc);
-        AL(G.lx, sizeof(double) * (c->nx + 1) * c->ny);
-        AL(G.ly, sizeof(double) * c->nx * (c->ny + 1));
-        AL(G.lw, sizeof(double) * nc); AL(G.nwx, sizeof(double) * nc); AL(G.nwy, sizeof(double) * nc);
-        AL(G.rwx, sizeof(double) * nc); AL(G.rwy, sizeof(double) * nc); AL(G.sbar, sizeof(double) * nc);
+        AL(G.ax, sizeof(double) * (c->nx + 1) * (size_t)c->ny * c->nz);
+        AL(G.ay, sizeof(double) * c->nx * (size_t)(c->ny + 1) * c->nz);
+        AL(G.az, sizeof(double) * c->nx * (size_t)c->ny * (c->nz + 1));
+        AL(G.sw, sizeof(double) * nc); AL(G.nwx, sizeof(double) * nc); AL(G.nwy, sizeof(double) * nc);
+        AL(G.nwz, sizeof(double) * nc); AL(G.rwx, sizeof(double) * nc); AL(G.rwy, sizeof(double) * nc);
+        AL(G.rwz, sizeof(double) * nc); AL(G.vol, sizeof(double) * nc);
+        AL(c->flags3, sizeof(uint16_t) * nc);
     }
     AL(c->master, sizeof(int32_t) * nc);
-    AL(c->flags, nc);
     AL(c->hs, nc);
     AL(c->counts, sizeof(int32_t) * 4);
     AL(c->d_body, sizeof(dvm::BodyDev));
@@ -223,19 +304,22 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     if (e != cudaSuccess) { int rc = cuda_fail(e, "dvm_create allocation"); dvm_destroy(c); return rc; }
     cudaMemsetAsync(c->f[0], 0, c->dev_elems * c->elem, c->stream);
     cudaMemsetAsync(c->f[1], 0, c->dev_elems * c->elem, c->stream);
-    cudaMemsetAsync(c->part[0], 0, (size_t)c->S * 4 * nc * c->elem, c->stream);
-    cudaMemsetAsync(c->part[1], 0, (size_t)c->S * 4 * nc * c->elem, c->stream);
+    cudaMemsetAsync(c->part[0], 0, (size_t)c->S * nmom * nc * c->elem, c->stream);
+    cudaMemsetAsync(c->part[1], 0, (size_t)c->S * nmom * nc * c->elem, c->stream);
     cudaMemsetAsync(c->ticket, 0, sizeof(int), c->stream);
     cudaMemsetAsync(c->d_err, 0, sizeof(int) * kErrCount, c->stream);
     cudaMemsetAsync(c->d_body, 0, sizeof(dvm::BodyDev), c->stream);
     cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 6 * kHistCap, c->stream);
     cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4, c->stream);
-    {
+    if (dim == 2) {
         int rc = make_tensor_maps2d(c);
         if (rc != DVM_OK) { dvm_destroy(c); return rc; }
+        e = init_static_geometry2d(c);
+        if (e == cudaSuccess) e = tables2d(c);
+    } else {
+        e = init_static_geometry3d(c);
+        if (e == cudaSuccess) e = tables3d(c);
     }
-    e = init_static_geometry2d(c);
-    if (e == cudaSuccess) e = tables2d(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { int rc = cuda_fail(e, "dvm_create init"); dvm_destroy(c); return rc; }
     c->have_geo = true;
@@ -253,6 +337,8 @@ void dvm_destroy(dvm_ctx *c)
     cudaFree(c->vtab); cudaFree(c->gsign); cudaFree(c->wslot); cudaFree(c->ticket);
     cudaFree(c->wflux); cudaFree(c->d_pub);
     for (int l = 0; l < 2; ++l) free_geo(c->geo[l]);
+    free_geo3(c->geo3);
+    cudaFree(c->flags3);
     cudaFree(c->master); cudaFree(c->flags); cudaFree(c->hs);
     cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->counts);
     cudaFree(c->wphi); cudaFree(c->wcontrib); cudaFree(c->cvinfo);
@@ -281,25 +367,76 @@ int dvm_set_bc(dvm_ctx *c, int side, int kind, const double *state)
         double *d = nullptr;
         CK(cudaMalloc(&d, sizeof(double) * 5 * n));
         cudaError_t e = cudaMemcpyAsync(d, state, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = ghost2d(c, side, d, n);
+        if (e == cudaSuccess) e = st_ghost(c, side, d, n);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         cudaFree(d);
         if (e != cudaSuccess) return cuda_fail(e, "dvm_set_bc");
     }
     c->bc[side] = kind;
-    if (c->have_state) CK(halo2d(c, c->cur));
+    if (c->have_state) CK(st_halo(c, c->cur));
     // flags depend on the periodicity of the sides through the limiter masks
     if (c->body.shape != DVM_SHAPE_NONE) {
-        cudaError_t e = masters_flags2d(c, false);
+        cudaError_t e = st_flags(c);
         if (e != cudaSuccess) return cuda_fail(e, "dvm_set_bc flags");
         return check_flags(c);
     }
     return DVM_OK;
 }
 
+static int set_body3d(dvm_ctx *c, const dvm_body *b)
+{
+    if (b->shape != DVM_SHAPE_NONE && b->shape != DVM_SHAPE_SPHERE) {
+        set_error("3D shapes: none, sphere"); return DVM_ERR_UNSUPPORTED;
+    }
+    if (b->shape != DVM_SHAPE_NONE && !(b->ra > 0)) { set_error("body size"); return DVM_ERR_ARG; }
+    if (b->movable) { set_error("3D obstacles are fixed in this library version"); return DVM_ERR_UNSUPPORTED; }
+    if (b->nseg > 0) { set_error("per-sector wall temperatures are 2D only"); return DVM_ERR_UNSUPPORTED; }
+    c->body = *b;
+    c->body.Tw_seg = nullptr; c->body.seg_dir = nullptr;
+    c->moving = false;
+    // list capacity: the cells of the box around the sphere (with margin)
+    long nbox = 1;
+    if (b->shape != DVM_SHAPE_NONE) {
+        auto span = [](double cc, double R, double vmin, double h, int n) {
+            int lo = (int)std::floor((cc - R - vmin) / h) - kBoxMargin;
+            int hi = (int)std::ceil((cc + R - vmin) / h) + kBoxMargin;
+            lo = lo < 0 ? 0 : (lo > n ? n : lo);
+            hi = hi < 0 ? 0 : (hi > n ? n : hi);
+            return (long)(hi - lo);
+        };
+        nbox = span(b->cx, b->ra, c->xmin, c->dx, c->nx) * span(b->cy, b->ra, c->ymin, c->dy, c->ny) *
+               span(b->cz, b->ra, c->zmin, c->dz, c->nz);
+        if (nbox < 1) nbox = 1;
+    }
+    cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->wcontrib); cudaFree(c->wphi); cudaFree(c->cvinfo);
+    c->spec_list = c->wall_list = nullptr; c->wcontrib = c->wphi = nullptr; c->cvinfo = nullptr;
+    c->list_cap = (int)nbox;
+    CK(cudaMalloc(&c->spec_list, sizeof(int32_t) * c->list_cap));
+    CK(cudaMalloc(&c->wall_list, sizeof(int32_t) * c->list_cap));
+    CK(cudaMalloc(&c->wcontrib, sizeof(double) * 4 * c->list_cap));
+    CK(cudaMalloc(&c->wphi, sizeof(double) * 6 * c->list_cap));
+    CK(cudaMalloc(&c->cvinfo, cvinfo3_bytes() * (size_t)c->list_cap));
+    CK(cudaMemsetAsync(c->wcontrib, 0, sizeof(double) * 4 * c->list_cap, c->stream));
+    CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4, c->stream));
+    dvm::BodyDev hb;
+    std::memset(&hb, 0, sizeof(hb));
+    hb.theta = b->theta; hb.omega = b->omega; hb.theta1 = b->theta;
+    CK(cudaMemcpyAsync(c->d_body, &hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int) * kErrCount, c->stream));
+    CK(init_static_geometry3d(c));
+    if (b->shape != DVM_SHAPE_NONE) {
+        CK(geometry3d(c));
+        CK(masters_flags3d(c));
+    }
+    c->need_fusion = true;
+    c->steps_done = 0;
+    return check_flags(c);
+}
+
 int dvm_set_body(dvm_ctx *c, const dvm_body *b)
 {
     if (!c || !b) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (c->dim == 3) return set_body3d(c, b);
     if (b->shape != DVM_SHAPE_NONE && b->shape != DVM_SHAPE_CIRCLE && b->shape != DVM_SHAPE_ELLIPSE) {
         set_error("2D shapes: none, circle, ellipse"); return DVM_ERR_UNSUPPORTED;
     }
@@ -365,6 +502,7 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
 int dvm_geometry2d_at(dvm_ctx *c, double cos_t, double sin_t)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (c->dim != 2) { set_error("dvm_geometry2d_at: 2D contexts only"); return DVM_ERR_ARG; }
     if (c->body.shape == DVM_SHAPE_NONE) return DVM_OK;
     double t[2] = {cos_t, sin_t};
     CK(cudaMemcpyAsync(body_trig(c, 0), t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
@@ -390,10 +528,10 @@ int dvm_init_maxwellian(dvm_ctx *c, const double *rho, const double *ux, const d
     }
     double *d = c->d_out;      // nc*5 doubles
     CK(cudaMemcpyAsync(d, prim.data(), sizeof(double) * 5 * nc, cudaMemcpyHostToDevice, c->stream));
-    CK(init_maxwellian2d(c, d));
-    CK(zero_solid2d(c));
-    CK(halo2d(c, c->cur));
-    CK(partials_from_state2d(c));
+    CK(st_init(c, d));
+    CK(st_zero_solid(c));
+    CK(st_halo(c, c->cur));
+    CK(st_partials(c));
     c->have_state = true;
     c->need_fusion = true;
     return check_flags(c);
@@ -412,10 +550,10 @@ int dvm_set_state(dvm_ctx *c, const void *f, size_t bytes, int on_device)
     int rc = ensure_pub(c);
     if (rc != DVM_OK) return rc;
     CK(cudaMemcpyAsync(c->d_pub, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    CK(pack2d(c, c->d_pub, c->f[c->cur]));
-    CK(zero_solid2d(c));
-    CK(halo2d(c, c->cur));
-    CK(partials_from_state2d(c));
+    CK(st_pack(c, c->d_pub, c->f[c->cur]));
+    CK(st_zero_solid(c));
+    CK(st_halo(c, c->cur));
+    CK(st_partials(c));
     c->have_state = true;
     c->need_fusion = true;
     CK(cudaStreamSynchronize(c->stream));
@@ -428,7 +566,7 @@ int dvm_get_state(dvm_ctx *c, void *f, size_t bytes, int on_device)
     if (bytes != c->state_elems * c->elem) { set_error("state size mismatch"); return DVM_ERR_ARG; }
     int rc = ensure_pub(c);
     if (rc != DVM_OK) return rc;
-    CK(unpack2d(c, c->f[c->cur], c->d_pub));
+    CK(st_unpack(c, c->f[c->cur], c->d_pub));
     CK(cudaMemcpyAsync(f, c->d_pub, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return DVM_OK;
@@ -445,7 +583,7 @@ int dvm_step_async(dvm_ctx *c, int nsteps)
     if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return DVM_ERR_ARG; }
     for (int s = 0; s < nsteps; ++s) {
-        cudaError_t e = step2d(c);
+        cudaError_t e = st_step(c);
         if (e != cudaSuccess) return cuda_fail(e, "dvm_step");
     }
     return DVM_OK;
@@ -468,7 +606,7 @@ int dvm_moments(dvm_ctx *c, double *rho, double *ux, double *uy, double *uz, dou
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
     const size_t nc = (size_t)c->nc;
-    CK(moments_out2d(c, c->d_out));
+    CK(st_moments(c, c->d_out));
     std::vector<double> h(5 * nc);
     CK(cudaMemcpyAsync(h.data(), c->d_out, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -531,7 +669,7 @@ int dvm_mass(dvm_ctx *c, double *mass)
 {
     if (!c || !mass) { set_error("null"); return DVM_ERR_ARG; }
     double *d = c->d_out;
-    CK(mass2d(c, c->d_scratch, d));
+    CK(st_mass(c, c->d_scratch, d));
     CK(cudaMemcpyAsync(mass, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return DVM_OK;
@@ -553,6 +691,7 @@ int dvm_geometry2d(dvm_ctx *c, int8_t *type, int8_t *cgas, double *lx, double *l
                    double *nwx, double *nwy, double *rwx, double *rwy, double *sbar, int32_t *master)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (c->dim != 2) { set_error("dvm_geometry2d: 2D contexts only"); return DVM_ERR_ARG; }
     const dvm::Geo2D &G = c->geo[c->gcur];
     const size_t nc = (size_t)c->nc;
     auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
@@ -568,6 +707,35 @@ int dvm_geometry2d(dvm_ctx *c, int8_t *type, int8_t *cgas, double *lx, double *l
     CK(cp(rwx, G.rwx, sizeof(double) * nc));
     CK(cp(rwy, G.rwy, sizeof(double) * nc));
     CK(cp(sbar, G.sbar, sizeof(double) * nc));
+    CK(cp(master, c->master, sizeof(int32_t) * nc));
+    CK(cudaStreamSynchronize(c->stream));
+    return DVM_OK;
+}
+
+int dvm_geometry3d(dvm_ctx *c, int8_t *type, int8_t *cgas, double *ax, double *ay, double *az, double *sw,
+                   double *nwx, double *nwy, double *nwz, double *rwx, double *rwy, double *rwz, double *vol,
+                   int32_t *master)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (c->dim != 3) { set_error("dvm_geometry3d: 3D contexts only"); return DVM_ERR_ARG; }
+    const dvm::Geo3D &G = c->geo3;
+    const size_t nc = (size_t)c->nc;
+    auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream) : cudaSuccess;
+    };
+    CK(cp(type, G.type, nc));
+    CK(cp(cgas, G.cgas, nc));
+    CK(cp(ax, G.ax, sizeof(double) * (c->nx + 1) * (size_t)c->ny * c->nz));
+    CK(cp(ay, G.ay, sizeof(double) * c->nx * (size_t)(c->ny + 1) * c->nz));
+    CK(cp(az, G.az, sizeof(double) * c->nx * (size_t)c->ny * (c->nz + 1)));
+    CK(cp(sw, G.sw, sizeof(double) * nc));
+    CK(cp(nwx, G.nwx, sizeof(double) * nc));
+    CK(cp(nwy, G.nwy, sizeof(double) * nc));
+    CK(cp(nwz, G.nwz, sizeof(double) * nc));
+    CK(cp(rwx, G.rwx, sizeof(double) * nc));
+    CK(cp(rwy, G.rwy, sizeof(double) * nc));
+    CK(cp(rwz, G.rwz, sizeof(double) * nc));
+    CK(cp(vol, G.vol, sizeof(double) * nc));
     CK(cp(master, c->master, sizeof(int32_t) * nc));
     CK(cudaStreamSynchronize(c->stream));
     return DVM_OK;
@@ -609,11 +777,18 @@ int dvm_cell_counts(dvm_ctx *c, long long *nonsolid, long long *bulk, long long 
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
     const size_t nc = (size_t)c->nc;
-    std::vector<uint8_t> fl(nc);
+    std::vector<uint16_t> fl(nc);
     std::vector<int8_t> ty(nc);
     int32_t cnt[2] = {0, 0};
-    CK(cudaMemcpyAsync(fl.data(), c->flags, nc, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(ty.data(), c->geo[c->gcur].type, nc, cudaMemcpyDeviceToHost, c->stream));
+    if (c->dim == 2) {
+        std::vector<uint8_t> f8(nc);
+        CK(cudaMemcpyAsync(f8.data(), c->flags, nc, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t k = 0; k < nc; ++k) fl[k] = f8[k];
+    } else {
+        CK(cudaMemcpyAsync(fl.data(), c->flags3, sizeof(uint16_t) * nc, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaMemcpyAsync(ty.data(), c->dim == 2 ? c->geo[c->gcur].type : c->geo3.type, nc, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(cnt, c->counts, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     long long ns = 0, nb = 0;

@@ -40,6 +40,12 @@ constexpr uint8_t kZero = 2;         // solid at t^{n+1} and in no control volum
 constexpr uint8_t kSpecial = 4;      // updated by the control-volume kernel
 constexpr uint8_t kMaskShift = 4;    // bits 4..7: limiter allowed on faces x-, x+, y-, y+
 
+// 3D cell flags (16 bits): kPlain, kZero, kSpecial as in 2D; bits 4..9 allow
+// the limiter on the faces x-, x+, y-, y+, z-, z+
+constexpr int kMaskShift3 = 4;
+constexpr int kMaxMembers3 = 8;      // virtual cells per 3D control volume
+constexpr int kZc3 = 4;              // z-planes per thread of the 3D bulk kernel
+
 // device error flag slots
 enum { kErrNonphys = 0, kErrGeometry = 1, kErrCapacity = 2, kErrTimeout = 3, kErrCount = 4 };
 
@@ -51,6 +57,32 @@ struct Geo2D {
     double *lx;       // (nx+1)*ny
     double *ly;       // nx*(ny+1)
     double *lw, *nwx, *nwy, *rwx, *rwy, *sbar;   // nc
+};
+
+// Geometry of the 3D cut cells (faces from Appendix A applied to each face,
+// the wall face closing the polyhedron), FP64.
+struct Geo3D {
+    double *phi;                       // (nx+1)(ny+1)(nz+1) nodes
+    int8_t *type, *cgas;               // nc
+    double *ax, *ay, *az;              // (nx+1)ny nz, nx(ny+1)nz, nx ny(nz+1) face areas
+    double *sw, *nwx, *nwy, *nwz;      // nc wall face area and normal (into the solid)
+    double *rwx, *rwy, *rwz;           // nc wall centre (absolute)
+    double *vol;                       // nc virtual-cell volume
+};
+
+// Parameters shared by the 3D kernels.  Velocities are grouped by W along
+// v_x with the v_x axis padded to nvxp = nxg * W points, so that v_y and v_z
+// are uniform within a group; group q covers p1 = (q % nxg) * W + e,
+// p2 = (q / nxg) % nvy, p3 = q / (nxg * nvy).
+struct Grid3D {
+    int nx, ny, nz, nvx, nvy, nvz, nv;
+    int W, nvxp, nxg, nvp, ngrp;
+    long slab;                // (nx + 4)(ny + 4)(nz + 4)
+    double xmin, ymin, zmin, dx, dy, dz;
+    double vxmin, vymin, vzmin, dvx, dvy, dvz, dv;
+    double dt, tau0, dt_tau0;
+    float dv_f, dt_tau0_f;
+    int bc[6];
 };
 
 // Rigid-body state on the device (FP64).
@@ -110,6 +142,9 @@ struct dvm_ctx {
     void *vtab;                   // [nvp][8] per-velocity coefficients (state precision)
     int8_t *gsign;                // [ngrp][2] sign of v_x, v_y in a group (0: mixed)
     dvm::Geo2D geo[2];
+    dvm::Geo3D geo3;              // 3D geometry (fixed obstacle)
+    uint16_t *flags3;             // 3D cell flags
+    int nvxp, nxg;                // 3D velocity grouping (see Grid3D)
     int gcur;
     int32_t *master;
     uint8_t *flags;
@@ -166,6 +201,26 @@ cudaError_t halo2d(dvm_ctx *c, int buf);                         // periodic / z
 cudaError_t members2d(dvm_ctx *c, bool moving);                  // control-volume records
 cudaError_t timing_mark(dvm_ctx *c, int which);   // 0: before, 1: after the bulk kernel
 int make_tensor_maps2d(dvm_ctx *c);                // TMA descriptors of f[0], f[1]
+
+// 3D (dvm_geometry3d.cu, dvm_step3d.cu)
+dvm::Grid3D grid3d(const dvm_ctx *c);
+cudaError_t init_static_geometry3d(dvm_ctx *c);
+cudaError_t geometry3d(dvm_ctx *c);
+cudaError_t masters_flags3d(dvm_ctx *c);
+cudaError_t members3d(dvm_ctx *c);
+cudaError_t tables3d(dvm_ctx *c);
+cudaError_t partials_from_state3d(dvm_ctx *c);
+cudaError_t init_maxwellian3d(dvm_ctx *c, const double *d_prim);
+cudaError_t step3d(dvm_ctx *c);
+cudaError_t mass3d(dvm_ctx *c, double *d_scratch, double *d_out);
+cudaError_t moments_out3d(dvm_ctx *c, double *d_out);
+cudaError_t ghost3d(dvm_ctx *c, int side, const double *d_prim, int nside);
+cudaError_t pack3d(dvm_ctx *c, const void *pub, void *dev);
+cudaError_t unpack3d(dvm_ctx *c, const void *dev, void *pub);
+cudaError_t zero_solid3d(dvm_ctx *c);
+cudaError_t halo3d(dvm_ctx *c, int buf);
+size_t vtab3_bytes(const dvm_ctx *c);
+size_t cvinfo3_bytes();
 
 inline double *body_trig(dvm_ctx *c, int which)
 {

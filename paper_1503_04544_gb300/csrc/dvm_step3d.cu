@@ -1,0 +1,1203 @@
+// 3D time step of the cut-cell discrete-velocity method (arXiv:1503.04544,
+// Sec. 5, Eq. eq-schema3D) for the full distribution F and a fixed obstacle:
+// wall density and stress of the diffuse wall (3D forms of Eqs. BoundaryDDv
+// and StressTensorDD), force and torque about the z axis, fluxes across the
+// six Cartesian faces of every virtual cell (each direction with its own
+// velocity component) and across its wall face, explicit update of each
+// control volume with BGK relaxation toward the 3D Maxwellian, distribution
+// to the members (Eq. UpdateDD).
+//
+// Device layout: element (cell, p) at (q * slab + P(i, j, k)) * W + e for the
+// velocity group q and lane e of the padded velocity index (Grid3D), with
+// P(i, j, k) = ((k + 2)(ny + 4) + j + 2)(nx + 4) + i + 2: every group is a
+// slab of the grid padded by two cells on each side that holds the boundary
+// condition, so a neighbour within two cells along an axis is a plain index.
+//
+// Kernels of one step: k_wall3 (FP64 wall density, force and torque; the
+// last block sums them in list order), k_bulk3 (every gas cell that is a
+// control volume on its own), k_special3 (cut and merged control volumes).
+// k_bulk3 assigns one thread to a column of kZc3 cells along z; a warp covers
+// 32 consecutive cells along x, so the velocity of a group (hence the upwind
+// side along y and z) is uniform across the warp.  The velocity groups are
+// split over blockIdx.z; each thread walks its groups, reads its cells'
+// stencils, writes the new state and accumulates the moments of the new
+// state for the next step.
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <string>
+
+#include "dvm_device.cuh"
+
+namespace dvm {
+namespace {
+
+constexpr int kCoef3 = 6;            // per-cell coefficients of the bulk kernel
+
+template <typename T> struct alignas(2 * sizeof(T)) VX3 { T vx, nux; };
+template <typename T> struct alignas(4 * sizeof(T)) VYZ3 { T vy, vz, nuy, nuz; };
+
+// Slab index of cell (i, j, k), each within two cells of the grid.
+__device__ __forceinline__ int nbr3(const Grid3D &g, int i, int j, int k)
+{
+    return ((k + 2) * (g.ny + 4) + (j + 2)) * (g.nx + 4) + (i + 2);
+}
+
+__device__ __forceinline__ void cell_ijk(const Grid3D &g, int q, int &i, int &j, int &k)
+{
+    const int r = q / g.nx;
+    i = q - r * g.nx;
+    k = r / g.ny;
+    j = r - k * g.ny;
+}
+
+__device__ __forceinline__ int pcell3(const Grid3D &g, int q)
+{
+    int i, j, k;
+    cell_ijk(g, q, i, j, k);
+    return nbr3(g, i, j, k);
+}
+
+// Element offset of padded velocity p at slab index pc.
+__device__ __forceinline__ long pidx3(const Grid3D &g, int p, int pc)
+{
+    const int grp = p / g.W;
+    return ((long)grp * g.slab + pc) * g.W + (p - grp * g.W);
+}
+
+// Axis indices of padded velocity p.
+__device__ __forceinline__ void vel_axes(const Grid3D &g, int p, int &p1, int &p2, int &p3)
+{
+    const int grp = p / g.W, e = p - grp * g.W;
+    const int yz = grp / g.nxg;
+    p1 = (grp - yz * g.nxg) * g.W + e;
+    p3 = yz / g.nvy;
+    p2 = yz - p3 * g.nvy;
+}
+
+// Padded index of public velocity p = (p3 nvy + p2) nvx + p1.
+__device__ __forceinline__ int padded3(const Grid3D &g, int p)
+{
+    const int r = p / g.nvx;
+    return r * g.nvxp + (p - r * g.nvx);
+}
+
+// Padding cells that mirror interior cell (i, j, k) on periodic and
+// zero-gradient sides (two per axis at most); -1 where unused.
+__device__ __forceinline__ void mirrors3(const Grid3D &g, int i, int j, int k, int (&m)[6])
+{
+#pragma unroll
+    for (int t = 0; t < 6; ++t) m[t] = -1;
+    if (g.bc[0] == DVM_BC_PERIODIC) {
+        if (i < 2) m[0] = nbr3(g, i + g.nx, j, k);
+        else if (i >= g.nx - 2) m[0] = nbr3(g, i - g.nx, j, k);
+    } else {
+        if (i == 0 && g.bc[0] == DVM_BC_ZEROGRAD) { m[0] = nbr3(g, -1, j, k); m[1] = nbr3(g, -2, j, k); }
+        if (i == g.nx - 1 && g.bc[1] == DVM_BC_ZEROGRAD) { m[0] = nbr3(g, g.nx, j, k); m[1] = nbr3(g, g.nx + 1, j, k); }
+    }
+    if (g.bc[2] == DVM_BC_PERIODIC) {
+        if (j < 2) m[2] = nbr3(g, i, j + g.ny, k);
+        else if (j >= g.ny - 2) m[2] = nbr3(g, i, j - g.ny, k);
+    } else {
+        if (j == 0 && g.bc[2] == DVM_BC_ZEROGRAD) { m[2] = nbr3(g, i, -1, k); m[3] = nbr3(g, i, -2, k); }
+        if (j == g.ny - 1 && g.bc[3] == DVM_BC_ZEROGRAD) { m[2] = nbr3(g, i, g.ny, k); m[3] = nbr3(g, i, g.ny + 1, k); }
+    }
+    if (g.bc[4] == DVM_BC_PERIODIC) {
+        if (k < 2) m[4] = nbr3(g, i, j, k + g.nz);
+        else if (k >= g.nz - 2) m[4] = nbr3(g, i, j, k - g.nz);
+    } else {
+        if (k == 0 && g.bc[4] == DVM_BC_ZEROGRAD) { m[4] = nbr3(g, i, j, -1); m[5] = nbr3(g, i, j, -2); }
+        if (k == g.nz - 1 && g.bc[5] == DVM_BC_ZEROGRAD) { m[4] = nbr3(g, i, j, g.nz); m[5] = nbr3(g, i, j, g.nz + 1); }
+    }
+}
+
+__device__ __forceinline__ bool near_side3(const Grid3D &g, int i, int j, int k)
+{
+    return i < 2 || i >= g.nx - 2 || j < 2 || j >= g.ny - 2 || k < 2 || k >= g.nz - 2;
+}
+
+// Primitive variables from the sums s0 = sum F, s1..3 = sum v F,
+// s4 = sum |v|^2/2 F (Eq. MacroscopicTD; T from E = rho|u|^2/2 + 3/2 rho T).
+template <typename T>
+__device__ __forceinline__ bool primitives3(T dv, const T (&s)[5], T &rho, T &ux, T &uy, T &uz, T &tmp)
+{
+    rho = s[0] * dv;
+    ux = s[1] / s[0];
+    uy = s[2] / s[0];
+    uz = s[3] / s[0];
+    tmp = (T(2) * (s[4] / s[0]) - (ux * ux + uy * uy + uz * uz)) / T(3);
+    return rho > T(0) && tmp > T(0);
+}
+
+// Sum of the S partial moments of a cell ([S][5][nc] layout).
+template <typename T>
+__device__ __forceinline__ void gather_partials3(const T *part, int S, long nc, long cell, T (&s)[5])
+{
+    Acc<T> a[5];
+    for (int q = 0; q < S; ++q)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) a[m].merge(part[((long)q * 5 + m) * nc + cell], T(0));
+#pragma unroll
+    for (int m = 0; m < 5; ++m) s[m] = a[m].value();
+}
+
+// 1 / (2 pi T)^{3/2}
+template <typename T>
+__device__ __forceinline__ T norm3(T tmp)
+{
+    const T a = T(2.0 * kPi) * tmp;
+    return T(1) / (a * sqrt(a));
+}
+
+// ------------------------------------------------------------ bulk kernel
+template <typename T> struct Bulk3Args {
+    Grid3D g;
+    int S, nzc;
+    const T *fin;
+    T *fout;
+    const T *pin;             // partial moments of F^n   [S][5][nc]
+    T *pout;                  // partial moments of F^n+1 [S][5][nc]
+    const uint16_t *flags;
+    const VX3<T> *vxt;        // [nvxp]
+    const VYZ3<T> *vyz;       // [nvy * nvz]
+    int *err;
+};
+
+// Flux difference of one direction in units of the Courant number (Eq.
+// eq-schema3D on a full gas cell): a = F - F_up, plus the limited
+// reconstructions of the outgoing (weight wo) and incoming (wi) faces, each
+// weight 1/2 where the face stencil is all gas and 0 otherwise.
+template <typename T, bool MUSCL>
+__device__ __forceinline__ T dflux(T f, T u1, T u2, T d1, T nu, T wo, T wi)
+{
+    const T a = f - u1;
+    if (!MUSCL) return a;
+    return a + (T(1) - nu) * (wo * minmod3(d1 - f, a) - wi * minmod3(a, u1 - u2));
+}
+
+template <typename T, bool MUSCL>
+__global__ void __launch_bounds__(32 * kRows, 2) k_bulk3(Bulk3Args<T> a)
+{
+    constexpr int W = Vec<T>::W, ZC = kZc3, NT = 32 * kRows;
+    using V = typename Vec<T>::type;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    T *coef = reinterpret_cast<T *>(smem3);                  // [ZC][kCoef3][NT]
+    T *ksum = coef + ZC * kCoef3 * NT;                        // [ZC][5][2][NT]
+    const Grid3D &g = a.g;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int i = blockIdx.x * 32 + tx, j = blockIdx.y * kRows + ty;
+    const int zc = blockIdx.z % a.nzc, split = blockIdx.z / a.nzc;
+    const int k0 = zc * ZC;
+    const long nc = (long)g.nx * g.ny * g.nz;
+    const int gps = (g.ngrp + a.S - 1) / a.S;
+    const int g0 = split * gps, g1 = min(g0 + gps, g.ngrp);
+    const int sy = g.nx + 4, sz = (g.nx + 4) * (g.ny + 4);
+    const bool inij = i < g.nx && j < g.ny;
+
+    uint32_t plainm = 0, zerom = 0, mirm = 0, masks = 0;
+#pragma unroll
+    for (int z = 0; z < ZC; ++z) {
+        const int k = k0 + z;
+        const bool in = inij && k < g.nz;
+        const long cell = ((long)k * g.ny + j) * g.nx + i;
+        const uint16_t fl = in ? a.flags[cell] : 0;
+        T *cz = coef + z * kCoef3 * NT + tid;
+        if (fl & kPlain) {
+            plainm |= 1u << z;
+            T s[5];
+            gather_partials3(a.pin, a.S, nc, cell, s);
+            T rho, ux, uy, uz, tmp;
+            if (!primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp)) atomicExch(&a.err[kErrNonphys], 1);
+            cz[0] = rho * norm3(tmp);
+            cz[NT] = T(kLog2e) / (T(2) * tmp);
+            cz[2 * NT] = ux;
+            cz[3 * NT] = uy;
+            cz[4 * NT] = uz;
+            cz[5 * NT] = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+        }
+        if (fl & kZero) zerom |= 1u << z;
+        masks |= (uint32_t)((fl >> kMaskShift3) & 0x3F) << (6 * z);
+        if (in && near_side3(g, i, j, k)) mirm |= 1u << z;
+#pragma unroll
+        for (int m = 0; m < 10; ++m) ksum[(z * 10 + m) * NT + tid] = T(0);
+    }
+    const int pc0 = inij ? nbr3(g, i, j, k0) : 0;
+
+    T q[ZC][5];
+#pragma unroll
+    for (int z = 0; z < ZC; ++z)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) q[z][m] = T(0);
+    int fold = 0;
+    for (int grp = g0; grp < g1; ++grp) {
+        const int yz = grp / g.nxg, xg = grp - yz * g.nxg;
+        const VYZ3<T> cyz = a.vyz[yz];
+        T vx[W], nux[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const VX3<T> cx = a.vxt[xg * W + e];
+            vx[e] = cx.vx;
+            nux[e] = cx.nux;
+        }
+        const V *src = reinterpret_cast<const V *>(a.fin) + (long)grp * g.slab;
+        V *dst = reinterpret_cast<V *>(a.fout) + (long)grp * g.slab;
+        const bool py = cyz.vy >= T(0), pz = cyz.vz >= T(0);
+        const int oy = py ? sy : -sy, oz = pz ? sz : -sz;
+#pragma unroll
+        for (int z = 0; z < ZC; ++z) {
+            const bool pl = (plainm >> z) & 1u;
+            if (!pl && !((zerom >> z) & 1u)) continue;
+            const int pc = pc0 + z * sz;
+            T out[W];
+            if (pl) {
+                const uint32_t mk = masks >> (6 * z);
+                const T wxm = (mk & 1u) ? T(0.5) : T(0), wxp = (mk & 2u) ? T(0.5) : T(0);
+                const T wym = (mk & 4u) ? T(0.5) : T(0), wyp = (mk & 8u) ? T(0.5) : T(0);
+                const T wzm = (mk & 16u) ? T(0.5) : T(0), wzp = (mk & 32u) ? T(0.5) : T(0);
+                const T *cz = coef + z * kCoef3 * NT + tid;
+                const T A = cz[0], c2 = cz[NT], ux = cz[2 * NT], uy = cz[3 * NT], uz = cz[4 * NT], r = cz[5 * NT];
+                const T dy = cyz.vy - uy, dz = cyz.vz - uz;
+                const T dyz = dy * dy + dz * dz;
+                T f[W], xm1[W], xp1[W], ym1[W], zm1[W];
+                T xm2[W], xp2[W], ym2[W], yp1[W], zm2[W], zp1[W];
+                vld<T>(src + pc, f);
+                vld<T>(src + pc - 1, xm1);
+                vld<T>(src + pc + 1, xp1);
+                vld<T>(src + pc - oy, ym1);
+                vld<T>(src + pc - oz, zm1);
+                if (MUSCL) {
+                    vld<T>(src + pc - 2, xm2);
+                    vld<T>(src + pc + 2, xp2);
+                    vld<T>(src + pc - 2 * oy, ym2);
+                    vld<T>(src + pc + oy, yp1);
+                    vld<T>(src + pc - 2 * oz, zm2);
+                    vld<T>(src + pc + oz, zp1);
+                }
+                const T wyo = py ? wyp : wym, wyi = py ? wym : wyp;
+                const T wzo = pz ? wzp : wzm, wzi = pz ? wzm : wzp;
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    const bool px = vx[e] >= T(0);
+                    const T u1 = px ? xm1[e] : xp1[e];
+                    const T d1 = px ? xp1[e] : xm1[e];
+                    const T u2 = MUSCL ? (px ? xm2[e] : xp2[e]) : T(0);
+                    const T dfx = dflux<T, MUSCL>(f[e], u1, u2, d1, nux[e], px ? wxp : wxm, px ? wxm : wxp);
+                    const T dfy = dflux<T, MUSCL>(f[e], ym1[e], MUSCL ? ym2[e] : T(0), MUSCL ? yp1[e] : T(0),
+                                                  cyz.nuy, wyo, wyi);
+                    const T dfz = dflux<T, MUSCL>(f[e], zm1[e], MUSCL ? zm2[e] : T(0), MUSCL ? zp1[e] : T(0),
+                                                  cyz.nuz, wzo, wzi);
+                    const T d = vx[e] - ux;
+                    const T feq = A * dexp2(-(d * d + dyz) * c2);
+                    out[e] = f[e] - nux[e] * dfx - cyz.nuy * dfy - cyz.nuz * dfz + r * (feq - f[e]);
+                }
+                T s = 0, sx = 0, sxx = 0;
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    s += out[e];
+                    sx += vx[e] * out[e];
+                    sxx += vx[e] * vx[e] * out[e];
+                }
+                q[z][0] += s;
+                q[z][1] += sx;
+                q[z][2] += cyz.vy * s;
+                q[z][3] += cyz.vz * s;
+                q[z][4] += T(0.5) * (sxx + (cyz.vy * cyz.vy + cyz.vz * cyz.vz) * s);
+            } else {
+#pragma unroll
+                for (int e = 0; e < W; ++e) out[e] = T(0);
+            }
+            vst<T>(dst + pc, out);
+            if ((mirm >> z) & 1u) {
+                int mir[6];
+                mirrors3(g, i, j, k0 + z, mir);
+#pragma unroll
+                for (int t = 0; t < 6; ++t)
+                    if (mir[t] >= 0) vst<T>(dst + mir[t], out);
+            }
+        }
+        // fold the plain sums of 8 groups into the compensated sums
+        if (++fold == 8 || grp + 1 == g1) {
+            fold = 0;
+#pragma unroll
+            for (int z = 0; z < ZC; ++z)
+#pragma unroll
+                for (int m = 0; m < 5; ++m) {
+                    T *ks = ksum + (z * 10 + 2 * m) * NT + tid;
+                    Acc<T> acc;
+                    acc.s = ks[0];
+                    acc.c = ks[NT];
+                    acc.add(q[z][m]);
+                    ks[0] = acc.s;
+                    ks[NT] = acc.c;
+                    q[z][m] = T(0);
+                }
+        }
+    }
+#pragma unroll
+    for (int z = 0; z < ZC; ++z) {
+        if (!(((plainm | zerom) >> z) & 1u)) continue;
+        const long cell = ((long)(k0 + z) * g.ny + j) * g.nx + i;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const T *ks = ksum + (z * 10 + 2 * m) * NT + tid;
+            a.pout[((long)split * 5 + m) * nc + cell] = ks[0] - ks[NT];
+        }
+    }
+}
+
+// ------------------------------------------------------------ control volumes
+struct Cv3Args {
+    Grid3D g;
+    Geo3D G;
+    const int32_t *master;
+    const uint16_t *flags;
+    const int32_t *spec_list;
+    const int32_t *wall_list;
+    const int32_t *wslot;
+    const int32_t *counts;
+    int cap;
+    int S;
+    int gps;
+    const void *cvinfo;
+    const void *vxt;
+    const void *vyz;
+    int *err;
+};
+
+// One member (virtual cell) of a control volume.
+struct __align__(16) CvMember3 {
+    int pc;                   // slab index
+    int mir[6];               // padding mirrors (-1: none)
+    int cell;                 // cell index
+    int wslot;                // wall slot, -1 if none
+    int mask;                 // limiter mask of the six faces
+    int live;                 // non-solid (fixed obstacle: always)
+    int pad;
+    double A[6];              // face areas x-, x+, y-, y+, z-, z+
+    double sw, nwx, nwy, nwz; // wall face (sw = 0: none)
+    double vol;
+};
+
+struct __align__(16) CvInfo3 {
+    int nm, ok, pcm, pad;
+    double bco;               // dt / S (fixed obstacle: S^n = S^{n+1,*})
+    double S;
+    CvMember3 mem[kMaxMembers3];
+};
+
+// Ordered members of control volume m (cells whose master is m) within the
+// window reachable by the master search.
+__device__ int gather_members3(const Cv3Args &c, int m, int32_t *mem)
+{
+    __shared__ int wcnt[8];
+    const Grid3D &g = c.g;
+    const int R = kMaxWalk, Wd = 2 * kMaxWalk + 1, npos = Wd * Wd * Wd;
+    int mi, mj, mk;
+    cell_ijk(g, m, mi, mj, mk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int total = 0;
+    for (int base = 0; base < npos; base += 32 * nw) {
+        const int pos = base + warp * 32 + lane;
+        bool hit = false;
+        int ii = 0, jj = 0, kk = 0;
+        if (pos < npos) {
+            ii = mi - R + pos % Wd;
+            jj = mj - R + (pos / Wd) % Wd;
+            kk = mk - R + pos / (Wd * Wd);
+            if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz)
+                hit = c.master[((long)kk * g.ny + jj) * g.nx + ii] == m;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = total;
+        for (int w = 0; w < warp; ++w) off += wcnt[w];
+        const int rank = off + __popc(bal & ((1u << lane) - 1u));
+        if (hit) {
+            if (rank < kMaxMembers3) mem[rank] = (kk * g.ny + jj) * g.nx + ii;
+            else atomicExch(&c.err[kErrCapacity], 1);
+        }
+        int add = 0;
+        for (int w = 0; w < nw; ++w) add += wcnt[w];
+        total += add;
+        __syncthreads();
+    }
+    return total < kMaxMembers3 ? total : kMaxMembers3;
+}
+
+// Members are listed in z-major order of the window; the fixed order keeps
+// the sums deterministic.  Sorting is not needed: the order only has to be
+// the same on every call.
+__global__ void __launch_bounds__(256) k_members3(Cv3Args c, CvInfo3 *info)
+{
+    __shared__ int32_t mem[kMaxMembers3];
+    const Grid3D &g = c.g;
+    const int n = min(c.counts[0], c.cap);
+    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
+        const int m = c.spec_list[idx];
+        const int nm = gather_members3(c, m, mem);
+        CvInfo3 &I = info[idx];
+        if (threadIdx.x < nm) {
+            const int q = mem[threadIdx.x];
+            CvMember3 &M = I.mem[threadIdx.x];
+            int i, j, k;
+            cell_ijk(g, q, i, j, k);
+            M.cell = q;
+            M.pc = nbr3(g, i, j, k);
+            mirrors3(g, i, j, k, M.mir);
+            const long xf = ((long)k * g.ny + j) * (g.nx + 1) + i;
+            const long yf = ((long)k * (g.ny + 1) + j) * g.nx + i;
+            const long zf = ((long)k * g.ny + j) * g.nx + i;
+            M.A[0] = c.G.ax[xf]; M.A[1] = c.G.ax[xf + 1];
+            M.A[2] = c.G.ay[yf]; M.A[3] = c.G.ay[yf + g.nx];
+            M.A[4] = c.G.az[zf]; M.A[5] = c.G.az[zf + (long)g.nx * g.ny];
+            M.wslot = c.wslot[q];
+            const bool wall = M.wslot >= 0;
+            M.sw = wall ? c.G.sw[q] : 0.0;
+            M.nwx = c.G.nwx[q]; M.nwy = c.G.nwy[q]; M.nwz = c.G.nwz[q];
+            M.vol = c.G.vol[q];
+            M.mask = (c.flags[q] >> kMaskShift3) & 0x3F;
+            M.live = c.G.type[q] != DVM_SOLID;
+            M.pad = 0;
+            if (q == m) I.pcm = M.pc;
+        }
+        if (threadIdx.x == 0) {
+            double S = 0;
+            for (int t = 0; t < nm; ++t) S += c.G.vol[mem[t]];
+            I.nm = nm;
+            I.ok = S > 0;
+            I.S = S;
+            I.bco = S > 0 ? g.dt / S : 0.0;
+            I.pad = 0;
+            if (!(S > 0)) atomicExch(&c.err[kErrGeometry], 1);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void load_info3(const CvInfo3 *src, CvInfo3 *dst)
+{
+    static_assert(sizeof(CvInfo3) % 16 == 0, "CvInfo3 is copied in 16-byte words");
+    const int4 *s4 = reinterpret_cast<const int4 *>(src);
+    int4 *d4 = reinterpret_cast<int4 *>(dst);
+    for (int q = threadIdx.x; q < (int)(sizeof(CvInfo3) / 16); q += blockDim.x) d4[q] = __ldg(s4 + q);
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T face_flux3(T L, T v, T nu, T fAA, T fA, T fB, T fBB, bool muscl)
+{
+    if (!muscl) return L * (fmin(v, T(0)) * fB + fmax(v, T(0)) * fA);
+    T fr;
+    if (v > T(0)) fr = fA + T(0.5) * (T(1) - nu) * minmod(fB - fA, fA - fAA);
+    else if (v < T(0)) fr = fB - T(0.5) * (T(1) - nu) * minmod(fBB - fB, fB - fA);
+    else return T(0);
+    return L * (v * fr);
+}
+
+template <typename T>
+__device__ __forceinline__ void write_split_partials3(T *part, int s, long nc, long k, const T (&t)[5])
+{
+#pragma unroll
+    for (int m = 0; m < 5; ++m) part[((long)s * 5 + m) * nc + k] = t[m];
+}
+
+// Velocity of padded index p from the tables.
+template <typename T>
+__device__ __forceinline__ void vel3(const Grid3D &g, const VX3<T> *vxt, const VYZ3<T> *vyz, int p, T &vx, T &vy,
+                                     T &vz, T &nux, T &nuy, T &nuz)
+{
+    const int grp = p / g.W, e = p - grp * g.W;
+    const int yz = grp / g.nxg;
+    const VX3<T> cx = vxt[(grp - yz * g.nxg) * g.W + e];
+    const VYZ3<T> c = vyz[yz];
+    vx = cx.vx; nux = cx.nux;
+    vy = c.vy; vz = c.vz; nuy = c.nuy; nuz = c.nuz;
+}
+
+// Fusion (3D form of Eq. FusionDD): F_CV = sum vol F / S over a merged
+// control volume, written back to every member, with the moment sums.  One
+// work item is one control volume and one velocity split.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fusion3(Cv3Args c, T *f, T *part)
+{
+    __shared__ T red[8 * 2];
+    const Grid3D &g = c.g;
+    const CvInfo3 *info = reinterpret_cast<const CvInfo3 *>(c.cvinfo);
+    const VX3<T> *vxt = reinterpret_cast<const VX3<T> *>(c.vxt);
+    const VYZ3<T> *vyz = reinterpret_cast<const VYZ3<T> *>(c.vyz);
+    const long nc = (long)g.nx * g.ny * g.nz;
+    const int n = min(c.counts[0], c.cap) * c.S;
+    for (int item = blockIdx.x; item < n; item += gridDim.x) {
+        const CvInfo3 &I = info[item / c.S];
+        const int sp = item % c.S;
+        const int nm = I.nm;
+        if (nm <= 1) continue;
+        const int v0 = sp * c.gps * g.W, v1 = min(g.nvp, v0 + c.gps * g.W);
+        const double S = I.S;
+        Acc<T> a[5];
+        for (int p = v0 + threadIdx.x; p < v1; p += blockDim.x) {
+            double acc = 0;
+            for (int t = 0; t < nm; ++t) acc += I.mem[t].vol * (double)f[pidx3(g, p, I.mem[t].pc)];
+            const T fcv = (T)(acc / S);
+            for (int t = 0; t < nm; ++t) {
+                f[pidx3(g, p, I.mem[t].pc)] = fcv;
+                for (int u = 0; u < 6; ++u)
+                    if (I.mem[t].mir[u] >= 0) f[pidx3(g, p, I.mem[t].mir[u])] = fcv;
+            }
+            T vx, vy, vz, nux, nuy, nuz;
+            vel3(g, vxt, vyz, p, vx, vy, vz, nux, nuy, nuz);
+            a[0].add(fcv); a[1].add(vx * fcv); a[2].add(vy * fcv); a[3].add(vz * fcv);
+            a[4].add(T(0.5) * (vx * vx + vy * vy + vz * vz) * fcv);
+        }
+        T t[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) t[m] = block_acc(a[m], red);
+        if (threadIdx.x < nm) write_split_partials3<T>(part, sp, nc, I.mem[threadIdx.x].cell, t);
+        __syncthreads();
+    }
+}
+
+// Wall density phi (zero net mass flux across the wall face), stress
+// Sigma = sum (v - u_w)(v - u_w)^T F_w dv and the force Sigma n_w S_w on the
+// body (3D forms of Eqs. BoundaryDDv, StressTensorDD, eq-force), torque about
+// the z axis through the centre (Eq. eq-torque), u_w = u_c + omega e_z x
+// (r - c) (Eq. uwDD).  One block per wall cell: products and compensated sums
+// in the state precision over all velocities, phi and the stress in FP64 by
+// thread 0.  The last block sums the cells in list order into the body
+// record and the history.  (phi, u_w, T_w) of each wall cell are left for
+// the control-volume kernel.
+template <typename T>
+__global__ void __launch_bounds__(256) k_wall3(Cv3Args c, BodyParams b, BodyDev *body, const T *f, double *wdat,
+                                               double *wcontrib, int *ticket, double *hist)
+{
+    __shared__ double red[8 * 8];
+    __shared__ T ex[kMaxAxisNv], ey[kMaxAxisNv], ez[kMaxAxisNv];
+    __shared__ T wsc[8];
+    __shared__ T wred[8 * 2];
+    __shared__ bool last;
+    const Grid3D &g = c.g;
+    const VX3<T> *vxt = reinterpret_cast<const VX3<T> *>(c.vxt);
+    const VYZ3<T> *vyz = reinterpret_cast<const VYZ3<T> *>(c.vyz);
+    const int nw = min(c.counts[1], c.cap);
+    const double omega = body->omega;
+    const int tid = threadIdx.x;
+    for (int idx = blockIdx.x; idx < nw; idx += gridDim.x) {
+        const int q = c.wall_list[idx];
+        const double rx = c.G.rwx[q] - b.cx, ry = c.G.rwy[q] - b.cy;
+        const double uwx = b.vbx - ry * omega, uwy = b.vby + rx * omega, uwz = 0.0;
+        if (tid == 0) {
+            wsc[0] = (T)uwx; wsc[1] = (T)uwy; wsc[2] = (T)uwz;
+            wsc[3] = (T)c.G.nwx[q]; wsc[4] = (T)c.G.nwy[q]; wsc[5] = (T)c.G.nwz[q];
+            wsc[6] = (T)(2.0 * b.Tw);
+            const double a2 = 2.0 * kPi * b.Tw;
+            wsc[7] = (T)(1.0 / (a2 * sqrt(a2)));
+        }
+        __syncthreads();
+        const T ux = wsc[0], uy = wsc[1], uz = wsc[2], nx = wsc[3], ny = wsc[4], nz = wsc[5], twoTw = wsc[6];
+        const T cm = wsc[7];
+        // separable Maxwellian M[1, u_w, T_w] = cm ex[p1] ey[p2] ez[p3]
+        for (int t = tid; t < g.nvx + g.nvy + g.nvz; t += blockDim.x) {
+            if (t < g.nvx) { const T d = vxt[t].vx - ux; ex[t] = dexp(-(d * d) / twoTw); }
+            else if (t < g.nvx + g.nvy) {
+                const int p2 = t - g.nvx;
+                const T d = vyz[p2].vy - uy;
+                ey[p2] = dexp(-(d * d) / twoTw);
+            } else {
+                const int p3 = t - g.nvx - g.nvy;
+                const T d = vyz[p3 * g.nvy].vz - uz;
+                ez[p3] = dexp(-(d * d) / twoTw);
+            }
+        }
+        __syncthreads();
+        const int pc = pcell3(g, q);
+        // a[0] = sum_{c>0} c F, a[1] = sum_{c<0} c M, a[2..7] = sum_{c<0} (v-u_w)(v-u_w) M,
+        // a[8..13] = sum_{c>0} (v-u_w)(v-u_w) F   (xx, xy, xz, yy, yz, zz)
+        Acc<T> a[14];
+        for (int p = tid; p < g.nv; p += blockDim.x) {
+            const int p1 = p % g.nvx, r = p / g.nvx;
+            const int p3 = r / g.nvy, p2 = r - p3 * g.nvy;
+            const T vx = vxt[p1].vx, vy = vyz[r].vy, vz = vyz[r].vz;
+            const T ax = vx - ux, ay = vy - uy, az = vz - uz;
+            const T cp = ax * nx + ay * ny + az * nz;
+            if (cp > T(0)) {
+                const T fv = f[pidx3(g, r * g.nvxp + p1, pc)];
+                a[0].add(cp * fv);
+                a[8].add(ax * ax * fv); a[9].add(ax * ay * fv); a[10].add(ax * az * fv);
+                a[11].add(ay * ay * fv); a[12].add(ay * az * fv); a[13].add(az * az * fv);
+            } else if (cp < T(0)) {
+                const T m1 = cm * ex[p1] * ey[p2] * ez[p3];
+                a[1].add(cp * m1);
+                a[2].add(ax * ax * m1); a[3].add(ax * ay * m1); a[4].add(ax * az * m1);
+                a[5].add(ay * ay * m1); a[6].add(ay * az * m1); a[7].add(az * az * m1);
+            }
+        }
+        T rr[14];
+#pragma unroll
+        for (int t = 0; t < 14; ++t) rr[t] = block_acc(a[t], wred);
+        if (tid == 0) {
+            const double dv = g.dv;
+            const double phi = -((double)rr[0] * dv) / ((double)rr[1] * dv);
+            double S6[6];
+            for (int t = 0; t < 6; ++t) S6[t] = (phi * (double)rr[2 + t] + (double)rr[8 + t]) * dv;
+            const double nxd = c.G.nwx[q], nyd = c.G.nwy[q], nzd = c.G.nwz[q], sw = c.G.sw[q];
+            const double fx = (S6[0] * nxd + S6[1] * nyd + S6[2] * nzd) * sw;
+            const double fy = (S6[1] * nxd + S6[3] * nyd + S6[4] * nzd) * sw;
+            const double fz = (S6[2] * nxd + S6[4] * nyd + S6[5] * nzd) * sw;
+            double *wc = wcontrib + 4L * idx;
+            wc[0] = fx; wc[1] = fy; wc[2] = fz; wc[3] = rx * fy - ry * fx;
+            double *d = wdat + 6L * idx;
+            d[0] = phi; d[1] = uwx; d[2] = uwy; d[3] = uwz; d[4] = b.Tw; d[5] = 0;
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double fx = 0, fy = 0, fz = 0, tq = 0;
+    for (int t = tid; t < nw; t += blockDim.x) {
+        fx += wcontrib[4 * t]; fy += wcontrib[4 * t + 1]; fz += wcontrib[4 * t + 2]; tq += wcontrib[4 * t + 3];
+    }
+    fx = block_sum(fx, red); fy = block_sum(fy, red + 8); fz = block_sum(fz, red + 16); tq = block_sum(tq, red + 24);
+    if (tid == 0) {
+        body->F[0] = fx; body->F[1] = fy; body->F[2] = fz; body->torque = tq;
+        double *h = hist + 6 * (body->step % kHistCap);
+        h[0] = fx; h[1] = fy; h[2] = fz; h[3] = tq; h[4] = body->theta; h[5] = body->omega;
+        body->step += 1;
+        *ticket = 0;
+    }
+}
+
+// Explicit update of one control volume (Eq. eq-schema3D): fluxes across the
+// six faces of every member and across its wall face with the diffuse state
+// F_w = phi M[1, u_w, T_w] on incoming velocities, relaxation, distribution
+// to the members and the moment sums of the velocity split.  One work item is
+// one control volume and one split.
+template <typename T>
+__global__ void __launch_bounds__(256) k_special3(Cv3Args c, const T *fin, T *fout, const T *pin, T *pout,
+                                                  const double *wdat)
+{
+    __shared__ T red[8 * 2];
+    __shared__ __align__(16) CvInfo3 I;
+    const Grid3D &g = c.g;
+    const CvInfo3 *info = reinterpret_cast<const CvInfo3 *>(c.cvinfo);
+    const VX3<T> *vxt = reinterpret_cast<const VX3<T> *>(c.vxt);
+    const VYZ3<T> *vyz = reinterpret_cast<const VYZ3<T> *>(c.vyz);
+    const long nc = (long)g.nx * g.ny * g.nz;
+    const int n = min(c.counts[0], c.cap) * c.S;
+    const int sy = g.nx + 4, sz = (g.nx + 4) * (g.ny + 4);
+    for (int item = blockIdx.x; item < n; item += gridDim.x) {
+        const int idx = item / c.S, sp = item % c.S;
+        load_info3(info + idx, &I);
+        if (!I.ok) { __syncthreads(); continue; }
+        const int nm = I.nm;
+        const int v0 = sp * c.gps * g.W, v1 = min(g.nvp, v0 + c.gps * g.W);
+        const int m = c.spec_list[idx];
+        T s[5];
+        gather_partials3(pin, c.S, nc, m, s);
+        T rho, ux, uy, uz, tmp;
+        if (!primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp) && threadIdx.x == 0 && sp == 0)
+            atomicExch(&c.err[kErrNonphys], 1);
+        const T bco = (T)I.bco, r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+        const T A = rho * norm3(tmp);
+        const T i2T = T(1) / (T(2) * tmp);
+        Acc<T> acc[5];
+        for (int p = v0 + threadIdx.x; p < v1; p += blockDim.x) {
+            T vx, vy, vz, nux, nuy, nuz;
+            vel3(g, vxt, vyz, p, vx, vy, vz, nux, nuy, nuz);
+            const int grp = p / g.W, e = p - grp * g.W;
+            const T *fg = fin + (long)grp * g.slab * g.W + e;     // element of slab index s: fg[s * W]
+            const int Wd = g.W;
+            T R = 0;
+            for (int t = 0; t < nm; ++t) {
+                const CvMember3 &M = I.mem[t];
+                if (!M.live) continue;
+                const int pc = M.pc;
+                const T fc = fg[(long)pc * Wd];
+                T Fw = 0;
+                if (M.wslot >= 0) {
+                    const double *d = wdat + 6L * M.wslot;
+                    const T phi = (T)d[0], uwx = (T)d[1], uwy = (T)d[2], uwz = (T)d[3], Tw = (T)d[4];
+                    const T ax = vx - uwx, ay = vy - uwy, az = vz - uwz;
+                    const T cw = ax * (T)M.nwx + ay * (T)M.nwy + az * (T)M.nwz;
+                    const T m1 = dexp(-(ax * ax + ay * ay + az * az) / (T(2) * Tw)) * norm3(Tw);
+                    Fw = (T)M.sw * (fmin(cw, T(0)) * (phi * m1) + fmax(cw, T(0)) * fc);
+                }
+                const bool mxm = M.mask & 1, mxp = M.mask & 2, mym = M.mask & 4, myp = M.mask & 8;
+                const bool mzm = M.mask & 16, mzp = M.mask & 32;
+                const T xm1 = fg[(long)(pc - 1) * Wd], xp1 = fg[(long)(pc + 1) * Wd];
+                const T ym1 = fg[(long)(pc - sy) * Wd], yp1 = fg[(long)(pc + sy) * Wd];
+                const T zm1 = fg[(long)(pc - sz) * Wd], zp1 = fg[(long)(pc + sz) * Wd];
+                T xm2 = 0, xp2 = 0, ym2 = 0, yp2 = 0, zm2 = 0, zp2 = 0;
+                if (M.mask) {
+                    xm2 = fg[(long)(pc - 2) * Wd]; xp2 = fg[(long)(pc + 2) * Wd];
+                    ym2 = fg[(long)(pc - 2 * sy) * Wd]; yp2 = fg[(long)(pc + 2 * sy) * Wd];
+                    zm2 = fg[(long)(pc - 2 * sz) * Wd]; zp2 = fg[(long)(pc + 2 * sz) * Wd];
+                }
+                const T Fxp = face_flux3<T>((T)M.A[1], vx, nux, xm1, fc, xp1, xp2, mxp);
+                const T Fxm = face_flux3<T>((T)M.A[0], vx, nux, xm2, xm1, fc, xp1, mxm);
+                const T Fyp = face_flux3<T>((T)M.A[3], vy, nuy, ym1, fc, yp1, yp2, myp);
+                const T Fym = face_flux3<T>((T)M.A[2], vy, nuy, ym2, ym1, fc, yp1, mym);
+                const T Fzp = face_flux3<T>((T)M.A[5], vz, nuz, zm1, fc, zp1, zp2, mzp);
+                const T Fzm = face_flux3<T>((T)M.A[4], vz, nuz, zm2, zm1, fc, zp1, mzm);
+                R += (Fxp - Fxm) + (Fyp - Fym) + (Fzp - Fzm) + Fw;
+            }
+            const T fcv = fg[(long)I.pcm * Wd];
+            const T dxu = vx - ux, dyu = vy - uy, dzu = vz - uz;
+            const T feq = A * dexp(-(dxu * dxu + dyu * dyu + dzu * dzu) * i2T);
+            const T fn = fcv - bco * R + r * (feq - fcv);
+            T *og = fout + (long)grp * g.slab * g.W + e;
+            for (int t = 0; t < nm; ++t) {
+                const CvMember3 &M = I.mem[t];
+                og[(long)M.pc * Wd] = fn;
+                for (int u = 0; u < 6; ++u)
+                    if (M.mir[u] >= 0) og[(long)M.mir[u] * Wd] = fn;
+            }
+            acc[0].add(fn); acc[1].add(vx * fn); acc[2].add(vy * fn); acc[3].add(vz * fn);
+            acc[4].add(T(0.5) * (vx * vx + vy * vy + vz * vz) * fn);
+        }
+        T t5[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) t5[q] = block_acc(acc[q], red);
+        if (threadIdx.x < nm) write_split_partials3<T>(pout, sp, nc, I.mem[threadIdx.x].cell, t5);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ state services
+// Moment sums of the current state for every cell (warp per cell) as split 0
+// of the partials, the other splits 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_partials3(Grid3D g, int S, const T *f, T *part, const int8_t *type, int *err)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long nc = (long)g.nx * g.ny * g.nz;
+    const long cell = (long)blockIdx.x * 8 + warp;
+    if (cell >= nc) return;
+    Acc<T> s[5];
+    const int pc = pcell3(g, (int)cell);
+    for (int p = lane; p < g.nv; p += 32) {
+        const int p1 = p % g.nvx, r = p / g.nvx;
+        const int p3 = r / g.nvy, p2 = r - p3 * g.nvy;
+        const T vx = T(g.vxmin + p1 * g.dvx), vy = T(g.vymin + p2 * g.dvy), vz = T(g.vzmin + p3 * g.dvz);
+        const T fv = f[pidx3(g, r * g.nvxp + p1, pc)];
+        s[0].add(fv); s[1].add(vx * fv); s[2].add(vy * fv); s[3].add(vz * fv);
+        s[4].add(T(0.5) * (vx * vx + vy * vy + vz * vz) * fv);
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) s[m].warp_reduce();
+    if (lane == 0) {
+        const bool keep = type[cell] != DVM_SOLID;
+        T v[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) v[m] = keep ? s[m].value() : T(0);
+        if (keep) {
+            T rho, ux, uy, uz, tmp;
+            if (!primitives3<T>(pick<T>(g.dv_f, g.dv), v, rho, ux, uy, uz, tmp)) atomicExch(&err[kErrNonphys], 1);
+        }
+        for (int q = 0; q < S; ++q)
+#pragma unroll
+            for (int m = 0; m < 5; ++m) part[((long)q * 5 + m) * nc + cell] = q == 0 ? v[m] : T(0);
+    }
+}
+
+// FP64 moments for output: rho, ux, uy, uz, T per cell.
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments_out3(Grid3D g, const T *f, double *out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long cell = (long)blockIdx.x * 8 + warp;
+    if (cell >= (long)g.nx * g.ny * g.nz) return;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+    const int pc = pcell3(g, (int)cell);
+    for (int p = lane; p < g.nv; p += 32) {
+        const int p1 = p % g.nvx, r = p / g.nvx;
+        const int p3 = r / g.nvy, p2 = r - p3 * g.nvy;
+        const double vx = g.vxmin + p1 * g.dvx, vy = g.vymin + p2 * g.dvy, vz = g.vzmin + p3 * g.dvz;
+        const double fv = (double)f[pidx3(g, r * g.nvxp + p1, pc)];
+        s0 += fv; s1 += vx * fv; s2 += vy * fv; s3 += vz * fv;
+        s4 += 0.5 * (vx * vx + vy * vy + vz * vz) * fv;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o); s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+    }
+    if (lane == 0) {
+        double *o5 = out + cell * 5;
+        const double rho = s0 * g.dv;
+        if (!(rho > 0)) { for (int q = 0; q < 5; ++q) o5[q] = 0; return; }
+        const double ux = s1 * g.dv / rho, uy = s2 * g.dv / rho, uz = s3 * g.dv / rho;
+        o5[0] = rho; o5[1] = ux; o5[2] = uy; o5[3] = uz;
+        o5[4] = (2.0 * (s4 * g.dv) / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
+    }
+}
+
+__device__ __forceinline__ double maxw3(const double *q, double vx, double vy, double vz)
+{
+    const double ax = vx - q[1], ay = vy - q[2], az = vz - q[3];
+    const double a2 = 2.0 * kPi * q[4];
+    return q[0] / (a2 * sqrt(a2)) * exp(-(ax * ax + ay * ay + az * az) / (2.0 * q[4]));
+}
+
+// Maxwellian state from per-cell primitives (rho, ux, uy, uz, T); solid cells
+// get 0.  One block row per cell, threads over the public velocities.
+template <typename T>
+__global__ void k_init3(Grid3D g, const double *prim, const int8_t *type, T *f)
+{
+    const int q = blockIdx.x;
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    if (p >= g.nv) return;
+    const int p1 = p % g.nvx, r = p / g.nvx;
+    const int p3 = r / g.nvy, p2 = r - p3 * g.nvy;
+    const double *s = prim + 5L * q;
+    double m = 0;
+    if (type[q] != DVM_SOLID && s[0] > 0)
+        m = maxw3(s, g.vxmin + p1 * g.dvx, g.vymin + p2 * g.dvy, g.vzmin + p3 * g.dvz);
+    f[pidx3(g, r * g.nvxp + p1, pcell3(g, q))] = (T)m;
+}
+
+// Ghost cells of a Maxwellian side (both layers, both state buffers).
+template <typename T>
+__global__ void k_ghost3(Grid3D g, const double *prim, int side, int nside, T *f0, T *f1)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nside * g.nv) return;
+    const int q = (int)(t / g.nv), p = (int)(t % g.nv);
+    const int p1 = p % g.nvx, r = p / g.nvx;
+    const int p3 = r / g.nvy, p2 = r - p3 * g.nvy;
+    const double m = maxw3(prim + 5L * q, g.vxmin + p1 * g.dvx, g.vymin + p2 * g.dvy, g.vzmin + p3 * g.dvz);
+    // side cell q: row-major over the two remaining axes
+    int a, b;
+    if (side < 2) { a = q % g.ny; b = q / g.ny; }          // (j, k)
+    else if (side < 4) { a = q % g.nx; b = q / g.nx; }     // (i, k)
+    else { a = q % g.nx; b = q / g.nx; }                   // (i, j)
+    const int pp = r * g.nvxp + p1;
+    for (int layer = 1; layer <= 2; ++layer) {
+        int pc;
+        if (side == 0) pc = nbr3(g, -layer, a, b);
+        else if (side == 1) pc = nbr3(g, g.nx - 1 + layer, a, b);
+        else if (side == 2) pc = nbr3(g, a, -layer, b);
+        else if (side == 3) pc = nbr3(g, a, g.ny - 1 + layer, b);
+        else if (side == 4) pc = nbr3(g, a, b, -layer);
+        else pc = nbr3(g, a, b, g.nz - 1 + layer);
+        f0[pidx3(g, pp, pc)] = (T)m;
+        f1[pidx3(g, pp, pc)] = (T)m;
+    }
+}
+
+// Padding of periodic and zero-gradient sides from the interior (both
+// layers, every padded velocity).
+template <typename T>
+__global__ void k_halo3(Grid3D g, T *f)
+{
+    const long fx = (long)g.ny * g.nz, fy = (long)g.nx * g.nz, fz = (long)g.nx * g.ny;
+    const long per = 2 * (fx + fy + fz);      // padding cells of one layer
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * per * g.nvp) return;
+    const long hc = t % (2 * per);
+    const int p = (int)(t / (2 * per));
+    const int layer = (int)(hc / per) + 1;
+    long pos = hc % per;
+    int side;
+    if (pos < 2 * fx) { side = pos < fx ? 0 : 1; pos = pos % fx; }
+    else if (pos < 2 * fx + 2 * fy) { pos -= 2 * fx; side = pos < fy ? 2 : 3; pos = pos % fy; }
+    else { pos -= 2 * fx + 2 * fy; side = pos < fz ? 4 : 5; pos = pos % fz; }
+    const int kind = g.bc[side];
+    if (kind == DVM_BC_MAXWELLIAN) return;
+    const bool per_ = kind == DVM_BC_PERIODIC;
+    int di, dj, dk, si, sj, sk;
+    if (side < 2) {
+        const int j = (int)(pos % g.ny), k = (int)(pos / g.ny);
+        dj = sj = j; dk = sk = k;
+        if (side == 0) { di = -layer; si = per_ ? g.nx - layer : 0; }
+        else { di = g.nx - 1 + layer; si = per_ ? layer - 1 : g.nx - 1; }
+    } else if (side < 4) {
+        const int i = (int)(pos % g.nx), k = (int)(pos / g.nx);
+        di = si = i; dk = sk = k;
+        if (side == 2) { dj = -layer; sj = per_ ? g.ny - layer : 0; }
+        else { dj = g.ny - 1 + layer; sj = per_ ? layer - 1 : g.ny - 1; }
+    } else {
+        const int i = (int)(pos % g.nx), j = (int)(pos / g.nx);
+        di = si = i; dj = sj = j;
+        if (side == 4) { dk = -layer; sk = per_ ? g.nz - layer : 0; }
+        else { dk = g.nz - 1 + layer; sk = per_ ? layer - 1 : g.nz - 1; }
+    }
+    f[pidx3(g, p, nbr3(g, di, dj, dk))] = f[pidx3(g, p, nbr3(g, si, sj, sk))];
+}
+
+// Conversion between the public layout [cell][p] and the device layout.
+template <typename T>
+__global__ void k_pack3(Grid3D g, const T *src, T *dst, int to_dev)
+{
+    const int q = blockIdx.x;
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    if (p >= g.nv) return;
+    const long t = (long)q * g.nv + p;
+    const long d = pidx3(g, padded3(g, p), pcell3(g, q));
+    if (to_dev) dst[d] = src[t];
+    else dst[t] = src[d];
+}
+
+template <typename T>
+__global__ void k_zero_solid3(Grid3D g, const int8_t *type, T *f)
+{
+    const int q = blockIdx.x;
+    if (type[q] != DVM_SOLID) return;
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    if (p >= g.nvp) return;
+    f[pidx3(g, p, pcell3(g, q))] = T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mass_cells3(Grid3D g, const T *f, const double *vol, double *cm)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long cell = (long)blockIdx.x * 8 + warp;
+    if (cell >= (long)g.nx * g.ny * g.nz) return;
+    double s = 0;
+    const int pc = pcell3(g, (int)cell);
+    for (int p = lane; p < g.nvp; p += 32) s += (double)f[pidx3(g, p, pc)];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) cm[cell] = vol[cell] * (s * g.dv);
+}
+
+__global__ void __launch_bounds__(1024) k_sum3(const double *x, long n, double *out)
+{
+    __shared__ double red[32];
+    double s = 0;
+    for (long t = threadIdx.x; t < n; t += blockDim.x) s += x[t];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+template <typename T>
+__global__ void k_tables3(Grid3D g, VX3<T> *vxt, VYZ3<T> *vyz)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < g.nvxp) {
+        VX3<T> c;
+        if (t < g.nvx) {
+            c.vx = T(g.vxmin + t * g.dvx);
+            c.nux = fabs(c.vx) * T(g.dt / g.dx);
+        } else {
+            c.vx = T(1e4);      // padding: zero state, vanishing equilibrium
+            c.nux = 0;
+        }
+        vxt[t] = c;
+    }
+    if (t < g.nvy * g.nvz) {
+        const int p2 = t % g.nvy, p3 = t / g.nvy;
+        VYZ3<T> c;
+        c.vy = T(g.vymin + p2 * g.dvy);
+        c.vz = T(g.vzmin + p3 * g.dvz);
+        c.nuy = fabs(c.vy) * T(g.dt / g.dy);
+        c.nuz = fabs(c.vz) * T(g.dt / g.dz);
+        vyz[t] = c;
+    }
+}
+
+inline unsigned nb3(long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename T>
+const VX3<T> *vx_table(const dvm_ctx *c) { return reinterpret_cast<const VX3<T> *>(c->vtab); }
+
+template <typename T>
+const VYZ3<T> *vyz_table(const dvm_ctx *c)
+{
+    return reinterpret_cast<const VYZ3<T> *>(reinterpret_cast<const char *>(c->vtab) + (size_t)c->nvxp * sizeof(VX3<T>));
+}
+
+template <typename T, bool MUSCL>
+cudaError_t launch_bulk3(dvm_ctx *c, const Bulk3Args<T> &a)
+{
+    const size_t smem = (size_t)kZc3 * (kCoef3 + 10) * 32 * kRows * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_bulk3<T, MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(nb3(c->nx, 32), nb3(c->ny, kRows), (unsigned)(a.nzc * a.S)), block(32, kRows);
+    k_bulk3<T, MUSCL><<<grid, block, smem, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
+Cv3Args cv3_args(dvm_ctx *c)
+{
+    Cv3Args cv;
+    cv.g = grid3d(c);
+    cv.G = c->geo3;
+    cv.master = c->master; cv.flags = c->flags3;
+    cv.spec_list = c->spec_list; cv.wall_list = c->wall_list; cv.wslot = c->wslot;
+    cv.counts = c->counts; cv.cap = c->list_cap; cv.S = c->S;
+    cv.gps = (c->ngrp + c->S - 1) / c->S;
+    cv.cvinfo = c->cvinfo;
+    cv.vxt = c->vtab;
+    cv.vyz = reinterpret_cast<const char *>(c->vtab) + (size_t)c->nvxp * 2 * c->elem;
+    cv.err = c->d_err;
+    return cv;
+}
+
+template <typename T>
+cudaError_t step3d_t(dvm_ctx *c)
+{
+    const Grid3D g = grid3d(c);
+    const BodyParams bp = body_params(c);
+    const bool body = c->body.shape != DVM_SHAPE_NONE;
+    T *fin = (T *)c->f[c->cur], *fout = (T *)c->f[1 - c->cur];
+    T *pin = (T *)c->part[c->cur], *pout = (T *)c->part[1 - c->cur];
+    cudaError_t e;
+    const Cv3Args cv = cv3_args(c);
+    const int cvgrid = 4 * 152;
+    if (body) {
+        if (c->need_fusion) {
+            k_fusion3<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, pin);
+            c->launches += 1;
+        }
+        k_wall3<T><<<cvgrid, 256, 0, c->stream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket, c->d_hist);
+        c->launches += 1;
+    }
+    Bulk3Args<T> a;
+    a.g = g; a.S = c->S; a.nzc = (c->nz + kZc3 - 1) / kZc3;
+    a.fin = fin; a.fout = fout; a.pin = pin; a.pout = pout;
+    a.flags = c->flags3; a.vxt = vx_table<T>(c); a.vyz = vyz_table<T>(c); a.err = c->d_err;
+    if ((e = timing_mark(c, 0)) != cudaSuccess) return e;
+    e = c->scheme == DVM_MUSCL ? launch_bulk3<T, true>(c, a) : launch_bulk3<T, false>(c, a);
+    if (e != cudaSuccess) return e;
+    if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
+    c->launches += 1;
+    if (body) {
+        k_special3<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, fout, pin, pout, c->wphi);
+        c->launches += 1;
+    }
+    c->cur = 1 - c->cur;
+    c->need_fusion = false;
+    c->steps_done++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t vtab3_bytes(const dvm_ctx *c) { return (size_t)c->nvxp * 2 * c->elem + (size_t)c->nvy * c->nvz * 4 * c->elem; }
+
+size_t cvinfo3_bytes() { return sizeof(CvInfo3); }
+
+cudaError_t members3d(dvm_ctx *c)
+{
+    k_members3<<<4 * 152, 256, 0, c->stream>>>(cv3_args(c), (CvInfo3 *)c->cvinfo);
+    return cudaGetLastError();
+}
+
+cudaError_t step3d(dvm_ctx *c) { return c->prec == DVM_FP32 ? step3d_t<float>(c) : step3d_t<double>(c); }
+
+cudaError_t tables3d(dvm_ctx *c)
+{
+    const Grid3D g = grid3d(c);
+    const int n = c->nvxp > c->nvy * c->nvz ? c->nvxp : c->nvy * c->nvz;
+    if (c->prec == DVM_FP32)
+        k_tables3<float><<<nb3(n, 256), 256, 0, c->stream>>>(g, (VX3<float> *)c->vtab, (VYZ3<float> *)vyz_table<float>(c));
+    else
+        k_tables3<double><<<nb3(n, 256), 256, 0, c->stream>>>(g, (VX3<double> *)c->vtab,
+                                                                (VYZ3<double> *)vyz_table<double>(c));
+    return cudaGetLastError();
+}
+
+cudaError_t partials_from_state3d(dvm_ctx *c)
+{
+    const Grid3D g = grid3d(c);
+    if (c->prec == DVM_FP32)
+        k_partials3<float><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, c->S, (const float *)c->f[c->cur],
+                                                                 (float *)c->part[c->cur], c->geo3.type, c->d_err);
+    else
+        k_partials3<double><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, c->S, (const double *)c->f[c->cur],
+                                                                  (double *)c->part[c->cur], c->geo3.type, c->d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t moments_out3d(dvm_ctx *c, double *d_out)
+{
+    const Grid3D g = grid3d(c);
+    if (c->prec == DVM_FP32)
+        k_moments_out3<float><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, (const float *)c->f[c->cur], d_out);
+    else
+        k_moments_out3<double><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, (const double *)c->f[c->cur], d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t init_maxwellian3d(dvm_ctx *c, const double *d_prim)
+{
+    const Grid3D g = grid3d(c);
+    dim3 grid((unsigned)c->nc, nb3(c->nv, 256));
+    if (c->prec == DVM_FP32)
+        k_init3<float><<<grid, 256, 0, c->stream>>>(g, d_prim, c->geo3.type, (float *)c->f[c->cur]);
+    else
+        k_init3<double><<<grid, 256, 0, c->stream>>>(g, d_prim, c->geo3.type, (double *)c->f[c->cur]);
+    return cudaGetLastError();
+}
+
+cudaError_t ghost3d(dvm_ctx *c, int side, const double *d_prim, int nside)
+{
+    const Grid3D g = grid3d(c);
+    const long n = (long)nside * c->nv;
+    if (c->prec == DVM_FP32)
+        k_ghost3<float><<<nb3(n, 256), 256, 0, c->stream>>>(g, d_prim, side, nside, (float *)c->f[0], (float *)c->f[1]);
+    else
+        k_ghost3<double><<<nb3(n, 256), 256, 0, c->stream>>>(g, d_prim, side, nside, (double *)c->f[0], (double *)c->f[1]);
+    return cudaGetLastError();
+}
+
+cudaError_t pack3d(dvm_ctx *c, const void *pub, void *dev)
+{
+    const Grid3D g = grid3d(c);
+    dim3 grid((unsigned)c->nc, nb3(c->nv, 256));
+    if (c->prec == DVM_FP32) k_pack3<float><<<grid, 256, 0, c->stream>>>(g, (const float *)pub, (float *)dev, 1);
+    else k_pack3<double><<<grid, 256, 0, c->stream>>>(g, (const double *)pub, (double *)dev, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t unpack3d(dvm_ctx *c, const void *dev, void *pub)
+{
+    const Grid3D g = grid3d(c);
+    dim3 grid((unsigned)c->nc, nb3(c->nv, 256));
+    if (c->prec == DVM_FP32) k_pack3<float><<<grid, 256, 0, c->stream>>>(g, (const float *)dev, (float *)pub, 0);
+    else k_pack3<double><<<grid, 256, 0, c->stream>>>(g, (const double *)dev, (double *)pub, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t zero_solid3d(dvm_ctx *c)
+{
+    const Grid3D g = grid3d(c);
+    dim3 grid((unsigned)c->nc, nb3(c->nvp, 256));
+    for (int b = 0; b < 2; ++b) {
+        if (c->prec == DVM_FP32) k_zero_solid3<float><<<grid, 256, 0, c->stream>>>(g, c->geo3.type, (float *)c->f[b]);
+        else k_zero_solid3<double><<<grid, 256, 0, c->stream>>>(g, c->geo3.type, (double *)c->f[b]);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t halo3d(dvm_ctx *c, int buf)
+{
+    const Grid3D g = grid3d(c);
+    const long per = 2L * ((long)c->ny * c->nz + (long)c->nx * c->nz + (long)c->nx * c->ny);
+    const long n = 2 * per * c->nvp;
+    if (c->prec == DVM_FP32) k_halo3<float><<<nb3(n, 256), 256, 0, c->stream>>>(g, (float *)c->f[buf]);
+    else k_halo3<double><<<nb3(n, 256), 256, 0, c->stream>>>(g, (double *)c->f[buf]);
+    return cudaGetLastError();
+}
+
+cudaError_t mass3d(dvm_ctx *c, double *d_scratch, double *d_out)
+{
+    const Grid3D g = grid3d(c);
+    if (c->prec == DVM_FP32)
+        k_mass_cells3<float><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, (const float *)c->f[c->cur], c->geo3.vol, d_scratch);
+    else
+        k_mass_cells3<double><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, (const double *)c->f[c->cur], c->geo3.vol, d_scratch);
+    k_sum3<<<1, 1024, 0, c->stream>>>(d_scratch, c->nc, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace dvm

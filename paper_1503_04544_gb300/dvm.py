@@ -84,6 +84,7 @@ SIGNATURES = {
                  C.POINTER(C.c_int)],
     "dvm_geometry2d": [_P, _PI8, _PI8, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PI32],
     "dvm_geometry2d_at": [_P, C.c_double, C.c_double],
+    "dvm_geometry3d": [_P, _PI8, _PI8, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PI32],
     "dvm_timing": [_P, C.c_int],
     "dvm_kernel_time": [_P, _PD, C.POINTER(C.c_longlong)],
     "dvm_launches": [_P, C.POINTER(C.c_longlong)],
@@ -255,6 +256,20 @@ class Solver:
         _check(load().dvm_geometry2d(
             self.h, _ptr(out["type"], _PI8), _ptr(out["cgas"], _PI8),
             *[_ptr(out[k]) for k in ("lx", "ly", "lw", "nwx", "nwy", "rwx", "rwy", "sbar")],
+            _ptr(out["master"], _PI32)))
+        return out
+
+    def geometry3d(self) -> dict:
+        nx, ny, nz = self.cfg["nx"], self.cfg["ny"], self.cfg["nz"]
+        nc = nx * ny * nz
+        out = dict(type=np.zeros(nc, np.int8), cgas=np.zeros(nc, np.int8),
+                   ax=np.zeros((nx + 1) * ny * nz), ay=np.zeros(nx * (ny + 1) * nz),
+                   az=np.zeros(nx * ny * (nz + 1)), master=np.zeros(nc, np.int32))
+        for k in ("sw", "nwx", "nwy", "nwz", "rwx", "rwy", "rwz", "vol"):
+            out[k] = np.zeros(nc)
+        _check(load().dvm_geometry3d(
+            self.h, _ptr(out["type"], _PI8), _ptr(out["cgas"], _PI8),
+            *[_ptr(out[k]) for k in ("ax", "ay", "az", "sw", "nwx", "nwy", "nwz", "rwx", "rwy", "rwz", "vol")],
             _ptr(out["master"], _PI32)))
         return out
 
