@@ -3,13 +3,15 @@
 
 Default workload: 2D fixed cylinder, 256x256 cells on [0,1]^2, cylinder
 r = 0.1, 32x32 velocities on [-8,8)^2, Mach-2 inflow, Kn 0.05, MUSCL-minmod,
-FP32 state.  One bench step is one time step of the whole method (wall
-density and stress, force/torque, fluxes, relaxation, cut-cell control
-volumes, moments).  Metric: (cell, velocity) pair updates per second over
-the non-solid cells.
+FP32 state.  ``--workload sphere``: 3D fixed sphere, 96^3 cells on [0,1]^3,
+r = 0.15, 20^3 velocities on [-5,5)^3, Mach-1.5 inflow, Kn 0.1, MUSCL-minmod.
+One bench step is one time step of the whole method (wall density and
+stress, force/torque, fluxes, relaxation, cut-cell control volumes,
+moments).  Metric: (cell, velocity) pair updates per second over the
+non-solid cells.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
-                  [--impl gb300|reference]
+                  [--workload cylinder|sphere|ellipse|bump] [--impl gb300|reference]
 
 For N > 1 each rank runs an independent replica (the path is not sharded
 here); value = pairs updated by all ranks / max-over-ranks time.
@@ -41,14 +43,26 @@ def workload(name: str):
         return W.rotating_ellipse(nx=512, nv=40)
     if name == "bump":
         return W.periodic_bump()
+    if name == "sphere":
+        return W.sphere_mach15(n=96, nv=20, scheme=1)
     raise SystemExit(f"unknown workload {name}")
 
 
+DEFAULT_STEPS = {"cylinder": 2000, "ellipse": 500, "bump": 2000, "sphere": 60}
+
+
+def _dims(cfg):
+    if cfg.get("dim", 2) == 3:
+        return [cfg["nx"], cfg["ny"], cfg["nz"]], [cfg["nvx"], cfg["nvy"], cfg["nvz"]]
+    return [cfg["nx"], cfg["ny"]], [cfg["nvx"], cfg["nvy"]]
+
+
 def config_dict(cfg, prec, nsolid_free, extra=None):
+    cells, vels = _dims(cfg)
     d = {
         "workload": cfg["name"],
-        "cells": [cfg["nx"], cfg["ny"]],
-        "velocities": [cfg["nvx"], cfg["nvy"]],
+        "cells": cells,
+        "velocities": vels,
         "scheme": "muscl-minmod" if cfg.get("scheme", 0) == 1 else "upwind",
         "precision": prec,
         "pairs_per_step": nsolid_free,
@@ -69,11 +83,11 @@ def read_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(kernel_src: str):
+def recorded_traffic(summary: str, kernel_src: str):
     """DRAM bytes per launch of the bulk kernel from the committed ncu summary,
     or None if the kernel source changed since the capture."""
     import hashlib
-    summ = os.path.join(ROOT, "profiles", "k_bulk_cylinder_fp32.md")
+    summ = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(summ):
         return None
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
@@ -130,14 +144,28 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_sample_cfg(cfg):
+    """The oracle's bounded sample: the 2D workloads as they are; the 3D
+    sphere on a 24^3 grid with the same velocity grid, physics and scheme
+    (one full step at 96^3 takes minutes on the host cores)."""
+    if cfg.get("dim", 2) == 3:
+        from paper_1503_04544_gb300 import workloads as W
+        return W.sphere_mach15(n=24, nv=cfg["nvx"], scheme=cfg.get("scheme", 1))
+    return cfg
+
+
 def cpu_baseline(cfg, budget_s: float = 20.0, max_steps: int = 4):
     """Time the FP64 oracle as it stands on the host cores (bounded sample)."""
     import numpy as np
     import oracle
+    cfg = cpu_sample_cfg(cfg)
     F = oracle.initial_state(cfg)
-    g = oracle.geometry2d(cfg)
-    nonsolid = int(np.sum(g["type"] != 2))
-    pairs = nonsolid * cfg["nvx"] * cfg["nvy"]
+    if cfg.get("dim", 2) == 3:
+        g = oracle.geometry3d(cfg)
+        pairs = int(np.sum(g["type"] != 2)) * cfg["nvx"] * cfg["nvy"] * cfg["nvz"]
+    else:
+        g = oracle.geometry2d(cfg)
+        pairs = int(np.sum(g["type"] != 2)) * cfg["nvx"] * cfg["nvy"]
     done = 0
     t0 = time.perf_counter()
     while done < max_steps:
@@ -172,13 +200,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--workload", default="cylinder")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS.get(args.workload, 2000)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -263,7 +293,10 @@ def main():
         peak, peak_kind = read_peaks()
         avg_bulk_s = bulk_ms / max(nb, 1) / 1e3
         achieved = bulk_pairs * bytes_per_pair / avg_bulk_s / 1e9
-        traffic = recorded_traffic(os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step2d.cu"))
+        dim3 = cfg.get("dim", 2) == 3
+        traffic = recorded_traffic(
+            f"k_bulk{'3' if dim3 else ''}_{args.workload}_{args.precision}.md",
+            os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step3d.cu" if dim3 else "dvm_step2d.cu"))
         line = {
             "metric": METRIC,
             "value": world * pairs_per_step * args.steps / (ms_max / 1e3),
@@ -283,7 +316,7 @@ def main():
                                    "cut_cell_cvs": counts["cvs"], "wall_cells": counts["walls"]}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_bulk (fused stream + relax + moments)",
+                         "kernel": ("k_bulk3" if dim3 else "k_bulk") + " (fused stream + relax + moments)",
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
                          "bytes_per_pair": bytes_per_pair,
                          "bulk_ms_per_launch": avg_bulk_s * 1e3,

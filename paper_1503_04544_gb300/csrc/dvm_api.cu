@@ -236,15 +236,31 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
         c->slab = (long)(c->nx + 4) * (c->ny + 4) * (c->nz + 4);
     }
     c->dev_elems = (size_t)c->ngrp * c->ncomp * c->slab * c->W;
-    {
+    if (dim == 2) {
         // velocity splits: enough blocks for a few waves on 152 SMs
-        long blocks = (long)((c->nx + 31) / 32) * ((c->ny + kRows - 1) / kRows);
-        if (dim == 3) blocks *= (c->nz + kZc3 - 1) / kZc3;
+        const long blocks = (long)((c->nx + 31) / 32) * ((c->ny + kRows - 1) / kRows);
         int S = (int)((1200 + blocks - 1) / blocks);
         if (S < 1) S = 1;
         if (S > 16) S = 16;
         if (S > c->ngrp) S = c->ngrp;
         c->S = S;
+    } else {
+        // one resident block per SM (tiles of 32 x 12 cells in FP32, 32 x 8 in
+        // FP64, columns of 4 cells): the smallest split count giving at least
+        // four waves on 152 SMs with a last wave at least 95% full, else the
+        // best-filled count up to 24
+        const long slots = 152;
+        const int rows = precision == DVM_FP32 ? 12 : 8;
+        const long blocks = (long)((c->nx + 31) / 32) * ((c->ny + rows - 1) / rows) * ((c->nz + 3) / 4);
+        int best = 1;
+        double best_eff = 0;
+        for (int S = 1; S <= 24 && S <= c->ngrp; ++S) {
+            const long nb = blocks * S, waves = (nb + slots - 1) / slots;
+            const double eff = (double)nb / ((double)slots * waves);
+            if (waves >= 4 && eff >= 0.95) { best = S; break; }
+            if (eff > best_eff + 1e-9) { best_eff = eff; best = S; }
+        }
+        c->S = best;
     }
     const int nmom = dim == 2 ? 4 : 5;
     if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
@@ -317,6 +333,8 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
         e = init_static_geometry2d(c);
         if (e == cudaSuccess) e = tables2d(c);
     } else {
+        int rc = make_tensor_maps3d(c);
+        if (rc != DVM_OK) { dvm_destroy(c); return rc; }
         e = init_static_geometry3d(c);
         if (e == cudaSuccess) e = tables3d(c);
     }

@@ -44,7 +44,6 @@ constexpr uint8_t kMaskShift = 4;    // bits 4..7: limiter allowed on faces x-, 
 // the limiter on the faces x-, x+, y-, y+, z-, z+
 constexpr int kMaskShift3 = 4;
 constexpr int kMaxMembers3 = 8;      // virtual cells per 3D control volume
-constexpr int kZc3 = 4;              // z-planes per thread of the 3D bulk kernel
 
 // device error flag slots
 enum { kErrNonphys = 0, kErrGeometry = 1, kErrCapacity = 2, kErrTimeout = 3, kErrCount = 4 };
@@ -118,7 +117,7 @@ struct BodyParams {
 }  // namespace dvm
 
 struct dvm_ctx {
-    CUtensorMap tmap[2];          // TMA descriptors of the two state buffers
+    CUtensorMap tmap[2];          // TMA descriptors of the two state buffers (2D or 3D view)
     int dim, nx, ny, nz;
     double xmin, xmax, ymin, ymax, zmin, zmax, dx, dy, dz;
     int nvx, nvy, nvz, nv;
@@ -220,6 +219,7 @@ cudaError_t unpack3d(dvm_ctx *c, const void *dev, void *pub);
 cudaError_t zero_solid3d(dvm_ctx *c);
 cudaError_t halo3d(dvm_ctx *c, int buf);
 size_t vtab3_bytes(const dvm_ctx *c);
+int make_tensor_maps3d(dvm_ctx *c);                // TMA descriptors of f[0], f[1] (3D)
 size_t cvinfo3_bytes();
 
 inline double *body_trig(dvm_ctx *c, int which)

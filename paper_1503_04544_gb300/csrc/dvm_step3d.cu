@@ -16,12 +16,12 @@
 // Kernels of one step: k_wall3 (FP64 wall density, force and torque; the
 // last block sums them in list order), k_bulk3 (every gas cell that is a
 // control volume on its own), k_special3 (cut and merged control volumes).
-// k_bulk3 assigns one thread to a column of kZc3 cells along z; a warp covers
-// 32 consecutive cells along x, so the velocity of a group (hence the upwind
+// k_bulk3 assigns one thread to a column of cells along z; a warp covers 32
+// consecutive cells along x, so the velocity of a group (hence the upwind
 // side along y and z) is uniform across the warp.  The velocity groups are
-// split over blockIdx.z; each thread walks its groups, reads its cells'
-// stencils, writes the new state and accumulates the moments of the new
-// state for the next step.
+// split over blockIdx.z; each block streams the planes of its column through
+// shared memory with TMA, writes the new state and accumulates the moments of
+// the new state for the next step.
 #include <cudaTypedefs.h>
 
 #include <cstdio>
@@ -63,16 +63,6 @@ __device__ __forceinline__ long pidx3(const Grid3D &g, int p, int pc)
 {
     const int grp = p / g.W;
     return ((long)grp * g.slab + pc) * g.W + (p - grp * g.W);
-}
-
-// Axis indices of padded velocity p.
-__device__ __forceinline__ void vel_axes(const Grid3D &g, int p, int &p1, int &p2, int &p3)
-{
-    const int grp = p / g.W, e = p - grp * g.W;
-    const int yz = grp / g.nxg;
-    p1 = (grp - yz * g.nxg) * g.W + e;
-    p3 = yz / g.nvy;
-    p2 = yz - p3 * g.nvy;
 }
 
 // Padded index of public velocity p = (p3 nvy + p2) nvx + p1.
@@ -163,183 +153,361 @@ template <typename T> struct Bulk3Args {
     int *err;
 };
 
-// Flux difference of one direction in units of the Courant number (Eq.
-// eq-schema3D on a full gas cell): a = F - F_up, plus the limited
-// reconstructions of the outgoing (weight wo) and incoming (wi) faces, each
-// weight 1/2 where the face stencil is all gas and 0 otherwise.
+constexpr int kZc3 = 4;                           // z-planes per block column
+constexpr int kRing3 = 8;                         // shared-memory planes in flight
+constexpr int kPlaneX = 32 + 4;                   // tile width plus a two-cell halo
+
+// Tile rows of the bulk kernel (one consumer warp each): 12 in FP32, so that
+// with the producer warp no SM sub-partition holds more than 4 warps and a
+// thread keeps 128 registers; 8 in FP64 (shared memory of the per-cell state).
+template <typename T> __host__ __device__ constexpr int rows3() { return sizeof(T) == 4 ? 12 : 8; }
+template <typename T> __host__ __device__ constexpr int plane_cells3() { return kPlaneX * (rows3<T>() + 4); }
+
+template <typename T>
+size_t bulk3_smem()
+{
+    return (size_t)kRing3 * plane_cells3<T>() * 16 + (size_t)kZc3 * (kCoef3 + 10) * 32 * rows3<T>() * sizeof(T) +
+           2 * kRing3 * sizeof(uint64_t);
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z, int w)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Flux difference along one axis in units of the Courant number on a full gas
+// cell (Eq. eq-schema3D), with the neighbours taken on the upwind side:
+// a = F - F_up plus the limited reconstructions of the outgoing and incoming
+// faces; ko, ki are (1 - nu)/2 where the face stencil is all gas, else 0.
 template <typename T, bool MUSCL>
-__device__ __forceinline__ T dflux(T f, T u1, T u2, T d1, T nu, T wo, T wi)
+__device__ __forceinline__ T dflux(T f, T u1, T u2, T d1, T ko, T ki)
 {
     const T a = f - u1;
     if (!MUSCL) return a;
-    return a + (T(1) - nu) * (wo * minmod3(d1 - f, a) - wi * minmod3(a, u1 - u2));
+    return fma(-ki, minmod3(a, u1 - u2), fma(ko, minmod3(d1 - f, a), a));
 }
 
+// Bulk update of every gas cell that is a control volume on its own.
+//
+// Block = a tile of 32 x R cells in (x, y) and a column of kZc3 cells in z
+// (blockIdx.z = split * nzc + column), R consumer warps (one per tile row)
+// and one producer warp.  For each velocity group of its split the producer
+// streams the kZc3 + 4 planes of the column (tile plus a two-cell halo, one
+// TMA load each) into a ring of kRing3 shared-memory stages, refilling a stage
+// once every consumer warp has released it.  The consumers march up the
+// column: x/y neighbours come from the plane's stage; along z the cell values,
+// their differences and the face value at z + 1/2 (the z - 1/2 face of the
+// next cell) roll through registers.  Every wait is bounded and records
+// kErrTimeout instead of blocking.  The neighbours of a group are taken on its
+// upwind side (uniform within a group along y and z, and along x except for
+// the group that contains v_x = 0).  Moments of the new state are summed per
+// cell in registers over 8 groups, then folded into compensated sums in
+// shared memory.
 template <typename T, bool MUSCL>
-__global__ void __launch_bounds__(32 * kRows, 2) k_bulk3(Bulk3Args<T> a)
+__global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
+    k_bulk3(Bulk3Args<T> a, const __grid_constant__ CUtensorMap tmap)
 {
-    constexpr int W = Vec<T>::W, ZC = kZc3, NT = 32 * kRows;
+    constexpr int W = Vec<T>::W, ZC = kZc3, R = rows3<T>(), NT = 32 * R, NP = ZC + 4;
+    constexpr int PC = plane_cells3<T>(), PB = PC * 16;
     using V = typename Vec<T>::type;
-    extern __shared__ __align__(16) unsigned char smem3[];
-    T *coef = reinterpret_cast<T *>(smem3);                  // [ZC][kCoef3][NT]
-    T *ksum = coef + ZC * kCoef3 * NT;                        // [ZC][5][2][NT]
+    extern __shared__ __align__(128) unsigned char sm3[];
+    V *ring = reinterpret_cast<V *>(sm3);
+    T *coef = reinterpret_cast<T *>(sm3 + kRing3 * PB);             // [ZC][kCoef3][NT]
+    T *ksum = coef + ZC * kCoef3 * NT;                               // [ZC][5][2][NT]
+    uint64_t *full = reinterpret_cast<uint64_t *>(ksum + ZC * 10 * NT);
+    uint64_t *empty = full + kRing3;
     const Grid3D &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int i = blockIdx.x * 32 + tx, j = blockIdx.y * kRows + ty;
+    const bool producer = ty == R;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * R;
+    const int i = i0 + tx, j = j0 + ty;
     const int zc = blockIdx.z % a.nzc, split = blockIdx.z / a.nzc;
-    const int k0 = zc * ZC;
+    const int z0 = zc * ZC;
     const long nc = (long)g.nx * g.ny * g.nz;
     const int gps = (g.ngrp + a.S - 1) / a.S;
     const int g0 = split * gps, g1 = min(g0 + gps, g.ngrp);
-    const int sy = g.nx + 4, sz = (g.nx + 4) * (g.ny + 4);
-    const bool inij = i < g.nx && j < g.ny;
+    const int ngr = max(g1 - g0, 0);
+    const int total = ngr * NP;
+    const bool inij = !producer && i < g.nx && j < g.ny;
+    const int sz = (g.nx + 4) * (g.ny + 4);
 
-    uint32_t plainm = 0, zerom = 0, mirm = 0, masks = 0;
-#pragma unroll
-    for (int z = 0; z < ZC; ++z) {
-        const int k = k0 + z;
-        const bool in = inij && k < g.nz;
-        const long cell = ((long)k * g.ny + j) * g.nx + i;
-        const uint16_t fl = in ? a.flags[cell] : 0;
-        T *cz = coef + z * kCoef3 * NT + tid;
-        if (fl & kPlain) {
-            plainm |= 1u << z;
-            T s[5];
-            gather_partials3(a.pin, a.S, nc, cell, s);
-            T rho, ux, uy, uz, tmp;
-            if (!primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp)) atomicExch(&a.err[kErrNonphys], 1);
-            cz[0] = rho * norm3(tmp);
-            cz[NT] = T(kLog2e) / (T(2) * tmp);
-            cz[2 * NT] = ux;
-            cz[3 * NT] = uy;
-            cz[4 * NT] = uz;
-            cz[5 * NT] = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+    if (tid == 0) {
+        for (int st = 0; st < kRing3; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], R);
         }
-        if (fl & kZero) zerom |= 1u << z;
-        masks |= (uint32_t)((fl >> kMaskShift3) & 0x3F) << (6 * z);
-        if (in && near_side3(g, i, j, k)) mirm |= 1u << z;
-#pragma unroll
-        for (int m = 0; m < 10; ++m) ksum[(z * 10 + m) * NT + tid] = T(0);
+        mbar_fence_init();
     }
-    const int pc0 = inij ? nbr3(g, i, j, k0) : 0;
+    // per-cell data of the column: flags, and for plain cells the
+    // equilibrium in the form log2 M(v) = c0 + vx (c1 - c2 vx) - c2 dyz(v)
+    uint32_t plainm = 0, zerom = 0, mirm = 0, masks = 0;   // masks: byte t = limiter mask of cell t
+    static_assert(ZC <= 4, "one mask byte per column cell");
+    if (!producer) {
+#pragma unroll
+        for (int t = 0; t < ZC; ++t) {
+            const int k = z0 + t;
+            const bool in = inij && k < g.nz;
+            const long cell = ((long)k * g.ny + j) * g.nx + i;
+            const uint16_t fl = in ? a.flags[cell] : 0;
+            T *cz = coef + t * kCoef3 * NT + tid;
+            if (fl & kPlain) {
+                plainm |= 1u << t;
+                T s[5];
+                gather_partials3(a.pin, a.S, nc, cell, s);
+                T rho, ux, uy, uz, tmp;
+                if (!primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp)) atomicExch(&a.err[kErrNonphys], 1);
+                const T c2 = T(kLog2e) / (T(2) * tmp);
+                cz[0] = log2(rho * norm3(tmp)) - c2 * ux * ux;
+                cz[NT] = T(2) * c2 * ux;
+                cz[2 * NT] = c2;
+                cz[3 * NT] = uy;
+                cz[4 * NT] = uz;
+                cz[5 * NT] = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+            }
+            if (fl & kZero) zerom |= 1u << t;
+            masks |= (uint32_t)((fl >> kMaskShift3) & 0x3F) << (8 * t);
+            if (in && near_side3(g, i, j, k)) mirm |= 1u << t;
+#pragma unroll
+            for (int m = 0; m < 10; ++m) ksum[(t * 10 + m) * NT + tid] = T(0);
+        }
+    }
+    __syncthreads();
+
+    if (producer) {
+        if (tx == 0) {
+            for (int s = 0; s < total; ++s) {
+                const int slot = s % kRing3;
+                if (s >= kRing3 && !mbar_wait(&empty[slot], (uint32_t)(((s / kRing3) - 1) & 1)))
+                    atomicExch(&a.err[kErrTimeout], 1);
+                mbar_expect_tx(&full[slot], PB);
+                const int gi = s / NP, o = s - gi * NP;
+                // plane z0 - 2 + o of the column, padded index z0 + o
+                tma_load_4d(ring + slot * PC, &tmap, &full[slot], i0 * W, j0, z0 + o, g0 + gi);
+            }
+            // every issued copy has landed before the block exits
+            for (int s = max(total - kRing3, 0); s < total; ++s)
+                mbar_wait(&full[s % kRing3], (uint32_t)((s / kRing3) & 1));
+        }
+        return;
+    }
+
+    const int c0 = (ty + 2) * kPlaneX + tx + 2;
+    const int pc0 = inij ? nbr3(g, i, j, z0) : 0;
+    auto wait_full = [&](int s) -> const V * {
+        const int slot = s % kRing3;
+        if (!mbar_wait(&full[slot], (uint32_t)((s / kRing3) & 1))) atomicExch(&a.err[kErrTimeout], 1);
+        return ring + slot * PC;
+    };
+    auto release = [&](int s) {
+        __syncwarp();
+        if (tx == 0) mbar_arrive(&empty[s % kRing3]);
+    };
 
     T q[ZC][5];
 #pragma unroll
-    for (int z = 0; z < ZC; ++z)
+    for (int t = 0; t < ZC; ++t)
 #pragma unroll
-        for (int m = 0; m < 5; ++m) q[z][m] = T(0);
+        for (int m = 0; m < 5; ++m) q[t][m] = T(0);
     int fold = 0;
-    for (int grp = g0; grp < g1; ++grp) {
+    V *const fout = reinterpret_cast<V *>(a.fout);
+    for (int gi = 0; gi < ngr; ++gi) {
+        const int grp = g0 + gi;
         const int yz = grp / g.nxg, xg = grp - yz * g.nxg;
         const VYZ3<T> cyz = a.vyz[yz];
-        T vx[W], nux[W];
+        T vx[W], nux[W], kx[W];
+        bool xpos = true, xneg = true;
 #pragma unroll
         for (int e = 0; e < W; ++e) {
             const VX3<T> cx = a.vxt[xg * W + e];
             vx[e] = cx.vx;
             nux[e] = cx.nux;
+            kx[e] = T(0.5) * (T(1) - cx.nux);
+            xpos = xpos && cx.vx >= T(0);
+            xneg = xneg && cx.vx <= T(0);
         }
-        const V *src = reinterpret_cast<const V *>(a.fin) + (long)grp * g.slab;
-        V *dst = reinterpret_cast<V *>(a.fout) + (long)grp * g.slab;
+        const bool xuni = xpos || xneg;
+        const int ox = xpos ? 1 : -1;
         const bool py = cyz.vy >= T(0), pz = cyz.vz >= T(0);
-        const int oy = py ? sy : -sy, oz = pz ? sz : -sz;
+        const int oy = py ? kPlaneX : -kPlaneX;
+        const T ky = T(0.5) * (T(1) - cyz.nuy), kz = T(0.5) * (T(1) - cyz.nuz);
+        const T nzs = pz ? cyz.nuz : -cyz.nuz;
+        const T vyz2 = cyz.vy * cyz.vy + cyz.vz * cyz.vz;
+        V *dst = fout + (long)grp * g.slab;
+        const int base = gi * NP;
+        // rolling window along z: f at z - 1, z, z + 1 and the differences
+        // d(z - 1/2) = f(z) - f(z - 1), d(z + 1/2)
+        T fm1[W], f0[W], fp1[W], dm[W], dp[W], phim[W];
+        {
+            T fm2[W];
+            sld<T>(wait_full(base) + c0, fm2);
+            sld<T>(wait_full(base + 1) + c0, fm1);
+            sld<T>(wait_full(base + 2) + c0, f0);
+            sld<T>(wait_full(base + 3) + c0, fp1);
+            release(base);
+            release(base + 1);
+            // face value at z0 - 1/2
+            const T kw = (masks & 16u) ? kz : T(0);
 #pragma unroll
-        for (int z = 0; z < ZC; ++z) {
-            const bool pl = (plainm >> z) & 1u;
-            if (!pl && !((zerom >> z) & 1u)) continue;
-            const int pc = pc0 + z * sz;
-            T out[W];
-            if (pl) {
-                const uint32_t mk = masks >> (6 * z);
-                const T wxm = (mk & 1u) ? T(0.5) : T(0), wxp = (mk & 2u) ? T(0.5) : T(0);
-                const T wym = (mk & 4u) ? T(0.5) : T(0), wyp = (mk & 8u) ? T(0.5) : T(0);
-                const T wzm = (mk & 16u) ? T(0.5) : T(0), wzp = (mk & 32u) ? T(0.5) : T(0);
-                const T *cz = coef + z * kCoef3 * NT + tid;
-                const T A = cz[0], c2 = cz[NT], ux = cz[2 * NT], uy = cz[3 * NT], uz = cz[4 * NT], r = cz[5 * NT];
-                const T dy = cyz.vy - uy, dz = cyz.vz - uz;
-                const T dyz = dy * dy + dz * dz;
-                T f[W], xm1[W], xp1[W], ym1[W], zm1[W];
-                T xm2[W], xp2[W], ym2[W], yp1[W], zm2[W], zp1[W];
-                vld<T>(src + pc, f);
-                vld<T>(src + pc - 1, xm1);
-                vld<T>(src + pc + 1, xp1);
-                vld<T>(src + pc - oy, ym1);
-                vld<T>(src + pc - oz, zm1);
-                if (MUSCL) {
-                    vld<T>(src + pc - 2, xm2);
-                    vld<T>(src + pc + 2, xp2);
-                    vld<T>(src + pc - 2 * oy, ym2);
-                    vld<T>(src + pc + oy, yp1);
-                    vld<T>(src + pc - 2 * oz, zm2);
-                    vld<T>(src + pc + oz, zp1);
-                }
-                const T wyo = py ? wyp : wym, wyi = py ? wym : wyp;
-                const T wzo = pz ? wzp : wzm, wzi = pz ? wzm : wzp;
+            for (int e = 0; e < W; ++e) {
+                dm[e] = f0[e] - fm1[e];
+                dp[e] = fp1[e] - f0[e];
+            }
+            if (!MUSCL) {
 #pragma unroll
-                for (int e = 0; e < W; ++e) {
-                    const bool px = vx[e] >= T(0);
-                    const T u1 = px ? xm1[e] : xp1[e];
-                    const T d1 = px ? xp1[e] : xm1[e];
-                    const T u2 = MUSCL ? (px ? xm2[e] : xp2[e]) : T(0);
-                    const T dfx = dflux<T, MUSCL>(f[e], u1, u2, d1, nux[e], px ? wxp : wxm, px ? wxm : wxp);
-                    const T dfy = dflux<T, MUSCL>(f[e], ym1[e], MUSCL ? ym2[e] : T(0), MUSCL ? yp1[e] : T(0),
-                                                  cyz.nuy, wyo, wyi);
-                    const T dfz = dflux<T, MUSCL>(f[e], zm1[e], MUSCL ? zm2[e] : T(0), MUSCL ? zp1[e] : T(0),
-                                                  cyz.nuz, wzo, wzi);
-                    const T d = vx[e] - ux;
-                    const T feq = A * dexp2(-(d * d + dyz) * c2);
-                    out[e] = f[e] - nux[e] * dfx - cyz.nuy * dfy - cyz.nuz * dfz + r * (feq - f[e]);
-                }
-                T s = 0, sx = 0, sxx = 0;
+                for (int e = 0; e < W; ++e) phim[e] = pz ? fm1[e] : f0[e];
+            } else if (pz) {
 #pragma unroll
-                for (int e = 0; e < W; ++e) {
-                    s += out[e];
-                    sx += vx[e] * out[e];
-                    sxx += vx[e] * vx[e] * out[e];
-                }
-                q[z][0] += s;
-                q[z][1] += sx;
-                q[z][2] += cyz.vy * s;
-                q[z][3] += cyz.vz * s;
-                q[z][4] += T(0.5) * (sxx + (cyz.vy * cyz.vy + cyz.vz * cyz.vz) * s);
+                for (int e = 0; e < W; ++e) phim[e] = fma(kw, minmod3(dm[e], fm1[e] - fm2[e]), fm1[e]);
             } else {
 #pragma unroll
-                for (int e = 0; e < W; ++e) out[e] = T(0);
-            }
-            vst<T>(dst + pc, out);
-            if ((mirm >> z) & 1u) {
-                int mir[6];
-                mirrors3(g, i, j, k0 + z, mir);
-#pragma unroll
-                for (int t = 0; t < 6; ++t)
-                    if (mir[t] >= 0) vst<T>(dst + mir[t], out);
+                for (int e = 0; e < W; ++e) phim[e] = fma(-kw, minmod3(dp[e], dm[e]), f0[e]);
             }
         }
+#pragma unroll
+        for (int t = 0; t < ZC; ++t) {
+            // the plane of z was waited for as the z + 2 centre two steps ago
+            const V *pl = ring + ((base + t + 2) % kRing3) * PC;
+            T fp2[W];
+            sld<T>(wait_full(base + t + 4) + c0, fp2);
+            const uint32_t mk = (masks >> (8 * t)) & 0x3Fu;
+            // face value at z + 1/2, the z - 1/2 face of the next cell
+            T phip[W], dpp[W];
+#pragma unroll
+            for (int e = 0; e < W; ++e) dpp[e] = fp2[e] - fp1[e];
+            if (!MUSCL) {
+#pragma unroll
+                for (int e = 0; e < W; ++e) phip[e] = pz ? f0[e] : fp1[e];
+            } else {
+                const T kw = (mk & 32u) ? kz : T(0);
+                if (pz) {
+#pragma unroll
+                    for (int e = 0; e < W; ++e) phip[e] = fma(kw, minmod3(dp[e], dm[e]), f0[e]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < W; ++e) phip[e] = fma(-kw, minmod3(dpp[e], dp[e]), fp1[e]);
+                }
+            }
+            const bool pl_t = (plainm >> t) & 1u;
+            if (pl_t || ((zerom >> t) & 1u)) {
+                T out[W];
+                if (pl_t) {
+                    const T *cz = coef + t * kCoef3 * NT + tid;
+                    const T c0c = cz[0], c1 = cz[NT], c2 = cz[2 * NT], uy = cz[3 * NT], uz = cz[4 * NT], r = cz[5 * NT];
+                    const T dyv = cyz.vy - uy, dzv = cyz.vz - uz;
+                    const T cg = c0c - c2 * (dyv * dyv + dzv * dzv);
+                    const T omr = T(1) - r;
+                    const T kyo = (mk & (py ? 8u : 4u)) ? ky : T(0), kyi = (mk & (py ? 4u : 8u)) ? ky : T(0);
+                    T yu1[W], yu2[W], yd1[W];
+                    sld<T>(pl + c0 - oy, yu1);
+                    if (MUSCL) {
+                        sld<T>(pl + c0 - 2 * oy, yu2);
+                        sld<T>(pl + c0 + oy, yd1);
+                    }
+                    T dfx[W];
+                    if (xuni) {
+                        const T xo = (mk & (xpos ? 2u : 1u)) ? T(1) : T(0), xi = (mk & (xpos ? 1u : 2u)) ? T(1) : T(0);
+                        T xu1[W], xu2[W], xd1[W];
+                        sld<T>(pl + c0 - ox, xu1);
+                        if (MUSCL) {
+                            sld<T>(pl + c0 - 2 * ox, xu2);
+                            sld<T>(pl + c0 + ox, xd1);
+                        }
+#pragma unroll
+                        for (int e = 0; e < W; ++e)
+                            dfx[e] = dflux<T, MUSCL>(f0[e], xu1[e], MUSCL ? xu2[e] : T(0), MUSCL ? xd1[e] : T(0),
+                                                     xo * kx[e], xi * kx[e]);
+                    } else {
+                        T xm1[W], xp1[W], xm2[W], xp2[W];
+                        sld<T>(pl + c0 - 1, xm1);
+                        sld<T>(pl + c0 + 1, xp1);
+                        if (MUSCL) {
+                            sld<T>(pl + c0 - 2, xm2);
+                            sld<T>(pl + c0 + 2, xp2);
+                        }
+                        const T kxm = (mk & 1u) ? T(1) : T(0), kxp = (mk & 2u) ? T(1) : T(0);
+#pragma unroll
+                        for (int e = 0; e < W; ++e) {
+                            const bool px = vx[e] >= T(0);
+                            dfx[e] = dflux<T, MUSCL>(f0[e], px ? xm1[e] : xp1[e], MUSCL ? (px ? xm2[e] : xp2[e]) : T(0),
+                                                     px ? xp1[e] : xm1[e], kx[e] * (px ? kxp : kxm),
+                                                     kx[e] * (px ? kxm : kxp));
+                        }
+                    }
+                    T s = 0, sx = 0, sxx = 0;
+#pragma unroll
+                    for (int e = 0; e < W; ++e) {
+                        const T dfy = dflux<T, MUSCL>(f0[e], yu1[e], MUSCL ? yu2[e] : T(0), MUSCL ? yd1[e] : T(0), kyo, kyi);
+                        const T feq = dexp2(fma(fma(-c2, vx[e], c1), vx[e], cg));
+                        T o = fma(r, feq, omr * f0[e]);
+                        o = fma(-nux[e], dfx[e], o);
+                        o = fma(-cyz.nuy, dfy, o);
+                        o = fma(-nzs, phip[e] - phim[e], o);     // nzs carries the sign of v_z
+                        out[e] = o;
+                        s += o;
+                        sx = fma(vx[e], o, sx);
+                        sxx = fma(vx[e] * vx[e], o, sxx);
+                    }
+                    q[t][0] += s;
+                    q[t][1] += sx;
+                    q[t][2] = fma(cyz.vy, s, q[t][2]);
+                    q[t][3] = fma(cyz.vz, s, q[t][3]);
+                    q[t][4] += T(0.5) * fma(vyz2, s, sxx);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < W; ++e) out[e] = T(0);
+                }
+                const int pc = pc0 + t * sz;
+                vst<T>(dst + pc, out);
+                if ((mirm >> t) & 1u) {
+                    int mir[6];
+                    mirrors3(g, i, j, z0 + t, mir);
+#pragma unroll
+                    for (int u = 0; u < 6; ++u)
+                        if (mir[u] >= 0) vst<T>(dst + mir[u], out);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                phim[e] = phip[e];
+                dm[e] = dp[e];
+                dp[e] = dpp[e];
+                fm1[e] = f0[e];
+                f0[e] = fp1[e];
+                fp1[e] = fp2[e];
+            }
+            release(base + t + 2);
+        }
+        release(base + ZC + 2);
+        release(base + ZC + 3);
         // fold the plain sums of 8 groups into the compensated sums
-        if (++fold == 8 || grp + 1 == g1) {
+        if (++fold == 8 || gi + 1 == ngr) {
             fold = 0;
 #pragma unroll
-            for (int z = 0; z < ZC; ++z)
+            for (int t = 0; t < ZC; ++t)
 #pragma unroll
                 for (int m = 0; m < 5; ++m) {
-                    T *ks = ksum + (z * 10 + 2 * m) * NT + tid;
+                    T *ks = ksum + (t * 10 + 2 * m) * NT + tid;
                     Acc<T> acc;
                     acc.s = ks[0];
                     acc.c = ks[NT];
-                    acc.add(q[z][m]);
+                    acc.add(q[t][m]);
                     ks[0] = acc.s;
                     ks[NT] = acc.c;
-                    q[z][m] = T(0);
+                    q[t][m] = T(0);
                 }
         }
     }
 #pragma unroll
-    for (int z = 0; z < ZC; ++z) {
-        if (!(((plainm | zerom) >> z) & 1u)) continue;
-        const long cell = ((long)(k0 + z) * g.ny + j) * g.nx + i;
+    for (int t = 0; t < ZC; ++t) {
+        if (!(((plainm | zerom) >> t) & 1u)) continue;
+        const long cell = ((long)(z0 + t) * g.ny + j) * g.nx + i;
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            const T *ks = ksum + (z * 10 + 2 * m) * NT + tid;
+            const T *ks = ksum + (t * 10 + 2 * m) * NT + tid;
             a.pout[((long)split * 5 + m) * nc + cell] = ks[0] - ks[NT];
         }
     }
@@ -1014,15 +1182,15 @@ const VYZ3<T> *vyz_table(const dvm_ctx *c)
 template <typename T, bool MUSCL>
 cudaError_t launch_bulk3(dvm_ctx *c, const Bulk3Args<T> &a)
 {
-    const size_t smem = (size_t)kZc3 * (kCoef3 + 10) * 32 * kRows * sizeof(T);
+    const size_t smem = bulk3_smem<T>();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_bulk3<T, MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(nb3(c->nx, 32), nb3(c->ny, kRows), (unsigned)(a.nzc * a.S)), block(32, kRows);
-    k_bulk3<T, MUSCL><<<grid, block, smem, c->stream>>>(a);
+    dim3 grid(nb3(c->nx, 32), nb3(c->ny, rows3<T>()), (unsigned)(a.nzc * a.S)), block(32, rows3<T>() + 1);
+    k_bulk3<T, MUSCL><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
     return cudaGetLastError();
 }
 
@@ -1081,6 +1249,43 @@ cudaError_t step3d_t(dvm_ctx *c)
 }
 
 }  // namespace
+
+// TMA descriptors of the two state buffers: a 4D view (x: padded cells of a
+// row times the W velocities of a group, y: padded rows, z: padded planes,
+// w: velocity group) with the bulk kernel's plane box (tile plus halo).
+int make_tensor_maps3d(dvm_ctx *c)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult qr;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+        if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return DVM_ERR_CUDA;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const int W = c->W;
+    const cuuint64_t dims[4] = {(cuuint64_t)(c->nx + 4) * W, (cuuint64_t)(c->ny + 4), (cuuint64_t)(c->nz + 4),
+                                (cuuint64_t)c->ngrp};
+    const cuuint64_t row = (cuuint64_t)(c->nx + 4) * W * c->elem;
+    const cuuint64_t strides[3] = {row, row * (c->ny + 4), (cuuint64_t)c->slab * W * c->elem};
+    const cuuint32_t box[4] = {(cuuint32_t)kPlaneX * W,
+                               (cuuint32_t)(c->prec == DVM_FP32 ? rows3<float>() : rows3<double>()) + 4, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = c->prec == DVM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = encode(&c->tmap[b], dt, 4, c->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled (3D) failed (" + std::to_string((int)r) + ")");
+            return DVM_ERR_CUDA;
+        }
+    }
+    return DVM_OK;
+}
 
 size_t vtab3_bytes(const dvm_ctx *c) { return (size_t)c->nvxp * 2 * c->elem + (size_t)c->nvy * c->nvz * 4 * c->elem; }
 
