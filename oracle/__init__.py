@@ -99,6 +99,8 @@ def _load():
             lib.orc_moments.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD]
             lib.orc_run2d.argtypes = [P, _PD, C.c_int, C.POINTER(_Hist), _PD, _PD]
             lib.orc_mass2d.argtypes = [P, _PD]; lib.orc_mass2d.restype = C.c_double
+            lib.orc_adjoint2d.argtypes = [P, _PD, C.c_int, _PD, _PD, _PD, _PD, _PD, _PD, _PD]
+            lib.orc_init_maxwellian_vjp.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD]
             lib.orc_geometry3d.argtypes = [P, C.POINTER(_Geo3d)]
             lib.orc_masters3d.argtypes = [P, C.POINTER(_Geo3d), _PI32]
             lib.orc_run3d.argtypes = [P, _PD, C.c_int, C.POINTER(_Hist)]
@@ -287,3 +289,37 @@ def run3d(cfg: dict, F: np.ndarray, nsteps: int) -> dict:
 
 def mass3d(cfg: dict, F: np.ndarray) -> float:
     return _load().orc_mass3d(_CfgHolder(cfg).ref, _ptr(np.ascontiguousarray(F)))
+
+
+def adjoint2d(cfg: dict, F0: np.ndarray, nsteps: int) -> dict:
+    """Drag J = F_x after ``nsteps`` steps and its discrete adjoint: dJ/dF0,
+    dJ/dT_w per sector (or the uniform T_w) and dJ/d(rho, ux, uy, uz, T) of
+    every Maxwellian side cell."""
+    lib = _load()
+    F0 = np.ascontiguousarray(F0, dtype=np.float64)
+    lam0 = np.zeros_like(F0)
+    ntw = max(int(cfg.get("nseg", 0)), 1)
+    gTw = np.zeros(ntw)
+    nside = [cfg["ny"], cfg["ny"], cfg["nx"], cfg["nx"]]
+    gbc = [np.zeros(5 * n) for n in nside]
+    J = np.zeros(1)
+    rc = lib.orc_adjoint2d(_CfgHolder(cfg).ref, _ptr(F0), int(nsteps), _ptr(J), _ptr(lam0), _ptr(gTw),
+                           *[_ptr(g) for g in gbc])
+    return dict(status=rc, J=float(J[0]), lam0=lam0, gTw=gTw, gbc=[g.reshape(-1, 5) for g in gbc])
+
+
+def init_maxwellian_vjp(cfg: dict, lam: np.ndarray) -> np.ndarray:
+    """d<lam, F0>/d(rho, ux, uy, uz, T) per cell for the Maxwellian initial
+    state of ``cfg['init']`` (solid cells have rho = 0 and give zeros)."""
+    lib = _load()
+    nc = ncells(cfg)
+    ini = cfg["init"]
+    rho = np.array(np.broadcast_to(np.asarray(ini["rho"], np.float64), (nc,)))
+    if cfg.get("shape", 0) != 0:
+        rho[geometry2d(cfg)["type"] == SOLID] = 0.0
+    comps = [np.ascontiguousarray(np.broadcast_to(np.asarray(ini.get(k, 0.0), np.float64), (nc,)))
+             for k in ("ux", "uy", "T")]
+    g = np.zeros((nc, 5))
+    lib.orc_init_maxwellian_vjp(_CfgHolder(cfg).ref, _ptr(rho), *[_ptr(a) for a in comps],
+                                _ptr(np.ascontiguousarray(lam, dtype=np.float64)), _ptr(g))
+    return g

@@ -1134,3 +1134,454 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
     for (int s = 0; s < 6; ++s) free(X.ghost[s]);
     return err;
 }
+
+/* ================================================================ 2D adjoint
+ * Discrete adjoint (reverse-mode derivative) of the fixed-body 2D step, for
+ * the drag J = F_x(F^N) of the state after N steps (Eqs. StressTensorDD,
+ * eq-force on the fused state, as the step itself evaluates it).  The step is
+ * the composition  F^n -> fusion (Eq. FusionDD) -> moments, wall density,
+ * fluxes, explicit update with relaxation (Eqs. BGKDD, BoundaryDDv, FluxDD,
+ * ExSchemeDD) -> distribution (Eq. UpdateDD); its transpose Jacobian is
+ * applied in the reverse order.  The limiter is piecewise linear: its
+ * derivative is the one of the branch the forward step takes (on a tie the
+ * branch the forward minmod returns).  Written as plain loops over cells,
+ * components and velocities, in the order of the forward code above. */
+
+typedef struct { long cell; int side, q; } orc_loc;
+
+/* Source of the value fval2d returns for cell (i, j): an interior cell, or a
+ * ghost (Maxwellian side, index along the side). */
+static orc_loc loc2d(const orc_ctx2d *x, int i, int j)
+{
+    const orc_cfg *c = x->c;
+    orc_loc L = {-1, -1, -1};
+    if (i < 0) {
+        if (c->bc[0] == ORC_BC_PERIODIC) i = wrap(i, x->nx);
+        else if (c->bc[0] == ORC_BC_MAXWELLIAN) { L.side = 0; L.q = j; return L; }
+        else i = 0;
+    } else if (i >= x->nx) {
+        if (c->bc[1] == ORC_BC_PERIODIC) i = wrap(i, x->nx);
+        else if (c->bc[1] == ORC_BC_MAXWELLIAN) { L.side = 1; L.q = j; return L; }
+        else i = x->nx - 1;
+    }
+    if (j < 0) {
+        if (c->bc[2] == ORC_BC_PERIODIC) j = wrap(j, x->ny);
+        else if (c->bc[2] == ORC_BC_MAXWELLIAN) { L.side = 2; L.q = i; return L; }
+        else j = 0;
+    } else if (j >= x->ny) {
+        if (c->bc[3] == ORC_BC_PERIODIC) j = wrap(j, x->ny);
+        else if (c->bc[3] == ORC_BC_MAXWELLIAN) { L.side = 3; L.q = i; return L; }
+        else j = x->ny - 1;
+    }
+    L.cell = (long)j * x->nx + i;
+    return L;
+}
+
+/* minmod with the derivative of the branch taken: d/da, d/db in {0, 1}. */
+static double minmod_d(double a, double b, double *da, double *db)
+{
+    *da = *db = 0.0;
+    if (a > 0 && b > 0) { if (a < b) { *da = 1.0; return a; } *db = 1.0; return b; }
+    if (a < 0 && b < 0) { if (a > b) { *da = 1.0; return a; } *db = 1.0; return b; }
+    return 0.0;
+}
+
+/* Derivatives of face_flux with respect to fAA, fA, fB, fBB. */
+static void face_flux_d(double L, double v, double nu, double fAA, double fA, double fB,
+                        double fBB, int muscl, double d[4])
+{
+    d[0] = d[1] = d[2] = d[3] = 0.0;
+    if (!muscl) { d[1] = L * fmax(v, 0.0); d[2] = L * fmin(v, 0.0); return; }
+    const double k = 0.5 * (1.0 - nu);
+    double da, db;
+    if (v > 0) {            /* fA + k mm(fB - fA, fA - fAA) */
+        minmod_d(fB - fA, fA - fAA, &da, &db);
+        d[1] = L * v * (1.0 + k * (db - da));
+        d[2] = L * v * (k * da);
+        d[0] = L * v * (-k * db);
+    } else if (v < 0) {     /* fB - k mm(fBB - fB, fB - fA) */
+        minmod_d(fBB - fB, fB - fA, &da, &db);
+        d[2] = L * v * (1.0 - k * (db - da));
+        d[3] = L * v * (-k * da);
+        d[1] = L * v * (k * db);
+    }
+}
+
+/* Sensitivities of the 2D Maxwellian M[rho, u, T](v) and of T/2 M. */
+static void maxw2d_d(double rho, double ux, double uy, double T, double vx, double vy,
+                     double *m, double dm[4], double dg[4])
+{
+    const double ax = vx - ux, ay = vy - uy;
+    *m = maxw2d(rho, ux, uy, T, vx, vy);
+    dm[0] = *m / rho;
+    dm[1] = *m * ax / T;
+    dm[2] = *m * ay / T;
+    dm[3] = *m * ((ax * ax + ay * ay) / (2.0 * T * T) - 1.0 / T);
+    for (int q = 0; q < 3; ++q) dg[q] = T / 2.0 * dm[q];
+    dg[3] = *m / 2.0 + T / 2.0 * dm[3];
+}
+
+typedef struct {
+    long nc;
+    int nv, ncv;
+    int32_t *master, *mstart, *mlist;
+    double *Sn;
+} orc_cvs;
+
+/* Fusion (Eq. FusionDD): Ft = F with every merged control volume replaced by
+ * its area-weighted average. */
+static void fuse2d(const orc_ctx2d *x, const orc_cvs *V, const double *F, double *Ft)
+{
+    const int nv = x->nv;
+    memcpy(Ft, F, sizeof(double) * V->nc * 2 * nv);
+    for (long m = 0; m < V->nc; ++m) {
+        const int nm = V->mstart[m + 1] - V->mstart[m];
+        if (nm <= 1) continue;
+        for (int comp = 0; comp < 2; ++comp)
+            for (int p = 0; p < nv; ++p) {
+                double s = 0;
+                for (int q = V->mstart[m]; q < V->mstart[m + 1]; ++q) {
+                    long kk = V->mlist[q];
+                    s += x->g->sbar[kk] * F[(kk * 2 + comp) * nv + p];
+                }
+                const double fcv = s / V->Sn[m];
+                for (int q = V->mstart[m]; q < V->mstart[m + 1]; ++q)
+                    Ft[((long)V->mlist[q] * 2 + comp) * nv + p] = fcv;
+            }
+    }
+}
+
+/* Transpose of the fusion: lam_k = (sbar_k / S) sum_{j in CV} nu_j. */
+static void fuse2d_T(const orc_ctx2d *x, const orc_cvs *V, const double *nu, double *lam)
+{
+    const int nv = x->nv;
+    memcpy(lam, nu, sizeof(double) * V->nc * 2 * nv);
+    for (long m = 0; m < V->nc; ++m) {
+        const int nm = V->mstart[m + 1] - V->mstart[m];
+        if (nm <= 1) continue;
+        for (int comp = 0; comp < 2; ++comp)
+            for (int p = 0; p < nv; ++p) {
+                double s = 0;
+                for (int q = V->mstart[m]; q < V->mstart[m + 1]; ++q)
+                    s += nu[((long)V->mlist[q] * 2 + comp) * nv + p];
+                for (int q = V->mstart[m]; q < V->mstart[m + 1]; ++q) {
+                    long kk = V->mlist[q];
+                    lam[(kk * 2 + comp) * nv + p] = x->g->sbar[kk] / V->Sn[m] * s;
+                }
+            }
+    }
+}
+
+/* Wall quantities of wall cell k for the state Ft: u_w, T_w, the incoming
+ * normalisation D = sum_{c<0} c M1 dv and phi (Eq. BoundaryDDv). */
+typedef struct { double uwx, uwy, Tw, D, phi, rx, ry; int sector; } orc_wall;
+
+static orc_wall wall2d(const orc_ctx2d *x, long k, const double *Ft)
+{
+    const orc_cfg *c = x->c;
+    const orc_geo2d *g = x->g;
+    orc_wall w;
+    w.rx = g->rwx[k] - c->cx; w.ry = g->rwy[k] - c->cy;
+    w.uwx = c->vbx - w.ry * c->omega; w.uwy = c->vby + w.rx * c->omega;
+    w.sector = c->nseg > 0 ? wall_sector(c, w.rx, w.ry) : 0;
+    w.Tw = c->nseg > 0 ? c->Tw_seg[w.sector] : c->Tw;
+    const double dv = x->dvx * x->dvy;
+    double num = 0, den = 0;
+    for (int p2 = 0; p2 < x->nv2; ++p2)
+        for (int p1 = 0; p1 < x->nv1; ++p1) {
+            const int p = p2 * x->nv1 + p1;
+            const double vx = c->vxmin + p1 * x->dvx, vy = c->vymin + p2 * x->dvy;
+            const double cp = (vx - w.uwx) * g->nwx[k] + (vy - w.uwy) * g->nwy[k];
+            if (cp > 0) num += cp * Ft[k * 2 * x->nv + p] * dv;
+            else if (cp < 0) den += cp * maxw2d(1.0, w.uwx, w.uwy, w.Tw, vx, vy) * dv;
+        }
+    w.D = den;
+    w.phi = -num / den;
+    return w;
+}
+
+/* dM1/dTw for M1 = M[1, u_w, T_w]. */
+static double dM1_dTw(double m1, double ax, double ay, double Tw)
+{
+    return m1 * ((ax * ax + ay * ay) / (2.0 * Tw * Tw) - 1.0 / Tw);
+}
+
+int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *Jout, double *lam0,
+                  double *gTw, double *gbc0, double *gbc1, double *gbc2, double *gbc3)
+{
+    if (c->dim != 2 || c->movable || c->shape == ORC_SHAPE_NONE || nsteps < 0) return ORC_ERR_ARG;
+    orc_ctx2d X;
+    X.c = c; X.nx = c->nx; X.ny = c->ny; X.nv1 = c->nvx; X.nv2 = c->nvy;
+    X.nv = X.nv1 * X.nv2;
+    X.dx = (c->xmax - c->xmin) / c->nx; X.dy = (c->ymax - c->ymin) / c->ny;
+    X.dvx = (c->vxmax - c->vxmin) / c->nvx; X.dvy = (c->vymax - c->vymin) / c->nvy;
+    X.dt = orc_dt(c);
+    const int nx = X.nx, ny = X.ny, nv = X.nv;
+    const long nc = (long)nx * ny, ns = nc * 2 * nv;
+    const double dt = X.dt, dv = X.dvx * X.dvy, tau0 = orc_tau0(c);
+    make_ghosts2d(&X);
+    orc_geo2d geo;
+    alloc_geo2d(&geo, nx, ny);
+    int err = orc_geometry2d(c, cos(c->theta), sin(c->theta), &geo);
+    X.g = &geo;
+    orc_cvs V;
+    V.nc = nc; V.nv = nv;
+    V.master = malloc(sizeof(int32_t) * nc);
+    V.mstart = malloc(sizeof(int32_t) * (nc + 1));
+    V.mlist = malloc(sizeof(int32_t) * nc);
+    V.Sn = calloc(nc, sizeof(double));
+    int32_t *cnt = calloc(nc, sizeof(int32_t));
+    if (!err) err = orc_masters2d(c, &geo, &geo, V.master);
+    /* forward states F^0 .. F^N */
+    double *Fs = malloc(sizeof(double) * ns * (size_t)(nsteps + 1));
+    double *Ft = malloc(sizeof(double) * ns), *nu = calloc(ns, sizeof(double));
+    double *lam = malloc(sizeof(double) * ns), *mu = malloc(sizeof(double) * ns);
+    double *gg[4] = {NULL, NULL, NULL, NULL};        /* sensitivities to ghost values */
+    double *gbc[4] = {gbc0, gbc1, gbc2, gbc3};
+    const int nside[4] = {ny, ny, nx, nx};
+    for (int s = 0; s < 4; ++s) {
+        if (X.ghost[s]) gg[s] = calloc((size_t)nside[s] * 2 * nv, sizeof(double));
+        if (gbc[s]) memset(gbc[s], 0, sizeof(double) * 5 * nside[s]);
+    }
+    const int ntw = c->nseg > 0 ? c->nseg : 1;
+    memset(gTw, 0, sizeof(double) * ntw);
+    if (err) goto done;
+    for (long k = 0; k < nc; ++k) if (V.master[k] >= 0) { cnt[V.master[k]]++; V.Sn[V.master[k]] += geo.sbar[k]; }
+    V.mstart[0] = 0;
+    for (long k = 0; k < nc; ++k) V.mstart[k + 1] = V.mstart[k] + cnt[k];
+    memset(cnt, 0, sizeof(int32_t) * nc);
+    for (long k = 0; k < nc; ++k)
+        if (V.master[k] >= 0) { int m = V.master[k]; V.mlist[V.mstart[m] + cnt[m]++] = (int32_t)k; }
+    memcpy(Fs, F0, sizeof(double) * ns);
+    for (int n = 0; n < nsteps && !err; ++n) {
+        memcpy(Fs + (size_t)(n + 1) * ns, Fs + (size_t)n * ns, sizeof(double) * ns);
+        err = orc_run2d(c, Fs + (size_t)(n + 1) * ns, 1, NULL, NULL, NULL);
+    }
+    if (err) goto done;
+
+    /* objective: J = F_x of the fused final state; nu = dJ/dFt */
+    {
+        fuse2d(&X, &V, Fs + (size_t)nsteps * ns, Ft);
+        memset(nu, 0, sizeof(double) * ns);
+        double J = 0;
+        for (long k = 0; k < nc; ++k) {
+            if (geo.type[k] != ORC_CUT || !(geo.lw[k] > 0)) continue;
+            const orc_wall w = wall2d(&X, k, Ft);
+            const double nwx = geo.nwx[k], nwy = geo.nwy[k], lw = geo.lw[k];
+            double sxx = 0, sxy = 0, sphi = 0, sTw = 0, dD = 0;
+            for (int p2 = 0; p2 < X.nv2; ++p2)
+                for (int p1 = 0; p1 < X.nv1; ++p1) {
+                    const int p = p2 * X.nv1 + p1;
+                    const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                    const double ax = vx - w.uwx, ay = vy - w.uwy, cp = ax * nwx + ay * nwy;
+                    const double wgt = (ax * ax * nwx + ax * ay * nwy) * lw * dv;   /* dFx / dF_w(p) */
+                    if (cp > 0) {
+                        const double f = Ft[k * 2 * nv + p];
+                        sxx += ax * ax * f * dv; sxy += ax * ay * f * dv;
+                        nu[k * 2 * nv + p] += wgt;
+                    } else if (cp < 0) {
+                        const double m1 = maxw2d(1.0, w.uwx, w.uwy, w.Tw, vx, vy);
+                        const double dm1 = dM1_dTw(m1, ax, ay, w.Tw);
+                        sxx += ax * ax * w.phi * m1 * dv; sxy += ax * ay * w.phi * m1 * dv;
+                        sphi += wgt * m1;
+                        sTw += wgt * w.phi * dm1;
+                        dD += cp * dm1 * dv;
+                    }
+                }
+            J += (sxx * nwx + sxy * nwy) * lw;
+            /* phi = -num / D: dphi/df(p) = -c_p dv / D (c_p > 0); dphi/dTw = -phi / D dD/dTw */
+            for (int p2 = 0; p2 < X.nv2; ++p2)
+                for (int p1 = 0; p1 < X.nv1; ++p1) {
+                    const int p = p2 * X.nv1 + p1;
+                    const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                    const double cp = (vx - w.uwx) * nwx + (vy - w.uwy) * nwy;
+                    if (cp > 0) nu[k * 2 * nv + p] += sphi * (-cp * dv / w.D);
+                }
+            gTw[w.sector] += sTw + sphi * (-w.phi / w.D) * dD;
+        }
+        *Jout = J;
+        fuse2d_T(&X, &V, nu, lam);
+    }
+
+    /* reverse sweep over the steps */
+    for (int n = nsteps - 1; n >= 0; --n) {
+        const double *Fn = Fs + (size_t)n * ns;
+        fuse2d(&X, &V, Fn, Ft);
+        X.F = Ft;
+        /* transpose of the distribution: mu_m = sum of lam over the members */
+        memset(mu, 0, sizeof(double) * ns);
+        for (long k = 0; k < nc; ++k) {
+            const int m = V.master[k];
+            if (m < 0) continue;
+            for (int q = 0; q < 2 * nv; ++q) mu[(long)m * 2 * nv + q] += lam[k * 2 * nv + q];
+        }
+        memset(nu, 0, sizeof(double) * ns);
+        for (long m = 0; m < nc; ++m) {
+            if (V.mstart[m + 1] - V.mstart[m] == 0) continue;
+            const double *mm = mu + m * 2 * nv;
+            const double *fc = Ft + m * 2 * nv;
+            /* relaxation: G = fcv - b R + r (Feq - fcv), r = dt rho / tau0 */
+            double u[3], rho, T;
+            cell_moments(c, fc, &rho, u, &T);
+            const double r = dt * rho / tau0, b = dt / V.Sn[m];
+            double sp[4] = {0, 0, 0, 0};          /* d/d(rho, ux, uy, T) of sum mu r Feq */
+            double srho_r = 0;                     /* via r(rho): sum mu (Feq - fcv) dt/tau0 */
+            for (int p2 = 0; p2 < X.nv2; ++p2)
+                for (int p1 = 0; p1 < X.nv1; ++p1) {
+                    const int p = p2 * X.nv1 + p1;
+                    const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                    double M, dm[4], dg[4];
+                    maxw2d_d(rho, u[0], u[1], T, vx, vy, &M, dm, dg);
+                    for (int q = 0; q < 4; ++q) sp[q] += r * (mm[p] * dm[q] + mm[nv + p] * dg[q]);
+                    srho_r += (mm[p] * (M - fc[p]) + mm[nv + p] * (T / 2.0 * M - fc[nv + p])) * dt / tau0;
+                    nu[m * 2 * nv + p] += mm[p] * (1.0 - r);
+                    nu[m * 2 * nv + nv + p] += mm[nv + p] * (1.0 - r);
+                }
+            sp[0] += srho_r;
+            /* chain (rho, ux, uy, T) -> conserved sums (m0, m1, m2, m3) = (rho, rho ux, rho uy, E) */
+            const double E = rho * (0.5 * (u[0] * u[0] + u[1] * u[1]) + 1.5 * T);
+            const double S0 = sp[0] - sp[1] * u[0] / rho - sp[2] * u[1] / rho +
+                              sp[3] * (-2.0 * E / (rho * rho) + 2.0 * (u[0] * u[0] + u[1] * u[1]) / rho) / 3.0;
+            const double S1 = sp[1] / rho - sp[3] * 2.0 * u[0] / (3.0 * rho);
+            const double S2 = sp[2] / rho - sp[3] * 2.0 * u[1] / (3.0 * rho);
+            const double S3 = sp[3] * 2.0 / (3.0 * rho);
+            for (int p2 = 0; p2 < X.nv2; ++p2)
+                for (int p1 = 0; p1 < X.nv1; ++p1) {
+                    const int p = p2 * X.nv1 + p1;
+                    const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                    nu[m * 2 * nv + p] += dv * (S0 + S1 * vx + S2 * vy + S3 * 0.5 * (vx * vx + vy * vy));
+                    nu[m * 2 * nv + nv + p] += dv * S3;
+                }
+            /* transport of every member: G -= b R */
+            for (int qq = V.mstart[m]; qq < V.mstart[m + 1]; ++qq) {
+                const long k = V.mlist[qq];
+                if (geo.type[k] == ORC_SOLID) continue;
+                const int i = (int)(k % nx), j = (int)(k / nx);
+                const int mus = c->scheme == ORC_MUSCL;
+                const int mxp = mus && isgas2d(&X, i - 1, j) && isgas2d(&X, i, j) && isgas2d(&X, i + 1, j) && isgas2d(&X, i + 2, j);
+                const int mxm = mus && isgas2d(&X, i - 2, j) && isgas2d(&X, i - 1, j) && isgas2d(&X, i, j) && isgas2d(&X, i + 1, j);
+                const int myp = mus && isgas2d(&X, i, j - 1) && isgas2d(&X, i, j) && isgas2d(&X, i, j + 1) && isgas2d(&X, i, j + 2);
+                const int mym = mus && isgas2d(&X, i, j - 2) && isgas2d(&X, i, j - 1) && isgas2d(&X, i, j) && isgas2d(&X, i, j + 1);
+                const double lxp = geo.lx[j * (nx + 1) + i + 1], lxm = geo.lx[j * (nx + 1) + i];
+                const double lyp = geo.ly[(j + 1) * nx + i], lym = geo.ly[j * nx + i];
+                /* the four faces: sign in R, length, axis, stencil cells (AA, A, B, BB) */
+                const struct { double sgn, L; int ax, muscl; int ci[4], cj[4]; } faces[4] = {
+                    {+1.0, lxp, 0, mxp, {i - 1, i, i + 1, i + 2}, {j, j, j, j}},
+                    {-1.0, lxm, 0, mxm, {i - 2, i - 1, i, i + 1}, {j, j, j, j}},
+                    {+1.0, lyp, 1, myp, {i, i, i, i}, {j - 1, j, j + 1, j + 2}},
+                    {-1.0, lym, 1, mym, {i, i, i, i}, {j - 2, j - 1, j, j + 1}}};
+                for (int fa = 0; fa < 4; ++fa) {
+                    orc_loc loc[4];
+                    for (int t = 0; t < 4; ++t) loc[t] = loc2d(&X, faces[fa].ci[t], faces[fa].cj[t]);
+                    for (int comp = 0; comp < 2; ++comp)
+                        for (int p2 = 0; p2 < X.nv2; ++p2)
+                            for (int p1 = 0; p1 < X.nv1; ++p1) {
+                                const int p = p2 * X.nv1 + p1;
+                                const double w = -b * mm[comp * nv + p] * faces[fa].sgn;
+                                if (w == 0.0) continue;
+                                const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                                const double v = faces[fa].ax == 0 ? vx : vy;
+                                const double nuc = faces[fa].ax == 0 ? fabs(vx) * dt / X.dx : fabs(vy) * dt / X.dy;
+                                double fv[4], d[4];
+                                for (int t = 0; t < 4; ++t) fv[t] = fval2d(&X, faces[fa].ci[t], faces[fa].cj[t], comp, p);
+                                face_flux_d(faces[fa].L, v, nuc, fv[0], fv[1], fv[2], fv[3], faces[fa].muscl, d);
+                                for (int t = 0; t < 4; ++t) {
+                                    if (d[t] == 0.0) continue;
+                                    if (loc[t].cell >= 0) nu[(loc[t].cell * 2 + comp) * nv + p] += w * d[t];
+                                    else gg[loc[t].side][((long)loc[t].q * 2 + comp) * nv + p] += w * d[t];
+                                }
+                            }
+                }
+                /* wall flux: lw (min(c,0) phi Mw + max(c,0) F) */
+                if (geo.type[k] == ORC_CUT && geo.lw[k] > 0) {
+                    const orc_wall ww = wall2d(&X, k, Ft);
+                    const double nwx = geo.nwx[k], nwy = geo.nwy[k], lw = geo.lw[k];
+                    double sphi = 0, sTw = 0, dD = 0;
+                    for (int p2 = 0; p2 < X.nv2; ++p2)
+                        for (int p1 = 0; p1 < X.nv1; ++p1) {
+                            const int p = p2 * X.nv1 + p1;
+                            const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                            const double ax = vx - ww.uwx, ay = vy - ww.uwy, cp = ax * nwx + ay * nwy;
+                            const double w0 = -b * mm[p], w1 = -b * mm[nv + p];
+                            if (cp > 0) {
+                                nu[k * 2 * nv + p] += w0 * lw * cp;
+                                nu[k * 2 * nv + nv + p] += w1 * lw * cp;
+                            } else if (cp < 0) {
+                                const double m1 = maxw2d(1.0, ww.uwx, ww.uwy, ww.Tw, vx, vy);
+                                const double dm1 = dM1_dTw(m1, ax, ay, ww.Tw);
+                                /* f_w = phi m1, g_w = phi Tw/2 m1 */
+                                sphi += lw * cp * (w0 * m1 + w1 * ww.Tw / 2.0 * m1);
+                                sTw += lw * cp * ww.phi * (w0 * dm1 + w1 * (m1 / 2.0 + ww.Tw / 2.0 * dm1));
+                                dD += cp * dm1 * dv;
+                            }
+                        }
+                    for (int p2 = 0; p2 < X.nv2; ++p2)
+                        for (int p1 = 0; p1 < X.nv1; ++p1) {
+                            const int p = p2 * X.nv1 + p1;
+                            const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                            const double cp = (vx - ww.uwx) * nwx + (vy - ww.uwy) * nwy;
+                            if (cp > 0) nu[k * 2 * nv + p] += sphi * (-cp * dv / ww.D);
+                        }
+                    gTw[ww.sector] += sTw + sphi * (-ww.phi / ww.D) * dD;
+                }
+            }
+        }
+        fuse2d_T(&X, &V, nu, lam);
+    }
+    memcpy(lam0, lam, sizeof(double) * ns);
+    /* ghost sensitivities -> (rho, ux, uy, uz, T) of the Maxwellian sides */
+    for (int s = 0; s < 4; ++s) {
+        if (!gg[s] || !gbc[s]) continue;
+        for (int q = 0; q < nside[s]; ++q) {
+            const double *st = c->bc_state[s] + 5 * q;
+            double *o = gbc[s] + 5 * q;
+            for (int p2 = 0; p2 < X.nv2; ++p2)
+                for (int p1 = 0; p1 < X.nv1; ++p1) {
+                    const int p = p2 * X.nv1 + p1;
+                    const double vx = c->vxmin + p1 * X.dvx, vy = c->vymin + p2 * X.dvy;
+                    double M, dm[4], dg[4];
+                    maxw2d_d(st[0], st[1], st[2], st[4], vx, vy, &M, dm, dg);
+                    const double a0 = gg[s][((long)q * 2) * nv + p], a1 = gg[s][((long)q * 2 + 1) * nv + p];
+                    o[0] += a0 * dm[0] + a1 * dg[0];
+                    o[1] += a0 * dm[1] + a1 * dg[1];
+                    o[2] += a0 * dm[2] + a1 * dg[2];
+                    o[4] += a0 * dm[3] + a1 * dg[3];
+                }
+        }
+    }
+done:
+    free_geo2d(&geo);
+    free(V.master); free(V.mstart); free(V.mlist); free(V.Sn); free(cnt);
+    free(Fs); free(Ft); free(nu); free(lam); free(mu);
+    for (int s = 0; s < 4; ++s) { free(X.ghost[s]); free(gg[s]); }
+    return err;
+}
+
+/* Transpose of the Maxwellian initial state (orc_init_maxwellian, 2D):
+ * g[cell][5] = d<lam, F0>/d(rho, ux, uy, uz, T) of each cell. */
+int orc_init_maxwellian_vjp(const orc_cfg *c, const double *rho, const double *ux, const double *uy,
+                            const double *T, const double *lam, double *g)
+{
+    if (c->dim != 2) return ORC_ERR_ARG;
+    const int nv1 = c->nvx, nv2 = c->nvy, nv = nv1 * nv2;
+    const long ncell = (long)c->nx * c->ny;
+    const double dvx = (c->vxmax - c->vxmin) / nv1, dvy = (c->vymax - c->vymin) / nv2;
+    for (long k = 0; k < ncell; ++k) {
+        double *o = g + 5 * k;
+        for (int q = 0; q < 5; ++q) o[q] = 0;
+        if (rho[k] <= 0) continue;
+        for (int p2 = 0; p2 < nv2; ++p2)
+            for (int p1 = 0; p1 < nv1; ++p1) {
+                const int p = p2 * nv1 + p1;
+                const double vx = c->vxmin + p1 * dvx, vy = c->vymin + p2 * dvy;
+                double M, dm[4], dg[4];
+                maxw2d_d(rho[k], ux[k], uy[k], T[k], vx, vy, &M, dm, dg);
+                const double a0 = lam[(k * 2) * nv + p], a1 = lam[(k * 2 + 1) * nv + p];
+                o[0] += a0 * dm[0] + a1 * dg[0];
+                o[1] += a0 * dm[1] + a1 * dg[1];
+                o[2] += a0 * dm[2] + a1 * dg[2];
+                o[4] += a0 * dm[3] + a1 * dg[3];
+            }
+    }
+    return ORC_OK;
+}

@@ -120,4 +120,16 @@ int orc_masters3d(const orc_cfg *c, const orc_geo3d *g, int32_t *master);
 int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h);
 double orc_mass3d(const orc_cfg *c, const double *F);
 
+
+/* ------------------------------------------------------------ 2D adjoint */
+
+/* Drag J = F_x(F^N) after nsteps fixed-body steps from F0, and its discrete
+ * adjoint: lam0 = dJ/dF0 (layout of F), gTw[nseg] (or gTw[0] for a uniform
+ * wall) = dJ/dT_w, gbc_s[5 * side cells] = dJ/d(rho, ux, uy, uz, T) of the
+ * Maxwellian side s (nullable; zeros for other sides). */
+int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *J, double *lam0,
+                  double *gTw, double *gbc0, double *gbc1, double *gbc2, double *gbc3);
+int orc_init_maxwellian_vjp(const orc_cfg *c, const double *rho, const double *ux,
+                            const double *uy, const double *T, const double *lam, double *g);
+
 #endif

@@ -140,12 +140,12 @@ def segment_directions(nseg: int) -> np.ndarray:
     return np.stack([np.cos(a), np.sin(a)], axis=1).ravel()
 
 
-def cylinder_adjoint(nx=256, nv=32, nseg=64, seed=0) -> dict:
+def cylinder_adjoint(nx=256, nv=32, nseg=64, seed=0, mach=2.0, steps=200) -> dict:
     """Cylinder flow with 64 per-sector wall temperatures in [0.8, 1.2]."""
-    cfg = cylinder_mach2(nx, nv)
+    cfg = cylinder_mach2(nx, nv, mach=mach)
     rng = np.random.default_rng(seed)
     cfg.update(nseg=nseg, Tw_seg=rng.uniform(0.8, 1.2, nseg), seg_dir=segment_directions(nseg),
-               steps=200, checkpoint_every=20, mach=2.0,
+               steps=steps, checkpoint_every=20, mach=mach,
                name=f"cylinder_adjoint_{nx}x{nx}_v{nv}x{nv}_seg{nseg}")
     return cfg
 
