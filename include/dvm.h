@@ -197,6 +197,28 @@ int dvm_geometry3d(dvm_ctx *ctx, int8_t *type, int8_t *cgas, double *ax, double 
  * bit-exact comparisons with an independent implementation. */
 int dvm_geometry2d_at(dvm_ctx *ctx, double cos_t, double sin_t);
 
+/* Drag gradient by the discrete adjoint (the paper has no adjoint: the step of
+ * Sec. 3.3.5 is differentiated as it stands; 2D, fixed obstacle).  Runs
+ * nsteps forward steps from the current state, checkpointing it every
+ * checkpoint_every steps on the device, and returns
+ *   J       F_x of the state after nsteps steps (Eqs. StressTensorDD, eq-force)
+ *   gTw     dJ/dT_w per wall sector [nseg], or [1] for a uniform wall
+ *   gbc_s   dJ/d(rho, ux, uy, uz, T) of every cell of Maxwellian side s
+ *           [5 * side cells] (nullable; zeros for other sides)
+ *   gprim0  dJ/d(rho, ux, uy, uz, T) of each cell of the initial Maxwellian
+ *           [5 * ncell] (nullable; needs a state set by dvm_init_maxwellian)
+ *   ms_forward, ms_reverse  device time of the checkpointed forward run and of
+ *           the reverse sweep (recomputation included), nullable.
+ * The reverse sweep recomputes each segment from its checkpoint onto a device
+ * tape of checkpoint_every states and applies the transposed step (limiter
+ * derivative of the branch the forward takes).  The context is left at the
+ * state after nsteps steps.  Device memory: ceil(nsteps/K) + K + 3 states.
+ * Errors: DVM_ERR_UNSUPPORTED (3D, no or moving obstacle), DVM_ERR_ARG,
+ * DVM_ERR_STATE, DVM_ERR_OOM, DVM_ERR_NONPHYSICAL. */
+int dvm_drag_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, double *J, double *gTw,
+                     double *gbc0, double *gbc1, double *gbc2, double *gbc3, double *gprim0,
+                     double *ms_forward, double *ms_reverse);
+
 /* Live timing of the dominant kernel (the fused bulk stream-and-relax
  * kernel): when enabled, every step records a CUDA event pair around its
  * launch on the context's stream.  dvm_kernel_time synchronises the stream,

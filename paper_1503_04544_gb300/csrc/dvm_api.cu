@@ -363,6 +363,9 @@ void dvm_destroy(dvm_ctx *c)
     cudaFree(c->d_body); cudaFree(c->d_hist); cudaFree(c->d_err);
     cudaFree(c->d_scratch); cudaFree(c->d_out);
     cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
+    for (int s = 0; s < 6; ++s) cudaFree(c->d_bcstate[s]);
+    cudaFree(c->d_prim0);
+    free_adjoint2d(c);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->ev_pool) {
         auto *pool = static_cast<std::vector<cudaEvent_t> *>(c->ev_pool);
@@ -382,12 +385,12 @@ int dvm_set_bc(dvm_ctx *c, int side, int kind, const double *state)
     if (kind == DVM_BC_MAXWELLIAN) {
         for (int q = 0; q < n; ++q)
             if (!(state[5 * q] > 0) || !(state[5 * q + 4] > 0)) { set_error("Maxwellian side: rho and T must be > 0"); return DVM_ERR_ARG; }
-        double *d = nullptr;
-        CK(cudaMalloc(&d, sizeof(double) * 5 * n));
+        // the side states stay on the device (the adjoint differentiates them)
+        if (!c->d_bcstate[side]) CK(cudaMalloc(&c->d_bcstate[side], sizeof(double) * 5 * n));
+        double *d = c->d_bcstate[side];
         cudaError_t e = cudaMemcpyAsync(d, state, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = st_ghost(c, side, d, n);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        cudaFree(d);
         if (e != cudaSuccess) return cuda_fail(e, "dvm_set_bc");
     }
     c->bc[side] = kind;
@@ -544,8 +547,10 @@ int dvm_init_maxwellian(dvm_ctx *c, const double *rho, const double *ux, const d
         prim[5 * k + 4] = T ? T[k] : 1.0;
         if (prim[5 * k] > 0 && !(prim[5 * k + 4] > 0)) { set_error("T must be > 0"); return DVM_ERR_ARG; }
     }
-    double *d = c->d_out;      // nc*5 doubles
+    if (!c->d_prim0) CK(cudaMalloc(&c->d_prim0, sizeof(double) * 5 * nc));
+    double *d = c->d_prim0;    // kept: the adjoint chains dJ/dF^0 to these primitives
     CK(cudaMemcpyAsync(d, prim.data(), sizeof(double) * 5 * nc, cudaMemcpyHostToDevice, c->stream));
+    c->have_prim0 = true;
     CK(st_init(c, d));
     CK(st_zero_solid(c));
     CK(st_halo(c, c->cur));
@@ -569,6 +574,7 @@ int dvm_set_state(dvm_ctx *c, const void *f, size_t bytes, int on_device)
     if (rc != DVM_OK) return rc;
     CK(cudaMemcpyAsync(c->d_pub, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(st_pack(c, c->d_pub, c->f[c->cur]));
+    c->have_prim0 = false;
     CK(st_zero_solid(c));
     CK(st_halo(c, c->cur));
     CK(st_partials(c));
@@ -757,6 +763,28 @@ int dvm_geometry3d(dvm_ctx *c, int8_t *type, int8_t *cgas, double *ax, double *a
     CK(cp(master, c->master, sizeof(int32_t) * nc));
     CK(cudaStreamSynchronize(c->stream));
     return DVM_OK;
+}
+
+int dvm_drag_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, double *J, double *gTw, double *gbc0,
+                     double *gbc1, double *gbc2, double *gbc3, double *gprim0, double *ms_forward,
+                     double *ms_reverse)
+{
+    if (!c || !J || !gTw) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (c->dim != 2) { set_error("dvm_drag_adjoint: 2D contexts only"); return DVM_ERR_UNSUPPORTED; }
+    if (c->body.shape == DVM_SHAPE_NONE || c->moving) {
+        set_error("dvm_drag_adjoint: needs a fixed obstacle"); return DVM_ERR_UNSUPPORTED;
+    }
+    if (!c->have_state) { set_error("no state"); return DVM_ERR_STATE; }
+    if (nsteps < 1 || checkpoint_every < 1) { set_error("nsteps and checkpoint_every must be >= 1"); return DVM_ERR_ARG; }
+    for (int d = 0; d < 2; ++d)
+        if ((c->bc[2 * d] == DVM_BC_PERIODIC) != (c->bc[2 * d + 1] == DVM_BC_PERIODIC)) {
+            set_error("opposite sides must both be periodic or both not");
+            return DVM_ERR_ARG;
+        }
+    double *gbc[4] = {gbc0, gbc1, gbc2, gbc3};
+    int rc = drag_adjoint2d(c, nsteps, checkpoint_every, J, gTw, gbc, gprim0, ms_forward, ms_reverse);
+    if (rc != DVM_OK) return rc;
+    return check_flags(c);
 }
 
 int dvm_timing(dvm_ctx *c, int enable)

@@ -190,5 +190,126 @@ __device__ __forceinline__ T block_sum(T v, T *red)
     return s;
 }
 
+// Slab index of cell (i, j), -2 <= i < nx + 2, -2 <= j < ny + 2: the slab is
+// the grid padded by two cells on every side, and the padding holds the
+// boundary-condition values (Maxwellian ghosts, periodic images or
+// zero-gradient copies), so a neighbour within two cells is a plain index.
+__device__ __forceinline__ long nbr(const Grid2D &g, int i, int j)
+{
+    return (long)(j + 2) * (g.nx + 4) + (i + 2);
+}
+
+// Cell coordinates of interior cell k = j*nx + i (2D grids have fewer than
+// 2^31 cells, so 32-bit arithmetic suffices).
+__device__ __forceinline__ void cell_ij(const Grid2D &g, long k, int &i, int &j)
+{
+    const int kk = (int)k;
+    j = kk / g.nx;
+    i = kk - j * g.nx;
+}
+
+// Slab index of interior cell k.
+__device__ __forceinline__ long pcell(const Grid2D &g, long k)
+{
+    int i, j;
+    cell_ij(g, k, i, j);
+    return nbr(g, i, j);
+}
+
+// Offset of (comp, p) within the device layout; add slab index * W.
+template <typename T>
+__device__ __forceinline__ long ebase(const Grid2D &g, int comp, int p)
+{
+    constexpr int W = Vec<T>::W;
+    return ((long)(p / W) * 2 + comp) * g.slab * W + (p % W);
+}
+
+// Element (interior cell k, comp, p) of the device layout.
+template <typename T>
+__device__ __forceinline__ long didx(const Grid2D &g, long k, int comp, int p)
+{
+    return ebase<T>(g, comp, p) + pcell(g, k) * Vec<T>::W;
+}
+
+// Padding cells that mirror interior cell (i, j) on periodic and
+// zero-gradient sides (at most two along each axis); -1 where unused.
+__device__ __forceinline__ void mirrors(const Grid2D &g, int i, int j, long (&m)[4])
+{
+    m[0] = m[1] = m[2] = m[3] = -1;
+    if (g.bc[0] == DVM_BC_PERIODIC) {
+        if (i < 2) m[0] = nbr(g, i + g.nx, j);
+        else if (i >= g.nx - 2) m[0] = nbr(g, i - g.nx, j);
+    } else {
+        if (i == 0 && g.bc[0] == DVM_BC_ZEROGRAD) { m[0] = nbr(g, -1, j); m[1] = nbr(g, -2, j); }
+        if (i == g.nx - 1 && g.bc[1] == DVM_BC_ZEROGRAD) { m[0] = nbr(g, g.nx, j); m[1] = nbr(g, g.nx + 1, j); }
+    }
+    if (g.bc[2] == DVM_BC_PERIODIC) {
+        if (j < 2) m[2] = nbr(g, i, j + g.ny);
+        else if (j >= g.ny - 2) m[2] = nbr(g, i, j - g.ny);
+    } else {
+        if (j == 0 && g.bc[2] == DVM_BC_ZEROGRAD) { m[2] = nbr(g, i, -1); m[3] = nbr(g, i, -2); }
+        if (j == g.ny - 1 && g.bc[3] == DVM_BC_ZEROGRAD) { m[2] = nbr(g, i, g.ny); m[3] = nbr(g, i, g.ny + 1); }
+    }
+}
+
+// Per-velocity coefficients: vx, vy, nu_x = |vx| dt/dx, nu_y = |vy| dt/dy.
+// Padded velocities carry a huge speed (their Maxwellian is 0) and zero
+// Courant numbers.
+template <typename T> struct alignas(4 * sizeof(T)) VCoef { T vx, vy, nux, nuy; };
+
+template <typename T>
+__device__ __forceinline__ VCoef<T> ld_coef(const VCoef<T> *p)
+{
+    VCoef<T> c;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        c.vx = a.x; c.vy = a.y; c.nux = a.z; c.nuy = a.w;
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        c.vx = a.x; c.vy = a.y; c.nux = b.x; c.nuy = b.y;
+    }
+    return c;
+}
+
+// Sector of a wall point for piecewise wall temperatures: the first s with
+// cross(d_s, r) >= 0 and cross(d_{s+1}, r) < 0.
+__device__ __forceinline__ double wall_temperature(const BodyParams &b, double rx, double ry)
+{
+    if (b.nseg <= 0) return b.Tw;
+    for (int s = 0; s < b.nseg; ++s) {
+        int t = (s + 1) % b.nseg;
+        double p = b.seg_dir[2 * s] * ry - b.seg_dir[2 * s + 1] * rx;
+        double q = b.seg_dir[2 * t] * ry - b.seg_dir[2 * t + 1] * rx;
+        if (p >= 0 && q < 0) return b.Tw_seg[s];
+    }
+    return b.Tw_seg[0];
+}
+
+// One member (virtual cell) of a control volume, as the update needs it.
+struct __align__(16) CvMember {
+    long pc;                  // slab index
+    long mir[4];              // padding mirrors (-1: none)
+    int i, j;
+    double L[4];              // Cartesian edge lengths at t^n: x-, x+, y-, y+
+    double lw, nwx, nwy;      // wall edge at t^n (lw = 0: no wall)
+    double sb;                // virtual-cell area at t^n
+    int wslot;                // wall slot, -1 if none
+    int mask;                 // limiter mask of the faces
+    int live, keep;           // non-solid at t^n / at t^{n+1}
+};
+
+// A control volume: members in cell order, the master's slab index and the
+// area ratios of Eq. ExSchemeDD, all fixed between geometry updates.
+struct __align__(16) CvInfo {
+    int nm;
+    int ok;                   // S^{n+1,*} > 0
+    long pcm;
+    double a;                 // S^n / S^{n+1,*}
+    double bco;               // dt / S^{n+1,*}
+    double Sn;
+    CvMember mem[kMaxMembers];
+};
+
 }  // namespace
 }  // namespace dvm

@@ -165,6 +165,10 @@ struct dvm_ctx {
     double *d_scratch;            // nc doubles (mass)
     double *d_out;                // nc*5 doubles (moments output)
     void *d_pub;                  // staging buffer in the public layout
+    double *d_bcstate[6];         // (rho, ux, uy, uz, T) per cell of each Maxwellian side
+    double *d_prim0;              // primitives of the last dvm_init_maxwellian (nc * 5)
+    bool have_prim0;
+    void *adj;                    // adjoint workspace (dvm_adjoint2d.cu)
     bool have_state, have_geo, need_fusion, moving;
     bool timing;
     void *ev_pool;                // std::vector<cudaEvent_t> of start/stop pairs
@@ -190,6 +194,7 @@ cudaError_t tables2d(dvm_ctx *c);
 cudaError_t partials_from_state2d(dvm_ctx *c);
 cudaError_t init_maxwellian2d(dvm_ctx *c, const double *d_prim);
 cudaError_t step2d(dvm_ctx *c);
+cudaError_t fusion2d(dvm_ctx *c, void *f, void *part);          // Eq. FusionDD on a buffer
 cudaError_t mass2d(dvm_ctx *c, double *d_scratch, double *d_out);
 cudaError_t moments_out2d(dvm_ctx *c, double *d_out);
 cudaError_t ghost2d(dvm_ctx *c, int side, const double *d_prim, int nside);
@@ -200,6 +205,10 @@ cudaError_t halo2d(dvm_ctx *c, int buf);                         // periodic / z
 cudaError_t members2d(dvm_ctx *c, bool moving);                  // control-volume records
 cudaError_t timing_mark(dvm_ctx *c, int which);   // 0: before, 1: after the bulk kernel
 int make_tensor_maps2d(dvm_ctx *c);                // TMA descriptors of f[0], f[1]
+// adjoint (dvm_adjoint2d.cu)
+int drag_adjoint2d(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double *const *gbc, double *gprim0,
+                   double *ms_forward, double *ms_reverse);
+void free_adjoint2d(dvm_ctx *c);
 
 // 3D (dvm_geometry3d.cu, dvm_step3d.cu)
 dvm::Grid3D grid3d(const dvm_ctx *c);

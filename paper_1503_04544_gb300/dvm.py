@@ -85,6 +85,7 @@ SIGNATURES = {
     "dvm_geometry2d": [_P, _PI8, _PI8, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PI32],
     "dvm_geometry2d_at": [_P, C.c_double, C.c_double],
     "dvm_geometry3d": [_P, _PI8, _PI8, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PI32],
+    "dvm_drag_adjoint": [_P, C.c_int, C.c_int, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD],
     "dvm_timing": [_P, C.c_int],
     "dvm_kernel_time": [_P, _PD, C.POINTER(C.c_longlong)],
     "dvm_launches": [_P, C.POINTER(C.c_longlong)],
@@ -275,6 +276,24 @@ class Solver:
 
     def geometry2d_at(self, cos_t: float, sin_t: float):
         _check(load().dvm_geometry2d_at(self.h, float(cos_t), float(sin_t)))
+
+    def drag_adjoint(self, nsteps: int, checkpoint_every: int = 20, want_init: bool = True) -> dict:
+        """Drag J = F_x after ``nsteps`` steps and its gradient (dvm_drag_adjoint):
+        dJ/dT_w per sector, per Maxwellian side cell and per initial-state
+        cell, with the device times of the forward and reverse sweeps."""
+        ns = max(int(self.cfg.get("nseg", 0)), 1)
+        gtw = np.zeros(ns)
+        nside = [self.cfg["ny"], self.cfg["ny"], self.cfg["nx"], self.cfg["nx"]]
+        gbc = [np.zeros(5 * n) for n in nside]
+        gp = np.zeros(5 * self.ncell) if want_init else None
+        J = np.zeros(1)
+        tf = np.zeros(1)
+        tr = np.zeros(1)
+        _check(load().dvm_drag_adjoint(self.h, int(nsteps), int(checkpoint_every), _ptr(J), _ptr(gtw),
+                                       *[_ptr(g) for g in gbc], _ptr(gp), _ptr(tf), _ptr(tr)))
+        return dict(J=float(J[0]), gTw=gtw, gbc=[g.reshape(-1, 5) for g in gbc],
+                    gprim0=None if gp is None else gp.reshape(-1, 5), ms_forward=float(tf[0]),
+                    ms_reverse=float(tr[0]))
 
     # -------------------------------------------------------------- instrumentation
     def timing(self, enable: bool):

@@ -1,0 +1,135 @@
+"""Drag gradient by the discrete adjoint on the GPU (dvm_drag_adjoint) against
+the oracle's FP64 adjoint and against central finite differences.  GPU only.
+
+dJ/dMach = sqrt(5/3) (sum of dJ/dux over the inflow side cells and over the
+initial-state cells): the Mach number sets u = Ma sqrt(gamma) in the inflow
+Maxwellian and in the initial state.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_04544_gb300 import dvm
+from paper_1503_04544_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SQ = math.sqrt(5.0 / 3.0)
+
+
+def gpu_adjoint(cfg, prec, steps, K):
+    s = dvm.Solver(cfg, prec)
+    s.init_maxwellian()
+    out = s.drag_adjoint(steps, K)
+    s.close()
+    out["gmach"] = SQ * (out["gbc"][0][:, 1].sum() + out["gprim0"][:, 1].sum())
+    return out
+
+
+def oracle_adjoint(cfg, steps):
+    a = oracle.adjoint2d(cfg, oracle.initial_state(cfg), steps)
+    assert a["status"] == 0
+    gi = oracle.init_maxwellian_vjp(cfg, a["lam0"])
+    a["gprim0"] = gi
+    a["gmach"] = SQ * (gi[:, 1].sum() + a["gbc"][0][:, 1].sum())
+    return a
+
+
+def small(scheme, **kw):
+    """24^2 cylinder, 12^2 velocities, 8 wall sectors.  The initial state is a
+    smooth non-uniform Maxwellian field: in a uniform state every limiter
+    difference is exactly 0, where minmod has no derivative and rounding-level
+    differences between two implementations select different branches."""
+    cfg = W.cylinder_adjoint(nx=24, nv=12, nseg=8, steps=12)
+    cfg["scheme"] = scheme
+    x = (np.arange(24) + 0.5) / 24
+    X, Y = np.meshgrid(x, x)
+    u = SQ * 2.0
+    cfg["init"] = dict(rho=(1.0 + 0.2 * np.sin(2 * np.pi * X) * np.cos(np.pi * Y)).ravel(),
+                       ux=(u * (1.0 + 0.1 * np.cos(2 * np.pi * Y))).ravel(),
+                       uy=(0.2 * np.sin(2 * np.pi * X)).ravel(), uz=0.0, T=(1.0 + 0.1 * X * Y).ravel())
+    cfg.update(kw)
+    return cfg
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("prec", [dvm.FP64, dvm.FP32])
+def test_adjoint_matches_oracle_adjoint(scheme, prec):
+    """Cylinder, 8 wall sectors, Mach-2 inflow: J, dJ/dT_w, dJ/d(inflow state),
+    dJ/d(initial state) and dJ/dMach against the oracle's adjoint (12 steps,
+    checkpoints every 5: a partial last segment)."""
+    cfg = small(scheme)
+    g = gpu_adjoint(cfg, prec, 12, 5)
+    o = oracle_adjoint(cfg, 12)
+    tol = 1e-10 if prec == dvm.FP64 else 2e-4
+    assert abs(g["J"] - o["J"]) <= (1e-12 if prec == dvm.FP64 else 1e-5) * abs(o["J"])
+    sc = np.abs(o["gTw"]).max()
+    assert np.abs(g["gTw"] - o["gTw"]).max() <= tol * sc, (g["gTw"], o["gTw"])
+    sb = np.abs(o["gbc"][0]).max()
+    assert np.abs(g["gbc"][0] - o["gbc"][0]).max() <= tol * sb
+    si = np.abs(o["gprim0"]).max()
+    assert np.abs(g["gprim0"] - o["gprim0"]).max() <= tol * si
+    assert abs(g["gmach"] - o["gmach"]) <= tol * abs(o["gmach"])
+
+
+@pytest.mark.parametrize("bc", [[0, 0, 0, 0, 0, 0], [2, 2, 2, 2, 0, 0]])
+def test_adjoint_other_boundaries(bc):
+    """Periodic and zero-gradient boxes (pads that copy interior cells are
+    folded back onto them in the transpose), drifting initial gas, MUSCL."""
+    cfg = small(1, bc=bc, bc_state=[None] * 6)
+    g = gpu_adjoint(cfg, dvm.FP64, 10, 4)
+    o = oracle_adjoint(cfg, 10)
+    assert abs(g["J"] - o["J"]) <= 1e-12 * abs(o["J"])
+    assert np.abs(g["gTw"] - o["gTw"]).max() <= 1e-10 * np.abs(o["gTw"]).max()
+    assert np.abs(g["gprim0"] - o["gprim0"]).max() <= 1e-10 * np.abs(o["gprim0"]).max()
+
+
+def test_adjoint_fp32_against_fp64_finite_differences():
+    """FP32 forward and adjoint against FP64 central differences (h = 1e-6)
+    of the FP64 GPU forward, on a 64^2 cylinder with 16^2 velocities and 64
+    sectors over 40 steps (checkpoints every 10): every sector temperature and
+    the Mach number within 1e-4 of the largest finite-difference gradient."""
+    def J(tw=None, mach=2.0):
+        cfg = W.cylinder_adjoint(nx=64, nv=16, nseg=64, mach=mach, steps=40)
+        if tw is not None:
+            cfg["Tw_seg"] = tw
+        s = dvm.Solver(cfg, dvm.FP64)
+        s.init_maxwellian()
+        s.step(41)
+        v = s.history(1)["Fx"][0]          # force of the state after 40 steps
+        s.close()
+        return v, cfg
+    J0, cfg = J()
+    g = gpu_adjoint(cfg, dvm.FP32, 40, 10)
+    assert abs(g["J"] - J0) <= 1e-5 * abs(J0)
+    h = 1e-6
+    tw = cfg["Tw_seg"].copy()
+    fd = np.zeros(64)
+    for s_ in range(64):
+        tp, tm = tw.copy(), tw.copy()
+        tp[s_] += h
+        tm[s_] -= h
+        fd[s_] = (J(tp)[0] - J(tm)[0]) / (2 * h)
+    fdm = (J(mach=2.0 + h)[0] - J(mach=2.0 - h)[0]) / (2 * h)
+    scale = max(np.abs(fd).max(), abs(fdm))
+    assert np.abs(g["gTw"] - fd).max() <= 1e-4 * scale, np.abs(g["gTw"] - fd).max() / scale
+    assert abs(g["gmach"] - fdm) <= 1e-4 * scale
+
+
+def test_adjoint_errors():
+    cfg = W.base2d(16, 16, 4, 4.0)
+    s = dvm.Solver(cfg, dvm.FP64)
+    s.init_maxwellian()
+    with pytest.raises(dvm.DVMError) as e:
+        s.drag_adjoint(3, 2)
+    assert e.value.code == dvm.ERR_UNSUPPORTED
+    s.close()
+    cfg = W.base3d(8, 4, 4.0, shape=3, ra=0.2)
+    s = dvm.Solver(cfg, dvm.FP64)
+    s.init_maxwellian()
+    with pytest.raises(dvm.DVMError) as e:
+        s.drag_adjoint(3, 2)
+    assert e.value.code == dvm.ERR_UNSUPPORTED
+    s.close()
