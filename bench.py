@@ -180,6 +180,44 @@ def cpu_baseline(cfg, budget_s: float = 20.0, max_steps: int = 4):
                       f"{el:.1f} s"}
 
 
+def adjoint_cost(precision_fp32: bool = True):
+    """Cost of the drag gradient at the adjoint workload (256^2 cylinder, 32^2
+    velocities, 64 wall sectors, 200 steps, checkpoints every 20): device time
+    of the plain forward run, of the checkpointed forward and of the reverse
+    sweep (recomputation and transposed steps)."""
+    import torch
+    from paper_1503_04544_gb300 import dvm
+    from paper_1503_04544_gb300 import workloads as W
+    cfg = W.cylinder_adjoint(nx=256, nv=32, nseg=64, steps=200)
+    prec = dvm.FP32 if precision_fp32 else dvm.FP64
+    # a dedicated stream: the library enqueues on it and the events below are
+    # recorded on it
+    stream = torch.cuda.Stream()
+    s = dvm.Solver(cfg, prec, stream=stream.cuda_stream)
+    s.init_maxwellian()
+    s.step(3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    s.init_maxwellian()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step_async(200)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1)
+    s.init_maxwellian()
+    out = s.drag_adjoint(200, 20)
+    s.close()
+    return {"workload": cfg["name"], "steps": 200, "checkpoint_every": 20,
+            "precision": "fp32" if precision_fp32 else "fp64",
+            "ms_forward": ms_fwd, "ms_checkpointed_forward": out["ms_forward"],
+            "ms_reverse": out["ms_reverse"],
+            "reverse_over_forward": out["ms_reverse"] / ms_fwd,
+            "gradient_over_forward": (out["ms_forward"] + out["ms_reverse"]) / ms_fwd,
+            "note": "reverse = recomputation from checkpoints + transposed steps; "
+                    "gradient = checkpointed forward + reverse"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -206,6 +244,7 @@ def main():
     ap.add_argument("--workload", default="cylinder")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the drag-gradient cost measurement")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = DEFAULT_STEPS.get(args.workload, 2000)
@@ -327,6 +366,8 @@ def main():
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(cfg)
+        if world == 1 and args.workload == "cylinder" and not args.no_adjoint:
+            line["adjoint"] = adjoint_cost(prec == dvm.FP32)
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:

@@ -166,28 +166,32 @@ __global__ void __launch_bounds__(256) k_adj_mu(AdjArgs a, const T *lam, T *mucv
     }
 }
 
-// Relaxation through the moments, per control volume (warp per master
-// cell): with G = F - b R + r (Feq - F), r = dt rho / tau0, the moment
-// sensitivities S = d/d(rho, rho u, E) of sum_p mu r Feq + mu (Feq - F) dt/tau0
-// drho.  aux[m] = (r, S0, S1, S2, S3).
+// Relaxation through the moments, per control volume (one thread per master
+// cell, 32 consecutive cells along x per warp, vector loads of each velocity
+// group): with G = F - b R + r (Feq - F), r = dt rho / tau0, the moment
+// sensitivities S = d/d(rho, rho u, E) of sum_p mu r Feq + mu (Feq - F)
+// dt/tau0 drho.  aux[m] = (r, S0, S1, S2, S3).
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const T *lam, const T *mucv, T *aux)
+__global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const T *part, int S, const T *lam,
+                                                   const T *mucv, T *aux)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Grid2D &g = a.g;
-    const long m = (long)blockIdx.x * 8 + warp;
-    if (m >= (long)g.nx * g.ny) return;
-    if (a.master[m] != (int32_t)m) return;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int m = j * g.nx + i;
+    if (a.master[m] != m) return;
+    constexpr int W = Vec<T>::W;
     const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
-    const long pc = pcell(g, m) * Vec<T>::W;
+    const long pc = nbr(g, i, j) * W;
+    // moments of F^n: the partial sums the forward step read ([S][4][nc])
+    const long nc = (long)g.nx * g.ny;
     Acc<T> s0, s1, s2, s3;
-    for (int p = lane; p < g.nv; p += 32) {
-        const VCoef<T> vc = ld_coef(vt + p);
-        const T fv = f[ebase<T>(g, 0, p) + pc], gv = f[ebase<T>(g, 1, p) + pc];
-        s0.add(fv); s1.add(vc.vx * fv); s2.add(vc.vy * fv);
-        s3.add(T(0.5) * (vc.vx * vc.vx + vc.vy * vc.vy) * fv + gv);
+    for (int q = 0; q < S; ++q) {
+        s0.merge(part[((long)q * 4 + 0) * nc + m], T(0));
+        s1.merge(part[((long)q * 4 + 1) * nc + m], T(0));
+        s2.merge(part[((long)q * 4 + 2) * nc + m], T(0));
+        s3.merge(part[((long)q * 4 + 3) * nc + m], T(0));
     }
-    s0.warp_reduce(); s1.warp_reduce(); s2.warp_reduce(); s3.warp_reduce();
     const T dv = pick<T>(g.dv_f, g.dv);
     const T rho = s0.value() * dv, ux = s1.value() / s0.value(), uy = s2.value() / s0.value();
     const T E = s3.value() * dv;
@@ -195,33 +199,47 @@ __global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const 
     const T dtt = pick<T>(g.dt_tau0_f, g.dt_tau0);
     const T r = dtt * rho;
     const T A = rho / (T(2.0 * kPi) * tmp), i2T = T(1) / (T(2) * tmp);
+    const int cx = a.cvx[m];
     Acc<T> q0, q1, q2, q3, qr;
-    for (int p = lane; p < g.nv; p += 32) {
-        const VCoef<T> vc = ld_coef(vt + p);
-        const T ax = vc.vx - ux, ay = vc.vy - uy, a2 = ax * ax + ay * ay;
-        const T M = A * dexp(-a2 * i2T);
-        const T mf = mu_of<T>(a, lam, mucv, (int)m, 0, p), mg = mu_of<T>(a, lam, mucv, (int)m, 1, p);
-        const T fv = f[ebase<T>(g, 0, p) + pc], gv = f[ebase<T>(g, 1, p) + pc];
-        // dM/d(rho, ux, uy, T) and d(T/2 M)/d(...)
-        const T d0 = M / rho, d1 = M * ax / tmp, d2 = M * ay / tmp, d3 = M * (a2 * i2T / tmp - T(1) / tmp);
-        const T h = tmp / T(2);
-        q0.add(r * (mf * d0 + mg * h * d0));
-        q1.add(r * (mf * d1 + mg * h * d1));
-        q2.add(r * (mf * d2 + mg * h * d2));
-        q3.add(r * (mf * d3 + mg * (M / T(2) + h * d3)));
-        qr.add((mf * (M - fv) + mg * (h * M - gv)) * dtt);
+    for (int p = 0; p < g.nvp; p += W) {
+        T fv[W], gv[W], mf[W], mg[W];
+        vld<T>(reinterpret_cast<const typename Vec<T>::type *>(f + ebase<T>(g, 0, p) + pc), fv);
+        vld<T>(reinterpret_cast<const typename Vec<T>::type *>(f + ebase<T>(g, 1, p) + pc), gv);
+        if (cx >= 0) {
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                mf[e] = mucv[((long)cx * 2) * g.nvp + p + e];
+                mg[e] = mucv[((long)cx * 2 + 1) * g.nvp + p + e];
+            }
+        } else {
+            vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 0, p) + pc), mf);
+            vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 1, p) + pc), mg);
+        }
+        T t0 = 0, t1 = 0, t2 = 0, t3 = 0, tr = 0;
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const VCoef<T> vc = ld_coef(vt + p + e);
+            const T ax = vc.vx - ux, ay = vc.vy - uy, a2 = ax * ax + ay * ay;
+            const T M = A * dexp(-a2 * i2T);
+            // dM/d(rho, ux, uy, T) and d(T/2 M)/d(...)
+            const T d0 = M / rho, d1 = M * ax / tmp, d2 = M * ay / tmp, d3 = M * (a2 * i2T / tmp - T(1) / tmp);
+            const T h = tmp / T(2);
+            t0 += mf[e] * d0 + mg[e] * h * d0;
+            t1 += mf[e] * d1 + mg[e] * h * d1;
+            t2 += mf[e] * d2 + mg[e] * h * d2;
+            t3 += mf[e] * d3 + mg[e] * (M / T(2) + h * d3);
+            tr += mf[e] * (M - fv[e]) + mg[e] * (h * M - gv[e]);
+        }
+        q0.add(r * t0); q1.add(r * t1); q2.add(r * t2); q3.add(r * t3); qr.add(tr * dtt);
     }
-    q0.warp_reduce(); q1.warp_reduce(); q2.warp_reduce(); q3.warp_reduce(); qr.warp_reduce();
-    if (lane == 0) {
-        const T sp0 = q0.value() + qr.value(), sp1 = q1.value(), sp2 = q2.value(), sp3 = q3.value();
-        const T S0 = sp0 - sp1 * ux / rho - sp2 * uy / rho +
-                     sp3 * (T(-2) * E / (rho * rho) + T(2) * (ux * ux + uy * uy) / rho) / T(3);
-        const T S1 = sp1 / rho - sp3 * T(2) * ux / (T(3) * rho);
-        const T S2 = sp2 / rho - sp3 * T(2) * uy / (T(3) * rho);
-        const T S3 = sp3 * T(2) / (T(3) * rho);
-        T *o = aux + 5 * m;
-        o[0] = r; o[1] = S0; o[2] = S1; o[3] = S2; o[4] = S3;
-    }
+    const T sp0 = q0.value() + qr.value(), sp1 = q1.value(), sp2 = q2.value(), sp3 = q3.value();
+    const T S0 = sp0 - sp1 * ux / rho - sp2 * uy / rho +
+                 sp3 * (T(-2) * E / (rho * rho) + T(2) * (ux * ux + uy * uy) / rho) / T(3);
+    const T S1 = sp1 / rho - sp3 * T(2) * ux / (T(3) * rho);
+    const T S2 = sp2 / rho - sp3 * T(2) * uy / (T(3) * rho);
+    const T S3 = sp3 * T(2) / (T(3) * rho);
+    T *o = aux + 5 * (long)m;
+    o[0] = r; o[1] = S0; o[2] = S1; o[3] = S2; o[4] = S3;
 }
 
 // Sum over the faces along one axis whose stencil reads position (ci, cj) of
@@ -229,7 +247,7 @@ __global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const 
 // times the flux derivative at that stencil slot.  The faces are those
 // between columns ii and ii + 1 for ii = c - 2 .. c + 1 along the axis; a
 // slot counts when its value comes from the target (cell or ghost).
-template <typename T>
+template <typename T, bool ALIASFREE>
 __device__ T gather_axis(const AdjArgs &a, const T *f, const T *lam, const T *mucv, int axis, int ti, int tj,
                          Loc target, int comp, int p, T v, T nu)
 {
@@ -277,31 +295,30 @@ __device__ T gather_axis(const AdjArgs &a, const T *f, const T *lam, const T *mu
         }
         T d[4];
         face_flux_d<T>(L, v, nu, fv[0], fv[1], fv[2], fv[3], lim, d);
-        for (int t = 0; t < 4; ++t) {
-            if (d[t] == T(0)) continue;
-            const Loc l = locate(g, si[t], sj[t]);
-            if (l.cell == target.cell && l.side == target.side && l.q == target.q) acc += Wf * d[t];
+        if (ALIASFREE) {
+            // away from the sides only the slot at the cell's own position reads it
+            acc += Wf * d[c - ii + 1];
+        } else {
+            for (int t = 0; t < 4; ++t) {
+                if (d[t] == T(0)) continue;
+                const Loc l = locate(g, si[t], sj[t]);
+                if (l.cell == target.cell && l.side == target.side && l.q == target.q) acc += Wf * d[t];
+            }
         }
     }
     return acc;
 }
 
-// nu of every (cell, velocity): relaxation terms for control-volume masters and
-// the face-flux transposes; written to lam_out (the wall and fusion kernels
-// complete it).
+// nu of one (cell, velocity): relaxation terms for control-volume masters and
+// the face-flux transposes (generic: any cell, any boundary).
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a, const T *f, const T *lam, const T *mucv,
-                                                    const T *aux, T *lam_out)
+__device__ __forceinline__ void gather_generic(const AdjArgs &a, const T *f, const T *lam, const T *mucv, const T *aux,
+                                               T *lam_out, int k, int p)
 {
     const Grid2D &g = a.g;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long nc = (long)g.nx * g.ny;
-    if (t >= nc * g.nvp) return;
-    const int p = (int)(t % g.nvp);
-    const int k = (int)(t / g.nvp);
     constexpr int W = Vec<T>::W;
     const long pk = pcell(g, k) * W;
-    if (a.master[k] < 0) {
+    if (a.master[k] < 0 || p >= g.nv) {
         lam_out[ebase<T>(g, 0, p) + pk] = T(0);
         lam_out[ebase<T>(g, 1, p) + pk] = T(0);
         return;
@@ -314,18 +331,176 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a, const T *f, const
     const T dv = pick<T>(g.dv_f, g.dv);
     for (int comp = 0; comp < 2; ++comp) {
         T nu = 0;
-        if (p < g.nv) {
-            if (ismaster) {
-                const T *o = aux + 5 * (long)k;
-                nu += mu_of<T>(a, lam, mucv, k, comp, p) * (T(1) - o[0]);
-                nu += comp == 0 ? dv * (o[1] + o[2] * vc.vx + o[3] * vc.vy + o[4] * T(0.5) * (vc.vx * vc.vx + vc.vy * vc.vy))
-                                : dv * o[4];
-            }
-            nu += gather_axis<T>(a, f, lam, mucv, 0, ki, kj, me, comp, p, vc.vx, vc.nux);
-            nu += gather_axis<T>(a, f, lam, mucv, 1, ki, kj, me, comp, p, vc.vy, vc.nuy);
+        if (ismaster) {
+            const T *o = aux + 5 * (long)k;
+            nu += mu_of<T>(a, lam, mucv, k, comp, p) * (T(1) - o[0]);
+            nu += comp == 0 ? dv * (o[1] + o[2] * vc.vx + o[3] * vc.vy + o[4] * T(0.5) * (vc.vx * vc.vx + vc.vy * vc.vy))
+                            : dv * o[4];
+        }
+        if (ki >= 2 && ki < g.nx - 2 && kj >= 2 && kj < g.ny - 2) {
+            nu += gather_axis<T, true>(a, f, lam, mucv, 0, ki, kj, me, comp, p, vc.vx, vc.nux);
+            nu += gather_axis<T, true>(a, f, lam, mucv, 1, ki, kj, me, comp, p, vc.vy, vc.nuy);
+        } else {
+            nu += gather_axis<T, false>(a, f, lam, mucv, 0, ki, kj, me, comp, p, vc.vx, vc.nux);
+            nu += gather_axis<T, false>(a, f, lam, mucv, 1, ki, kj, me, comp, p, vc.vy, vc.nuy);
         }
         lam_out[ebase<T>(g, comp, p) + pk] = nu;
     }
+}
+
+// Generic gather over the listed cells (those near walls, merged control
+// volumes or non-periodic sides), one thread per (listed cell, velocity).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_gather_list(AdjArgs a, const T *f, const T *lam, const T *mucv,
+                                                         const T *aux, const int32_t *list, int nlist, T *lam_out)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nlist * a.g.nvp) return;
+    gather_generic<T>(a, f, lam, mucv, aux, lam_out, list[t / a.g.nvp], (int)(t % a.g.nvp));
+}
+
+// Transpose of the face fluxes along one axis for a cell deep in the gas
+// (all cells within three along the axis are plain gas cells and no
+// non-periodic side is within reach): with W_f = b (mu_B - mu_A) L and the
+// limited face value phi = F_up + k mm(...) the cell receives, for v > 0,
+//   W(k+1/2) (1 + k (db - da))_{k+1/2} + W(k-1/2) k da_{k-1/2} - W(k+3/2) k db_{k+3/2}
+// and the mirror image for v < 0 (da, db: the branch the forward minmod takes).
+// f2m..f2p: F at offsets -2..+2, l2m..l2p: mu at offsets -2..+2; bl = b L v.
+template <typename T, bool MUSCL>
+__device__ __forceinline__ T adj_axis(T bl, T nu, T f2m, T f1m, T f0, T f1p, T f2p, T l2m, T l1m, T l0, T l1p, T l2p)
+{
+    if (bl == T(0)) return T(0);
+    if (!MUSCL) return bl > T(0) ? bl * (l1p - l0) : bl * (l0 - l1m);
+    const T k = T(0.5) * (T(1) - nu);
+    T da, db, r;
+    if (bl > T(0)) {
+        minmod_d(f1p - f0, f0 - f1m, da, db);            // face k+1/2
+        r = (l1p - l0) * (T(1) + k * (db - da));
+        minmod_d(f0 - f1m, f1m - f2m, da, db);           // face k-1/2
+        r += (l0 - l1m) * (k * da);
+        minmod_d(f2p - f1p, f1p - f0, da, db);           // face k+3/2
+        r -= (l2p - l1p) * (k * db);
+    } else {
+        minmod_d(f1p - f0, f0 - f1m, da, db);            // face k-1/2 (k is its B)
+        r = (l0 - l1m) * (T(1) - k * (db - da));
+        minmod_d(f2p - f1p, f1p - f0, da, db);           // face k+1/2 (k is its A)
+        r += (l1p - l0) * (k * db);
+        minmod_d(f0 - f1m, f1m - f2m, da, db);           // face k-3/2 (k is its BB)
+        r -= (l1m - l2m) * (k * da);
+    }
+    return bl * r;
+}
+
+// Fast gather for the cells flagged in fast[] (one thread per cell, 32
+// consecutive cells along x per warp, vector loads of each velocity group),
+// relaxation terms included; other cells are left to k_adj_gather_list.
+template <typename T, bool MUSCL>
+__global__ void __launch_bounds__(256) k_adj_gather_fast(AdjArgs a, const T *f, const T *lam, const T *aux,
+                                                         const uint8_t *fast, T *lam_out)
+{
+    const Grid2D &g = a.g;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k = j * g.nx + i;
+    if (!fast[k]) return;
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
+    const long pc = nbr(g, i, j);
+    const long sy = g.nx + 4;
+    const T *o = aux + 5 * (long)k;
+    const T r = o[0], S0 = o[1], S1 = o[2], S2 = o[3], S3 = o[4];
+    const T dv = pick<T>(g.dv_f, g.dv);
+    const T *bown = reinterpret_cast<const T *>(a.bown);
+    const T b = bown[k];
+    const T Lx = (T)g.dy, Ly = (T)g.dx;
+    for (int p = 0; p < g.nvp; p += W) {
+        T vx[W], vy[W], nux[W], nuy[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const VCoef<T> vc = ld_coef(vt + p + e);
+            vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
+        }
+        for (int comp = 0; comp < 2; ++comp) {
+            const V *F = reinterpret_cast<const V *>(f + ebase<T>(g, comp, p));
+            const V *Lm = reinterpret_cast<const V *>(lam + ebase<T>(g, comp, p));
+            T c0[W], fx[4][W], fy[4][W], l0[W], lx[4][W], ly[4][W];
+            vld<T>(F + pc, c0);
+            vld<T>(Lm + pc, l0);
+            const long offx[4] = {-2, -1, 1, 2};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                vld<T>(F + pc + offx[t], fx[t]);
+                vld<T>(F + pc + offx[t] * sy, fy[t]);
+                vld<T>(Lm + pc + offx[t], lx[t]);
+                vld<T>(Lm + pc + offx[t] * sy, ly[t]);
+            }
+            T out[W];
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                T nu = l0[e] * (T(1) - r);
+                nu += comp == 0 ? dv * (S0 + S1 * vx[e] + S2 * vy[e] + S3 * T(0.5) * (vx[e] * vx[e] + vy[e] * vy[e]))
+                                : dv * S3;
+                if (p + e < g.nv) {
+                    nu += adj_axis<T, MUSCL>(b * Lx * vx[e], nux[e], fx[0][e], fx[1][e], c0[e], fx[2][e], fx[3][e],
+                                             lx[0][e], lx[1][e], l0[e], lx[2][e], lx[3][e]);
+                    nu += adj_axis<T, MUSCL>(b * Ly * vy[e], nuy[e], fy[0][e], fy[1][e], c0[e], fy[2][e], fy[3][e],
+                                             ly[0][e], ly[1][e], l0[e], ly[2][e], ly[3][e]);
+                } else {
+                    nu = T(0);
+                }
+                out[e] = nu;
+            }
+            vst<T>(reinterpret_cast<V *>(lam_out + ebase<T>(g, comp, p)) + pc, out);
+        }
+    }
+}
+
+// Cells eligible for the fast gather: plain gas cells whose neighbours within
+// three cells along each axis are plain gas cells, at least two cells from
+// every side (no boundary pad then aliases the cell, and the faces it reads
+// separate interior cells; the adjoint buffers carry no boundary padding).
+__global__ void k_adj_fastmask(Grid2D g, const uint8_t *flags, uint8_t *fast)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long)g.nx * g.ny) return;
+    int i, j;
+    cell_ij(g, k, i, j);
+    bool ok = (flags[k] & kPlain) != 0 && i >= 2 && i < g.nx - 2 && j >= 2 && j < g.ny - 2;
+    for (int d = -3; d <= 3 && ok; ++d) {
+        const int ii = i + d, jj = j + d;
+        // neighbours beyond a side are boundary values: the face masks of the
+        // forward step count them as gas
+        ok = (ii < 0 || ii >= g.nx || (flags[(long)j * g.nx + ii] & kPlain)) &&
+             (jj < 0 || jj >= g.ny || (flags[(long)jj * g.nx + i] & kPlain));
+    }
+    fast[k] = ok ? 1 : 0;
+}
+
+// Compact list of the cells not eligible for the fast gather (one block).
+__global__ void __launch_bounds__(1024) k_adj_slowlist(long nc, const uint8_t *fast, int32_t *list, int *count)
+{
+    __shared__ int wsum[32];
+    __shared__ int tot;
+    int n = 0;
+    for (long base = 0; base < nc; base += blockDim.x) {
+        const long k = base + threadIdx.x;
+        const bool slow = k < nc && !fast[k];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const unsigned bal = __ballot_sync(0xffffffffu, slow);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { const int v = wsum[w]; wsum[w] = acc; acc += v; }
+            tot = acc;
+        }
+        __syncthreads();
+        if (slow) list[n + wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = (int32_t)k;
+        n += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = n;
 }
 
 struct WallAdj {
@@ -484,8 +659,8 @@ __global__ void __launch_bounds__(256) k_adj_ghost(AdjArgs a, const T *f, const 
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
             const VCoef<T> vc = ld_coef(vt + p);
             const T v = axis == 0 ? vc.vx : vc.vy, nu = axis == 0 ? vc.nux : vc.nuy;
-            const double s0 = (double)gather_axis<T>(a, f, lam, mucv, axis, ti, tj, target, 0, p, v, nu);
-            const double s1 = (double)gather_axis<T>(a, f, lam, mucv, axis, ti, tj, target, 1, p, v, nu);
+            const double s0 = (double)gather_axis<T, false>(a, f, lam, mucv, axis, ti, tj, target, 0, p, v, nu);
+            const double s1 = (double)gather_axis<T, false>(a, f, lam, mucv, axis, ti, tj, target, 1, p, v, nu);
             const double ax = (double)vc.vx - st[1], ay = (double)vc.vy - st[2], a2 = ax * ax + ay * ay;
             const double M = st[0] / (2.0 * kPi * st[4]) * exp(-a2 / (2.0 * st[4]));
             const double d0 = M / st[0], d1 = M * ax / st[4], d2 = M * ay / st[4];
@@ -505,41 +680,43 @@ __global__ void __launch_bounds__(256) k_adj_ghost(AdjArgs a, const T *f, const 
     }
 }
 
-// dJ/d(rho, ux, uy, uz, T) of a Maxwellian initial state from lambda^0 (warp
-// per cell).
+// dJ/d(rho, ux, uy, uz, T) of a Maxwellian initial state from lambda^0 (one
+// thread per cell, 32 consecutive cells along x per warp, FP64 sums).
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_init(Grid2D g, const T *lam, const double *prim, const int8_t *type,
                                                   double *gout)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long k = (long)blockIdx.x * 8 + warp;
-    if (k >= (long)g.nx * g.ny) return;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const long k = (long)j * g.nx + i;
     const double *st = prim + 5 * k;
     double o0 = 0, o1 = 0, o2 = 0, o3 = 0;
     if (type[k] != DVM_SOLID && st[0] > 0) {
-        const long pk = pcell(g, k) * Vec<T>::W;
-        for (int p = lane; p < g.nv; p += 32) {
-            const double vx = g.vxmin + (p % g.nvx) * g.dvx, vy = g.vymin + (p / g.nvx) * g.dvy;
-            const double ax = vx - st[1], ay = vy - st[2], a2 = ax * ax + ay * ay;
-            const double M = st[0] / (2.0 * kPi * st[4]) * exp(-a2 / (2.0 * st[4]));
-            const double d0 = M / st[0], d1 = M * ax / st[4], d2 = M * ay / st[4];
-            const double d3 = M * (a2 / (2.0 * st[4] * st[4]) - 1.0 / st[4]);
-            const double h = st[4] / 2.0;
-            const double l0 = (double)lam[ebase<T>(g, 0, p) + pk], l1 = (double)lam[ebase<T>(g, 1, p) + pk];
-            o0 += l0 * d0 + l1 * h * d0;
-            o1 += l0 * d1 + l1 * h * d1;
-            o2 += l0 * d2 + l1 * h * d2;
-            o3 += l0 * d3 + l1 * (M / 2.0 + h * d3);
+        constexpr int W = Vec<T>::W;
+        const long pk = nbr(g, i, j) * W;
+        for (int p0 = 0; p0 < g.nvp; p0 += W) {
+            T l0[W], l1[W];
+            vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 0, p0) + pk), l0);
+            vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 1, p0) + pk), l1);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const int p = p0 + e;
+                if (p >= g.nv) break;
+                const double vx = g.vxmin + (p % g.nvx) * g.dvx, vy = g.vymin + (p / g.nvx) * g.dvy;
+                const double ax = vx - st[1], ay = vy - st[2], a2 = ax * ax + ay * ay;
+                const double M = st[0] / (2.0 * kPi * st[4]) * exp(-a2 / (2.0 * st[4]));
+                const double d0 = M / st[0], d1 = M * ax / st[4], d2 = M * ay / st[4];
+                const double d3 = M * (a2 / (2.0 * st[4] * st[4]) - 1.0 / st[4]);
+                const double h = st[4] / 2.0;
+                o0 += (double)l0[e] * d0 + (double)l1[e] * h * d0;
+                o1 += (double)l0[e] * d1 + (double)l1[e] * h * d1;
+                o2 += (double)l0[e] * d2 + (double)l1[e] * h * d2;
+                o3 += (double)l0[e] * d3 + (double)l1[e] * (M / 2.0 + h * d3);
+            }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        o0 += __shfl_xor_sync(0xffffffffu, o0, o); o1 += __shfl_xor_sync(0xffffffffu, o1, o);
-        o2 += __shfl_xor_sync(0xffffffffu, o2, o); o3 += __shfl_xor_sync(0xffffffffu, o3, o);
-    }
-    if (lane == 0) {
-        double *o = gout + 5 * k;
-        o[0] = o0; o[1] = o1; o[2] = o2; o[3] = 0; o[4] = o3;
-    }
+    double *o = gout + 5 * k;
+    o[0] = o0; o[1] = o1; o[2] = o2; o[3] = 0; o[4] = o3;
 }
 
 inline unsigned nba(long n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -552,9 +729,13 @@ struct AdjWork {
     int32_t *cvx = nullptr, *rev = nullptr;
     double *gtw = nullptr, *jwall = nullptr, *gbc = nullptr, *ginit = nullptr;
     int32_t *wsec = nullptr;
+    uint8_t *fast = nullptr;                         // cells of the fast gather
+    int32_t *slow = nullptr, *nslow_d = nullptr;     // the other cells
+    int nslow = 0;
     void *fin = nullptr, *finpart = nullptr;         // F^N and its partial moments
     void *scratch_part = nullptr;                    // partial moments written by a tape fusion
-    std::vector<void *> ckpt, ckpt_part, tape;
+    std::vector<void *> ckpt, ckpt_part, tape, ptape;
+    std::vector<CUtensorMap> tmaps;                  // TMA descriptors of the tape buffers
     int cap = 0;
 };
 
@@ -564,9 +745,11 @@ void release(AdjWork &w)
     cudaFree(w.mucv); cudaFree(w.aux); cudaFree(w.bown); cudaFree(w.cvx); cudaFree(w.rev);
     cudaFree(w.gtw); cudaFree(w.jwall); cudaFree(w.gbc); cudaFree(w.ginit); cudaFree(w.wsec);
     cudaFree(w.fin); cudaFree(w.finpart); cudaFree(w.scratch_part);
+    cudaFree(w.fast); cudaFree(w.slow); cudaFree(w.nslow_d);
     for (void *p : w.ckpt) cudaFree(p);
     for (void *p : w.ckpt_part) cudaFree(p);
     for (void *p : w.tape) cudaFree(p);
+    for (void *p : w.ptape) cudaFree(p);
     w = AdjWork();
 }
 
@@ -587,14 +770,21 @@ AdjArgs adj_args(dvm_ctx *c, const AdjWork &w)
 
 // One reverse step: lam_in = lambda^{n+1}, f = F^n (device layout) -> lam_out.
 template <typename T>
-cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *lam_in, T *lam_out)
+cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, const T *lam_in, T *lam_out)
 {
     const AdjArgs a = adj_args(c, w);
     const int cvgrid = 4 * 152;
     T *mucv = (T *)w.mucv, *aux = (T *)w.aux;
     k_adj_mu<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_in, mucv);
-    k_adj_relax<T><<<nba(c->nc, 8), 256, 0, c->stream>>>(a, f, lam_in, mucv, aux);
-    k_adj_gather<T><<<nba((long)c->nc * c->nvp, 256), 256, 0, c->stream>>>(a, f, lam_in, mucv, aux, lam_out);
+    const dim3 cgrid(nba(c->nx, 32), nba(c->ny, 8)), cblock(32, 8);
+    k_adj_relax<T><<<cgrid, cblock, 0, c->stream>>>(a, f, part, c->S, lam_in, mucv, aux);
+    if (c->scheme == DVM_MUSCL)
+        k_adj_gather_fast<T, true><<<cgrid, cblock, 0, c->stream>>>(a, f, lam_in, aux, w.fast, lam_out);
+    else
+        k_adj_gather_fast<T, false><<<cgrid, cblock, 0, c->stream>>>(a, f, lam_in, aux, w.fast, lam_out);
+    if (w.nslow > 0)
+        k_adj_gather_list<T><<<nba((long)w.nslow * c->nvp, 256), 256, 0, c->stream>>>(a, f, lam_in, mucv, aux, w.slow,
+                                                                                      w.nslow, lam_out);
     k_adj_wall<T><<<cvgrid, 256, 0, c->stream>>>(a, f, lam_in, mucv, lam_out, w.gtw, w.jwall, w.wsec, 0);
     k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_out);
     const int nside[4] = {c->ny, c->ny, c->nx, c->nx};
@@ -603,7 +793,7 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *lam_in, T 
         if (c->bc[s] == DVM_BC_MAXWELLIAN && c->d_bcstate[s])
             k_adj_ghost<T><<<nside[s], 256, 0, c->stream>>>(a, f, lam_in, mucv, s, nside[s], c->d_bcstate[s],
                                                             w.gbc + 5L * s * nmax);
-    c->launches += 5;
+    c->launches += 6;
     return cudaGetLastError();
 }
 
@@ -635,6 +825,9 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMalloc(&w.fin, bytes));
         AC(cudaMalloc(&w.finpart, partb));
         AC(cudaMalloc(&w.scratch_part, partb));
+        AC(cudaMalloc(&w.fast, c->nc));
+        AC(cudaMalloc(&w.slow, sizeof(int32_t) * c->nc));
+        AC(cudaMalloc(&w.nslow_d, sizeof(int)));
         w.bytes_state = bytes;
         w.cap = c->list_cap;
     }
@@ -646,10 +839,19 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         w.ckpt_part.push_back(q);
     }
     while ((int)w.tape.size() < K) {
-        void *p = nullptr;
+        void *p = nullptr, *q = nullptr;
         AC(cudaMalloc(&p, bytes));
+        AC(cudaMalloc(&q, partb));
         w.tape.push_back(p);
+        w.ptape.push_back(q);
+        CUtensorMap m;
+        const int rc = encode_tensor_map2d(c, p, &m);
+        if (rc != DVM_OK) return rc;
+        w.tmaps.push_back(m);
     }
+    // the tape buffers take the boundary padding (Maxwellian ghosts) of the state
+    for (int t = 0; t < K; ++t)
+        AC(cudaMemcpyAsync(w.tape[t], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     AC(cudaMemsetAsync(w.gbc, 0, sizeof(double) * 5 * 4 * nmax, c->stream));
     AC(cudaMemsetAsync(w.gtw, 0, sizeof(double) * c->list_cap, c->stream));
     {
@@ -657,6 +859,10 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         k_adj_rev<<<nba(c->list_cap, 256), 256, 0, c->stream>>>(c->spec_list, c->counts, c->list_cap, w.rev);
         k_adj_setup<T><<<nba(c->nc, 256), 256, 0, c->stream>>>(g, c->master, c->flags, w.rev, (const CvInfo *)c->cvinfo,
                                                                 w.cvx, (T *)w.bown);
+        k_adj_fastmask<<<nba(c->nc, 256), 256, 0, c->stream>>>(g, c->flags, w.fast);
+        k_adj_slowlist<<<1, 1024, 0, c->stream>>>(c->nc, w.fast, w.slow, w.nslow_d);
+        AC(cudaMemcpyAsync(&w.nslow, w.nslow_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        AC(cudaStreamSynchronize(c->stream));
     }
     cudaEvent_t ev[3];
     for (int q = 0; q < 3; ++q) AC(cudaEventCreate(&ev[q]));
@@ -684,24 +890,38 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     k_adj_wall<T><<<cvgrid, 256, 0, c->stream>>>(a, (const T *)c->f[c->cur], lamA, (const T *)w.mucv, lamA, w.gtw,
                                                  w.jwall, w.wsec, 1);
     k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lamA);
-    // reverse sweep, segment by segment: recompute the segment onto the tape,
-    // then apply the transposed steps backwards
+    // reverse sweep, segment by segment: recompute the segment onto the tape
+    // (each step writes the next tape buffer), then apply the transposed steps
+    // backwards
+    void *f_orig[2] = {c->f[0], c->f[1]};
+    const CUtensorMap tm_orig[2] = {c->tmap[0], c->tmap[1]};
+    const int cur_orig = c->cur;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-        const int n0 = sgi * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
-        AC(cudaMemcpyAsync(c->f[c->cur], w.ckpt[sgi], bytes, cudaMemcpyDeviceToDevice, c->stream));
+        const int n0 = sgi * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps, len = n1 - n0;
+        AC(cudaMemcpyAsync(w.tape[0], w.ckpt[sgi], bytes, cudaMemcpyDeviceToDevice, c->stream));
         AC(cudaMemcpyAsync(c->part[c->cur], w.ckpt_part[sgi], partb, cudaMemcpyDeviceToDevice, c->stream));
-        c->need_fusion = (sgi == 0) ? fuse0 : false;
-        for (int n = n0; n < n1; ++n) {
-            AC(cudaMemcpyAsync(w.tape[n - n0], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
-            // the step linearises around the fused state (members of merged
-            // control volumes are equal after every step, not necessarily in
-            // the initial state)
-            if (n == 0 && fuse0) AC(fusion2d(c, w.tape[0], w.scratch_part));
-            if (n + 1 < n1) AC(step2d(c));
+        // the step linearises around the fused state (members of merged control
+        // volumes are equal after every step, not necessarily in the initial state)
+        if (sgi == 0 && fuse0) AC(fusion2d(c, w.tape[0], c->part[c->cur]));
+        c->need_fusion = false;
+        for (int t = 0; t < len; ++t) {
+            if (t + 1 < len) {
+                c->f[c->cur] = w.tape[t];
+                c->f[1 - c->cur] = w.tape[t + 1];
+                c->tmap[c->cur] = w.tmaps[t];
+                c->tmap[1 - c->cur] = w.tmaps[t + 1];
+                AC(step2d(c));
+                AC(cudaMemcpyAsync(w.ptape[t], c->part[1 - c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
+            } else {
+                AC(cudaMemcpyAsync(w.ptape[t], c->part[c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
+            }
         }
-        for (int n = n1 - 1; n >= n0; --n) {
-            AC(adjoint_step<T>(c, w, (const T *)w.tape[n - n0], lamA, lamB));
-            T *t = lamA; lamA = lamB; lamB = t;
+        c->f[0] = f_orig[0]; c->f[1] = f_orig[1];
+        c->tmap[0] = tm_orig[0]; c->tmap[1] = tm_orig[1];
+        c->cur = cur_orig;
+        for (int t = len - 1; t >= 0; --t) {
+            AC(adjoint_step<T>(c, w, (const T *)w.tape[t], (const T *)w.ptape[t], lamA, lamB));
+            T *tt = lamA; lamA = lamB; lamB = tt;
         }
     }
     AC(cudaEventRecord(ev[2], c->stream));
@@ -721,7 +941,8 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     }
     if (gprim0) {
         if (!c->have_prim0) { set_error("dvm_drag_adjoint: gprim0 needs a state set by dvm_init_maxwellian"); return DVM_ERR_STATE; }
-        k_adj_init<T><<<nba(c->nc, 8), 256, 0, c->stream>>>(grid2d(c), lamA, c->d_prim0, c->geo[c->gcur].type, w.ginit);
+        k_adj_init<T><<<dim3(nba(c->nx, 32), nba(c->ny, 8)), dim3(32, 8), 0, c->stream>>>(grid2d(c), lamA, c->d_prim0,
+                                                                                      c->geo[c->gcur].type, w.ginit);
         AC(cudaMemcpyAsync(gprim0, w.ginit, sizeof(double) * 5 * c->nc, cudaMemcpyDeviceToHost, c->stream));
     }
     // leave the context at F^N, as after nsteps forward steps

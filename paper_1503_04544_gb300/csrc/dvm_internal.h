@@ -205,6 +205,7 @@ cudaError_t halo2d(dvm_ctx *c, int buf);                         // periodic / z
 cudaError_t members2d(dvm_ctx *c, bool moving);                  // control-volume records
 cudaError_t timing_mark(dvm_ctx *c, int which);   // 0: before, 1: after the bulk kernel
 int make_tensor_maps2d(dvm_ctx *c);                // TMA descriptors of f[0], f[1]
+int encode_tensor_map2d(dvm_ctx *c, void *buf, CUtensorMap *map);
 // adjoint (dvm_adjoint2d.cu)
 int drag_adjoint2d(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double *const *gbc, double *gprim0,
                    double *ms_forward, double *ms_reverse);

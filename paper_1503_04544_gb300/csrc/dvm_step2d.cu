@@ -1072,10 +1072,9 @@ cudaError_t step2d_t(dvm_ctx *c)
 
 }  // namespace
 
-// TMA descriptors of the two state buffers: a 3D view (x: padded cells of a
-// row times the W velocities of a group, y: padded rows, z: group and
-// component) of each slab; the box is the bulk kernel's tile with its halo.
-int make_tensor_maps2d(dvm_ctx *c)
+// TMA descriptor of a state buffer in the device layout (any buffer with the
+// layout of f[0], f[1]).
+int encode_tensor_map2d(dvm_ctx *c, void *buf, CUtensorMap *map)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -1094,14 +1093,23 @@ int make_tensor_maps2d(dvm_ctx *c)
     const cuuint32_t box[3] = {(cuuint32_t)kTileX * W, (cuuint32_t)kTileY, 2};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = c->prec == DVM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    CUresult r = encode(map, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        return DVM_ERR_CUDA;
+    }
+    return DVM_OK;
+}
+
+// TMA descriptors of the two state buffers: a 3D view (x: padded cells of a
+// row times the W velocities of a group, y: padded rows, z: group and
+// component) of each slab; the box is the bulk kernel's tile with its halo.
+int make_tensor_maps2d(dvm_ctx *c)
+{
     for (int b = 0; b < 2; ++b) {
-        CUresult r = encode(&c->tmap[b], dt, 3, c->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-            return DVM_ERR_CUDA;
-        }
+        const int rc = encode_tensor_map2d(c, c->f[b], &c->tmap[b]);
+        if (rc != DVM_OK) return rc;
     }
     return DVM_OK;
 }
