@@ -1,11 +1,14 @@
 """Run one of the benchmark problems through libdvm and report what it computed.
 
     python -m paper_1503_04544_gb300.run --workload sphere --cells 40 --nv 16 --steps 5
+    python -m paper_1503_04544_gb300.run --workload adjoint --steps 20 --checkpoint-every 10
 
 Builds the problem (optionally at other grid and velocity sizes), installs
 the Maxwellian initial state, advances ``--steps`` steps and prints one JSON
 line with the force and torque of the last step, the total mass and the
-measured milliseconds per step.  Every computation runs in the CUDA library.
+measured milliseconds per step.  ``--workload adjoint`` (the cylinder with 64
+wall sectors) instead computes the drag after ``--steps`` steps and its
+gradient by the discrete adjoint.  Every computation runs in the CUDA library.
 """
 from __future__ import annotations
 
@@ -26,21 +29,33 @@ def problem(name: str, cells: int | None, nv: int | None, scheme: int) -> dict:
         return W.periodic_bump(nx=cells or 32, nv=nv or 16)
     if name == "sphere":
         return W.sphere_mach15(n=cells or 96, nv=nv or 20, scheme=scheme)
+    if name == "adjoint":
+        cfg = W.cylinder_adjoint(nx=cells or 256, nv=nv or 32, nseg=64)
+        cfg["scheme"] = scheme
+        return cfg
     raise SystemExit(f"unknown workload {name}")
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "ellipse", "bump", "sphere"])
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "ellipse", "bump", "sphere", "adjoint"])
     ap.add_argument("--cells", type=int, default=None, help="cells per axis (default: the problem's)")
     ap.add_argument("--nv", type=int, default=None, help="velocities per axis (default: the problem's)")
     ap.add_argument("--scheme", type=int, default=1, choices=[0, 1], help="0 upwind, 1 MUSCL-minmod")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--checkpoint-every", type=int, default=20)
     args = ap.parse_args(argv)
     cfg = problem(args.workload, args.cells, args.nv, args.scheme)
     s = dvm.Solver(cfg, dvm.FP32 if args.precision == "fp32" else dvm.FP64)
     s.init_maxwellian()
+    if args.workload == "adjoint":
+        out = s.drag_adjoint(args.steps, args.checkpoint_every)
+        print(json.dumps({"workload": cfg["name"], "steps": args.steps, "J": out["J"],
+                          "dJ_dTw_max": float(abs(out["gTw"]).max()), "ms_forward": out["ms_forward"],
+                          "ms_reverse": out["ms_reverse"]}))
+        s.close()
+        return
     s.step(1)
     t0 = time.perf_counter()
     s.step(args.steps)
