@@ -8,20 +8,24 @@
 // explicit update with relaxation (Eqs. BGKDD, BoundaryDDv, FluxDD,
 // ExSchemeDD) -> distribution (Eq. UpdateDD).  Its transposed Jacobian is
 // applied to lambda^{n+1} in the reverse order:
-//   k_adj_mu      transpose of the distribution: mu = sum of lambda over the
-//                 members of each cut/merged control volume;
-//   k_adj_relax   per control volume: the relaxation through the moments
-//                 (sums over the velocities of mu dM/d(rho, u, T));
-//   k_adj_gather  per (cell, velocity): relaxation terms and the face-flux
-//                 transposes of every face whose stencil reads the cell (the
-//                 limiter derivative is the one of the branch the forward
-//                 step takes), boundary pads folded back onto the cells they
-//                 copy;
-//   k_adj_wall    per wall cell: the diffuse flux and the wall density
-//                 coupling (Eq. BoundaryDDv), and dJ/dT_w;
-//   k_adj_fuseT   transpose of the fusion of merged control volumes;
-//   k_adj_ghost   sensitivities of the Maxwellian ghost cells, chained to
-//                 (rho, u, T) of each inflow cell.
+//   k_adj_mu       transpose of the distribution: mu = sum of lambda over the
+//                  members of each cut/merged control volume;
+//   k_adj_relax    per control volume and velocity split: the relaxation
+//                  through the moments (sums over the velocities of
+//                  mu dM/d(rho, u, T)), finished by k_adj_relax_fin;
+//   k_adj_gather_* per (cell, velocity): relaxation terms and the face-flux
+//                  transposes of every face whose stencil reads the cell;
+//                  the limiter derivative is the one of the branch the
+//                  forward step took (recorded by the recomputation for
+//                  the cells deep in the gas, re-derived from F^n elsewhere);
+//   k_adj_wall     per wall cell: the diffuse flux and the wall density
+//                  coupling (Eq. BoundaryDDv), and dJ/dT_w;
+//   k_adj_pads     the boundary pads: the step reads them but does not
+//                  update them, so their sensitivities are gathered like a
+//                  cell's and folded back onto the cells they copy
+//                  (periodic, zero-gradient) or chained to (rho, u, T) of
+//                  the Maxwellian ghost state;
+//   k_adj_fuseT    transpose of the fusion of merged control volumes.
 // The driver dvm_drag_adjoint checkpoints the forward run every K steps,
 // recomputes each segment onto a device tape and sweeps it backwards.
 #include <cstring>
@@ -49,36 +53,8 @@ struct AdjArgs {
     const void *bown;         // dt / S of the cell's control volume (state precision), 0 if none
     int muscl;
     double omega;
+    int *err;                 // device error flags (kErrTimeout)
 };
-
-struct Loc { int cell, side, q; };
-
-// Source of the padded value at cell (i, j) within two cells of the grid: an
-// interior cell, or a Maxwellian ghost (side, index along the side).
-__device__ __forceinline__ Loc locate(const Grid2D &g, int i, int j)
-{
-    Loc L{-1, -1, -1};
-    if (i < 0) {
-        if (g.bc[0] == DVM_BC_PERIODIC) i += g.nx;
-        else if (g.bc[0] == DVM_BC_MAXWELLIAN) { L.side = 0; L.q = j; return L; }
-        else i = 0;
-    } else if (i >= g.nx) {
-        if (g.bc[1] == DVM_BC_PERIODIC) i -= g.nx;
-        else if (g.bc[1] == DVM_BC_MAXWELLIAN) { L.side = 1; L.q = j; return L; }
-        else i = g.nx - 1;
-    }
-    if (j < 0) {
-        if (g.bc[2] == DVM_BC_PERIODIC) j += g.ny;
-        else if (g.bc[2] == DVM_BC_MAXWELLIAN) { L.side = 2; L.q = i; return L; }
-        else j = 0;
-    } else if (j >= g.ny) {
-        if (g.bc[3] == DVM_BC_PERIODIC) j -= g.ny;
-        else if (g.bc[3] == DVM_BC_MAXWELLIAN) { L.side = 3; L.q = i; return L; }
-        else j = g.ny - 1;
-    }
-    L.cell = j * g.nx + i;
-    return L;
-}
 
 // minmod with the derivative of the branch taken (ties: the second argument).
 template <typename T>
@@ -166,24 +142,16 @@ __global__ void __launch_bounds__(256) k_adj_mu(AdjArgs a, const T *lam, T *mucv
     }
 }
 
-// Relaxation through the moments, per control volume (one thread per master
-// cell, 32 consecutive cells along x per warp, vector loads of each velocity
-// group): with G = F - b R + r (Feq - F), r = dt rho / tau0, the moment
-// sensitivities S = d/d(rho, rho u, E) of sum_p mu r Feq + mu (Feq - F)
-// dt/tau0 drho.  aux[m] = (r, S0, S1, S2, S3).
+// Relaxation through the moments, per control volume and velocity split
+// (one thread per master cell, 32 consecutive cells along x per warp, vector
+// loads of each velocity group; split blockIdx.z takes every gridDim.z-th
+// block of groups): with G = F - b R + r (Feq - F), r = dt rho / tau0, the
+// partial sums over the split of mu r dFeq/d(rho, ux, uy, T) and of
+// mu (Feq - F) dt/tau0, rpart[z][5][nc].
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const T *part, int S, const T *lam,
-                                                   const T *mucv, T *aux)
+__device__ __forceinline__ void cell_moments(const Grid2D &g, const T *part, int S, long m, T &rho, T &ux, T &uy,
+                                             T &E, T &tmp)
 {
-    const Grid2D &g = a.g;
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    const int m = j * g.nx + i;
-    if (a.master[m] != m) return;
-    constexpr int W = Vec<T>::W;
-    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
-    const long pc = nbr(g, i, j) * W;
-    // moments of F^n: the partial sums the forward step read ([S][4][nc])
     const long nc = (long)g.nx * g.ny;
     Acc<T> s0, s1, s2, s3;
     for (int q = 0; q < S; ++q) {
@@ -193,15 +161,41 @@ __global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const 
         s3.merge(part[((long)q * 4 + 3) * nc + m], T(0));
     }
     const T dv = pick<T>(g.dv_f, g.dv);
-    const T rho = s0.value() * dv, ux = s1.value() / s0.value(), uy = s2.value() / s0.value();
-    const T E = s3.value() * dv;
-    const T tmp = (T(2) * E / rho - (ux * ux + uy * uy)) / T(3);
+    rho = s0.value() * dv;
+    ux = s1.value() / s0.value();
+    uy = s2.value() / s0.value();
+    E = s3.value() * dv;
+    tmp = (T(2) * E / rho - (ux * ux + uy * uy)) / T(3);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const T *part, int S, const T *lam,
+                                                   const T *mucv, T *rpart)
+{
+    const Grid2D &g = a.g;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int m = j * g.nx + i;
+    if (a.master[m] != m) return;
+    constexpr int W = Vec<T>::W;
+    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
+    const long pc = nbr(g, i, j) * W;
+    const long nc = (long)g.nx * g.ny;
+    T rho, ux, uy, E, tmp;
+    cell_moments<T>(g, part, S, m, rho, ux, uy, E, tmp);
     const T dtt = pick<T>(g.dt_tau0_f, g.dt_tau0);
     const T r = dtt * rho;
-    const T A = rho / (T(2.0 * kPi) * tmp), i2T = T(1) / (T(2) * tmp);
+    const T A = rho / (T(2.0 * kPi) * tmp), i2T = T(1) / (T(2) * tmp), c2 = T(kLog2e) * i2T;
+    const T h = tmp / T(2);
     const int cx = a.cvx[m];
-    Acc<T> q0, q1, q2, q3, qr;
-    for (int p = 0; p < g.nvp; p += W) {
+    const int gps = (g.ngrp + gridDim.z - 1) / gridDim.z;
+    const int q0 = blockIdx.z * gps, q1 = min(q0 + gps, g.ngrp);
+    // with u = mu_f + T/2 mu_g: dM/drho = M / rho, dM/du = M (v - u) / T,
+    // dM/dT = M (|v - u|^2 / (2T) - 1) / T, d(T/2 M) = T/2 dM + M/2 dT; the
+    // factors 1/rho and 1/T are applied once after the sums
+    Acc<T> a0, a1, a2, a3, ar;
+    for (int q = q0; q < q1; ++q) {
+        const int p = q * W;
         T fv[W], gv[W], mf[W], mg[W];
         vld<T>(reinterpret_cast<const typename Vec<T>::type *>(f + ebase<T>(g, 0, p) + pc), fv);
         vld<T>(reinterpret_cast<const typename Vec<T>::type *>(f + ebase<T>(g, 1, p) + pc), gv);
@@ -215,65 +209,86 @@ __global__ void __launch_bounds__(256) k_adj_relax(AdjArgs a, const T *f, const 
             vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 0, p) + pc), mf);
             vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 1, p) + pc), mg);
         }
-        T t0 = 0, t1 = 0, t2 = 0, t3 = 0, tr = 0;
+        T t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, tr = 0;
 #pragma unroll
         for (int e = 0; e < W; ++e) {
             const VCoef<T> vc = ld_coef(vt + p + e);
             const T ax = vc.vx - ux, ay = vc.vy - uy, a2 = ax * ax + ay * ay;
-            const T M = A * dexp(-a2 * i2T);
-            // dM/d(rho, ux, uy, T) and d(T/2 M)/d(...)
-            const T d0 = M / rho, d1 = M * ax / tmp, d2 = M * ay / tmp, d3 = M * (a2 * i2T / tmp - T(1) / tmp);
-            const T h = tmp / T(2);
-            t0 += mf[e] * d0 + mg[e] * h * d0;
-            t1 += mf[e] * d1 + mg[e] * h * d1;
-            t2 += mf[e] * d2 + mg[e] * h * d2;
-            t3 += mf[e] * d3 + mg[e] * (M / T(2) + h * d3);
+            const T M = A * dexp2(-a2 * c2);
+            const T mu = M * (mf[e] + h * mg[e]);
+            t0 += mu;
+            t1 += mu * ax;
+            t2 += mu * ay;
+            t3 += mu * (a2 * i2T - T(1));
+            t4 += mg[e] * M;
             tr += mf[e] * (M - fv[e]) + mg[e] * (h * M - gv[e]);
         }
-        q0.add(r * t0); q1.add(r * t1); q2.add(r * t2); q3.add(r * t3); qr.add(tr * dtt);
+        a0.add(t0); a1.add(t1); a2.add(t2); a3.add(t3 + t4 * T(0.5) * tmp); ar.add(tr);
     }
+    const T rr = r / rho, rt = r / tmp;
+    T *o = rpart + (long)blockIdx.z * 5 * nc + m;
+    o[0] = rr * a0.value(); o[nc] = rt * a1.value(); o[2 * nc] = rt * a2.value(); o[3 * nc] = rt * a3.value();
+    o[4 * nc] = dtt * ar.value();
+}
+
+// Sum of the splits and the chain to the conserved moments:
+// aux[m] = (r, S0, S1, S2, S3), S = d/d(rho, rho ux, rho uy, E).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_relax_fin(AdjArgs a, const T *part, int S, const T *rpart, int Z,
+                                                       T *aux)
+{
+    const Grid2D &g = a.g;
+    const long m = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nc = (long)g.nx * g.ny;
+    if (m >= nc || a.master[m] != m) return;
+    T rho, ux, uy, E, tmp;
+    cell_moments<T>(g, part, S, m, rho, ux, uy, E, tmp);
+    Acc<T> q0, q1, q2, q3, qr;
+    for (int z = 0; z < Z; ++z) {
+        const T *o = rpart + (long)z * 5 * nc + m;
+        q0.merge(o[0], T(0)); q1.merge(o[nc], T(0)); q2.merge(o[2 * nc], T(0)); q3.merge(o[3 * nc], T(0));
+        qr.merge(o[4 * nc], T(0));
+    }
+    const T r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
     const T sp0 = q0.value() + qr.value(), sp1 = q1.value(), sp2 = q2.value(), sp3 = q3.value();
     const T S0 = sp0 - sp1 * ux / rho - sp2 * uy / rho +
                  sp3 * (T(-2) * E / (rho * rho) + T(2) * (ux * ux + uy * uy) / rho) / T(3);
     const T S1 = sp1 / rho - sp3 * T(2) * ux / (T(3) * rho);
     const T S2 = sp2 / rho - sp3 * T(2) * uy / (T(3) * rho);
     const T S3 = sp3 * T(2) / (T(3) * rho);
-    T *o = aux + 5 * (long)m;
+    T *o = aux + 5 * m;
     o[0] = r; o[1] = S0; o[2] = S1; o[3] = S2; o[4] = S3;
 }
 
-// Sum over the faces along one axis whose stencil reads position (ci, cj) of
-// the weight W_f (adjoint of the two control volumes the face separates)
-// times the flux derivative at that stencil slot.  The faces are those
-// between columns ii and ii + 1 for ii = c - 2 .. c + 1 along the axis; a
-// slot counts when its value comes from the target (cell or ghost).
-template <typename T, bool ALIASFREE>
+// Sum over the faces along one axis whose stencil reads padded position
+// (ti, tj) -- a cell, or a boundary pad along the axis -- of the weight W_f
+// (adjoint of the two control volumes the face separates) times the flux
+// derivative at that stencil slot.  The faces are those between positions
+// ii and ii + 1 along the axis for ii = c - 2 .. c + 1.  The step reads the
+// pads but does not update them: a pad on either side of a face adds no
+// weight, and a face between two pads none at all.
+template <typename T>
 __device__ T gather_axis(const AdjArgs &a, const T *f, const T *lam, const T *mucv, int axis, int ti, int tj,
-                         Loc target, int comp, int p, T v, T nu)
+                         int comp, int p, T v, T nu)
 {
     const Grid2D &g = a.g;
     constexpr int W = Vec<T>::W;
     const int n = axis == 0 ? g.nx : g.ny;
-    const bool per = g.bc[axis == 0 ? 0 : 2] == DVM_BC_PERIODIC;
     const int c = axis == 0 ? ti : tj;
     const long eb = ebase<T>(g, comp, p);
     const T *bown = reinterpret_cast<const T *>(a.bown);
     T acc = 0;
     for (int ii = c - 2; ii <= c + 1; ++ii) {
-        int fi = ii;
-        if (per) { if (fi < 0) fi += n; else if (fi >= n) fi -= n; }
-        else if (fi < -1 || fi > n - 1) continue;       // not a face of any cell
-        // the face between A (column fi) and B (column fi + 1) along the axis
-        int ia = axis == 0 ? fi : ti, ja = axis == 0 ? tj : fi;
-        int ib = axis == 0 ? fi + 1 : ti, jb = axis == 0 ? tj : fi + 1;
-        if (ib >= g.nx) ib -= g.nx;                     // periodic wrap of B
-        if (jb >= g.ny) jb -= g.ny;
-        const bool aint = per || fi >= 0, bint = per || fi + 1 <= n - 1;
+        const bool aint = ii >= 0 && ii < n, bint = ii + 1 >= 0 && ii + 1 < n;
+        if (!aint && !bint) continue;
+        // the face between A (position ii) and B (position ii + 1) along the axis
+        const int ia = axis == 0 ? ii : ti, ja = axis == 0 ? tj : ii;
+        const int ib = axis == 0 ? ii + 1 : ti, jb = axis == 0 ? tj : ii + 1;
         const int A = aint ? ja * g.nx + ia : -1;
         const int B = bint ? jb * g.nx + ib : -1;
         // length and limiter flag as the forward step uses them
         T L;
-        bool lim = false;
+        bool lim;
         if (A >= 0) {
             L = axis == 0 ? (T)a.G.lx[(long)ja * (g.nx + 1) + ia + 1] : (T)a.G.ly[(long)(ja + 1) * g.nx + ia];
             lim = a.muscl && ((a.flags[A] >> kMaskShift) & (axis == 0 ? 2 : 8));
@@ -285,32 +300,22 @@ __device__ T gather_axis(const AdjArgs &a, const T *f, const T *lam, const T *mu
         const T Wf = (A >= 0 ? -bown[A] * mu_of<T>(a, lam, mucv, A, comp, p) : T(0)) +
                      (B >= 0 ? bown[B] * mu_of<T>(a, lam, mucv, B, comp, p) : T(0));
         if (Wf == T(0)) continue;
-        // stencil AA, A, B, BB in padded coordinates around the face
+        // stencil AA, A, B, BB (positions ii - 1 .. ii + 2, within the padding)
         T fv[4];
-        int si[4], sj[4];
+#pragma unroll
         for (int t = 0; t < 4; ++t) {
-            si[t] = axis == 0 ? fi - 1 + t : ti;
-            sj[t] = axis == 0 ? tj : fi - 1 + t;
-            fv[t] = f[eb + nbr(g, si[t], sj[t]) * W];
+            const int pos = ii - 1 + t;
+            fv[t] = f[eb + nbr(g, axis == 0 ? pos : ti, axis == 0 ? tj : pos) * W];
         }
         T d[4];
         face_flux_d<T>(L, v, nu, fv[0], fv[1], fv[2], fv[3], lim, d);
-        if (ALIASFREE) {
-            // away from the sides only the slot at the cell's own position reads it
-            acc += Wf * d[c - ii + 1];
-        } else {
-            for (int t = 0; t < 4; ++t) {
-                if (d[t] == T(0)) continue;
-                const Loc l = locate(g, si[t], sj[t]);
-                if (l.cell == target.cell && l.side == target.side && l.q == target.q) acc += Wf * d[t];
-            }
-        }
+        acc += Wf * d[c - ii + 1];
     }
     return acc;
 }
 
-// nu of one (cell, velocity): relaxation terms for control-volume masters and
-// the face-flux transposes (generic: any cell, any boundary).
+// nu of one (cell, velocity) of the generic list: relaxation terms for
+// control-volume masters and the face-flux transposes along both axes.
 template <typename T>
 __device__ __forceinline__ void gather_generic(const AdjArgs &a, const T *f, const T *lam, const T *mucv, const T *aux,
                                                T *lam_out, int k, int p)
@@ -326,7 +331,6 @@ __device__ __forceinline__ void gather_generic(const AdjArgs &a, const T *f, con
     const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p);
     int ki, kj;
     cell_ij(g, k, ki, kj);
-    const Loc me{k, -1, -1};
     const bool ismaster = a.master[k] == k;
     const T dv = pick<T>(g.dv_f, g.dv);
     for (int comp = 0; comp < 2; ++comp) {
@@ -337,19 +341,14 @@ __device__ __forceinline__ void gather_generic(const AdjArgs &a, const T *f, con
             nu += comp == 0 ? dv * (o[1] + o[2] * vc.vx + o[3] * vc.vy + o[4] * T(0.5) * (vc.vx * vc.vx + vc.vy * vc.vy))
                             : dv * o[4];
         }
-        if (ki >= 2 && ki < g.nx - 2 && kj >= 2 && kj < g.ny - 2) {
-            nu += gather_axis<T, true>(a, f, lam, mucv, 0, ki, kj, me, comp, p, vc.vx, vc.nux);
-            nu += gather_axis<T, true>(a, f, lam, mucv, 1, ki, kj, me, comp, p, vc.vy, vc.nuy);
-        } else {
-            nu += gather_axis<T, false>(a, f, lam, mucv, 0, ki, kj, me, comp, p, vc.vx, vc.nux);
-            nu += gather_axis<T, false>(a, f, lam, mucv, 1, ki, kj, me, comp, p, vc.vy, vc.nuy);
-        }
+        nu += gather_axis<T>(a, f, lam, mucv, 0, ki, kj, comp, p, vc.vx, vc.nux);
+        nu += gather_axis<T>(a, f, lam, mucv, 1, ki, kj, comp, p, vc.vy, vc.nuy);
         lam_out[ebase<T>(g, comp, p) + pk] = nu;
     }
 }
 
-// Generic gather over the listed cells (those near walls, merged control
-// volumes or non-periodic sides), one thread per (listed cell, velocity).
+// Generic gather over the listed cells (those near cut cells and merged
+// control volumes), one thread per (listed cell, velocity).
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_gather_list(AdjArgs a, const T *f, const T *lam, const T *mucv,
                                                          const T *aux, const int32_t *list, int nlist, T *lam_out)
@@ -359,133 +358,210 @@ __global__ void __launch_bounds__(256) k_adj_gather_list(AdjArgs a, const T *f, 
     gather_generic<T>(a, f, lam, mucv, aux, lam_out, list[t / a.g.nvp], (int)(t % a.g.nvp));
 }
 
-// Transpose of the face fluxes along one axis for a cell deep in the gas
-// (all cells within three along the axis are plain gas cells and no
-// non-periodic side is within reach): with W_f = b (mu_B - mu_A) L and the
-// limited face value phi = F_up + k mm(...) the cell receives, for v > 0,
-//   W(k+1/2) (1 + k (db - da))_{k+1/2} + W(k-1/2) k da_{k-1/2} - W(k+3/2) k db_{k+3/2}
-// and the mirror image for v < 0 (da, db: the branch the forward minmod takes).
-// f2m..f2p: F at offsets -2..+2, l2m..l2p: mu at offsets -2..+2; bl = b L v.
+// Transpose of the face fluxes along one axis for a cell deep in the gas, in
+// the upwind direction u of the velocity: the face downwind of position m
+// carries |v| L phi_m from m to m + u, phi_m = F_m + k mm(F_{m+u} - F_m,
+// F_m - F_{m-u}) with k = (1 - nu)/2, and its adjoint weight is b |v| L
+// (lambda_{m+u} - lambda_m) = nu (lambda_{m+u} - lambda_m) between plain
+// cells (b = dt/(dx dy)).  The cell receives the weights of the faces
+// downwind of k - u, k, k + u times the derivative of their phi with respect
+// to F_k; sm, sk, sp are the recorded branches of those three faces (1: the
+// first minmod argument, 2: the second, 0: none or first order).
+// lm, l0, lp, lq: lambda at k - u, k, k + u, k + 2u (0 at pads).
 template <typename T, bool MUSCL>
-__device__ __forceinline__ T adj_axis(T bl, T nu, T f2m, T f1m, T f0, T f1p, T f2p, T l2m, T l1m, T l0, T l1p, T l2p)
+__device__ __forceinline__ T adj_axis(T kap, T lm, T l0, T lp, T lq, uint32_t sm, uint32_t sk, uint32_t sp)
 {
-    if (bl == T(0)) return T(0);
-    if (!MUSCL) return bl > T(0) ? bl * (l1p - l0) : bl * (l0 - l1m);
-    const T k = T(0.5) * (T(1) - nu);
-    T da, db, r;
-    if (bl > T(0)) {
-        minmod_d(f1p - f0, f0 - f1m, da, db);            // face k+1/2
-        r = (l1p - l0) * (T(1) + k * (db - da));
-        minmod_d(f0 - f1m, f1m - f2m, da, db);           // face k-1/2
-        r += (l0 - l1m) * (k * da);
-        minmod_d(f2p - f1p, f1p - f0, da, db);           // face k+3/2
-        r -= (l2p - l1p) * (k * db);
-    } else {
-        minmod_d(f1p - f0, f0 - f1m, da, db);            // face k-1/2 (k is its B)
-        r = (l0 - l1m) * (T(1) - k * (db - da));
-        minmod_d(f2p - f1p, f1p - f0, da, db);           // face k+1/2 (k is its A)
-        r += (l1p - l0) * (k * db);
-        minmod_d(f0 - f1m, f1m - f2m, da, db);           // face k-3/2 (k is its BB)
-        r -= (l1m - l2m) * (k * da);
-    }
-    return bl * r;
+    const T wk = lp - l0;
+    if (!MUSCL) return wk;
+    T corr = T(0);
+    if (sk & 1u) corr -= wk;
+    else if (sk & 2u) corr += wk;
+    if (sm & 1u) corr += l0 - lm;
+    if (sp & 2u) corr -= lq - lp;
+    return wk + kap * corr;
 }
 
-// Fast gather for the cells flagged in fast[] (one thread per cell, 32
-// consecutive cells along x per warp, vector loads of each velocity group),
-// relaxation terms included; other cells are left to k_adj_gather_list.
+// Shared-memory stages of the fast gather: lambda of both components of one
+// velocity group over the block's cells and a two-cell halo, and the branch
+// words of the same tile (row of 36 words), 128-byte aligned.
+constexpr int kAdjStages = 4;
+constexpr int kAdjLamBytes = 2 * kTileY * kTileX * 16;
+constexpr int kAdjBitsBytes = ((kTileY * kTileX * 4 + 127) / 128) * 128;
+constexpr int kAdjStageBytes = kAdjLamBytes + kAdjBitsBytes;
+
+// Fast gather for the cells flagged in fast[] (one thread per cell, 32 x
+// kRows cells per block, the velocity groups split over blockIdx.z),
+// relaxation terms included.  Reads lambda^{n+1} and, for MUSCL, the limiter
+// branches recorded for F^n, not F^n itself.  Each group's tile of lambda
+// (both components) and of the branch words arrives by TMA in a
+// kAdjStages-deep shared-memory ring on "full" mbarriers; each warp releases
+// a stage on its "empty" mbarrier, and thread 0 refills a stage only after
+// all warps released it.  Every wait is bounded (on timeout the kernel sets
+// kErrTimeout and goes on).  Other cells are left to k_adj_gather_list.
 template <typename T, bool MUSCL>
-__global__ void __launch_bounds__(256) k_adj_gather_fast(AdjArgs a, const T *f, const T *lam, const T *aux,
-                                                         const uint8_t *fast, T *lam_out)
+__global__ void __launch_bounds__(32 * kRows, 2) k_adj_gather_fast(AdjArgs a, const __grid_constant__ CUtensorMap lmap,
+                                                                   const __grid_constant__ CUtensorMap bmap,
+                                                                   const int8_t *gsign, const T *aux,
+                                                                   const uint8_t *fast, T *lam_out)
 {
-    const Grid2D &g = a.g;
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    const int k = j * g.nx + i;
-    if (!fast[k]) return;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
-    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
-    const long pc = nbr(g, i, j);
-    const long sy = g.nx + 4;
-    const T *o = aux + 5 * (long)k;
-    const T r = o[0], S0 = o[1], S1 = o[2], S2 = o[3], S3 = o[4];
-    const T dv = pick<T>(g.dv_f, g.dv);
-    const T *bown = reinterpret_cast<const T *>(a.bown);
-    const T b = bown[k];
-    const T Lx = (T)g.dy, Ly = (T)g.dx;
-    for (int p = 0; p < g.nvp; p += W) {
-        T vx[W], vy[W], nux[W], nuy[W];
-#pragma unroll
-        for (int e = 0; e < W; ++e) {
-            const VCoef<T> vc = ld_coef(vt + p + e);
-            vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
+    constexpr uint32_t kBytes = MUSCL ? kAdjLamBytes + kTileY * kTileX * 4 : kAdjLamBytes;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kAdjStages * kAdjStageBytes);
+    uint64_t *empty = full + kAdjStages;
+    const Grid2D &g = a.g;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kRows;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool inside = i < g.nx && j < g.ny;
+    const long k = inside ? (long)j * g.nx + i : 0;
+    const bool isfast = inside && fast[k];
+    const int gps = (g.ngrp + gridDim.z - 1) / gridDim.z;
+    const int g0 = blockIdx.z * gps, g1 = min(g0 + gps, g.ngrp);
+    const int ngr = max(g1 - g0, 0);
+    const auto issue = [&](int st, int q) {
+        unsigned char *dst = smem + (long)st * kAdjStageBytes;
+        mbar_expect_tx(&full[st], kBytes);
+        tma_load_3d(dst, &lmap, &full[st], i0 * W, j0, q * 2);
+        if (MUSCL) tma_load_3d(dst + kAdjLamBytes, &bmap, &full[st], i0, j0, q);
+    };
+    if (tid == 0) {
+        for (int st = 0; st < kAdjStages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], kRows);
         }
-        for (int comp = 0; comp < 2; ++comp) {
-            const V *F = reinterpret_cast<const V *>(f + ebase<T>(g, comp, p));
-            const V *Lm = reinterpret_cast<const V *>(lam + ebase<T>(g, comp, p));
-            T c0[W], fx[4][W], fy[4][W], l0[W], lx[4][W], ly[4][W];
-            vld<T>(F + pc, c0);
-            vld<T>(Lm + pc, l0);
-            const long offx[4] = {-2, -1, 1, 2};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                vld<T>(F + pc + offx[t], fx[t]);
-                vld<T>(F + pc + offx[t] * sy, fy[t]);
-                vld<T>(Lm + pc + offx[t], lx[t]);
-                vld<T>(Lm + pc + offx[t] * sy, ly[t]);
-            }
-            T out[W];
+        mbar_fence_init();
+        for (int st = 0; st < kAdjStages - 1 && st < ngr; ++st) issue(st, g0 + st);
+    }
+    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
+    T omr = 0, S0 = 0, S1 = 0, S2 = 0, S3 = 0;
+    if (isfast) {
+        const T *o = aux + 5 * k;
+        omr = T(1) - o[0]; S0 = o[1]; S1 = o[2]; S2 = o[3]; S3 = o[4];
+    }
+    const T dv = pick<T>(g.dv_f, g.dv);
+    const long pc = nbr(g, i, j);
+    const int c0 = (ty + 2) * kTileX + tx + 2;
+    __syncthreads();
+
+    for (int it = 0; it < ngr; ++it) {
+        const int q = g0 + it, st = it % kAdjStages;
+        if (tid == 0 && it + kAdjStages - 1 < ngr) {
+            const int kk = it + kAdjStages - 1, s2 = kk % kAdjStages;
+            if (kk >= kAdjStages && !mbar_wait(&empty[s2], (uint32_t)((kk / kAdjStages - 1) & 1)))
+                atomicExch(&a.err[kErrTimeout], 1);
+            issue(s2, g0 + kk);
+        }
+        if (!mbar_wait(&full[st], (uint32_t)((it / kAdjStages) & 1))) atomicExch(&a.err[kErrTimeout], 1);
+        if (isfast) {
+            const unsigned char *base = smem + (long)st * kAdjStageBytes;
+            const uint32_t *bt = reinterpret_cast<const uint32_t *>(base + kAdjLamBytes);
+            const int p = q * W;
+            T vx[W], vy[W], nux[W], nuy[W], rel0[W];
 #pragma unroll
             for (int e = 0; e < W; ++e) {
-                T nu = l0[e] * (T(1) - r);
-                nu += comp == 0 ? dv * (S0 + S1 * vx[e] + S2 * vy[e] + S3 * T(0.5) * (vx[e] * vx[e] + vy[e] * vy[e]))
-                                : dv * S3;
-                if (p + e < g.nv) {
-                    nu += adj_axis<T, MUSCL>(b * Lx * vx[e], nux[e], fx[0][e], fx[1][e], c0[e], fx[2][e], fx[3][e],
-                                             lx[0][e], lx[1][e], l0[e], lx[2][e], lx[3][e]);
-                    nu += adj_axis<T, MUSCL>(b * Ly * vy[e], nuy[e], fy[0][e], fy[1][e], c0[e], fy[2][e], fy[3][e],
-                                             ly[0][e], ly[1][e], l0[e], ly[2][e], ly[3][e]);
-                } else {
-                    nu = T(0);
-                }
-                out[e] = nu;
+                const VCoef<T> vc = ld_coef(vt + p + e);
+                vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
+                rel0[e] = dv * (S0 + S1 * vx[e] + S2 * vy[e] + S3 * T(0.5) * (vx[e] * vx[e] + vy[e] * vy[e]));
             }
-            vst<T>(reinterpret_cast<V *>(lam_out + ebase<T>(g, comp, p)) + pc, out);
+            const int sgx = gsign[2 * q], sgy = gsign[2 * q + 1];
+            uint32_t bo = 0, bxm = 0, bxp = 0, bym = 0, byp = 0;
+            if (MUSCL) {
+                bo = bt[c0]; bxm = bt[c0 - 1]; bxp = bt[c0 + 1]; bym = bt[c0 - kTileX]; byp = bt[c0 + kTileX];
+            }
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                const V *t = reinterpret_cast<const V *>(base) + comp * kTileY * kTileX;
+                T l0[W], out[W];
+                sld<T>(t + c0, l0);
+                if (sgx != 0 && sgy != 0) {
+                    // upwind direction uniform over the group
+                    const int ux = sgx > 0 ? 1 : -1, uy = sgy > 0 ? kTileX : -kTileX;
+                    T xm[W], xp[W], xq[W], ym[W], yp[W], yq[W];
+                    sld<T>(t + c0 + ux, xp);
+                    sld<T>(t + c0 + uy, yp);
+                    if (MUSCL) {
+                        sld<T>(t + c0 - ux, xm); sld<T>(t + c0 + 2 * ux, xq);
+                        sld<T>(t + c0 - uy, ym); sld<T>(t + c0 + 2 * uy, yq);
+                    }
+                    const uint32_t smx = sgx > 0 ? bxm : bxp, spx = sgx > 0 ? bxp : bxm;
+                    const uint32_t smy = sgy > 0 ? bym : byp, spy = sgy > 0 ? byp : bym;
+#pragma unroll
+                    for (int e = 0; e < W; ++e) {
+                        const int shx = ((comp * 2 + 0) * W + e) * 2, shy = ((comp * 2 + 1) * W + e) * 2;
+                        T nu = l0[e] * omr + (comp == 0 ? rel0[e] : dv * S3);
+                        nu += nux[e] * adj_axis<T, MUSCL>(T(0.5) * (T(1) - nux[e]), MUSCL ? xm[e] : T(0), l0[e],
+                                                          xp[e], MUSCL ? xq[e] : T(0), smx >> shx, bo >> shx,
+                                                          spx >> shx);
+                        nu += nuy[e] * adj_axis<T, MUSCL>(T(0.5) * (T(1) - nuy[e]), MUSCL ? ym[e] : T(0), l0[e],
+                                                          yp[e], MUSCL ? yq[e] : T(0), smy >> shy, bo >> shy,
+                                                          spy >> shy);
+                        out[e] = p + e < g.nv ? nu : T(0);
+                    }
+                } else {
+                    // per-element direction
+                    T x2m[W], x1m[W], x1p[W], x2p[W], y2m[W], y1m[W], y1p[W], y2p[W];
+                    sld<T>(t + c0 - 2, x2m); sld<T>(t + c0 - 1, x1m); sld<T>(t + c0 + 1, x1p); sld<T>(t + c0 + 2, x2p);
+                    sld<T>(t + c0 - 2 * kTileX, y2m); sld<T>(t + c0 - kTileX, y1m);
+                    sld<T>(t + c0 + kTileX, y1p); sld<T>(t + c0 + 2 * kTileX, y2p);
+#pragma unroll
+                    for (int e = 0; e < W; ++e) {
+                        const int shx = ((comp * 2 + 0) * W + e) * 2, shy = ((comp * 2 + 1) * W + e) * 2;
+                        const bool px = vx[e] >= T(0), py = vy[e] >= T(0);
+                        T nu = l0[e] * omr + (comp == 0 ? rel0[e] : dv * S3);
+                        nu += nux[e] * adj_axis<T, MUSCL>(T(0.5) * (T(1) - nux[e]), px ? x1m[e] : x1p[e], l0[e],
+                                                          px ? x1p[e] : x1m[e], px ? x2p[e] : x2m[e],
+                                                          (px ? bxm : bxp) >> shx, bo >> shx, (px ? bxp : bxm) >> shx);
+                        nu += nuy[e] * adj_axis<T, MUSCL>(T(0.5) * (T(1) - nuy[e]), py ? y1m[e] : y1p[e], l0[e],
+                                                          py ? y1p[e] : y1m[e], py ? y2p[e] : y2m[e],
+                                                          (py ? bym : byp) >> shy, bo >> shy, (py ? byp : bym) >> shy);
+                        out[e] = p + e < g.nv ? nu : T(0);
+                    }
+                }
+                vst<T>(reinterpret_cast<V *>(lam_out + ebase<T>(g, comp, p)) + pc, out);
+            }
         }
+        __syncwarp();
+        if (tx == 0) mbar_arrive(&empty[st]);
+    }
+    if (tid == 0) {
+        // every issued copy has landed before the block exits
+        for (int kk = max(ngr - kAdjStages, 0); kk < ngr; ++kk)
+            mbar_wait(&full[kk % kAdjStages], (uint32_t)((kk / kAdjStages) & 1));
     }
 }
 
 // Cells eligible for the fast gather: plain gas cells whose neighbours within
-// three cells along each axis are plain gas cells, at least two cells from
-// every side (no boundary pad then aliases the cell, and the faces it reads
-// separate interior cells; the adjoint buffers carry no boundary padding).
+// two cells along each axis are plain gas cells or boundary pads (a pad adds
+// no adjoint weight; the branch of a face between a pad and a plain cell is
+// recorded by that cell).
 __global__ void k_adj_fastmask(Grid2D g, const uint8_t *flags, uint8_t *fast)
 {
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long)g.nx * g.ny) return;
     int i, j;
     cell_ij(g, k, i, j);
-    bool ok = (flags[k] & kPlain) != 0 && i >= 2 && i < g.nx - 2 && j >= 2 && j < g.ny - 2;
-    for (int d = -3; d <= 3 && ok; ++d) {
+    bool ok = (flags[k] & kPlain) != 0;
+    for (int d = -2; d <= 2 && ok; ++d) {
         const int ii = i + d, jj = j + d;
-        // neighbours beyond a side are boundary values: the face masks of the
-        // forward step count them as gas
         ok = (ii < 0 || ii >= g.nx || (flags[(long)j * g.nx + ii] & kPlain)) &&
              (jj < 0 || jj >= g.ny || (flags[(long)jj * g.nx + i] & kPlain));
     }
     fast[k] = ok ? 1 : 0;
 }
 
-// Compact list of the cells not eligible for the fast gather (one block).
-__global__ void __launch_bounds__(1024) k_adj_slowlist(long nc, const uint8_t *fast, int32_t *list, int *count)
+// Compact list of the cells in a control volume that are not eligible for
+// the fast gather (one block); cells in no control volume keep lambda = 0.
+__global__ void __launch_bounds__(1024) k_adj_slowlist(long nc, const uint8_t *fast, const int32_t *master,
+                                                      int32_t *list, int *count)
 {
     __shared__ int wsum[32];
     __shared__ int tot;
     int n = 0;
     for (long base = 0; base < nc; base += blockDim.x) {
         const long k = base + threadIdx.x;
-        const bool slow = k < nc && !fast[k];
+        const bool slow = k < nc && !fast[k] && master[k] >= 0;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const unsigned bal = __ballot_sync(0xffffffffu, slow);
         if (lane == 0) wsum[warp] = __popc(bal);
@@ -533,28 +609,68 @@ __device__ __forceinline__ WallAdj wall_adj(const AdjArgs &a, long k)
     return w;
 }
 
+// Per wall cell, once per adjoint run (the body is fixed): the wall data,
+// and for every velocity leaving the gas (c < 0) the wall Maxwellian M1 =
+// M[1, u_w, T_w] and dM1/dT_w; with D = sum_{c<0} c M1 dv and dD/dT_w.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj *wadj, double2 *wm, double2 *wd,
+                                                      int32_t *wsec)
+{
+    __shared__ double red[8 * 2];
+    const Grid2D &g = a.g;
+    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
+    const double dv = g.dv;
+    for (int idx = blockIdx.x; idx < nw; idx += gridDim.x) {
+        const WallAdj w = wall_adj(a, a.wall_list[idx]);
+        const double cmw = 1.0 / (2.0 * kPi * w.Tw);
+        double den = 0, dD = 0;
+        for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
+            const VCoef<T> vc = ld_coef(vt + p);
+            const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
+            const double cp = ax * w.nwx + ay * w.nwy;
+            double m1 = 0, dm1 = 0;
+            if (cp < 0) {
+                const double a2 = ax * ax + ay * ay;
+                m1 = cmw * exp(-a2 / (2.0 * w.Tw));
+                dm1 = m1 * (a2 / (2.0 * w.Tw * w.Tw) - 1.0 / w.Tw);
+                den += cp * m1 * dv;
+                dD += cp * dm1 * dv;
+            }
+            wm[(long)idx * g.nv + p] = make_double2(m1, dm1);
+        }
+        den = block_sum(den, red);
+        dD = block_sum(dD, red + 8);
+        if (threadIdx.x == 0) {
+            wadj[idx] = w;
+            wd[idx] = make_double2(den, dD);
+            wsec[idx] = w.sector;
+        }
+        __syncthreads();
+    }
+}
+
 // Wall cells: the diffuse flux lw (min(c,0) phi Mw + max(c,0) F) of the update
 // (objective = 0) or the force functional (objective = 1), through phi =
 // -sum_{c>0} c f dv / D, D = sum_{c<0} c M1 dv, with dJ/dT_w per wall slot.
-// One block per wall cell, FP64 reductions.
+// One block per wall cell, FP64 reductions; M1, D and their T_w derivatives
+// from k_adj_wall_pre.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, const T *f, const T *lam, const T *mucv, T *lam_out,
-                                                  double *gtw, double *jwall, int32_t *wsec, int objective)
+__global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, int nw, const WallAdj *wadj, const double2 *wm,
+                                                  const double2 *wd, const T *f, const T *lam, const T *mucv,
+                                                  T *lam_out, double *gtw, double *jwall, int objective)
 {
-    __shared__ double red[8 * 8];
+    __shared__ double red[8 * 5];
     const Grid2D &g = a.g;
     const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
     const T *bown = reinterpret_cast<const T *>(a.bown);
-    const int nw = min(a.counts[1], a.cap);
     constexpr int W = Vec<T>::W;
     const double dv = g.dv;
     for (int idx = blockIdx.x; idx < nw; idx += gridDim.x) {
         const int k = a.wall_list[idx];
-        const WallAdj w = wall_adj(a, k);
+        const WallAdj w = wadj[idx];
         const long pk = pcell(g, k) * W;
-        const double cmw = 1.0 / (2.0 * kPi * w.Tw);
         const double bk = objective ? 0.0 : (double)bown[k];
-        double num = 0, den = 0, sphi = 0, sTw = 0, dD = 0, sxx = 0, sxy = 0;
+        double num = 0, sphi = 0, sTw = 0, sxx = 0, sxy = 0;
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
             const VCoef<T> vc = ld_coef(vt + p);
             const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
@@ -564,26 +680,23 @@ __global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, const T *f, const T
                 num += cp * fv * dv;
                 sxx += ax * ax * fv * dv; sxy += ax * ay * fv * dv;
             } else if (cp < 0) {
-                const double a2 = ax * ax + ay * ay;
-                const double m1 = cmw * exp(-a2 / (2.0 * w.Tw));
-                const double dm1 = m1 * (a2 / (2.0 * w.Tw * w.Tw) - 1.0 / w.Tw);
-                den += cp * m1 * dv;
-                dD += cp * dm1 * dv;
+                const double2 m = wm[(long)idx * g.nv + p];
                 if (objective) {
                     const double wgt = (ax * ax * w.nwx + ax * ay * w.nwy) * w.lw * dv;
-                    sphi += wgt * m1;
-                    sTw += wgt * dm1;          // times phi below
+                    sphi += wgt * m.x;
+                    sTw += wgt * m.y;          // times phi below
                 } else {
                     const double w0 = -bk * (double)mu_of<T>(a, lam, mucv, k, 0, p);
                     const double w1 = -bk * (double)mu_of<T>(a, lam, mucv, k, 1, p);
-                    sphi += w.lw * cp * (w0 * m1 + w1 * w.Tw / 2.0 * m1);
-                    sTw += w.lw * cp * (w0 * dm1 + w1 * (m1 / 2.0 + w.Tw / 2.0 * dm1));   // times phi below
+                    sphi += w.lw * cp * (w0 * m.x + w1 * w.Tw / 2.0 * m.x);
+                    sTw += w.lw * cp * (w0 * m.y + w1 * (m.x / 2.0 + w.Tw / 2.0 * m.y));   // times phi below
                 }
             }
         }
-        num = block_sum(num, red); den = block_sum(den, red + 8); sphi = block_sum(sphi, red + 16);
-        sTw = block_sum(sTw, red + 24); dD = block_sum(dD, red + 32);
-        sxx = block_sum(sxx, red + 40); sxy = block_sum(sxy, red + 48);
+        num = block_sum(num, red); sphi = block_sum(sphi, red + 8); sTw = block_sum(sTw, red + 16);
+        sxx = block_sum(sxx, red + 24); sxy = block_sum(sxy, red + 32);
+        const double2 D = wd[idx];
+        const double den = D.x, dD = D.y;
         const double phi = -num / den;
         // per-velocity terms of the wall cell
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
@@ -604,7 +717,6 @@ __global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, const T *f, const T
         }
         if (threadIdx.x == 0) {
             gtw[idx] += phi * sTw + sphi * (-phi / den) * dD;
-            wsec[idx] = w.sector;
             if (objective) {
                 // the incoming part of the stress: phi times the M1 sums
                 const double sin_xx_xy = sphi;          // sum (ax^2 nwx + ax ay nwy) lw dv M1
@@ -636,32 +748,66 @@ __global__ void __launch_bounds__(256) k_adj_fuseT(AdjArgs a, T *lam_out)
     }
 }
 
-// Maxwellian ghost cells: sensitivity of the ghost value of side s, index q,
-// then chained to (rho, ux, uy, T) of that side cell; one block per side cell.
+// The two pad layers of one side: their sensitivities (the flux transposes
+// along the side's axis that read them) go to the cells they copy -- the
+// boundary cell for a zero-gradient side, the periodic images -- or, for a
+// Maxwellian side, are summed over the steps per (side cell, component,
+// velocity) into pacc (the ghost state is the same at every step; the chain
+// to (rho, u, T) is k_adj_ghost_chain).  One thread per (side cell,
+// velocity); the sides are launched one after the other (a corner cell
+// receives from two sides).
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_ghost(AdjArgs a, const T *f, const T *lam, const T *mucv, int side,
-                                                   int nside, const double *prim, double *gbc)
+__global__ void __launch_bounds__(256) k_adj_pads(AdjArgs a, const T *f, const T *lam, const T *mucv, int side,
+                                                  int nside, double *pacc, T *lam_out)
+{
+    const Grid2D &g = a.g;
+    constexpr int W = Vec<T>::W;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nside * g.nvp) return;
+    const int q = (int)(t / g.nvp), p = (int)(t % g.nvp);
+    if (p >= g.nv) return;
+    const int axis = side < 2 ? 0 : 1;
+    const int kind = g.bc[side];
+    const int n = axis == 0 ? g.nx : g.ny;
+    // positions of the inner (1) and outer (2) pad along the axis, and the
+    // cells they copy
+    const int c1 = (side & 1) ? n : -1, c2 = (side & 1) ? n + 1 : -2;
+    const int i1 = axis == 0 ? c1 : q, j1 = axis == 0 ? q : c1;
+    const int i2 = axis == 0 ? c2 : q, j2 = axis == 0 ? q : c2;
+    const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p);
+    const T v = axis == 0 ? vc.vx : vc.vy, nu = axis == 0 ? vc.nux : vc.nuy;
+    int t1, t2;
+    if (kind == DVM_BC_PERIODIC) {
+        t1 = (side & 1) ? 0 : n - 1;
+        t2 = n > 1 ? ((side & 1) ? 1 : n - 2) : t1;
+    } else {
+        t1 = t2 = (side & 1) ? n - 1 : 0;
+    }
+    const long k1 = axis == 0 ? (long)q * g.nx + t1 : (long)t1 * g.nx + q;
+    const long k2 = axis == 0 ? (long)q * g.nx + t2 : (long)t2 * g.nx + q;
+#pragma unroll 1
+    for (int u = 0; u < 4; ++u) {
+        const int comp = u >> 1, layer = u & 1;
+        const T e = gather_axis<T>(a, f, lam, mucv, axis, layer ? i2 : i1, layer ? j2 : j1, comp, p, v, nu);
+        if (kind == DVM_BC_MAXWELLIAN) pacc[((long)q * 2 + comp) * g.nv + p] += (double)e;
+        else lam_out[ebase<T>(g, comp, p) + pcell(g, layer ? k2 : k1) * W] += e;
+    }
+}
+
+// Chain of the summed ghost sensitivities of a Maxwellian side to (rho, ux,
+// uy, T) of each side cell (ghost f = M[rho, u, T], g = T/2 M in both
+// layers); one block per side cell.
+__global__ void __launch_bounds__(256) k_adj_ghost_chain(Grid2D g, int nside, const double *prim, const double *pacc,
+                                                         double *gbc)
 {
     __shared__ double red[8 * 4];
-    const Grid2D &g = a.g;
-    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
-    const int axis = side < 2 ? 0 : 1;
     for (int q = blockIdx.x; q < nside; q += gridDim.x) {
-        // a cell adjacent to the ghost along the side's axis anchors the gather
-        int ti, tj;
-        if (side == 0) { ti = 0; tj = q; }
-        else if (side == 1) { ti = g.nx - 1; tj = q; }
-        else if (side == 2) { ti = q; tj = 0; }
-        else { ti = q; tj = g.ny - 1; }
-        const Loc target{-1, side, q};
         const double *st = prim + 5L * q;
         double o0 = 0, o1 = 0, o2 = 0, o3 = 0;
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
-            const VCoef<T> vc = ld_coef(vt + p);
-            const T v = axis == 0 ? vc.vx : vc.vy, nu = axis == 0 ? vc.nux : vc.nuy;
-            const double s0 = (double)gather_axis<T, false>(a, f, lam, mucv, axis, ti, tj, target, 0, p, v, nu);
-            const double s1 = (double)gather_axis<T, false>(a, f, lam, mucv, axis, ti, tj, target, 1, p, v, nu);
-            const double ax = (double)vc.vx - st[1], ay = (double)vc.vy - st[2], a2 = ax * ax + ay * ay;
+            const double s0 = pacc[((long)q * 2) * g.nv + p], s1 = pacc[((long)q * 2 + 1) * g.nv + p];
+            const double vx = g.vxmin + (p % g.nvx) * g.dvx, vy = g.vymin + (p / g.nvx) * g.dvy;
+            const double ax = vx - st[1], ay = vy - st[2], a2 = ax * ax + ay * ay;
             const double M = st[0] / (2.0 * kPi * st[4]) * exp(-a2 / (2.0 * st[4]));
             const double d0 = M / st[0], d1 = M * ax / st[4], d2 = M * ay / st[4];
             const double d3 = M * (a2 / (2.0 * st[4] * st[4]) - 1.0 / st[4]);
@@ -674,7 +820,7 @@ __global__ void __launch_bounds__(256) k_adj_ghost(AdjArgs a, const T *f, const 
         o0 = block_sum(o0, red); o1 = block_sum(o1, red + 8); o2 = block_sum(o2, red + 16); o3 = block_sum(o3, red + 24);
         if (threadIdx.x == 0) {
             double *o = gbc + 5L * q;
-            o[0] += o0; o[1] += o1; o[2] += o2; o[4] += o3;
+            o[0] = o0; o[1] = o1; o[2] = o2; o[3] = 0; o[4] = o3;
         }
         __syncthreads();
     }
@@ -732,6 +878,15 @@ struct AdjWork {
     uint8_t *fast = nullptr;                         // cells of the fast gather
     int32_t *slow = nullptr, *nslow_d = nullptr;     // the other cells
     int nslow = 0;
+    void *rpart = nullptr;                           // [Z][5][nc] split sums of the relaxation transpose
+    int Z = 1, Zf = 1;                               // velocity splits of the relaxation and the fast gather
+    std::vector<uint32_t *> tbits, sbits;            // limiter branches per tape slot / per segment end
+    std::vector<CUtensorMap> tbmap, sbmap;           // their TMA descriptors
+    CUtensorMap lmap[2];                             // TMA descriptors of lam[0], lam[1]
+    int nw = 0, nw_cap = 0;                          // wall cells and the capacity of the wall tables
+    WallAdj *wadj = nullptr;                         // per wall cell: wall data
+    double2 *wm = nullptr, *wd = nullptr;            // per wall cell: (M1, dM1/dT_w) per velocity, (D, dD/dT_w)
+    double *pacc = nullptr;                          // [side][cell][comp][nv] Maxwellian pad sensitivities
     void *fin = nullptr, *finpart = nullptr;         // F^N and its partial moments
     void *scratch_part = nullptr;                    // partial moments written by a tape fusion
     std::vector<void *> ckpt, ckpt_part, tape, ptape;
@@ -745,7 +900,10 @@ void release(AdjWork &w)
     cudaFree(w.mucv); cudaFree(w.aux); cudaFree(w.bown); cudaFree(w.cvx); cudaFree(w.rev);
     cudaFree(w.gtw); cudaFree(w.jwall); cudaFree(w.gbc); cudaFree(w.ginit); cudaFree(w.wsec);
     cudaFree(w.fin); cudaFree(w.finpart); cudaFree(w.scratch_part);
-    cudaFree(w.fast); cudaFree(w.slow); cudaFree(w.nslow_d);
+    cudaFree(w.fast); cudaFree(w.slow); cudaFree(w.nslow_d); cudaFree(w.rpart);
+    cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wd); cudaFree(w.pacc);
+    for (uint32_t *p : w.tbits) cudaFree(p);
+    for (uint32_t *p : w.sbits) cudaFree(p);
     for (void *p : w.ckpt) cudaFree(p);
     for (void *p : w.ckpt_part) cudaFree(p);
     for (void *p : w.tape) cudaFree(p);
@@ -765,35 +923,63 @@ AdjArgs adj_args(dvm_ctx *c, const AdjWork &w)
     a.cvx = w.cvx; a.bown = w.bown;
     a.muscl = c->scheme == DVM_MUSCL;
     a.omega = c->body.omega;
+    a.err = c->d_err;
     return a;
 }
 
-// One reverse step: lam_in = lambda^{n+1}, f = F^n (device layout) -> lam_out.
-template <typename T>
-cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, const T *lam_in, T *lam_out)
+// One reverse step: lam_in = lambda^{n+1}, f = F^n (device layout), bits =
+// the limiter branches the step took (MUSCL) -> lam_out.
+template <typename T, bool MUSCL>
+cudaError_t launch_gather_fast(dvm_ctx *c, const AdjArgs &a, const AdjWork &w, const CUtensorMap &lmap,
+                               const CUtensorMap *bmap, T *lam_out)
 {
+    const size_t smem = (size_t)kAdjStages * kAdjStageBytes + 2 * kAdjStages * sizeof(uint64_t);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_adj_gather_fast<T, MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid(nba(c->nx, 32), nba(c->ny, kRows), w.Zf), block(32, kRows);
+    k_adj_gather_fast<T, MUSCL><<<grid, block, smem, c->stream>>>(a, lmap, bmap ? *bmap : lmap, c->gsign,
+                                                                   (const T *)w.aux, w.fast, lam_out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, const CUtensorMap *bmap, int lin,
+                         T *lam_out)
+{
+    const T *lam_in = (const T *)w.lam[lin];
     const AdjArgs a = adj_args(c, w);
     const int cvgrid = 4 * 152;
     T *mucv = (T *)w.mucv, *aux = (T *)w.aux;
     k_adj_mu<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_in, mucv);
     const dim3 cgrid(nba(c->nx, 32), nba(c->ny, 8)), cblock(32, 8);
-    k_adj_relax<T><<<cgrid, cblock, 0, c->stream>>>(a, f, part, c->S, lam_in, mucv, aux);
-    if (c->scheme == DVM_MUSCL)
-        k_adj_gather_fast<T, true><<<cgrid, cblock, 0, c->stream>>>(a, f, lam_in, aux, w.fast, lam_out);
-    else
-        k_adj_gather_fast<T, false><<<cgrid, cblock, 0, c->stream>>>(a, f, lam_in, aux, w.fast, lam_out);
+    k_adj_relax<T><<<dim3(cgrid.x, cgrid.y, w.Z), cblock, 0, c->stream>>>(a, f, part, c->S, lam_in, mucv,
+                                                                          (T *)w.rpart);
+    k_adj_relax_fin<T><<<nba(c->nc, 256), 256, 0, c->stream>>>(a, part, c->S, (const T *)w.rpart, w.Z, aux);
+    cudaError_t e = c->scheme == DVM_MUSCL ? launch_gather_fast<T, true>(c, a, w, w.lmap[lin], bmap, lam_out)
+                                           : launch_gather_fast<T, false>(c, a, w, w.lmap[lin], nullptr, lam_out);
+    if (e != cudaSuccess) return e;
     if (w.nslow > 0)
         k_adj_gather_list<T><<<nba((long)w.nslow * c->nvp, 256), 256, 0, c->stream>>>(a, f, lam_in, mucv, aux, w.slow,
                                                                                       w.nslow, lam_out);
-    k_adj_wall<T><<<cvgrid, 256, 0, c->stream>>>(a, f, lam_in, mucv, lam_out, w.gtw, w.jwall, w.wsec, 0);
-    k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_out);
+    if (w.nw > 0)
+        k_adj_wall<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, f, lam_in, mucv, lam_out, w.gtw,
+                                                    w.jwall, 0);
+    int launched = 7;
     const int nside[4] = {c->ny, c->ny, c->nx, c->nx};
     const int nmax = c->nx > c->ny ? c->nx : c->ny;
-    for (int s = 0; s < 4; ++s)
-        if (c->bc[s] == DVM_BC_MAXWELLIAN && c->d_bcstate[s])
-            k_adj_ghost<T><<<nside[s], 256, 0, c->stream>>>(a, f, lam_in, mucv, s, nside[s], c->d_bcstate[s],
-                                                            w.gbc + 5L * s * nmax);
-    c->launches += 6;
+    for (int s = 0; s < 4; ++s) {
+        if (c->bc[s] == DVM_BC_MAXWELLIAN && !c->d_bcstate[s]) continue;
+        k_adj_pads<T><<<nba((long)nside[s] * c->nvp, 256), 256, 0, c->stream>>>(
+            a, f, lam_in, mucv, s, nside[s], w.pacc + (long)s * nmax * 2 * c->nv, lam_out);
+        ++launched;
+    }
+    k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_out);
+    c->launches += launched;
     return cudaGetLastError();
 }
 
@@ -811,7 +997,11 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
 #define AC(call) do { e = (call); if (e != cudaSuccess) return cuda_fail(e, #call); } while (0)
     if (w.bytes_state != bytes || w.cap != c->list_cap) {
         release(w);
-        for (int b = 0; b < 2; ++b) AC(cudaMalloc(&w.lam[b], bytes));
+        for (int b = 0; b < 2; ++b) {
+            AC(cudaMalloc(&w.lam[b], bytes));
+            const int rc = encode_tensor_map2d(c, w.lam[b], &w.lmap[b]);
+            if (rc != DVM_OK) return rc;
+        }
         AC(cudaMalloc(&w.aux, (size_t)c->nc * 5 * c->elem));
         AC(cudaMalloc(&w.bown, (size_t)c->nc * c->elem));
         AC(cudaMalloc(&w.cvx, sizeof(int32_t) * c->nc));
@@ -828,6 +1018,10 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMalloc(&w.fast, c->nc));
         AC(cudaMalloc(&w.slow, sizeof(int32_t) * c->nc));
         AC(cudaMalloc(&w.nslow_d, sizeof(int)));
+        w.Z = c->ngrp < 8 ? c->ngrp : 8;
+        w.Zf = c->ngrp < 4 ? c->ngrp : 4;
+        AC(cudaMalloc(&w.pacc, sizeof(double) * 4 * nmax * 2 * c->nv));
+        AC(cudaMalloc(&w.rpart, (size_t)w.Z * 5 * c->nc * c->elem));
         w.bytes_state = bytes;
         w.cap = c->list_cap;
     }
@@ -849,6 +1043,26 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         if (rc != DVM_OK) return rc;
         w.tmaps.push_back(m);
     }
+    // limiter branches of the tape states (MUSCL): one buffer per tape slot but
+    // the last, whose branches the checkpointed forward run records once per
+    // segment; pad words that no cell writes stay 0
+    const bool rec = c->scheme == DVM_MUSCL;
+    const size_t bitsb = (size_t)c->ngrp * bits_slab(c) * sizeof(uint32_t);
+    for (int pass = 0; pass < 2 && rec; ++pass) {
+        std::vector<uint32_t *> &v = pass ? w.sbits : w.tbits;
+        std::vector<CUtensorMap> &mv = pass ? w.sbmap : w.tbmap;
+        const int want = pass ? nseg : K - 1;
+        while ((int)v.size() < want) {
+            uint32_t *p = nullptr;
+            AC(cudaMalloc(&p, bitsb));
+            AC(cudaMemsetAsync(p, 0, bitsb, c->stream));
+            v.push_back(p);
+            CUtensorMap m;
+            const int rc = encode_bits_map2d(c, p, &m);
+            if (rc != DVM_OK) return rc;
+            mv.push_back(m);
+        }
+    }
     // the tape buffers take the boundary padding (Maxwellian ghosts) of the state
     for (int t = 0; t < K; ++t)
         AC(cudaMemcpyAsync(w.tape[t], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -860,9 +1074,23 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         k_adj_setup<T><<<nba(c->nc, 256), 256, 0, c->stream>>>(g, c->master, c->flags, w.rev, (const CvInfo *)c->cvinfo,
                                                                 w.cvx, (T *)w.bown);
         k_adj_fastmask<<<nba(c->nc, 256), 256, 0, c->stream>>>(g, c->flags, w.fast);
-        k_adj_slowlist<<<1, 1024, 0, c->stream>>>(c->nc, w.fast, w.slow, w.nslow_d);
+        k_adj_slowlist<<<1, 1024, 0, c->stream>>>(c->nc, w.fast, c->master, w.slow, w.nslow_d);
         AC(cudaMemcpyAsync(&w.nslow, w.nslow_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        int32_t cnt0[2];
+        AC(cudaMemcpyAsync(cnt0, c->counts, sizeof(cnt0), cudaMemcpyDeviceToHost, c->stream));
         AC(cudaStreamSynchronize(c->stream));
+        w.nw = cnt0[1] < c->list_cap ? cnt0[1] : c->list_cap;
+        if (w.nw > w.nw_cap) {
+            cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wd);
+            w.wadj = nullptr; w.wm = w.wd = nullptr; w.nw_cap = 0;
+            AC(cudaMalloc(&w.wadj, sizeof(WallAdj) * w.nw));
+            AC(cudaMalloc(&w.wm, sizeof(double2) * w.nw * c->nv));
+            AC(cudaMalloc(&w.wd, sizeof(double2) * w.nw));
+            w.nw_cap = w.nw;
+        }
+        if (w.nw > 0)
+            k_adj_wall_pre<T><<<w.nw, 256, 0, c->stream>>>(adj_args(c, w), w.nw, w.wadj, w.wm, w.wd, w.wsec);
+        AC(cudaMemsetAsync(w.pacc, 0, sizeof(double) * 4 * nmax * 2 * c->nv, c->stream));
     }
     cudaEvent_t ev[3];
     for (int q = 0; q < 3; ++q) AC(cudaEventCreate(&ev[q]));
@@ -875,7 +1103,11 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
             AC(cudaMemcpyAsync(w.ckpt[n / K], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
             AC(cudaMemcpyAsync(w.ckpt_part[n / K], c->part[c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
         }
-        AC(step2d(c));
+        // the last step of each segment records its limiter branches
+        if (rec && (n % K == K - 1 || n == nsteps - 1)) c->rec_bits = w.sbits[n / K];
+        const cudaError_t es = step2d(c);
+        c->rec_bits = nullptr;
+        AC(es);
     }
     AC(cudaEventRecord(ev[1], c->stream));
     AC(cudaMemcpyAsync(w.fin, c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -885,10 +1117,14 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     const AdjArgs a = adj_args(c, w);
     const int cvgrid = 4 * 152;
     // objective on F^N: lambda^N = fusion^T dJ/dF
-    T *lamA = (T *)w.lam[0], *lamB = (T *)w.lam[1];
-    AC(cudaMemsetAsync(lamA, 0, bytes, c->stream));
-    k_adj_wall<T><<<cvgrid, 256, 0, c->stream>>>(a, (const T *)c->f[c->cur], lamA, (const T *)w.mucv, lamA, w.gtw,
-                                                 w.jwall, w.wsec, 1);
+    int lin = 0;                                      // lambda^{n+1} is lam[lin]
+    T *lamA = (T *)w.lam[0];
+    // cells in no control volume and the pads keep lambda = 0 in both buffers
+    AC(cudaMemsetAsync(w.lam[0], 0, bytes, c->stream));
+    AC(cudaMemsetAsync(w.lam[1], 0, bytes, c->stream));
+    if (w.nw > 0)
+        k_adj_wall<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, (const T *)c->f[c->cur], lamA,
+                                                    (const T *)w.mucv, lamA, w.gtw, w.jwall, 1);
     k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lamA);
     // reverse sweep, segment by segment: recompute the segment onto the tape
     // (each step writes the next tape buffer), then apply the transposed steps
@@ -910,7 +1146,10 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
                 c->f[1 - c->cur] = w.tape[t + 1];
                 c->tmap[c->cur] = w.tmaps[t];
                 c->tmap[1 - c->cur] = w.tmaps[t + 1];
-                AC(step2d(c));
+                if (rec) c->rec_bits = w.tbits[t];
+                const cudaError_t es = step2d(c);
+                c->rec_bits = nullptr;
+                AC(es);
                 AC(cudaMemcpyAsync(w.ptape[t], c->part[1 - c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
             } else {
                 AC(cudaMemcpyAsync(w.ptape[t], c->part[c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
@@ -920,8 +1159,9 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         c->tmap[0] = tm_orig[0]; c->tmap[1] = tm_orig[1];
         c->cur = cur_orig;
         for (int t = len - 1; t >= 0; --t) {
-            AC(adjoint_step<T>(c, w, (const T *)w.tape[t], (const T *)w.ptape[t], lamA, lamB));
-            T *tt = lamA; lamA = lamB; lamB = tt;
+            const CUtensorMap *bm = !rec ? nullptr : (t == len - 1 ? &w.sbmap[sgi] : &w.tbmap[t]);
+            AC(adjoint_step<T>(c, w, (const T *)w.tape[t], (const T *)w.ptape[t], bm, lin, (T *)w.lam[1 - lin]));
+            lin = 1 - lin;
         }
     }
     AC(cudaEventRecord(ev[2], c->stream));
@@ -934,6 +1174,11 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     AC(cudaMemcpyAsync(gt.data(), w.gtw, sizeof(double) * c->list_cap, cudaMemcpyDeviceToHost, c->stream));
     AC(cudaMemcpyAsync(ws.data(), w.wsec, sizeof(int32_t) * c->list_cap, cudaMemcpyDeviceToHost, c->stream));
     const int nside[4] = {c->ny, c->ny, c->nx, c->nx};
+    for (int s = 0; s < 4; ++s)
+        if (c->bc[s] == DVM_BC_MAXWELLIAN && c->d_bcstate[s])
+            k_adj_ghost_chain<<<nside[s], 256, 0, c->stream>>>(grid2d(c), nside[s], c->d_bcstate[s],
+                                                               w.pacc + (long)s * nmax * 2 * c->nv,
+                                                               w.gbc + 5L * s * nmax);
     for (int s = 0; s < 4; ++s) {
         if (!gbc || !gbc[s]) continue;
         if (c->bc[s] != DVM_BC_MAXWELLIAN) { std::memset(gbc[s], 0, sizeof(double) * 5 * nside[s]); continue; }
@@ -941,8 +1186,8 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     }
     if (gprim0) {
         if (!c->have_prim0) { set_error("dvm_drag_adjoint: gprim0 needs a state set by dvm_init_maxwellian"); return DVM_ERR_STATE; }
-        k_adj_init<T><<<dim3(nba(c->nx, 32), nba(c->ny, 8)), dim3(32, 8), 0, c->stream>>>(grid2d(c), lamA, c->d_prim0,
-                                                                                      c->geo[c->gcur].type, w.ginit);
+        k_adj_init<T><<<dim3(nba(c->nx, 32), nba(c->ny, 8)), dim3(32, 8), 0, c->stream>>>(
+            grid2d(c), (const T *)w.lam[lin], c->d_prim0, c->geo[c->gcur].type, w.ginit);
         AC(cudaMemcpyAsync(gprim0, w.ginit, sizeof(double) * 5 * c->nc, cudaMemcpyDeviceToHost, c->stream));
     }
     // leave the context at F^N, as after nsteps forward steps

@@ -169,6 +169,7 @@ struct dvm_ctx {
     double *d_prim0;              // primitives of the last dvm_init_maxwellian (nc * 5)
     bool have_prim0;
     void *adj;                    // adjoint workspace (dvm_adjoint2d.cu)
+    uint32_t *rec_bits;           // if set, the 2D MUSCL bulk kernel records its limiter branches here
     bool have_state, have_geo, need_fusion, moving;
     bool timing;
     void *ev_pool;                // std::vector<cudaEvent_t> of start/stop pairs
@@ -206,6 +207,7 @@ cudaError_t members2d(dvm_ctx *c, bool moving);                  // control-volu
 cudaError_t timing_mark(dvm_ctx *c, int which);   // 0: before, 1: after the bulk kernel
 int make_tensor_maps2d(dvm_ctx *c);                // TMA descriptors of f[0], f[1]
 int encode_tensor_map2d(dvm_ctx *c, void *buf, CUtensorMap *map);
+int encode_bits_map2d(dvm_ctx *c, void *buf, CUtensorMap *map);  // limiter-branch words (bits_pitch rows)
 // adjoint (dvm_adjoint2d.cu)
 int drag_adjoint2d(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double *const *gbc, double *gprim0,
                    double *ms_forward, double *ms_reverse);
@@ -231,6 +233,12 @@ cudaError_t halo3d(dvm_ctx *c, int buf);
 size_t vtab3_bytes(const dvm_ctx *c);
 int make_tensor_maps3d(dvm_ctx *c);                // TMA descriptors of f[0], f[1] (3D)
 size_t cvinfo3_bytes();
+
+// Limiter-branch words of the 2D MUSCL step (recorded for the adjoint): one
+// uint32 per (velocity group, padded cell) with the row pitch rounded up to
+// a multiple of 4 words (16-byte rows for TMA).
+inline int bits_pitch(const dvm_ctx *c) { return (c->nx + 4 + 3) & ~3; }
+inline long bits_slab(const dvm_ctx *c) { return (long)bits_pitch(c) * (c->ny + 4); }
 
 inline double *body_trig(dvm_ctx *c, int which)
 {

@@ -65,6 +65,9 @@ template <typename T> struct BulkArgs {
     const uint8_t *flags;
     const VCoef<T> *vt;       // [nvp]
     const int8_t *gsign;      // [ngrp][2]
+    uint32_t *bits;           // [ngrp][bslab] limiter branches of the downwind faces (recording only)
+    int bpitch;               // row pitch of the branch words
+    long bslab;               // branch words per group
     int *err;
 };
 
@@ -72,17 +75,30 @@ template <typename T> struct BulkArgs {
 constexpr int kStageBytes = 2 * kTileY * kTileX * 16;     // both components of one group
 
 
+// Branch the limited reconstruction of a downwind face took (recorded for the
+// discrete adjoint): 1 when minmod returned its first argument a (the
+// downwind difference), 2 when it returned the second b (the upwind
+// difference; also on a tie), 0 when it returned 0 or the face is first order.
+template <typename T>
+__device__ __forceinline__ uint32_t branch_bits(T m, T a, T b, T w)
+{
+    return (w == T(0) || m == T(0)) ? 0u : (m == b ? 2u : (m == a ? 1u : 0u));
+}
+
 // Update of one component of one velocity group for the thread's cell from
 // the shared-memory tile (Eq. ExSchemeDD on a full gas cell, fluxes of Eq.
 // FluxDD in difference form with the limited reconstruction), moment sums.
 // c0 is the tile index of the cell; ux1/uy1 the tile offsets of one cell step
 // towards the upwind side along x/y (sign-uniform groups), else per element.
-template <typename T, bool MUSCL, int COMP, bool UNIFORM>
+// With REC the branches of the two downwind faces are or-ed into bw, those of
+// the two upwind (incoming) faces into bi, at bit ((COMP * 2 + axis) * W + e) * 2.
+template <typename T, bool MUSCL, int COMP, bool UNIFORM, bool REC>
 __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0, int ux1, int uy1,
                                           const T (&vx)[Vec<T>::W], const T (&vy)[Vec<T>::W],
                                           const T (&nux)[Vec<T>::W], const T (&nuy)[Vec<T>::W],
                                           const T (&feq)[Vec<T>::W], T wxm, T wxp, T wym, T wyp, T r,
-                                          T (&out)[Vec<T>::W], T &q0, T &q1, T &q2, T &q3)
+                                          T (&out)[Vec<T>::W], T &q0, T &q1, T &q2, T &q3, uint32_t &bw,
+                                          uint32_t &bi)
 {
     constexpr int W = Vec<T>::W;
     T f[W];
@@ -105,8 +121,16 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
             const T ax = f[e] - u1[e], ay = f[e] - w1[e];
             T dfx = ax, dfy = ay;
             if (MUSCL) {
-                dfx += (T(1) - nux[e]) * (cxo * minmod3(d1[e] - f[e], ax) - cxi * minmod3(ax, u1[e] - u2[e]));
-                dfy += (T(1) - nuy[e]) * (cyo * minmod3(e1[e] - f[e], ay) - cyi * minmod3(ay, w1[e] - w2[e]));
+                const T bx = d1[e] - f[e], by = e1[e] - f[e], cx = u1[e] - u2[e], cy = w1[e] - w2[e];
+                const T mxo = minmod3(bx, ax), myo = minmod3(by, ay), mxi = minmod3(ax, cx), myi = minmod3(ay, cy);
+                dfx += (T(1) - nux[e]) * (cxo * mxo - cxi * mxi);
+                dfy += (T(1) - nuy[e]) * (cyo * myo - cyi * myi);
+                if (REC) {
+                    bw |= branch_bits(mxo, bx, ax, cxo) << (((COMP * 2 + 0) * W + e) * 2);
+                    bw |= branch_bits(myo, by, ay, cyo) << (((COMP * 2 + 1) * W + e) * 2);
+                    bi |= branch_bits(mxi, ax, cx, cxi) << (((COMP * 2 + 0) * W + e) * 2);
+                    bi |= branch_bits(myi, ay, cy, cyi) << (((COMP * 2 + 1) * W + e) * 2);
+                }
             }
             out[e] = f[e] - nux[e] * dfx - nuy[e] * dfy + r * (feq[e] - f[e]);
         }
@@ -129,8 +153,16 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
                 const T e1 = py ? yp[e] : ym[e], w2 = py ? ym2[e] : yp2[e];
                 const T cxo = px ? wxp : wxm, cxi = px ? wxm : wxp;
                 const T cyo = py ? wyp : wym, cyi = py ? wym : wyp;
-                dfx += (T(1) - nux[e]) * (cxo * minmod3(d1 - f[e], ax) - cxi * minmod3(ax, u1 - u2));
-                dfy += (T(1) - nuy[e]) * (cyo * minmod3(e1 - f[e], ay) - cyi * minmod3(ay, w1 - w2));
+                const T bx = d1 - f[e], by = e1 - f[e], cx = u1 - u2, cy = w1 - w2;
+                const T mxo = minmod3(bx, ax), myo = minmod3(by, ay), mxi = minmod3(ax, cx), myi = minmod3(ay, cy);
+                dfx += (T(1) - nux[e]) * (cxo * mxo - cxi * mxi);
+                dfy += (T(1) - nuy[e]) * (cyo * myo - cyi * myi);
+                if (REC) {
+                    bw |= branch_bits(mxo, bx, ax, cxo) << (((COMP * 2 + 0) * W + e) * 2);
+                    bw |= branch_bits(myo, by, ay, cyo) << (((COMP * 2 + 1) * W + e) * 2);
+                    bi |= branch_bits(mxi, ax, cx, cxi) << (((COMP * 2 + 0) * W + e) * 2);
+                    bi |= branch_bits(myi, ay, cy, cyi) << (((COMP * 2 + 1) * W + e) * 2);
+                }
             }
             out[e] = f[e] - nux[e] * dfx - nuy[e] * dfy + r * (feq[e] - f[e]);
         }
@@ -171,7 +203,13 @@ __device__ __forceinline__ void store_cell(typename Vec<T>::type *slab, long pc,
 // Every wait is bounded: on timeout the kernel records kErrTimeout and goes
 // on without blocking.  Threads of non-plain cells only take part in the
 // barriers.
-template <typename T, bool MUSCL>
+// With REC (recomputation for the discrete adjoint) each plain cell also
+// writes the limiter branches of its downwind faces, one word per group at
+// its padded index (row pitch bpitch); a cell on a side also writes the
+// branches of its face on that side, for the velocities entering through it,
+// at the padded index of the pad across that face (the face is "downwind" of
+// that pad).
+template <typename T, bool MUSCL, bool REC>
 __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int W = Vec<T>::W;
@@ -257,25 +295,47 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                 const T dx = vc.vx - ux, dy = vc.vy - uy;
                 feq[e] = A * dexp2(-(dx * dx + dy * dy) * c2);
             }
+            uint32_t bw = 0, bi = 0;
             if (sx != 0 && sy != 0) {
                 const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
-                bulk_tile<T, MUSCL, 0, true>(tile, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
-                                             out, q0, q1, q2, q3);
+                bulk_tile<T, MUSCL, 0, true, REC>(tile, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
+                                                  out, q0, q1, q2, q3, bw, bi);
                 store_cell<T>(o0, pc, mir, anymir, out);
 #pragma unroll
                 for (int e = 0; e < W; ++e) feq[e] *= gfac;
-                bulk_tile<T, MUSCL, 1, true>(tile + kTileY * kTileX, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm,
-                                             wxp, wym, wyp, r, out, q0, q1, q2, q3);
+                bulk_tile<T, MUSCL, 1, true, REC>(tile + kTileY * kTileX, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm,
+                                                  wxp, wym, wyp, r, out, q0, q1, q2, q3, bw, bi);
                 store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
             } else {
-                bulk_tile<T, MUSCL, 0, false>(tile, c0, 1, kTileX, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
-                                              out, q0, q1, q2, q3);
+                bulk_tile<T, MUSCL, 0, false, REC>(tile, c0, 1, kTileX, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
+                                                   out, q0, q1, q2, q3, bw, bi);
                 store_cell<T>(o0, pc, mir, anymir, out);
 #pragma unroll
                 for (int e = 0; e < W; ++e) feq[e] *= gfac;
-                bulk_tile<T, MUSCL, 1, false>(tile + kTileY * kTileX, c0, 1, kTileX, vx, vy, nux, nuy, feq, wxm,
-                                              wxp, wym, wyp, r, out, q0, q1, q2, q3);
+                bulk_tile<T, MUSCL, 1, false, REC>(tile + kTileY * kTileX, c0, 1, kTileX, vx, vy, nux, nuy, feq,
+                                                   wxm, wxp, wym, wyp, r, out, q0, q1, q2, q3, bw, bi);
                 store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
+            }
+            if (REC) {
+                uint32_t *bq = a.bits + (long)q * a.bslab;
+                const auto bix = [&](int ii, int jj) { return (long)(jj + 2) * a.bpitch + ii + 2; };
+                bq[bix(i, j)] = bw;
+                if (i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1) {
+                    // fields of the velocities that enter through each side
+                    uint32_t xin = 0, xout = 0, yin = 0, yout = 0;
+#pragma unroll
+                    for (int e = 0; e < W; ++e)
+#pragma unroll
+                        for (int cp = 0; cp < 2; ++cp) {
+                            const uint32_t fx = 3u << (((cp * 2 + 0) * W + e) * 2), fy = 3u << (((cp * 2 + 1) * W + e) * 2);
+                            if (vx[e] >= T(0)) xin |= fx; else xout |= fx;
+                            if (vy[e] >= T(0)) yin |= fy; else yout |= fy;
+                        }
+                    if (i == 0) bq[bix(-1, j)] = bi & xin;
+                    if (i == g.nx - 1) bq[bix(g.nx, j)] = bi & xout;
+                    if (j == 0) bq[bix(i, -1)] = bi & yin;
+                    if (j == g.ny - 1) bq[bix(i, g.ny)] = bi & yout;
+                }
             }
             // fold the plain sums of 8 groups into the compensated sums
             if (++fold == 8) {
@@ -1000,18 +1060,19 @@ __global__ void k_tables(Grid2D g, VCoef<T> *vt, int8_t *gsign)
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
-template <typename T, bool MUSCL>
+template <typename T, bool MUSCL, bool REC>
 cudaError_t launch_bulk(dvm_ctx *c, const BulkArgs<T> &a)
 {
     const size_t smem = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_bulk<T, MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_bulk<T, MUSCL, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(nblk(c->nx, 32), nblk(c->ny, kRows), c->S), block(32, kRows);
-    k_bulk<T, MUSCL><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
+    k_bulk<T, MUSCL, REC><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
     return cudaGetLastError();
 }
 
@@ -1054,8 +1115,12 @@ cudaError_t step2d_t(dvm_ctx *c)
     BulkArgs<T> a;
     a.g = g; a.S = c->S; a.fin = fin; a.fout = fout; a.pin = pin; a.pout = pout;
     a.flags = c->flags; a.vt = (const VCoef<T> *)c->vtab; a.gsign = c->gsign; a.err = c->d_err;
+    a.bits = c->rec_bits;
+    a.bpitch = bits_pitch(c);
+    a.bslab = bits_slab(c);
     if ((e = timing_mark(c, 0)) != cudaSuccess) return e;
-    e = c->scheme == DVM_MUSCL ? launch_bulk<T, true>(c, a) : launch_bulk<T, false>(c, a);
+    if (c->scheme != DVM_MUSCL) e = launch_bulk<T, false, false>(c, a);
+    else e = c->rec_bits ? launch_bulk<T, true, true>(c, a) : launch_bulk<T, true, false>(c, a);
     if (e != cudaSuccess) return e;
     if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
     c->launches += 1;
@@ -1072,21 +1137,45 @@ cudaError_t step2d_t(dvm_ctx *c)
 
 }  // namespace
 
-// TMA descriptor of a state buffer in the device layout (any buffer with the
-// layout of f[0], f[1]).
-int encode_tensor_map2d(dvm_ctx *c, void *buf, CUtensorMap *map)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
-            set_error("cuTensorMapEncodeTiled is not available from the driver");
-            return DVM_ERR_CUDA;
-        }
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return nullptr;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    return encode;
+}
+
+// TMA descriptor of a buffer of limiter-branch words ([ngrp][ny + 4][pitch]
+// uint32): one box is the block's tile (36 x 12 words) of one group.
+int encode_bits_map2d(dvm_ctx *c, void *buf, CUtensorMap *map)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) { set_error("cuTensorMapEncodeTiled is not available from the driver"); return DVM_ERR_CUDA; }
+    const cuuint64_t dims[3] = {(cuuint64_t)bits_pitch(c), (cuuint64_t)(c->ny + 4), (cuuint64_t)c->ngrp};
+    const cuuint64_t strides[2] = {(cuuint64_t)bits_pitch(c) * 4, (cuuint64_t)bits_slab(c) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, buf, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        return DVM_ERR_CUDA;
+    }
+    return DVM_OK;
+}
+
+// TMA descriptor of a state buffer in the device layout (any buffer with the
+// layout of f[0], f[1]).
+int encode_tensor_map2d(dvm_ctx *c, void *buf, CUtensorMap *map)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) { set_error("cuTensorMapEncodeTiled is not available from the driver"); return DVM_ERR_CUDA; }
     const int W = c->W;
     const cuuint64_t dims[3] = {(cuuint64_t)(c->nx + 4) * W, (cuuint64_t)(c->ny + 4), (cuuint64_t)2 * c->ngrp};
     const cuuint64_t strides[2] = {(cuuint64_t)(c->nx + 4) * W * c->elem, (cuuint64_t)c->slab * W * c->elem};
