@@ -20,7 +20,7 @@
 //                  the cells deep in the gas, re-derived from F^n elsewhere);
 //   k_adj_wall     per wall cell: the diffuse flux and the wall density
 //                  coupling (Eq. BoundaryDDv), and dJ/dT_w;
-//   k_adj_pads     the boundary pads: the step reads them but does not
+//   k_adj_pads*    the boundary pads: the step reads them but does not
 //                  update them, so their sensitivities are gathered like a
 //                  cell's and folded back onto the cells they copy
 //                  (periodic, zero-gradient) or chained to (rho, u, T) of
@@ -97,6 +97,17 @@ __device__ __forceinline__ T mu_of(const AdjArgs &a, const T *lam, const T *mucv
     return lam[ebase<T>(a.g, comp, p) + pcell(a.g, k) * Vec<T>::W];
 }
 
+// mu of cell k for the W velocities of the group starting at p.
+template <typename T>
+__device__ __forceinline__ void mu_of_v(const AdjArgs &a, const T *lam, const T *mucv, int k, int comp, int p,
+                                        T (&r)[Vec<T>::W])
+{
+    using V = typename Vec<T>::type;
+    const int cx = a.cvx[k];
+    if (cx >= 0) vld<T>(reinterpret_cast<const V *>(mucv + ((long)cx * 2 + comp) * a.g.nvp + p), r);
+    else vld<T>(reinterpret_cast<const V *>(lam + ebase<T>(a.g, comp, p)) + pcell(a.g, k), r);
+}
+
 // ------------------------------------------------------------ set-up
 __global__ void k_adj_rev(const int32_t *spec_list, const int32_t *counts, int cap, int32_t *rev)
 {
@@ -130,15 +141,20 @@ __global__ void __launch_bounds__(256) k_adj_mu(AdjArgs a, const T *lam, T *mucv
     const CvInfo *info = reinterpret_cast<const CvInfo *>(a.cvinfo);
     const int n = min(a.counts[0], a.cap);
     constexpr int W = Vec<T>::W;
+    __shared__ long pcs[kMaxMembers];
     for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
         const CvInfo &I = info[idx];
+        const int nm = I.nm;
+        if (threadIdx.x < nm) pcs[threadIdx.x] = I.mem[threadIdx.x].pc * W;
+        __syncthreads();
         for (int e = threadIdx.x; e < 2 * a.g.nvp; e += blockDim.x) {
             const int comp = e / a.g.nvp, p = e - comp * a.g.nvp;
             const long base = ebase<T>(a.g, comp, p);
             T s = 0;
-            for (int t = 0; t < I.nm; ++t) s += lam[base + I.mem[t].pc * W];
+            for (int t = 0; t < nm; ++t) s += lam[base + pcs[t]];
             mucv[((long)idx * 2 + comp) * a.g.nvp + p] = s;
         }
+        __syncthreads();
     }
 }
 
@@ -263,21 +279,23 @@ __global__ void __launch_bounds__(256) k_adj_relax_fin(AdjArgs a, const T *part,
 // Sum over the faces along one axis whose stencil reads padded position
 // (ti, tj) -- a cell, or a boundary pad along the axis -- of the weight W_f
 // (adjoint of the two control volumes the face separates) times the flux
-// derivative at that stencil slot.  The faces are those between positions
-// ii and ii + 1 along the axis for ii = c - 2 .. c + 1.  The step reads the
-// pads but does not update them: a pad on either side of a face adds no
-// weight, and a face between two pads none at all.
+// derivative at that stencil slot, for the W velocities of the group at p.
+// The faces are those between positions ii and ii + 1 along the axis for
+// ii = c - 2 .. c + 1.  The step reads the pads but does not update them: a
+// pad on either side of a face adds no weight, and a face between two pads
+// none at all.
 template <typename T>
-__device__ T gather_axis(const AdjArgs &a, const T *f, const T *lam, const T *mucv, int axis, int ti, int tj,
-                         int comp, int p, T v, T nu)
+__device__ void gather_axis(const AdjArgs &a, const T *f, const T *lam, const T *mucv, int axis, int ti, int tj,
+                            int comp, int p, const T (&v)[Vec<T>::W], const T (&nu)[Vec<T>::W],
+                            T (&acc)[Vec<T>::W])
 {
-    const Grid2D &g = a.g;
+    using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
+    const Grid2D &g = a.g;
     const int n = axis == 0 ? g.nx : g.ny;
     const int c = axis == 0 ? ti : tj;
-    const long eb = ebase<T>(g, comp, p);
+    const V *F = reinterpret_cast<const V *>(f + ebase<T>(g, comp, p));
     const T *bown = reinterpret_cast<const T *>(a.bown);
-    T acc = 0;
     for (int ii = c - 2; ii <= c + 1; ++ii) {
         const bool aint = ii >= 0 && ii < n, bint = ii + 1 >= 0 && ii + 1 < n;
         if (!aint && !bint) continue;
@@ -297,65 +315,78 @@ __device__ T gather_axis(const AdjArgs &a, const T *f, const T *lam, const T *mu
             lim = a.muscl && ((a.flags[B] >> kMaskShift) & (axis == 0 ? 1 : 4));
         }
         if (L == T(0)) continue;
-        const T Wf = (A >= 0 ? -bown[A] * mu_of<T>(a, lam, mucv, A, comp, p) : T(0)) +
-                     (B >= 0 ? bown[B] * mu_of<T>(a, lam, mucv, B, comp, p) : T(0));
-        if (Wf == T(0)) continue;
+        const T bA = A >= 0 ? bown[A] : T(0), bB = B >= 0 ? bown[B] : T(0);
+        if (bA == T(0) && bB == T(0)) continue;
+        T Wf[W], mA[W], mB[W];
+        if (bA != T(0)) mu_of_v<T>(a, lam, mucv, A, comp, p, mA);
+        if (bB != T(0)) mu_of_v<T>(a, lam, mucv, B, comp, p, mB);
+#pragma unroll
+        for (int e = 0; e < W; ++e) Wf[e] = (bA != T(0) ? -bA * mA[e] : T(0)) + (bB != T(0) ? bB * mB[e] : T(0));
         // stencil AA, A, B, BB (positions ii - 1 .. ii + 2, within the padding)
-        T fv[4];
+        T fv[4][W];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int pos = ii - 1 + t;
-            fv[t] = f[eb + nbr(g, axis == 0 ? pos : ti, axis == 0 ? tj : pos) * W];
+            vld<T>(F + nbr(g, axis == 0 ? pos : ti, axis == 0 ? tj : pos), fv[t]);
         }
-        T d[4];
-        face_flux_d<T>(L, v, nu, fv[0], fv[1], fv[2], fv[3], lim, d);
-        acc += Wf * d[c - ii + 1];
+        const int slot = c - ii + 1;
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            T d[4];
+            face_flux_d<T>(L, v[e], nu[e], fv[0][e], fv[1][e], fv[2][e], fv[3][e], lim, d);
+            acc[e] += Wf[e] * d[slot];
+        }
     }
-    return acc;
 }
 
-// nu of one (cell, velocity) of the generic list: relaxation terms for
-// control-volume masters and the face-flux transposes along both axes.
+// Generic gather over the listed cells (those near cut cells and merged
+// control volumes): relaxation terms for control-volume masters and the
+// face-flux transposes along both axes.  One thread per (listed cell,
+// velocity group), consecutive threads on consecutive listed cells.
 template <typename T>
-__device__ __forceinline__ void gather_generic(const AdjArgs &a, const T *f, const T *lam, const T *mucv, const T *aux,
-                                               T *lam_out, int k, int p)
+__global__ void __launch_bounds__(256) k_adj_gather_list(AdjArgs a, const T *f, const T *lam, const T *mucv,
+                                                         const T *aux, const int32_t *list, int nlist, T *lam_out)
 {
-    const Grid2D &g = a.g;
+    using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
-    const long pk = pcell(g, k) * W;
-    if (a.master[k] < 0 || p >= g.nv) {
-        lam_out[ebase<T>(g, 0, p) + pk] = T(0);
-        lam_out[ebase<T>(g, 1, p) + pk] = T(0);
-        return;
+    const Grid2D &g = a.g;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nlist * g.ngrp) return;
+    const int q = (int)(t / nlist), k = list[t % nlist];
+    const int p = q * W;
+    const long pk = pcell(g, k);
+    T vx[W], vy[W], nux[W], nuy[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p + e);
+        vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
     }
-    const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p);
     int ki, kj;
     cell_ij(g, k, ki, kj);
     const bool ismaster = a.master[k] == k;
     const T dv = pick<T>(g.dv_f, g.dv);
     for (int comp = 0; comp < 2; ++comp) {
-        T nu = 0;
+        T nu[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) nu[e] = T(0);
         if (ismaster) {
             const T *o = aux + 5 * (long)k;
-            nu += mu_of<T>(a, lam, mucv, k, comp, p) * (T(1) - o[0]);
-            nu += comp == 0 ? dv * (o[1] + o[2] * vc.vx + o[3] * vc.vy + o[4] * T(0.5) * (vc.vx * vc.vx + vc.vy * vc.vy))
-                            : dv * o[4];
+            T m[W];
+            mu_of_v<T>(a, lam, mucv, k, comp, p, m);
+#pragma unroll
+            for (int e = 0; e < W; ++e)
+                nu[e] = m[e] * (T(1) - o[0]) +
+                        (comp == 0 ? dv * (o[1] + o[2] * vx[e] + o[3] * vy[e] +
+                                           o[4] * T(0.5) * (vx[e] * vx[e] + vy[e] * vy[e]))
+                                   : dv * o[4]);
         }
-        nu += gather_axis<T>(a, f, lam, mucv, 0, ki, kj, comp, p, vc.vx, vc.nux);
-        nu += gather_axis<T>(a, f, lam, mucv, 1, ki, kj, comp, p, vc.vy, vc.nuy);
-        lam_out[ebase<T>(g, comp, p) + pk] = nu;
+        gather_axis<T>(a, f, lam, mucv, 0, ki, kj, comp, p, vx, nux, nu);
+        gather_axis<T>(a, f, lam, mucv, 1, ki, kj, comp, p, vy, nuy, nu);
+#pragma unroll
+        for (int e = 0; e < W; ++e)
+            if (p + e >= g.nv) nu[e] = T(0);
+        vst<T>(reinterpret_cast<V *>(lam_out + ebase<T>(g, comp, p)) + pk, nu);
     }
-}
-
-// Generic gather over the listed cells (those near cut cells and merged
-// control volumes), one thread per (listed cell, velocity).
-template <typename T>
-__global__ void __launch_bounds__(256) k_adj_gather_list(AdjArgs a, const T *f, const T *lam, const T *mucv,
-                                                         const T *aux, const int32_t *list, int nlist, T *lam_out)
-{
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)nlist * a.g.nvp) return;
-    gather_generic<T>(a, f, lam, mucv, aux, lam_out, list[t / a.g.nvp], (int)(t % a.g.nvp));
 }
 
 // Transpose of the face fluxes along one axis for a cell deep in the gas, in
@@ -532,6 +563,94 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_adj_gather_fast(AdjArgs a, co
     }
 }
 
+// Pads beyond a side, from its boundary cell (lambda of the pads is 0, the
+// branch word of the inner pad P1 is the one its boundary face recorded):
+// for a velocity entering through the side the inner pad receives nu
+// (lambda_0 (1 - k s1(P1) + k s2(P1)) - k s2(0) (lambda_1 - lambda_0)) and the
+// outer pad -nu k s2(P1) lambda_0; for one leaving, the inner pad receives
+// -nu k s1(0) lambda_0.  lambda_1 is the next cell inwards; the return value
+// is the sum over both pads (both copy the boundary cell, or both hold the
+// same ghost value).
+template <typename T, bool MUSCL>
+__device__ __forceinline__ T pad_pair(bool inward, T nu, T l0, T l1, uint32_t bp1, uint32_t bo)
+{
+    const T kap = T(0.5) * (T(1) - nu);
+    if (inward) {
+        T r = l0;
+        if (MUSCL) {
+            if (bp1 & 1u) r -= kap * l0;
+            else if (bp1 & 2u) r += kap * l0;
+            if (bo & 2u) r -= kap * (l1 - l0);
+            if (bp1 & 2u) r -= kap * l0;
+        }
+        return nu * r;
+    }
+    return (MUSCL && (bo & 1u)) ? -nu * kap * l0 : T(0);
+}
+
+// Pads of a zero-gradient or Maxwellian side whose boundary cell is a fast
+// cell (one thread per (side cell, velocity group), after the fast gather):
+// folded onto the boundary cell (zero-gradient) or summed over the steps
+// into pacc (Maxwellian; a reduction without return, one adder per address
+// and step, so the sum is deterministic).
+template <typename T, bool MUSCL>
+__global__ void __launch_bounds__(256) k_adj_pads_fast(AdjArgs a, const T *lam, const uint32_t *bits, long bslab,
+                                                       int bpitch, int side, int nside, const uint8_t *fast,
+                                                       double *pacc, T *lam_out)
+{
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    const Grid2D &g = a.g;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nside * g.ngrp) return;
+    const int q = (int)(t % nside), grp = (int)(t / nside), p = grp * W;
+    const int axis = side >> 1;
+    const int n = axis == 0 ? g.nx : g.ny;
+    const int ib = (side & 1) ? n - 1 : 0;                  // boundary cell along the axis
+    const int ci = axis == 0 ? ib : q, cj = axis == 0 ? q : ib;
+    const long k = (long)cj * g.nx + ci;
+    if (!fast[k]) return;
+    const int di = axis == 0 ? ((side & 1) ? 1 : -1) : 0, dj = axis == 1 ? ((side & 1) ? 1 : -1) : 0;
+    uint32_t bo = 0, bp1 = 0;
+    if (MUSCL) {
+        const uint32_t *bq = bits + (long)grp * bslab;
+        bo = bq[(long)(cj + 2) * bpitch + ci + 2];
+        bp1 = bq[(long)(cj + dj + 2) * bpitch + ci + di + 2];
+    }
+    T vv[W], nu[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p + e);
+        vv[e] = axis == 0 ? vc.vx : vc.vy;
+        nu[e] = axis == 0 ? vc.nux : vc.nuy;
+    }
+    for (int comp = 0; comp < 2; ++comp) {
+        const V *L = reinterpret_cast<const V *>(lam + ebase<T>(g, comp, p));
+        T l0[W], l1[W], ps[W];
+        vld<T>(L + nbr(g, ci, cj), l0);
+        vld<T>(L + nbr(g, ci - di, cj - dj), l1);
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const int sh = ((comp * 2 + axis) * W + e) * 2;
+            const bool inward = (side & 1) ? vv[e] < T(0) : vv[e] > T(0);
+            ps[e] = p + e < g.nv ? pad_pair<T, MUSCL>(inward, nu[e], l0[e], l1[e], bp1 >> sh, bo >> sh) : T(0);
+        }
+        if (g.bc[side] == DVM_BC_MAXWELLIAN) {
+            double *o = pacc + ((long)q * 2 + comp) * g.nv + p;
+#pragma unroll
+            for (int e = 0; e < W; ++e)
+                if (p + e < g.nv) atomicAdd(o + e, (double)ps[e]);
+        } else {
+            V *o = reinterpret_cast<V *>(lam_out + ebase<T>(g, comp, p)) + nbr(g, ci, cj);
+            T cur[W];
+            vld<T>(o, cur);
+#pragma unroll
+            for (int e = 0; e < W; ++e) cur[e] += ps[e];
+            vst<T>(o, cur);
+        }
+    }
+}
+
 // Cells eligible for the fast gather: plain gas cells whose neighbours within
 // two cells along each axis are plain gas cells or boundary pads (a pad adds
 // no adjoint weight; the branch of a face between a pad and a plain cell is
@@ -549,6 +668,22 @@ __global__ void k_adj_fastmask(Grid2D g, const uint8_t *flags, uint8_t *fast)
              (jj < 0 || jj >= g.ny || (flags[(long)jj * g.nx + i] & kPlain));
     }
     fast[k] = ok ? 1 : 0;
+}
+
+// Side cells whose pads the generic pad kernel has to gather (all of them on
+// periodic sides, those whose boundary cell is not a fast cell elsewhere).
+__global__ void k_adj_padcount(Grid2D g, const uint8_t *fast, int padsides, int *cnt)
+{
+    const int side = blockIdx.y;
+    const int nside = side < 2 ? g.ny : g.nx;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nside) return;
+    bool need = true;
+    if ((padsides >> side) & 1) {
+        const int tb = (side & 1) ? (side < 2 ? g.nx : g.ny) - 1 : 0;
+        need = !fast[side < 2 ? (long)q * g.nx + tb : (long)tb * g.nx + q];
+    }
+    if (need) atomicAdd(&cnt[side], 1);
 }
 
 // Compact list of the cells in a control volume that are not eligible for
@@ -609,11 +744,17 @@ __device__ __forceinline__ WallAdj wall_adj(const AdjArgs &a, long k)
     return w;
 }
 
+// Per (wall cell, velocity): c = (v - u_w) . n_w, and M1, dM1/dT_w for c < 0.
+struct __align__(16) WallVel {
+    double cp, m1, dm1;
+};
+
 // Per wall cell, once per adjoint run (the body is fixed): the wall data,
-// and for every velocity leaving the gas (c < 0) the wall Maxwellian M1 =
-// M[1, u_w, T_w] and dM1/dT_w; with D = sum_{c<0} c M1 dv and dD/dT_w.
+// and per velocity c = (v - u_w) . n_w and, for the velocities leaving the
+// gas (c < 0), the wall Maxwellian M1 = M[1, u_w, T_w] and dM1/dT_w; with
+// D = sum_{c<0} c M1 dv and dD/dT_w.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj *wadj, double2 *wm, double2 *wd,
+__global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj *wadj, WallVel *wm, double2 *wd,
                                                       int32_t *wsec)
 {
     __shared__ double red[8 * 2];
@@ -636,7 +777,7 @@ __global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj
                 den += cp * m1 * dv;
                 dD += cp * dm1 * dv;
             }
-            wm[(long)idx * g.nv + p] = make_double2(m1, dm1);
+            wm[(long)idx * g.nv + p] = WallVel{cp, m1, dm1};
         }
         den = block_sum(den, red);
         dD = block_sum(dD, red + 8);
@@ -652,10 +793,10 @@ __global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj
 // Wall cells: the diffuse flux lw (min(c,0) phi Mw + max(c,0) F) of the update
 // (objective = 0) or the force functional (objective = 1), through phi =
 // -sum_{c>0} c f dv / D, D = sum_{c<0} c M1 dv, with dJ/dT_w per wall slot.
-// One block per wall cell, FP64 reductions; M1, D and their T_w derivatives
-// from k_adj_wall_pre.
+// One block per wall cell, FP64 reductions; c, M1, D and their T_w
+// derivatives from k_adj_wall_pre.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, int nw, const WallAdj *wadj, const double2 *wm,
+__global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, int nw, const WallAdj *wadj, const WallVel *wm,
                                                   const double2 *wd, const T *f, const T *lam, const T *mucv,
                                                   T *lam_out, double *gtw, double *jwall, int objective)
 {
@@ -670,47 +811,54 @@ __global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, int nw, const WallA
         const WallAdj w = wadj[idx];
         const long pk = pcell(g, k) * W;
         const double bk = objective ? 0.0 : (double)bown[k];
+        const double hT = 0.5 * w.Tw, blw = -bk * w.lw;
+        const WallVel *tab = wm + (long)idx * g.nv;
+        // sums over the velocities (the dv of num, sxx, sxy applied after the sums)
         double num = 0, sphi = 0, sTw = 0, sxx = 0, sxy = 0;
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
-            const VCoef<T> vc = ld_coef(vt + p);
-            const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
-            const double cp = ax * w.nwx + ay * w.nwy;
+            const WallVel m = tab[p];
+            const double cp = m.cp;
             if (cp > 0) {
                 const double fv = (double)f[ebase<T>(g, 0, p) + pk];
-                num += cp * fv * dv;
-                sxx += ax * ax * fv * dv; sxy += ax * ay * fv * dv;
-            } else if (cp < 0) {
-                const double2 m = wm[(long)idx * g.nv + p];
+                num += cp * fv;
                 if (objective) {
+                    const VCoef<T> vc = ld_coef(vt + p);
+                    const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
+                    sxx += ax * ax * fv; sxy += ax * ay * fv;
+                }
+            } else if (cp < 0) {
+                if (objective) {
+                    const VCoef<T> vc = ld_coef(vt + p);
+                    const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
                     const double wgt = (ax * ax * w.nwx + ax * ay * w.nwy) * w.lw * dv;
-                    sphi += wgt * m.x;
-                    sTw += wgt * m.y;          // times phi below
+                    sphi += wgt * m.m1;
+                    sTw += wgt * m.dm1;          // times phi below
                 } else {
-                    const double w0 = -bk * (double)mu_of<T>(a, lam, mucv, k, 0, p);
-                    const double w1 = -bk * (double)mu_of<T>(a, lam, mucv, k, 1, p);
-                    sphi += w.lw * cp * (w0 * m.x + w1 * w.Tw / 2.0 * m.x);
-                    sTw += w.lw * cp * (w0 * m.y + w1 * (m.x / 2.0 + w.Tw / 2.0 * m.y));   // times phi below
+                    const double w0 = blw * (double)mu_of<T>(a, lam, mucv, k, 0, p);
+                    const double w1 = blw * (double)mu_of<T>(a, lam, mucv, k, 1, p);
+                    sphi += cp * m.m1 * (w0 + w1 * hT);
+                    sTw += cp * (w0 * m.dm1 + w1 * (0.5 * m.m1 + hT * m.dm1));   // times phi below
                 }
             }
         }
-        num = block_sum(num, red); sphi = block_sum(sphi, red + 8); sTw = block_sum(sTw, red + 16);
-        sxx = block_sum(sxx, red + 24); sxy = block_sum(sxy, red + 32);
+        num = block_sum(num, red) * dv; sphi = block_sum(sphi, red + 8); sTw = block_sum(sTw, red + 16);
+        sxx = block_sum(sxx, red + 24) * dv; sxy = block_sum(sxy, red + 32) * dv;
         const double2 D = wd[idx];
         const double den = D.x, dD = D.y;
-        const double phi = -num / den;
+        const double phi = -num / den, sd = -sphi * dv / den;
         // per-velocity terms of the wall cell
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
-            const VCoef<T> vc = ld_coef(vt + p);
-            const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
-            const double cp = ax * w.nwx + ay * w.nwy;
+            const double cp = tab[p].cp;
             if (!(cp > 0)) continue;
             const long e0 = ebase<T>(g, 0, p) + pk, e1 = ebase<T>(g, 1, p) + pk;
-            double add0 = sphi * (-cp * dv / den), add1 = 0;
+            double add0 = sd * cp, add1 = 0;
             if (objective) {
+                const VCoef<T> vc = ld_coef(vt + p);
+                const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
                 add0 += (ax * ax * w.nwx + ax * ay * w.nwy) * w.lw * dv;
             } else {
-                add0 += -bk * (double)mu_of<T>(a, lam, mucv, k, 0, p) * w.lw * cp;
-                add1 += -bk * (double)mu_of<T>(a, lam, mucv, k, 1, p) * w.lw * cp;
+                add0 += blw * (double)mu_of<T>(a, lam, mucv, k, 0, p) * cp;
+                add1 += blw * (double)mu_of<T>(a, lam, mucv, k, 1, p) * cp;
             }
             lam_out[e0] = (T)((double)lam_out[e0] + add0);
             if (add1 != 0) lam_out[e1] = (T)((double)lam_out[e1] + add1);
@@ -735,16 +883,25 @@ __global__ void __launch_bounds__(256) k_adj_fuseT(AdjArgs a, T *lam_out)
     const CvInfo *info = reinterpret_cast<const CvInfo *>(a.cvinfo);
     const int n = min(a.counts[0], a.cap);
     constexpr int W = Vec<T>::W;
+    __shared__ long pcs[kMaxMembers];
+    __shared__ T ratio[kMaxMembers];
     for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
         const CvInfo &I = info[idx];
-        if (I.nm <= 1) continue;
+        const int nm = I.nm;
+        if (nm <= 1) continue;
+        if (threadIdx.x < nm) {
+            pcs[threadIdx.x] = I.mem[threadIdx.x].pc * W;
+            ratio[threadIdx.x] = (T)(I.mem[threadIdx.x].sb / I.Sn);
+        }
+        __syncthreads();
         for (int e = threadIdx.x; e < 2 * a.g.nvp; e += blockDim.x) {
             const int comp = e / a.g.nvp, p = e - comp * a.g.nvp;
             const long base = ebase<T>(a.g, comp, p);
             T s = 0;
-            for (int t = 0; t < I.nm; ++t) s += lam_out[base + I.mem[t].pc * W];
-            for (int t = 0; t < I.nm; ++t) lam_out[base + I.mem[t].pc * W] = (T)(I.mem[t].sb / I.Sn) * s;
+            for (int t = 0; t < nm; ++t) s += lam_out[base + pcs[t]];
+            for (int t = 0; t < nm; ++t) lam_out[base + pcs[t]] = ratio[t] * s;
         }
+        __syncthreads();
     }
 }
 
@@ -754,28 +911,40 @@ __global__ void __launch_bounds__(256) k_adj_fuseT(AdjArgs a, T *lam_out)
 // Maxwellian side, are summed over the steps per (side cell, component,
 // velocity) into pacc (the ghost state is the same at every step; the chain
 // to (rho, u, T) is k_adj_ghost_chain).  One thread per (side cell,
-// velocity); the sides are launched one after the other (a corner cell
-// receives from two sides).
+// velocity group); the sides are launched one after the other (a corner
+// cell receives from two sides).  Side cells whose boundary cell is a fast
+// cell of a zero-gradient or Maxwellian side are left to k_adj_pads_fast.
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_pads(AdjArgs a, const T *f, const T *lam, const T *mucv, int side,
-                                                  int nside, double *pacc, T *lam_out)
+                                                  int nside, const uint8_t *fast, int padsides, double *pacc,
+                                                  T *lam_out)
 {
-    const Grid2D &g = a.g;
     constexpr int W = Vec<T>::W;
+    const Grid2D &g = a.g;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)nside * g.nvp) return;
-    const int q = (int)(t / g.nvp), p = (int)(t % g.nvp);
-    if (p >= g.nv) return;
+    if (t >= (long)nside * g.ngrp) return;
+    const int q = (int)(t % nside), p = (int)(t / nside) * W;
     const int axis = side < 2 ? 0 : 1;
     const int kind = g.bc[side];
     const int n = axis == 0 ? g.nx : g.ny;
+    // the boundary cell of a zero-gradient or Maxwellian side took them if it
+    // is a fast cell
+    if ((padsides >> side) & 1) {
+        const int tb = (side & 1) ? n - 1 : 0;
+        if (fast[axis == 0 ? (long)q * g.nx + tb : (long)tb * g.nx + q]) return;
+    }
     // positions of the inner (1) and outer (2) pad along the axis, and the
     // cells they copy
     const int c1 = (side & 1) ? n : -1, c2 = (side & 1) ? n + 1 : -2;
     const int i1 = axis == 0 ? c1 : q, j1 = axis == 0 ? q : c1;
     const int i2 = axis == 0 ? c2 : q, j2 = axis == 0 ? q : c2;
-    const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p);
-    const T v = axis == 0 ? vc.vx : vc.vy, nu = axis == 0 ? vc.nux : vc.nuy;
+    T v[W], nu[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p + e);
+        v[e] = axis == 0 ? vc.vx : vc.vy;
+        nu[e] = axis == 0 ? vc.nux : vc.nuy;
+    }
     int t1, t2;
     if (kind == DVM_BC_PERIODIC) {
         t1 = (side & 1) ? 0 : n - 1;
@@ -788,9 +957,16 @@ __global__ void __launch_bounds__(256) k_adj_pads(AdjArgs a, const T *f, const T
 #pragma unroll 1
     for (int u = 0; u < 4; ++u) {
         const int comp = u >> 1, layer = u & 1;
-        const T e = gather_axis<T>(a, f, lam, mucv, axis, layer ? i2 : i1, layer ? j2 : j1, comp, p, v, nu);
-        if (kind == DVM_BC_MAXWELLIAN) pacc[((long)q * 2 + comp) * g.nv + p] += (double)e;
-        else lam_out[ebase<T>(g, comp, p) + pcell(g, layer ? k2 : k1) * W] += e;
+        T e[W];
+#pragma unroll
+        for (int x = 0; x < W; ++x) e[x] = T(0);
+        gather_axis<T>(a, f, lam, mucv, axis, layer ? i2 : i1, layer ? j2 : j1, comp, p, v, nu, e);
+#pragma unroll
+        for (int x = 0; x < W; ++x) {
+            if (p + x >= g.nv) continue;
+            if (kind == DVM_BC_MAXWELLIAN) pacc[((long)q * 2 + comp) * g.nv + p + x] += (double)e[x];
+            else lam_out[ebase<T>(g, comp, p + x) + pcell(g, layer ? k2 : k1) * W] += e[x];
+        }
     }
 }
 
@@ -878,6 +1054,7 @@ struct AdjWork {
     uint8_t *fast = nullptr;                         // cells of the fast gather
     int32_t *slow = nullptr, *nslow_d = nullptr;     // the other cells
     int nslow = 0;
+    int padneed[4] = {0, 0, 0, 0};                   // side cells left to the generic pad kernel
     void *rpart = nullptr;                           // [Z][5][nc] split sums of the relaxation transpose
     int Z = 1, Zf = 1;                               // velocity splits of the relaxation and the fast gather
     std::vector<uint32_t *> tbits, sbits;            // limiter branches per tape slot / per segment end
@@ -885,7 +1062,8 @@ struct AdjWork {
     CUtensorMap lmap[2];                             // TMA descriptors of lam[0], lam[1]
     int nw = 0, nw_cap = 0;                          // wall cells and the capacity of the wall tables
     WallAdj *wadj = nullptr;                         // per wall cell: wall data
-    double2 *wm = nullptr, *wd = nullptr;            // per wall cell: (M1, dM1/dT_w) per velocity, (D, dD/dT_w)
+    WallVel *wm = nullptr;                           // per wall cell and velocity: c, M1, dM1/dT_w
+    double2 *wd = nullptr;                           // per wall cell: (D, dD/dT_w)
     double *pacc = nullptr;                          // [side][cell][comp][nv] Maxwellian pad sensitivities
     void *fin = nullptr, *finpart = nullptr;         // F^N and its partial moments
     void *scratch_part = nullptr;                    // partial moments written by a tape fusion
@@ -929,6 +1107,16 @@ AdjArgs adj_args(dvm_ctx *c, const AdjWork &w)
 
 // One reverse step: lam_in = lambda^{n+1}, f = F^n (device layout), bits =
 // the limiter branches the step took (MUSCL) -> lam_out.
+// Sides whose pads k_adj_pads_fast takes from fast boundary cells:
+// zero-gradient sides and Maxwellian sides with a parameter state.
+inline int pad_sides(const dvm_ctx *c)
+{
+    int m = 0;
+    for (int s = 0; s < 4; ++s)
+        if (c->bc[s] == DVM_BC_ZEROGRAD || (c->bc[s] == DVM_BC_MAXWELLIAN && c->d_bcstate[s])) m |= 1 << s;
+    return m;
+}
+
 template <typename T, bool MUSCL>
 cudaError_t launch_gather_fast(dvm_ctx *c, const AdjArgs &a, const AdjWork &w, const CUtensorMap &lmap,
                                const CUtensorMap *bmap, T *lam_out)
@@ -948,8 +1136,8 @@ cudaError_t launch_gather_fast(dvm_ctx *c, const AdjArgs &a, const AdjWork &w, c
 }
 
 template <typename T>
-cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, const CUtensorMap *bmap, int lin,
-                         T *lam_out)
+cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, const uint32_t *bits,
+                         const CUtensorMap *bmap, int lin, T *lam_out)
 {
     const T *lam_in = (const T *)w.lam[lin];
     const AdjArgs a = adj_args(c, w);
@@ -964,18 +1152,32 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
                                            : launch_gather_fast<T, false>(c, a, w, w.lmap[lin], nullptr, lam_out);
     if (e != cudaSuccess) return e;
     if (w.nslow > 0)
-        k_adj_gather_list<T><<<nba((long)w.nslow * c->nvp, 256), 256, 0, c->stream>>>(a, f, lam_in, mucv, aux, w.slow,
-                                                                                      w.nslow, lam_out);
+        k_adj_gather_list<T><<<nba((long)w.nslow * c->ngrp, 256), 256, 0, c->stream>>>(a, f, lam_in, mucv, aux,
+                                                                                       w.slow, w.nslow, lam_out);
     if (w.nw > 0)
         k_adj_wall<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, f, lam_in, mucv, lam_out, w.gtw,
                                                     w.jwall, 0);
     int launched = 7;
     const int nside[4] = {c->ny, c->ny, c->nx, c->nx};
     const int nmax = c->nx > c->ny ? c->nx : c->ny;
+    const int ps = pad_sides(c);
+    for (int s = 0; s < 4; ++s) {
+        if (!((ps >> s) & 1)) continue;
+        const unsigned nb = nba((long)nside[s] * c->ngrp, 256);
+        double *pa = w.pacc + (long)s * nmax * 2 * c->nv;
+        if (c->scheme == DVM_MUSCL)
+            k_adj_pads_fast<T, true><<<nb, 256, 0, c->stream>>>(a, lam_in, bits, bits_slab(c), bits_pitch(c), s,
+                                                                nside[s], w.fast, pa, lam_out);
+        else
+            k_adj_pads_fast<T, false><<<nb, 256, 0, c->stream>>>(a, lam_in, nullptr, 0, 0, s, nside[s], w.fast, pa,
+                                                                 lam_out);
+        ++launched;
+    }
     for (int s = 0; s < 4; ++s) {
         if (c->bc[s] == DVM_BC_MAXWELLIAN && !c->d_bcstate[s]) continue;
-        k_adj_pads<T><<<nba((long)nside[s] * c->nvp, 256), 256, 0, c->stream>>>(
-            a, f, lam_in, mucv, s, nside[s], w.pacc + (long)s * nmax * 2 * c->nv, lam_out);
+        if (w.padneed[s] == 0) continue;
+        k_adj_pads<T><<<nba((long)nside[s] * c->ngrp, 256), 256, 0, c->stream>>>(
+            a, f, lam_in, mucv, s, nside[s], w.fast, ps, w.pacc + (long)s * nmax * 2 * c->nv, lam_out);
         ++launched;
     }
     k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_out);
@@ -1017,7 +1219,7 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMalloc(&w.scratch_part, partb));
         AC(cudaMalloc(&w.fast, c->nc));
         AC(cudaMalloc(&w.slow, sizeof(int32_t) * c->nc));
-        AC(cudaMalloc(&w.nslow_d, sizeof(int)));
+        AC(cudaMalloc(&w.nslow_d, 5 * sizeof(int)));
         w.Z = c->ngrp < 8 ? c->ngrp : 8;
         w.Zf = c->ngrp < 4 ? c->ngrp : 4;
         AC(cudaMalloc(&w.pacc, sizeof(double) * 4 * nmax * 2 * c->nv));
@@ -1078,13 +1280,16 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMemcpyAsync(&w.nslow, w.nslow_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         int32_t cnt0[2];
         AC(cudaMemcpyAsync(cnt0, c->counts, sizeof(cnt0), cudaMemcpyDeviceToHost, c->stream));
+        AC(cudaMemsetAsync(w.nslow_d + 1, 0, 4 * sizeof(int), c->stream));
+        k_adj_padcount<<<dim3(nba(nmax, 256), 4), 256, 0, c->stream>>>(g, w.fast, pad_sides(c), w.nslow_d + 1);
+        AC(cudaMemcpyAsync(w.padneed, w.nslow_d + 1, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         AC(cudaStreamSynchronize(c->stream));
         w.nw = cnt0[1] < c->list_cap ? cnt0[1] : c->list_cap;
         if (w.nw > w.nw_cap) {
             cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wd);
-            w.wadj = nullptr; w.wm = w.wd = nullptr; w.nw_cap = 0;
+            w.wadj = nullptr; w.wm = nullptr; w.wd = nullptr; w.nw_cap = 0;
             AC(cudaMalloc(&w.wadj, sizeof(WallAdj) * w.nw));
-            AC(cudaMalloc(&w.wm, sizeof(double2) * w.nw * c->nv));
+            AC(cudaMalloc(&w.wm, sizeof(WallVel) * w.nw * c->nv));
             AC(cudaMalloc(&w.wd, sizeof(double2) * w.nw));
             w.nw_cap = w.nw;
         }
@@ -1160,7 +1365,9 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         c->cur = cur_orig;
         for (int t = len - 1; t >= 0; --t) {
             const CUtensorMap *bm = !rec ? nullptr : (t == len - 1 ? &w.sbmap[sgi] : &w.tbmap[t]);
-            AC(adjoint_step<T>(c, w, (const T *)w.tape[t], (const T *)w.ptape[t], bm, lin, (T *)w.lam[1 - lin]));
+            const uint32_t *bits = !rec ? nullptr : (t == len - 1 ? w.sbits[sgi] : w.tbits[t]);
+            AC(adjoint_step<T>(c, w, (const T *)w.tape[t], (const T *)w.ptape[t], bits, bm, lin,
+                               (T *)w.lam[1 - lin]));
             lin = 1 - lin;
         }
     }
