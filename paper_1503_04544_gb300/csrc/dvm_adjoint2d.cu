@@ -18,7 +18,7 @@
 //                  the limiter derivative is the one of the branch the
 //                  forward step took (recorded by the recomputation for
 //                  the cells deep in the gas, re-derived from F^n elsewhere);
-//   k_adj_wall     per wall cell: the diffuse flux and the wall density
+//   k_adj_wall_*   per wall cell: the diffuse flux and the wall density
 //                  coupling (Eq. BoundaryDDv), and dJ/dT_w;
 //   k_adj_pads*    the boundary pads: the step reads them but does not
 //                  update them, so their sensitivities are gathered like a
@@ -134,28 +134,24 @@ __global__ void k_adj_setup(Grid2D g, const int32_t *master, const uint8_t *flag
 }
 
 // ------------------------------------------------------------ step kernels
-// mu of every cut or merged control volume: the sum of lambda over its members.
+// mu of every cut or merged control volume: the sum of lambda over its
+// members (one block per (control volume, chunk of velocities)).
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_mu(AdjArgs a, const T *lam, T *mucv)
 {
-    const CvInfo *info = reinterpret_cast<const CvInfo *>(a.cvinfo);
-    const int n = min(a.counts[0], a.cap);
-    constexpr int W = Vec<T>::W;
     __shared__ long pcs[kMaxMembers];
-    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
-        const CvInfo &I = info[idx];
-        const int nm = I.nm;
-        if (threadIdx.x < nm) pcs[threadIdx.x] = I.mem[threadIdx.x].pc * W;
-        __syncthreads();
-        for (int e = threadIdx.x; e < 2 * a.g.nvp; e += blockDim.x) {
-            const int comp = e / a.g.nvp, p = e - comp * a.g.nvp;
-            const long base = ebase<T>(a.g, comp, p);
-            T s = 0;
-            for (int t = 0; t < nm; ++t) s += lam[base + pcs[t]];
-            mucv[((long)idx * 2 + comp) * a.g.nvp + p] = s;
-        }
-        __syncthreads();
-    }
+    const CvInfo &I = reinterpret_cast<const CvInfo *>(a.cvinfo)[blockIdx.x];
+    constexpr int W = Vec<T>::W;
+    const int nm = I.nm;
+    if (threadIdx.x < nm) pcs[threadIdx.x] = I.mem[threadIdx.x].pc * W;
+    __syncthreads();
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= 2 * a.g.nvp) return;
+    const int comp = e / a.g.nvp, p = e - comp * a.g.nvp;
+    const long base = ebase<T>(a.g, comp, p);
+    T s = 0;
+    for (int t = 0; t < nm; ++t) s += lam[base + pcs[t]];
+    mucv[((long)blockIdx.x * 2 + comp) * a.g.nvp + p] = s;
 }
 
 // Relaxation through the moments, per control volume and velocity split
@@ -339,54 +335,162 @@ __device__ void gather_axis(const AdjArgs &a, const T *f, const T *lam, const T 
     }
 }
 
-// Generic gather over the listed cells (those near cut cells and merged
-// control volumes): relaxation terms for control-volume masters and the
-// face-flux transposes along both axes.  One thread per (listed cell,
-// velocity group), consecutive threads on consecutive listed cells.
+// What the generic gather needs of one face whose stencil reads a listed
+// cell, fixed for a fixed body: the adjoint sources of its two sides (>= 0:
+// padded cell of lambda; < 0: -(index + 1) of a merged control volume's mu),
+// their weights b (0 for a pad), the face length, the padded cells of its
+// four stencil values, the stencil slot of the listed cell, and whether the
+// limiter is used (bit 0) and the record is live (bit 1).
+template <typename T> struct __align__(16) FaceRec {
+    int srcA, srcB;
+    int fpos[4];
+    T L, bA, bB;
+    int bits;                 // 1: limiter, 2: live; slot in bits 4..5
+};
+
+// Face records of the listed cells: record (idx, axis, t) is the face
+// between positions c - 2 + t and c - 1 + t along the axis (the loop of
+// gather_axis); one thread per record.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_gather_list(AdjArgs a, const T *f, const T *lam, const T *mucv,
-                                                         const T *aux, const int32_t *list, int nlist, T *lam_out)
+__global__ void k_adj_listrec(AdjArgs a, const int32_t *list, int nlist, FaceRec<T> *rec)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nlist * 8) return;
+    const Grid2D &g = a.g;
+    const int idx = (int)(t >> 3), axis = (int)((t >> 2) & 1), slotf = (int)(t & 3);
+    const int k = list[idx];
+    int ti, tj;
+    cell_ij(g, k, ti, tj);
+    const int n = axis == 0 ? g.nx : g.ny;
+    const int c = axis == 0 ? ti : tj;
+    const int ii = c - 2 + slotf;
+    FaceRec<T> R{};
+    const bool aint = ii >= 0 && ii < n, bint = ii + 1 >= 0 && ii + 1 < n;
+    if (aint || bint) {
+        const int ia = axis == 0 ? ii : ti, ja = axis == 0 ? tj : ii;
+        const int ib = axis == 0 ? ii + 1 : ti, jb = axis == 0 ? tj : ii + 1;
+        const int A = aint ? ja * g.nx + ia : -1;
+        const int B = bint ? jb * g.nx + ib : -1;
+        T L;
+        bool lim;
+        if (A >= 0) {
+            L = axis == 0 ? (T)a.G.lx[(long)ja * (g.nx + 1) + ia + 1] : (T)a.G.ly[(long)(ja + 1) * g.nx + ia];
+            lim = a.muscl && ((a.flags[A] >> kMaskShift) & (axis == 0 ? 2 : 8));
+        } else {
+            L = axis == 0 ? (T)a.G.lx[(long)jb * (g.nx + 1) + ib] : (T)a.G.ly[(long)jb * g.nx + ib];
+            lim = a.muscl && ((a.flags[B] >> kMaskShift) & (axis == 0 ? 1 : 4));
+        }
+        const T *bown = reinterpret_cast<const T *>(a.bown);
+        const T bA = A >= 0 ? bown[A] : T(0), bB = B >= 0 ? bown[B] : T(0);
+        if (L != T(0) && (bA != T(0) || bB != T(0))) {
+            const auto src = [&](int cell) { return a.cvx[cell] >= 0 ? -(a.cvx[cell] + 1) : (int)pcell(g, cell); };
+            R.srcA = bA != T(0) ? src(A) : 0;
+            R.srcB = bB != T(0) ? src(B) : 0;
+            for (int q = 0; q < 4; ++q) {
+                const int pos = ii - 1 + q;
+                R.fpos[q] = (int)nbr(g, axis == 0 ? pos : ti, axis == 0 ? tj : pos);
+            }
+            R.L = L; R.bA = bA; R.bB = bB;
+            R.bits = (lim ? 1 : 0) | 2 | ((c - ii + 1) << 4);
+        }
+    }
+    rec[t] = R;
+}
+
+// lambda or mu of an adjoint source for the W velocities at p.
+template <typename T>
+__device__ __forceinline__ void src_load(const Grid2D &g, const T *lam, const T *mucv, int src, int comp, int p,
+                                         T (&r)[Vec<T>::W])
+{
+    using V = typename Vec<T>::type;
+    if (src < 0) vld<T>(reinterpret_cast<const V *>(mucv + ((long)(-src - 1) * 2 + comp) * g.nvp + p), r);
+    else vld<T>(reinterpret_cast<const V *>(lam + ebase<T>(g, comp, p)) + src, r);
+}
+
+// Generic gather over the listed cells from their face records: relaxation
+// terms for control-volume masters and the face-flux transposes along both
+// axes.  A block takes 64 (listed cell, velocity group) items, consecutive on
+// consecutive listed cells; its four quarters take the (component, axis)
+// pairs, four face records each, and the sums meet in shared memory.
+constexpr int kRecItems = 64;
+template <typename T>
+__global__ void __launch_bounds__(4 * kRecItems) k_adj_gather_rec(AdjArgs a, const T *f, const T *lam,
+                                                                  const T *mucv, const T *aux, const int32_t *list,
+                                                                  int nlist, const FaceRec<T> *rec, T *lam_out)
 {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
+    __shared__ T part[4][kRecItems][W];
     const Grid2D &g = a.g;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)nlist * g.ngrp) return;
-    const int q = (int)(t / nlist), k = list[t % nlist];
+    const int sub = threadIdx.x / kRecItems, it = threadIdx.x % kRecItems;
+    const int comp = sub >> 1, ax = sub & 1;
+    const long t = (long)blockIdx.x * kRecItems + it;
+    const bool live = t < (long)nlist * g.ngrp;
+    const int q = live ? (int)(t / nlist) : 0, idx = live ? (int)(t % nlist) : 0;
     const int p = q * W;
-    const long pk = pcell(g, k);
-    T vx[W], vy[W], nux[W], nuy[W];
+    T acc[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) acc[e] = T(0);
+    if (live) {
+        T v[W], nu[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p + e);
+            v[e] = ax ? vc.vy : vc.vx;
+            nu[e] = ax ? vc.nuy : vc.nux;
+        }
+        const V *F = reinterpret_cast<const V *>(f + ebase<T>(g, comp, p));
+        const FaceRec<T> *R0 = rec + (long)idx * 8 + ax * 4;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const FaceRec<T> R = R0[r];
+            if (!(R.bits & 2)) continue;
+            T mA[W], mB[W], fv[4][W];
+            if (R.bA != T(0)) src_load<T>(g, lam, mucv, R.srcA, comp, p, mA);
+            if (R.bB != T(0)) src_load<T>(g, lam, mucv, R.srcB, comp, p, mB);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) vld<T>(F + R.fpos[u], fv[u]);
+            const int slot = (R.bits >> 4) & 3;
+            const bool lim = R.bits & 1;
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const T Wf = (R.bA != T(0) ? -R.bA * mA[e] : T(0)) + (R.bB != T(0) ? R.bB * mB[e] : T(0));
+                T d[4];
+                face_flux_d<T>(R.L, v[e], nu[e], fv[0][e], fv[1][e], fv[2][e], fv[3][e], lim, d);
+                acc[e] += Wf * d[slot];
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) part[sub][it][e] = acc[e];
+    __syncthreads();
+    if (sub >= 2 || !live) return;
+    // quarter 0 and 1: component 0 and 1 of the item, relaxation terms
+    const int k = list[idx];
+    T out[W], vx[W], vy[W];
 #pragma unroll
     for (int e = 0; e < W; ++e) {
         const VCoef<T> vc = ld_coef(reinterpret_cast<const VCoef<T> *>(a.vt) + p + e);
-        vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
+        vx[e] = vc.vx; vy[e] = vc.vy;
+        out[e] = T(0);
     }
-    int ki, kj;
-    cell_ij(g, k, ki, kj);
-    const bool ismaster = a.master[k] == k;
-    const T dv = pick<T>(g.dv_f, g.dv);
-    for (int comp = 0; comp < 2; ++comp) {
-        T nu[W];
-#pragma unroll
-        for (int e = 0; e < W; ++e) nu[e] = T(0);
-        if (ismaster) {
-            const T *o = aux + 5 * (long)k;
-            T m[W];
-            mu_of_v<T>(a, lam, mucv, k, comp, p, m);
-#pragma unroll
-            for (int e = 0; e < W; ++e)
-                nu[e] = m[e] * (T(1) - o[0]) +
-                        (comp == 0 ? dv * (o[1] + o[2] * vx[e] + o[3] * vy[e] +
-                                           o[4] * T(0.5) * (vx[e] * vx[e] + vy[e] * vy[e]))
-                                   : dv * o[4]);
-        }
-        gather_axis<T>(a, f, lam, mucv, 0, ki, kj, comp, p, vx, nux, nu);
-        gather_axis<T>(a, f, lam, mucv, 1, ki, kj, comp, p, vy, nuy, nu);
+    if (a.master[k] == k) {
+        const T dv = pick<T>(g.dv_f, g.dv);
+        const T *o = aux + 5 * (long)k;
+        T m[W];
+        mu_of_v<T>(a, lam, mucv, k, sub, p, m);
 #pragma unroll
         for (int e = 0; e < W; ++e)
-            if (p + e >= g.nv) nu[e] = T(0);
-        vst<T>(reinterpret_cast<V *>(lam_out + ebase<T>(g, comp, p)) + pk, nu);
+            out[e] = m[e] * (T(1) - o[0]) +
+                     (sub == 0 ? dv * (o[1] + o[2] * vx[e] + o[3] * vy[e] + o[4] * T(0.5) * (vx[e] * vx[e] + vy[e] * vy[e]))
+                               : dv * o[4]);
     }
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        out[e] += part[sub * 2][it][e] + part[sub * 2 + 1][it][e];
+        if (p + e >= g.nv) out[e] = T(0);
+    }
+    vst<T>(reinterpret_cast<V *>(lam_out + ebase<T>(g, sub, p)) + pcell(g, k), out);
 }
 
 // Transpose of the face fluxes along one axis for a cell deep in the gas, in
@@ -428,7 +532,7 @@ constexpr int kAdjStageBytes = kAdjLamBytes + kAdjBitsBytes;
 // kAdjStages-deep shared-memory ring on "full" mbarriers; each warp releases
 // a stage on its "empty" mbarrier, and thread 0 refills a stage only after
 // all warps released it.  Every wait is bounded (on timeout the kernel sets
-// kErrTimeout and goes on).  Other cells are left to k_adj_gather_list.
+// kErrTimeout and goes on).  Other cells are left to k_adj_gather_rec.
 template <typename T, bool MUSCL>
 __global__ void __launch_bounds__(32 * kRows, 2) k_adj_gather_fast(AdjArgs a, const __grid_constant__ CUtensorMap lmap,
                                                                    const __grid_constant__ CUtensorMap bmap,
@@ -589,20 +693,26 @@ __device__ __forceinline__ T pad_pair(bool inward, T nu, T l0, T l1, uint32_t bp
 }
 
 // Pads of a zero-gradient or Maxwellian side whose boundary cell is a fast
-// cell (one thread per (side cell, velocity group), after the fast gather):
+// cell (one thread per (side, side cell, velocity group), after the fast
+// gather; the two sides of one axis together, as they touch distinct cells):
 // folded onto the boundary cell (zero-gradient) or summed over the steps
 // into pacc (Maxwellian; a reduction without return, one adder per address
 // and step, so the sum is deterministic).
 template <typename T, bool MUSCL>
 __global__ void __launch_bounds__(256) k_adj_pads_fast(AdjArgs a, const T *lam, const uint32_t *bits, long bslab,
-                                                       int bpitch, int side, int nside, const uint8_t *fast,
-                                                       double *pacc, T *lam_out)
+                                                       int bpitch, int side0, int sides, int nside, int padmask,
+                                                       const uint8_t *fast, double *pacc, int nmax, T *lam_out)
 {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     const Grid2D &g = a.g;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)nside * g.ngrp) return;
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long per = (long)nside * g.ngrp;
+    if (t >= per * sides) return;
+    const int side = side0 + (int)(t / per);
+    t %= per;
+    if (!((padmask >> side) & 1)) return;
+    pacc += (long)side * nmax * 2 * g.nv;
     const int q = (int)(t % nside), grp = (int)(t / nside), p = grp * W;
     const int axis = side >> 1;
     const int n = axis == 0 ? g.nx : g.ny;
@@ -744,9 +854,13 @@ __device__ __forceinline__ WallAdj wall_adj(const AdjArgs &a, long k)
     return w;
 }
 
-// Per (wall cell, velocity): c = (v - u_w) . n_w, and M1, dM1/dT_w for c < 0.
+// Per (wall cell, velocity): c = (v - u_w) . n_w, and M1, dM1/dT_w for c < 0;
+// in FP64 (the objective) and in the state precision (the transposed steps).
 struct __align__(16) WallVel {
     double cp, m1, dm1;
+};
+template <typename T> struct WallVelT {
+    T cp, m1, dm1;
 };
 
 // Per wall cell, once per adjoint run (the body is fixed): the wall data,
@@ -754,8 +868,8 @@ struct __align__(16) WallVel {
 // gas (c < 0), the wall Maxwellian M1 = M[1, u_w, T_w] and dM1/dT_w; with
 // D = sum_{c<0} c M1 dv and dD/dT_w.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj *wadj, WallVel *wm, double2 *wd,
-                                                      int32_t *wsec)
+__global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj *wadj, WallVel *wm, WallVelT<T> *wt,
+                                                      double2 *wd, int32_t *wsec)
 {
     __shared__ double red[8 * 2];
     const Grid2D &g = a.g;
@@ -778,6 +892,7 @@ __global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj
                 dD += cp * dm1 * dv;
             }
             wm[(long)idx * g.nv + p] = WallVel{cp, m1, dm1};
+            wt[(long)idx * g.nv + p] = WallVelT<T>{(T)cp, (T)m1, (T)dm1};
         }
         den = block_sum(den, red);
         dD = block_sum(dD, red + 8);
@@ -790,119 +905,136 @@ __global__ void __launch_bounds__(256) k_adj_wall_pre(AdjArgs a, int nw, WallAdj
     }
 }
 
-// Wall cells: the diffuse flux lw (min(c,0) phi Mw + max(c,0) F) of the update
-// (objective = 0) or the force functional (objective = 1), through phi =
-// -sum_{c>0} c f dv / D, D = sum_{c<0} c M1 dv, with dJ/dT_w per wall slot.
-// One block per wall cell, FP64 reductions; c, M1, D and their T_w
-// derivatives from k_adj_wall_pre.
+// Wall cells of a transposed step: the diffuse flux lw (min(c,0) phi M1 +
+// max(c,0) F) of the update, through phi = -sum_{c>0} c f dv / D, D =
+// sum_{c<0} c M1 dv, with dJ/dT_w per wall slot.  One block per wall cell;
+// the per-velocity terms in the state precision with compensated sums (FP64
+// arithmetic is scarce on this GPU), phi and the T_w chain in FP64.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_wall(AdjArgs a, int nw, const WallAdj *wadj, const WallVel *wm,
-                                                  const double2 *wd, const T *f, const T *lam, const T *mucv,
-                                                  T *lam_out, double *gtw, double *jwall, int objective)
+__global__ void __launch_bounds__(256) k_adj_wall_step(AdjArgs a, int nw, const WallAdj *wadj,
+                                                       const WallVelT<T> *wt, const double2 *wd, const T *f,
+                                                       const T *lam, const T *mucv, T *lam_out, double *gtw)
+{
+    __shared__ T red[8 * 2];
+    const Grid2D &g = a.g;
+    const T *bown = reinterpret_cast<const T *>(a.bown);
+    constexpr int W = Vec<T>::W;
+    for (int idx = blockIdx.x; idx < nw; idx += gridDim.x) {
+        const int k = a.wall_list[idx];
+        const WallAdj w = wadj[idx];
+        const long pk = pcell(g, k) * W;
+        const T hT = (T)(0.5 * w.Tw), blw = -bown[k] * (T)w.lw;
+        const WallVelT<T> *tab = wt + (long)idx * g.nv;
+        Acc<T> num, sphi, sTw;
+        for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
+            const WallVelT<T> m = tab[p];
+            if (m.cp > T(0)) {
+                num.add(m.cp * f[ebase<T>(g, 0, p) + pk]);
+            } else if (m.cp < T(0)) {
+                const T w0 = blw * mu_of<T>(a, lam, mucv, k, 0, p);
+                const T w1 = blw * mu_of<T>(a, lam, mucv, k, 1, p);
+                sphi.add(m.cp * m.m1 * (w0 + w1 * hT));
+                sTw.add(m.cp * (w0 * m.dm1 + w1 * (T(0.5) * m.m1 + hT * m.dm1)));   // times phi below
+            }
+        }
+        const double numd = (double)block_acc(num, red) * g.dv;
+        const double sphid = (double)block_acc(sphi, red);
+        const double sTwd = (double)block_acc(sTw, red);
+        const double2 D = wd[idx];
+        const double phi = -numd / D.x;
+        const T sd = (T)(-sphid * g.dv / D.x);
+        // per-velocity terms of the wall cell
+        for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
+            const T cp = tab[p].cp;
+            if (!(cp > T(0))) continue;
+            const long e0 = ebase<T>(g, 0, p) + pk, e1 = ebase<T>(g, 1, p) + pk;
+            lam_out[e0] += cp * (sd + blw * mu_of<T>(a, lam, mucv, k, 0, p));
+            lam_out[e1] += cp * blw * mu_of<T>(a, lam, mucv, k, 1, p);
+        }
+        if (threadIdx.x == 0) gtw[idx] += phi * sTwd + sphid * (-phi / D.x) * D.y;
+        __syncthreads();
+    }
+}
+
+// The objective J = F_x of the wall stress (Eqs. StressTensorDD, eq-force) on
+// the wall cells: dJ/dF into lambda (outgoing velocities directly, incoming
+// ones through phi = -sum_{c>0} c f dv / D), J per wall slot and its direct
+// T_w derivative.  One block per wall cell, FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_wall_obj(AdjArgs a, int nw, const WallAdj *wadj, const WallVel *wm,
+                                                      const double2 *wd, const T *f, T *lam_out, double *gtw,
+                                                      double *jwall)
 {
     __shared__ double red[8 * 5];
     const Grid2D &g = a.g;
     const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(a.vt);
-    const T *bown = reinterpret_cast<const T *>(a.bown);
     constexpr int W = Vec<T>::W;
     const double dv = g.dv;
     for (int idx = blockIdx.x; idx < nw; idx += gridDim.x) {
         const int k = a.wall_list[idx];
         const WallAdj w = wadj[idx];
         const long pk = pcell(g, k) * W;
-        const double bk = objective ? 0.0 : (double)bown[k];
-        const double hT = 0.5 * w.Tw, blw = -bk * w.lw;
         const WallVel *tab = wm + (long)idx * g.nv;
         // sums over the velocities (the dv of num, sxx, sxy applied after the sums)
         double num = 0, sphi = 0, sTw = 0, sxx = 0, sxy = 0;
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
             const WallVel m = tab[p];
-            const double cp = m.cp;
-            if (cp > 0) {
+            const VCoef<T> vc = ld_coef(vt + p);
+            const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
+            if (m.cp > 0) {
                 const double fv = (double)f[ebase<T>(g, 0, p) + pk];
-                num += cp * fv;
-                if (objective) {
-                    const VCoef<T> vc = ld_coef(vt + p);
-                    const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
-                    sxx += ax * ax * fv; sxy += ax * ay * fv;
-                }
-            } else if (cp < 0) {
-                if (objective) {
-                    const VCoef<T> vc = ld_coef(vt + p);
-                    const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
-                    const double wgt = (ax * ax * w.nwx + ax * ay * w.nwy) * w.lw * dv;
-                    sphi += wgt * m.m1;
-                    sTw += wgt * m.dm1;          // times phi below
-                } else {
-                    const double w0 = blw * (double)mu_of<T>(a, lam, mucv, k, 0, p);
-                    const double w1 = blw * (double)mu_of<T>(a, lam, mucv, k, 1, p);
-                    sphi += cp * m.m1 * (w0 + w1 * hT);
-                    sTw += cp * (w0 * m.dm1 + w1 * (0.5 * m.m1 + hT * m.dm1));   // times phi below
-                }
+                num += m.cp * fv;
+                sxx += ax * ax * fv; sxy += ax * ay * fv;
+            } else if (m.cp < 0) {
+                const double wgt = (ax * ax * w.nwx + ax * ay * w.nwy) * w.lw * dv;
+                sphi += wgt * m.m1;
+                sTw += wgt * m.dm1;          // times phi below
             }
         }
         num = block_sum(num, red) * dv; sphi = block_sum(sphi, red + 8); sTw = block_sum(sTw, red + 16);
         sxx = block_sum(sxx, red + 24) * dv; sxy = block_sum(sxy, red + 32) * dv;
         const double2 D = wd[idx];
-        const double den = D.x, dD = D.y;
-        const double phi = -num / den, sd = -sphi * dv / den;
-        // per-velocity terms of the wall cell
+        const double phi = -num / D.x, sd = -sphi * dv / D.x;
         for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
             const double cp = tab[p].cp;
             if (!(cp > 0)) continue;
-            const long e0 = ebase<T>(g, 0, p) + pk, e1 = ebase<T>(g, 1, p) + pk;
-            double add0 = sd * cp, add1 = 0;
-            if (objective) {
-                const VCoef<T> vc = ld_coef(vt + p);
-                const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
-                add0 += (ax * ax * w.nwx + ax * ay * w.nwy) * w.lw * dv;
-            } else {
-                add0 += blw * (double)mu_of<T>(a, lam, mucv, k, 0, p) * cp;
-                add1 += blw * (double)mu_of<T>(a, lam, mucv, k, 1, p) * cp;
-            }
-            lam_out[e0] = (T)((double)lam_out[e0] + add0);
-            if (add1 != 0) lam_out[e1] = (T)((double)lam_out[e1] + add1);
+            const VCoef<T> vc = ld_coef(vt + p);
+            const double ax = (double)vc.vx - w.uwx, ay = (double)vc.vy - w.uwy;
+            const long e0 = ebase<T>(g, 0, p) + pk;
+            lam_out[e0] = (T)((double)lam_out[e0] + sd * cp + (ax * ax * w.nwx + ax * ay * w.nwy) * w.lw * dv);
         }
         if (threadIdx.x == 0) {
-            gtw[idx] += phi * sTw + sphi * (-phi / den) * dD;
-            if (objective) {
-                // the incoming part of the stress: phi times the M1 sums
-                const double sin_xx_xy = sphi;          // sum (ax^2 nwx + ax ay nwy) lw dv M1
-                jwall[idx] = (sxx * w.nwx + sxy * w.nwy) * w.lw + phi * sin_xx_xy;
-            }
+            gtw[idx] += phi * sTw + sphi * (-phi / D.x) * D.y;
+            // the incoming part of the stress: phi times the M1 sums
+            jwall[idx] = (sxx * w.nwx + sxy * w.nwy) * w.lw + phi * sphi;
         }
         __syncthreads();
     }
 }
 
 // Transpose of the fusion: lam_k = (sbar_k / S) sum_{j in CV} nu_j for merged
-// control volumes.
+// control volumes (one block per (control volume, chunk of velocities)).
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_fuseT(AdjArgs a, T *lam_out)
 {
-    const CvInfo *info = reinterpret_cast<const CvInfo *>(a.cvinfo);
-    const int n = min(a.counts[0], a.cap);
-    constexpr int W = Vec<T>::W;
     __shared__ long pcs[kMaxMembers];
     __shared__ T ratio[kMaxMembers];
-    for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
-        const CvInfo &I = info[idx];
-        const int nm = I.nm;
-        if (nm <= 1) continue;
-        if (threadIdx.x < nm) {
-            pcs[threadIdx.x] = I.mem[threadIdx.x].pc * W;
-            ratio[threadIdx.x] = (T)(I.mem[threadIdx.x].sb / I.Sn);
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < 2 * a.g.nvp; e += blockDim.x) {
-            const int comp = e / a.g.nvp, p = e - comp * a.g.nvp;
-            const long base = ebase<T>(a.g, comp, p);
-            T s = 0;
-            for (int t = 0; t < nm; ++t) s += lam_out[base + pcs[t]];
-            for (int t = 0; t < nm; ++t) lam_out[base + pcs[t]] = ratio[t] * s;
-        }
-        __syncthreads();
+    const CvInfo &I = reinterpret_cast<const CvInfo *>(a.cvinfo)[blockIdx.x];
+    constexpr int W = Vec<T>::W;
+    const int nm = I.nm;
+    if (nm <= 1) return;
+    if (threadIdx.x < nm) {
+        pcs[threadIdx.x] = I.mem[threadIdx.x].pc * W;
+        ratio[threadIdx.x] = (T)(I.mem[threadIdx.x].sb / I.Sn);
     }
+    __syncthreads();
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= 2 * a.g.nvp) return;
+    const int comp = e / a.g.nvp, p = e - comp * a.g.nvp;
+    const long base = ebase<T>(a.g, comp, p);
+    T s = 0;
+    for (int t = 0; t < nm; ++t) s += lam_out[base + pcs[t]];
+    for (int t = 0; t < nm; ++t) lam_out[base + pcs[t]] = ratio[t] * s;
 }
 
 // The two pad layers of one side: their sensitivities (the flux transposes
@@ -1055,6 +1187,8 @@ struct AdjWork {
     int32_t *slow = nullptr, *nslow_d = nullptr;     // the other cells
     int nslow = 0;
     int padneed[4] = {0, 0, 0, 0};                   // side cells left to the generic pad kernel
+    int ncv = 0;                                     // cut and merged control volumes
+    void *frec = nullptr;                            // FaceRec per (listed cell, axis, face)
     void *rpart = nullptr;                           // [Z][5][nc] split sums of the relaxation transpose
     int Z = 1, Zf = 1;                               // velocity splits of the relaxation and the fast gather
     std::vector<uint32_t *> tbits, sbits;            // limiter branches per tape slot / per segment end
@@ -1063,12 +1197,14 @@ struct AdjWork {
     int nw = 0, nw_cap = 0;                          // wall cells and the capacity of the wall tables
     WallAdj *wadj = nullptr;                         // per wall cell: wall data
     WallVel *wm = nullptr;                           // per wall cell and velocity: c, M1, dM1/dT_w
+    void *wt = nullptr;                              // the same in the state precision
     double2 *wd = nullptr;                           // per wall cell: (D, dD/dT_w)
     double *pacc = nullptr;                          // [side][cell][comp][nv] Maxwellian pad sensitivities
     void *fin = nullptr, *finpart = nullptr;         // F^N and its partial moments
     void *scratch_part = nullptr;                    // partial moments written by a tape fusion
     std::vector<void *> ckpt, ckpt_part, tape, ptape;
     std::vector<CUtensorMap> tmaps;                  // TMA descriptors of the tape buffers
+    std::vector<CUtensorMap> cmaps;                  // TMA descriptors of the checkpoints
     int cap = 0;
 };
 
@@ -1079,7 +1215,7 @@ void release(AdjWork &w)
     cudaFree(w.gtw); cudaFree(w.jwall); cudaFree(w.gbc); cudaFree(w.ginit); cudaFree(w.wsec);
     cudaFree(w.fin); cudaFree(w.finpart); cudaFree(w.scratch_part);
     cudaFree(w.fast); cudaFree(w.slow); cudaFree(w.nslow_d); cudaFree(w.rpart);
-    cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wd); cudaFree(w.pacc);
+    cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wt); cudaFree(w.wd); cudaFree(w.pacc); cudaFree(w.frec);
     for (uint32_t *p : w.tbits) cudaFree(p);
     for (uint32_t *p : w.sbits) cudaFree(p);
     for (void *p : w.ckpt) cudaFree(p);
@@ -1141,9 +1277,9 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
 {
     const T *lam_in = (const T *)w.lam[lin];
     const AdjArgs a = adj_args(c, w);
-    const int cvgrid = 4 * 152;
     T *mucv = (T *)w.mucv, *aux = (T *)w.aux;
-    k_adj_mu<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_in, mucv);
+    const dim3 cvg((unsigned)(w.ncv > 0 ? w.ncv : 1), nba(2L * c->nvp, 256));
+    if (w.ncv > 0) k_adj_mu<T><<<cvg, 256, 0, c->stream>>>(a, lam_in, mucv);
     const dim3 cgrid(nba(c->nx, 32), nba(c->ny, 8)), cblock(32, 8);
     k_adj_relax<T><<<dim3(cgrid.x, cgrid.y, w.Z), cblock, 0, c->stream>>>(a, f, part, c->S, lam_in, mucv,
                                                                           (T *)w.rpart);
@@ -1152,26 +1288,31 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
                                            : launch_gather_fast<T, false>(c, a, w, w.lmap[lin], nullptr, lam_out);
     if (e != cudaSuccess) return e;
     if (w.nslow > 0)
-        k_adj_gather_list<T><<<nba((long)w.nslow * c->ngrp, 256), 256, 0, c->stream>>>(a, f, lam_in, mucv, aux,
-                                                                                       w.slow, w.nslow, lam_out);
+        k_adj_gather_rec<T><<<nba((long)w.nslow * c->ngrp, kRecItems), 4 * kRecItems, 0, c->stream>>>(
+            a, f, lam_in, mucv, aux, w.slow, w.nslow, (const FaceRec<T> *)w.frec, lam_out);
     if (w.nw > 0)
-        k_adj_wall<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, f, lam_in, mucv, lam_out, w.gtw,
-                                                    w.jwall, 0);
+        k_adj_wall_step<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, (const WallVelT<T> *)w.wt, w.wd, f,
+                                                         lam_in, mucv, lam_out, w.gtw);
     int launched = 7;
     const int nside[4] = {c->ny, c->ny, c->nx, c->nx};
     const int nmax = c->nx > c->ny ? c->nx : c->ny;
     const int ps = pad_sides(c);
-    for (int s = 0; s < 4; ++s) {
-        if (!((ps >> s) & 1)) continue;
-        const unsigned nb = nba((long)nside[s] * c->ngrp, 256);
-        double *pa = w.pacc + (long)s * nmax * 2 * c->nv;
-        if (c->scheme == DVM_MUSCL)
-            k_adj_pads_fast<T, true><<<nb, 256, 0, c->stream>>>(a, lam_in, bits, bits_slab(c), bits_pitch(c), s,
-                                                                nside[s], w.fast, pa, lam_out);
-        else
-            k_adj_pads_fast<T, false><<<nb, 256, 0, c->stream>>>(a, lam_in, nullptr, 0, 0, s, nside[s], w.fast, pa,
-                                                                 lam_out);
-        ++launched;
+    for (int ax = 0; ax < 2; ++ax) {
+        // both sides of the axis in one launch when they touch distinct cells
+        const int n = ax == 0 ? c->nx : c->ny;
+        for (int s = 2 * ax; s < 2 * ax + 2; s += n > 1 ? 2 : 1) {
+            const int sides = n > 1 ? 2 : 1;
+            if (!((ps >> s) & (sides == 2 ? 3 : 1))) continue;
+            const unsigned nb = nba((long)nside[s] * c->ngrp * sides, 256);
+            if (c->scheme == DVM_MUSCL)
+                k_adj_pads_fast<T, true><<<nb, 256, 0, c->stream>>>(a, lam_in, bits, bits_slab(c), bits_pitch(c), s,
+                                                                    sides, nside[s], ps, w.fast, w.pacc, nmax,
+                                                                    lam_out);
+            else
+                k_adj_pads_fast<T, false><<<nb, 256, 0, c->stream>>>(a, lam_in, nullptr, 0, 0, s, sides, nside[s], ps,
+                                                                     w.fast, w.pacc, nmax, lam_out);
+            ++launched;
+        }
     }
     for (int s = 0; s < 4; ++s) {
         if (c->bc[s] == DVM_BC_MAXWELLIAN && !c->d_bcstate[s]) continue;
@@ -1180,7 +1321,7 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
             a, f, lam_in, mucv, s, nside[s], w.fast, ps, w.pacc + (long)s * nmax * 2 * c->nv, lam_out);
         ++launched;
     }
-    k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lam_out);
+    if (w.ncv > 0) k_adj_fuseT<T><<<cvg, 256, 0, c->stream>>>(a, lam_out);
     c->launches += launched;
     return cudaGetLastError();
 }
@@ -1219,6 +1360,7 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMalloc(&w.scratch_part, partb));
         AC(cudaMalloc(&w.fast, c->nc));
         AC(cudaMalloc(&w.slow, sizeof(int32_t) * c->nc));
+        AC(cudaMalloc(&w.frec, sizeof(FaceRec<T>) * 8 * c->nc));
         AC(cudaMalloc(&w.nslow_d, 5 * sizeof(int)));
         w.Z = c->ngrp < 8 ? c->ngrp : 8;
         w.Zf = c->ngrp < 4 ? c->ngrp : 4;
@@ -1233,6 +1375,10 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMalloc(&q, partb));
         w.ckpt.push_back(p);
         w.ckpt_part.push_back(q);
+        CUtensorMap m;
+        const int rc = encode_tensor_map2d(c, p, &m);
+        if (rc != DVM_OK) return rc;
+        w.cmaps.push_back(m);
     }
     while ((int)w.tape.size() < K) {
         void *p = nullptr, *q = nullptr;
@@ -1285,16 +1431,22 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMemcpyAsync(w.padneed, w.nslow_d + 1, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         AC(cudaStreamSynchronize(c->stream));
         w.nw = cnt0[1] < c->list_cap ? cnt0[1] : c->list_cap;
+        w.ncv = cnt0[0] < c->list_cap ? cnt0[0] : c->list_cap;
         if (w.nw > w.nw_cap) {
-            cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wd);
-            w.wadj = nullptr; w.wm = nullptr; w.wd = nullptr; w.nw_cap = 0;
+            cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wt); cudaFree(w.wd);
+            w.wadj = nullptr; w.wm = nullptr; w.wt = nullptr; w.wd = nullptr; w.nw_cap = 0;
             AC(cudaMalloc(&w.wadj, sizeof(WallAdj) * w.nw));
             AC(cudaMalloc(&w.wm, sizeof(WallVel) * w.nw * c->nv));
+            AC(cudaMalloc(&w.wt, sizeof(WallVelT<double>) * w.nw * c->nv));
             AC(cudaMalloc(&w.wd, sizeof(double2) * w.nw));
             w.nw_cap = w.nw;
         }
+        if (w.nslow > 0)
+            k_adj_listrec<T><<<nba((long)w.nslow * 8, 256), 256, 0, c->stream>>>(adj_args(c, w), w.slow, w.nslow,
+                                                                              (FaceRec<T> *)w.frec);
         if (w.nw > 0)
-            k_adj_wall_pre<T><<<w.nw, 256, 0, c->stream>>>(adj_args(c, w), w.nw, w.wadj, w.wm, w.wd, w.wsec);
+            k_adj_wall_pre<T><<<w.nw, 256, 0, c->stream>>>(adj_args(c, w), w.nw, w.wadj, w.wm, (WallVelT<T> *)w.wt,
+                                                            w.wd, w.wsec);
         AC(cudaMemsetAsync(w.pacc, 0, sizeof(double) * 4 * nmax * 2 * c->nv, c->stream));
     }
     cudaEvent_t ev[3];
@@ -1328,46 +1480,48 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     AC(cudaMemsetAsync(w.lam[0], 0, bytes, c->stream));
     AC(cudaMemsetAsync(w.lam[1], 0, bytes, c->stream));
     if (w.nw > 0)
-        k_adj_wall<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, (const T *)c->f[c->cur], lamA,
-                                                    (const T *)w.mucv, lamA, w.gtw, w.jwall, 1);
-    k_adj_fuseT<T><<<cvgrid, 256, 0, c->stream>>>(a, lamA);
+        k_adj_wall_obj<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, (const T *)c->f[c->cur], lamA,
+                                                        w.gtw, w.jwall);
+    if (w.ncv > 0)
+        k_adj_fuseT<T><<<dim3((unsigned)w.ncv, nba(2L * c->nvp, 256)), 256, 0, c->stream>>>(a, lamA);
     // reverse sweep, segment by segment: recompute the segment onto the tape
     // (each step writes the next tape buffer), then apply the transposed steps
     // backwards
-    void *f_orig[2] = {c->f[0], c->f[1]};
+    void *f_orig[2] = {c->f[0], c->f[1]}, *p_orig[2] = {c->part[0], c->part[1]};
     const CUtensorMap tm_orig[2] = {c->tmap[0], c->tmap[1]};
     const int cur_orig = c->cur;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps, len = n1 - n0;
-        AC(cudaMemcpyAsync(w.tape[0], w.ckpt[sgi], bytes, cudaMemcpyDeviceToDevice, c->stream));
-        AC(cudaMemcpyAsync(c->part[c->cur], w.ckpt_part[sgi], partb, cudaMemcpyDeviceToDevice, c->stream));
+        // tape slot 0 is the checkpoint itself; step t writes slot t + 1 (state
+        // and partial moments) directly
+        const auto fslot = [&](int t) { return t == 0 ? w.ckpt[sgi] : w.tape[t]; };
+        const auto pslot = [&](int t) { return t == 0 ? w.ckpt_part[sgi] : w.ptape[t]; };
+        const auto mslot = [&](int t) { return t == 0 ? w.cmaps[sgi] : w.tmaps[t]; };
         // the step linearises around the fused state (members of merged control
         // volumes are equal after every step, not necessarily in the initial state)
-        if (sgi == 0 && fuse0) AC(fusion2d(c, w.tape[0], c->part[c->cur]));
+        if (sgi == 0 && fuse0) AC(fusion2d(c, fslot(0), pslot(0)));
         c->need_fusion = false;
-        for (int t = 0; t < len; ++t) {
-            if (t + 1 < len) {
-                c->f[c->cur] = w.tape[t];
-                c->f[1 - c->cur] = w.tape[t + 1];
-                c->tmap[c->cur] = w.tmaps[t];
-                c->tmap[1 - c->cur] = w.tmaps[t + 1];
-                if (rec) c->rec_bits = w.tbits[t];
-                const cudaError_t es = step2d(c);
-                c->rec_bits = nullptr;
-                AC(es);
-                AC(cudaMemcpyAsync(w.ptape[t], c->part[1 - c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
-            } else {
-                AC(cudaMemcpyAsync(w.ptape[t], c->part[c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
-            }
+        for (int t = 0; t + 1 < len; ++t) {
+            c->f[c->cur] = fslot(t);
+            c->f[1 - c->cur] = fslot(t + 1);
+            c->part[c->cur] = pslot(t);
+            c->part[1 - c->cur] = pslot(t + 1);
+            c->tmap[c->cur] = mslot(t);
+            c->tmap[1 - c->cur] = mslot(t + 1);
+            if (rec) c->rec_bits = w.tbits[t];
+            const cudaError_t es = step2d(c);
+            c->rec_bits = nullptr;
+            c->cur = 1 - c->cur;            // keep the same slot parity: step2d advanced it
+            AC(es);
         }
         c->f[0] = f_orig[0]; c->f[1] = f_orig[1];
+        c->part[0] = p_orig[0]; c->part[1] = p_orig[1];
         c->tmap[0] = tm_orig[0]; c->tmap[1] = tm_orig[1];
         c->cur = cur_orig;
         for (int t = len - 1; t >= 0; --t) {
             const CUtensorMap *bm = !rec ? nullptr : (t == len - 1 ? &w.sbmap[sgi] : &w.tbmap[t]);
             const uint32_t *bits = !rec ? nullptr : (t == len - 1 ? w.sbits[sgi] : w.tbits[t]);
-            AC(adjoint_step<T>(c, w, (const T *)w.tape[t], (const T *)w.ptape[t], bits, bm, lin,
-                               (T *)w.lam[1 - lin]));
+            AC(adjoint_step<T>(c, w, (const T *)fslot(t), (const T *)pslot(t), bits, bm, lin, (T *)w.lam[1 - lin]));
             lin = 1 - lin;
         }
     }
