@@ -1135,7 +1135,10 @@ __global__ void __launch_bounds__(256) k_adj_ghost_chain(Grid2D g, int nside, co
 }
 
 // dJ/d(rho, ux, uy, uz, T) of a Maxwellian initial state from lambda^0 (one
-// thread per cell, 32 consecutive cells along x per warp, FP64 sums).
+// thread per cell, 32 consecutive cells along x per warp).  With u = lambda_f
+// + T/2 lambda_g: dJ/drho = sum u M / rho, dJ/du = sum u M (v - u) / T, dJ/dT =
+// sum u M (|v - u|^2 / (2T) - 1) / T + sum lambda_g M / 2; the Maxwellian and
+// the compensated sums in the state precision, the final factors in FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_init(Grid2D g, const T *lam, const double *prim, const int8_t *type,
                                                   double *gout)
@@ -1148,26 +1151,31 @@ __global__ void __launch_bounds__(256) k_adj_init(Grid2D g, const T *lam, const 
     if (type[k] != DVM_SOLID && st[0] > 0) {
         constexpr int W = Vec<T>::W;
         const long pk = nbr(g, i, j) * W;
+        const T ux = (T)st[1], uy = (T)st[2], tmp = (T)st[4];
+        const T A = (T)(st[0] / (2.0 * kPi * st[4])), i2T = (T)(0.5 / st[4]), c2 = (T)(kLog2e * 0.5 / st[4]);
+        const T h = tmp / T(2);
+        Acc<T> a0, a1, a2, a3, a4;
         for (int p0 = 0; p0 < g.nvp; p0 += W) {
             T l0[W], l1[W];
             vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 0, p0) + pk), l0);
             vld<T>(reinterpret_cast<const typename Vec<T>::type *>(lam + ebase<T>(g, 1, p0) + pk), l1);
+            T t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0;
 #pragma unroll
             for (int e = 0; e < W; ++e) {
                 const int p = p0 + e;
                 if (p >= g.nv) break;
-                const double vx = g.vxmin + (p % g.nvx) * g.dvx, vy = g.vymin + (p / g.nvx) * g.dvy;
-                const double ax = vx - st[1], ay = vy - st[2], a2 = ax * ax + ay * ay;
-                const double M = st[0] / (2.0 * kPi * st[4]) * exp(-a2 / (2.0 * st[4]));
-                const double d0 = M / st[0], d1 = M * ax / st[4], d2 = M * ay / st[4];
-                const double d3 = M * (a2 / (2.0 * st[4] * st[4]) - 1.0 / st[4]);
-                const double h = st[4] / 2.0;
-                o0 += (double)l0[e] * d0 + (double)l1[e] * h * d0;
-                o1 += (double)l0[e] * d1 + (double)l1[e] * h * d1;
-                o2 += (double)l0[e] * d2 + (double)l1[e] * h * d2;
-                o3 += (double)l0[e] * d3 + (double)l1[e] * (M / 2.0 + h * d3);
+                const T ax = (T)(g.vxmin + (p % g.nvx) * g.dvx) - ux, ay = (T)(g.vymin + (p / g.nvx) * g.dvy) - uy;
+                const T q2 = ax * ax + ay * ay;
+                const T M = A * dexp2(-q2 * c2);
+                const T mu = M * (l0[e] + h * l1[e]);
+                t0 += mu; t1 += mu * ax; t2 += mu * ay; t3 += mu * (q2 * i2T - T(1)); t4 += l1[e] * M;
             }
+            a0.add(t0); a1.add(t1); a2.add(t2); a3.add(t3); a4.add(t4);
         }
+        o0 = (double)a0.value() / st[0];
+        o1 = (double)a1.value() / st[4];
+        o2 = (double)a2.value() / st[4];
+        o3 = (double)a3.value() / st[4] + 0.5 * (double)a4.value();
     }
     double *o = gout + 5 * k;
     o[0] = o0; o[1] = o1; o[2] = o2; o[3] = 0; o[4] = o3;
@@ -1472,7 +1480,6 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     dvm::BodyDev body_end;
     AC(cudaMemcpyAsync(&body_end, c->d_body, sizeof(body_end), cudaMemcpyDeviceToHost, c->stream));
     const AdjArgs a = adj_args(c, w);
-    const int cvgrid = 4 * 152;
     // objective on F^N: lambda^N = fusion^T dJ/dF
     int lin = 0;                                      // lambda^{n+1} is lam[lin]
     T *lamA = (T *)w.lam[0];
