@@ -180,6 +180,85 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
     }
 }
 
+// Packed FP32 form of bulk_tile for a sign-uniform group with the limited
+// reconstruction: the differences, the flux combination, the update and the
+// moment sums on pairs of velocities with the f32x2 instructions (the minmod
+// min/max stay scalar).  Same formulas as bulk_tile; the moment sums go to
+// per-lane accumulators Q (q0, q1, q2, q3 of bulk_tile).  P: per-element
+// coefficient pairs -nux, -nuy, 1 - nux, 1 - nuy, vx, vy, |v|^2/2.
+struct PairCoef { F2 nnx[2], nny[2], onx[2], ony[2], vx[2], vy[2], ke[2]; };
+
+template <int COMP, bool REC>
+__device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, int uy1, const PairCoef &P,
+                                             const F2 (&feq)[2], float wxm, float wxp, float wym, float wyp, F2 r,
+                                             float (&out)[4], F2 (&Q)[4], uint32_t &bw, uint32_t &bi)
+{
+    float f[4], u1[4], w1[4], d1[4], u2[4], e1[4], w2[4];
+    sld<float>(t + c0, f);
+    sld<float>(t + c0 - ux1, u1);
+    sld<float>(t + c0 - uy1, w1);
+    sld<float>(t + c0 + ux1, d1);
+    sld<float>(t + c0 - 2 * ux1, u2);
+    sld<float>(t + c0 + uy1, e1);
+    sld<float>(t + c0 - 2 * uy1, w2);
+    const bool px = ux1 > 0, py = uy1 > 0;
+    const float cxo = px ? wxp : wxm, cxi = px ? wxm : wxp;
+    const float cyo = py ? wyp : wym, cyi = py ? wym : wyp;
+    const F2 CXO = f2(cxo), NCXI = f2(-cxi), CYO = f2(cyo), NCYI = f2(-cyi);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int a0 = 2 * h, a1 = 2 * h + 1;
+        const F2 F = f2(f[a0], f[a1]), U1 = f2(u1[a0], u1[a1]), W1 = f2(w1[a0], w1[a1]);
+        const F2 AX = sub2(F, U1), AY = sub2(F, W1);
+        const F2 BX = sub2(f2(d1[a0], d1[a1]), F), BY = sub2(f2(e1[a0], e1[a1]), F);
+        const F2 CX = sub2(U1, f2(u2[a0], u2[a1])), CY = sub2(W1, f2(w2[a0], w2[a1]));
+        float ax[2], ay[2], bx[2], by[2], cx[2], cy[2], mxo[2], mxi[2], myo[2], myi[2];
+        f2_get(AX, ax[0], ax[1]); f2_get(AY, ay[0], ay[1]);
+        f2_get(BX, bx[0], bx[1]); f2_get(BY, by[0], by[1]);
+        f2_get(CX, cx[0], cx[1]); f2_get(CY, cy[0], cy[1]);
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            mxo[l] = minmod3(bx[l], ax[l]); mxi[l] = minmod3(ax[l], cx[l]);
+            myo[l] = minmod3(by[l], ay[l]); myi[l] = minmod3(ay[l], cy[l]);
+            if (REC) {
+                const int e = 2 * h + l;
+                bw |= branch_bits(mxo[l], bx[l], ax[l], cxo) << (((COMP * 2 + 0) * 4 + e) * 2);
+                bw |= branch_bits(myo[l], by[l], ay[l], cyo) << (((COMP * 2 + 1) * 4 + e) * 2);
+                bi |= branch_bits(mxi[l], ax[l], cx[l], cxi) << (((COMP * 2 + 0) * 4 + e) * 2);
+                bi |= branch_bits(myi[l], ay[l], cy[l], cyi) << (((COMP * 2 + 1) * 4 + e) * 2);
+            }
+        }
+        const F2 TX = fma2(NCXI, f2(mxi[0], mxi[1]), mul2(CXO, f2(mxo[0], mxo[1])));
+        const F2 TY = fma2(NCYI, f2(myi[0], myi[1]), mul2(CYO, f2(myo[0], myo[1])));
+        const F2 DFX = fma2(P.onx[h], TX, AX), DFY = fma2(P.ony[h], TY, AY);
+        F2 O = fma2(P.nnx[h], DFX, F);
+        O = fma2(P.nny[h], DFY, O);
+        O = fma2(r, sub2(feq[h], F), O);
+        f2_get(O, out[a0], out[a1]);
+        if (COMP == 0) {
+            Q[0] = add2(Q[0], O);
+            Q[1] = fma2(P.vx[h], O, Q[1]);
+            Q[2] = fma2(P.vy[h], O, Q[2]);
+            Q[3] = fma2(P.ke[h], O, Q[3]);
+        } else {
+            Q[3] = add2(Q[3], O);
+        }
+    }
+}
+
+// Adds the two lanes of each packed moment sum to q0..q3 and clears them.
+template <typename T>
+__device__ __forceinline__ void fold_pairs(F2 (&Q)[4], T &q0, T &q1, T &q2, T &q3)
+{
+    float a, b;
+    f2_get(Q[0], a, b); q0 += a + b;
+    f2_get(Q[1], a, b); q1 += a + b;
+    f2_get(Q[2], a, b); q2 += a + b;
+    f2_get(Q[3], a, b); q3 += a + b;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Q[m] = f2(0.f);
+}
+
 // Store of one (group, component) vector of a cell and of its padding
 // mirrors (cells within two cells of a periodic or zero-gradient side).
 template <typename T>
@@ -272,6 +351,9 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
 
     Acc<T> m0, m1, m2, m3;
     T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+    F2 Qp[4];                 // per-lane sums of the packed FP32 path
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Qp[m] = f2(0.f);
     int fold = 0;
     for (int it = 0; it < ngr; ++it) {
         const int q = g0 + it, st = it % kStages;
@@ -296,6 +378,33 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                 feq[e] = A * dexp2(-(dx * dx + dy * dy) * c2);
             }
             uint32_t bw = 0, bi = 0;
+            if constexpr (sizeof(T) == 4 && MUSCL) {
+                if (sx != 0 && sy != 0) {
+                    // packed FP32 path of the sign-uniform groups
+                    const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
+                    PairCoef P;
+                    F2 fq[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int a0 = 2 * h, a1 = 2 * h + 1;
+                        P.nnx[h] = f2(-nux[a0], -nux[a1]); P.nny[h] = f2(-nuy[a0], -nuy[a1]);
+                        P.onx[h] = f2(T(1) - nux[a0], T(1) - nux[a1]); P.ony[h] = f2(T(1) - nuy[a0], T(1) - nuy[a1]);
+                        P.vx[h] = f2(vx[a0], vx[a1]); P.vy[h] = f2(vy[a0], vy[a1]);
+                        P.ke[h] = f2(T(0.5) * (vx[a0] * vx[a0] + vy[a0] * vy[a0]),
+                                     T(0.5) * (vx[a1] * vx[a1] + vy[a1] * vy[a1]));
+                        fq[h] = f2(feq[a0], feq[a1]);
+                    }
+                    const F2 r2 = f2(r);
+                    bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw, bi);
+                    store_cell<T>(o0, pc, mir, anymir, out);
+                    const F2 gf = f2(gfac);
+                    fq[0] = mul2(fq[0], gf); fq[1] = mul2(fq[1], gf);
+                    bulk_tile_x2<1, REC>(tile + kTileY * kTileX, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out,
+                                         Qp, bw, bi);
+                    store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
+                    goto stored;
+                }
+            }
             if (sx != 0 && sy != 0) {
                 const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
                 bulk_tile<T, MUSCL, 0, true, REC>(tile, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
@@ -316,6 +425,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                                                    wxm, wxp, wym, wyp, r, out, q0, q1, q2, q3, bw, bi);
                 store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
             }
+        stored:
             if (REC) {
                 uint32_t *bq = a.bits + (long)q * a.bslab;
                 const auto bix = [&](int ii, int jj) { return (long)(jj + 2) * a.bpitch + ii + 2; };
@@ -339,6 +449,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
             }
             // fold the plain sums of 8 groups into the compensated sums
             if (++fold == 8) {
+                if constexpr (sizeof(T) == 4 && MUSCL) fold_pairs(Qp, q0, q1, q2, q3);
                 m0.add(q0); m1.add(q1); m2.add(q2); m3.add(q3);
                 q0 = q1 = q2 = q3 = 0;
                 fold = 0;
@@ -359,6 +470,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
         for (int k = max(ngr - kStages, 0); k < ngr; ++k) mbar_wait(&full[k % kStages], (uint32_t)((k / kStages) & 1));
     }
     if (plain) {
+        if constexpr (sizeof(T) == 4 && MUSCL) fold_pairs(Qp, q0, q1, q2, q3);
         m0.add(q0); m1.add(q1); m2.add(q2); m3.add(q3);
         a.pout[((long)split * 4 + 0) * nc + cell] = m0.value();
         a.pout[((long)split * 4 + 1) * nc + cell] = m1.value();
