@@ -188,10 +188,14 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
 // coefficient pairs -nux, -nuy, 1 - nux, 1 - nuy, vx, vy, |v|^2/2.
 struct PairCoef { F2 nnx[2], nny[2], onx[2], ony[2], vx[2], vy[2], ke[2]; };
 
+// Branch code of a minmod value m that is one of its arguments or 0 (b: the
+// second argument): 0 for zero, 2 for b (also on a tie), else 1.
+__device__ __forceinline__ uint32_t bcode(float m, float b) { return m == 0.f ? 0u : (m == b ? 2u : 1u); }
+
 template <int COMP, bool REC>
 __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, int uy1, const PairCoef &P,
                                              const F2 (&feq)[2], float wxm, float wxp, float wym, float wyp, F2 r,
-                                             float (&out)[4], F2 (&Q)[4], uint32_t &bw, uint32_t &bi)
+                                             float (&out)[4], F2 (&Q)[4], uint32_t &bw, uint32_t &bi, bool edge)
 {
     float f[4], u1[4], w1[4], d1[4], u2[4], e1[4], w2[4];
     sld<float>(t + c0, f);
@@ -205,6 +209,7 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
     const float cxo = px ? wxp : wxm, cxi = px ? wxm : wxp;
     const float cyo = py ? wyp : wym, cyi = py ? wym : wyp;
     const F2 CXO = f2(cxo), NCXI = f2(-cxi), CYO = f2(cyo), NCYI = f2(-cyi);
+    uint32_t lo = 0, li = 0;          // branch codes before the face-weight masks
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int a0 = 2 * h, a1 = 2 * h + 1;
@@ -222,10 +227,13 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
             myo[l] = minmod3(by[l], ay[l]); myi[l] = minmod3(ay[l], cy[l]);
             if (REC) {
                 const int e = 2 * h + l;
-                bw |= branch_bits(mxo[l], bx[l], ax[l], cxo) << (((COMP * 2 + 0) * 4 + e) * 2);
-                bw |= branch_bits(myo[l], by[l], ay[l], cyo) << (((COMP * 2 + 1) * 4 + e) * 2);
-                bi |= branch_bits(mxi[l], ax[l], cx[l], cxi) << (((COMP * 2 + 0) * 4 + e) * 2);
-                bi |= branch_bits(myi[l], ay[l], cy[l], cyi) << (((COMP * 2 + 1) * 4 + e) * 2);
+                lo |= bcode(mxo[l], ax[l]) << (((COMP * 2 + 0) * 4 + e) * 2);
+                lo |= bcode(myo[l], ay[l]) << (((COMP * 2 + 1) * 4 + e) * 2);
+                // incoming faces: only a cell on a side stores them
+                if (edge) {
+                    li |= bcode(mxi[l], cx[l]) << (((COMP * 2 + 0) * 4 + e) * 2);
+                    li |= bcode(myi[l], cy[l]) << (((COMP * 2 + 1) * 4 + e) * 2);
+                }
             }
         }
         const F2 TX = fma2(NCXI, f2(mxi[0], mxi[1]), mul2(CXO, f2(mxo[0], mxo[1])));
@@ -243,6 +251,13 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
         } else {
             Q[3] = add2(Q[3], O);
         }
+    }
+    if (REC) {
+        // first-order faces record no branch: x fields 0x00FF00FF, y fields 0xFF00FF00
+        const uint32_t mo = (cxo != 0.f ? 0x00FF00FFu : 0u) | (cyo != 0.f ? 0xFF00FF00u : 0u);
+        const uint32_t mi = (cxi != 0.f ? 0x00FF00FFu : 0u) | (cyi != 0.f ? 0xFF00FF00u : 0u);
+        bw |= lo & mo;
+        bi |= li & mi;
     }
 }
 
@@ -311,6 +326,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     const int ngr = max(g1 - g0, 0);
     const uint8_t fl = inside ? a.flags[cell] : 0;
     const bool plain = (fl & kPlain) != 0, zero = (fl & kZero) != 0;
+    const bool edge = i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1;   // a cell on a side
     V *fout = reinterpret_cast<V *>(a.fout);
 
     if (tid == 0) {
@@ -395,12 +411,12 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                         fq[h] = f2(feq[a0], feq[a1]);
                     }
                     const F2 r2 = f2(r);
-                    bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw, bi);
+                    bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw, bi, edge);
                     store_cell<T>(o0, pc, mir, anymir, out);
                     const F2 gf = f2(gfac);
                     fq[0] = mul2(fq[0], gf); fq[1] = mul2(fq[1], gf);
                     bulk_tile_x2<1, REC>(tile + kTileY * kTileX, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out,
-                                         Qp, bw, bi);
+                                         Qp, bw, bi, edge);
                     store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
                     goto stored;
                 }
@@ -430,7 +446,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                 uint32_t *bq = a.bits + (long)q * a.bslab;
                 const auto bix = [&](int ii, int jj) { return (long)(jj + 2) * a.bpitch + ii + 2; };
                 bq[bix(i, j)] = bw;
-                if (i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1) {
+                if (edge) {
                     // fields of the velocities that enter through each side
                     uint32_t xin = 0, xout = 0, yin = 0, yout = 0;
 #pragma unroll
