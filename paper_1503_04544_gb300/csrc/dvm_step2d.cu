@@ -192,6 +192,34 @@ struct PairCoef { F2 nnx[2], nny[2], onx[2], ony[2], vx[2], vy[2], ke[2]; };
 // second argument): 0 for zero, 2 for b (also on a tie), else 1.
 __device__ __forceinline__ uint32_t bcode(float m, float b) { return m == 0.f ? 0u : (m == b ? 2u : 1u); }
 
+// Three-input minimum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// The two limiter values of one axis that share the difference a: the
+// downwind face minmod(b, a) and the upwind face minmod(a, c), with
+// minmod(x, y) = median(x, y, 0) = min(max(x, y), max(x, 0), max(y, 0))
+// (exact: the median is one of its arguments); max(a, 0) serves both.
+__device__ __forceinline__ void minmod_pair(float b, float a, float c, float &mo, float &mi)
+{
+    const float za = fmaxf(a, 0.f);
+    mo = fmin3(fmaxf(b, a), fmaxf(b, 0.f), za);
+    mi = fmin3(fmaxf(a, c), za, fmaxf(c, 0.f));
+}
+
+// 2^x by the hardware approximation (relative error a few ulp; results below
+// the smallest normal number flush to 0).
+__device__ __forceinline__ float ex2_fast(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int COMP, bool REC>
 __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, int uy1, const PairCoef &P,
                                              const F2 (&feq)[2], float wxm, float wxp, float wym, float wyp, F2 r,
@@ -223,8 +251,8 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
         f2_get(CX, cx[0], cx[1]); f2_get(CY, cy[0], cy[1]);
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-            mxo[l] = minmod3(bx[l], ax[l]); mxi[l] = minmod3(ax[l], cx[l]);
-            myo[l] = minmod3(by[l], ay[l]); myi[l] = minmod3(ay[l], cy[l]);
+            minmod_pair(bx[l], ax[l], cx[l], mxo[l], mxi[l]);
+            minmod_pair(by[l], ay[l], cy[l], myo[l], myi[l]);
             if (REC) {
                 const int e = 2 * h + l;
                 lo |= bcode(mxo[l], ax[l]) << (((COMP * 2 + 0) * 4 + e) * 2);
@@ -342,7 +370,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     }
 
     // equilibrium of the cell at t^n
-    T A = 0, c2 = 0, r = 0, gfac = 0, ux = 0, uy = 0;
+    T A = 0, c2 = 0, r = 0, gfac = 0, ux = 0, uy = 0, el0 = 0, e1x = 0, e1y = 0;
     if (plain) {
         T s[4];
         gather_partials(a.pin, a.S, nc, cell, s);
@@ -353,6 +381,12 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
         c2 = T(kLog2e) / (T(2) * tmp);
         r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
         gfac = tmp / T(2);
+        // log2 M(v) = el0 + vx (e1x - c2 vx) + vy (e1y - c2 vy) (packed path)
+        if (!REC) {
+            el0 = log2(A) - c2 * (ux * ux + uy * uy);
+            e1x = T(2) * c2 * ux;
+            e1y = T(2) * c2 * uy;
+        }
     }
     const int mask = fl >> kMaskShift;
     // limiter weights of the faces x-, x+, y-, y+ (1/2 where the limited
@@ -390,8 +424,6 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
             for (int e = 0; e < W; ++e) {
                 const VCoef<T> vc = ld_coef(a.vt + q * W + e);
                 vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
-                const T dx = vc.vx - ux, dy = vc.vy - uy;
-                feq[e] = A * dexp2(-(dx * dx + dy * dy) * c2);
             }
             uint32_t bw = 0, bi = 0;
             if constexpr (sizeof(T) == 4 && MUSCL) {
@@ -408,7 +440,19 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                         P.vx[h] = f2(vx[a0], vx[a1]); P.vy[h] = f2(vy[a0], vy[a1]);
                         P.ke[h] = f2(T(0.5) * (vx[a0] * vx[a0] + vy[a0] * vy[a0]),
                                      T(0.5) * (vx[a1] * vx[a1] + vy[a1] * vy[a1]));
-                        fq[h] = f2(feq[a0], feq[a1]);
+                        float fe[2];
+#pragma unroll
+                        for (int l = 0; l < 2; ++l) {
+                            const int e = 2 * h + l;
+                            if (REC) {      // the recording variant keeps fewer per-cell registers
+                                const T dx = vx[e] - ux, dy = vy[e] - uy;
+                                fe[l] = A * dexp2(-(dx * dx + dy * dy) * c2);
+                            } else {
+                                fe[l] = ex2_fast(fmaf(fmaf(-c2, vx[e], e1x), vx[e],
+                                                      fmaf(fmaf(-c2, vy[e], e1y), vy[e], el0)));
+                            }
+                        }
+                        fq[h] = f2(fe[0], fe[1]);
                     }
                     const F2 r2 = f2(r);
                     bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw, bi, edge);
@@ -420,6 +464,11 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                     store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
                     goto stored;
                 }
+            }
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const T dx = vx[e] - ux, dy = vy[e] - uy;
+                feq[e] = A * dexp2(-(dx * dx + dy * dy) * c2);
             }
             if (sx != 0 && sy != 0) {
                 const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
