@@ -138,6 +138,39 @@ __device__ __forceinline__ T minmod3(T a, T b)
     return fmax(fmin(a, b), fmin(fmax(a, b), T(0)));
 }
 
+// Three-input minimum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// The two limiter values of one axis that share the difference a: the
+// downwind face minmod(b, a) and the upwind face minmod(a, c), with
+// minmod(x, y) = median(x, y, 0) = min(max(x, y), max(x, 0), max(y, 0))
+// (exact: the median is one of its arguments); max(a, 0) serves both.
+__device__ __forceinline__ void minmod_pair(float b, float a, float c, float &mo, float &mi)
+{
+    const float za = fmaxf(a, 0.f);
+    mo = fmin3(fmaxf(b, a), fmaxf(b, 0.f), za);
+    mi = fmin3(fmaxf(a, c), za, fmaxf(c, 0.f));
+}
+__device__ __forceinline__ void minmod_pair(double b, double a, double c, double &mo, double &mi)
+{
+    mo = minmod3(b, a);
+    mi = minmod3(a, c);
+}
+
+// 2^x by the hardware approximation (relative error a few ulp; results below
+// the smallest normal number flush to 0).
+__device__ __forceinline__ float ex2_fast(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <typename T>
 __device__ __forceinline__ void sld(const typename Vec<T>::type *p, T (&r)[Vec<T>::W])
 {

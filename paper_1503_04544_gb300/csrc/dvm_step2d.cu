@@ -192,34 +192,6 @@ struct PairCoef { F2 nnx[2], nny[2], onx[2], ony[2], vx[2], vy[2], ke[2]; };
 // second argument): 0 for zero, 2 for b (also on a tie), else 1.
 __device__ __forceinline__ uint32_t bcode(float m, float b) { return m == 0.f ? 0u : (m == b ? 2u : 1u); }
 
-// Three-input minimum (one instruction on sm_100 and later).
-__device__ __forceinline__ float fmin3(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
-// The two limiter values of one axis that share the difference a: the
-// downwind face minmod(b, a) and the upwind face minmod(a, c), with
-// minmod(x, y) = median(x, y, 0) = min(max(x, y), max(x, 0), max(y, 0))
-// (exact: the median is one of its arguments); max(a, 0) serves both.
-__device__ __forceinline__ void minmod_pair(float b, float a, float c, float &mo, float &mi)
-{
-    const float za = fmaxf(a, 0.f);
-    mo = fmin3(fmaxf(b, a), fmaxf(b, 0.f), za);
-    mi = fmin3(fmaxf(a, c), za, fmaxf(c, 0.f));
-}
-
-// 2^x by the hardware approximation (relative error a few ulp; results below
-// the smallest normal number flush to 0).
-__device__ __forceinline__ float ex2_fast(float x)
-{
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 template <int COMP, bool REC>
 __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, int uy1, const PairCoef &P,
                                              const F2 (&feq)[2], float wxm, float wxp, float wym, float wyp, F2 r,

@@ -163,11 +163,15 @@ constexpr int kPlaneX = 32 + 4;                   // tile width plus a two-cell 
 template <typename T> __host__ __device__ constexpr int rows3() { return sizeof(T) == 4 ? 12 : 8; }
 template <typename T> __host__ __device__ constexpr int plane_cells3() { return kPlaneX * (rows3<T>() + 4); }
 
+// Velocity tables staged in shared memory by the bulk kernel: all of v_x and
+// up to kVyzStage (v_y, v_z) pairs (more are read from global memory).
+constexpr int kVyzStage = 512;
+
 template <typename T>
 size_t bulk3_smem()
 {
     return (size_t)kRing3 * plane_cells3<T>() * 16 + (size_t)kZc3 * (kCoef3 + 10) * 32 * rows3<T>() * sizeof(T) +
-           2 * kRing3 * sizeof(uint64_t);
+           2 * kRing3 * sizeof(uint64_t) + (size_t)kMaxAxisNv * sizeof(VX3<T>) + (size_t)kVyzStage * sizeof(VYZ3<T>);
 }
 
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z, int w)
@@ -188,8 +192,14 @@ __device__ __forceinline__ T dflux(T f, T u1, T u2, T d1, T ko, T ki)
 {
     const T a = f - u1;
     if (!MUSCL) return a;
-    return fma(-ki, minmod3(a, u1 - u2), fma(ko, minmod3(d1 - f, a), a));
+    T mo, mi;
+    minmod_pair(d1 - f, a, u1 - u2, mo, mi);
+    return fma(-ki, mi, fma(ko, mo, a));
 }
+
+// 2^x in the state precision: the hardware approximation in FP32.
+__device__ __forceinline__ float exp2_state(float x) { return ex2_fast(x); }
+__device__ __forceinline__ double exp2_state(double x) { return exp2(x); }
 
 // Bulk update of every gas cell that is a control volume on its own.
 //
@@ -220,6 +230,8 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
     T *ksum = coef + ZC * kCoef3 * NT;                               // [ZC][5][2][NT]
     uint64_t *full = reinterpret_cast<uint64_t *>(ksum + ZC * 10 * NT);
     uint64_t *empty = full + kRing3;
+    VX3<T> *svx = reinterpret_cast<VX3<T> *>(empty + kRing3);          // [kMaxAxisNv]
+    VYZ3<T> *svyz = reinterpret_cast<VYZ3<T> *>(svx + kMaxAxisNv);       // [kVyzStage]
     const Grid3D &g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const bool producer = ty == R;
@@ -242,6 +254,14 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
         }
         mbar_fence_init();
     }
+    // the velocity tables of the groups, staged once per block
+    const int nyz = g.nvy * g.nvz;
+    const bool stage_yz = nyz <= kVyzStage;
+    for (int q = tid; q < g.nvxp; q += blockDim.x * blockDim.y) svx[q] = a.vxt[q];
+    if (stage_yz)
+        for (int q = tid; q < nyz; q += blockDim.x * blockDim.y) svyz[q] = a.vyz[q];
+    const VX3<T> *vxtab = svx;
+    const VYZ3<T> *vyztab = stage_yz ? svyz : a.vyz;
     // per-cell data of the column: flags, and for plain cells the
     // equilibrium in the form log2 M(v) = c0 + vx (c1 - c2 vx) - c2 dyz(v)
     uint32_t plainm = 0, zerom = 0, mirm = 0, masks = 0;   // masks: byte t = limiter mask of cell t
@@ -317,12 +337,12 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
     for (int gi = 0; gi < ngr; ++gi) {
         const int grp = g0 + gi;
         const int yz = grp / g.nxg, xg = grp - yz * g.nxg;
-        const VYZ3<T> cyz = a.vyz[yz];
+        const VYZ3<T> cyz = vyztab[yz];
         T vx[W], nux[W], kx[W];
         bool xpos = true, xneg = true;
 #pragma unroll
         for (int e = 0; e < W; ++e) {
-            const VX3<T> cx = a.vxt[xg * W + e];
+            const VX3<T> cx = vxtab[xg * W + e];
             vx[e] = cx.vx;
             nux[e] = cx.nux;
             kx[e] = T(0.5) * (T(1) - cx.nux);
@@ -441,7 +461,7 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
 #pragma unroll
                     for (int e = 0; e < W; ++e) {
                         const T dfy = dflux<T, MUSCL>(f0[e], yu1[e], MUSCL ? yu2[e] : T(0), MUSCL ? yd1[e] : T(0), kyo, kyi);
-                        const T feq = dexp2(fma(fma(-c2, vx[e], c1), vx[e], cg));
+                        const T feq = exp2_state(fma(fma(-c2, vx[e], c1), vx[e], cg));
                         T o = fma(r, feq, omr * f0[e]);
                         o = fma(-nux[e], dfx[e], o);
                         o = fma(-cyz.nuy, dfy, o);
