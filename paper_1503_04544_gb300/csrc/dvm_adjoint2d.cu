@@ -1196,6 +1196,8 @@ struct AdjWork {
     int nslow = 0;
     int padneed[4] = {0, 0, 0, 0};                   // side cells left to the generic pad kernel
     int ncv = 0;                                     // cut and merged control volumes
+    cudaStream_t side = nullptr;                     // second stream of a transposed step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *frec = nullptr;                            // FaceRec per (listed cell, axis, face)
     void *rpart = nullptr;                           // [Z][5][nc] split sums of the relaxation transpose
     int Z = 1, Zf = 1;                               // velocity splits of the relaxation and the fast gather
@@ -1224,6 +1226,9 @@ void release(AdjWork &w)
     cudaFree(w.fin); cudaFree(w.finpart); cudaFree(w.scratch_part);
     cudaFree(w.fast); cudaFree(w.slow); cudaFree(w.nslow_d); cudaFree(w.rpart);
     cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wt); cudaFree(w.wd); cudaFree(w.pacc); cudaFree(w.frec);
+    if (w.ev_fork) cudaEventDestroy(w.ev_fork);
+    if (w.ev_join) cudaEventDestroy(w.ev_join);
+    if (w.side) cudaStreamDestroy(w.side);
     for (uint32_t *p : w.tbits) cudaFree(p);
     for (uint32_t *p : w.sbits) cudaFree(p);
     for (void *p : w.ckpt) cudaFree(p);
@@ -1292,15 +1297,22 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
     k_adj_relax<T><<<dim3(cgrid.x, cgrid.y, w.Z), cblock, 0, c->stream>>>(a, f, part, c->S, lam_in, mucv,
                                                                           (T *)w.rpart);
     k_adj_relax_fin<T><<<nba(c->nc, 256), 256, 0, c->stream>>>(a, part, c->S, (const T *)w.rpart, w.Z, aux);
-    cudaError_t e = c->scheme == DVM_MUSCL ? launch_gather_fast<T, true>(c, a, w, w.lmap[lin], bmap, lam_out)
-                                           : launch_gather_fast<T, false>(c, a, w, w.lmap[lin], nullptr, lam_out);
+    // the listed cells (record gather, then the wall terms of the wall cells
+    // among them) on the side stream, concurrently with the fast cells and
+    // their pads: the two write disjoint cells
+    cudaError_t e = cudaEventRecord(w.ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.ev_fork, 0);
     if (e != cudaSuccess) return e;
     if (w.nslow > 0)
-        k_adj_gather_rec<T><<<nba((long)w.nslow * c->ngrp, kRecItems), 4 * kRecItems, 0, c->stream>>>(
+        k_adj_gather_rec<T><<<nba((long)w.nslow * c->ngrp, kRecItems), 4 * kRecItems, 0, w.side>>>(
             a, f, lam_in, mucv, aux, w.slow, w.nslow, (const FaceRec<T> *)w.frec, lam_out);
     if (w.nw > 0)
-        k_adj_wall_step<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, (const WallVelT<T> *)w.wt, w.wd, f,
-                                                         lam_in, mucv, lam_out, w.gtw);
+        k_adj_wall_step<T><<<w.nw, 256, 0, w.side>>>(a, w.nw, w.wadj, (const WallVelT<T> *)w.wt, w.wd, f, lam_in,
+                                                      mucv, lam_out, w.gtw);
+    if ((e = cudaEventRecord(w.ev_join, w.side)) != cudaSuccess) return e;
+    e = c->scheme == DVM_MUSCL ? launch_gather_fast<T, true>(c, a, w, w.lmap[lin], bmap, lam_out)
+                               : launch_gather_fast<T, false>(c, a, w, w.lmap[lin], nullptr, lam_out);
+    if (e != cudaSuccess) return e;
     int launched = 7;
     const int nside[4] = {c->ny, c->ny, c->nx, c->nx};
     const int nmax = c->nx > c->ny ? c->nx : c->ny;
@@ -1322,6 +1334,7 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
             ++launched;
         }
     }
+    if ((e = cudaStreamWaitEvent(c->stream, w.ev_join, 0)) != cudaSuccess) return e;
     for (int s = 0; s < 4; ++s) {
         if (c->bc[s] == DVM_BC_MAXWELLIAN && !c->d_bcstate[s]) continue;
         if (w.padneed[s] == 0) continue;
@@ -1370,6 +1383,9 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMalloc(&w.slow, sizeof(int32_t) * c->nc));
         AC(cudaMalloc(&w.frec, sizeof(FaceRec<T>) * 8 * c->nc));
         AC(cudaMalloc(&w.nslow_d, 5 * sizeof(int)));
+        AC(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+        AC(cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming));
+        AC(cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming));
         w.Z = c->ngrp < 8 ? c->ngrp : 8;
         w.Zf = c->ngrp < 4 ? c->ngrp : 4;
         AC(cudaMalloc(&w.pacc, sizeof(double) * 4 * nmax * 2 * c->nv));
