@@ -1198,6 +1198,9 @@ struct AdjWork {
     int ncv = 0;                                     // cut and merged control volumes
     cudaStream_t side = nullptr;                     // second stream of a transposed step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t rstream = nullptr;                  // recomputation, one segment ahead of the reverse sweep
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr};      // recomputation into tape set s done
+    cudaEvent_t ev_used[2] = {nullptr, nullptr};     // transposed steps reading tape set s done
     void *frec = nullptr;                            // FaceRec per (listed cell, axis, face)
     void *rpart = nullptr;                           // [Z][5][nc] split sums of the relaxation transpose
     int Z = 1, Zf = 1;                               // velocity splits of the relaxation and the fast gather
@@ -1229,6 +1232,11 @@ void release(AdjWork &w)
     if (w.ev_fork) cudaEventDestroy(w.ev_fork);
     if (w.ev_join) cudaEventDestroy(w.ev_join);
     if (w.side) cudaStreamDestroy(w.side);
+    for (int q = 0; q < 2; ++q) {
+        if (w.ev_rec[q]) cudaEventDestroy(w.ev_rec[q]);
+        if (w.ev_used[q]) cudaEventDestroy(w.ev_used[q]);
+    }
+    if (w.rstream) cudaStreamDestroy(w.rstream);
     for (uint32_t *p : w.tbits) cudaFree(p);
     for (uint32_t *p : w.sbits) cudaFree(p);
     for (void *p : w.ckpt) cudaFree(p);
@@ -1384,6 +1392,11 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         AC(cudaMalloc(&w.frec, sizeof(FaceRec<T>) * 8 * c->nc));
         AC(cudaMalloc(&w.nslow_d, 5 * sizeof(int)));
         AC(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+        AC(cudaStreamCreateWithFlags(&w.rstream, cudaStreamNonBlocking));
+        for (int q = 0; q < 2; ++q) {
+            AC(cudaEventCreateWithFlags(&w.ev_rec[q], cudaEventDisableTiming));
+            AC(cudaEventCreateWithFlags(&w.ev_used[q], cudaEventDisableTiming));
+        }
         AC(cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming));
         AC(cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming));
         w.Z = c->ngrp < 8 ? c->ngrp : 8;
@@ -1404,7 +1417,9 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         if (rc != DVM_OK) return rc;
         w.cmaps.push_back(m);
     }
-    while ((int)w.tape.size() < K) {
+    // two tape sets: the recomputation of one segment fills one while the
+    // reverse sweep reads the other
+    while ((int)w.tape.size() < 2 * K) {
         void *p = nullptr, *q = nullptr;
         AC(cudaMalloc(&p, bytes));
         AC(cudaMalloc(&q, partb));
@@ -1423,7 +1438,7 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     for (int pass = 0; pass < 2 && rec; ++pass) {
         std::vector<uint32_t *> &v = pass ? w.sbits : w.tbits;
         std::vector<CUtensorMap> &mv = pass ? w.sbmap : w.tbmap;
-        const int want = pass ? nseg : K - 1;
+        const int want = pass ? nseg : 2 * (K - 1);
         while ((int)v.size() < want) {
             uint32_t *p = nullptr;
             AC(cudaMalloc(&p, bitsb));
@@ -1513,40 +1528,64 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     void *f_orig[2] = {c->f[0], c->f[1]}, *p_orig[2] = {c->part[0], c->part[1]};
     const CUtensorMap tm_orig[2] = {c->tmap[0], c->tmap[1]};
     const int cur_orig = c->cur;
-    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-        const int n0 = sgi * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps, len = n1 - n0;
-        // tape slot 0 is the checkpoint itself; step t writes slot t + 1 (state
-        // and partial moments) directly
-        const auto fslot = [&](int t) { return t == 0 ? w.ckpt[sgi] : w.tape[t]; };
-        const auto pslot = [&](int t) { return t == 0 ? w.ckpt_part[sgi] : w.ptape[t]; };
-        const auto mslot = [&](int t) { return t == 0 ? w.cmaps[sgi] : w.tmaps[t]; };
+    cudaStream_t main_stream = c->stream;
+    // tape slot 0 of segment sgi is its checkpoint; slot t > 0 is slot t of
+    // tape set sgi % 2; step t writes slot t + 1 (state and partial moments)
+    const auto fslot = [&](int sgi, int t) { return t == 0 ? w.ckpt[sgi] : w.tape[(sgi & 1) * K + t]; };
+    const auto pslot = [&](int sgi, int t) { return t == 0 ? w.ckpt_part[sgi] : w.ptape[(sgi & 1) * K + t]; };
+    const auto mslot = [&](int sgi, int t) { return t == 0 ? w.cmaps[sgi] : w.tmaps[(sgi & 1) * K + t]; };
+    const auto bslot = [&](int sgi, int t) { return (sgi & 1) * (K - 1) + t; };
+    const auto seglen = [&](int sgi) {
+        const int n0 = sgi * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
+        return n1 - n0;
+    };
+    bool used[2] = {false, false};
+    // recomputation of segment sgi on the recomputation stream
+    const auto recompute = [&](int sgi) -> cudaError_t {
+        const int set = sgi & 1, len = seglen(sgi);
+        cudaError_t er = cudaSuccess;
+        if (used[set] && (er = cudaStreamWaitEvent(w.rstream, w.ev_used[set], 0)) != cudaSuccess) return er;
+        c->stream = w.rstream;
         // the step linearises around the fused state (members of merged control
         // volumes are equal after every step, not necessarily in the initial state)
-        if (sgi == 0 && fuse0) AC(fusion2d(c, fslot(0), pslot(0)));
+        if (sgi == 0 && fuse0) er = fusion2d(c, fslot(0, 0), pslot(0, 0));
         c->need_fusion = false;
-        for (int t = 0; t + 1 < len; ++t) {
-            c->f[c->cur] = fslot(t);
-            c->f[1 - c->cur] = fslot(t + 1);
-            c->part[c->cur] = pslot(t);
-            c->part[1 - c->cur] = pslot(t + 1);
-            c->tmap[c->cur] = mslot(t);
-            c->tmap[1 - c->cur] = mslot(t + 1);
-            if (rec) c->rec_bits = w.tbits[t];
-            const cudaError_t es = step2d(c);
+        for (int t = 0; er == cudaSuccess && t + 1 < len; ++t) {
+            c->f[c->cur] = fslot(sgi, t);
+            c->f[1 - c->cur] = fslot(sgi, t + 1);
+            c->part[c->cur] = pslot(sgi, t);
+            c->part[1 - c->cur] = pslot(sgi, t + 1);
+            c->tmap[c->cur] = mslot(sgi, t);
+            c->tmap[1 - c->cur] = mslot(sgi, t + 1);
+            if (rec) c->rec_bits = w.tbits[bslot(sgi, t)];
+            er = step2d(c);
             c->rec_bits = nullptr;
             c->cur = 1 - c->cur;            // keep the same slot parity: step2d advanced it
-            AC(es);
         }
         c->f[0] = f_orig[0]; c->f[1] = f_orig[1];
         c->part[0] = p_orig[0]; c->part[1] = p_orig[1];
         c->tmap[0] = tm_orig[0]; c->tmap[1] = tm_orig[1];
         c->cur = cur_orig;
+        c->stream = main_stream;
+        if (er == cudaSuccess) er = cudaEventRecord(w.ev_rec[set], w.rstream);
+        return er;
+    };
+    // the checkpoints are written by the forward run on the main stream
+    AC(cudaStreamWaitEvent(w.rstream, ev[1], 0));
+    AC(recompute(nseg - 1));
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int set = sgi & 1, len = seglen(sgi);
+        if (sgi > 0) AC(recompute(sgi - 1));           // the next segment, while this one is swept
+        AC(cudaStreamWaitEvent(c->stream, w.ev_rec[set], 0));
         for (int t = len - 1; t >= 0; --t) {
-            const CUtensorMap *bm = !rec ? nullptr : (t == len - 1 ? &w.sbmap[sgi] : &w.tbmap[t]);
-            const uint32_t *bits = !rec ? nullptr : (t == len - 1 ? w.sbits[sgi] : w.tbits[t]);
-            AC(adjoint_step<T>(c, w, (const T *)fslot(t), (const T *)pslot(t), bits, bm, lin, (T *)w.lam[1 - lin]));
+            const CUtensorMap *bm = !rec ? nullptr : (t == len - 1 ? &w.sbmap[sgi] : &w.tbmap[bslot(sgi, t)]);
+            const uint32_t *bits = !rec ? nullptr : (t == len - 1 ? w.sbits[sgi] : w.tbits[bslot(sgi, t)]);
+            AC(adjoint_step<T>(c, w, (const T *)fslot(sgi, t), (const T *)pslot(sgi, t), bits, bm, lin,
+                               (T *)w.lam[1 - lin]));
             lin = 1 - lin;
         }
+        AC(cudaEventRecord(w.ev_used[set], c->stream));
+        used[set] = true;
     }
     AC(cudaEventRecord(ev[2], c->stream));
     // J and dJ/dT_w per sector: ordered sums over the wall list on the host
