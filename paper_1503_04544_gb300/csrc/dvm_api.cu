@@ -263,6 +263,12 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
         c->S = best;
     }
     const int nmom = dim == 2 ? 4 : 5;
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->wstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_wfork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_wjoin, cudaEventDisableTiming);
+        if (e != cudaSuccess) { delete c; return cuda_fail(e, "wall stream"); }
+    }
     if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
     else {
         cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -373,6 +379,9 @@ void dvm_destroy(dvm_ctx *c)
         delete pool;
     }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->ev_wfork) cudaEventDestroy(c->ev_wfork);
+    if (c->ev_wjoin) cudaEventDestroy(c->ev_wjoin);
+    if (c->wstream) cudaStreamDestroy(c->wstream);
     delete c;
 }
 

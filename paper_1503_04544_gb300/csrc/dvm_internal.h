@@ -132,6 +132,8 @@ struct dvm_ctx {
     int S;                        // velocity splits of the bulk kernel
     cudaStream_t stream;
     bool own_stream;
+    cudaStream_t wstream;         // the wall kernel's stream (concurrent with the bulk kernel)
+    cudaEvent_t ev_wfork, ev_wjoin;
     int bc[6];
     dvm_body body;
     double *d_Twseg, *d_segdir;

@@ -1257,8 +1257,14 @@ cudaError_t step2d_t(dvm_ctx *c)
             k_fusion<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, pin);
             c->launches += 1;
         }
-        k_wall<T><<<cvgrid, 256, 0, c->stream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
-                                                  c->d_hist, moving ? 1 : 0);
+        // the wall kernel (wall density, stress, force, rotation) runs beside the
+        // bulk kernel, which reads none of its outputs; the control-volume
+        // kernel waits for it
+        if ((e = cudaEventRecord(c->ev_wfork, c->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->wstream, c->ev_wfork, 0)) != cudaSuccess) return e;
+        k_wall<T><<<cvgrid, 256, 0, c->wstream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
+                                                   c->d_hist, moving ? 1 : 0);
+        if ((e = cudaEventRecord(c->ev_wjoin, c->wstream)) != cudaSuccess) return e;
         c->launches += 1;
     }
     BulkArgs<T> a;
@@ -1274,6 +1280,7 @@ cudaError_t step2d_t(dvm_ctx *c)
     if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
     c->launches += 1;
     if (body) {
+        if ((e = cudaStreamWaitEvent(c->stream, c->ev_wjoin, 0)) != cudaSuccess) return e;
         k_special<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, fout, pin, pout, c->wphi);
         c->launches += 1;
     }
