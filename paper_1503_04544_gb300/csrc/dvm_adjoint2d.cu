@@ -692,6 +692,64 @@ __device__ __forceinline__ T pad_pair(bool inward, T nu, T l0, T l1, uint32_t bp
     return (MUSCL && (bo & 1u)) ? -nu * kap * l0 : T(0);
 }
 
+// Branch words of the boundary faces: for every plain cell on a side and
+// velocity group, the limiter branch of its face on that side for the
+// velocities entering through it, minmod(F_0 - F_P1, F_P1 - F_P2) with P1, P2
+// the pads beyond the face (the upwind face of the cell, "downwind" of P1),
+// written at the padded index of P1 in the branch words of F^n.  Same
+// operands and direction rule as the forward step (the group's sign when its
+// velocities share it, else each element's); 0 where the face is first
+// order.  One thread per (side, side cell, velocity group).
+template <typename T>
+__device__ __forceinline__ uint32_t branch_code(T m, T b) { return m == T(0) ? 0u : (m == b ? 2u : 1u); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_padwords(Grid2D g, const T *f, const uint8_t *flags, const int8_t *gsign,
+                                                      const VCoef<T> *vt, uint32_t *bits, long bslab, int bpitch)
+{
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    const int nmax = g.nx > g.ny ? g.nx : g.ny;
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long per = (long)nmax * g.ngrp;
+    if (t >= 4 * per) return;
+    const int side = (int)(t / per);
+    t %= per;
+    const int q = (int)(t % nmax), grp = (int)(t / nmax), p = grp * W;
+    const int axis = side >> 1;
+    const int n = axis == 0 ? g.nx : g.ny, nside = axis == 0 ? g.ny : g.nx;
+    if (q >= nside) return;
+    const int ib = (side & 1) ? n - 1 : 0;
+    const int ci = axis == 0 ? ib : q, cj = axis == 0 ? q : ib;
+    const uint8_t fl = flags[(long)cj * g.nx + ci];
+    if (!(fl & kPlain)) return;
+    const int di = axis == 0 ? ((side & 1) ? 1 : -1) : 0, dj = axis == 1 ? ((side & 1) ? 1 : -1) : 0;
+    // the incoming face on this side: x- / x+ / y- / y+ limiter mask bit
+    const bool wi = (fl >> kMaskShift) & (1 << side);
+    const int sg = gsign[2 * grp + axis];
+    uint32_t word = 0;
+    if (wi) {
+        for (int comp = 0; comp < 2; ++comp) {
+            const V *F = reinterpret_cast<const V *>(f + ebase<T>(g, comp, p));
+            T f0[W], f1[W], f2v[W];
+            vld<T>(F + nbr(g, ci, cj), f0);
+            vld<T>(F + nbr(g, ci + di, cj + dj), f1);
+            vld<T>(F + nbr(g, ci + 2 * di, cj + 2 * dj), f2v);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const VCoef<T> vc = ld_coef(vt + p + e);
+                const T v = axis == 0 ? vc.vx : vc.vy;
+                const bool pos = sg != 0 ? sg > 0 : v >= T(0);
+                const bool entering = (side & 1) ? !pos : pos;
+                if (!entering) continue;
+                const T a = f0[e] - f1[e], c = f1[e] - f2v[e];
+                word |= branch_code(minmod3(a, c), c) << (((comp * 2 + axis) * W + e) * 2);
+            }
+        }
+    }
+    bits[(long)grp * bslab + (long)(cj + dj + 2) * bpitch + ci + di + 2] = word;
+}
+
 // Pads of a zero-gradient or Maxwellian side whose boundary cell is a fast
 // cell (one thread per (side, side cell, velocity group), after the fast
 // gather; the two sides of one axis together, as they touch distinct cells):
@@ -1299,6 +1357,12 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
     const T *lam_in = (const T *)w.lam[lin];
     const AdjArgs a = adj_args(c, w);
     T *mucv = (T *)w.mucv, *aux = (T *)w.aux;
+    if (bits) {
+        const int nmax = c->nx > c->ny ? c->nx : c->ny;
+        k_adj_padwords<T><<<nba(4L * nmax * c->ngrp, 256), 256, 0, c->stream>>>(
+            a.g, f, c->flags, c->gsign, (const VCoef<T> *)c->vtab, const_cast<uint32_t *>(bits), bits_slab(c),
+            bits_pitch(c));
+    }
     const dim3 cvg((unsigned)(w.ncv > 0 ? w.ncv : 1), nba(2L * c->nvp, 256));
     if (w.ncv > 0) k_adj_mu<T><<<cvg, 256, 0, c->stream>>>(a, lam_in, mucv);
     const dim3 cgrid(nba(c->nx, 32), nba(c->ny, 8)), cblock(32, 8);

@@ -90,15 +90,14 @@ __device__ __forceinline__ uint32_t branch_bits(T m, T a, T b, T w)
 // FluxDD in difference form with the limited reconstruction), moment sums.
 // c0 is the tile index of the cell; ux1/uy1 the tile offsets of one cell step
 // towards the upwind side along x/y (sign-uniform groups), else per element.
-// With REC the branches of the two downwind faces are or-ed into bw, those of
-// the two upwind (incoming) faces into bi, at bit ((COMP * 2 + axis) * W + e) * 2.
+// With REC the branches of the two downwind faces are or-ed into bw at bit
+// ((COMP * 2 + axis) * W + e) * 2.
 template <typename T, bool MUSCL, int COMP, bool UNIFORM, bool REC>
 __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0, int ux1, int uy1,
                                           const T (&vx)[Vec<T>::W], const T (&vy)[Vec<T>::W],
                                           const T (&nux)[Vec<T>::W], const T (&nuy)[Vec<T>::W],
                                           const T (&feq)[Vec<T>::W], T wxm, T wxp, T wym, T wyp, T r,
-                                          T (&out)[Vec<T>::W], T &q0, T &q1, T &q2, T &q3, uint32_t &bw,
-                                          uint32_t &bi)
+                                          T (&out)[Vec<T>::W], T &q0, T &q1, T &q2, T &q3, uint32_t &bw)
 {
     constexpr int W = Vec<T>::W;
     T f[W];
@@ -128,8 +127,6 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
                 if (REC) {
                     bw |= branch_bits(mxo, bx, ax, cxo) << (((COMP * 2 + 0) * W + e) * 2);
                     bw |= branch_bits(myo, by, ay, cyo) << (((COMP * 2 + 1) * W + e) * 2);
-                    bi |= branch_bits(mxi, ax, cx, cxi) << (((COMP * 2 + 0) * W + e) * 2);
-                    bi |= branch_bits(myi, ay, cy, cyi) << (((COMP * 2 + 1) * W + e) * 2);
                 }
             }
             out[e] = f[e] - nux[e] * dfx - nuy[e] * dfy + r * (feq[e] - f[e]);
@@ -160,8 +157,6 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
                 if (REC) {
                     bw |= branch_bits(mxo, bx, ax, cxo) << (((COMP * 2 + 0) * W + e) * 2);
                     bw |= branch_bits(myo, by, ay, cyo) << (((COMP * 2 + 1) * W + e) * 2);
-                    bi |= branch_bits(mxi, ax, cx, cxi) << (((COMP * 2 + 0) * W + e) * 2);
-                    bi |= branch_bits(myi, ay, cy, cyi) << (((COMP * 2 + 1) * W + e) * 2);
                 }
             }
             out[e] = f[e] - nux[e] * dfx - nuy[e] * dfy + r * (feq[e] - f[e]);
@@ -195,7 +190,7 @@ __device__ __forceinline__ uint32_t bcode(float m, float b) { return m == 0.f ? 
 template <int COMP, bool REC>
 __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, int uy1, const PairCoef &P,
                                              const F2 (&feq)[2], float wxm, float wxp, float wym, float wyp, F2 r,
-                                             float (&out)[4], F2 (&Q)[4], uint32_t &bw, uint32_t &bi, bool edge)
+                                             float (&out)[4], F2 (&Q)[4], uint32_t &bw)
 {
     float f[4], u1[4], w1[4], d1[4], u2[4], e1[4], w2[4];
     sld<float>(t + c0, f);
@@ -209,7 +204,7 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
     const float cxo = px ? wxp : wxm, cxi = px ? wxm : wxp;
     const float cyo = py ? wyp : wym, cyi = py ? wym : wyp;
     const F2 CXO = f2(cxo), NCXI = f2(-cxi), CYO = f2(cyo), NCYI = f2(-cyi);
-    uint32_t lo = 0, li = 0;          // branch codes before the face-weight masks
+    uint32_t lo = 0;                  // branch codes before the face-weight masks
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int a0 = 2 * h, a1 = 2 * h + 1;
@@ -229,11 +224,6 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
                 const int e = 2 * h + l;
                 lo |= bcode(mxo[l], ax[l]) << (((COMP * 2 + 0) * 4 + e) * 2);
                 lo |= bcode(myo[l], ay[l]) << (((COMP * 2 + 1) * 4 + e) * 2);
-                // incoming faces: only a cell on a side stores them
-                if (edge) {
-                    li |= bcode(mxi[l], cx[l]) << (((COMP * 2 + 0) * 4 + e) * 2);
-                    li |= bcode(myi[l], cy[l]) << (((COMP * 2 + 1) * 4 + e) * 2);
-                }
             }
         }
         const F2 TX = fma2(NCXI, f2(mxi[0], mxi[1]), mul2(CXO, f2(mxo[0], mxo[1])));
@@ -255,9 +245,7 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
     if (REC) {
         // first-order faces record no branch: x fields 0x00FF00FF, y fields 0xFF00FF00
         const uint32_t mo = (cxo != 0.f ? 0x00FF00FFu : 0u) | (cyo != 0.f ? 0xFF00FF00u : 0u);
-        const uint32_t mi = (cxi != 0.f ? 0x00FF00FFu : 0u) | (cyi != 0.f ? 0xFF00FF00u : 0u);
         bw |= lo & mo;
-        bi |= li & mi;
     }
 }
 
@@ -299,10 +287,7 @@ __device__ __forceinline__ void store_cell(typename Vec<T>::type *slab, long pc,
 // barriers.
 // With REC (recomputation for the discrete adjoint) each plain cell also
 // writes the limiter branches of its downwind faces, one word per group at
-// its padded index (row pitch bpitch); a cell on a side also writes the
-// branches of its face on that side, for the velocities entering through it,
-// at the padded index of the pad across that face (the face is "downwind" of
-// that pad).
+// its padded index (row pitch bpitch).
 template <typename T, bool MUSCL, bool REC>
 __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __grid_constant__ CUtensorMap tmap)
 {
@@ -326,7 +311,6 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     const int ngr = max(g1 - g0, 0);
     const uint8_t fl = inside ? a.flags[cell] : 0;
     const bool plain = (fl & kPlain) != 0, zero = (fl & kZero) != 0;
-    const bool edge = i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1;   // a cell on a side
     V *fout = reinterpret_cast<V *>(a.fout);
 
     if (tid == 0) {
@@ -397,7 +381,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                 const VCoef<T> vc = ld_coef(a.vt + q * W + e);
                 vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
             }
-            uint32_t bw = 0, bi = 0;
+            uint32_t bw = 0;
             if constexpr (sizeof(T) == 4 && MUSCL) {
                 if (sx != 0 && sy != 0) {
                     // packed FP32 path of the sign-uniform groups
@@ -427,12 +411,12 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                         fq[h] = f2(fe[0], fe[1]);
                     }
                     const F2 r2 = f2(r);
-                    bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw, bi, edge);
+                    bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw);
                     store_cell<T>(o0, pc, mir, anymir, out);
                     const F2 gf = f2(gfac);
                     fq[0] = mul2(fq[0], gf); fq[1] = mul2(fq[1], gf);
                     bulk_tile_x2<1, REC>(tile + kTileY * kTileX, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out,
-                                         Qp, bw, bi, edge);
+                                         Qp, bw);
                     store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
                     goto stored;
                 }
@@ -445,45 +429,25 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
             if (sx != 0 && sy != 0) {
                 const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
                 bulk_tile<T, MUSCL, 0, true, REC>(tile, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
-                                                  out, q0, q1, q2, q3, bw, bi);
+                                                  out, q0, q1, q2, q3, bw);
                 store_cell<T>(o0, pc, mir, anymir, out);
 #pragma unroll
                 for (int e = 0; e < W; ++e) feq[e] *= gfac;
                 bulk_tile<T, MUSCL, 1, true, REC>(tile + kTileY * kTileX, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm,
-                                                  wxp, wym, wyp, r, out, q0, q1, q2, q3, bw, bi);
+                                                  wxp, wym, wyp, r, out, q0, q1, q2, q3, bw);
                 store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
             } else {
                 bulk_tile<T, MUSCL, 0, false, REC>(tile, c0, 1, kTileX, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
-                                                   out, q0, q1, q2, q3, bw, bi);
+                                                   out, q0, q1, q2, q3, bw);
                 store_cell<T>(o0, pc, mir, anymir, out);
 #pragma unroll
                 for (int e = 0; e < W; ++e) feq[e] *= gfac;
                 bulk_tile<T, MUSCL, 1, false, REC>(tile + kTileY * kTileX, c0, 1, kTileX, vx, vy, nux, nuy, feq,
-                                                   wxm, wxp, wym, wyp, r, out, q0, q1, q2, q3, bw, bi);
+                                                   wxm, wxp, wym, wyp, r, out, q0, q1, q2, q3, bw);
                 store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
             }
         stored:
-            if (REC) {
-                uint32_t *bq = a.bits + (long)q * a.bslab;
-                const auto bix = [&](int ii, int jj) { return (long)(jj + 2) * a.bpitch + ii + 2; };
-                bq[bix(i, j)] = bw;
-                if (edge) {
-                    // fields of the velocities that enter through each side
-                    uint32_t xin = 0, xout = 0, yin = 0, yout = 0;
-#pragma unroll
-                    for (int e = 0; e < W; ++e)
-#pragma unroll
-                        for (int cp = 0; cp < 2; ++cp) {
-                            const uint32_t fx = 3u << (((cp * 2 + 0) * W + e) * 2), fy = 3u << (((cp * 2 + 1) * W + e) * 2);
-                            if (vx[e] >= T(0)) xin |= fx; else xout |= fx;
-                            if (vy[e] >= T(0)) yin |= fy; else yout |= fy;
-                        }
-                    if (i == 0) bq[bix(-1, j)] = bi & xin;
-                    if (i == g.nx - 1) bq[bix(g.nx, j)] = bi & xout;
-                    if (j == 0) bq[bix(i, -1)] = bi & yin;
-                    if (j == g.ny - 1) bq[bix(i, g.ny)] = bi & yout;
-                }
-            }
+            if (REC) a.bits[(long)q * a.bslab + (long)(j + 2) * a.bpitch + i + 2] = bw;
             // fold the plain sums of 8 groups into the compensated sums
             if (++fold == 8) {
                 if constexpr (sizeof(T) == 4 && MUSCL) fold_pairs(Qp, q0, q1, q2, q3);
