@@ -1221,14 +1221,14 @@ cudaError_t step2d_t(dvm_ctx *c)
             k_fusion<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, pin);
             c->launches += 1;
         }
-        // the wall kernel (wall density, stress, force, rotation) runs beside the
-        // bulk kernel, which reads none of its outputs; the control-volume
-        // kernel waits for it
+        // the wall kernel (wall density, stress, force, rotation) and then the
+        // control-volume kernel run on the side stream beside the bulk kernel:
+        // both read F^n and write only the cut and merged control volumes,
+        // the bulk kernel only the plain cells
         if ((e = cudaEventRecord(c->ev_wfork, c->stream)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->wstream, c->ev_wfork, 0)) != cudaSuccess) return e;
         k_wall<T><<<cvgrid, 256, 0, c->wstream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
                                                    c->d_hist, moving ? 1 : 0);
-        if ((e = cudaEventRecord(c->ev_wjoin, c->wstream)) != cudaSuccess) return e;
         c->launches += 1;
     }
     BulkArgs<T> a;
@@ -1244,8 +1244,10 @@ cudaError_t step2d_t(dvm_ctx *c)
     if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
     c->launches += 1;
     if (body) {
+        k_special<T><<<cvgrid, 256, 0, c->wstream>>>(cv, fin, fout, pin, pout, c->wphi);
+        if ((e = cudaEventRecord(c->ev_wjoin, c->wstream)) != cudaSuccess) return e;
+        // the step ends when both streams are done
         if ((e = cudaStreamWaitEvent(c->stream, c->ev_wjoin, 0)) != cudaSuccess) return e;
-        k_special<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, fout, pin, pout, c->wphi);
         c->launches += 1;
     }
     c->cur = 1 - c->cur;
