@@ -1246,7 +1246,13 @@ cudaError_t step3d_t(dvm_ctx *c)
             k_fusion3<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, pin);
             c->launches += 1;
         }
-        k_wall3<T><<<cvgrid, 256, 0, c->stream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket, c->d_hist);
+        // the wall kernel and then the control-volume kernel run on the side
+        // stream beside the bulk kernel: both read F^n and write only the cut
+        // and merged control volumes, the bulk kernel only the plain cells
+        if ((e = cudaEventRecord(c->ev_wfork, c->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->wstream, c->ev_wfork, 0)) != cudaSuccess) return e;
+        k_wall3<T><<<cvgrid, 256, 0, c->wstream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
+                                                    c->d_hist);
         c->launches += 1;
     }
     Bulk3Args<T> a;
@@ -1259,7 +1265,10 @@ cudaError_t step3d_t(dvm_ctx *c)
     if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
     c->launches += 1;
     if (body) {
-        k_special3<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, fout, pin, pout, c->wphi);
+        k_special3<T><<<cvgrid, 256, 0, c->wstream>>>(cv, fin, fout, pin, pout, c->wphi);
+        if ((e = cudaEventRecord(c->ev_wjoin, c->wstream)) != cudaSuccess) return e;
+        // the step ends when both streams are done
+        if ((e = cudaStreamWaitEvent(c->stream, c->ev_wjoin, 0)) != cudaSuccess) return e;
         c->launches += 1;
     }
     c->cur = 1 - c->cur;
