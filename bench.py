@@ -154,8 +154,9 @@ def cpu_sample_cfg(cfg):
     return cfg
 
 
-def cpu_baseline(cfg, budget_s: float = 20.0, max_steps: int = 4):
-    """Time the FP64 oracle as it stands on the host cores (bounded sample)."""
+def cpu_baseline(cfg, budget_s: float = 12.0, max_steps: int = 1000):
+    """Time the FP64 oracle as it stands on the host cores: whole steps from the
+    initial state until about budget_s seconds of work (a bounded sample)."""
     import numpy as np
     import oracle
     cfg = cpu_sample_cfg(cfg)
