@@ -219,6 +219,25 @@ def adjoint_cost(precision_fp32: bool = True):
                     "gradient = checkpointed forward + reverse"}
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of ``values`` over the ranks of the default process
+    group; the values themselves when no group of more than one rank exists."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_throughput(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job rate of ``world`` independent replicas (weak scaling): the units
+    every rank processed over the slowest rank's time."""
+    if seconds <= 0.0:
+        raise ValueError("non-positive time")
+    return world * units_per_rank / seconds
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -302,10 +321,6 @@ def main():
     ms = e0.elapsed_time(e1)
     bulk_ms, nb = s.kernel_time()
     s.timing(False)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     barrier()
 
     # end to end through the public API with pinned host buffers
@@ -322,9 +337,10 @@ def main():
     m = s.moments()
     barrier()
     e2e_s = time.perf_counter() - t0
+    ms_max, e2e_s = max_over_ranks([ms, e2e_s], "cuda")
     h2d = s.state_size * s.elem
     d2h = 5 * 8 * s.ncell
-    e2e = {"value": world * pairs_per_step * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": replica_throughput(pairs_per_step * args.steps, e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "per run: state H2D from pinned host memory, K steps, moments D2H"}
     assert np.isfinite(m["rho"]).all()
@@ -339,7 +355,7 @@ def main():
             os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step3d.cu" if dim3 else "dvm_step2d.cu"))
         line = {
             "metric": METRIC,
-            "value": world * pairs_per_step * args.steps / (ms_max / 1e3),
+            "value": replica_throughput(pairs_per_step * args.steps, ms_max / 1e3, world),
             "unit": UNIT,
             "n_gpus": world,
             "steps": args.steps,
