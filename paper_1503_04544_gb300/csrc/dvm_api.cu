@@ -290,6 +290,7 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     if (dim == 2) {
         AL(c->vtab, (size_t)c->nvp * vcoef_bytes(c->prec));
         AL(c->gsign, (size_t)2 * c->ngrp);
+        AL(c->ptab, (size_t)c->ngrp * 7 * 16);
         for (int l = 0; l < 2; ++l) {
             dvm::Geo2D &G = c->geo[l];
             AL(G.phi, sizeof(double) * (c->nx + 1) * (c->ny + 1));
@@ -358,7 +359,7 @@ void dvm_destroy(dvm_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->part[0]); cudaFree(c->part[1]);
-    cudaFree(c->vtab); cudaFree(c->gsign); cudaFree(c->wslot); cudaFree(c->ticket);
+    cudaFree(c->vtab); cudaFree(c->ptab); cudaFree(c->gsign); cudaFree(c->wslot); cudaFree(c->ticket);
     cudaFree(c->wflux); cudaFree(c->d_pub);
     for (int l = 0; l < 2; ++l) free_geo(c->geo[l]);
     free_geo3(c->geo3);

@@ -141,6 +141,7 @@ struct dvm_ctx {
     int cur;
     void *part[2];                // [S][4][nc] partial moment sums, paired with f
     void *vtab;                   // [nvp][8] per-velocity coefficients (state precision)
+    void *ptab;                   // [ngrp][7] float4: FP32 coefficients of a group in packed-pair order (2D)
     int8_t *gsign;                // [ngrp][2] sign of v_x, v_y in a group (0: mixed)
     dvm::Geo2D geo[2];
     dvm::Geo3D geo3;              // 3D geometry (fixed obstacle)

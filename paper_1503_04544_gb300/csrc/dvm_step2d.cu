@@ -64,6 +64,7 @@ template <typename T> struct BulkArgs {
     T *pout;                  // partial moments of f^n+1 [S][4][nc]
     const uint8_t *flags;
     const VCoef<T> *vt;       // [nvp]
+    const ulonglong2 *pt;     // [ngrp][7] packed-pair coefficients (FP32 path)
     const int8_t *gsign;      // [ngrp][2]
     uint32_t *bits;           // [ngrp][bslab] limiter branches of the downwind faces (recording only)
     int bpitch;               // row pitch of the branch words
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
         c2 = T(kLog2e) / (T(2) * tmp);
         r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
         gfac = tmp / T(2);
-        // log2 M(v) = el0 + vx (e1x - c2 vx) + vy (e1y - c2 vy) (packed path)
+        // log2 M(v) = el0 + e1x vx + e1y vy - c2 |v|^2 (packed path)
         if (!REC) {
             el0 = log2(A) - c2 * (ux * ux + uy * uy);
             e1x = T(2) * c2 * ux;
@@ -355,6 +356,11 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     const bool anymir = __any_sync(0xffffffffu, inside && (mir[0] >= 0 || mir[2] >= 0));
     __syncthreads();
 
+    // the exponent's per-cell terms as pairs (packed path)
+    F2 EL0, E1X, E1Y, NC2;
+    if constexpr (sizeof(T) == 4 && MUSCL && !REC) {
+        EL0 = f2(el0); E1X = f2(e1x); E1Y = f2(e1y); NC2 = f2(-2.f * c2);
+    }
     Acc<T> m0, m1, m2, m3;
     T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
     F2 Qp[4];                 // per-lane sums of the packed FP32 path
@@ -376,39 +382,45 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
         if (plain) {
             const int sx = a.gsign[2 * q], sy = a.gsign[2 * q + 1];
             T vx[W], vy[W], nux[W], nuy[W], feq[W], out[W];
-#pragma unroll
-            for (int e = 0; e < W; ++e) {
-                const VCoef<T> vc = ld_coef(a.vt + q * W + e);
-                vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
-            }
             uint32_t bw = 0;
             if constexpr (sizeof(T) == 4 && MUSCL) {
                 if (sx != 0 && sy != 0) {
-                    // packed FP32 path of the sign-uniform groups
+                    // packed FP32 path of the sign-uniform groups, coefficients
+                    // from the group's rows of the packed table
                     const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
                     PairCoef P;
+                    {
+                        const ulonglong2 *pt = a.pt + (long)q * 7;
+                        F2 *rows[7] = {P.nnx, P.nny, P.onx, P.ony, P.vx, P.vy, P.ke};
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) {
+                            const ulonglong2 v = __ldg(pt + k);
+                            rows[k][0].v = v.x;
+                            rows[k][1].v = v.y;
+                        }
+                    }
                     F2 fq[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int a0 = 2 * h, a1 = 2 * h + 1;
-                        P.nnx[h] = f2(-nux[a0], -nux[a1]); P.nny[h] = f2(-nuy[a0], -nuy[a1]);
-                        P.onx[h] = f2(T(1) - nux[a0], T(1) - nux[a1]); P.ony[h] = f2(T(1) - nuy[a0], T(1) - nuy[a1]);
-                        P.vx[h] = f2(vx[a0], vx[a1]); P.vy[h] = f2(vy[a0], vy[a1]);
-                        P.ke[h] = f2(T(0.5) * (vx[a0] * vx[a0] + vy[a0] * vy[a0]),
-                                     T(0.5) * (vx[a1] * vx[a1] + vy[a1] * vy[a1]));
-                        float fe[2];
+                        if (REC) {          // the recording variant keeps fewer per-cell registers
+                            float pvx[2], pvy[2], fe[2];
+                            f2_get(P.vx[h], pvx[0], pvx[1]);
+                            f2_get(P.vy[h], pvy[0], pvy[1]);
 #pragma unroll
-                        for (int l = 0; l < 2; ++l) {
-                            const int e = 2 * h + l;
-                            if (REC) {      // the recording variant keeps fewer per-cell registers
-                                const T dx = vx[e] - ux, dy = vy[e] - uy;
+                            for (int l = 0; l < 2; ++l) {
+                                const T dx = pvx[l] - ux, dy = pvy[l] - uy;
                                 fe[l] = A * dexp2(-(dx * dx + dy * dy) * c2);
-                            } else {
-                                fe[l] = ex2_fast(fmaf(fmaf(-c2, vx[e], e1x), vx[e],
-                                                      fmaf(fmaf(-c2, vy[e], e1y), vy[e], el0)));
                             }
+                            fq[h] = f2(fe[0], fe[1]);
+                        } else {
+                            // log2 M = el0 - 2 c2 |v|^2/2 + e1x vx + e1y vy
+                            F2 X = fma2(NC2, P.ke[h], EL0);
+                            X = fma2(E1X, P.vx[h], X);
+                            X = fma2(E1Y, P.vy[h], X);
+                            float x0, x1;
+                            f2_get(X, x0, x1);
+                            fq[h] = f2(ex2_fast(x0), ex2_fast(x1));
                         }
-                        fq[h] = f2(fe[0], fe[1]);
                     }
                     const F2 r2 = f2(r);
                     bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw);
@@ -420,6 +432,11 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                     store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
                     goto stored;
                 }
+            }
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const VCoef<T> vc = ld_coef(a.vt + q * W + e);
+                vx[e] = vc.vx; vy[e] = vc.vy; nux[e] = vc.nux; nuy[e] = vc.nuy;
             }
 #pragma unroll
             for (int e = 0; e < W; ++e) {
@@ -1139,9 +1156,12 @@ __global__ void __launch_bounds__(1024) k_sum(const double *x, long n, double *o
     if (threadIdx.x == 0) *out = s;
 }
 
-// Per-velocity coefficients and per-group sign of the velocity components.
+// Per-velocity coefficients, per-group sign of the velocity components and
+// the FP32 coefficients of each group in the order of the packed path: seven
+// float4 rows -nux, -nuy, 1 - nux, 1 - nuy, vx, vy, |v|^2/2 over the group's
+// four lanes (lanes 0, 1 and 2, 3 form the two pairs).
 template <typename T>
-__global__ void k_tables(Grid2D g, VCoef<T> *vt, int8_t *gsign)
+__global__ void k_tables(Grid2D g, VCoef<T> *vt, int8_t *gsign, float4 *ptab)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int W = Vec<T>::W;
@@ -1168,6 +1188,23 @@ __global__ void k_tables(Grid2D g, VCoef<T> *vt, int8_t *gsign)
         }
         gsign[2 * p] = xp ? 1 : (xn ? -1 : 0);
         gsign[2 * p + 1] = yp ? 1 : (yn ? -1 : 0);
+        float row[7][4];
+        for (int e = 0; e < 4; ++e) {
+            const int q = p * 4 + e;
+            float vx = 1e4f, vy = 1e4f, nux = 0.f, nuy = 0.f;    // padding lanes: feq = 0, no transport
+            if (q < g.nv) {
+                vx = float(g.vxmin + (q % g.nvx) * g.dvx);
+                vy = float(g.vymin + (q / g.nvx) * g.dvy);
+                nux = fabsf(vx) * float(g.dt / g.dx);
+                nuy = fabsf(vy) * float(g.dt / g.dy);
+            }
+            row[0][e] = -nux; row[1][e] = -nuy;
+            row[2][e] = 1.f - nux; row[3][e] = 1.f - nuy;
+            row[4][e] = vx; row[5][e] = vy;
+            row[6][e] = 0.5f * (vx * vx + vy * vy);
+        }
+        if (W == 4)
+            for (int r = 0; r < 7; ++r) ptab[p * 7 + r] = make_float4(row[r][0], row[r][1], row[r][2], row[r][3]);
     }
 }
 
@@ -1234,6 +1271,7 @@ cudaError_t step2d_t(dvm_ctx *c)
     BulkArgs<T> a;
     a.g = g; a.S = c->S; a.fin = fin; a.fout = fout; a.pin = pin; a.pout = pout;
     a.flags = c->flags; a.vt = (const VCoef<T> *)c->vtab; a.gsign = c->gsign; a.err = c->d_err;
+    a.pt = (const ulonglong2 *)c->ptab;
     a.bits = c->rec_bits;
     a.bpitch = bits_pitch(c);
     a.bslab = bits_slab(c);
@@ -1371,9 +1409,11 @@ cudaError_t tables2d(dvm_ctx *c)
     Grid2D g = grid2d(c);
     const int n = c->nvp > c->ngrp ? c->nvp : c->ngrp;
     if (c->prec == DVM_FP32)
-        k_tables<float><<<nblk(n, 256), 256, 0, c->stream>>>(g, (VCoef<float> *)c->vtab, c->gsign);
+        k_tables<float><<<nblk(n, 256), 256, 0, c->stream>>>(g, (VCoef<float> *)c->vtab, c->gsign,
+                                                              (float4 *)c->ptab);
     else
-        k_tables<double><<<nblk(n, 256), 256, 0, c->stream>>>(g, (VCoef<double> *)c->vtab, c->gsign);
+        k_tables<double><<<nblk(n, 256), 256, 0, c->stream>>>(g, (VCoef<double> *)c->vtab, c->gsign,
+                                                               (float4 *)c->ptab);
     return cudaGetLastError();
 }
 
