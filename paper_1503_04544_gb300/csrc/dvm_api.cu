@@ -237,12 +237,18 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     }
     c->dev_elems = (size_t)c->ngrp * c->ncomp * c->slab * c->W;
     if (dim == 2) {
-        // velocity splits: enough blocks for a few waves on 152 SMs
+        // velocity splits: the count that minimises the load of the busiest
+        // SM, ceil(blocks / 152) blocks of (groups per split + 5) group
+        // times each (5: the per-block prologue and pipeline fill, fitted
+        // to measured bulk times); ties go to the smaller count
         const long blocks = (long)((c->nx + 31) / 32) * ((c->ny + kRows - 1) / kRows);
-        int S = (int)((1200 + blocks - 1) / blocks);
-        if (S < 1) S = 1;
-        if (S > 16) S = 16;
-        if (S > c->ngrp) S = c->ngrp;
+        int S = 1;
+        long best = -1;
+        for (int s = 1; s <= 16 && s <= c->ngrp; ++s) {
+            const long per_sm = (blocks * s + 151) / 152;
+            const long cost = per_sm * ((c->ngrp + s - 1) / s + 5);
+            if (best < 0 || cost < best) { best = cost; S = s; }
+        }
         c->S = S;
     } else {
         // one resident block per SM (tiles of 32 x 12 cells in FP32, 32 x 8 in
