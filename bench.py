@@ -33,6 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-velocity pair updates/s"
 UNIT = "pair-updates/s"
 FALLBACK_HBM_GBS = 6800.0
+# FP64 ceiling of the 2D FP64 line: 152 SMs x 2 FP64 FMA lanes per clock x
+# 2 flop x 2.07 GHz (the part's nominal 1.25 TFLOP/s FP64 rate)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# algorithmic FP64 flops of one 2D MUSCL pair update (f and g): limited
+# fluxes 2 x 16, update 2 x 7, Maxwellian 9, moments 8 (add/sub/mul 1,
+# fma 2, exp 1, min/max 0)
+FP64_FLOPS_PER_PAIR = 63
 
 
 def workload(name: str):
@@ -353,6 +360,22 @@ def main():
         traffic = recorded_traffic(
             f"k_bulk{'3' if dim3 else ''}_{args.workload}_{args.precision}.md",
             os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step3d.cu" if dim3 else "dvm_step2d.cu"))
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": ("k_bulk3" if dim3 else "k_bulk") + " (fused stream + relax + moments)",
+                    "peak_source": f"{peak_kind} HBM copy bandwidth",
+                    "bytes_per_pair": bytes_per_pair,
+                    "bulk_ms_per_launch": avg_bulk_s * 1e3,
+                    "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)}
+        if prec == dvm.FP64 and not dim3 and cfg.get("scheme", 1) == 1:
+            # the FP64 step is bound by the FP64 pipe on this part: report
+            # that ceiling, with the HBM view beside it
+            gflops = FP64_FLOPS_PER_PAIR * bulk_pairs / avg_bulk_s / 1e9
+            hbm = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "peak_source", "bytes_per_pair")}
+            roofline.update({"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                             "frac": gflops / FP64_PEAK_GFLOPS, "flops_per_pair": FP64_FLOPS_PER_PAIR,
+                             "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes/clock x 2 flop x 2.07 GHz",
+                             "hbm": hbm})
         line = {
             "metric": METRIC,
             "value": replica_throughput(pairs_per_step * args.steps, ms_max / 1e3, world),
@@ -370,13 +393,7 @@ def main():
                                   {"parallelism": f"replicas{world}" if world > 1 else "single",
                                    "bulk_pairs_per_step": bulk_pairs,
                                    "cut_cell_cvs": counts["cvs"], "wall_cells": counts["walls"]}),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": ("k_bulk3" if dim3 else "k_bulk") + " (fused stream + relax + moments)",
-                         "peak_source": f"{peak_kind} HBM copy bandwidth",
-                         "bytes_per_pair": bytes_per_pair,
-                         "bulk_ms_per_launch": avg_bulk_s * 1e3,
-                         "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)},
+            "roofline": roofline,
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -138,6 +138,20 @@ __device__ __forceinline__ T minmod3(T a, T b)
     return fmax(fmin(a, b), fmin(fmax(a, b), T(0)));
 }
 
+// The same for FP64 with integer operations on the bit patterns: the
+// magnitudes of IEEE-754 doubles order as their bits without the sign, and
+// the result is one of the arguments or zero, so it is exact (a zero result
+// may differ in the sign of zero).  The integer pipe is far wider than the
+// FP64 pipe, which on this part carries two lanes per clock per SM.
+__device__ __forceinline__ double minmod3(double a, double b)
+{
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const unsigned long long ma = (unsigned long long)ia & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long mb = (unsigned long long)ib & 0x7FFFFFFFFFFFFFFFull;
+    const long long r = ma <= mb ? ia : ib;
+    return (ia ^ ib) < 0 ? 0.0 : __longlong_as_double(r);
+}
+
 // Three-input minimum (one instruction on sm_100 and later).
 __device__ __forceinline__ float fmin3(float a, float b, float c)
 {
