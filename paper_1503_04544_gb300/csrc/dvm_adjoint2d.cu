@@ -523,6 +523,8 @@ constexpr int kAdjStages = 4;
 constexpr int kAdjLamBytes = 2 * kTileY * kTileX * 16;
 constexpr int kAdjBitsBytes = ((kTileY * kTileX * 4 + 127) / 128) * 128;
 constexpr int kAdjStageBytes = kAdjLamBytes + kAdjBitsBytes;
+static_assert(kAdjLamBytes % 128 == 0 && kAdjStageBytes % 128 == 0,
+              "tensor-copy destinations start on 128-byte boundaries");
 
 // Fast gather for the cells flagged in fast[] (one thread per cell, 32 x
 // kRows cells per block, the velocity groups split over blockIdx.z),

@@ -32,6 +32,10 @@ constexpr int kRows = 8;             // cell rows per block of the bulk kernel
 constexpr int kStages = 4;           // shared-memory stages of the bulk kernel's TMA ring
 constexpr int kTileX = 32 + 4;       // tile width with a two-cell halo on each side
 constexpr int kTileY = kRows + 4;    // tile height with a two-cell halo
+// a stage of both components, 2 x kTileY x kTileX x 16 B, is a multiple of
+// 128 B for any kRows: every stage of the bulk kernel's ring is a
+// tensor-copy destination on a 128-byte boundary
+static_assert((2 * kTileY * kTileX * 16) % 128 == 0, "tensor-copy destinations start on 128-byte boundaries");
 constexpr long kWaitLimit = 1L << 20; // bound of every mbarrier wait (polls)
 
 // cell flag bits

@@ -162,6 +162,9 @@ constexpr int kPlaneX = 32 + 4;                   // tile width plus a two-cell 
 // thread keeps 128 registers; 8 in FP64 (shared memory of the per-cell state).
 template <typename T> __host__ __device__ constexpr int rows3() { return sizeof(T) == 4 ? 12 : 8; }
 template <typename T> __host__ __device__ constexpr int plane_cells3() { return kPlaneX * (rows3<T>() + 4); }
+// Ring slot stride in 16-byte cells: every slot is the destination of a
+// tensor copy and starts on a 128-byte boundary.
+template <typename T> __host__ __device__ constexpr int plane_stride3() { return (plane_cells3<T>() * 16 + 127) / 128 * 8; }
 
 // Velocity tables staged in shared memory by the bulk kernel: all of v_x and
 // up to kVyzStage (v_y, v_z) pairs (more are read from global memory).
@@ -170,7 +173,7 @@ constexpr int kVyzStage = 512;
 template <typename T>
 size_t bulk3_smem()
 {
-    return (size_t)kRing3 * plane_cells3<T>() * 16 + (size_t)kZc3 * (kCoef3 + 10) * 32 * rows3<T>() * sizeof(T) +
+    return (size_t)kRing3 * plane_stride3<T>() * 16 + (size_t)kZc3 * (kCoef3 + 10) * 32 * rows3<T>() * sizeof(T) +
            2 * kRing3 * sizeof(uint64_t) + (size_t)kMaxAxisNv * sizeof(VX3<T>) + (size_t)kVyzStage * sizeof(VYZ3<T>);
 }
 
@@ -222,11 +225,12 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
     k_bulk3(Bulk3Args<T> a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int W = Vec<T>::W, ZC = kZc3, R = rows3<T>(), NT = 32 * R, NP = ZC + 4;
-    constexpr int PC = plane_cells3<T>(), PB = PC * 16;
+    constexpr int PC = plane_stride3<T>(), PB = plane_cells3<T>() * 16;
+    static_assert((PC * 16) % 128 == 0, "tensor-copy destinations start on 128-byte boundaries");
     using V = typename Vec<T>::type;
     extern __shared__ __align__(128) unsigned char sm3[];
     V *ring = reinterpret_cast<V *>(sm3);
-    T *coef = reinterpret_cast<T *>(sm3 + kRing3 * PB);             // [ZC][kCoef3][NT]
+    T *coef = reinterpret_cast<T *>(sm3 + kRing3 * PC * 16);        // [ZC][kCoef3][NT]
     T *ksum = coef + ZC * kCoef3 * NT;                               // [ZC][5][2][NT]
     uint64_t *full = reinterpret_cast<uint64_t *>(ksum + ZC * 10 * NT);
     uint64_t *empty = full + kRing3;
