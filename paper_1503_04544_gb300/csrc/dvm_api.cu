@@ -251,12 +251,12 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
         }
         c->S = S;
     } else {
-        // one resident block per SM (tiles of 32 x 12 cells in FP32, 32 x 8 in
+        // one resident block per SM (tiles of 32 x 11 cells in FP32, 32 x 8 in
         // FP64, columns of 4 cells): the smallest split count giving at least
         // four waves on 152 SMs with a last wave at least 95% full, else the
         // best-filled count up to 24
         const long slots = 152;
-        const int rows = precision == DVM_FP32 ? 12 : 8;
+        const int rows = precision == DVM_FP32 ? 11 : 8;
         const long blocks = (long)((c->nx + 31) / 32) * ((c->ny + rows - 1) / rows) * ((c->nz + 3) / 4);
         int best = 1;
         double best_eff = 0;

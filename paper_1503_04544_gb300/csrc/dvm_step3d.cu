@@ -157,10 +157,12 @@ constexpr int kZc3 = 4;                           // z-planes per block column
 constexpr int kRing3 = 8;                         // shared-memory planes in flight
 constexpr int kPlaneX = 32 + 4;                   // tile width plus a two-cell halo
 
-// Tile rows of the bulk kernel (one consumer warp each): 12 in FP32, so that
-// with the producer warp no SM sub-partition holds more than 4 warps and a
-// thread keeps 128 registers; 8 in FP64 (shared memory of the per-cell state).
-template <typename T> __host__ __device__ constexpr int rows3() { return sizeof(T) == 4 ? 12 : 8; }
+// Tile rows of the bulk kernel (one consumer warp each): 11 in FP32, so that
+// with the producer warp the block's 12 warps put 3 on each SM sub-partition
+// and a thread may hold up to 168 registers (it uses about 160, without
+// spills; 12 rows would cap it at 128); 8 in FP64 (shared memory of the
+// per-cell state).
+template <typename T> __host__ __device__ constexpr int rows3() { return sizeof(T) == 4 ? 11 : 8; }
 template <typename T> __host__ __device__ constexpr int plane_cells3() { return kPlaneX * (rows3<T>() + 4); }
 // Ring slot stride in 16-byte cells: every slot is the destination of a
 // tensor copy and starts on a 128-byte boundary.
