@@ -90,14 +90,24 @@ def read_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_source_hash(kernel_src: str) -> str:
+    """sha256/16 over a kernel's source file and the two headers it includes
+    (the device helpers and the shared constants such as tile and ring sizes)."""
+    import hashlib
+    d = os.path.dirname(kernel_src)
+    h = hashlib.sha256()
+    for f in (kernel_src, os.path.join(d, "dvm_device.cuh"), os.path.join(d, "dvm_internal.h")):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(summary: str, kernel_src: str):
     """DRAM bytes per launch of the bulk kernel from the committed ncu summary,
     or None if the kernel source changed since the capture."""
-    import hashlib
     summ = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(summ):
         return None
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash(kernel_src)
     rec = {}
     for line in open(summ):
         if line.startswith("- ") and ":" in line:

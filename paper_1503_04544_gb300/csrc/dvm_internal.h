@@ -29,7 +29,7 @@ constexpr int kHistCap = 1 << 15;    // steps kept in the force/angle history
 constexpr int kMaxMembers = 16;      // virtual cells per control volume
 constexpr int kMaxAxisNv = 64;       // velocity points per axis
 constexpr int kRows = 8;             // cell rows per block of the bulk kernel
-constexpr int kStages = 4;           // shared-memory stages of the bulk kernel's TMA ring
+constexpr int kStages = 5;           // shared-memory stages of the bulk kernel's TMA ring
 constexpr int kTileX = 32 + 4;       // tile width with a two-cell halo on each side
 constexpr int kTileY = kRows + 4;    // tile height with a two-cell halo
 // a stage of both components, 2 x kTileY x kTileX x 16 B, is a multiple of
