@@ -149,7 +149,8 @@ int dvm_check(dvm_ctx *ctx);
 
 /* Per-cell moments of the current state (Eq. MacroscopicDDv): density,
  * velocity and temperature into host arrays of ncell entries (uz may be NULL
- * in 2D).  Solid cells give 0. */
+ * in 2D).  The velocity sums are compensated in the state precision and the
+ * moments formed from them in FP64.  Solid cells give 0. */
 int dvm_moments(dvm_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *T);
 
 /* Force (F[0..2]) and torque about the z axis exerted by the gas on the body

@@ -122,6 +122,30 @@ template <typename T> struct Acc {
     __device__ __forceinline__ T value() const { return s - c; }
 };
 
+// Velocity chunks of the state-moment kernels (set-up and output): a block
+// holds 32 consecutive cells of a row and kMomChunks warps, one chunk of the
+// velocity groups each.
+constexpr int kMomChunks = 8;
+
+// Merges the compensated sums of the kMomChunks warps of a block into warp 0,
+// chunk by chunk in order (the same result on every run).
+template <typename T, int NM>
+__device__ __forceinline__ void merge_chunks(Acc<T> (&s)[NM])
+{
+    __shared__ T sh[NM][2][kMomChunks][32];
+    const int w = threadIdx.y, l = threadIdx.x;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        sh[m][0][w][l] = s[m].s;
+        sh[m][1][w][l] = s[m].c;
+    }
+    __syncthreads();
+    if (w == 0)
+        for (int k = 1; k < kMomChunks; ++k)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) s[m].merge(sh[m][0][k][l], sh[m][1][k][l]);
+}
+
 // A scalar in the state precision without FP64 arithmetic in FP32 kernels.
 template <typename T>
 __device__ __forceinline__ T pick(float f, double d)

@@ -990,64 +990,86 @@ __global__ void k_advance(BodyDev *b, double dt, int moving)
     b->trig[3] = sin(b->theta1);
 }
 
-// Moment sums of the current state for every cell (warp per cell), written
-// as split 0 of the partials (other splits 0).  Solid cells give zeros.
+// Moment sums of cells (i, j) of one row over a chunk of the velocity
+// groups: f, v_x f, v_y f and |v|^2/2 f + g (Eq. MacroscopicDDv), per group
+// plain over its lanes and compensated across groups.  The lanes of a warp
+// are 32 consecutive cells, so each group's vector of the 32 cells is one
+// coalesced read; warp threadIdx.y takes the threadIdx.y-th of kMomChunks
+// chunks.
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_partials(Grid2D g, int S, const T *f, T *part,
-                                                  const int8_t *type, int *err)
+__device__ __forceinline__ void state_sums2d(const Grid2D &g, const T *f, const VCoef<T> *vt, int i, int j,
+                                             Acc<T> (&s)[4])
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long nc = (long)g.nx * g.ny;
-    const long cell = (long)blockIdx.x * 8 + warp;
-    if (cell >= nc) return;
-    Acc<T> s0, s1, s2, s3;
-    const long pc = pcell(g, cell) * Vec<T>::W;
-    for (int p = lane; p < g.nv; p += 32) {
-        const T vx = T(g.vxmin + (p % g.nvx) * g.dvx), vy = T(g.vymin + (p / g.nvx) * g.dvy);
-        const T fv = f[ebase<T>(g, 0, p) + pc];
-        s0.add(fv); s1.add(vx * fv); s2.add(vy * fv);
-        s3.add(T(0.5) * (vx * vx + vy * vy) * fv);
-        s3.add(f[ebase<T>(g, 1, p) + pc]);
-    }
-    s0.warp_reduce(); s1.warp_reduce(); s2.warp_reduce(); s3.warp_reduce();
-    if (lane == 0) {
-        const bool keep = type[cell] != DVM_SOLID;
-        if (keep) {
-            T rho, ux, uy, tmp;
-            if (!primitives<T>(pick<T>(g.dv_f, g.dv), s0.value(), s1.value(), s2.value(), s3.value(), rho, ux, uy, tmp))
-                atomicExch(&err[kErrNonphys], 1);
+    constexpr int W = Vec<T>::W;
+    using V = typename Vec<T>::type;
+    if (i >= g.nx) return;
+    const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
+    const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+    const long pc = nbr(g, i, j);
+    const V *fv = reinterpret_cast<const V *>(f);
+    for (int q = q0; q < q1; ++q) {
+        T a[W], b[W];
+        vld<T>(fv + (long)q * 2 * g.slab + pc, a);
+        vld<T>(fv + ((long)q * 2 + 1) * g.slab + pc, b);
+        T t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            if (q * W + e >= g.nv) continue;
+            const VCoef<T> c = ld_coef(vt + q * W + e);
+            t0 += a[e];
+            t1 += c.vx * a[e];
+            t2 += c.vy * a[e];
+            t3 += T(0.5) * (c.vx * c.vx + c.vy * c.vy) * a[e] + b[e];
         }
-        write_member_partials<T>(part, S, nc, cell, keep, s0.value(), s1.value(), s2.value(), s3.value());
+        s[0].add(t0); s[1].add(t1); s[2].add(t2); s[3].add(t3);
     }
 }
 
-// FP64 moments for output: rho, ux, uy, uz(=0), T per cell.
+// Partial moment sums of a state (set-up, not the time step): the whole sum
+// goes to split 0, zeros to the others and to solid cells.
 template <typename T>
-__global__ void __launch_bounds__(256) k_moments_out(Grid2D g, const T *f, double *out)
+__global__ void __launch_bounds__(32 * kMomChunks) k_partials(Grid2D g, int S, const T *f, const VCoef<T> *vt,
+                                                              T *part, const int8_t *type, int *err)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long cell = (long)blockIdx.x * 8 + warp;
-    if (cell >= (long)g.nx * g.ny) return;
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    const long pc = pcell(g, cell) * Vec<T>::W;
-    for (int p = lane; p < g.nv; p += 32) {
-        const double vx = g.vxmin + (p % g.nvx) * g.dvx, vy = g.vymin + (p / g.nvx) * g.dvy;
-        const double fv = (double)f[ebase<T>(g, 0, p) + pc];
-        s0 += fv; s1 += vx * fv; s2 += vy * fv;
-        s3 += 0.5 * (vx * vx + vy * vy) * fv + (double)f[ebase<T>(g, 1, p) + pc];
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y;
+    Acc<T> s[4];
+    state_sums2d<T>(g, f, vt, i, j, s);
+    merge_chunks<T, 4>(s);
+    if (threadIdx.y != 0 || i >= g.nx) return;
+    const long nc = (long)g.nx * g.ny, cell = (long)j * g.nx + i;
+    const bool keep = type[cell] != DVM_SOLID;
+    if (keep) {
+        T rho, ux, uy, tmp;
+        if (!primitives<T>(pick<T>(g.dv_f, g.dv), s[0].value(), s[1].value(), s[2].value(), s[3].value(), rho, ux,
+                           uy, tmp))
+            atomicExch(&err[kErrNonphys], 1);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o); s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+    write_member_partials<T>(part, S, nc, cell, keep, s[0].value(), s[1].value(), s[2].value(), s[3].value());
+}
+
+// Moments for output: rho, ux, uy, uz (= 0), T per cell, formed in FP64 from
+// the sums (compensated in the state precision).
+template <typename T>
+__global__ void __launch_bounds__(32 * kMomChunks) k_moments_out(Grid2D g, const T *f, const VCoef<T> *vt,
+                                                                 double *out)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y;
+    Acc<T> s[4];
+    state_sums2d<T>(g, f, vt, i, j, s);
+    merge_chunks<T, 4>(s);
+    if (threadIdx.y != 0 || i >= g.nx) return;
+    double *o5 = out + ((long)j * g.nx + i) * 5;
+    const double s0 = (double)s[0].s - (double)s[0].c, s1 = (double)s[1].s - (double)s[1].c;
+    const double s2 = (double)s[2].s - (double)s[2].c, s3 = (double)s[3].s - (double)s[3].c;
+    const double rho = s0 * g.dv;
+    if (!(rho > 0)) {
+        for (int q = 0; q < 5; ++q) o5[q] = 0;
+        return;
     }
-    if (lane == 0) {
-        double *o5 = out + cell * 5;
-        const double rho = s0 * g.dv;
-        if (!(rho > 0)) { for (int q = 0; q < 5; ++q) o5[q] = 0; return; }
-        const double ux = s1 * g.dv / rho, uy = s2 * g.dv / rho;
-        o5[0] = rho; o5[1] = ux; o5[2] = uy; o5[3] = 0;
-        o5[4] = (2.0 * (s3 * g.dv) / rho - (ux * ux + uy * uy)) / 3.0;
-    }
+    const double ux = s1 * g.dv / rho, uy = s2 * g.dv / rho;
+    o5[0] = rho; o5[1] = ux; o5[2] = uy; o5[3] = 0;
+    o5[4] = (2.0 * (s3 * g.dv) / rho - (ux * ux + uy * uy)) / 3.0;
 }
 
 // Maxwellian state from per-cell primitives (rho, ux, uy, uz, T); solid
@@ -1143,16 +1165,24 @@ __global__ void k_pack(Grid2D g, const T *src, T *dst, int to_dev)
     else dst[t] = src[d];
 }
 
-// Zero the state of every solid cell (they belong to no control volume).
+// Zero the state of every solid cell (they belong to no control volume): one
+// thread per cell and chunk of the velocity groups (blockIdx.y); only the
+// threads of solid cells store, whole group vectors of both components.
 template <typename T>
 __global__ void k_zero_solid(Grid2D g, const int8_t *type, T *f)
 {
-    const long k = blockIdx.x;            // one block per cell, threads over (comp, p)
-    if (type[k] != DVM_SOLID) return;
-    const int e = blockIdx.y * blockDim.x + threadIdx.x;
-    if (e >= 2 * g.nvp) return;
-    const int comp = e >= g.nvp, p = e - comp * g.nvp;
-    f[ebase<T>(g, comp, p) + pcell(g, k) * Vec<T>::W] = T(0);
+    using V = typename Vec<T>::type;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long)g.nx * g.ny || type[k] != DVM_SOLID) return;
+    const int gps = (g.ngrp + gridDim.y - 1) / gridDim.y;
+    const int q0 = blockIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+    const long pc = pcell(g, k);
+    V *fv = reinterpret_cast<V *>(f);
+    const T z[Vec<T>::W] = {};
+    for (int q = q0; q < q1; ++q) {
+        vst<T>(fv + (long)q * 2 * g.slab + pc, z);
+        vst<T>(fv + ((long)q * 2 + 1) * g.slab + pc, z);
+    }
 }
 
 // Per-cell mass sbar * sum_p f dv (FP64), then a fixed-order sum.
@@ -1442,24 +1472,28 @@ cudaError_t tables2d(dvm_ctx *c)
 cudaError_t partials_from_state2d(dvm_ctx *c)
 {
     Grid2D g = grid2d(c);
-    const long nc = (long)c->nx * c->ny;
+    const dim3 grid(nblk(c->nx, 32), c->ny), block(32, kMomChunks);
     if (c->prec == DVM_FP32)
-        k_partials<float><<<nblk(nc, 8), 256, 0, c->stream>>>(g, c->S, (const float *)c->f[c->cur],
-                                                              (float *)c->part[c->cur], c->geo[c->gcur].type, c->d_err);
+        k_partials<float><<<grid, block, 0, c->stream>>>(g, c->S, (const float *)c->f[c->cur],
+                                                         (const VCoef<float> *)c->vtab, (float *)c->part[c->cur],
+                                                         c->geo[c->gcur].type, c->d_err);
     else
-        k_partials<double><<<nblk(nc, 8), 256, 0, c->stream>>>(g, c->S, (const double *)c->f[c->cur],
-                                                               (double *)c->part[c->cur], c->geo[c->gcur].type, c->d_err);
+        k_partials<double><<<grid, block, 0, c->stream>>>(g, c->S, (const double *)c->f[c->cur],
+                                                          (const VCoef<double> *)c->vtab, (double *)c->part[c->cur],
+                                                          c->geo[c->gcur].type, c->d_err);
     return cudaGetLastError();
 }
 
 cudaError_t moments_out2d(dvm_ctx *c, double *d_out)
 {
     Grid2D g = grid2d(c);
-    const long nc = (long)c->nx * c->ny;
+    const dim3 grid(nblk(c->nx, 32), c->ny), block(32, kMomChunks);
     if (c->prec == DVM_FP32)
-        k_moments_out<float><<<nblk(nc, 8), 256, 0, c->stream>>>(g, (const float *)c->f[c->cur], d_out);
+        k_moments_out<float><<<grid, block, 0, c->stream>>>(g, (const float *)c->f[c->cur],
+                                                            (const VCoef<float> *)c->vtab, d_out);
     else
-        k_moments_out<double><<<nblk(nc, 8), 256, 0, c->stream>>>(g, (const double *)c->f[c->cur], d_out);
+        k_moments_out<double><<<grid, block, 0, c->stream>>>(g, (const double *)c->f[c->cur],
+                                                             (const VCoef<double> *)c->vtab, d_out);
     return cudaGetLastError();
 }
 
@@ -1499,7 +1533,7 @@ cudaError_t pack2d(dvm_ctx *c, const void *pub, void *dev)
 cudaError_t zero_solid2d(dvm_ctx *c)
 {
     Grid2D g = grid2d(c);
-    dim3 grid((unsigned)(c->nx * c->ny), nblk(2 * c->nvp, 256));
+    const dim3 grid(nblk((long)c->nx * c->ny, 256), 8);
     for (int b = 0; b < 2; ++b) {
         if (c->prec == DVM_FP32)
             k_zero_solid<float><<<grid, 256, 0, c->stream>>>(g, c->geo[c->gcur].type, (float *)c->f[b]);

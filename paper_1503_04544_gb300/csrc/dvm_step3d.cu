@@ -962,72 +962,100 @@ __global__ void __launch_bounds__(256) k_special3(Cv3Args c, const T *fin, T *fo
 }
 
 // ------------------------------------------------------------ state services
-// Moment sums of the current state for every cell (warp per cell) as split 0
-// of the partials, the other splits 0.
+// Moment sums of cells (i, j, k) of one x-row over a chunk of the velocity
+// groups: F, v_x F, v_y F, v_z F and |v|^2/2 F (Eq. MacroscopicTD), per
+// group plain over its lanes and compensated across groups.  The lanes of a
+// warp are 32 consecutive cells, so each group's vector of the 32 cells is
+// one coalesced read; warp threadIdx.y takes the threadIdx.y-th of
+// kMomChunks chunks.
 template <typename T>
-__global__ void __launch_bounds__(256) k_partials3(Grid3D g, int S, const T *f, T *part, const int8_t *type, int *err)
+__device__ __forceinline__ void state_sums3d(const Grid3D &g, const T *f, const VX3<T> *vxt, const VYZ3<T> *vyz,
+                                             int i, int j, int k, Acc<T> (&s)[5])
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long nc = (long)g.nx * g.ny * g.nz;
-    const long cell = (long)blockIdx.x * 8 + warp;
-    if (cell >= nc) return;
-    Acc<T> s[5];
-    const int pc = pcell3(g, (int)cell);
-    for (int p = lane; p < g.nv; p += 32) {
-        const int p1 = p % g.nvx, r = p / g.nvx;
-        const int p3 = r / g.nvy, p2 = r - p3 * g.nvy;
-        const T vx = T(g.vxmin + p1 * g.dvx), vy = T(g.vymin + p2 * g.dvy), vz = T(g.vzmin + p3 * g.dvz);
-        const T fv = f[pidx3(g, r * g.nvxp + p1, pc)];
-        s[0].add(fv); s[1].add(vx * fv); s[2].add(vy * fv); s[3].add(vz * fv);
-        s[4].add(T(0.5) * (vx * vx + vy * vy + vz * vz) * fv);
-    }
+    constexpr int W = Vec<T>::W;
+    using V = typename Vec<T>::type;
+    if (i >= g.nx) return;
+    const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
+    const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+    if (q0 >= q1) return;
+    const long pc = nbr3(g, i, j, k);
+    const V *fv = reinterpret_cast<const V *>(f);
+    int r = q0 / g.nxg, xg = q0 - r * g.nxg;
+    for (int q = q0; q < q1; ++q) {
+        T a[W];
+        vld<T>(fv + (long)q * g.slab + pc, a);
+        T t0 = 0, t1 = 0, t2 = 0;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) s[m].warp_reduce();
-    if (lane == 0) {
-        const bool keep = type[cell] != DVM_SOLID;
-        T v[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) v[m] = keep ? s[m].value() : T(0);
-        if (keep) {
-            T rho, ux, uy, uz, tmp;
-            if (!primitives3<T>(pick<T>(g.dv_f, g.dv), v, rho, ux, uy, uz, tmp)) atomicExch(&err[kErrNonphys], 1);
+        for (int e = 0; e < W; ++e) {
+            const int p1 = xg * W + e;
+            if (p1 >= g.nvx) continue;
+            const T vx = vxt[p1].vx;
+            t0 += a[e];
+            t1 += vx * a[e];
+            t2 += vx * vx * a[e];
         }
-        for (int q = 0; q < S; ++q)
-#pragma unroll
-            for (int m = 0; m < 5; ++m) part[((long)q * 5 + m) * nc + cell] = q == 0 ? v[m] : T(0);
+        const VYZ3<T> cy = vyz[r];
+        s[0].add(t0);
+        s[1].add(t1);
+        s[2].add(cy.vy * t0);
+        s[3].add(cy.vz * t0);
+        s[4].add(T(0.5) * fma(cy.vy * cy.vy + cy.vz * cy.vz, t0, t2));
+        if (++xg == g.nxg) {
+            xg = 0;
+            ++r;
+        }
     }
 }
 
-// FP64 moments for output: rho, ux, uy, uz, T per cell.
+// Partial moment sums of a state (set-up, not the time step): the whole sum
+// goes to split 0, zeros to the others and to solid cells.
 template <typename T>
-__global__ void __launch_bounds__(256) k_moments_out3(Grid3D g, const T *f, double *out)
+__global__ void __launch_bounds__(32 * kMomChunks) k_partials3(Grid3D g, int S, const T *f, const VX3<T> *vxt,
+                                                               const VYZ3<T> *vyz, T *part, const int8_t *type,
+                                                               int *err)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long cell = (long)blockIdx.x * 8 + warp;
-    if (cell >= (long)g.nx * g.ny * g.nz) return;
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
-    const int pc = pcell3(g, (int)cell);
-    for (int p = lane; p < g.nv; p += 32) {
-        const int p1 = p % g.nvx, r = p / g.nvx;
-        const int p3 = r / g.nvy, p2 = r - p3 * g.nvy;
-        const double vx = g.vxmin + p1 * g.dvx, vy = g.vymin + p2 * g.dvy, vz = g.vzmin + p3 * g.dvz;
-        const double fv = (double)f[pidx3(g, r * g.nvxp + p1, pc)];
-        s0 += fv; s1 += vx * fv; s2 += vy * fv; s3 += vz * fv;
-        s4 += 0.5 * (vx * vx + vy * vy + vz * vz) * fv;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    Acc<T> s[5];
+    state_sums3d<T>(g, f, vxt, vyz, i, j, k, s);
+    merge_chunks<T, 5>(s);
+    if (threadIdx.y != 0 || i >= g.nx) return;
+    const long nc = (long)g.nx * g.ny * g.nz, cell = ((long)k * g.ny + j) * g.nx + i;
+    const bool keep = type[cell] != DVM_SOLID;
+    T v[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) v[m] = keep ? s[m].value() : T(0);
+    if (keep) {
+        T rho, ux, uy, uz, tmp;
+        if (!primitives3<T>(pick<T>(g.dv_f, g.dv), v, rho, ux, uy, uz, tmp)) atomicExch(&err[kErrNonphys], 1);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o); s3 += __shfl_xor_sync(0xffffffffu, s3, o);
-        s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+    for (int q = 0; q < S; ++q)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) part[((long)q * 5 + m) * nc + cell] = q == 0 ? v[m] : T(0);
+}
+
+// Moments for output: rho, ux, uy, uz, T per cell, formed in FP64 from the
+// sums (compensated in the state precision).
+template <typename T>
+__global__ void __launch_bounds__(32 * kMomChunks) k_moments_out3(Grid3D g, const T *f, const VX3<T> *vxt,
+                                                                  const VYZ3<T> *vyz, double *out)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    Acc<T> s[5];
+    state_sums3d<T>(g, f, vxt, vyz, i, j, k, s);
+    merge_chunks<T, 5>(s);
+    if (threadIdx.y != 0 || i >= g.nx) return;
+    double *o5 = out + (((long)k * g.ny + j) * g.nx + i) * 5;
+    double d[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) d[m] = (double)s[m].s - (double)s[m].c;
+    const double rho = d[0] * g.dv;
+    if (!(rho > 0)) {
+        for (int q = 0; q < 5; ++q) o5[q] = 0;
+        return;
     }
-    if (lane == 0) {
-        double *o5 = out + cell * 5;
-        const double rho = s0 * g.dv;
-        if (!(rho > 0)) { for (int q = 0; q < 5; ++q) o5[q] = 0; return; }
-        const double ux = s1 * g.dv / rho, uy = s2 * g.dv / rho, uz = s3 * g.dv / rho;
-        o5[0] = rho; o5[1] = ux; o5[2] = uy; o5[3] = uz;
-        o5[4] = (2.0 * (s4 * g.dv) / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
-    }
+    const double ux = d[1] * g.dv / rho, uy = d[2] * g.dv / rho, uz = d[3] * g.dv / rho;
+    o5[0] = rho; o5[1] = ux; o5[2] = uy; o5[3] = uz;
+    o5[4] = (2.0 * (d[4] * g.dv) / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
 }
 
 __device__ __forceinline__ double maxw3(const double *q, double vx, double vy, double vz)
@@ -1136,14 +1164,20 @@ __global__ void k_pack3(Grid3D g, const T *src, T *dst, int to_dev)
     else dst[t] = src[d];
 }
 
+// Zero the state of every solid cell: one thread per cell and chunk of the
+// velocity groups (blockIdx.y); only the threads of solid cells store.
 template <typename T>
 __global__ void k_zero_solid3(Grid3D g, const int8_t *type, T *f)
 {
-    const int q = blockIdx.x;
-    if (type[q] != DVM_SOLID) return;
-    const int p = blockIdx.y * blockDim.x + threadIdx.x;
-    if (p >= g.nvp) return;
-    f[pidx3(g, p, pcell3(g, q))] = T(0);
+    using V = typename Vec<T>::type;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long)g.nx * g.ny * g.nz || type[k] != DVM_SOLID) return;
+    const int gps = (g.ngrp + gridDim.y - 1) / gridDim.y;
+    const int q0 = blockIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+    const long pc = pcell3(g, (int)k);
+    V *fv = reinterpret_cast<V *>(f);
+    const T z[Vec<T>::W] = {};
+    for (int q = q0; q < q1; ++q) vst<T>(fv + (long)q * g.slab + pc, z);
 }
 
 template <typename T>
@@ -1349,22 +1383,28 @@ cudaError_t tables3d(dvm_ctx *c)
 cudaError_t partials_from_state3d(dvm_ctx *c)
 {
     const Grid3D g = grid3d(c);
+    const dim3 grid(nb3(c->nx, 32), c->ny, c->nz), block(32, kMomChunks);
     if (c->prec == DVM_FP32)
-        k_partials3<float><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, c->S, (const float *)c->f[c->cur],
-                                                                 (float *)c->part[c->cur], c->geo3.type, c->d_err);
+        k_partials3<float><<<grid, block, 0, c->stream>>>(g, c->S, (const float *)c->f[c->cur], vx_table<float>(c),
+                                                          vyz_table<float>(c), (float *)c->part[c->cur], c->geo3.type,
+                                                          c->d_err);
     else
-        k_partials3<double><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, c->S, (const double *)c->f[c->cur],
-                                                                  (double *)c->part[c->cur], c->geo3.type, c->d_err);
+        k_partials3<double><<<grid, block, 0, c->stream>>>(g, c->S, (const double *)c->f[c->cur],
+                                                           vx_table<double>(c), vyz_table<double>(c),
+                                                           (double *)c->part[c->cur], c->geo3.type, c->d_err);
     return cudaGetLastError();
 }
 
 cudaError_t moments_out3d(dvm_ctx *c, double *d_out)
 {
     const Grid3D g = grid3d(c);
+    const dim3 grid(nb3(c->nx, 32), c->ny, c->nz), block(32, kMomChunks);
     if (c->prec == DVM_FP32)
-        k_moments_out3<float><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, (const float *)c->f[c->cur], d_out);
+        k_moments_out3<float><<<grid, block, 0, c->stream>>>(g, (const float *)c->f[c->cur], vx_table<float>(c),
+                                                             vyz_table<float>(c), d_out);
     else
-        k_moments_out3<double><<<nb3(c->nc, 8), 256, 0, c->stream>>>(g, (const double *)c->f[c->cur], d_out);
+        k_moments_out3<double><<<grid, block, 0, c->stream>>>(g, (const double *)c->f[c->cur], vx_table<double>(c),
+                                                              vyz_table<double>(c), d_out);
     return cudaGetLastError();
 }
 
@@ -1411,7 +1451,7 @@ cudaError_t unpack3d(dvm_ctx *c, const void *dev, void *pub)
 cudaError_t zero_solid3d(dvm_ctx *c)
 {
     const Grid3D g = grid3d(c);
-    dim3 grid((unsigned)c->nc, nb3(c->nvp, 256));
+    const dim3 grid(nb3(c->nc, 256), 8);
     for (int b = 0; b < 2; ++b) {
         if (c->prec == DVM_FP32) k_zero_solid3<float><<<grid, 256, 0, c->stream>>>(g, c->geo3.type, (float *)c->f[b]);
         else k_zero_solid3<double><<<grid, 256, 0, c->stream>>>(g, c->geo3.type, (double *)c->f[b]);
