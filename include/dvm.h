@@ -143,9 +143,20 @@ int dvm_get_state(dvm_ctx *ctx, void *f, size_t bytes, int on_device);
 int dvm_step(dvm_ctx *ctx, int nsteps);
 
 /* Same as dvm_step but without the final synchronisation and flag check
- * (for timing and graph capture); dvm_check() reads the flags later. */
+ * (for timing and graph capture); dvm_check() reads the flags later.
+ * From 8 steps on, with per-launch timing (dvm_timing) off, the steps after
+ * the first of the call (and the first after a state change) go to the
+ * device as replays of a CUDA graph of two steps captured on the context's
+ * stream: the same kernels in the same order, so the state is bitwise that
+ * of launch-by-launch stepping.  If the stream cannot be captured (the legacy
+ * default stream, or a capture already in progress) the call steps launch by
+ * launch. */
 int dvm_step_async(dvm_ctx *ctx, int nsteps);
 int dvm_check(dvm_ctx *ctx);
+
+/* Switch the two-step graph replays of dvm_step / dvm_step_async on
+ * (enable != 0, the default) or off.  Errors: DVM_ERR_ARG for a null ctx. */
+int dvm_graphs(dvm_ctx *ctx, int enable);
 
 /* Per-cell moments of the current state (Eq. MacroscopicDDv): density,
  * velocity and temperature into host arrays of ncell entries (uz may be NULL

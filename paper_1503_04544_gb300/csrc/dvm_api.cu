@@ -134,10 +134,21 @@ static void free_geo3(dvm::Geo3D &G)
     std::memset(&G, 0, sizeof(G));
 }
 
+// Executable graphs of finished dvm_step calls, destroyed once the stream has
+// been synchronised (their launches have completed).
+static void destroy_retired(dvm_ctx *c)
+{
+    auto *v = static_cast<std::vector<cudaGraphExec_t> *>(c->gretired);
+    if (!v) return;
+    for (cudaGraphExec_t x : *v) cudaGraphExecDestroy(x);
+    v->clear();
+}
+
 static int check_flags(dvm_ctx *c)
 {
     CK(cudaMemcpyAsync(c->h_err, c->d_err, kErrCount * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    destroy_retired(c);
     int rc = DVM_OK;
     if (c->h_err[kErrGeometry]) { set_error("geometry: saddle cell or master search left its bounds"); rc = DVM_ERR_GEOMETRY; }
     else if (c->h_err[kErrCapacity]) { set_error("geometry: control-volume list or member capacity exceeded"); rc = DVM_ERR_GEOMETRY; }
@@ -160,6 +171,52 @@ static cudaError_t st_partials(dvm_ctx *c) { return c->dim == 2 ? partials_from_
 static cudaError_t st_pack(dvm_ctx *c, const void *pub, void *dev) { return c->dim == 2 ? pack2d(c, pub, dev) : pack3d(c, pub, dev); }
 static cudaError_t st_unpack(dvm_ctx *c, const void *dev, void *pub) { return c->dim == 2 ? unpack2d(c, dev, pub) : unpack3d(c, dev, pub); }
 static cudaError_t st_step(dvm_ctx *c) { return c->dim == 2 ? step2d(c) : step3d(c); }
+
+constexpr int kGraphMinSteps = 8;    // shorter runs are not worth a capture
+
+// `pairs` replays of a captured pair of steps.  A step writes the other state
+// buffer (and, for a moving body, the other geometry level), so two steps
+// leave the context's buffers as they found them and the pair replays as it
+// is: one graph launch per two steps in place of their kernel launches and
+// the gaps between them.  The capture advances the host bookkeeping of two
+// steps that have not run (step and launch counts); it is put back and
+// advanced per replay.  *done is the number of steps enqueued: 0 when the
+// stream cannot be captured, the caller then steps launch by launch.
+static cudaError_t graph_steps(dvm_ctx *c, int pairs, int *done)
+{
+    *done = 0;
+    const long long steps0 = c->steps_done, launches0 = c->launches;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    cudaError_t es = st_step(c);
+    if (es == cudaSuccess) es = st_step(c);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+    const long long dl = c->launches - launches0;
+    c->steps_done = steps0;
+    c->launches = launches0;
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = es == cudaSuccess && ee == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        // not capturable here: nothing was enqueued, step launch by launch
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    // destroyed once the stream has been synchronised
+    static_cast<std::vector<cudaGraphExec_t> *>(c->gretired)->push_back(exec);
+    for (int r = 0; r < pairs; ++r) {
+        const cudaError_t e = cudaGraphLaunch(exec, c->stream);
+        if (e != cudaSuccess) return e;
+        c->steps_done += 2;
+        c->launches += dl;
+        *done += 2;
+    }
+    return cudaSuccess;
+}
 static cudaError_t st_moments(dvm_ctx *c, double *d) { return c->dim == 2 ? moments_out2d(c, d) : moments_out3d(c, d); }
 static cudaError_t st_mass(dvm_ctx *c, double *s, double *d) { return c->dim == 2 ? mass2d(c, s, d) : mass3d(c, s, d); }
 static cudaError_t st_init(dvm_ctx *c, const double *d) { return c->dim == 2 ? init_maxwellian2d(c, d) : init_maxwellian3d(c, d); }
@@ -355,7 +412,9 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     if (e != cudaSuccess) { int rc = cuda_fail(e, "dvm_create init"); dvm_destroy(c); return rc; }
     c->have_geo = true;
     c->ev_pool = new (std::nothrow) std::vector<cudaEvent_t>();
-    if (!c->ev_pool) { dvm_destroy(c); set_error("host allocation"); return DVM_ERR_OOM; }
+    c->gretired = new (std::nothrow) std::vector<cudaGraphExec_t>();
+    c->graphs = true;
+    if (!c->ev_pool || !c->gretired) { dvm_destroy(c); set_error("host allocation"); return DVM_ERR_OOM; }
     *out = c;
     return DVM_OK;
 }
@@ -380,6 +439,10 @@ void dvm_destroy(dvm_ctx *c)
     cudaFree(c->d_prim0);
     free_adjoint2d(c);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->gretired) {
+        destroy_retired(c);
+        delete static_cast<std::vector<cudaGraphExec_t> *>(c->gretired);
+    }
     if (c->ev_pool) {
         auto *pool = static_cast<std::vector<cudaEvent_t> *>(c->ev_pool);
         for (cudaEvent_t e : *pool) cudaEventDestroy(e);
@@ -622,10 +685,32 @@ int dvm_step_async(dvm_ctx *c, int nsteps)
         }
     if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return DVM_ERR_ARG; }
-    for (int s = 0; s < nsteps; ++s) {
+    int s = 0;
+    // the first step after a state change (control-volume fusion), short runs
+    // and runs with per-launch timing go launch by launch; the rest as
+    // replays of a two-step graph (timing marks inside a graph, as event-record
+    // nodes, cost about 1 % of the step)
+    for (; s < nsteps && (s == 0 || c->need_fusion); ++s) {
         cudaError_t e = st_step(c);
         if (e != cudaSuccess) return cuda_fail(e, "dvm_step");
     }
+    if (c->graphs && !c->timing && !c->rec_bits && nsteps - s >= kGraphMinSteps) {
+        int done = 0;
+        cudaError_t e = graph_steps(c, (nsteps - s) / 2, &done);
+        if (e != cudaSuccess) return cuda_fail(e, "dvm_step (graph)");
+        s += done;
+    }
+    for (; s < nsteps; ++s) {
+        cudaError_t e = st_step(c);
+        if (e != cudaSuccess) return cuda_fail(e, "dvm_step");
+    }
+    return DVM_OK;
+}
+
+int dvm_graphs(dvm_ctx *c, int enable)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    c->graphs = enable != 0;
     return DVM_OK;
 }
 

@@ -181,6 +181,8 @@ struct dvm_ctx {
     bool timing;
     void *ev_pool;                // std::vector<cudaEvent_t> of start/stop pairs
     int ev_used;
+    bool graphs;                  // dvm_step replays two-step CUDA graphs (dvm_graphs)
+    void *gretired;               // std::vector<cudaGraphExec_t> launched, destroyed once the stream is idle
     long long launches;
 };
 

@@ -74,6 +74,7 @@ SIGNATURES = {
     "dvm_get_state": [_P, _P, C.c_size_t, C.c_int],
     "dvm_step": [_P, C.c_int],
     "dvm_step_async": [_P, C.c_int],
+    "dvm_graphs": [_P, C.c_int],
     "dvm_check": [_P],
     "dvm_moments": [_P, _PD, _PD, _PD, _PD, _PD],
     "dvm_wall_force": [_P, _PD, _PD],
@@ -213,6 +214,10 @@ class Solver:
 
     def step_async(self, n: int = 1):
         _check(load().dvm_step_async(self.h, int(n)))
+
+    def graphs(self, enable: bool = True):
+        """Two-step CUDA graph replays in step / step_async (on by default)."""
+        _check(load().dvm_graphs(self.h, int(bool(enable))))
 
     def check(self):
         _check(load().dvm_check(self.h))
