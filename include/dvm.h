@@ -150,7 +150,8 @@ int dvm_step(dvm_ctx *ctx, int nsteps);
  * stream: the same kernels in the same order, so the state is bitwise that
  * of launch-by-launch stepping.  If the stream cannot be captured (the legacy
  * default stream, or a capture already in progress) the call steps launch by
- * launch. */
+ * launch.  The graphs are released at the next dvm_check / dvm_step; a call
+ * that finds 64 of them unreleased waits for the stream once to release them. */
 int dvm_step_async(dvm_ctx *ctx, int nsteps);
 int dvm_check(dvm_ctx *ctx);
 

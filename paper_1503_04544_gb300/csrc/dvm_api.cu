@@ -173,6 +173,7 @@ static cudaError_t st_unpack(dvm_ctx *c, const void *dev, void *pub) { return c-
 static cudaError_t st_step(dvm_ctx *c) { return c->dim == 2 ? step2d(c) : step3d(c); }
 
 constexpr int kGraphMinSteps = 8;    // shorter runs are not worth a capture
+constexpr size_t kGraphKeep = 64;    // launched graphs kept before a release
 
 // `pairs` replays of a captured pair of steps.  A step writes the other state
 // buffer (and, for a moving body, the other geometry level), so two steps
@@ -185,6 +186,13 @@ constexpr int kGraphMinSteps = 8;    // shorter runs are not worth a capture
 static cudaError_t graph_steps(dvm_ctx *c, int pairs, int *done)
 {
     *done = 0;
+    // a caller that never checks the flags would keep every launched graph:
+    // past kGraphKeep of them, wait for the stream once and release them
+    if (static_cast<std::vector<cudaGraphExec_t> *>(c->gretired)->size() >= kGraphKeep) {
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return e;
+        destroy_retired(c);
+    }
     const long long steps0 = c->steps_done, launches0 = c->launches;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();

@@ -74,3 +74,20 @@ def test_graph_timing_marks():
     assert n == 31
     assert ms > 0
     s.close()
+
+
+def test_graph_many_async_calls():
+    """70 unchecked dvm_step_async calls of 10 steps each (one step launch by
+    launch, four replays of the two-step graph, one more step) pass the point
+    where the launched graphs are released with one wait; the state still
+    agrees bit for bit with 700 steps launch by launch."""
+    cfg = W.cylinder_mach2(nx=32, nv=16)
+    s = dvm.Solver(cfg, dvm.FP32)
+    s.init_maxwellian()
+    for _ in range(70):
+        s.step_async(10)
+    s.check()
+    F = s.get_state()
+    s.close()
+    ref = run(cfg, dvm.FP32, 700, graphs=False)
+    assert np.array_equal(F, ref["F"])
