@@ -55,7 +55,7 @@ class _Cfg(C.Structure):
         ("vbx", C.c_double), ("vby", C.c_double), ("mass", C.c_double), ("inertia", C.c_double),
         ("movable", C.c_int), ("Tw", C.c_double), ("nseg", C.c_int),
         ("Tw_seg", C.POINTER(C.c_double)), ("seg_dir", C.POINTER(C.c_double)),
-        ("axis", C.c_int),
+        ("axis", C.c_int), ("time_scheme", C.c_int),
     ]
 
 
@@ -142,6 +142,7 @@ class _CfgHolder:
             s.Tw_seg = _ptr(tw)
             s.seg_dir = _ptr(sd)
         s.axis = int(cfg.get("axis", 2))
+        s.time_scheme = int(cfg.get("time_scheme", 0))   # 0 explicit, 1 semi-implicit (Eq. ImpSchemeDD)
         self.s = s
         self.cfg = cfg
 

@@ -7,7 +7,9 @@
  * 2D path: reduced (f, g) BGK model (Sec. 2.2, Eq. BGKDD), explicit
  * first-order scheme on control volumes (Eq. ExSchemeDD) with upwind fluxes
  * (Eq. FluxDD), discrete diffuse reflection (Eq. BoundaryDDv), the 7-step
- * iteration of Sec. 3.3.5 and the Appendix A geometry.
+ * iteration of Sec. 3.3.5 and the Appendix A geometry.  With
+ * time_scheme = ORC_IMEX the update is the first-order semi-implicit scheme
+ * (Eq. ImpSchemeDD) instead, in 2D and 3D.
  */
 #include "dvm_oracle.h"
 #include <math.h>
@@ -301,6 +303,42 @@ typedef struct {
 
 /* Periodic image of index a on an axis of n cells (any a, also when the
  * stencil reaches further than n cells). */
+/* Implicit relaxation of the first-order semi-implicit scheme (Eq.
+ * ImpSchemeDD) on the transported values fk of one control volume (the first
+ * two terms of the scheme).  Summing the scheme over the velocities makes the
+ * collision term vanish, so rho, u and T at t^{n+1} are the moments of the
+ * transported values; with them f^{n+1} = (f_T + nu M) / (1 + nu), where
+ * nu = dt / tau^{n+1} = dt rho^{n+1} / tau0 and M is the Maxwellian of
+ * Eq. BGKDD (2D: g_T relaxes towards T/2 M).  reading: the discrete moments of
+ * M are taken equal to rho, u, T, as for the direct moments of the explicit
+ * scheme. */
+static int imex_relax(const orc_cfg *c, double dt, double tau0, double *fk)
+{
+    double rho, u[3], T;
+    if (cell_moments(c, fk, &rho, u, &T)) return ORC_ERR_NONPHYSICAL;
+    const double nu = dt * rho / tau0;
+    const int nv1 = c->nvx, nv2 = c->nvy, nv3 = c->dim == 3 ? c->nvz : 1;
+    const int nv = nv1 * nv2 * nv3;
+    const double dvx = (c->vxmax - c->vxmin) / nv1, dvy = (c->vymax - c->vymin) / nv2;
+    const double dvz = c->dim == 3 ? (c->vzmax - c->vzmin) / nv3 : 1.0;
+    for (int p3 = 0; p3 < nv3; ++p3)
+        for (int p2 = 0; p2 < nv2; ++p2)
+            for (int p1 = 0; p1 < nv1; ++p1) {
+                int p = (p3 * nv2 + p2) * nv1 + p1;
+                double vx = c->vxmin + p1 * dvx, vy = c->vymin + p2 * dvy;
+                if (c->dim == 3) {
+                    double vz = c->vzmin + p3 * dvz;
+                    double M = maxw3d(rho, u[0], u[1], u[2], T, vx, vy, vz);
+                    fk[p] = (fk[p] + nu * M) / (1.0 + nu);
+                } else {
+                    double M = maxw2d(rho, u[0], u[1], T, vx, vy);
+                    fk[p] = (fk[p] + nu * M) / (1.0 + nu);
+                    fk[nv + p] = (fk[nv + p] + nu * (T / 2.0 * M)) / (1.0 + nu);
+                }
+            }
+    return ORC_OK;
+}
+
 static int wrap(int a, int n)
 {
     a %= n;
@@ -568,9 +606,10 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
             wphi[k] = phi; wux[k] = uwx; wuy[k] = uwy; wT[k] = Tw;
         }
         double omega1 = moving ? omega + dt * Tq / c->inertia : omega;   /* Eq. motionDD_vit */
-        /* Step 6: explicit scheme (Eq. ExSchemeDD) on every control volume. */
-        int badcv = 0;
-        #pragma omp parallel reduction(|:badcv)
+        /* Step 6: explicit scheme (Eq. ExSchemeDD), or the first-order
+         * semi-implicit one (Eq. ImpSchemeDD), on every control volume. */
+        int badcv = 0, badrelax = 0;
+        #pragma omp parallel reduction(|:badcv, badrelax)
         {
             double *R = malloc(sizeof(double) * 2 * nv);
             #pragma omp for schedule(dynamic, 16)
@@ -627,6 +666,13 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
                 }
                 double tau = tau0 / mrho[m];
                 double a = Sn[m] / Sp[m], b = dt / Sp[m], r = dt / tau;
+                if (c->time_scheme == ORC_IMEX) {
+                    for (int comp = 0; comp < 2; ++comp)
+                        for (int p = 0; p < nv; ++p)
+                            Fnew[(m * 2 + comp) * nv + p] = a * F[(m * 2 + comp) * nv + p] - b * R[comp * nv + p];
+                    if (imex_relax(c, dt, tau0, Fnew + m * 2 * nv)) badrelax = 1;
+                    continue;
+                }
                 for (int comp = 0; comp < 2; ++comp)
                     for (int p2 = 0; p2 < X.nv2; ++p2)
                         for (int p1 = 0; p1 < X.nv1; ++p1) {
@@ -640,6 +686,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
             free(R);
         }
         if (badcv) { err = ORC_ERR_GEOMETRY; break; }
+        if (badrelax) { err = ORC_ERR_NONPHYSICAL; break; }
         /* Step 7: distribution (Eq. UpdateDD).  reading: cells that are
          * solid at t^{n+1} hold zero. */
         #pragma omp parallel for
@@ -1042,8 +1089,9 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
             Tq += rx * fk3[1] - ry * fk3[0];
             wphi[q] = phi; wu[3 * q] = uw[0]; wu[3 * q + 1] = uw[1]; wu[3 * q + 2] = uw[2]; wT[q] = Tw;
         }
-        /* explicit scheme (Eq. eq-schema3D) */
-        #pragma omp parallel
+        /* explicit scheme (Eq. eq-schema3D), or the semi-implicit one */
+        int badrelax3 = 0;
+        #pragma omp parallel reduction(|:badrelax3)
         {
             double *R = malloc(sizeof(double) * nv);
             #pragma omp for schedule(dynamic, 16)
@@ -1095,6 +1143,12 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
                 }
                 double tau = tau0 / mr[m];
                 double a = 1.0, b = dt / S[m], r = dt / tau;   /* fixed body: V^n = V^{n+1,*} */
+                if (c->time_scheme == ORC_IMEX) {
+                    /* the semi-implicit scheme (Eq. ImpSchemeDD) in 3D */
+                    for (int p = 0; p < nv; ++p) Fnew[m * nv + p] = a * F[m * nv + p] - b * R[p];
+                    if (imex_relax(c, dt, tau0, Fnew + m * nv)) badrelax3 = 1;
+                    continue;
+                }
                 for (int p3 = 0; p3 < X.nv3; ++p3)
                     for (int p2 = 0; p2 < X.nv2; ++p2)
                         for (int p1 = 0; p1 < X.nv1; ++p1) {
@@ -1106,6 +1160,7 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
             }
             free(R);
         }
+        if (badrelax3) { err = ORC_ERR_NONPHYSICAL; break; }
         #pragma omp parallel for
         for (long q = 0; q < nc; ++q) {
             int m = master[q];

@@ -28,6 +28,7 @@ enum { ORC_BC_PERIODIC = 0, ORC_BC_MAXWELLIAN = 1, ORC_BC_ZEROGRAD = 2 };
 enum { ORC_SHAPE_NONE = 0, ORC_SHAPE_CIRCLE = 1, ORC_SHAPE_ELLIPSE = 2,
        ORC_SHAPE_SPHERE = 3 };
 enum { ORC_UPWIND = 0, ORC_MUSCL = 1 };
+enum { ORC_EXPLICIT = 0, ORC_IMEX = 1 };  /* Eq. ExSchemeDD | Eq. ImpSchemeDD */
 
 /* Problem statement.  2D uses the x/y fields, 3D also the z ones. */
 typedef struct {
@@ -57,6 +58,8 @@ typedef struct {
     const double *seg_dir;         /* [2*nseg] sector boundary directions */
     int axis;                      /* 3D circle: axis of the infinite cylinder
                                       (0 x, 1 y, 2 z) */
+    int time_scheme;               /* ORC_EXPLICIT (Eq. ExSchemeDD) or ORC_IMEX
+                                      (first-order semi-implicit, Eq. ImpSchemeDD) */
 } orc_cfg;
 
 /* Geometry of one time level (2D): every array is caller-owned.          */
