@@ -51,6 +51,7 @@ typedef enum {
 
 enum { DVM_FP32 = 32, DVM_FP64 = 64 };
 enum { DVM_UPWIND = 0, DVM_MUSCL = 1 };
+enum { DVM_EXPLICIT = 0, DVM_IMEX = 1 };   /* time schemes, see dvm_set_time_scheme */
 enum { DVM_BC_PERIODIC = 0, DVM_BC_MAXWELLIAN = 1, DVM_BC_ZEROGRAD = 2 };
 enum { DVM_SHAPE_NONE = 0, DVM_SHAPE_CIRCLE = 1, DVM_SHAPE_ELLIPSE = 2, DVM_SHAPE_SPHERE = 3 };
 enum { DVM_GAS = 0, DVM_CUT = 1, DVM_SOLID = 2 };
@@ -119,6 +120,15 @@ void dvm_destroy(dvm_ctx *ctx);
  * sides; 3D: row-major over the two remaining axes).  Opposite sides must
  * both be periodic or both not.  Errors: DVM_ERR_ARG. */
 int dvm_set_bc(dvm_ctx *ctx, int side, int kind, const double *state);
+
+/* Time scheme of dvm_step (Sec. 3.3): DVM_EXPLICIT, the first-order explicit
+ * scheme (Eq. ExSchemeDD, the default; 3D Eq. eq-schema3D), or DVM_IMEX, the
+ * first-order semi-implicit scheme (Eq. ImpSchemeDD): explicit transport,
+ * then an implicit relaxation towards the Maxwellian of the moments at
+ * t^{n+1} (the moments of the transported values), which lifts the dt < tau
+ * limit of the explicit scheme at small Knudsen numbers.  The drag adjoint
+ * differentiates the explicit scheme only.  Errors: DVM_ERR_ARG. */
+int dvm_set_time_scheme(dvm_ctx *ctx, int scheme);
 
 /* Place the obstacle and build the Appendix A geometry on the device (level
  * set, cell types, edge lengths, wall edges, areas, control volumes).

@@ -715,6 +715,14 @@ int dvm_step_async(dvm_ctx *c, int nsteps)
     return DVM_OK;
 }
 
+int dvm_set_time_scheme(dvm_ctx *c, int scheme)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (scheme != DVM_EXPLICIT && scheme != DVM_IMEX) { set_error("time scheme must be DVM_EXPLICIT or DVM_IMEX"); return DVM_ERR_ARG; }
+    c->time_scheme = scheme;
+    return DVM_OK;
+}
+
 int dvm_graphs(dvm_ctx *c, int enable)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
@@ -880,6 +888,10 @@ int dvm_drag_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, double *J, do
 {
     if (!c || !J || !gTw) { set_error("null argument"); return DVM_ERR_ARG; }
     if (c->dim != 2) { set_error("dvm_drag_adjoint: 2D contexts only"); return DVM_ERR_UNSUPPORTED; }
+    if (c->time_scheme != DVM_EXPLICIT) {
+        set_error("dvm_drag_adjoint: the explicit time scheme only");
+        return DVM_ERR_UNSUPPORTED;
+    }
     if (c->body.shape == DVM_SHAPE_NONE || c->moving) {
         set_error("dvm_drag_adjoint: needs a fixed obstacle"); return DVM_ERR_UNSUPPORTED;
     }

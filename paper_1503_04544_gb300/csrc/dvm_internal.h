@@ -182,6 +182,7 @@ struct dvm_ctx {
     void *ev_pool;                // std::vector<cudaEvent_t> of start/stop pairs
     int ev_used;
     bool graphs;                  // dvm_step replays two-step CUDA graphs (dvm_graphs)
+    int time_scheme;              // DVM_EXPLICIT or DVM_IMEX (dvm_set_time_scheme)
     void *gretired;               // std::vector<cudaGraphExec_t> launched, destroyed once the stream is idle
     long long launches;
 };

@@ -1072,6 +1072,78 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_moments_out(Grid2D g, const
     o5[4] = (2.0 * (s3 * g.dv) / rho - (ux * ux + uy * uy)) / 3.0;
 }
 
+// Implicit relaxation of the first-order semi-implicit scheme (Eq.
+// ImpSchemeDD), after a transport pass that ran without relaxation: the
+// moments at t^{n+1} are those of the transported values (the collision term
+// sums to zero over the velocities), read from the partial sums the transport
+// kernels wrote.  Every gas cell relaxes towards their Maxwellian,
+// f = (f* + nu M) / (1 + nu) and g = (g* + nu T/2 M) / (1 + nu) with
+// nu = dt / tau^{n+1} = (dt / tau0) rho, in place and in its padding mirrors,
+// and the partial sums become those of the relaxed state (split 0; zeros in
+// the others).  Cells solid at t^{n+1} (type) keep their zero state.
+// Block = 32 consecutive cells of a row x kMomChunks warps, one chunk of the
+// velocity groups each.
+template <typename T>
+__global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_tau0, T *f, const VCoef<T> *vt,
+                                                          T *part, const int8_t *type, int *err)
+{
+    constexpr int W = Vec<T>::W;
+    using V = typename Vec<T>::type;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y;
+    const long nc = (long)g.nx * g.ny, cell = (long)j * g.nx + i;
+    bool gas = i < g.nx && type[cell] != DVM_SOLID;
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    if (gas) gather_partials(part, S, nc, cell, s);
+    T rho = 0, ux = 0, uy = 0, tmp = 0;
+    if (gas && !primitives<T>(pick<T>(g.dv_f, g.dv), s[0], s[1], s[2], s[3], rho, ux, uy, tmp)) {
+        if (threadIdx.y == 0) atomicExch(&err[kErrNonphys], 1);
+        gas = false;
+    }
+    Acc<T> a4[4];
+    if (gas) {
+        const T A = rho / (T(2.0 * kPi) * tmp), c2 = T(kLog2e) / (T(2) * tmp);
+        const T nu = dt_tau0 * rho, inv = T(1) / (T(1) + nu), half = tmp / T(2);
+        const long pc = nbr(g, i, j);
+        long mir[4];
+        mirrors(g, i, j, mir);
+        V *fv = reinterpret_cast<V *>(f);
+        const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
+        const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+        for (int q = q0; q < q1; ++q) {
+            V *pa = fv + (long)q * 2 * g.slab, *pb = pa + g.slab;
+            T a[W], b[W];
+            vld<T>(pa + pc, a);
+            vld<T>(pb + pc, b);
+            T t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                if (q * W + e >= g.nv) continue;
+                const VCoef<T> c = ld_coef(vt + q * W + e);
+                const T dx = c.vx - ux, dy = c.vy - uy;
+                const T M = A * dexp2(-(dx * dx + dy * dy) * c2);
+                a[e] = (a[e] + nu * M) * inv;
+                b[e] = (b[e] + nu * half * M) * inv;
+                t0 += a[e];
+                t1 += c.vx * a[e];
+                t2 += c.vy * a[e];
+                t3 += T(0.5) * (c.vx * c.vx + c.vy * c.vy) * a[e] + b[e];
+            }
+            vst<T>(pa + pc, a);
+            vst<T>(pb + pc, b);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (mir[k] >= 0) {
+                    vst<T>(pa + mir[k], a);
+                    vst<T>(pb + mir[k], b);
+                }
+            a4[0].add(t0); a4[1].add(t1); a4[2].add(t2); a4[3].add(t3);
+        }
+    }
+    merge_chunks<T, 4>(a4);
+    if (threadIdx.y != 0 || i >= g.nx) return;
+    write_member_partials<T>(part, S, nc, cell, gas, a4[0].value(), a4[1].value(), a4[2].value(), a4[3].value());
+}
+
 // Maxwellian state from per-cell primitives (rho, ux, uy, uz, T); solid
 // cells get 0 (Eq. BGKDD for g).
 template <typename T>
@@ -1282,6 +1354,13 @@ template <typename T>
 cudaError_t step2d_t(dvm_ctx *c)
 {
     Grid2D g = grid2d(c);
+    // the semi-implicit scheme (Eq. ImpSchemeDD) transports without
+    // relaxation here; k_imex relaxes at the end of the step
+    const bool imex = c->time_scheme == DVM_IMEX;
+    if (imex) {
+        g.dt_tau0 = 0.0;
+        g.dt_tau0_f = 0.f;
+    }
     BodyParams bp = body_params(c);
     const bool body = c->body.shape != DVM_SHAPE_NONE;
     const bool moving = c->moving;
@@ -1338,6 +1417,13 @@ cudaError_t step2d_t(dvm_ctx *c)
         if ((e = cudaEventRecord(c->ev_wjoin, c->wstream)) != cudaSuccess) return e;
         // the step ends when both streams are done
         if ((e = cudaStreamWaitEvent(c->stream, c->ev_wjoin, 0)) != cudaSuccess) return e;
+        c->launches += 1;
+    }
+    if (imex) {
+        const dim3 grid(nblk(c->nx, 32), c->ny), block(32, kMomChunks);
+        const int8_t *type1 = c->geo[moving ? 1 - c->gcur : c->gcur].type;    // cell types at t^{n+1}
+        k_imex<T><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, (const VCoef<T> *)c->vtab,
+                                                 pout, type1, c->d_err);
         c->launches += 1;
     }
     c->cur = 1 - c->cur;

@@ -1058,6 +1058,80 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_moments_out3(Grid3D g, cons
     o5[4] = (2.0 * (d[4] * g.dv) / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
 }
 
+// Implicit relaxation of the semi-implicit scheme (Eq. ImpSchemeDD) in 3D,
+// after a transport pass without relaxation: every gas cell relaxes towards
+// the Maxwellian of the moments of its transported values (the partial sums),
+// F = (F* + nu M) / (1 + nu) with nu = (dt / tau0) rho, in place and in its
+// padding mirrors; the partial sums become those of the relaxed state.
+// Block = 32 consecutive cells of an x-row x kMomChunks warps, one chunk of
+// the velocity groups each.
+template <typename T>
+__global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt_tau0, T *f, const VX3<T> *vxt,
+                                                           const VYZ3<T> *vyz, T *part, const int8_t *type, int *err)
+{
+    constexpr int W = Vec<T>::W;
+    using V = typename Vec<T>::type;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const long nc = (long)g.nx * g.ny * g.nz, cell = ((long)k * g.ny + j) * g.nx + i;
+    bool gas = i < g.nx && type[cell] != DVM_SOLID;
+    T s[5] = {T(0), T(0), T(0), T(0), T(0)};
+    if (gas) gather_partials3(part, S, nc, cell, s);
+    T rho = 0, ux = 0, uy = 0, uz = 0, tmp = 0;
+    if (gas && !primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp)) {
+        if (threadIdx.y == 0) atomicExch(&err[kErrNonphys], 1);
+        gas = false;
+    }
+    Acc<T> a5[5];
+    const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
+    const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+    if (gas && q0 < q1) {
+        const T A = rho * norm3(tmp), c2 = T(kLog2e) / (T(2) * tmp);
+        const T nu = dt_tau0 * rho, inv = T(1) / (T(1) + nu);
+        const long pc = nbr3(g, i, j, k);
+        int mir[6];
+        mirrors3(g, i, j, k, mir);
+        V *fv = reinterpret_cast<V *>(f);
+        int r = q0 / g.nxg, xg = q0 - r * g.nxg;
+        for (int q = q0; q < q1; ++q) {
+            V *pa = fv + (long)q * g.slab;
+            T a[W];
+            vld<T>(pa + pc, a);
+            const VYZ3<T> cy = vyz[r];
+            const T dyz = (cy.vy - uy) * (cy.vy - uy) + (cy.vz - uz) * (cy.vz - uz);
+            T t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const int p1 = xg * W + e;
+                if (p1 >= g.nvx) continue;
+                const T vx = vxt[p1].vx, dx = vx - ux;
+                const T M = A * dexp2(-(dx * dx + dyz) * c2);
+                a[e] = (a[e] + nu * M) * inv;
+                t0 += a[e];
+                t1 += vx * a[e];
+                t2 += vx * vx * a[e];
+            }
+            vst<T>(pa + pc, a);
+#pragma unroll
+            for (int m = 0; m < 6; ++m)
+                if (mir[m] >= 0) vst<T>(pa + mir[m], a);
+            a5[0].add(t0);
+            a5[1].add(t1);
+            a5[2].add(cy.vy * t0);
+            a5[3].add(cy.vz * t0);
+            a5[4].add(T(0.5) * fma(cy.vy * cy.vy + cy.vz * cy.vz, t0, t2));
+            if (++xg == g.nxg) {
+                xg = 0;
+                ++r;
+            }
+        }
+    }
+    merge_chunks<T, 5>(a5);
+    if (threadIdx.y != 0 || i >= g.nx) return;
+    for (int q = 0; q < S; ++q)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) part[((long)q * 5 + m) * nc + cell] = (q == 0 && gas) ? a5[m].value() : T(0);
+}
+
 __device__ __forceinline__ double maxw3(const double *q, double vx, double vy, double vz)
 {
     const double ax = vx - q[1], ay = vy - q[2], az = vz - q[3];
@@ -1273,13 +1347,21 @@ Cv3Args cv3_args(dvm_ctx *c)
 template <typename T>
 cudaError_t step3d_t(dvm_ctx *c)
 {
-    const Grid3D g = grid3d(c);
+    Grid3D g = grid3d(c);
+    // the semi-implicit scheme (Eq. ImpSchemeDD) transports without
+    // relaxation here; k_imex3 relaxes at the end of the step
+    const bool imex = c->time_scheme == DVM_IMEX;
+    if (imex) {
+        g.dt_tau0 = 0.0;
+        g.dt_tau0_f = 0.f;
+    }
     const BodyParams bp = body_params(c);
     const bool body = c->body.shape != DVM_SHAPE_NONE;
     T *fin = (T *)c->f[c->cur], *fout = (T *)c->f[1 - c->cur];
     T *pin = (T *)c->part[c->cur], *pout = (T *)c->part[1 - c->cur];
     cudaError_t e;
-    const Cv3Args cv = cv3_args(c);
+    Cv3Args cv = cv3_args(c);
+    cv.g = g;                 // without the relaxation rate for the semi-implicit scheme
     const int cvgrid = 4 * 152;
     if (body) {
         if (c->need_fusion) {
@@ -1309,6 +1391,12 @@ cudaError_t step3d_t(dvm_ctx *c)
         if ((e = cudaEventRecord(c->ev_wjoin, c->wstream)) != cudaSuccess) return e;
         // the step ends when both streams are done
         if ((e = cudaStreamWaitEvent(c->stream, c->ev_wjoin, 0)) != cudaSuccess) return e;
+        c->launches += 1;
+    }
+    if (imex) {
+        const dim3 grid(nb3(c->nx, 32), c->ny, c->nz), block(32, kMomChunks);
+        k_imex3<T><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c), vyz_table<T>(c),
+                                                  pout, c->geo3.type, c->d_err);
         c->launches += 1;
     }
     c->cur = 1 - c->cur;

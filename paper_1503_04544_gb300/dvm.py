@@ -75,6 +75,7 @@ SIGNATURES = {
     "dvm_step": [_P, C.c_int],
     "dvm_step_async": [_P, C.c_int],
     "dvm_graphs": [_P, C.c_int],
+    "dvm_set_time_scheme": [_P, C.c_int],
     "dvm_check": [_P],
     "dvm_moments": [_P, _PD, _PD, _PD, _PD, _PD],
     "dvm_wall_force": [_P, _PD, _PD],
@@ -152,6 +153,8 @@ class Solver:
         self._keep = []
         if cfg.get("shape", 0):
             self.set_body(cfg)
+        if int(cfg.get("time_scheme", 0)):
+            self.set_time_scheme(int(cfg["time_scheme"]))
         dt = C.c_double()
         tau0 = C.c_double()
         nc = C.c_longlong()
@@ -214,6 +217,10 @@ class Solver:
 
     def step_async(self, n: int = 1):
         _check(load().dvm_step_async(self.h, int(n)))
+
+    def set_time_scheme(self, scheme: int):
+        """0: explicit (Eq. ExSchemeDD), 1: first-order semi-implicit (Eq. ImpSchemeDD)."""
+        _check(load().dvm_set_time_scheme(self.h, int(scheme)))
 
     def graphs(self, enable: bool = True):
         """Two-step CUDA graph replays in step / step_async (on by default)."""
