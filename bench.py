@@ -12,6 +12,7 @@ non-solid cells.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
                   [--workload cylinder|sphere|ellipse|bump] [--impl gb300|reference]
+                  [--time-scheme explicit|imex]
 
 For N > 1 each rank runs an independent replica (the path is not sharded
 here); value = pairs updated by all ranks / max-over-ranks time.
@@ -71,6 +72,7 @@ def config_dict(cfg, prec, nsolid_free, extra=None):
         "cells": cells,
         "velocities": vels,
         "scheme": "muscl-minmod" if cfg.get("scheme", 0) == 1 else "upwind",
+        "time_scheme": "semi-implicit" if cfg.get("time_scheme", 0) == 1 else "explicit",
         "precision": prec,
         "pairs_per_step": nsolid_free,
         "l2": "inputs larger than L2 (state per copy > 129 MB)",
@@ -260,6 +262,8 @@ def run_reference(args):
     if rank != 0:
         return
     cfg = workload(args.workload)
+    if args.time_scheme == "imex":
+        cfg["time_scheme"] = 1
     cb = cpu_baseline(cfg, budget_s=60.0, max_steps=max(1, min(args.steps, 8)))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -279,6 +283,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--workload", default="cylinder")
+    ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit",
+                    help="explicit (Eq. ExSchemeDD) or first-order semi-implicit (Eq. ImpSchemeDD) steps")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the drag-gradient cost measurement")
@@ -302,6 +308,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     cfg = workload(args.workload)
+    if args.time_scheme == "imex":
+        cfg["time_scheme"] = 1
     prec = dvm.FP32 if args.precision == "fp32" else dvm.FP64
     # a dedicated stream: the library enqueues on it and the events below
     # are recorded on it
@@ -410,7 +418,7 @@ def main():
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(cfg)
-        if world == 1 and args.workload == "cylinder" and not args.no_adjoint:
+        if world == 1 and args.workload == "cylinder" and args.time_scheme == "explicit" and not args.no_adjoint:
             line["adjoint"] = adjoint_cost(prec == dvm.FP32)
         print(json.dumps(line), flush=True)
     s.close()
