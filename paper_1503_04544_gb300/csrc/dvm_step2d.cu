@@ -1083,6 +1083,10 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_moments_out(Grid2D g, const
 // the others).  Cells solid at t^{n+1} (type) keep their zero state.
 // Block = 32 consecutive cells of a row x kMomChunks warps, one chunk of the
 // velocity groups each.
+// 2^x for the relaxation kernel: the hardware approximation in FP32.
+__device__ __forceinline__ float exp2_relax(float x) { return ex2_fast(x); }
+__device__ __forceinline__ double exp2_relax(double x) { return exp2(x); }
+
 template <typename T>
 __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_tau0, T *f, const VCoef<T> *vt,
                                                           T *part, const int8_t *type, int *err)
@@ -1109,6 +1113,7 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_
         V *fv = reinterpret_cast<V *>(f);
         const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
         const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+#pragma unroll 2
         for (int q = q0; q < q1; ++q) {
             V *pa = fv + (long)q * 2 * g.slab, *pb = pa + g.slab;
             T a[W], b[W];
@@ -1120,7 +1125,7 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_
                 if (q * W + e >= g.nv) continue;
                 const VCoef<T> c = ld_coef(vt + q * W + e);
                 const T dx = c.vx - ux, dy = c.vy - uy;
-                const T M = A * dexp2(-(dx * dx + dy * dy) * c2);
+                const T M = A * exp2_relax(-(dx * dx + dy * dy) * c2);
                 a[e] = (a[e] + nu * M) * inv;
                 b[e] = (b[e] + nu * half * M) * inv;
                 t0 += a[e];

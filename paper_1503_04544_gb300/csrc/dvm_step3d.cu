@@ -1092,6 +1092,7 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt
         mirrors3(g, i, j, k, mir);
         V *fv = reinterpret_cast<V *>(f);
         int r = q0 / g.nxg, xg = q0 - r * g.nxg;
+#pragma unroll 2
         for (int q = q0; q < q1; ++q) {
             V *pa = fv + (long)q * g.slab;
             T a[W];
@@ -1104,7 +1105,7 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt
                 const int p1 = xg * W + e;
                 if (p1 >= g.nvx) continue;
                 const T vx = vxt[p1].vx, dx = vx - ux;
-                const T M = A * dexp2(-(dx * dx + dyz) * c2);
+                const T M = A * exp2_state(-(dx * dx + dyz) * c2);
                 a[e] = (a[e] + nu * M) * inv;
                 t0 += a[e];
                 t1 += vx * a[e];
