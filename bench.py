@@ -56,7 +56,7 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-DEFAULT_STEPS = {"cylinder": 2000, "ellipse": 500, "bump": 2000, "sphere": 60}
+DEFAULT_STEPS = {"cylinder": 2000, "ellipse": 5000, "bump": 2000, "sphere": 60}
 
 
 def _dims(cfg):
