@@ -123,3 +123,25 @@ def test_time_scheme_argument_checked():
     with pytest.raises(dvm.DVMError):
         s.set_time_scheme(2)
     s.close()
+
+
+@pytest.mark.parametrize("prec", [dvm.FP64])
+def test_scheme_switch_mid_run(prec):
+    """5 explicit, 5 semi-implicit, 5 explicit steps: the explicit step after
+    the semi-implicit ones starts from the partial sums the relaxation kernel
+    wrote (those of the relaxed state); the oracle runs the same sequence."""
+    base = W.cylinder_mach2(nx=48, nv=16)
+    base.update(Kn=0.05)
+    ce, ci = dict(base, time_scheme=0), dict(base, time_scheme=1)
+    F0 = oracle.initial_state(ce)
+    Fo = F0.copy()
+    for cfg in (ce, ci, ce):
+        assert oracle.run(cfg, Fo, 5)["status"] == 0
+    s = dvm.Solver(ce, prec)
+    s.set_state(F0)
+    for scheme in (0, 1, 0):
+        s.set_time_scheme(scheme)
+        s.step(5)
+    Fg = s.get_state()
+    assert np.abs(Fg - Fo).max() <= 1e-12 * np.abs(Fo).max()
+    s.close()
