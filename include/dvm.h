@@ -146,6 +146,25 @@ int dvm_init_maxwellian(dvm_ctx *ctx, const double *rho, const double *ux,
 int dvm_set_state(dvm_ctx *ctx, const void *f, size_t bytes, int on_device);
 int dvm_get_state(dvm_ctx *ctx, void *f, size_t bytes, int on_device);
 
+/* Checkpoint and restart of the time iteration (Sec. 3.3.5; the paper runs
+ * long simulations but defines no file format, this one is the library's).
+ * dvm_save writes to the file `path` (created or truncated, caller-owned name)
+ * a header (grid and velocity grid sizes, precision, space and time schemes,
+ * velocity splits, body kind, dt, tau0, steps done), the state in the public
+ * layout of dvm_get_state, the partial moment sums of the current state and
+ * the rigid-body record (angle, angular velocity, the cos/sin of the angle as
+ * the device computed them, last force and torque).  dvm_load reads such a
+ * file into a context made with the same grid, velocity grid, precision,
+ * schemes and body: the state, the sums, the body (a moving body's geometry
+ * is rebuilt at the saved angle), the step count and the time scheme are
+ * restored, so that stepping continues bit for bit as the saved context
+ * would have.  The force history restarts empty.  Both synchronise the
+ * context's stream.  Errors: DVM_ERR_STATE (dvm_save before any state),
+ * DVM_ERR_ARG (file not writable or readable, not a checkpoint, or one of
+ * another problem), DVM_ERR_CUDA. */
+int dvm_save(dvm_ctx *ctx, const char *path);
+int dvm_load(dvm_ctx *ctx, const char *path);
+
 /* Advance nsteps explicit steps (the 7 steps of Sec. 3.3.5), enqueued on
  * the context's stream without host synchronisation inside the loop.  The
  * call synchronises once at the end to check the device error flags.

@@ -1,6 +1,7 @@
 // C-ABI of libdvm: context management, set-up, stepping and read-back.
 // Every entry point returns a dvm_status and records a thread-local message.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -681,6 +682,101 @@ int dvm_get_state(dvm_ctx *c, void *f, size_t bytes, int on_device)
     CK(cudaMemcpyAsync(f, c->d_pub, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return DVM_OK;
+}
+
+// Checkpoint file: a fixed header, then the state in the public layout, the
+// partial moment sums of the current buffer (device layout) and the device
+// body record, so that a loaded context continues bit for bit as the saved
+// one would have.
+struct CheckpointHeader {
+    char magic[8];            // "DVMCKPT1"
+    int32_t version, dim, precision, scheme, time_scheme, S;
+    int32_t nx, ny, nz, nvx, nvy, nvz, shape, movable, need_fusion, reserved;
+    double dt, tau0;
+    int64_t steps_done;
+    uint64_t state_bytes, part_bytes, body_bytes;
+};
+static const char kCkptMagic[8] = {'D', 'V', 'M', 'C', 'K', 'P', 'T', '1'};
+
+static size_t part_bytes(const dvm_ctx *c)
+{
+    return (size_t)c->S * (c->dim == 2 ? 4 : 5) * (size_t)c->nc * c->elem;
+}
+
+int dvm_save(dvm_ctx *c, const char *path)
+{
+    if (!c || !path) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (!c->have_state) { set_error("dvm_save: no state"); return DVM_ERR_STATE; }
+    CheckpointHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1; h.dim = c->dim; h.precision = c->prec; h.scheme = c->scheme; h.time_scheme = c->time_scheme;
+    h.S = c->S; h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.nvx = c->nvx; h.nvy = c->nvy; h.nvz = c->nvz;
+    h.shape = c->body.shape; h.movable = c->body.movable; h.need_fusion = c->need_fusion ? 1 : 0;
+    h.dt = c->dt; h.tau0 = c->tau0; h.steps_done = c->steps_done;
+    h.state_bytes = c->state_elems * c->elem;
+    h.part_bytes = part_bytes(c);
+    h.body_bytes = sizeof(dvm::BodyDev);
+    std::vector<char> state(h.state_bytes), part(h.part_bytes);
+    dvm::BodyDev hb;
+    int rc = dvm_get_state(c, state.data(), state.size(), 0);
+    if (rc != DVM_OK) return rc;
+    CK(cudaMemcpyAsync(part.data(), c->part[c->cur], part.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&hb, c->d_body, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) { set_error(std::string("dvm_save: cannot open ") + path); return DVM_ERR_ARG; }
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(state.data(), 1, state.size(), fp) == state.size() &&
+              std::fwrite(part.data(), 1, part.size(), fp) == part.size() && std::fwrite(&hb, sizeof(hb), 1, fp) == 1;
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) { set_error(std::string("dvm_save: write failed: ") + path); return DVM_ERR_ARG; }
+    return DVM_OK;
+}
+
+int dvm_load(dvm_ctx *c, const char *path)
+{
+    if (!c || !path) { set_error("null argument"); return DVM_ERR_ARG; }
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) { set_error(std::string("dvm_load: cannot open ") + path); return DVM_ERR_ARG; }
+    CheckpointHeader h;
+    std::vector<char> state, part;
+    dvm::BodyDev hb;
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, kCkptMagic, 8) == 0 && h.version == 1;
+    // the checkpoint must come from a context of the same problem
+    ok = ok && h.dim == c->dim && h.precision == c->prec && h.scheme == c->scheme && h.S == c->S &&
+         h.nx == c->nx && h.ny == c->ny && h.nz == c->nz && h.nvx == c->nvx && h.nvy == c->nvy &&
+         h.nvz == c->nvz && h.shape == c->body.shape && h.movable == c->body.movable && h.dt == c->dt &&
+         h.tau0 == c->tau0 && h.state_bytes == c->state_elems * c->elem && h.part_bytes == part_bytes(c) &&
+         h.body_bytes == sizeof(dvm::BodyDev) && (h.time_scheme == DVM_EXPLICIT || h.time_scheme == DVM_IMEX);
+    if (ok) {
+        state.resize(h.state_bytes);
+        part.resize(h.part_bytes);
+        ok = std::fread(state.data(), 1, state.size(), fp) == state.size() &&
+             std::fread(part.data(), 1, part.size(), fp) == part.size() && std::fread(&hb, sizeof(hb), 1, fp) == 1;
+    }
+    std::fclose(fp);
+    if (!ok) {
+        set_error(std::string("dvm_load: not a checkpoint of this problem (grid, velocities, precision, schemes, "
+                              "body, time step): ") + path);
+        return DVM_ERR_ARG;
+    }
+    // the body first: a moving body's geometry is rebuilt at the saved angle
+    // from the saved (cos, sin), which the saved run's current level used
+    CK(cudaMemcpyAsync(c->d_body, &hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream));
+    if (c->dim == 2 && c->moving) {
+        c->gcur = 0;
+        CK(geometry2d_level(c, 0, body_trig(c, 2)));
+        CK(geometry2d_level(c, 1, body_trig(c, 2)));
+        CK(masters_flags2d(c, false));
+    }
+    int rc = dvm_set_state(c, state.data(), state.size(), 0);
+    if (rc != DVM_OK) return rc;
+    // the saved partial sums, not ones recomputed from the state
+    CK(cudaMemcpyAsync(c->part[c->cur], part.data(), part.size(), cudaMemcpyHostToDevice, c->stream));
+    c->need_fusion = h.need_fusion != 0;
+    c->steps_done = h.steps_done;
+    c->time_scheme = h.time_scheme;
+    return check_flags(c);
 }
 
 int dvm_step_async(dvm_ctx *c, int nsteps)

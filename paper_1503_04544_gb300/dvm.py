@@ -75,6 +75,8 @@ SIGNATURES = {
     "dvm_step": [_P, C.c_int],
     "dvm_step_async": [_P, C.c_int],
     "dvm_graphs": [_P, C.c_int],
+    "dvm_save": [_P, C.c_char_p],
+    "dvm_load": [_P, C.c_char_p],
     "dvm_set_time_scheme": [_P, C.c_int],
     "dvm_check": [_P],
     "dvm_moments": [_P, _PD, _PD, _PD, _PD, _PD],
@@ -217,6 +219,14 @@ class Solver:
 
     def step_async(self, n: int = 1):
         _check(load().dvm_step_async(self.h, int(n)))
+
+    def save(self, path: str):
+        """Checkpoint the context's state, moment sums and body to ``path`` (dvm_save)."""
+        _check(load().dvm_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Restart from a checkpoint of the same problem (dvm_load)."""
+        _check(load().dvm_load(self.h, os.fsencode(path)))
 
     def set_time_scheme(self, scheme: int):
         """0: explicit (Eq. ExSchemeDD), 1: first-order semi-implicit (Eq. ImpSchemeDD)."""
