@@ -9,7 +9,8 @@
  * limited fluxes across the Cartesian edges of each virtual cell and the
  * diffuse-reflection flux across its wall edge (Eq. FluxDD, Eq.
  * BoundaryDDv), the explicit update of each control volume (Eq. ExSchemeDD)
- * and the wall stress, force, torque and rigid rotation (Sec. 3.3.4).  2D
+ * or the first-order semi-implicit one (Eq. ImpSchemeDD), and the wall
+ * stress, force, torque and rigid rotation (Sec. 3.3.4).  2D
  * uses the reduced pair (f, g) (Sec. 2.2); 3D uses the full F (Sec. 5).
  *
  * Conventions
@@ -165,11 +166,24 @@ int dvm_get_state(dvm_ctx *ctx, void *f, size_t bytes, int on_device);
 int dvm_save(dvm_ctx *ctx, const char *path);
 int dvm_load(dvm_ctx *ctx, const char *path);
 
-/* Advance nsteps explicit steps (the 7 steps of Sec. 3.3.5), enqueued on
- * the context's stream without host synchronisation inside the loop.  The
- * call synchronises once at the end to check the device error flags.
- * Errors: DVM_ERR_NONPHYSICAL, DVM_ERR_GEOMETRY, DVM_ERR_CUDA. */
+/* Advance nsteps steps (the 7 steps of Sec. 3.3.5; the time scheme of
+ * dvm_set_time_scheme), enqueued on the context's stream in chunks of up to
+ * 1024 steps without host synchronisation inside a chunk.  Before a chunk the
+ * call copies the stepping state on the device (state, moment sums, rigid
+ * body: one more state-sized device buffer, allocated at the first call);
+ * after it, it reads the device error flags and checks the moments of the
+ * chunk's last state.  On a failure it steps the chunk again one step at a
+ * time from the copy and leaves the state, the body and the step count at the
+ * last good step, the input of the first step that failed: no geometry
+ * error, and rho > 0 and T > 0 in every gas cell of its output.
+ * Errors: DVM_ERR_NONPHYSICAL, DVM_ERR_GEOMETRY, DVM_ERR_OOM (no memory for
+ * the copy), DVM_ERR_CUDA. */
 int dvm_step(dvm_ctx *ctx, int nsteps);
+
+/* dvm_step with (enable != 0, the default) or without the copy and the
+ * rollback above; without it a failing call leaves the state after its last
+ * step.  Errors: DVM_ERR_ARG for a null ctx. */
+int dvm_rollback(dvm_ctx *ctx, int enable);
 
 /* Same as dvm_step but without the final synchronisation and flag check
  * (for timing and graph capture); dvm_check() reads the flags later.

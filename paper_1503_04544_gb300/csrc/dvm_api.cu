@@ -446,6 +446,7 @@ void dvm_destroy(dvm_ctx *c)
     cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
     for (int s = 0; s < 6; ++s) cudaFree(c->d_bcstate[s]);
     cudaFree(c->d_prim0);
+    cudaFree(c->snap_f); cudaFree(c->snap_part); cudaFree(c->snap_scratch); cudaFree(c->snap_body);
     free_adjoint2d(c);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->gretired) {
@@ -832,11 +833,133 @@ int dvm_check(dvm_ctx *c)
     return check_flags(c);
 }
 
+// ---- dvm_step with a rollback to the last good step
+// dvm_step runs chunks of up to kCheckChunk steps.  Before a chunk it copies
+// the stepping state (state buffer, moment sums, rigid-body record, host
+// counters) on the device; after it, it reads the flags and checks the
+// moments of the chunk's last state.  If either fails, it goes back to the
+// copy and steps one at a time with the same checks, and leaves the state at
+// the input of the first step that failed.  The kernels are deterministic, so
+// the replay meets the same states.
+constexpr int kCheckChunk = 1024;
+
+struct StepMark {
+    int cur, gcur;
+    long long steps;
+    bool need_fusion;
+};
+
+static int ensure_snapshot(dvm_ctx *c)
+{
+    cudaError_t e = cudaSuccess;
+    if (!c->snap_f) e = cudaMalloc(&c->snap_f, c->dev_elems * c->elem);
+    if (e == cudaSuccess && !c->snap_part) e = cudaMalloc(&c->snap_part, part_bytes(c));
+    if (e == cudaSuccess && !c->snap_scratch) e = cudaMalloc(&c->snap_scratch, part_bytes(c));
+    if (e == cudaSuccess && !c->snap_body) e = cudaMalloc(&c->snap_body, sizeof(dvm::BodyDev));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("dvm_step: no device memory for the rollback copy of the state (dvm_rollback(ctx, 0) steps "
+                  "without it)");
+        return DVM_ERR_OOM;
+    }
+    return DVM_OK;
+}
+
+static cudaError_t take_snapshot(dvm_ctx *c, StepMark *m)
+{
+    m->cur = c->cur; m->gcur = c->gcur; m->steps = c->steps_done; m->need_fusion = c->need_fusion;
+    cudaError_t e = cudaMemcpyAsync(c->snap_f, c->f[c->cur], c->dev_elems * c->elem, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->snap_part, c->part[c->cur], part_bytes(c), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->snap_body, c->d_body, sizeof(dvm::BodyDev), cudaMemcpyDeviceToDevice, c->stream);
+    return e;
+}
+
+static cudaError_t restore_snapshot(dvm_ctx *c, const StepMark &m)
+{
+    c->cur = m.cur; c->gcur = m.gcur; c->steps_done = m.steps; c->need_fusion = m.need_fusion;
+    cudaError_t e = cudaMemcpyAsync(c->f[c->cur], c->snap_f, c->dev_elems * c->elem, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->part[c->cur], c->snap_part, part_bytes(c), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_body, c->snap_body, sizeof(dvm::BodyDev), cudaMemcpyDeviceToDevice, c->stream);
+    // a moving body's current geometry level, from the cos/sin it was built with
+    if (e == cudaSuccess && c->dim == 2 && c->moving) e = geometry2d_level(c, c->gcur, body_trig(c, 2));
+    if (e == cudaSuccess && c->dim == 2 && c->moving) e = masters_flags2d(c, false);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, kErrCount * sizeof(int), c->stream);
+    return e;
+}
+
+// Moments of the current state into the scratch sums: raises the
+// non-physical flag for a gas cell with rho <= 0 or T <= 0.
+static cudaError_t check_state(dvm_ctx *c)
+{
+    void *keep = c->part[c->cur];
+    c->part[c->cur] = c->snap_scratch;
+    const cudaError_t e = st_partials(c);
+    c->part[c->cur] = keep;
+    return e;
+}
+
+// Synchronises and tells whether a flag is raised (without clearing it).
+static cudaError_t flags_raised(dvm_ctx *c, bool *raised)
+{
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, kErrCount * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    destroy_retired(c);
+    *raised = false;
+    for (int k = 0; k < kErrCount; ++k) *raised = *raised || c->h_err[k] != 0;
+    return cudaSuccess;
+}
+
 int dvm_step(dvm_ctx *c, int nsteps)
 {
-    int rc = dvm_step_async(c, nsteps);
+    int rc = dvm_step_async(c, 0);             // the argument and state checks
     if (rc != DVM_OK) return rc;
+    if (c->rollback_off) {
+        rc = dvm_step_async(c, nsteps);
+        if (rc != DVM_OK) return rc;
+        return check_flags(c);
+    }
+    if (nsteps == 0) return check_flags(c);
+    if ((rc = ensure_snapshot(c)) != DVM_OK) return rc;
+    for (int done = 0; done < nsteps;) {
+        const int n = nsteps - done < kCheckChunk ? nsteps - done : kCheckChunk;
+        StepMark m;
+        CK(take_snapshot(c, &m));
+        if ((rc = dvm_step_async(c, n)) != DVM_OK) return rc;
+        CK(check_state(c));
+        bool bad = false;
+        CK(flags_raised(c, &bad));
+        if (bad) {
+            CK(restore_snapshot(c, m));
+            for (int k = 0; k < n; ++k) {
+                CK(take_snapshot(c, &m));
+                if ((rc = dvm_step_async(c, 1)) != DVM_OK) return rc;
+                CK(check_state(c));
+                CK(flags_raised(c, &bad));
+                if (bad) {
+                    rc = check_flags(c);       // message, flags cleared
+                    CK(restore_snapshot(c, m));
+                    CK(cudaStreamSynchronize(c->stream));
+                    set_error(dvm_last_error() + std::string("; the state is left at step ") +
+                              std::to_string(c->steps_done));
+                    return rc;
+                }
+            }
+        }
+        done += n;
+    }
     return check_flags(c);
+}
+
+int dvm_rollback(dvm_ctx *c, int enable)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    c->rollback_off = enable == 0;
+    return DVM_OK;
 }
 
 int dvm_moments(dvm_ctx *c, double *rho, double *ux, double *uy, double *uz, double *T)

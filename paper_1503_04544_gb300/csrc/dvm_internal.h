@@ -183,6 +183,10 @@ struct dvm_ctx {
     int ev_used;
     bool graphs;                  // dvm_step replays two-step CUDA graphs (dvm_graphs)
     int time_scheme;              // DVM_EXPLICIT or DVM_IMEX (dvm_set_time_scheme)
+    void *snap_f, *snap_part;     // dvm_step: state and moment sums at the last checked step
+    void *snap_scratch;           // dvm_step: moment sums of the state check
+    void *snap_body;              // dvm_step: rigid-body record at the last checked step
+    bool rollback_off;            // dvm_rollback(ctx, 0): dvm_step without snapshots
     void *gretired;               // std::vector<cudaGraphExec_t> launched, destroyed once the stream is idle
     long long launches;
 };

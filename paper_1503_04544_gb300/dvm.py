@@ -75,6 +75,7 @@ SIGNATURES = {
     "dvm_step": [_P, C.c_int],
     "dvm_step_async": [_P, C.c_int],
     "dvm_graphs": [_P, C.c_int],
+    "dvm_rollback": [_P, C.c_int],
     "dvm_save": [_P, C.c_char_p],
     "dvm_load": [_P, C.c_char_p],
     "dvm_set_time_scheme": [_P, C.c_int],
@@ -231,6 +232,10 @@ class Solver:
     def set_time_scheme(self, scheme: int):
         """0: explicit (Eq. ExSchemeDD), 1: first-order semi-implicit (Eq. ImpSchemeDD)."""
         _check(load().dvm_set_time_scheme(self.h, int(scheme)))
+
+    def rollback(self, enable: bool = True):
+        """dvm_step leaves the state at the last good step on a failure (on by default)."""
+        _check(load().dvm_rollback(self.h, int(bool(enable))))
 
     def graphs(self, enable: bool = True):
         """Two-step CUDA graph replays in step / step_async (on by default)."""
