@@ -1,0 +1,192 @@
+"""Parity with the FP64 CPU oracle at the full benchmark sizes, in the launch
+configuration the benchmark times (the library's own velocity-split count and
+tile shapes at these sizes, steps of at least 8 so that the two-step CUDA
+graph replays run).  GPU only.
+
+Each case first runs the GPU alone for a number of steps from the initial
+Maxwellian, so that the state carries the shock and wall layers around the
+body; that state (exactly, widened to FP64) is then the common start of a
+few further steps on both sides.
+
+- Cylinder, 256^2 cells x 32^2 velocities, MUSCL: the whole state, FP64 and
+  FP32, explicit and semi-implicit (Eqs. ExSchemeDD, ImpSchemeDD).
+- Rotating ellipse, 512^2 x 40^2, upwind, freely moving body: the whole
+  state, the torque history and the body angle and angular velocity.
+- Sphere, 96^3 x 20^3, MUSCL, FP32: a full step at this size takes the
+  oracle minutes and more host memory than a test should hold, so the oracle
+  steps a 40^3 block of cells that holds the whole sphere (every cut cell and
+  merged control volume) with the state of the full run; after n steps the
+  block's cells more than 2n cells from its faces are exact (the MUSCL
+  stencil reaches two cells), and those are compared, with the force, which
+  needs only the wall cells.
+
+Tolerances as in the small-size parity tests: FP64 state within 1e-12 of the
+largest value, FP32 moments within 1e-5 (relative; velocities on the scale
+max(|u|, 1)).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_04544_gb300 import dvm
+from paper_1503_04544_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {dvm.FP64: 1e-12, dvm.FP32: 1e-5}
+
+
+def rel_inf(a, b):
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).max()
+    s = np.abs(np.asarray(b, np.float64)).max()
+    return d / s if s > 0 else d
+
+
+def moment_errors(mg, mo, keys, live):
+    errs = {}
+    for k in keys:
+        ref = mo[k][live]
+        scale = np.abs(ref).max()
+        if k != "rho" and k != "T":
+            scale = max(scale, 1.0)
+        errs[k] = np.abs(mg[k][live] - ref).max() / scale
+    return errs
+
+
+def as64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def need_host_memory(gb):
+    """Skip when the host has less free memory than the case holds at its peak
+    (with a margin), rather than let the oracle run the host out of memory."""
+    try:
+        with open("/proc/meminfo") as fh:
+            avail = next(int(l.split()[1]) for l in fh if l.startswith("MemAvailable")) / 2 ** 20
+    except (OSError, StopIteration):
+        return
+    if avail < 1.5 * gb:
+        pytest.skip(f"needs about {gb} GB of free host memory, {avail:.0f} GB available")
+
+
+def lead_in(cfg, prec, steps):
+    s = dvm.Solver(cfg, prec)
+    s.init_maxwellian()
+    s.step(steps)
+    return s
+
+
+@pytest.mark.parametrize("prec,scheme", [(dvm.FP64, 0), (dvm.FP32, 0), (dvm.FP32, 1)],
+                         ids=["fp64-explicit", "fp32-explicit", "fp32-semi-implicit"])
+def test_cylinder_full_size(prec, scheme):
+    cfg = W.cylinder_mach2(nx=256, nv=32, scheme=1)
+    cfg["time_scheme"] = scheme
+    need_host_memory(6)
+    lead, n = 40, 10
+    s = lead_in(cfg, prec, lead)
+    Fo = np.array(s.get_state(), dtype=np.float64)
+    h = oracle.run(cfg, Fo, n)
+    assert h["status"] == 0
+    s.step(n)
+    Fg = s.get_state()
+    if prec == dvm.FP64:
+        assert rel_inf(Fg, Fo) < TOL[prec]
+    mo = oracle.moments(cfg, Fo)
+    mg = oracle.moments(cfg, as64(Fg))
+    errs = moment_errors(mg, mo, ("rho", "ux", "uy", "T"), mo["rho"] > 0)
+    assert max(errs.values()) < TOL[prec], errs
+    hg = s.history(lead + n)
+    assert rel_inf(hg["Fx"][lead:], h["Fx"]) < TOL[prec]
+    assert Fg.min() >= 0
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [dvm.FP32, dvm.FP64])
+def test_rotating_ellipse_full_size(prec):
+    cfg = W.rotating_ellipse(nx=512, nv=40)
+    need_host_memory(24)
+    lead, n = 60, 8
+    s = lead_in(cfg, prec, lead)
+    th0, om0 = s.body_state()
+    Fo = as64(s.get_state())
+    ocfg = dict(cfg, theta=th0, omega=om0)
+    h = oracle.run(ocfg, Fo, n)
+    assert h["status"] == 0
+    s.step(n)
+    th, om = s.body_state()
+    hg = s.history(lead + n)
+    Fg = s.get_state()
+    if prec == dvm.FP64:
+        assert rel_inf(Fg, Fo) < TOL[prec]
+        assert abs(th - h["theta"]) < 1e-10 * max(1.0, abs(h["theta"]))
+        assert abs(om - h["omega"]) < 1e-9 * max(1.0, abs(h["omega"]))
+        assert rel_inf(hg["torque"][lead:], h["torque"]) < 1e-9
+    else:
+        assert abs(th - h["theta"]) < 1e-7
+        assert rel_inf(hg["torque"][lead:], h["torque"]) < 1e-4
+    mo = oracle.moments(cfg, Fo)
+    mg = oracle.moments(cfg, as64(Fg))
+    errs = moment_errors(mg, mo, ("rho", "ux", "uy", "T"), mo["rho"] > 0)
+    assert max(errs.values()) < TOL[prec], errs
+    s.close()
+
+
+def sphere_block(cfg, lo, hi, dt):
+    """The problem restricted to cells lo..hi-1 on every axis (same cell size,
+    body, velocity grid, Knudsen number and time step; zero-gradient faces,
+    which only reach the cells within two of the block's faces)."""
+    n = cfg["nx"]
+    b = dict(cfg)
+    b.update(nx=hi - lo, ny=hi - lo, nz=hi - lo, dt=dt, bc=[2] * 6, bc_state=[None] * 6,
+             name=f"sphere_block_{lo}_{hi}")
+    for ax in ("x", "y", "z"):
+        b[ax + "min"] = lo / n
+        b[ax + "max"] = hi / n
+    return b
+
+
+def test_sphere_full_size_block():
+    torch = pytest.importorskip("torch")
+    need_host_memory(20)
+    cfg = W.sphere_mach15(n=96, nv=20, scheme=1)
+    n, nv = cfg["nx"], cfg["nvx"] * cfg["nvy"] * cfg["nvz"]
+    lo, hi, steps = 28, 68, 2
+    lead = 20
+    s = lead_in(cfg, dvm.FP32, lead)
+    full = torch.empty(s.state_size, dtype=torch.float32, device="cuda")
+
+    def block():
+        s.get_state(full)
+        v = full.view(n, n, n, nv)[lo:hi, lo:hi, lo:hi, :]
+        return as64(v.contiguous().cpu().numpy()).ravel()
+
+    bcfg = sphere_block(cfg, lo, hi, s.dt)
+    # the block's geometry is the full grid's: every cut cell lies inside,
+    # away from the block faces
+    gb = oracle.geometry3d(bcfg)
+    assert gb["status"] == 0
+    tg = s.geometry3d()["type"].reshape(n, n, n)[lo:hi, lo:hi, lo:hi].ravel()
+    assert np.array_equal(gb["type"], tg)
+    cut = np.argwhere((gb["type"] == 1).reshape(hi - lo, hi - lo, hi - lo))
+    assert cut.min() >= 2 * steps and cut.max() < hi - lo - 2 * steps
+
+    Fo = block()
+    h = oracle.run3d(bcfg, Fo, steps)
+    assert h["status"] == 0
+    s.step(steps)
+    Fg = block()
+    del full
+    m = hi - lo
+    inner = np.zeros((m, m, m), bool)
+    e = 2 * steps
+    inner[e:m - e, e:m - e, e:m - e] = True
+    inner = inner.ravel()
+    mo = oracle.moments(bcfg, Fo)
+    mg = oracle.moments(bcfg, Fg)
+    errs = moment_errors(mg, mo, ("rho", "ux", "uy", "uz", "T"), inner & (mo["rho"] > 0))
+    assert max(errs.values()) < TOL[dvm.FP32], errs
+    Fi = Fo.reshape(m ** 3, nv)[inner]
+    assert rel_inf(Fg.reshape(m ** 3, nv)[inner], Fi) < TOL[dvm.FP32]
+    hg = s.history(lead + steps)
+    assert rel_inf(hg["Fx"][lead:], h["Fx"]) < TOL[dvm.FP32]
+    s.close()
