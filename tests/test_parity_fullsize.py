@@ -14,11 +14,15 @@ few further steps on both sides.
   state, the torque history and the body angle and angular velocity.
 - Sphere, 96^3 x 20^3, MUSCL, FP32: a full step at this size takes the
   oracle minutes and more host memory than a test should hold, so the oracle
-  steps a 40^3 block of cells that holds the whole sphere (every cut cell and
-  merged control volume) with the state of the full run; after n steps the
-  block's cells more than 2n cells from its faces are exact (the MUSCL
-  stencil reaches two cells), and those are compared, with the force, which
-  needs only the wall cells.
+  steps the corner block [0, 68)^3 of the grid, which holds the whole sphere
+  (every cut cell and merged control volume), with the state of the full
+  run.  Its cell size is the full grid's bit for bit, so its geometry and
+  control volumes are too (checked, against the library's); after n steps
+  the block's cells more than 2n cells from its high faces are exact (the
+  MUSCL stencil reaches two cells), and those are compared, with the force,
+  which needs only the wall cells.  A block that does not start at the
+  origin has node coordinates rounded differently, and the tie-breaks of
+  the master search (Appendix A.3) then pick other control volumes.
 
 Tolerances as in the small-size parity tests: FP64 state within 1e-12 of the
 largest value, FP32 moments within 1e-5 (relative; velocities on the scale
@@ -28,6 +32,7 @@ import numpy as np
 import pytest
 
 import oracle
+from block3d import GEO3, block_view, corner_block, full_index
 from paper_1503_04544_gb300 import dvm
 from paper_1503_04544_gb300 import workloads as W
 
@@ -131,44 +136,37 @@ def test_rotating_ellipse_full_size(prec):
     s.close()
 
 
-def sphere_block(cfg, lo, hi, dt):
-    """The problem restricted to cells lo..hi-1 on every axis (same cell size,
-    body, velocity grid, Knudsen number and time step; zero-gradient faces,
-    which only reach the cells within two of the block's faces)."""
-    n = cfg["nx"]
-    b = dict(cfg)
-    b.update(nx=hi - lo, ny=hi - lo, nz=hi - lo, dt=dt, bc=[2] * 6, bc_state=[None] * 6,
-             name=f"sphere_block_{lo}_{hi}")
-    for ax in ("x", "y", "z"):
-        b[ax + "min"] = lo / n
-        b[ax + "max"] = hi / n
-    return b
-
-
 def test_sphere_full_size_block():
     torch = pytest.importorskip("torch")
-    need_host_memory(20)
+    need_host_memory(80)
     cfg = W.sphere_mach15(n=96, nv=20, scheme=1)
     n, nv = cfg["nx"], cfg["nvx"] * cfg["nvy"] * cfg["nvz"]
-    lo, hi, steps = 28, 68, 2
-    lead = 20
+    m, steps, lead = 68, 2, 20
     s = lead_in(cfg, dvm.FP32, lead)
+    bcfg = corner_block(cfg, m, s.dt)
+    # the block's geometry and control volumes are the full grid's bit for
+    # bit (a1 parity at this size), every cut cell well inside
+    gg = s.geometry3d()
+    gb = oracle.geometry3d(bcfg)
+    assert gb["status"] == 0
+    for k in GEO3:
+        assert np.array_equal(gb[k], block_view(gg[k], n, m)), k
+    assert np.array_equal(gb["ax"], block_view(gg["ax"], n, m, (n, n, n + 1)))
+    assert np.array_equal(gb["ay"], block_view(gg["ay"], n, m, (n, n + 1, n)))
+    assert np.array_equal(gb["az"], block_view(gg["az"], n, m, (n + 1, n, n)))
+    mb, rc = oracle.masters3d(bcfg, gb)
+    assert rc == 0
+    assert np.array_equal(full_index(mb, n, m), block_view(gg["master"], n, m))
+    e = m - 2 * steps
+    cut = np.argwhere((gb["type"] == oracle.CUT).reshape(m, m, m))
+    assert cut.max() < e
+
     full = torch.empty(s.state_size, dtype=torch.float32, device="cuda")
 
     def block():
         s.get_state(full)
-        v = full.view(n, n, n, nv)[lo:hi, lo:hi, lo:hi, :]
+        v = full.view(n, n, n, nv)[:m, :m, :m, :]
         return as64(v.contiguous().cpu().numpy()).ravel()
-
-    bcfg = sphere_block(cfg, lo, hi, s.dt)
-    # the block's geometry is the full grid's: every cut cell lies inside,
-    # away from the block faces
-    gb = oracle.geometry3d(bcfg)
-    assert gb["status"] == 0
-    tg = s.geometry3d()["type"].reshape(n, n, n)[lo:hi, lo:hi, lo:hi].ravel()
-    assert np.array_equal(gb["type"], tg)
-    cut = np.argwhere((gb["type"] == 1).reshape(hi - lo, hi - lo, hi - lo))
-    assert cut.min() >= 2 * steps and cut.max() < hi - lo - 2 * steps
 
     Fo = block()
     h = oracle.run3d(bcfg, Fo, steps)
@@ -176,10 +174,8 @@ def test_sphere_full_size_block():
     s.step(steps)
     Fg = block()
     del full
-    m = hi - lo
     inner = np.zeros((m, m, m), bool)
-    e = 2 * steps
-    inner[e:m - e, e:m - e, e:m - e] = True
+    inner[:e, :e, :e] = True
     inner = inner.ravel()
     mo = oracle.moments(bcfg, Fo)
     mg = oracle.moments(bcfg, Fg)
