@@ -55,7 +55,7 @@ class _Cfg(C.Structure):
         ("vbx", C.c_double), ("vby", C.c_double), ("mass", C.c_double), ("inertia", C.c_double),
         ("movable", C.c_int), ("Tw", C.c_double), ("nseg", C.c_int),
         ("Tw_seg", C.POINTER(C.c_double)), ("seg_dir", C.POINTER(C.c_double)),
-        ("axis", C.c_int), ("time_scheme", C.c_int),
+        ("axis", C.c_int), ("time_scheme", C.c_int), ("model", C.c_int), ("Pr", C.c_double),
     ]
 
 
@@ -105,6 +105,8 @@ def _load():
             lib.orc_masters3d.argtypes = [P, C.POINTER(_Geo3d), _PI32]
             lib.orc_run3d.argtypes = [P, _PD, C.c_int, C.POINTER(_Hist)]
             lib.orc_mass3d.argtypes = [P, _PD]; lib.orc_mass3d.restype = C.c_double
+            lib.orc_heat_flux.argtypes = [P, _PD, _PD]
+            lib.orc_equilibrium.argtypes = [P, C.c_double, _PD, C.c_double, _PD, _PD]
             _lib = lib
     return _lib
 
@@ -143,6 +145,8 @@ class _CfgHolder:
             s.seg_dir = _ptr(sd)
         s.axis = int(cfg.get("axis", 2))
         s.time_scheme = int(cfg.get("time_scheme", 0))   # 0 explicit, 1 semi-implicit (Eq. ImpSchemeDD)
+        s.model = int(cfg.get("model", 0))               # 0 BGK (Eq. BGKDD), 1 Shakhov (Eq. ShakhovDD)
+        s.Pr = float(cfg.get("Pr", 1.0))
         self.s = s
         self.cfg = cfg
 
@@ -228,6 +232,26 @@ def moments(cfg: dict, F: np.ndarray) -> dict:
     out = {k: np.zeros(nc) for k in ("rho", "ux", "uy", "uz", "T")}
     lib.orc_moments(_CfgHolder(cfg).ref, _ptr(np.ascontiguousarray(F)),
                     *[_ptr(out[k]) for k in ("rho", "ux", "uy", "uz", "T")])
+    return out
+
+
+def heat_flux(cfg: dict, fk: np.ndarray) -> tuple[np.ndarray, int]:
+    """Heat flux q (3 components) of one cell's state ``fk`` about its own
+    velocity (Eq. MacroscopicDDv in 2D, Sec. 2.1 in 3D)."""
+    q = np.zeros(3)
+    rc = _load().orc_heat_flux(_CfgHolder(cfg).ref, _ptr(np.ascontiguousarray(fk, np.float64)), _ptr(q))
+    return q, rc
+
+
+def equilibrium(cfg: dict, rho: float, u, T: float, q) -> np.ndarray:
+    """One cell's equilibrium of ``cfg['model']`` (BGK, Eq. BGKDD; Shakhov,
+    Eq. ShakhovDD) on the velocity grid, in the state layout."""
+    out = np.zeros(ncomp(cfg) * nvel(cfg))
+    u3 = np.zeros(3); u3[: len(u)] = u
+    q3 = np.zeros(3); q3[: len(q)] = q
+    rc = _load().orc_equilibrium(_CfgHolder(cfg).ref, float(rho), _ptr(u3), float(T), _ptr(q3), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_equilibrium: status {rc}")
     return out
 
 

@@ -9,7 +9,9 @@
  * (Eq. FluxDD), discrete diffuse reflection (Eq. BoundaryDDv), the 7-step
  * iteration of Sec. 3.3.5 and the Appendix A geometry.  With
  * time_scheme = ORC_IMEX the update is the first-order semi-implicit scheme
- * (Eq. ImpSchemeDD) instead, in 2D and 3D.
+ * (Eq. ImpSchemeDD) instead, in 2D and 3D.  With model = ORC_SHAKHOV the
+ * explicit scheme relaxes towards the Shakhov equilibrium (Eq. ShakhovDD in
+ * 2D, the form of Sec. 2.1 in 3D) with the heat flux of the control volume.
  */
 #include "dvm_oracle.h"
 #include <math.h>
@@ -290,6 +292,96 @@ int orc_moments(const orc_cfg *c, const double *F, double *rho, double *ux,
     return ORC_OK;
 }
 
+/* ---------------------------------------------------------- collision model */
+
+/* Heat flux of one cell's state about its velocity u (R = 1): reduced 2D
+ * q = sum (v - u)(|v - u|^2/2 f + g) dv (Eq. MacroscopicDDv), 3D
+ * q = sum (v - u)|v - u|^2/2 F dv (the heat flux of Sec. 2.1). */
+static void cell_heat_flux(const orc_cfg *c, const double *fk, const double *u, double *q)
+{
+    const int nv1 = c->nvx, nv2 = c->nvy, nv3 = c->dim == 3 ? c->nvz : 1;
+    const int nv = nv1 * nv2 * nv3;
+    const double dvx = (c->vxmax - c->vxmin) / nv1, dvy = (c->vymax - c->vymin) / nv2;
+    const double dvz = c->dim == 3 ? (c->vzmax - c->vzmin) / nv3 : 1.0;
+    double s[3] = {0, 0, 0};
+    for (int p3 = 0; p3 < nv3; ++p3)
+        for (int p2 = 0; p2 < nv2; ++p2)
+            for (int p1 = 0; p1 < nv1; ++p1) {
+                int p = (p3 * nv2 + p2) * nv1 + p1;
+                double ax = c->vxmin + p1 * dvx - u[0], ay = c->vymin + p2 * dvy - u[1];
+                double az = c->dim == 3 ? c->vzmin + p3 * dvz - u[2] : 0.0;
+                double w = 0.5 * (ax * ax + ay * ay + az * az) * fk[p];
+                if (c->dim == 2) w += fk[nv + p];
+                s[0] += ax * w; s[1] += ay * w; s[2] += az * w;
+            }
+    double dv = dvx * dvy * (c->dim == 3 ? dvz : 1.0);
+    q[0] = s[0] * dv; q[1] = s[1] * dv; q[2] = s[2] * dv;
+}
+
+/* Equilibrium of the collision model at velocity v (R = 1, P = rho T).
+ * BGK: the Maxwellian, and in 2D g = T/2 M (Eq. BGKDD).  Shakhov: the
+ * Maxwellian times 1 + (1 - Pr)(v - u).q (|v - u|^2/T - 5)/(5 P T) in 3D
+ * (Sec. 2.1); in 2D f and g of Eq. ShakhovDD, with -4 and -2 in place of -5. */
+static void equilibrium_at(const orc_cfg *c, double rho, const double *u, double T, const double *q,
+                           double vx, double vy, double vz, double *fe, double *ge)
+{
+    if (c->dim == 3) {
+        double M = maxw3d(rho, u[0], u[1], u[2], T, vx, vy, vz);
+        if (c->model == ORC_SHAKHOV) {
+            double ax = vx - u[0], ay = vy - u[1], az = vz - u[2];
+            double cq = ax * q[0] + ay * q[1] + az * q[2];
+            M *= 1.0 + (1.0 - c->Pr) * cq * ((ax * ax + ay * ay + az * az) / T - 5.0) / (5.0 * rho * T * T);
+        }
+        *fe = M;
+        return;
+    }
+    double M = maxw2d(rho, u[0], u[1], T, vx, vy);
+    double sf = 1.0, sg = 1.0;
+    if (c->model == ORC_SHAKHOV) {
+        double ax = vx - u[0], ay = vy - u[1];
+        double cq = ax * q[0] + ay * q[1];
+        double c2 = (ax * ax + ay * ay) / T;
+        double k = (1.0 - c->Pr) * cq / (5.0 * rho * T * T);
+        sf = 1.0 + k * (c2 - 4.0);
+        sg = 1.0 + k * (c2 - 2.0);
+    }
+    *fe = M * sf;
+    if (ge) *ge = T / 2.0 * M * sg;
+}
+
+static int model_ok(const orc_cfg *c)
+{
+    if (c->model == ORC_BGK) return 1;
+    return c->model == ORC_SHAKHOV && c->Pr >= 0 && c->time_scheme == ORC_EXPLICIT;
+}
+
+int orc_heat_flux(const orc_cfg *c, const double *fk, double *q)
+{
+    double rho, u[3], T;
+    int rc = cell_moments(c, fk, &rho, u, &T);
+    cell_heat_flux(c, fk, u, q);
+    return rc;
+}
+
+int orc_equilibrium(const orc_cfg *c, double rho, const double *u, double T,
+                    const double *q, double *fk)
+{
+    if (!model_ok(c) || !(rho > 0) || !(T > 0)) return ORC_ERR_ARG;
+    const int nv1 = c->nvx, nv2 = c->nvy, nv3 = c->dim == 3 ? c->nvz : 1;
+    const int nv = nv1 * nv2 * nv3;
+    const double dvx = (c->vxmax - c->vxmin) / nv1, dvy = (c->vymax - c->vymin) / nv2;
+    const double dvz = c->dim == 3 ? (c->vzmax - c->vzmin) / nv3 : 1.0;
+    for (int p3 = 0; p3 < nv3; ++p3)
+        for (int p2 = 0; p2 < nv2; ++p2)
+            for (int p1 = 0; p1 < nv1; ++p1) {
+                int p = (p3 * nv2 + p2) * nv1 + p1;
+                double vz = c->dim == 3 ? c->vzmin + p3 * dvz : 0.0;
+                equilibrium_at(c, rho, u, T, q, c->vxmin + p1 * dvx, c->vymin + p2 * dvy, vz, &fk[p],
+                               c->dim == 2 ? &fk[nv + p] : NULL);
+            }
+    return ORC_OK;
+}
+
 /* ---------------------------------------------------------------- 2D step */
 
 typedef struct {
@@ -487,6 +579,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
               double *theta_out, double *omega_out)
 {
     if (c->dim != 2 || c->nx < 2 || c->ny < 1 || c->nvx < 1 || c->nvy < 1) return ORC_ERR_ARG;
+    if (!model_ok(c)) return ORC_ERR_ARG;
     orc_ctx2d X;
     X.c = c; X.nx = c->nx; X.ny = c->ny; X.nv1 = c->nvx; X.nv2 = c->nvy;
     X.nv = X.nv1 * X.nv2;
@@ -511,6 +604,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
     double *Sn = malloc(sizeof(double) * nc), *Sp = malloc(sizeof(double) * nc);
     double *mrho = malloc(sizeof(double) * nc), *mux = malloc(sizeof(double) * nc);
     double *muy = malloc(sizeof(double) * nc), *mT = malloc(sizeof(double) * nc);
+    double *mq = calloc((size_t)nc * 3, sizeof(double));
     double *wphi = malloc(sizeof(double) * nc), *wux = malloc(sizeof(double) * nc);
     double *wuy = malloc(sizeof(double) * nc), *wT = malloc(sizeof(double) * nc);
     double *Fnew = malloc(sizeof(double) * nc * 2 * nv);
@@ -565,6 +659,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
             double u[3], r, T;
             if (cell_moments(c, F + m * 2 * nv, &r, u, &T)) nonphys = 1;
             mrho[m] = r; mux[m] = u[0]; muy[m] = u[1]; mT[m] = T;
+            if (c->model == ORC_SHAKHOV) cell_heat_flux(c, F + m * 2 * nv, u, mq + 3 * m);
         }
         if (nonphys) { err = ORC_ERR_NONPHYSICAL; break; }
         /* Step 4: wall density phi (Eq. BoundaryDDv) at every wall edge;
@@ -673,15 +768,17 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
                     if (imex_relax(c, dt, tau0, Fnew + m * 2 * nv)) badrelax = 1;
                     continue;
                 }
-                for (int comp = 0; comp < 2; ++comp)
-                    for (int p2 = 0; p2 < X.nv2; ++p2)
-                        for (int p1 = 0; p1 < X.nv1; ++p1) {
-                            int p = p2 * X.nv1 + p1;
+                const double um[3] = {mux[m], muy[m], 0.0};
+                for (int p2 = 0; p2 < X.nv2; ++p2)
+                    for (int p1 = 0; p1 < X.nv1; ++p1) {
+                        int p = p2 * X.nv1 + p1;
+                        double eq[2];
+                        equilibrium_at(c, mrho[m], um, mT[m], mq + 3 * m, vx[p1], vy[p2], 0.0, &eq[0], &eq[1]);
+                        for (int comp = 0; comp < 2; ++comp) {
                             double fcv = F[(m * 2 + comp) * nv + p];
-                            double feq = maxw2d(mrho[m], mux[m], muy[m], mT[m], vx[p1], vy[p2]);
-                            if (comp == 1) feq = mT[m] / 2.0 * feq;
-                            Fnew[(m * 2 + comp) * nv + p] = a * fcv - b * R[comp * nv + p] + a * r * (feq - fcv);
+                            Fnew[(m * 2 + comp) * nv + p] = a * fcv - b * R[comp * nv + p] + a * r * (eq[comp] - fcv);
                         }
+                    }
             }
             free(R);
         }
@@ -719,7 +816,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
     if (omega_out) *omega_out = omega;
     free_geo2d(&ga); free_geo2d(&gb);
     free(master); free(mstart); free(mlist); free(cnt); free(Sn); free(Sp);
-    free(mrho); free(mux); free(muy); free(mT);
+    free(mrho); free(mux); free(muy); free(mT); free(mq);
     free(wphi); free(wux); free(wuy); free(wT); free(Fnew); free(vx); free(vy);
     for (int s = 0; s < 4; ++s) free(X.ghost[s]);
     return err;
@@ -977,7 +1074,7 @@ double orc_mass3d(const orc_cfg *c, const double *F)
 
 int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
 {
-    if (c->dim != 3 || c->movable) return ORC_ERR_ARG;
+    if (c->dim != 3 || c->movable || !model_ok(c)) return ORC_ERR_ARG;
     orc_ctx3d X;
     X.c = c; X.nx = c->nx; X.ny = c->ny; X.nz = c->nz;
     X.nv1 = c->nvx; X.nv2 = c->nvy; X.nv3 = c->nvz; X.nv = X.nv1 * X.nv2 * X.nv3;
@@ -1013,6 +1110,7 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
     int32_t *mstart = malloc(sizeof(int32_t) * (nc + 1)), *mlist = malloc(sizeof(int32_t) * nc), *cnt = malloc(sizeof(int32_t) * nc);
     double *S = malloc(sizeof(double) * nc);
     double *mr = malloc(sizeof(double) * nc), *mu = malloc(sizeof(double) * 3 * nc), *mT = malloc(sizeof(double) * nc);
+    double *mq = calloc((size_t)nc * 3, sizeof(double));
     double *wphi = malloc(sizeof(double) * nc), *wu = malloc(sizeof(double) * 3 * nc), *wT = malloc(sizeof(double) * nc);
     double *Fnew = malloc(sizeof(double) * nc * nv);
     double *vx = malloc(sizeof(double) * X.nv1), *vy = malloc(sizeof(double) * X.nv2), *vz = malloc(sizeof(double) * X.nv3);
@@ -1048,6 +1146,7 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
             double u[3], r, T;
             if (cell_moments(c, F + m * nv, &r, u, &T)) nonphys = 1;
             mr[m] = r; mu[3 * m] = u[0]; mu[3 * m + 1] = u[1]; mu[3 * m + 2] = u[2]; mT[m] = T;
+            if (c->model == ORC_SHAKHOV) cell_heat_flux(c, F + m * nv, u, mq + 3 * m);
         }
         if (nonphys) { err = ORC_ERR_NONPHYSICAL; break; }
         /* wall density and stress (3D forms of Eqs. BoundaryTD, StressTensorDD) */
@@ -1154,7 +1253,8 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
                         for (int p1 = 0; p1 < X.nv1; ++p1) {
                             int p = (p3 * X.nv2 + p2) * X.nv1 + p1;
                             double fcv = F[m * nv + p];
-                            double feq = maxw3d(mr[m], mu[3 * m], mu[3 * m + 1], mu[3 * m + 2], mT[m], vx[p1], vy[p2], vz[p3]);
+                            double feq;
+                            equilibrium_at(c, mr[m], mu + 3 * m, mT[m], mq + 3 * m, vx[p1], vy[p2], vz[p3], &feq, NULL);
                             Fnew[m * nv + p] = a * fcv - b * R[p] + a * r * (feq - fcv);
                         }
             }
@@ -1184,7 +1284,7 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
         }
     }
     free_geo3d(&geo);
-    free(master); free(mstart); free(mlist); free(cnt); free(S); free(mr); free(mu); free(mT);
+    free(master); free(mstart); free(mlist); free(cnt); free(S); free(mr); free(mu); free(mT); free(mq);
     free(wphi); free(wu); free(wT); free(Fnew); free(vx); free(vy); free(vz);
     for (int s = 0; s < 6; ++s) free(X.ghost[s]);
     return err;
@@ -1365,6 +1465,7 @@ int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *Jout, 
                   double *gTw, double *gbc0, double *gbc1, double *gbc2, double *gbc3)
 {
     if (c->dim != 2 || c->movable || c->shape == ORC_SHAPE_NONE || nsteps < 0) return ORC_ERR_ARG;
+    if (c->model != ORC_BGK || c->time_scheme != ORC_EXPLICIT) return ORC_ERR_ARG;
     orc_ctx2d X;
     X.c = c; X.nx = c->nx; X.ny = c->ny; X.nv1 = c->nvx; X.nv2 = c->nvy;
     X.nv = X.nv1 * X.nv2;

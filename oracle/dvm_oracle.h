@@ -29,6 +29,7 @@ enum { ORC_SHAPE_NONE = 0, ORC_SHAPE_CIRCLE = 1, ORC_SHAPE_ELLIPSE = 2,
        ORC_SHAPE_SPHERE = 3 };
 enum { ORC_UPWIND = 0, ORC_MUSCL = 1 };
 enum { ORC_EXPLICIT = 0, ORC_IMEX = 1 };  /* Eq. ExSchemeDD | Eq. ImpSchemeDD */
+enum { ORC_BGK = 0, ORC_SHAKHOV = 1 };    /* Eq. BGKDD | Eq. ShakhovDD (Sec. 2.1) */
 
 /* Problem statement.  2D uses the x/y fields, 3D also the z ones. */
 typedef struct {
@@ -60,6 +61,8 @@ typedef struct {
                                       (0 x, 1 y, 2 z) */
     int time_scheme;               /* ORC_EXPLICIT (Eq. ExSchemeDD) or ORC_IMEX
                                       (first-order semi-implicit, Eq. ImpSchemeDD) */
+    int model;                     /* ORC_BGK or ORC_SHAKHOV (explicit scheme only) */
+    double Pr;                     /* Prandtl number of the Shakhov model */
 } orc_cfg;
 
 /* Geometry of one time level (2D): every array is caller-owned.          */
@@ -94,6 +97,17 @@ int orc_init_maxwellian(const orc_cfg *c, const double *rho, const double *ux,
                         double *F);
 int orc_moments(const orc_cfg *c, const double *F, double *rho, double *ux,
                 double *uy, double *uz, double *T);
+
+/* Heat flux q[3] of one cell's state fk (layout [component][p]) about its own
+ * velocity: reduced 2D q = sum (v - u)(|v - u|^2/2 f + g) dv (Eq.
+ * MacroscopicDDv), 3D q = sum (v - u)|v - u|^2/2 F dv (Sec. 2.1). */
+int orc_heat_flux(const orc_cfg *c, const double *fk, double *q);
+
+/* Equilibrium of the configured collision model for (rho, u[3], T, q[3])
+ * on the velocity grid, into one cell's state fk: BGK (Eq. BGKDD, the 3D
+ * Maxwellian) or Shakhov (Eq. ShakhovDD in 2D, the 3D form of Sec. 2.1). */
+int orc_equilibrium(const orc_cfg *c, double rho, const double *u, double T,
+                    const double *q, double *fk);
 int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
               double *theta_out, double *omega_out);
 double orc_mass2d(const orc_cfg *c, const double *F);
