@@ -53,6 +53,7 @@ typedef enum {
 enum { DVM_FP32 = 32, DVM_FP64 = 64 };
 enum { DVM_UPWIND = 0, DVM_MUSCL = 1 };
 enum { DVM_EXPLICIT = 0, DVM_IMEX = 1 };   /* time schemes, see dvm_set_time_scheme */
+enum { DVM_BGK = 0, DVM_SHAKHOV = 1 };     /* collision models, see dvm_set_collision_model */
 enum { DVM_BC_PERIODIC = 0, DVM_BC_MAXWELLIAN = 1, DVM_BC_ZEROGRAD = 2 };
 enum { DVM_SHAPE_NONE = 0, DVM_SHAPE_CIRCLE = 1, DVM_SHAPE_ELLIPSE = 2, DVM_SHAPE_SPHERE = 3 };
 enum { DVM_GAS = 0, DVM_CUT = 1, DVM_SOLID = 2 };
@@ -130,6 +131,20 @@ int dvm_set_bc(dvm_ctx *ctx, int side, int kind, const double *state);
  * limit of the explicit scheme at small Knudsen numbers.  The drag adjoint
  * differentiates the explicit scheme only.  Errors: DVM_ERR_ARG. */
 int dvm_set_time_scheme(dvm_ctx *ctx, int scheme);
+
+/* Collision model (Sec. 2.1-2.2): DVM_BGK (Eq. BGKDD, the default) or
+ * DVM_SHAKHOV with Prandtl number Pr >= 0 (Eq. ShakhovDD): the explicit
+ * scheme relaxes towards
+ *   f_S = M [1 + (1 - Pr) c.q (|c|^2/T - 4) / (5 P T)],
+ *   g_S = T/2 M [1 + (1 - Pr) c.q (|c|^2/T - 2) / (5 P T)],
+ * c = v - u, P = rho T (R = 1), with the heat flux
+ * q = sum c (|c|^2/2 f + g) dv of the control volume at t^n (Eq.
+ * MacroscopicDDv).  Pr = 1 is the BGK model.  The Shakhov model is
+ * implemented for 2D problems with a fixed or no obstacle and the explicit
+ * scheme; other combinations return DVM_ERR_UNSUPPORTED here, from
+ * dvm_set_time_scheme or from dvm_step (a moving obstacle), and the drag
+ * adjoint is BGK only.  Errors: DVM_ERR_ARG (model or Pr), DVM_ERR_UNSUPPORTED. */
+int dvm_set_collision_model(dvm_ctx *ctx, int model, double Pr);
 
 /* Place the obstacle and build the Appendix A geometry on the device (level
  * set, cell types, edge lengths, wall edges, areas, control volumes).

@@ -171,7 +171,23 @@ static cudaError_t st_zero_solid(dvm_ctx *c) { return c->dim == 2 ? zero_solid2d
 static cudaError_t st_partials(dvm_ctx *c) { return c->dim == 2 ? partials_from_state2d(c) : partials_from_state3d(c); }
 static cudaError_t st_pack(dvm_ctx *c, const void *pub, void *dev) { return c->dim == 2 ? pack2d(c, pub, dev) : pack3d(c, pub, dev); }
 static cudaError_t st_unpack(dvm_ctx *c, const void *dev, void *pub) { return c->dim == 2 ? unpack2d(c, dev, pub) : unpack3d(c, dev, pub); }
-static cudaError_t st_step(dvm_ctx *c) { return c->dim == 2 ? step2d(c) : step3d(c); }
+// One time step; with the Shakhov model (2D) its relaxation term follows
+// the step (Eq. ShakhovDD).
+static cudaError_t st_step(dvm_ctx *c)
+{
+    cudaError_t e = c->dim == 2 ? step2d(c) : step3d(c);
+    if (e == cudaSuccess && c->model == DVM_SHAKHOV) e = shakhov2d(c);
+    return e;
+}
+
+// Why the Shakhov model cannot run on this context (nullptr: it can).
+static const char *shakhov_unsupported(const dvm_ctx *c)
+{
+    if (c->dim != 2) return "Shakhov model: 2D problems only in this library version";
+    if (c->time_scheme != DVM_EXPLICIT) return "Shakhov model: the explicit time scheme only";
+    if (c->moving) return "Shakhov model: fixed obstacles only in this library version";
+    return nullptr;
+}
 
 constexpr int kGraphMinSteps = 8;    // shorter runs are not worth a capture
 constexpr size_t kGraphKeep = 64;    // launched graphs kept before a release
@@ -790,6 +806,8 @@ int dvm_step_async(dvm_ctx *c, int nsteps)
         }
     if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return DVM_ERR_ARG; }
+    if (c->model == DVM_SHAKHOV)
+        if (const char *why = shakhov_unsupported(c)) { set_error(why); return DVM_ERR_UNSUPPORTED; }
     int s = 0;
     // the first step after a state change (control-volume fusion), short runs
     // and runs with per-launch timing go launch by launch; the rest as
@@ -816,7 +834,24 @@ int dvm_set_time_scheme(dvm_ctx *c, int scheme)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
     if (scheme != DVM_EXPLICIT && scheme != DVM_IMEX) { set_error("time scheme must be DVM_EXPLICIT or DVM_IMEX"); return DVM_ERR_ARG; }
+    if (scheme == DVM_IMEX && c->model == DVM_SHAKHOV) {
+        set_error("Shakhov model: the explicit time scheme only");
+        return DVM_ERR_UNSUPPORTED;
+    }
     c->time_scheme = scheme;
+    return DVM_OK;
+}
+
+int dvm_set_collision_model(dvm_ctx *c, int model, double Pr)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (model != DVM_BGK && model != DVM_SHAKHOV) { set_error("collision model must be DVM_BGK or DVM_SHAKHOV"); return DVM_ERR_ARG; }
+    if (model == DVM_SHAKHOV) {
+        if (!(Pr >= 0) || !std::isfinite(Pr)) { set_error("Prandtl number must be finite and >= 0"); return DVM_ERR_ARG; }
+        if (const char *why = shakhov_unsupported(c)) { set_error(why); return DVM_ERR_UNSUPPORTED; }
+    }
+    c->model = model;
+    c->Pr = model == DVM_SHAKHOV ? Pr : 1.0;
     return DVM_OK;
 }
 
@@ -1111,6 +1146,7 @@ int dvm_drag_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, double *J, do
         set_error("dvm_drag_adjoint: the explicit time scheme only");
         return DVM_ERR_UNSUPPORTED;
     }
+    if (c->model != DVM_BGK) { set_error("dvm_drag_adjoint: the BGK model only"); return DVM_ERR_UNSUPPORTED; }
     if (c->body.shape == DVM_SHAPE_NONE || c->moving) {
         set_error("dvm_drag_adjoint: needs a fixed obstacle"); return DVM_ERR_UNSUPPORTED;
     }

@@ -183,6 +183,8 @@ struct dvm_ctx {
     int ev_used;
     bool graphs;                  // dvm_step replays two-step CUDA graphs (dvm_graphs)
     int time_scheme;              // DVM_EXPLICIT or DVM_IMEX (dvm_set_time_scheme)
+    int model;                    // DVM_BGK or DVM_SHAKHOV (dvm_set_collision_model)
+    double Pr;                    // Prandtl number of the Shakhov model
     void *snap_f, *snap_part;     // dvm_step: state and moment sums at the last checked step
     void *snap_scratch;           // dvm_step: moment sums of the state check
     void *snap_body;              // dvm_step: rigid-body record at the last checked step
@@ -209,6 +211,7 @@ cudaError_t tables2d(dvm_ctx *c);
 cudaError_t partials_from_state2d(dvm_ctx *c);
 cudaError_t init_maxwellian2d(dvm_ctx *c, const double *d_prim);
 cudaError_t step2d(dvm_ctx *c);
+cudaError_t shakhov2d(dvm_ctx *c);                             // Eq. ShakhovDD term after a step (dvm_shakhov2d.cu)
 cudaError_t fusion2d(dvm_ctx *c, void *f, void *part);          // Eq. FusionDD on a buffer
 cudaError_t mass2d(dvm_ctx *c, double *d_scratch, double *d_out);
 cudaError_t moments_out2d(dvm_ctx *c, double *d_out);

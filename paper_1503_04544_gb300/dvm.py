@@ -24,6 +24,8 @@ OK, ERR_ARG, ERR_CFL, ERR_GEOMETRY, ERR_NONPHYSICAL, ERR_CUDA, ERR_OOM, ERR_STAT
 FP32, FP64 = 32, 64
 UPWIND, MUSCL = 0, 1
 PERIODIC, MAXWELLIAN, ZEROGRAD = 0, 1, 2
+EXPLICIT, IMEX = 0, 1
+BGK, SHAKHOV = 0, 1
 
 
 class DVMError(RuntimeError):
@@ -79,6 +81,7 @@ SIGNATURES = {
     "dvm_save": [_P, C.c_char_p],
     "dvm_load": [_P, C.c_char_p],
     "dvm_set_time_scheme": [_P, C.c_int],
+    "dvm_set_collision_model": [_P, C.c_int, C.c_double],
     "dvm_check": [_P],
     "dvm_moments": [_P, _PD, _PD, _PD, _PD, _PD],
     "dvm_wall_force": [_P, _PD, _PD],
@@ -158,6 +161,8 @@ class Solver:
             self.set_body(cfg)
         if int(cfg.get("time_scheme", 0)):
             self.set_time_scheme(int(cfg["time_scheme"]))
+        if int(cfg.get("model", 0)):
+            self.set_collision_model(int(cfg["model"]), float(cfg.get("Pr", 1.0)))
         dt = C.c_double()
         tau0 = C.c_double()
         nc = C.c_longlong()
@@ -232,6 +237,10 @@ class Solver:
     def set_time_scheme(self, scheme: int):
         """0: explicit (Eq. ExSchemeDD), 1: first-order semi-implicit (Eq. ImpSchemeDD)."""
         _check(load().dvm_set_time_scheme(self.h, int(scheme)))
+
+    def set_collision_model(self, model: int, Pr: float = 1.0):
+        """0: BGK (Eq. BGKDD), 1: Shakhov with Prandtl number Pr (Eq. ShakhovDD)."""
+        _check(load().dvm_set_collision_model(self.h, int(model), float(Pr)))
 
     def rollback(self, enable: bool = True):
         """dvm_step leaves the state at the last good step on a failure (on by default)."""

@@ -9,7 +9,8 @@ body; that state (exactly, widened to FP64) is then the common start of a
 few further steps on both sides.
 
 - Cylinder, 256^2 cells x 32^2 velocities, MUSCL: the whole state, FP64 and
-  FP32, explicit and semi-implicit (Eqs. ExSchemeDD, ImpSchemeDD).
+  FP32, explicit and semi-implicit (Eqs. ExSchemeDD, ImpSchemeDD), and the
+  Shakhov model (Eq. ShakhovDD, Pr = 2/3).
 - Rotating ellipse, 512^2 x 40^2, upwind, freely moving body: the whole
   state, the torque history and the body angle and angular velocity.
 - Sphere, 96^3 x 20^3, MUSCL, FP32: a full step at this size takes the
@@ -81,11 +82,14 @@ def lead_in(cfg, prec, steps):
     return s
 
 
-@pytest.mark.parametrize("prec,scheme", [(dvm.FP64, 0), (dvm.FP32, 0), (dvm.FP32, 1)],
-                         ids=["fp64-explicit", "fp32-explicit", "fp32-semi-implicit"])
-def test_cylinder_full_size(prec, scheme):
+@pytest.mark.parametrize("prec,scheme,model", [(dvm.FP64, 0, 0), (dvm.FP32, 0, 0), (dvm.FP32, 1, 0),
+                                               (dvm.FP32, 0, 1)],
+                         ids=["fp64-explicit", "fp32-explicit", "fp32-semi-implicit", "fp32-shakhov"])
+def test_cylinder_full_size(prec, scheme, model):
     cfg = W.cylinder_mach2(nx=256, nv=32, scheme=1)
     cfg["time_scheme"] = scheme
+    if model:
+        cfg.update(model=dvm.SHAKHOV, Pr=2.0 / 3.0)
     need_host_memory(6)
     lead, n = 40, 10
     s = lead_in(cfg, prec, lead)
