@@ -106,7 +106,8 @@ def test_cylinder_full_size(prec, scheme, model):
     assert max(errs.values()) < TOL[prec], errs
     hg = s.history(lead + n)
     assert rel_inf(hg["Fx"][lead:], h["Fx"]) < TOL[prec]
-    assert Fg.min() >= 0
+    if not model:
+        assert Fg.min() >= 0      # the Shakhov equilibrium itself can be negative in its tails
     s.close()
 
 

@@ -103,7 +103,7 @@ def test_ragged_no_body(prec, scheme):
 def test_heat_flux_relaxes_at_rate_pr(Pr):
     """Homogeneous periodic gas with a heat flux: each explicit step
     multiplies it by 1 - Pr dt/tau and leaves rho, u, T fixed."""
-    n, nv, win = 4, 80, 12.0
+    n, nv, win = 4, 64, 12.0
     cfg = shakhov(W.base2d(n, n, nv, win, Kn=0.5, bc=[0] * 6), Pr=Pr)
     rho, u, T, q = 1.2, (0.4, -0.3), 1.3, (0.2, -0.15)
     start = oracle.equilibrium(dict(cfg, model=1, Pr=0.0), rho, u, T, q)
