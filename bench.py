@@ -12,7 +12,7 @@ non-solid cells.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
                   [--workload cylinder|sphere|ellipse|bump] [--impl gb300|reference]
-                  [--time-scheme explicit|imex]
+                  [--time-scheme explicit|imex] [--model bgk|shakhov]
 
 For N > 1 each rank runs an independent replica (the path is not sharded
 here); value = pairs updated by all ranks / max-over-ranks time.
@@ -74,6 +74,7 @@ def config_dict(cfg, prec, nsolid_free, extra=None):
         "velocities": vels,
         "scheme": "muscl-minmod" if cfg.get("scheme", 0) == 1 else "upwind",
         "time_scheme": "semi-implicit" if cfg.get("time_scheme", 0) == 1 else "explicit",
+        "collision": "shakhov, Pr 2/3" if cfg.get("model", 0) == 1 else "bgk",
         "precision": prec,
         "pairs_per_step": nsolid_free,
         "l2": "inputs larger than L2 (state per copy > 129 MB)",
@@ -265,6 +266,8 @@ def run_reference(args):
     cfg = workload(args.workload)
     if args.time_scheme == "imex":
         cfg["time_scheme"] = 1
+    if args.model == "shakhov":
+        cfg.update(model=1, Pr=2.0 / 3.0)
     cb = cpu_baseline(cfg, budget_s=60.0, max_steps=max(1, min(args.steps, 8)))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -286,6 +289,8 @@ def main():
     ap.add_argument("--workload", default="cylinder")
     ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit",
                     help="explicit (Eq. ExSchemeDD) or first-order semi-implicit (Eq. ImpSchemeDD) steps")
+    ap.add_argument("--model", choices=["bgk", "shakhov"], default="bgk",
+                    help="collision model: BGK (Eq. BGKDD) or Shakhov with Pr = 2/3 (Eq. ShakhovDD, 2D)")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the drag-gradient cost measurement")
@@ -311,6 +316,8 @@ def main():
     cfg = workload(args.workload)
     if args.time_scheme == "imex":
         cfg["time_scheme"] = 1
+    if args.model == "shakhov":
+        cfg.update(model=1, Pr=2.0 / 3.0)
     prec = dvm.FP32 if args.precision == "fp32" else dvm.FP64
     # a dedicated stream: the library enqueues on it and the events below
     # are recorded on it
@@ -421,7 +428,8 @@ def main():
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(cfg)
-        if world == 1 and args.workload == "cylinder" and args.time_scheme == "explicit" and not args.no_adjoint:
+        if (world == 1 and args.workload == "cylinder" and args.time_scheme == "explicit" and args.model == "bgk"
+                and not args.no_adjoint):
             line["adjoint"] = adjoint_cost(prec == dvm.FP32)
         print(json.dumps(line), flush=True)
     s.close()

@@ -45,8 +45,15 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--checkpoint-every", type=int, default=20)
+    ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit")
+    ap.add_argument("--model", choices=["bgk", "shakhov"], default="bgk",
+                    help="collision model (Shakhov: Pr = 2/3, 2D)")
     args = ap.parse_args(argv)
     cfg = problem(args.workload, args.cells, args.nv, args.scheme)
+    if args.time_scheme == "imex":
+        cfg["time_scheme"] = 1
+    if args.model == "shakhov":
+        cfg.update(model=1, Pr=2.0 / 3.0)
     s = dvm.Solver(cfg, dvm.FP32 if args.precision == "fp32" else dvm.FP64)
     s.init_maxwellian()
     if args.workload == "adjoint":
