@@ -354,6 +354,13 @@ def main():
     ms = e0.elapsed_time(e1)
     bulk_ms, nb = s.kernel_time()
     s.timing(False)
+    shak_ms, ns = 0.0, 0
+    if cfg.get("model", 0) == 1:
+        # the Shakhov term's kernel, timed over a second run of the same steps
+        s.timing(2)
+        s.step_async(min(args.steps, 500))
+        shak_ms, ns = s.kernel_time()
+        s.timing(False)
     barrier()
 
     # end to end through the public API with pinned host buffers
@@ -393,7 +400,26 @@ def main():
                     "bytes_per_pair": bytes_per_pair,
                     "bulk_ms_per_launch": avg_bulk_s * 1e3,
                     "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)}
-        if prec == dvm.FP64 and not dim3 and cfg.get("scheme", 1) == 1:
+        if ns:
+            # Shakhov: k_shakhov reads F^n of every gas cell (heat flux) and
+            # reads and writes F^{n+1}: 3 x 2 components per pair
+            avg_s = shak_ms / ns / 1e3
+            sb = 3 * s.ncomp * s.elem
+            ach = pairs_per_step * sb / avg_s / 1e9
+            shak = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "frac_of_nominal": ach / NOMINAL_HBM_GBS,
+                    "traffic": recorded_traffic(f"k_shakhov_{args.workload}_{args.precision}.md",
+                                                os.path.join(ROOT, "paper_1503_04544_gb300", "csrc",
+                                                             "dvm_shakhov2d.cu")),
+                    "kernel": "k_shakhov (heat flux of F^n + Shakhov term on F^{n+1} + moments)",
+                    "peak_source": f"{peak_kind} HBM copy bandwidth", "bytes_per_pair": sb,
+                    "ms_per_launch": avg_s * 1e3, "share_of_step": avg_s * 1e3 / (ms / args.steps)}
+            if avg_s > avg_bulk_s:
+                shak["k_bulk"] = roofline
+                roofline = shak
+            else:
+                roofline["k_shakhov"] = shak
+        if prec == dvm.FP64 and not dim3 and cfg.get("scheme", 1) == 1 and roofline["kernel"].startswith("k_bulk"):
             # the FP64 step is bound by the FP64 pipe on this part: report
             # that ceiling, with the HBM view beside it
             gflops = FP64_FLOPS_PER_PAIR * bulk_pairs / avg_bulk_s / 1e9

@@ -290,11 +290,12 @@ int dvm_drag_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, double *J, 
                      double *gbc0, double *gbc1, double *gbc2, double *gbc3, double *gprim0,
                      double *ms_forward, double *ms_reverse);
 
-/* Live timing of the dominant kernel (the fused bulk stream-and-relax
- * kernel): when enabled, every step records a CUDA event pair around its
- * launch on the context's stream.  dvm_kernel_time synchronises the stream,
- * returns the summed duration in milliseconds and the number of timed
- * launches, and clears the record. */
+/* Live timing of one kernel: enable = 1 the fused bulk stream-and-relax
+ * kernel, 2 the Shakhov term (dvm_set_collision_model), 0 off.  Every step
+ * records a CUDA event pair around that kernel's launch on the context's
+ * stream.  dvm_kernel_time synchronises the stream, returns the summed
+ * duration in milliseconds and the number of timed launches, and clears the
+ * record. */
 int dvm_timing(dvm_ctx *ctx, int enable);
 int dvm_kernel_time(dvm_ctx *ctx, double *bulk_ms, long long *launches);
 

@@ -22,9 +22,11 @@ int cuda_fail(cudaError_t e, const char *where)
     return e == cudaErrorMemoryAllocation ? DVM_ERR_OOM : DVM_ERR_CUDA;
 }
 
-cudaError_t timing_mark(dvm_ctx *c, int which)
+cudaError_t timing_mark(dvm_ctx *c, int which) { return timing_mark_kernel(c, 1, which); }
+
+cudaError_t timing_mark_kernel(dvm_ctx *c, int kernel, int which)
 {
-    if (!c->timing) return cudaSuccess;
+    if (c->timing != kernel) return cudaSuccess;
     auto *pool = static_cast<std::vector<cudaEvent_t> *>(c->ev_pool);
     const size_t need = 2 * (size_t)(c->ev_used + 1);
     while (pool->size() < need) {
@@ -1166,7 +1168,7 @@ int dvm_drag_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, double *J, do
 int dvm_timing(dvm_ctx *c, int enable)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
-    c->timing = enable != 0;
+    c->timing = enable == 2 ? 2 : (enable != 0 ? 1 : 0);
     c->ev_used = 0;
     return DVM_OK;
 }

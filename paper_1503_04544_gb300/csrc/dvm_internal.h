@@ -178,7 +178,7 @@ struct dvm_ctx {
     void *adj;                    // adjoint workspace (dvm_adjoint2d.cu)
     uint32_t *rec_bits;           // if set, the 2D MUSCL bulk kernel records its limiter branches here
     bool have_state, have_geo, need_fusion, moving;
-    bool timing;
+    int timing;                   // dvm_timing: 0 off, 1 the bulk kernel, 2 the Shakhov kernel
     void *ev_pool;                // std::vector<cudaEvent_t> of start/stop pairs
     int ev_used;
     bool graphs;                  // dvm_step replays two-step CUDA graphs (dvm_graphs)
@@ -222,6 +222,7 @@ cudaError_t zero_solid2d(dvm_ctx *c);                            // both state b
 cudaError_t halo2d(dvm_ctx *c, int buf);                         // periodic / zero-gradient padding
 cudaError_t members2d(dvm_ctx *c, bool moving);                  // control-volume records
 cudaError_t timing_mark(dvm_ctx *c, int which);   // 0: before, 1: after the bulk kernel
+cudaError_t timing_mark_kernel(dvm_ctx *c, int kernel, int which);   // the same for kernel 1 (bulk) or 2 (Shakhov)
 int make_tensor_maps2d(dvm_ctx *c);                // TMA descriptors of f[0], f[1]
 int encode_tensor_map2d(dvm_ctx *c, void *buf, CUtensorMap *map);
 int encode_bits_map2d(dvm_ctx *c, void *buf, CUtensorMap *map);  // limiter-branch words (bits_pitch rows)

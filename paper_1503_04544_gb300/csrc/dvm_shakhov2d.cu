@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(32 * kMomChunks)
     if (gas) {
         const long pm = pcell(g, m);
         const V *fv = reinterpret_cast<const V *>(fin);
+#pragma unroll 4
         for (int q = q0; q < q1; ++q) {
             T a[W], b[W];
             vld<T>(fv + (long)q * 2 * g.slab + pm, a);
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(32 * kMomChunks)
         long mir[4];
         mirrors(g, i, j, mir);
         V *fo = reinterpret_cast<V *>(fout);
+#pragma unroll 4
         for (int q = q0; q < q1; ++q) {
             V *pa = fo + (long)q * 2 * g.slab, *pb = pa + g.slab;
             T a[W], b[W];
@@ -160,11 +162,14 @@ cudaError_t shakhov2d_t(dvm_ctx *c)
     T *fout = (T *)c->f[c->cur], *pout = (T *)c->part[c->cur];
     const Grid2D g = grid2d(c);
     const dim3 grid((unsigned)((c->nx + 31) / 32), (unsigned)c->ny), block(32, kMomChunks);
+    cudaError_t e = timing_mark_kernel(c, 2, 0);
+    if (e != cudaSuccess) return e;
     k_shakhov<T><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), T(1.0 - c->Pr), fin, pin, fout, pout,
                                                  (const VCoef<T> *)c->vtab, c->master, c->geo[c->gcur].type,
                                                  c->d_err);
     c->launches += 1;
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return timing_mark_kernel(c, 2, 1);
 }
 
 }  // namespace

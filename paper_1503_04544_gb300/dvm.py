@@ -332,8 +332,10 @@ class Solver:
                     ms_reverse=float(tr[0]))
 
     # -------------------------------------------------------------- instrumentation
-    def timing(self, enable: bool):
-        _check(load().dvm_timing(self.h, int(bool(enable))))
+    def timing(self, enable):
+        """Event timing of one kernel per step: True/1 the bulk kernel, 2 the
+        Shakhov term, False/0 off."""
+        _check(load().dvm_timing(self.h, int(enable)))
 
     def kernel_time(self):
         ms = C.c_double()
