@@ -77,7 +77,6 @@ __global__ void __launch_bounds__(32 * kMomChunks)
     if (gas) {
         const long pm = pcell(g, m);
         const V *fv = reinterpret_cast<const V *>(fin);
-#pragma unroll 4
         for (int q = q0; q < q1; ++q) {
             T a[W], b[W];
             vld<T>(fv + (long)q * 2 * g.slab + pm, a);
@@ -113,7 +112,6 @@ __global__ void __launch_bounds__(32 * kMomChunks)
         long mir[4];
         mirrors(g, i, j, mir);
         V *fo = reinterpret_cast<V *>(fout);
-#pragma unroll 4
         for (int q = q0; q < q1; ++q) {
             V *pa = fo + (long)q * 2 * g.slab, *pb = pa + g.slab;
             T a[W], b[W];
