@@ -139,8 +139,9 @@ int dvm_set_time_scheme(dvm_ctx *ctx, int scheme);
  *   g_S = T/2 M [1 + (1 - Pr) c.q (|c|^2/T - 2) / (5 P T)],
  * c = v - u, P = rho T (R = 1), with the heat flux
  * q = sum c (|c|^2/2 f + g) dv of the control volume at t^n (Eq.
- * MacroscopicDDv).  Pr = 1 is the BGK model.  The Shakhov model is
- * implemented for 2D problems with a fixed or no obstacle and the explicit
+ * MacroscopicDDv); in 3D F_S = M [1 + (1 - Pr) c.q (|c|^2/T - 5) / (5 P T)]
+ * with q = sum c |c|^2/2 F dv (Sec. 2.1).  Pr = 1 is the BGK model.  The
+ * Shakhov model is implemented with a fixed or no obstacle and the explicit
  * scheme; other combinations return DVM_ERR_UNSUPPORTED here, from
  * dvm_set_time_scheme or from dvm_step (a moving obstacle), and the drag
  * adjoint is BGK only.  Errors: DVM_ERR_ARG (model or Pr), DVM_ERR_UNSUPPORTED. */

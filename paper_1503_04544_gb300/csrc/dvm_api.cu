@@ -173,19 +173,22 @@ static cudaError_t st_zero_solid(dvm_ctx *c) { return c->dim == 2 ? zero_solid2d
 static cudaError_t st_partials(dvm_ctx *c) { return c->dim == 2 ? partials_from_state2d(c) : partials_from_state3d(c); }
 static cudaError_t st_pack(dvm_ctx *c, const void *pub, void *dev) { return c->dim == 2 ? pack2d(c, pub, dev) : pack3d(c, pub, dev); }
 static cudaError_t st_unpack(dvm_ctx *c, const void *dev, void *pub) { return c->dim == 2 ? unpack2d(c, dev, pub) : unpack3d(c, dev, pub); }
-// One time step; with the Shakhov model (2D) its relaxation term follows
-// the step (Eq. ShakhovDD).
+namespace dvm {
+cudaError_t shakhov3d(dvm_ctx *c);   // the Shakhov term of the 3D step (dvm_shakhov3d.cu)
+}
+
+// One time step; with the Shakhov model its relaxation term follows the
+// step (Eq. ShakhovDD in 2D, the form of Sec. 2.1 in 3D).
 static cudaError_t st_step(dvm_ctx *c)
 {
     cudaError_t e = c->dim == 2 ? step2d(c) : step3d(c);
-    if (e == cudaSuccess && c->model == DVM_SHAKHOV) e = shakhov2d(c);
+    if (e == cudaSuccess && c->model == DVM_SHAKHOV) e = c->dim == 2 ? shakhov2d(c) : shakhov3d(c);
     return e;
 }
 
 // Why the Shakhov model cannot run on this context (nullptr: it can).
 static const char *shakhov_unsupported(const dvm_ctx *c)
 {
-    if (c->dim != 2) return "Shakhov model: 2D problems only in this library version";
     if (c->time_scheme != DVM_EXPLICIT) return "Shakhov model: the explicit time scheme only";
     if (c->moving) return "Shakhov model: fixed obstacles only in this library version";
     return nullptr;

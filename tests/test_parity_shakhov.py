@@ -1,5 +1,6 @@
-"""Parity of the Shakhov collision model (Eq. ShakhovDD, explicit scheme) of
-the CUDA library with the FP64 CPU oracle, reduced 2D (f, g) model.  GPU only.
+"""Parity of the Shakhov collision model (explicit scheme) of the CUDA
+library with the FP64 CPU oracle: the reduced 2D (f, g) model of Eq.
+ShakhovDD and the full 3D F of Sec. 2.1.  GPU only.
 
 Tolerances as for BGK: FP64 state within 1e-12 of the largest value, FP32
 moments within 1e-5 (relative; velocities on the scale max(|u|, 1)).
@@ -28,10 +29,11 @@ def moments_err(cfg, Fo, Fg):
     mg = oracle.moments(cfg, np.asarray(Fg, np.float64))
     live = mo["rho"] > 0
     errs = {}
-    for k in ("rho", "ux", "uy", "T"):
+    keys = ("rho", "ux", "uy", "uz", "T") if cfg.get("dim", 2) == 3 else ("rho", "ux", "uy", "T")
+    for k in keys:
         ref = mo[k][live]
         scale = np.abs(ref).max()
-        if k in ("ux", "uy"):
+        if k in ("ux", "uy", "uz"):
             scale = max(scale, 1.0)
         errs[k] = np.abs(mg[k][live] - ref).max() / scale
     return errs
@@ -142,11 +144,6 @@ def test_unsupported_combinations_are_reported():
         s.set_collision_model(dvm.SHAKHOV, PR)
     assert e.value.code == dvm.ERR_UNSUPPORTED
     s.close()
-    s = dvm.Solver(W.sphere_mach15(n=12, nv=6), dvm.FP32)
-    with pytest.raises(dvm.DVMError) as e:
-        s.set_collision_model(dvm.SHAKHOV, PR)
-    assert e.value.code == dvm.ERR_UNSUPPORTED
-    s.close()
     ell = W.rotating_ellipse(nx=32, nv=8)
     s = dvm.Solver(ell, dvm.FP32)
     with pytest.raises(dvm.DVMError) as e:
@@ -160,4 +157,74 @@ def test_unsupported_combinations_are_reported():
     with pytest.raises(dvm.DVMError) as e:
         s.step(1)
     assert e.value.code == dvm.ERR_UNSUPPORTED
+    s.close()
+
+
+# ------------------------------------------------------------------ 3D
+@pytest.mark.parametrize("prec", [dvm.FP64, dvm.FP32])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_sphere_small_3d(prec, scheme):
+    """Mach-1.5 sphere, 20^3 cells x 8^3 velocities: state, moments, drag."""
+    cfg = W.sphere_mach15(n=20, nv=8, scheme=scheme)
+    cfg["ra"] = 0.23
+    cfg = shakhov(cfg)
+    steps = 10
+    F0 = oracle.initial_state(cfg)
+    Fo = F0.copy()
+    h = oracle.run3d(cfg, Fo, steps)
+    assert h["status"] == 0
+    s = dvm.Solver(cfg, prec)
+    s.set_state(F0)
+    s.step(steps)
+    Fg = s.get_state()
+    errs = moments_err(cfg, Fo, Fg)
+    assert max(errs.values()) < TOL[prec], errs
+    if prec == dvm.FP64:
+        assert rel_inf(Fg, Fo) < TOL[prec]
+    fs = np.abs(h["Fx"]).max()
+    assert np.abs(s.history(steps)["Fx"] - h["Fx"]).max() <= 10 * TOL[prec] * fs
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [dvm.FP64, dvm.FP32])
+@pytest.mark.parametrize("dims,nvs,bc", [((12, 10, 9), (6, 5, 4), [0] * 6),
+                                         ((9, 7, 11), (6, 6, 5), [2] * 6)])
+def test_ragged_no_body_3d(prec, dims, nvs, bc):
+    nx, ny, nz = dims
+    cfg = W.base3d(nx, nvs[0], 5.0, ny=ny, nz=nz, nvy=nvs[1], nvz=nvs[2], scheme=1, Kn=0.2, cfl=0.45, bc=list(bc))
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    z = (np.arange(nz) + 0.5) / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    bump = np.exp(-((X - 0.5) ** 2 + (Y - 0.4) ** 2 + (Z - 0.6) ** 2) / 0.03).ravel()
+    cfg["init"] = dict(rho=1.0 + 0.3 * bump, ux=0.1, uy=-0.05, uz=0.05, T=1.0 + 0.5 * bump)
+    cfg = shakhov(cfg, Pr=0.5)
+    F0 = oracle.initial_state(cfg)
+    Fo = F0.copy()
+    assert oracle.run3d(cfg, Fo, 8)["status"] == 0
+    s = dvm.Solver(cfg, prec)
+    s.set_state(F0)
+    s.step(8)
+    Fg = s.get_state()
+    errs = moments_err(cfg, Fo, Fg)
+    assert max(errs.values()) < TOL[prec], errs
+    if prec == dvm.FP64:
+        assert rel_inf(Fg, Fo) < TOL[prec]
+    s.close()
+
+
+def test_heat_flux_relaxes_at_rate_pr_3d():
+    n, nv, win, Pr = 2, 40, 11.0, PR
+    cfg = shakhov(W.base3d(n, nv, win, Kn=0.5, bc=[0] * 6), Pr=Pr)
+    rho, u, T, q = 1.2, (0.4, -0.3, 0.2), 1.3, (0.2, -0.15, 0.1)
+    start = oracle.equilibrium(dict(cfg, model=1, Pr=0.0), rho, u, T, q)
+    s = dvm.Solver(cfg, dvm.FP64)
+    s.set_state(np.tile(start, n ** 3))
+    steps = 12
+    s.step(steps)
+    cell = s.get_state()[: start.size]
+    q0, _ = oracle.heat_flux(cfg, start)
+    qn, _ = oracle.heat_flux(cfg, cell)
+    r = s.dt * rho / s.tau0
+    assert np.allclose(qn, (1.0 - Pr * r) ** steps * q0, rtol=0, atol=1e-10 * np.abs(q0).max())
     s.close()
