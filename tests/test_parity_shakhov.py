@@ -214,7 +214,7 @@ def test_ragged_no_body_3d(prec, dims, nvs, bc):
 
 
 def test_heat_flux_relaxes_at_rate_pr_3d():
-    n, nv, win, Pr = 2, 40, 11.0, PR
+    n, nv, win, Pr = 4, 40, 11.0, PR
     cfg = shakhov(W.base3d(n, nv, win, Kn=0.5, bc=[0] * 6), Pr=Pr)
     rho, u, T, q = 1.2, (0.4, -0.3, 0.2), 1.3, (0.2, -0.15, 0.1)
     start = oracle.equilibrium(dict(cfg, model=1, Pr=0.0), rho, u, T, q)
