@@ -290,7 +290,7 @@ def main():
     ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit",
                     help="explicit (Eq. ExSchemeDD) or first-order semi-implicit (Eq. ImpSchemeDD) steps")
     ap.add_argument("--model", choices=["bgk", "shakhov"], default="bgk",
-                    help="collision model: BGK (Eq. BGKDD) or Shakhov with Pr = 2/3 (Eq. ShakhovDD, 2D)")
+                    help="collision model: BGK (Eq. BGKDD) or Shakhov with Pr = 2/3 (Eq. ShakhovDD; Sec. 2.1 in 3D)")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the drag-gradient cost measurement")
@@ -408,10 +408,11 @@ def main():
             ach = pairs_per_step * sb / avg_s / 1e9
             shak = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                     "frac_of_nominal": ach / NOMINAL_HBM_GBS,
-                    "traffic": recorded_traffic(f"k_shakhov_{args.workload}_{args.precision}.md",
+                    "traffic": recorded_traffic(f"k_shakhov{'3' if dim3 else ''}_{args.workload}_{args.precision}.md",
                                                 os.path.join(ROOT, "paper_1503_04544_gb300", "csrc",
-                                                             "dvm_shakhov2d.cu")),
-                    "kernel": "k_shakhov (heat flux of F^n + Shakhov term on F^{n+1} + moments)",
+                                                             "dvm_shakhov3d.cu" if dim3 else "dvm_shakhov2d.cu")),
+                    "kernel": ("k_shakhov3" if dim3 else "k_shakhov")
+                    + " (heat flux of F^n + Shakhov term on F^{n+1} + moments)",
                     "peak_source": f"{peak_kind} HBM copy bandwidth", "bytes_per_pair": sb,
                     "ms_per_launch": avg_s * 1e3, "share_of_step": avg_s * 1e3 / (ms / args.steps)}
             if avg_s > avg_bulk_s:

@@ -47,7 +47,7 @@ def main(argv=None):
     ap.add_argument("--checkpoint-every", type=int, default=20)
     ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit")
     ap.add_argument("--model", choices=["bgk", "shakhov"], default="bgk",
-                    help="collision model (Shakhov: Pr = 2/3, 2D)")
+                    help="collision model (Shakhov: Pr = 2/3)")
     args = ap.parse_args(argv)
     cfg = problem(args.workload, args.cells, args.nv, args.scheme)
     if args.time_scheme == "imex":
