@@ -384,6 +384,46 @@ def test_rigid_rotation_kinematics():
     np.testing.assert_allclose(h["omega_hist"], 2.0, rtol=1e-15)
 
 
+def test_rigid_rotation_ode_finite_inertia():
+    """Eqs. motionDD_vit and motionDD_posit with a finite moment of inertia
+    J: an ellipse that turns in a uniform drifting gas at Kn -> infinity and
+    dt -> 0, where the torque of the first step is the continuous
+    free-molecular torque (closed form, the pin of
+    test_wall_stress_free_molecular_closed_form).  Then
+      omega^1 = omega^0 + dt T^0 / J     (torque at t^n, divided by J),
+      theta^1 = theta^0 + dt omega^0     (explicit Euler, the old omega),
+    and every later step follows the same recurrence with the torque the
+    step reports.  dt / J = 20, so the first step changes omega by more than
+    its initial value: a sign flip of the torque term, J swapped with the
+    mass (m = 1 here), the torque of t^{n+1} or theta advanced with the new
+    omega all fail.  (The torque falls as omega grows, dT/domega ~ -0.02, so
+    the explicit recurrence converges towards the omega of zero torque.)"""
+    U, rho, T, Tw = (0.7, -0.2), 1.3, 0.9, 1.5
+    om0, th0, dt = 0.05, 0.4, 1e-9
+    J = dt / 20.0
+    cfg = W.base2d(64, 64, 64, 10.0, shape=2, ra=0.2, rb=0.08, theta=th0, omega=om0, movable=1,
+                   mass=1.0, inertia=J, Tw=Tw, Kn=1e6, dt=dt,
+                   init=dict(rho=rho, ux=U[0], uy=U[1], uz=0.0, T=T))
+    _, tc = _free_molecular(cfg, oracle.geometry2d(cfg), U, rho, T, om0, Tw)
+    F = oracle.initial_state(cfg)
+    n = 6
+    h = oracle.run(cfg, F, n)
+    assert h["status"] == 0
+    om, th, tq = h["omega_hist"], h["theta_hist"], h["torque"]
+    # first step against the closed-form torque, within its O(dv^2)
+    # quadrature bound (2e-4 |F| size) scaled by dt / J
+    tol = dt / J * 2e-4 * 0.9 * cfg["ra"]
+    assert abs(om[0] - (om0 + dt * tc / J)) < tol, (om[0], om0 + dt * tc / J)
+    assert om[0] - om0 > 0.06
+    assert th[0] == th0 + dt * om0
+    # the recurrence over the following steps, with the torque each reports
+    for k in range(1, n):
+        assert abs(om[k] - (om[k - 1] + dt * tq[k] / J)) <= 1e-14 * abs(om[k]), k
+        assert th[k] == th[k - 1] + dt * om[k - 1], k
+    # omega changes at every step (the torque term is live)
+    assert np.abs(np.diff(om)).min() > 0.005
+
+
 def test_positivity_under_cfl():
     """Sec. 3.4.1: the explicit scheme keeps f >= 0 under the CFL condition,
     including cut and merged cells (Mach-2 cylinder, strong gradients)."""
