@@ -311,8 +311,9 @@ int dvm_cell_counts(dvm_ctx *ctx, long long *nonsolid, long long *bulk, long lon
 
 /* Total mass of a state, allocating no device memory.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc,
- * such as code running while a stream is captured into a CUDA graph or a hook
- * inside a framework whose allocator owns all device memory.
+ * such as a hook inside a framework whose allocator owns all device memory
+ * and forbids allocation while the hook runs, or a loop with a fixed memory
+ * budget that must not grow once it runs.
  *   f      device pointer, state in the public layout [cell][comp][p],
  *          FP32 or FP64 as `precision` says; only component 0 is summed
  *   sbar   device pointer, ncell cell areas (2D) or volumes (3D)
@@ -320,11 +321,14 @@ int dvm_cell_counts(dvm_ctx *ctx, long long *nonsolid, long long *bulk, long lon
  *   mass   device pointer, receives sum_cells sbar * sum_p f dv (FP64)
  *   stream cudaStream_t or NULL (legacy default stream); asynchronous
  * The scratch (one FP64 value per cell) is a static device array of 2^20
- * cells held by every GPU that loads the library until exit; larger states
- * are rejected with DVM_ERR_ARG.  The first call on a device looks up the
- * array's address with that device current: make it before any stream
- * capture.  All calls share the array, so calls whose work overlaps on the
- * GPU (different streams, no ordering) race; order them.
+ * cells (8 MiB) held by every GPU that loads the library until exit; larger
+ * states are rejected with DVM_ERR_ARG.  The first call on a device (and the
+ * first in a new context of it, e.g. after cudaDeviceReset) looks up the
+ * array's address with that device current: make that call before any
+ * stream capture.  Every entry the call reads from the array it writes
+ * first, so no clearing is needed.  All calls share the array, so calls
+ * whose work overlaps on the GPU (different streams, no ordering) race;
+ * order them.
  * Errors: DVM_ERR_ARG, DVM_ERR_CUDA. */
 int dvm_mass_noalloc(const void *f, int precision, long long ncell, int ncomp, int nv,
                      const double *sbar, double dv, double *mass, void *stream);

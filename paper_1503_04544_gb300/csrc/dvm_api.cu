@@ -709,16 +709,71 @@ int dvm_get_state(dvm_ctx *c, void *f, size_t bytes, int on_device)
 // Checkpoint file: a fixed header, then the state in the public layout, the
 // partial moment sums of the current buffer (device layout) and the device
 // body record, so that a loaded context continues bit for bit as the saved
-// one would have.
+// one would have.  The header carries the sizes and schemes and a hash of
+// everything else that defines the problem (problem_hash), so that a
+// checkpoint of another obstacle, wall temperature, inflow or collision model
+// is refused.
 struct CheckpointHeader {
     char magic[8];            // "DVMCKPT1"
     int32_t version, dim, precision, scheme, time_scheme, S;
-    int32_t nx, ny, nz, nvx, nvy, nvz, shape, movable, need_fusion, reserved;
+    int32_t nx, ny, nz, nvx, nvy, nvz, shape, movable, need_fusion, model;
     double dt, tau0;
     int64_t steps_done;
     uint64_t state_bytes, part_bytes, body_bytes;
+    uint64_t problem;         // problem_hash
 };
 static const char kCkptMagic[8] = {'D', 'V', 'M', 'C', 'K', 'P', 'T', '1'};
+static const int32_t kCkptVersion = 2;
+
+// 64-bit FNV-1a over the bytes of a sequence of values.
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void bytes(const void *p, size_t n)
+    {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t k = 0; k < n; ++k) { h ^= b[k]; h *= 1099511628211ull; }
+    }
+    void val(int32_t v) { bytes(&v, sizeof(v)); }
+};
+
+// Hash of the problem definition beyond the header's sizes: domain and
+// velocity-grid extents, Kn, Lref, cfl, the collision model and Pr, the kind
+// of every side and the states of the Maxwellian sides, and the obstacle
+// (shape, centre, sizes, translation velocity, mass, inertia, movability,
+// wall temperature and the per-sector temperatures and directions).  The
+// body's angle and angular velocity are state, saved in the body record.
+static int problem_hash(dvm_ctx *c, uint64_t *out)
+{
+    Fnv f;
+    const double ext[] = {c->xmin, c->xmax, c->ymin, c->ymax, c->zmin, c->zmax, c->vxmin, c->vxmax,
+                          c->vymin, c->vymax, c->vzmin, c->vzmax, c->Kn, c->Lref, c->cfl, c->Pr};
+    f.bytes(ext, sizeof(ext));
+    f.val((int32_t)c->model);
+    for (int side = 0; side < 2 * c->dim; ++side) {
+        f.val((int32_t)c->bc[side]);
+        if (c->bc[side] == DVM_BC_MAXWELLIAN && c->d_bcstate[side]) {
+            std::vector<double> st((size_t)5 * side_cells(c, side));
+            CK(cudaMemcpy(st.data(), c->d_bcstate[side], st.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            f.bytes(st.data(), st.size() * sizeof(double));
+        }
+    }
+    const dvm_body &b = c->body;
+    f.val((int32_t)b.shape);
+    if (b.shape != DVM_SHAPE_NONE) {
+        const double bd[] = {b.cx, b.cy, b.cz, b.ra, b.rb, b.vbx, b.vby, b.mass, b.inertia, b.Tw};
+        f.bytes(bd, sizeof(bd));
+        f.val((int32_t)b.movable);
+        f.val((int32_t)b.nseg);
+        if (b.nseg > 0 && c->d_Twseg && c->d_segdir) {
+            std::vector<double> t((size_t)3 * b.nseg);
+            CK(cudaMemcpy(t.data(), c->d_Twseg, sizeof(double) * b.nseg, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(t.data() + b.nseg, c->d_segdir, sizeof(double) * 2 * b.nseg, cudaMemcpyDeviceToHost));
+            f.bytes(t.data(), t.size() * sizeof(double));
+        }
+    }
+    *out = f.h;
+    return DVM_OK;
+}
 
 static size_t part_bytes(const dvm_ctx *c)
 {
@@ -732,16 +787,19 @@ int dvm_save(dvm_ctx *c, const char *path)
     CheckpointHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1; h.dim = c->dim; h.precision = c->prec; h.scheme = c->scheme; h.time_scheme = c->time_scheme;
+    h.version = kCkptVersion; h.dim = c->dim; h.precision = c->prec; h.scheme = c->scheme; h.time_scheme = c->time_scheme;
     h.S = c->S; h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.nvx = c->nvx; h.nvy = c->nvy; h.nvz = c->nvz;
     h.shape = c->body.shape; h.movable = c->body.movable; h.need_fusion = c->need_fusion ? 1 : 0;
     h.dt = c->dt; h.tau0 = c->tau0; h.steps_done = c->steps_done;
     h.state_bytes = c->state_elems * c->elem;
     h.part_bytes = part_bytes(c);
     h.body_bytes = sizeof(dvm::BodyDev);
+    h.model = c->model;
+    int rc = problem_hash(c, &h.problem);
+    if (rc != DVM_OK) return rc;
     std::vector<char> state(h.state_bytes), part(h.part_bytes);
     dvm::BodyDev hb;
-    int rc = dvm_get_state(c, state.data(), state.size(), 0);
+    rc = dvm_get_state(c, state.data(), state.size(), 0);
     if (rc != DVM_OK) return rc;
     CK(cudaMemcpyAsync(part.data(), c->part[c->cur], part.size(), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&hb, c->d_body, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
@@ -760,16 +818,21 @@ int dvm_load(dvm_ctx *c, const char *path)
     if (!c || !path) { set_error("null argument"); return DVM_ERR_ARG; }
     FILE *fp = std::fopen(path, "rb");
     if (!fp) { set_error(std::string("dvm_load: cannot open ") + path); return DVM_ERR_ARG; }
+    uint64_t mine = 0;
+    int hrc = problem_hash(c, &mine);
+    if (hrc != DVM_OK) { std::fclose(fp); return hrc; }
     CheckpointHeader h;
     std::vector<char> state, part;
     dvm::BodyDev hb;
-    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, kCkptMagic, 8) == 0 && h.version == 1;
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, kCkptMagic, 8) == 0 &&
+              h.version == kCkptVersion;
     // the checkpoint must come from a context of the same problem
     ok = ok && h.dim == c->dim && h.precision == c->prec && h.scheme == c->scheme && h.S == c->S &&
          h.nx == c->nx && h.ny == c->ny && h.nz == c->nz && h.nvx == c->nvx && h.nvy == c->nvy &&
          h.nvz == c->nvz && h.shape == c->body.shape && h.movable == c->body.movable && h.dt == c->dt &&
          h.tau0 == c->tau0 && h.state_bytes == c->state_elems * c->elem && h.part_bytes == part_bytes(c) &&
-         h.body_bytes == sizeof(dvm::BodyDev) && (h.time_scheme == DVM_EXPLICIT || h.time_scheme == DVM_IMEX);
+         h.body_bytes == sizeof(dvm::BodyDev) && (h.time_scheme == DVM_EXPLICIT || h.time_scheme == DVM_IMEX) &&
+         h.model == c->model && h.problem == mine;
     if (ok) {
         state.resize(h.state_bytes);
         part.resize(h.part_bytes);
@@ -779,7 +842,7 @@ int dvm_load(dvm_ctx *c, const char *path)
     std::fclose(fp);
     if (!ok) {
         set_error(std::string("dvm_load: not a checkpoint of this problem (grid, velocities, precision, schemes, "
-                              "body, time step): ") + path);
+                              "collision model, boundary states, body, wall temperatures, time step): ") + path);
         return DVM_ERR_ARG;
     }
     // the body first: a moving body's geometry is rebuilt at the saved angle

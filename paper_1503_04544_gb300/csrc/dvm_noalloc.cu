@@ -1,13 +1,14 @@
 // Total-mass diagnostic that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph, or inside a host framework whose allocator owns
-// all device memory (a custom-call or plugin hook that must not allocate
-// while it executes).  dvm_mass_noalloc serves them: it computes the same
+// Some callers cannot call cudaMalloc: code inside a host framework whose
+// allocator owns all device memory (a custom-call or plugin hook that must not
+// allocate while it executes), or a loop with a fixed memory budget that may
+// not grow its footprint once it runs.  dvm_mass_noalloc serves them: it computes the same
 // quantity as dvm_mass from buffers the caller already holds, and keeps its
 // only scratch, one partial mass per cell, in the file-scope device array
 // below.  That array is part of the library image: every GPU on which the
 // library is loaded holds it (8 MiB) until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -23,9 +24,44 @@ constexpr int kMaxDevices = 64;
 // Per-cell partial masses of the last call.  Shared by every call on a device.
 static __device__ __align__(256) double g_cell_mass[kNoAllocMaxCells];
 
-// Device address of g_cell_mass, looked up once per device.
+// Device address of g_cell_mass, looked up once per device and CUDA context:
+// a context created after a cudaDeviceReset holds its own copy of the array,
+// so the address is looked up again when the current context's id changes
+// (context ids are unique for the life of the process).
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    double *ptr;
+};
 std::mutex g_setup_mutex;
-double *g_scratch[kMaxDevices] = {nullptr};
+ScratchSlot g_scratch[kMaxDevices] = {};
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context; false if there is none yet or
+// the driver does not provide the calls.
+bool current_context_id(unsigned long long *id)
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PfnCtxGetCurrent>(fn);
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PfnCtxGetId>(fn);
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 // Partial mass of one cell: sbar * sum_p f dv over the first component of a
 // state in the public layout [cell][comp][p] (one warp per cell).
@@ -60,21 +96,28 @@ __global__ void __launch_bounds__(1024) k_sum_mass(const double *scratch, long l
     }
 }
 
-// Address of the static scratch on the current device (set-up on first use).
+// Address of the static scratch on the current device (set-up on the first
+// call on a device, and again on the first call in a new context of it).
 int scratch_on_current_device(double **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return dvm::cuda_fail(e, "dvm_mass_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) { dvm::set_error("dvm_mass_noalloc: device index out of range"); return DVM_ERR_ARG; }
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch[dev]) {
+    ScratchSlot &slot = g_scratch[dev];
+    if (!slot.ptr || !have_id || slot.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_cell_mass);
         if (e != cudaSuccess || !p) return dvm::cuda_fail(e, "dvm_mass_noalloc: cudaGetSymbolAddress");
-        g_scratch[dev] = static_cast<double *>(p);
+        // the lookup makes the device's primary context current if none was
+        unsigned long long now = 0;
+        slot.ctx_id = current_context_id(&now) ? now : 0;
+        slot.ptr = static_cast<double *>(p);
     }
-    *out = g_scratch[dev];
+    *out = slot.ptr;
     return DVM_OK;
 }
 

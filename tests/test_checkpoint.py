@@ -79,6 +79,32 @@ def test_load_rejects_other_problem_and_garbage(tmp_path):
     t.close()
 
 
+def test_load_rejects_same_sizes_other_problem(tmp_path):
+    """The same grid, velocities, precision and time step, but another wall
+    temperature, obstacle size, inflow state or collision model: the header's
+    problem hash refuses the checkpoint."""
+    base = W.cylinder_mach2(nx=48, nv=16)
+    s = dvm.Solver(base, dvm.FP32)
+    s.init_maxwellian()
+    path = str(tmp_path / "a.dvm")
+    s.save(path)
+    s.close()
+    same = dvm.Solver(base, dvm.FP32)
+    same.load(path)                       # the same problem loads
+    same.close()
+    others = [W.cylinder_mach2(nx=48, nv=16, Tw=1.3), W.cylinder_mach2(nx=48, nv=16, mach=1.5)]
+    bigger = W.cylinder_mach2(nx=48, nv=16)
+    bigger["ra"] = 0.12
+    shak = W.cylinder_mach2(nx=48, nv=16)
+    shak.update(model=1, Pr=2.0 / 3.0)
+    others += [bigger, shak]
+    for other in others:
+        t = dvm.Solver(other, dvm.FP32)
+        with pytest.raises(dvm.DVMError):
+            t.load(path)
+        t.close()
+
+
 def test_save_needs_a_state(tmp_path):
     s = dvm.Solver(W.cylinder_mach2(nx=32, nv=8), dvm.FP32)
     with pytest.raises(dvm.DVMError):
