@@ -56,6 +56,7 @@ class _Cfg(C.Structure):
         ("movable", C.c_int), ("Tw", C.c_double), ("nseg", C.c_int),
         ("Tw_seg", C.POINTER(C.c_double)), ("seg_dir", C.POINTER(C.c_double)),
         ("axis", C.c_int), ("time_scheme", C.c_int), ("model", C.c_int), ("Pr", C.c_double),
+        ("conservative", C.c_int),
     ]
 
 
@@ -107,6 +108,7 @@ def _load():
             lib.orc_mass3d.argtypes = [P, _PD]; lib.orc_mass3d.restype = C.c_double
             lib.orc_heat_flux.argtypes = [P, _PD, _PD]
             lib.orc_equilibrium.argtypes = [P, C.c_double, _PD, C.c_double, _PD, _PD]
+            lib.orc_equilibrium_params.argtypes = [P, _PD, _PD, C.POINTER(C.c_int)]
             _lib = lib
     return _lib
 
@@ -147,6 +149,7 @@ class _CfgHolder:
         s.time_scheme = int(cfg.get("time_scheme", 0))   # 0 explicit, 1 semi-implicit (Eq. ImpSchemeDD)
         s.model = int(cfg.get("model", 0))               # 0 BGK (Eq. BGKDD), 1 Shakhov (Eq. ShakhovDD)
         s.Pr = float(cfg.get("Pr", 1.0))
+        s.conservative = int(cfg.get("conservative", 0))  # 1: Newton on the discrete moments (Sec. 3.1)
         self.s = s
         self.cfg = cfg
 
@@ -253,6 +256,17 @@ def equilibrium(cfg: dict, rho: float, u, T: float, q) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"orc_equilibrium: status {rc}")
     return out
+
+
+def equilibrium_params(cfg: dict, fk: np.ndarray) -> tuple[np.ndarray, int, int]:
+    """(rho, ux, uy, uz, T) of one cell's equilibrium: the direct moments, or
+    with cfg['conservative'] the Newton root of Sec. 3.1; the Newton
+    iterations taken and the status."""
+    out = np.zeros(5)
+    it = C.c_int(0)
+    rc = _load().orc_equilibrium_params(_CfgHolder(cfg).ref, _ptr(np.ascontiguousarray(fk, np.float64)),
+                                        _ptr(out), C.byref(it))
+    return out, it.value, rc
 
 
 def run(cfg: dict, F: np.ndarray, nsteps: int) -> dict:

@@ -292,6 +292,151 @@ int orc_moments(const orc_cfg *c, const double *F, double *rho, double *ux,
     return ORC_OK;
 }
 
+/* ------------------------------------------- conservative discrete equilibrium */
+
+/* Solve A x = b (n <= 5) by Gaussian elimination with partial pivoting;
+ * A and b are overwritten.  Returns 0 on success, 1 for a singular matrix. */
+static int solve_small(int n, double A[5][5], double *b, double *x)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(A[i][k]) > fabs(A[piv][k])) piv = i;
+        if (!(fabs(A[piv][k]) > 0)) return 1;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) { double t = A[k][j]; A[k][j] = A[piv][j]; A[piv][j] = t; }
+            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double l = A[i][k] / A[k][k];
+            for (int j = k; j < n; ++j) A[i][j] -= l * A[k][j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < n; ++j) s -= A[i][j] * x[j];
+        x[i] = s / A[i][i];
+    }
+    return 0;
+}
+
+/* Conservative equilibrium parameters (Sec. 3.1, the paragraph after Eq.
+ * MacroscopicDDv): the (rho, u, T) put into the equilibrium are not the direct
+ * moments of the state but the ones whose discrete equilibrium has the same
+ * discrete moments as the state, so that the collision term conserves mass,
+ * momentum and energy exactly on the velocity grid.  With theta = (rho, u, T)
+ * and the equilibrium E_p(theta) = M[rho, u, T](v_p) (2D: and T/2 M for g),
+ * the equations are, for phi = 1, v_d and the energy weight,
+ *   sum_p phi(v_p) E_p(theta) dv = sum_p phi(v_p) f_p dv,
+ * 2D energy: sum (|v|^2/2 + T/2) M dv = sum (|v|^2/2 f + g) dv;
+ * 3D energy: sum |v|^2/2 M dv = sum |v|^2/2 F dv.
+ * The root does not depend on the variant of Newton's method that finds it;
+ * this one takes plain Newton steps from the direct moments, with the exact
+ * Jacobian summed over the whole grid:
+ *   dM/drho = M / rho, dM/du_d = M (v_d - u_d) / T,
+ *   dM/dT = M (|v - u|^2 / (2 T^2) - dim / (2 T)),
+ * and in 2D the energy row also gets d(T/2 M)/dT = T/2 dM/dT + M/2.  Stops
+ * when the largest step, relative to rho, sqrt(T) (velocities) and T, is
+ * below 1e-13 (one more step then follows from the quadratic convergence
+ * already taken), at most 50 steps. */
+static int conservative_params(const orc_cfg *c, const double *fk, double *rho, double *u, double *T,
+                               int *iters)
+{
+    const int D = c->dim, n = D + 2;
+    const int nv1 = c->nvx, nv2 = c->nvy, nv3 = D == 3 ? c->nvz : 1;
+    const int nv = nv1 * nv2 * nv3;
+    const double dvx = (c->vxmax - c->vxmin) / nv1, dvy = (c->vymax - c->vymin) / nv2;
+    const double dvz = D == 3 ? (c->vzmax - c->vzmin) / nv3 : 1.0;
+    const double dv = dvx * dvy * dvz;
+    /* moments of the state */
+    double tgt[5] = {0, 0, 0, 0, 0};
+    for (int p3 = 0; p3 < nv3; ++p3)
+        for (int p2 = 0; p2 < nv2; ++p2)
+            for (int p1 = 0; p1 < nv1; ++p1) {
+                int p = (p3 * nv2 + p2) * nv1 + p1;
+                double v[3] = {c->vxmin + p1 * dvx, c->vymin + p2 * dvy, D == 3 ? c->vzmin + p3 * dvz : 0.0};
+                double f = fk[p];
+                tgt[0] += f * dv;
+                for (int d = 0; d < D; ++d) tgt[1 + d] += v[d] * f * dv;
+                double e = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * f;
+                if (D == 2) e += fk[nv + p];
+                tgt[n - 1] += e * dv;
+            }
+    int rc = cell_moments(c, fk, rho, u, T);
+    if (rc) return rc;
+    double th[5];
+    th[0] = *rho;
+    for (int d = 0; d < D; ++d) th[1 + d] = u[d];
+    th[n - 1] = *T;
+    int it = 0, done = 0;
+    for (it = 0; it < 50 && !done; ++it) {
+        double m[5] = {0, 0, 0, 0, 0}, J[5][5];
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) J[i][j] = 0;
+        const double r = th[0], Tt = th[n - 1];
+        if (!(r > 0) || !(Tt > 0)) return ORC_ERR_NONPHYSICAL;
+        double uu[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) uu[d] = th[1 + d];
+        for (int p3 = 0; p3 < nv3; ++p3)
+            for (int p2 = 0; p2 < nv2; ++p2)
+                for (int p1 = 0; p1 < nv1; ++p1) {
+                    double v[3] = {c->vxmin + p1 * dvx, c->vymin + p2 * dvy, D == 3 ? c->vzmin + p3 * dvz : 0.0};
+                    double M = D == 3 ? maxw3d(r, uu[0], uu[1], uu[2], Tt, v[0], v[1], v[2])
+                                      : maxw2d(r, uu[0], uu[1], Tt, v[0], v[1]);
+                    double c2 = 0;
+                    for (int d = 0; d < D; ++d) c2 += (v[d] - uu[d]) * (v[d] - uu[d]);
+                    double dM[5];
+                    dM[0] = M / r;
+                    for (int d = 0; d < D; ++d) dM[1 + d] = M * (v[d] - uu[d]) / Tt;
+                    dM[n - 1] = M * (c2 / (2.0 * Tt * Tt) - D / (2.0 * Tt));
+                    double half_v2 = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                    double phi[5];
+                    phi[0] = 1.0;
+                    for (int d = 0; d < D; ++d) phi[1 + d] = v[d];
+                    phi[n - 1] = D == 2 ? half_v2 + Tt / 2.0 : half_v2;
+                    for (int i = 0; i < n; ++i) {
+                        m[i] += phi[i] * M * dv;
+                        for (int j = 0; j < n; ++j) J[i][j] += phi[i] * dM[j] * dv;
+                    }
+                    if (D == 2) J[n - 1][n - 1] += 0.5 * M * dv;   /* d(T/2)/dT times M, from g */
+                }
+        double res[5], step[5];
+        for (int i = 0; i < n; ++i) res[i] = tgt[i] - m[i];
+        if (solve_small(n, J, res, step)) return ORC_ERR_NONPHYSICAL;
+        double big = fabs(step[0]) / th[0];
+        for (int d = 0; d < D; ++d) big = fmax(big, fabs(step[1 + d]) / sqrt(Tt));
+        big = fmax(big, fabs(step[n - 1]) / Tt);
+        for (int i = 0; i < n; ++i) th[i] += step[i];
+        if (big < 1e-13) done = 1;
+    }
+    if (iters) *iters = it;
+    if (!done) return ORC_ERR_NONPHYSICAL;
+    *rho = th[0];
+    for (int d = 0; d < 3; ++d) u[d] = d < D ? th[1 + d] : 0.0;
+    *T = th[n - 1];
+    return (*rho > 0 && *T > 0) ? ORC_OK : ORC_ERR_NONPHYSICAL;
+}
+
+/* Equilibrium parameters of one cell: the direct moments (Eq.
+ * MacroscopicDDv), or the conservative ones of Sec. 3.1. */
+static int equilibrium_params(const orc_cfg *c, const double *fk, double *rho, double *u, double *T)
+{
+    if (c->conservative) return conservative_params(c, fk, rho, u, T, NULL);
+    return cell_moments(c, fk, rho, u, T);
+}
+
+int orc_equilibrium_params(const orc_cfg *c, const double *fk, double *out, int *iters)
+{
+    double rho, u[3] = {0, 0, 0}, T;
+    int rc;
+    if (iters) *iters = 0;
+    if (c->conservative) rc = conservative_params(c, fk, &rho, u, &T, iters);
+    else rc = cell_moments(c, fk, &rho, u, &T);
+    out[0] = rho; out[1] = u[0]; out[2] = u[1]; out[3] = u[2]; out[4] = T;
+    return rc;
+}
+
 /* ---------------------------------------------------------- collision model */
 
 /* Heat flux of one cell's state about its velocity u (R = 1): reduced 2D
@@ -351,6 +496,7 @@ static void equilibrium_at(const orc_cfg *c, double rho, const double *u, double
 
 static int model_ok(const orc_cfg *c)
 {
+    if (c->conservative && c->model != ORC_BGK) return 0;   /* conservative equilibrium: BGK */
     if (c->model == ORC_BGK) return 1;
     return c->model == ORC_SHAKHOV && c->Pr >= 0 && c->time_scheme == ORC_EXPLICIT;
 }
@@ -401,14 +547,19 @@ typedef struct {
  * collision term vanish, so rho, u and T at t^{n+1} are the moments of the
  * transported values; with them f^{n+1} = (f_T + nu M) / (1 + nu), where
  * nu = dt / tau^{n+1} = dt rho^{n+1} / tau0 and M is the Maxwellian of
- * Eq. BGKDD (2D: g_T relaxes towards T/2 M).  reading: the discrete moments of
- * M are taken equal to rho, u, T, as for the direct moments of the explicit
- * scheme. */
+ * Eq. BGKDD (2D: g_T relaxes towards T/2 M).  reading: with the direct
+ * moments the discrete moments of M are taken equal to rho, u, T, as in the
+ * explicit scheme; with the conservative parameters of Sec. 3.1 they are
+ * equal by construction, so the relaxed state keeps the discrete moments of
+ * the transported one. */
 static int imex_relax(const orc_cfg *c, double dt, double tau0, double *fk)
 {
-    double rho, u[3], T;
-    if (cell_moments(c, fk, &rho, u, &T)) return ORC_ERR_NONPHYSICAL;
-    const double nu = dt * rho / tau0;
+    double rho, u[3], T, rd, ud[3], Td;
+    if (cell_moments(c, fk, &rd, ud, &Td)) return ORC_ERR_NONPHYSICAL;
+    /* tau from the direct density; the Maxwellian from the equilibrium
+     * parameters (direct or conservative, Sec. 3.1) */
+    if (equilibrium_params(c, fk, &rho, u, &T)) return ORC_ERR_NONPHYSICAL;
+    const double nu = dt * rd / tau0;
     const int nv1 = c->nvx, nv2 = c->nvy, nv3 = c->dim == 3 ? c->nvz : 1;
     const int nv = nv1 * nv2 * nv3;
     const double dvx = (c->vxmax - c->vxmin) / nv1, dvy = (c->vymax - c->vymin) / nv2;
@@ -604,6 +755,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
     double *Sn = malloc(sizeof(double) * nc), *Sp = malloc(sizeof(double) * nc);
     double *mrho = malloc(sizeof(double) * nc), *mux = malloc(sizeof(double) * nc);
     double *muy = malloc(sizeof(double) * nc), *mT = malloc(sizeof(double) * nc);
+    double *tau_rho = malloc(sizeof(double) * nc);
     double *mq = calloc((size_t)nc * 3, sizeof(double));
     double *wphi = malloc(sizeof(double) * nc), *wux = malloc(sizeof(double) * nc);
     double *wuy = malloc(sizeof(double) * nc), *wT = malloc(sizeof(double) * nc);
@@ -651,15 +803,20 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
                 }
         }
         X.F = F; X.g = gn;
-        /* moments of f_CV^n and the BGK equilibrium inputs (Eq. BGKDD) */
+        /* moments of f_CV^n and the BGK equilibrium inputs (Eq. BGKDD): the
+         * direct density sets tau; the equilibrium takes the direct moments
+         * or the conservative parameters of Sec. 3.1 */
         int nonphys = 0;
         #pragma omp parallel for reduction(|:nonphys)
         for (long m = 0; m < nc; ++m) {
             if (mstart[m + 1] - mstart[m] == 0) continue;
             double u[3], r, T;
             if (cell_moments(c, F + m * 2 * nv, &r, u, &T)) nonphys = 1;
-            mrho[m] = r; mux[m] = u[0]; muy[m] = u[1]; mT[m] = T;
+            tau_rho[m] = r;
             if (c->model == ORC_SHAKHOV) cell_heat_flux(c, F + m * 2 * nv, u, mq + 3 * m);
+            if (c->conservative && c->time_scheme == ORC_EXPLICIT &&
+                conservative_params(c, F + m * 2 * nv, &r, u, &T, NULL)) nonphys = 1;
+            mrho[m] = r; mux[m] = u[0]; muy[m] = u[1]; mT[m] = T;
         }
         if (nonphys) { err = ORC_ERR_NONPHYSICAL; break; }
         /* Step 4: wall density phi (Eq. BoundaryDDv) at every wall edge;
@@ -759,7 +916,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
                                 R[comp * nv + p] += (fxp - fxm) + (fyp - fym) + fw;
                             }
                 }
-                double tau = tau0 / mrho[m];
+                double tau = tau0 / tau_rho[m];
                 double a = Sn[m] / Sp[m], b = dt / Sp[m], r = dt / tau;
                 if (c->time_scheme == ORC_IMEX) {
                     for (int comp = 0; comp < 2; ++comp)
@@ -816,7 +973,7 @@ int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
     if (omega_out) *omega_out = omega;
     free_geo2d(&ga); free_geo2d(&gb);
     free(master); free(mstart); free(mlist); free(cnt); free(Sn); free(Sp);
-    free(mrho); free(mux); free(muy); free(mT); free(mq);
+    free(mrho); free(mux); free(muy); free(mT); free(mq); free(tau_rho);
     free(wphi); free(wux); free(wuy); free(wT); free(Fnew); free(vx); free(vy);
     for (int s = 0; s < 4; ++s) free(X.ghost[s]);
     return err;
@@ -1110,6 +1267,7 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
     int32_t *mstart = malloc(sizeof(int32_t) * (nc + 1)), *mlist = malloc(sizeof(int32_t) * nc), *cnt = malloc(sizeof(int32_t) * nc);
     double *S = malloc(sizeof(double) * nc);
     double *mr = malloc(sizeof(double) * nc), *mu = malloc(sizeof(double) * 3 * nc), *mT = malloc(sizeof(double) * nc);
+    double *tau_rho = malloc(sizeof(double) * nc);
     double *mq = calloc((size_t)nc * 3, sizeof(double));
     double *wphi = malloc(sizeof(double) * nc), *wu = malloc(sizeof(double) * 3 * nc), *wT = malloc(sizeof(double) * nc);
     double *Fnew = malloc(sizeof(double) * nc * nv);
@@ -1145,8 +1303,11 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
             if (mstart[m + 1] - mstart[m] == 0) continue;
             double u[3], r, T;
             if (cell_moments(c, F + m * nv, &r, u, &T)) nonphys = 1;
-            mr[m] = r; mu[3 * m] = u[0]; mu[3 * m + 1] = u[1]; mu[3 * m + 2] = u[2]; mT[m] = T;
+            tau_rho[m] = r;
             if (c->model == ORC_SHAKHOV) cell_heat_flux(c, F + m * nv, u, mq + 3 * m);
+            if (c->conservative && c->time_scheme == ORC_EXPLICIT &&
+                conservative_params(c, F + m * nv, &r, u, &T, NULL)) nonphys = 1;
+            mr[m] = r; mu[3 * m] = u[0]; mu[3 * m + 1] = u[1]; mu[3 * m + 2] = u[2]; mT[m] = T;
         }
         if (nonphys) { err = ORC_ERR_NONPHYSICAL; break; }
         /* wall density and stress (3D forms of Eqs. BoundaryTD, StressTensorDD) */
@@ -1240,7 +1401,7 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
                                 R[p] += (fxp - fxm) + (fyp - fym) + (fzp - fzm) + fw;
                             }
                 }
-                double tau = tau0 / mr[m];
+                double tau = tau0 / tau_rho[m];
                 double a = 1.0, b = dt / S[m], r = dt / tau;   /* fixed body: V^n = V^{n+1,*} */
                 if (c->time_scheme == ORC_IMEX) {
                     /* the semi-implicit scheme (Eq. ImpSchemeDD) in 3D */
@@ -1284,7 +1445,7 @@ int orc_run3d(const orc_cfg *c, double *F, int nsteps, orc_hist *h)
         }
     }
     free_geo3d(&geo);
-    free(master); free(mstart); free(mlist); free(cnt); free(S); free(mr); free(mu); free(mT); free(mq);
+    free(master); free(mstart); free(mlist); free(cnt); free(S); free(mr); free(mu); free(mT); free(mq); free(tau_rho);
     free(wphi); free(wu); free(wT); free(Fnew); free(vx); free(vy); free(vz);
     for (int s = 0; s < 6; ++s) free(X.ghost[s]);
     return err;
@@ -1465,7 +1626,7 @@ int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *Jout, 
                   double *gTw, double *gbc0, double *gbc1, double *gbc2, double *gbc3)
 {
     if (c->dim != 2 || c->movable || c->shape == ORC_SHAPE_NONE || nsteps < 0) return ORC_ERR_ARG;
-    if (c->model != ORC_BGK || c->time_scheme != ORC_EXPLICIT) return ORC_ERR_ARG;
+    if (c->model != ORC_BGK || c->time_scheme != ORC_EXPLICIT || c->conservative) return ORC_ERR_ARG;
     orc_ctx2d X;
     X.c = c; X.nx = c->nx; X.ny = c->ny; X.nv1 = c->nvx; X.nv2 = c->nvy;
     X.nv = X.nv1 * X.nv2;

@@ -63,6 +63,10 @@ typedef struct {
                                       (first-order semi-implicit, Eq. ImpSchemeDD) */
     int model;                     /* ORC_BGK or ORC_SHAKHOV (explicit scheme only) */
     double Pr;                     /* Prandtl number of the Shakhov model */
+    int conservative;              /* 0: the equilibrium takes the direct moments
+                                      (Eq. MacroscopicDDv); 1: the (rho, u, T)
+                                      whose discrete equilibrium has the discrete
+                                      moments of the state (Sec. 3.1, Newton; BGK) */
 } orc_cfg;
 
 /* Geometry of one time level (2D): every array is caller-owned.          */
@@ -108,6 +112,12 @@ int orc_heat_flux(const orc_cfg *c, const double *fk, double *q);
  * Maxwellian) or Shakhov (Eq. ShakhovDD in 2D, the 3D form of Sec. 2.1). */
 int orc_equilibrium(const orc_cfg *c, double rho, const double *u, double T,
                     const double *q, double *fk);
+/* Parameters (rho, u[3], T) of one cell's equilibrium for the configured
+ * moments: the direct moments of fk (Eq. MacroscopicDDv), or with
+ * c->conservative the root of the discrete conservation equations of
+ * Sec. 3.1, found by Newton's method.  out[5] = rho, ux, uy, uz, T;
+ * iters (nullable) receives the Newton iterations taken. */
+int orc_equilibrium_params(const orc_cfg *c, const double *fk, double *out, int *iters);
 int orc_run2d(const orc_cfg *c, double *F, int nsteps, orc_hist *h,
               double *theta_out, double *omega_out);
 double orc_mass2d(const orc_cfg *c, const double *F);
