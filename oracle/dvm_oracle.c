@@ -498,7 +498,7 @@ static int model_ok(const orc_cfg *c)
 {
     if (c->conservative && c->model != ORC_BGK) return 0;   /* conservative equilibrium: BGK */
     if (c->model == ORC_BGK) return 1;
-    return c->model == ORC_SHAKHOV && c->Pr >= 0 && c->time_scheme == ORC_EXPLICIT;
+    return c->model == ORC_SHAKHOV && c->Pr >= 0;
 }
 
 int orc_heat_flux(const orc_cfg *c, const double *fk, double *q)
@@ -560,6 +560,17 @@ static int imex_relax(const orc_cfg *c, double dt, double tau0, double *fk)
      * parameters (direct or conservative, Sec. 3.1) */
     if (equilibrium_params(c, fk, &rho, u, &T)) return ORC_ERR_NONPHYSICAL;
     const double nu = dt * rd / tau0;
+    /* Shakhov (Eq. ShakhovDD): the equilibrium holds the heat flux at
+     * t^{n+1}.  reading: taking the heat-flux moment of the scheme with the
+     * model's property that its equilibrium carries (1 - Pr) q gives
+     * q^{n+1} = q_T / (1 + nu Pr), q_T the heat flux of the transported
+     * values about their own velocity (Eq. MacroscopicDDv). */
+    double q[3] = {0, 0, 0};
+    if (c->model == ORC_SHAKHOV) {
+        double qt[3];
+        cell_heat_flux(c, fk, ud, qt);
+        for (int d = 0; d < 3; ++d) q[d] = qt[d] / (1.0 + nu * c->Pr);
+    }
     const int nv1 = c->nvx, nv2 = c->nvy, nv3 = c->dim == 3 ? c->nvz : 1;
     const int nv = nv1 * nv2 * nv3;
     const double dvx = (c->vxmax - c->vxmin) / nv1, dvy = (c->vymax - c->vymin) / nv2;
@@ -569,15 +580,11 @@ static int imex_relax(const orc_cfg *c, double dt, double tau0, double *fk)
             for (int p1 = 0; p1 < nv1; ++p1) {
                 int p = (p3 * nv2 + p2) * nv1 + p1;
                 double vx = c->vxmin + p1 * dvx, vy = c->vymin + p2 * dvy;
-                if (c->dim == 3) {
-                    double vz = c->vzmin + p3 * dvz;
-                    double M = maxw3d(rho, u[0], u[1], u[2], T, vx, vy, vz);
-                    fk[p] = (fk[p] + nu * M) / (1.0 + nu);
-                } else {
-                    double M = maxw2d(rho, u[0], u[1], T, vx, vy);
-                    fk[p] = (fk[p] + nu * M) / (1.0 + nu);
-                    fk[nv + p] = (fk[nv + p] + nu * (T / 2.0 * M)) / (1.0 + nu);
-                }
+                double vz = c->dim == 3 ? c->vzmin + p3 * dvz : 0.0;
+                double fe, ge;
+                equilibrium_at(c, rho, u, T, q, vx, vy, vz, &fe, c->dim == 3 ? NULL : &ge);
+                fk[p] = (fk[p] + nu * fe) / (1.0 + nu);
+                if (c->dim == 2) fk[nv + p] = (fk[nv + p] + nu * ge) / (1.0 + nu);
             }
     return ORC_OK;
 }

@@ -11,7 +11,11 @@ come from the oracle's own formulas:
 - Pr = 1 is the BGK model bit for bit (2D cylinder, 3D sphere);
 - in a homogeneous gas the explicit scheme (Eq. ExSchemeDD) leaves rho, u
   and T fixed and multiplies the heat flux by 1 - Pr dt/tau each step
-  (the Prandtl number of the model); BGK gives 1 - dt/tau.
+  (the Prandtl number of the model); BGK gives 1 - dt/tau;
+- under the semi-implicit scheme (Eq. ImpSchemeDD) the heat flux is divided
+  by 1 + Pr dt/tau each step (the reading q^{n+1} = q_T / (1 + nu Pr)), Pr = 1
+  is the semi-implicit BGK scheme bit for bit, and a very stiff step lands on
+  the Maxwellian of the transported moments.
 """
 import numpy as np
 import pytest
@@ -131,10 +135,72 @@ def test_heat_flux_relaxes_at_rate_pr(dim, model, Pr):
         assert np.allclose(m1[k], m0[k], rtol=0, atol=1e-12)
 
 
-def test_shakhov_needs_the_explicit_scheme_and_pr():
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("Pr", [2.0 / 3.0, 0.3])
+def test_heat_flux_semi_implicit_rate(dim, Pr):
+    """Eq. ImpSchemeDD with the Shakhov equilibrium in a homogeneous gas: the
+    heat flux follows q^{n+1} = q^n / (1 + Pr nu), nu = dt/tau, at dt/tau = 4
+    (where the explicit scheme is unstable); rho, u and T stay fixed."""
+    cfg, F, start, rho = homogeneous(dim, Pr, 1)
+    tau = oracle.tau0(cfg) / rho
+    cfg = dict(cfg, time_scheme=1, dt=4.0 * tau)
+    q0, _ = oracle.heat_flux(cfg, start)
+    m0 = oracle.moments(cfg, F)
+    nu = 4.0
+    n = 6
+    run = oracle.run if dim == 2 else oracle.run3d
+    assert run(cfg, F, n)["status"] == 0
+    cell0 = F[: F.size // (2 ** dim)]
+    qn, _ = oracle.heat_flux(cfg, cell0)
+    expect = q0 / (1.0 + Pr * nu) ** n
+    assert np.allclose(qn, expect, rtol=0, atol=1e-10 * np.abs(q0).max()), (qn, expect)
+    m1 = oracle.moments(cfg, F)
+    for k in ("rho", "ux", "uy", "uz", "T"):
+        assert np.allclose(m1[k], m0[k], rtol=0, atol=1e-12)
+
+
+def test_pr_one_is_bgk_semi_implicit():
+    cfg = dict(W.cylinder_mach2(nx=32, nv=12), Kn=1e-3, time_scheme=1)
+    F0 = oracle.initial_state(cfg)
+    a, b = F0.copy(), F0.copy()
+    assert oracle.run(cfg, a, 5)["status"] == 0
+    assert oracle.run(dict(cfg, model=1, Pr=1.0), b, 5)["status"] == 0
+    assert np.array_equal(a, b)
+
+
+def test_stiff_semi_implicit_step_is_the_maxwellian():
+    """nu -> infinity: q^{n+1} -> 0 and the step gives the Maxwellian of the
+    transported state's moments (textbook 2D Maxwellian, fine grid)."""
+    cfg, F, start, rho = homogeneous(2, 2.0 / 3.0, 1)
+    cfg = dict(cfg, time_scheme=1, dt=1e9 * oracle.tau0(cfg) / rho)
+    m = oracle.moments(cfg, F)
+    assert oracle.run(cfg, F, 1)["status"] == 0
+    vx, vy = velocity_axis(cfg, "x"), velocity_axis(cfg, "y")
+    VX, VY = np.meshgrid(vx, vy)
+    r, ux, uy, T = m["rho"][0], m["ux"][0], m["uy"][0], m["T"][0]
+    M = (r / (2 * np.pi * T) * np.exp(-((VX - ux) ** 2 + (VY - uy) ** 2) / (2 * T))).ravel()
+    nv = M.size
+    assert np.abs(F[:nv] - M).max() <= 1e-8 * M.max()
+    assert np.abs(F[nv:2 * nv] - T / 2 * M).max() <= 1e-8 * M.max()
+
+
+def test_shakhov_needs_pr_and_direct_moments():
     cfg = W.cylinder_mach2(nx=16, nv=8)
     F = oracle.initial_state(cfg)
-    assert oracle.run(dict(cfg, model=1, Pr=2.0 / 3.0, time_scheme=1), F.copy(), 1)["status"] != 0
     assert oracle.run(dict(cfg, model=1, Pr=-0.5), F.copy(), 1)["status"] != 0
+    assert oracle.run(dict(cfg, model=1, Pr=2.0 / 3.0, conservative=1), F.copy(), 1)["status"] != 0
     with pytest.raises(ValueError):
         oracle.equilibrium(one_cell(2, 8, 4.0, model=1, Pr=-1.0), 1.0, (0, 0), 1.0, (0, 0))
+
+
+def test_pr_one_is_bgk_moving_body():
+    """A rotating ellipse (area ratios S^n / S^{n+1,*} of merged control
+    volumes, appearing cells): Pr = 1 is the BGK run bit for bit."""
+    cfg = W.rotating_ellipse(nx=48, nv=10, scheme=1)
+    F0 = oracle.initial_state(cfg)
+    a, b = F0.copy(), F0.copy()
+    ha = oracle.run(cfg, a, 6)
+    hb = oracle.run(dict(cfg, model=1, Pr=1.0), b, 6)
+    assert ha["status"] == 0 and hb["status"] == 0
+    assert np.array_equal(a, b)
+    assert np.array_equal(ha["torque"], hb["torque"])
