@@ -102,6 +102,7 @@ def _load():
             lib.orc_mass2d.argtypes = [P, _PD]; lib.orc_mass2d.restype = C.c_double
             lib.orc_adjoint2d.argtypes = [P, _PD, C.c_int, _PD, _PD, _PD, _PD, _PD, _PD, _PD]
             lib.orc_init_maxwellian_vjp.argtypes = [P, _PD, _PD, _PD, _PD, _PD, _PD]
+            lib.orc_adjoint2d_ex.argtypes = [P, _PD, C.c_int, C.c_int, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD]
             lib.orc_geometry3d.argtypes = [P, C.POINTER(_Geo3d)]
             lib.orc_masters3d.argtypes = [P, C.POINTER(_Geo3d), _PI32]
             lib.orc_run3d.argtypes = [P, _PD, C.c_int, C.POINTER(_Hist)]
@@ -344,6 +345,22 @@ def adjoint2d(cfg: dict, F0: np.ndarray, nsteps: int) -> dict:
     J = np.zeros(1)
     rc = lib.orc_adjoint2d(_CfgHolder(cfg).ref, _ptr(F0), int(nsteps), _ptr(J), _ptr(lam0), _ptr(gTw),
                            *[_ptr(g) for g in gbc])
+    return dict(status=rc, J=float(J[0]), lam0=lam0, gTw=gTw, gbc=[g.reshape(-1, 5) for g in gbc])
+
+
+def adjoint2d_seed(cfg: dict, F0: np.ndarray, nsteps: int, seed: np.ndarray | None,
+                   with_drag: bool = False) -> dict:
+    """The discrete adjoint for J = [with_drag] F_x(F^N) + <seed, F^N>."""
+    lib = _load()
+    F0 = np.ascontiguousarray(F0, dtype=np.float64)
+    lam0 = np.zeros_like(F0)
+    gTw = np.zeros(max(int(cfg.get("nseg", 0)), 1))
+    nside = [cfg["ny"], cfg["ny"], cfg["nx"], cfg["nx"]]
+    gbc = [np.zeros(5 * n) for n in nside]
+    J = np.zeros(1)
+    sd = None if seed is None else np.ascontiguousarray(seed, dtype=np.float64)
+    rc = lib.orc_adjoint2d_ex(_CfgHolder(cfg).ref, _ptr(F0), int(nsteps), int(bool(with_drag)), _ptr(sd),
+                              _ptr(J), _ptr(lam0), _ptr(gTw), *[_ptr(g) for g in gbc])
     return dict(status=rc, J=float(J[0]), lam0=lam0, gTw=gTw, gbc=[g.reshape(-1, 5) for g in gbc])
 
 

@@ -1632,6 +1632,16 @@ static double dM1_dTw(double m1, double ax, double ay, double Tw)
 int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *Jout, double *lam0,
                   double *gTw, double *gbc0, double *gbc1, double *gbc2, double *gbc3)
 {
+    return orc_adjoint2d_ex(c, F0, nsteps, 1, NULL, Jout, lam0, gTw, gbc0, gbc1, gbc2, gbc3);
+}
+
+/* The adjoint for J = [with_drag] F_x(F^N) + <seed, F^N>: the linear part's
+ * gradient, the seed, joins lambda^N after the drag part's fusion transpose
+ * (the drag is taken on the fused F^N, the functional on F^N itself). */
+int orc_adjoint2d_ex(const orc_cfg *c, const double *F0, int nsteps, int with_drag, const double *seed,
+                     double *Jout, double *lam0, double *gTw, double *gbc0, double *gbc1, double *gbc2,
+                     double *gbc3)
+{
     if (c->dim != 2 || c->movable || c->shape == ORC_SHAPE_NONE || nsteps < 0) return ORC_ERR_ARG;
     if (c->model != ORC_BGK || c->time_scheme != ORC_EXPLICIT || c->conservative) return ORC_ERR_ARG;
     orc_ctx2d X;
@@ -1688,7 +1698,7 @@ int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *Jout, 
         fuse2d(&X, &V, Fs + (size_t)nsteps * ns, Ft);
         memset(nu, 0, sizeof(double) * ns);
         double J = 0;
-        for (long k = 0; k < nc; ++k) {
+        for (long k = 0; k < nc && with_drag; ++k) {
             if (geo.type[k] != ORC_CUT || !(geo.lw[k] > 0)) continue;
             const orc_wall w = wall2d(&X, k, Ft);
             const double nwx = geo.nwx[k], nwy = geo.nwy[k], lw = geo.lw[k];
@@ -1725,6 +1735,8 @@ int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *Jout, 
         }
         *Jout = J;
         fuse2d_T(&X, &V, nu, lam);
+        if (seed)
+            for (long q = 0; q < ns; ++q) lam[q] += seed[q];
     }
 
     /* reverse sweep over the steps */

@@ -156,6 +156,11 @@ double orc_mass3d(const orc_cfg *c, const double *F);
  * Maxwellian side s (nullable; zeros for other sides). */
 int orc_adjoint2d(const orc_cfg *c, const double *F0, int nsteps, double *J, double *lam0,
                   double *gTw, double *gbc0, double *gbc1, double *gbc2, double *gbc3);
+/* The same for J = [with_drag] F_x(F^N) + <seed, F^N> (seed: dJ/dF^N of a
+ * linear functional of the state after nsteps steps, layout of F; nullable). */
+int orc_adjoint2d_ex(const orc_cfg *c, const double *F0, int nsteps, int with_drag, const double *seed,
+                     double *J, double *lam0, double *gTw, double *gbc0, double *gbc1, double *gbc2,
+                     double *gbc3);
 int orc_init_maxwellian_vjp(const orc_cfg *c, const double *rho, const double *ux,
                             const double *uy, const double *T, const double *lam, double *g);
 

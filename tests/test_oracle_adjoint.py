@@ -112,3 +112,60 @@ def test_uniform_wall_temperature():
     as_ = oracle.adjoint2d(cfg_s, oracle.initial_state(cfg_s), STEPS)
     assert abs(au["J"] - as_["J"]) <= 1e-13 * abs(au["J"])
     assert abs(au["gTw"][0] - as_["gTw"].sum()) <= 1e-12 * abs(au["gTw"][0])
+
+
+def _smooth(cfg):
+    x = (np.arange(NX) + 0.5) / NX
+    X, Y = np.meshgrid(x, x)
+    u = math.sqrt(5.0 / 3.0) * 2.0
+    cfg["init"] = dict(rho=(1.0 + 0.2 * np.sin(2 * np.pi * X) * np.cos(np.pi * Y)).ravel(),
+                       ux=(u * (1.0 + 0.1 * np.cos(2 * np.pi * Y))).ravel(),
+                       uy=(0.2 * np.sin(2 * np.pi * X)).ravel(), uz=0.0, T=(1.0 + 0.1 * X * Y).ravel())
+    return cfg
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_adjoint_linear_functional_directional_derivative(scheme):
+    """J = <seed, F^N> for a random seed on every non-solid cell, component
+    and velocity (no drag): <lambda^0, dF> equals the central difference of J
+    along a random relative perturbation dF of F^0, and one sector's dJ/dT_w
+    its central difference.  Every cell carries a sensitivity from the start,
+    the domain boundaries included."""
+    cfg = _smooth(problem(scheme))
+    steps = 6
+    F0 = oracle.initial_state(cfg)
+    rng = np.random.default_rng(9)
+    live = np.repeat(F0.reshape(-1, 2 * NV * NV).max(axis=1) > 0, 2 * NV * NV)
+    seed = rng.uniform(-1, 1, F0.size) * live
+    a = oracle.adjoint2d_seed(cfg, F0, steps, seed)
+    assert a["status"] == 0 and a["J"] == 0.0
+
+    def G(c, F):
+        F = F.copy()
+        assert oracle.run(c, F, steps)["status"] == 0
+        return float(seed @ F)
+
+    dF = F0 * rng.uniform(-1, 1, F0.size)
+    eps = 1e-7
+    fd = (G(cfg, F0 + eps * dF) - G(cfg, F0 - eps * dF)) / (2 * eps)
+    ad = float(a["lam0"] @ dF)
+    assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+    k = 3
+    tw = cfg["Tw_seg"].copy()
+    tp, tm = tw.copy(), tw.copy()
+    tp[k] += H
+    tm[k] -= H
+    fdt = (G(dict(cfg, Tw_seg=tp), F0) - G(dict(cfg, Tw_seg=tm), F0)) / (2 * H)
+    assert abs(a["gTw"][k] - fdt) <= 1e-6 * max(abs(fdt), np.abs(a["gTw"]).max()), (a["gTw"][k], fdt)
+
+
+def test_adjoint_drag_plus_seed_is_linear():
+    cfg = _smooth(problem(1))
+    F0 = oracle.initial_state(cfg)
+    seed = np.random.default_rng(2).uniform(-1, 1, F0.size)
+    a = oracle.adjoint2d_seed(cfg, F0, 5, None, with_drag=True)
+    b = oracle.adjoint2d_seed(cfg, F0, 5, seed)
+    c = oracle.adjoint2d_seed(cfg, F0, 5, seed, with_drag=True)
+    d = oracle.adjoint2d(cfg, F0, 5)
+    assert np.array_equal(a["lam0"], d["lam0"]) and a["J"] == d["J"]
+    assert np.abs(a["lam0"] + b["lam0"] - c["lam0"]).max() <= 1e-13 * np.abs(c["lam0"]).max()
