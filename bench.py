@@ -13,6 +13,16 @@ non-solid cells.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
                   [--workload cylinder|sphere|ellipse|bump] [--impl gb300|reference]
                   [--time-scheme explicit|imex] [--model bgk|shakhov]
+                  [--equilibrium direct|conservative]
+                  [--no-sublines] [--no-accuracy] [--no-adjoint] [--no-cpu-baseline]
+
+The default run (cylinder, FP32) also reports, nested in its line: the
+errors of the FP32 and FP64 GPU paths against the oracle after the oracle
+sample's steps and of FP32 against FP64 after the configuration's 2000
+steps (``accuracy``); the FP64 line of the same workload (``fp64``, against
+the measured FP64 FMA throughput); the 3D sphere line, 96^3 cells x 20^3
+velocities in FP32 (``sphere``); and the cost of the drag gradient
+(``adjoint``).
 
 For N > 1 each rank runs an independent replica (the path is not sharded
 here); value = pairs updated by all ranks / max-over-ranks time.
@@ -75,6 +85,7 @@ def config_dict(cfg, prec, nsolid_free, extra=None):
         "scheme": "muscl-minmod" if cfg.get("scheme", 0) == 1 else "upwind",
         "time_scheme": "semi-implicit" if cfg.get("time_scheme", 0) == 1 else "explicit",
         "collision": "shakhov, Pr 2/3" if cfg.get("model", 0) == 1 else "bgk",
+        "equilibrium": "conservative (Newton)" if cfg.get("conservative", 0) else "direct moments",
         "precision": prec,
         "pairs_per_step": nsolid_free,
         "l2": "inputs larger than L2 (state per copy > 129 MB)",
@@ -175,9 +186,11 @@ def cpu_sample_cfg(cfg):
     return cfg
 
 
-def cpu_baseline(cfg, budget_s: float = 12.0, max_steps: int = 1000):
+def cpu_baseline(cfg, budget_s: float = 12.0, max_steps: int = 1000, keep: bool = False):
     """Time the FP64 oracle as it stands on the host cores: whole steps from the
-    initial state until about budget_s seconds of work (a bounded sample)."""
+    initial state until about budget_s seconds of work (a bounded sample).
+    keep: also return the oracle's state and last drag (keys _F, _fx) for the
+    accuracy check of the GPU path."""
     import numpy as np
     import oracle
     cfg = cpu_sample_cfg(cfg)
@@ -189,17 +202,22 @@ def cpu_baseline(cfg, budget_s: float = 12.0, max_steps: int = 1000):
         g = oracle.geometry2d(cfg)
         pairs = int(np.sum(g["type"] != 2)) * cfg["nvx"] * cfg["nvy"]
     done = 0
+    fx = 0.0
     t0 = time.perf_counter()
     while done < max_steps:
-        oracle.run(cfg, F, 1)
+        h = oracle.run(cfg, F, 1)
+        fx = float(h["Fx"][0])
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": pairs * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} FP64 oracle step(s) of {cfg['name']} from the initial state, "
-                      f"{el:.1f} s"}
+    out = {"value": pairs * done / el, "unit": UNIT, "cores": cores, "kind": "oracle", "steps": done,
+           "sample": f"{done} FP64 oracle step(s) of {cfg['name']} from the initial state, {el:.1f} s"}
+    if keep:
+        out["_F"] = F
+        out["_fx"] = fx
+    return out
 
 
 def adjoint_cost(precision_fp32: bool = True):
@@ -268,6 +286,8 @@ def run_reference(args):
         cfg["time_scheme"] = 1
     if args.model == "shakhov":
         cfg.update(model=1, Pr=2.0 / 3.0)
+    if args.equilibrium == "conservative":
+        cfg["conservative"] = 1
     cb = cpu_baseline(cfg, budget_s=60.0, max_steps=max(1, min(args.steps, 8)))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -280,49 +300,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=None)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--workload", default="cylinder")
-    ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit",
-                    help="explicit (Eq. ExSchemeDD) or first-order semi-implicit (Eq. ImpSchemeDD) steps")
-    ap.add_argument("--model", choices=["bgk", "shakhov"], default="bgk",
-                    help="collision model: BGK (Eq. BGKDD) or Shakhov with Pr = 2/3 (Eq. ShakhovDD; Sec. 2.1 in 3D)")
-    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the drag-gradient cost measurement")
-    args = ap.parse_args()
-    if args.steps is None:
-        args.steps = DEFAULT_STEPS.get(args.workload, 2000)
-    if args.impl == "reference":
-        run_reference(args)
-        return
+def rel_errors(mg: dict, mo: dict, live, dim: int) -> dict:
+    """Per moment field ||m - m_ref||_inf / ||m_ref||_inf over the non-solid
+    cells; velocities are normalised by max(||u_ref||_inf, 1) (the velocity
+    unit is sqrt(R T0))."""
+    import numpy as np
+    out = {}
+    keys = ("rho", "ux", "uy", "uz", "T") if dim == 3 else ("rho", "ux", "uy", "T")
+    for k in keys:
+        ref = mo[k][live]
+        scale = np.abs(ref).max()
+        if k in ("ux", "uy", "uz"):
+            scale = max(scale, 1.0)
+        out[k] = float(np.abs(mg[k][live] - ref).max() / scale)
+    out["max"] = max(out.values())
+    return out
 
+
+def gpu_run(cfg, prec, steps, stream, F0=None):
+    """Moments and the force history of ``steps`` steps of ``cfg`` on the GPU
+    from its initial Maxwellian (or the state F0)."""
+    import numpy as np
+    from paper_1503_04544_gb300 import dvm
+    s = dvm.Solver(cfg, prec, stream=stream.cuda_stream)
+    if F0 is None:
+        s.init_maxwellian()
+    else:
+        s.set_state(F0)
+    done = 0
+    while done < steps:
+        k = min(1000, steps - done)
+        s.step_async(k)
+        s.check()
+        done += k
+    m = s.moments()
+    fx = s.history(min(steps, 32768))["Fx"]
+    s.close()
+    return m, (float(fx[-1]) if len(fx) else 0.0), np.asarray(fx)
+
+
+def fp32_vs_fp64(cfg, steps, stream) -> dict:
+    """FP32 moments and drag after ``steps`` steps against the FP64 GPU path
+    (which matches the oracle within 1e-12 per step) from the same initial
+    state."""
+    import numpy as np
+    from paper_1503_04544_gb300 import dvm
+    t0 = time.perf_counter()
+    m32, fx32, _ = gpu_run(cfg, dvm.FP32, steps, stream)
+    m64, fx64, _ = gpu_run(cfg, dvm.FP64, steps, stream)
+    live = m64["rho"] > 0
+    dim = cfg.get("dim", 2)
+    out = {"steps": steps, "moments": rel_errors(m32, m64, live, dim),
+           "drag": abs(fx32 - fx64) / max(abs(fx64), 1e-300), "drag_fp64": fx64,
+           "tolerance": 1e-5, "seconds": time.perf_counter() - t0}
+    out["pass"] = bool(out["moments"]["max"] <= 1e-5)
+    return out
+
+
+def vs_oracle(cfg, F_oracle, fx_oracle, done, stream) -> dict:
+    """GPU FP32 and FP64 runs of the oracle sample's ``done`` steps from the
+    same initial state, against the oracle's state (moments) and drag."""
+    import oracle
+    from paper_1503_04544_gb300 import dvm
+    mo = oracle.moments(cfg, F_oracle)
+    live = mo["rho"] > 0
+    dim = cfg.get("dim", 2)
+    out = {"steps": done, "workload": cfg["name"]}
+    for name, prec, tol in (("fp32", dvm.FP32, 1e-5), ("fp64", dvm.FP64, 1e-12)):
+        mg, fx, _ = gpu_run(cfg, prec, done, stream)
+        e = rel_errors(mg, mo, live, dim)
+        out[name] = {"moments": e, "drag": abs(fx - fx_oracle) / max(abs(fx_oracle), 1e-300),
+                     "tolerance": tol, "pass": bool(e["max"] <= tol)}
+    return out
+
+
+def measure(cfg, prec, args, world, local, stream, peak, peak_kind, fp64_peak=None):
+    """One bench line of ``cfg`` at precision ``prec``: device-timed steps with
+    per-launch timing of the dominant kernel, clocks, and the end-to-end run
+    through the public API with pinned host buffers."""
     import numpy as np
     import torch
     import torch.distributed as dist
     from paper_1503_04544_gb300 import dvm
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    cfg = workload(args.workload)
-    if args.time_scheme == "imex":
-        cfg["time_scheme"] = 1
-    if args.model == "shakhov":
-        cfg.update(model=1, Pr=2.0 / 3.0)
-    prec = dvm.FP32 if args.precision == "fp32" else dvm.FP64
-    # a dedicated stream: the library enqueues on it and the events below
-    # are recorded on it
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
+    prec_name = "fp32" if prec == dvm.FP32 else "fp64"
     s = dvm.Solver(cfg, prec, stream=stream.cuda_stream)
     s.init_maxwellian()
     s.step(max(args.warmup, 3))
@@ -384,82 +445,191 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "per run: state H2D from pinned host memory, K steps, moments D2H"}
     assert np.isfinite(m["rho"]).all()
-
-    if rank == 0:
-        peak, peak_kind = read_peaks()
-        avg_bulk_s = bulk_ms / max(nb, 1) / 1e3
-        achieved = bulk_pairs * bytes_per_pair / avg_bulk_s / 1e9
-        dim3 = cfg.get("dim", 2) == 3
-        traffic = recorded_traffic(
-            f"k_bulk{'3' if dim3 else ''}_{args.workload}_{args.precision}.md",
-            os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step3d.cu" if dim3 else "dvm_step2d.cu"))
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": traffic,
-                    "kernel": ("k_bulk3" if dim3 else "k_bulk") + " (fused stream + relax + moments)",
-                    "peak_source": f"{peak_kind} HBM copy bandwidth",
-                    "bytes_per_pair": bytes_per_pair,
-                    "bulk_ms_per_launch": avg_bulk_s * 1e3,
-                    "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)}
-        if ns:
-            # Shakhov: k_shakhov reads F^n of every gas cell (heat flux) and
-            # reads and writes F^{n+1}: 3 x 2 components per pair
-            avg_s = shak_ms / ns / 1e3
-            sb = 3 * s.ncomp * s.elem
-            ach = pairs_per_step * sb / avg_s / 1e9
-            shak = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "frac_of_nominal": ach / NOMINAL_HBM_GBS,
-                    "traffic": recorded_traffic(f"k_shakhov{'3' if dim3 else ''}_{args.workload}_{args.precision}.md",
-                                                os.path.join(ROOT, "paper_1503_04544_gb300", "csrc",
-                                                             "dvm_shakhov3d.cu" if dim3 else "dvm_shakhov2d.cu")),
-                    "kernel": ("k_shakhov3" if dim3 else "k_shakhov")
-                    + " (heat flux of F^n + Shakhov term on F^{n+1} + moments)",
-                    "peak_source": f"{peak_kind} HBM copy bandwidth", "bytes_per_pair": sb,
-                    "ms_per_launch": avg_s * 1e3, "share_of_step": avg_s * 1e3 / (ms / args.steps)}
-            if avg_s > avg_bulk_s:
-                shak["k_bulk"] = roofline
-                roofline = shak
-            else:
-                roofline["k_shakhov"] = shak
-        if prec == dvm.FP64 and not dim3 and cfg.get("scheme", 1) == 1 and roofline["kernel"].startswith("k_bulk"):
-            # the FP64 step is bound by the FP64 pipe on this part: report
-            # that ceiling, with the HBM view beside it
-            gflops = FP64_FLOPS_PER_PAIR * bulk_pairs / avg_bulk_s / 1e9
-            hbm = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "frac_of_nominal", "peak_source",
-                                            "bytes_per_pair")}
-            del roofline["frac_of_nominal"]
-            roofline.update({"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                             "frac": gflops / FP64_PEAK_GFLOPS, "flops_per_pair": FP64_FLOPS_PER_PAIR,
-                             "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes/clock x 2 flop x 2.07 GHz",
-                             "hbm": hbm})
-        line = {
-            "metric": METRIC,
-            "value": replica_throughput(pairs_per_step * args.steps, ms_max / 1e3, world),
-            "unit": UNIT,
-            "n_gpus": world,
-            "steps": args.steps,
-            "warmup": args.warmup,
-            "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True,
-            "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": "f32" if prec == dvm.FP32 else "f64",
-            "data": "synthetic",
-            "config": config_dict(cfg, args.precision, pairs_per_step,
-                                  {"parallelism": f"replicas{world}" if world > 1 else "single",
-                                   "bulk_pairs_per_step": bulk_pairs,
-                                   "cut_cell_cvs": counts["cvs"], "wall_cells": counts["walls"]}),
-            "roofline": roofline,
-            "clocks": clocks,
-            "e2e": e2e,
-            "gpu_launches": launches,
-        }
-        if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(cfg)
-        if (world == 1 and args.workload == "cylinder" and args.time_scheme == "explicit" and args.model == "bgk"
-                and not args.no_adjoint):
-            line["adjoint"] = adjoint_cost(prec == dvm.FP32)
-        print(json.dumps(line), flush=True)
+    del host
     s.close()
+
+    avg_bulk_s = bulk_ms / max(nb, 1) / 1e3
+    achieved = bulk_pairs * bytes_per_pair / avg_bulk_s / 1e9
+    dim3 = cfg.get("dim", 2) == 3
+    wl = workload_key(cfg)
+    traffic = recorded_traffic(
+        f"k_bulk{'3' if dim3 else ''}_{wl}_{prec_name}.md",
+        os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step3d.cu" if dim3 else "dvm_step2d.cu"))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": traffic,
+                "kernel": ("k_bulk3" if dim3 else "k_bulk") + " (fused stream + relax + moments)",
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "bytes_per_pair": bytes_per_pair,
+                "bulk_ms_per_launch": avg_bulk_s * 1e3,
+                "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)}
+    if ns:
+        # Shakhov: k_shakhov reads F^n of every gas cell (heat flux) and
+        # reads and writes F^{n+1}: 3 x 2 components per pair
+        avg_s = shak_ms / ns / 1e3
+        sb = 3 * s.ncomp * s.elem
+        ach = pairs_per_step * sb / avg_s / 1e9
+        shak = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "frac_of_nominal": ach / NOMINAL_HBM_GBS,
+                "traffic": recorded_traffic(f"k_shakhov{'3' if dim3 else ''}_{wl}_{prec_name}.md",
+                                            os.path.join(ROOT, "paper_1503_04544_gb300", "csrc",
+                                                         "dvm_shakhov3d.cu" if dim3 else "dvm_shakhov2d.cu")),
+                "kernel": ("k_shakhov3" if dim3 else "k_shakhov")
+                + " (heat flux of F^n + Shakhov term on F^{n+1} + moments)",
+                "peak_source": f"{peak_kind} HBM copy bandwidth", "bytes_per_pair": sb,
+                "ms_per_launch": avg_s * 1e3, "share_of_step": avg_s * 1e3 / (ms / args.steps)}
+        if avg_s > avg_bulk_s:
+            shak["k_bulk"] = roofline
+            roofline = shak
+        else:
+            roofline["k_shakhov"] = shak
+    if prec == dvm.FP64 and not dim3 and cfg.get("scheme", 1) == 1 and roofline["kernel"].startswith("k_bulk"):
+        # the FP64 step is bound by the FP64 pipe on this part: report that
+        # ceiling (the measured FP64 FMA throughput), with the HBM view beside it
+        gflops = FP64_FLOPS_PER_PAIR * bulk_pairs / avg_bulk_s / 1e9
+        hbm = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "frac_of_nominal", "peak_source",
+                                        "bytes_per_pair")}
+        del roofline["frac_of_nominal"]
+        pk = fp64_peak if fp64_peak else FP64_PEAK_GFLOPS
+        roofline.update({"bound": "alu", "achieved": gflops, "peak": pk, "unit": "GFLOP/s",
+                         "frac": gflops / pk, "flops_per_pair": FP64_FLOPS_PER_PAIR,
+                         "peak_source": ("measured: FP64 FMA throughput kernel (dvm_fp64_peak)" if fp64_peak
+                                         else "nominal: 152 SMs x 2 FP64 FMA lanes/clock x 2 flop x 2.07 GHz"),
+                         "peak_nominal": FP64_PEAK_GFLOPS, "hbm": hbm})
+    return {
+        "metric": METRIC,
+        "value": replica_throughput(pairs_per_step * args.steps, ms_max / 1e3, world),
+        "unit": UNIT,
+        "steps": args.steps,
+        "ms_per_step": ms_max / args.steps,
+        "dtype": "f32" if prec == dvm.FP32 else "f64",
+        "config": config_dict(cfg, prec_name, pairs_per_step,
+                              {"parallelism": f"replicas{world}" if world > 1 else "single",
+                               "bulk_pairs_per_step": bulk_pairs,
+                               "cut_cell_cvs": counts["cvs"], "wall_cells": counts["walls"]}),
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+
+
+def workload_key(cfg) -> str:
+    name = cfg.get("name", "")
+    for k in ("cylinder", "ellipse", "bump", "sphere"):
+        if k in name:
+            return k
+    return name
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--workload", default="cylinder")
+    ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit",
+                    help="explicit (Eq. ExSchemeDD) or first-order semi-implicit (Eq. ImpSchemeDD) steps")
+    ap.add_argument("--model", choices=["bgk", "shakhov"], default="bgk",
+                    help="collision model: BGK (Eq. BGKDD) or Shakhov with Pr = 2/3 (Eq. ShakhovDD; Sec. 2.1 in 3D)")
+    ap.add_argument("--equilibrium", choices=["direct", "conservative"], default="direct",
+                    help="BGK equilibrium from the direct moments (Eq. MacroscopicDDv) or the conservative "
+                         "Newton parameters (Sec. 3.1)")
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the drag-gradient cost measurement")
+    ap.add_argument("--no-sublines", action="store_true",
+                    help="default workload only: skip the FP64 and sphere sub-lines")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the error measurements")
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS.get(args.workload, 2000)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1503_04544_gb300 import dvm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cfg = workload(args.workload)
+    if args.time_scheme == "imex":
+        cfg["time_scheme"] = 1
+    if args.model == "shakhov":
+        cfg.update(model=1, Pr=2.0 / 3.0)
+    if args.equilibrium == "conservative":
+        cfg["conservative"] = 1
+    prec = dvm.FP32 if args.precision == "fp32" else dvm.FP64
+    # a dedicated stream: the library enqueues on it and the events are
+    # recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    peak, peak_kind = read_peaks()
+    fp64_pk = dvm.fp64_peak(stream.cuda_stream)
+    line = measure(cfg, prec, args, world, local, stream, peak, peak_kind, fp64_pk)
+    line.update({"n_gpus": world, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                 "vs_baseline": None, "data": "synthetic"})
+    default = (args.workload == "cylinder" and args.time_scheme == "explicit" and args.model == "bgk"
+               and args.precision == "fp32" and args.equilibrium == "direct")
+    if rank == 0 and world == 1:
+        acc = {}
+        cb = None
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline(cfg, keep=True)
+            if not args.no_accuracy:
+                acc["vs_oracle"] = vs_oracle(cpu_sample_cfg(cfg), cb.pop("_F"), cb.pop("_fx"), cb["steps"],
+                                             stream)
+            cb.pop("_F", None); cb.pop("_fx", None)
+            line["cpu_baseline"] = cb
+        if not args.no_accuracy:
+            run_len = int(cfg.get("steps", args.steps))
+            if cfg.get("dim", 2) == 3:
+                run_len = min(run_len, 20)    # FP64 sphere steps take ~0.3 s
+            acc["fp32_vs_fp64"] = fp32_vs_fp64(cfg, run_len, stream)
+        if acc:
+            line["accuracy"] = acc
+        if default and not args.no_adjoint:
+            line["adjoint"] = adjoint_cost(True)
+        if default and not args.no_sublines:
+            # the FP64 half of the metric on the same workload (at most 200
+            # timed steps: an FP64 step takes ~8 ms)
+            a64 = argparse.Namespace(**vars(args))
+            a64.steps = min(args.steps, 200)
+            sub = measure(cfg, dvm.FP64, a64, world, local, stream, peak, peak_kind, fp64_pk)
+            if cb is not None:
+                sub["cpu_baseline"] = dict(cb, note="the same oracle sample as the main line")
+            if "vs_oracle" in acc:
+                sub["accuracy"] = {"vs_oracle": {"steps": acc["vs_oracle"]["steps"],
+                                                 "fp64": acc["vs_oracle"]["fp64"]}}
+            line["fp64"] = sub
+            # the 3D sphere (96^3 cells x 20^3 velocities), FP32
+            scfg = workload("sphere")
+            sargs = argparse.Namespace(**vars(args))
+            sargs.workload = "sphere"
+            sargs.steps = min(args.steps, DEFAULT_STEPS["sphere"])
+            sub3 = measure(scfg, dvm.FP32, sargs, world, local, stream, peak, peak_kind, fp64_pk)
+            sacc = {}
+            if not args.no_cpu_baseline:
+                scb = cpu_baseline(scfg, keep=not args.no_accuracy)
+                if not args.no_accuracy:
+                    sacc["vs_oracle"] = vs_oracle(cpu_sample_cfg(scfg), scb.pop("_F"), scb.pop("_fx"),
+                                                  scb["steps"], stream)
+                scb.pop("_F", None); scb.pop("_fx", None)
+                sub3["cpu_baseline"] = scb
+            if not args.no_accuracy:
+                sacc["fp32_vs_fp64"] = fp32_vs_fp64(scfg, min(args.steps, 10), stream)
+            if sacc:
+                sub3["accuracy"] = sacc
+            line["sphere"] = sub3
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

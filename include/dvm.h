@@ -54,6 +54,7 @@ enum { DVM_FP32 = 32, DVM_FP64 = 64 };
 enum { DVM_UPWIND = 0, DVM_MUSCL = 1 };
 enum { DVM_EXPLICIT = 0, DVM_IMEX = 1 };   /* time schemes, see dvm_set_time_scheme */
 enum { DVM_BGK = 0, DVM_SHAKHOV = 1 };     /* collision models, see dvm_set_collision_model */
+enum { DVM_EQ_DIRECT = 0, DVM_EQ_CONSERVATIVE = 1 };   /* equilibrium moments, see dvm_set_equilibrium */
 enum { DVM_BC_PERIODIC = 0, DVM_BC_MAXWELLIAN = 1, DVM_BC_ZEROGRAD = 2 };
 enum { DVM_SHAPE_NONE = 0, DVM_SHAPE_CIRCLE = 1, DVM_SHAPE_ELLIPSE = 2, DVM_SHAPE_SPHERE = 3 };
 enum { DVM_GAS = 0, DVM_CUT = 1, DVM_SOLID = 2 };
@@ -147,6 +148,23 @@ int dvm_set_time_scheme(dvm_ctx *ctx, int scheme);
  * adjoint is BGK only.  Errors: DVM_ERR_ARG (model or Pr), DVM_ERR_UNSUPPORTED. */
 int dvm_set_collision_model(dvm_ctx *ctx, int model, double Pr);
 
+/* Moments that set the BGK equilibrium of each control volume (Sec. 3.1).
+ * DVM_EQ_DIRECT (the default): the direct discrete moments rho, u, T of the
+ * state (Eq. MacroscopicDDv).  DVM_EQ_CONSERVATIVE: the (rho, u, T) whose
+ * discrete equilibrium on the velocity grid (f_eq = M, 2D g_eq = T/2 M) has
+ * the discrete mass, momentum and energy of the state, found every step by
+ * Newton's method from the direct moments (one kernel, one thread per cell;
+ * FP32 or FP64 as the state), so that the collision term conserves them
+ * exactly on coarse velocity grids too.  The relaxation time stays
+ * tau0 / rho with the direct density.  Both time schemes (the semi-implicit
+ * one takes the parameters of the transported state); BGK only: with the
+ * Shakhov model, here or in dvm_set_collision_model, DVM_ERR_UNSUPPORTED,
+ * and the drag adjoint refuses the conservative mode.  A Newton iteration
+ * that does not converge (10 steps) or leaves rho or T non-positive makes the
+ * step fail with DVM_ERR_NONPHYSICAL.  Errors: DVM_ERR_ARG (mode),
+ * DVM_ERR_UNSUPPORTED, DVM_ERR_OOM. */
+int dvm_set_equilibrium(dvm_ctx *ctx, int mode);
+
 /* Place the obstacle and build the Appendix A geometry on the device (level
  * set, cell types, edge lengths, wall edges, areas, control volumes).
  * Errors: DVM_ERR_GEOMETRY, DVM_ERR_ARG. */
@@ -219,10 +237,54 @@ int dvm_check(dvm_ctx *ctx);
 int dvm_graphs(dvm_ctx *ctx, int enable);
 
 /* Per-cell moments of the current state (Eq. MacroscopicDDv): density,
- * velocity and temperature into host arrays of ncell entries (uz may be NULL
- * in 2D).  The velocity sums are compensated in the state precision and the
- * moments formed from them in FP64.  Solid cells give 0. */
-int dvm_moments(dvm_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *T);
+ * velocity and temperature into arrays of ncell entries (any pointer may be
+ * NULL; uz is 0 in 2D).  on_device = 0: host arrays; 1: device arrays on the
+ * context's device (written on the context's stream, which the call
+ * synchronises).  The velocity sums are compensated in the state precision
+ * and the moments formed from them in FP64.  Solid cells give 0.
+ * Errors: DVM_ERR_STATE on a velocity-split context (its moments need the
+ * sums over every rank), DVM_ERR_CUDA. */
+int dvm_moments(dvm_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *T, int on_device);
+
+/* Velocity split (Sec. 5.2, "velocity parallelization"): each rank holds
+ * every cell for a slab of the velocity grid, transports and relaxes its own
+ * velocities, and the ranks exchange one sum per step.  2D and 3D, explicit
+ * scheme, BGK (direct or conservative equilibrium), fixed or (2D) rotating
+ * obstacle.
+ *
+ * dvm_set_velocity_split declares that this context's velocity grid (given
+ * to dvm_create) is the rows [k0, k0 + n) of the last axis (v_y in 2D, v_z in
+ * 3D) of the whole grid `global` (the other axes and the step equal; k0 an
+ * integer).  Call it right after dvm_create, before dvm_set_body and any
+ * state.  Unless dvm_physics gave dt, the time step becomes the CFL step of
+ * the whole grid, so every rank steps with the same dt.  The context then
+ * steps only through the two calls below; dvm_step and dvm_moments return
+ * DVM_ERR_STATE, and dvm_mass gives the mass of this rank's velocities (sum
+ * it over the ranks).
+ *
+ * One step:
+ *   dvm_split_begin(ctx, xbuf)   enqueues the fusion of merged control
+ *       volumes and writes this rank's contributions to xbuf, a device buffer
+ *       of dvm_split_size FP64 elements (in both state precisions):
+ *       the moment sums of every cell, [D + 2][ncell] (2D: sum f, vx f,
+ *       vy f, |v|^2/2 f + g; 3D: sum F, vx F, vy F, vz F, |v|^2/2 F, over
+ *       this rank's velocities, Eq. MacroscopicDDv), then the wall sums of
+ *       every wall cell (2D [wall slot][8], 3D [wall slot][14]: outgoing
+ *       c f, incoming c M[1, u_w, T_w] and the stress products, Eqs.
+ *       BoundaryDDv, StressTensorDD);
+ *   the caller sums xbuf element-wise over the ranks, in place, on the
+ *       context's stream (an all-reduce: the only exchange of the step);
+ *   dvm_split_finish(ctx, xbuf)  finishes the step from the summed xbuf:
+ *       wall density, force, torque and rotation (identical on every rank),
+ *       fluxes, relaxation and the control volumes of this rank's velocities.
+ * Both calls are asynchronous; dvm_check reads the error flags.  The ranks
+ * must hold the same problem (grid, body, boundaries) and step in lockstep.
+ * Errors: DVM_ERR_ARG (not a slab, null buffer), DVM_ERR_STATE (order),
+ * DVM_ERR_UNSUPPORTED (semi-implicit, Shakhov), DVM_ERR_CUDA. */
+int dvm_set_velocity_split(dvm_ctx *ctx, const dvm_vgrid *global);
+int dvm_split_size(dvm_ctx *ctx, size_t *count);
+int dvm_split_begin(dvm_ctx *ctx, void *xbuf);
+int dvm_split_finish(dvm_ctx *ctx, void *xbuf);
 
 /* Force (F[0..2]) and torque about the z axis exerted by the gas on the body
  * at the start of the last step (Eqs. eq-force, eq-torque), FP64. */
@@ -291,6 +353,33 @@ int dvm_drag_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, double *J, 
                      double *gbc0, double *gbc1, double *gbc2, double *gbc3, double *gprim0,
                      double *ms_forward, double *ms_reverse);
 
+/* Discrete adjoint of nsteps steps for a general objective (the paper has
+ * no adjoint; the step of Sec. 3.3.5 is differentiated as it stands, with
+ * the same restrictions as dvm_drag_adjoint: 2D, fixed obstacle, explicit
+ * scheme, BGK with the direct moments):
+ *   J = [with_drag] F_x(F^N) + <seed, F^N>,
+ * F^N the state after nsteps steps as dvm_get_state returns it.
+ *   seed     dJ/dF^N of the linear part, public layout [cell][comp][p] in
+ *            the state precision, host or device (seed_on_device); nullable
+ *            if with_drag
+ *   lambda0  receives dJ/dF^0, public layout and state precision, host or
+ *            device (lambda0_on_device); nullable
+ *   J        receives F_x(F^N) when with_drag, else 0
+ *   gTw, gbc0..3, gprim0  as in dvm_drag_adjoint, for this J
+ * The context is left at F^N.  Errors as dvm_drag_adjoint, and DVM_ERR_ARG
+ * for no objective. */
+int dvm_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, int with_drag, const void *seed,
+                int seed_on_device, void *lambda0, int lambda0_on_device, double *J, double *gTw,
+                double *gbc0, double *gbc1, double *gbc2, double *gbc3, double *gprim0);
+
+/* One transposed step (vector-Jacobian product of the step of Sec. 3.3.5):
+ * lambda_n = (dF^{n+1}/dF^n)^T lambda_np1 around the current state F^n, and
+ * gTw[nseg] (or [1]) = <lambda_np1, dF^{n+1}/dT_w>.  Both buffers in the
+ * public layout and state precision, host (on_device = 0) or device (1).
+ * The context advances one step, to F^{n+1}.  dvm_adjoint with nsteps = 1,
+ * no drag and the seed lambda_np1. */
+int dvm_step_vjp(dvm_ctx *ctx, const void *lambda_np1, void *lambda_n, int on_device, double *gTw);
+
 /* Live timing of one kernel: enable = 1 the fused bulk stream-and-relax
  * kernel, 2 the Shakhov term (dvm_set_collision_model), 0 off.  Every step
  * records a CUDA event pair around that kernel's launch on the context's
@@ -299,6 +388,15 @@ int dvm_drag_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, double *J, 
  * record. */
 int dvm_timing(dvm_ctx *ctx, int enable);
 int dvm_kernel_time(dvm_ctx *ctx, double *bulk_ms, long long *launches);
+
+/* FP64 fused multiply-add throughput of the current device in GFLOP/s
+ * (instrumentation; the paper has no counterpart): the ceiling of the FP64
+ * step, which on this part is bound by the FP64 pipe rather than by HBM.  A
+ * kernel of 16 independent FMA chains per thread on 4 blocks of 256 threads
+ * per SM, timed with CUDA events on `stream` (a cudaStream_t or NULL), best
+ * of three launches after one untimed; 2 flop per FMA.  Allocates and frees
+ * a small output buffer.  Errors: DVM_ERR_ARG, DVM_ERR_CUDA. */
+int dvm_fp64_peak(void *stream, double *gflops);
 
 /* Number of kernels this context has launched since creation. */
 int dvm_launches(dvm_ctx *ctx, long long *count);

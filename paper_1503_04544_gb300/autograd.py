@@ -12,6 +12,10 @@ is requested it is computed together with J in one call.
 The Mach number sets u = Ma sqrt(5/3) in the inflow Maxwellian and in the
 initial state, so dJ/dMach = sqrt(5/3) (sum of dJ/du_x over the inflow cells
 and over the initial-state cells).
+
+``evolve(F0, cfg, nsteps)`` is the state after ``nsteps`` steps as a tensor
+differentiable in the initial state F0; its backward pass is the adjoint of
+the whole sweep with the incoming gradient as the seed (dvm_adjoint).
 """
 from __future__ import annotations
 
@@ -65,3 +69,42 @@ def drag(tw_seg: torch.Tensor, mach: torch.Tensor, nx: int = 256, nv: int = 32, 
          checkpoint_every: int = 20, precision: int = dvm.FP32) -> torch.Tensor:
     """Drag of the per-sector-temperature cylinder after ``nsteps`` steps."""
     return DragFunction.apply(tw_seg, mach, nx, nv, nsteps, checkpoint_every, precision)
+
+
+class EvolveFunction(torch.autograd.Function):
+    """F^N = Step^N(F^0) of a fixed-obstacle 2D problem, differentiable with
+    respect to the initial state: the backward pass is the library's
+    checkpointed adjoint with the seed dL/dF^N (dvm_adjoint, no drag term),
+    all on the GPU."""
+
+    @staticmethod
+    def forward(ctx, F0, cfg, nsteps, checkpoint_every, precision):
+        s = dvm.Solver(cfg, precision, stream=torch.cuda.current_stream().cuda_stream)
+        try:
+            s.set_state(F0.detach().contiguous())
+            s.step(nsteps)
+            FN = torch.empty_like(F0)
+            s.get_state(FN)
+        finally:
+            s.close()
+        ctx.save_for_backward(F0.detach())
+        ctx.cfg, ctx.nsteps, ctx.K, ctx.precision = cfg, nsteps, checkpoint_every, precision
+        return FN
+
+    @staticmethod
+    def backward(ctx, gFN):
+        (F0,) = ctx.saved_tensors
+        s = dvm.Solver(ctx.cfg, ctx.precision, stream=torch.cuda.current_stream().cuda_stream)
+        try:
+            s.set_state(F0.contiguous())
+            out = s.adjoint(ctx.nsteps, ctx.K, with_drag=False, seed=gFN.contiguous().to(F0.dtype))
+        finally:
+            s.close()
+        return out["lambda0"], None, None, None, None
+
+
+def evolve(F0: torch.Tensor, cfg: dict, nsteps: int, checkpoint_every: int = 20) -> torch.Tensor:
+    """``nsteps`` steps of ``cfg`` from the CUDA state ``F0`` (public layout;
+    float32 or float64 sets the precision), differentiable in ``F0``."""
+    precision = dvm.FP32 if F0.dtype == torch.float32 else dvm.FP64
+    return EvolveFunction.apply(F0, cfg, nsteps, checkpoint_every, precision)

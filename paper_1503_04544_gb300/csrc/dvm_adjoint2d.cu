@@ -1421,9 +1421,28 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
     return cudaGetLastError();
 }
 
+// Adds a state in the public layout [cell][comp][p] (a linear objective's
+// dJ/dF^N) to lambda in the padded device layout (interior cells only; the
+// pads stay 0).
+template <typename T>
+__global__ void k_adj_seed(Grid2D g, const T *pub, T *lam)
+{
+    const long k = blockIdx.x;            // one block per cell, threads over (comp, p)
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= 2 * g.nv) return;
+    const int comp = e >= g.nv, p = e - comp * g.nv;
+    const long d = ebase<T>(g, comp, p) + pcell(g, k) * Vec<T>::W;
+    lam[d] += pub[k * 2L * g.nv + e];
+}
+
+// The adjoint sweep for J = [with_drag] F_x(F^N) + <seed, F^N>: the drag
+// objective seeds lambda^N through the wall stress and the fusion transpose,
+// a linear functional adds its dJ/dF^N = seed (public layout, host or
+// device); lambda^0 = dJ/dF^0 can be returned in the public layout.
 template <typename T>
 int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double *const *gbc, double *gprim0,
-                   double *ms_forward, double *ms_reverse)
+                   double *ms_forward, double *ms_reverse, int with_drag, const void *seed, int seed_dev,
+                   void *lam0, int lam0_dev)
 {
     if (!c->adj) c->adj = new AdjWork();
     AdjWork &w = *static_cast<AdjWork *>(c->adj);
@@ -1583,11 +1602,24 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     // cells in no control volume and the pads keep lambda = 0 in both buffers
     AC(cudaMemsetAsync(w.lam[0], 0, bytes, c->stream));
     AC(cudaMemsetAsync(w.lam[1], 0, bytes, c->stream));
-    if (w.nw > 0)
-        k_adj_wall_obj<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, (const T *)c->f[c->cur], lamA,
-                                                        w.gtw, w.jwall);
-    if (w.ncv > 0)
-        k_adj_fuseT<T><<<dim3((unsigned)w.ncv, nba(2L * c->nvp, 256)), 256, 0, c->stream>>>(a, lamA);
+    AC(cudaMemsetAsync(w.jwall, 0, sizeof(double) * c->list_cap, c->stream));
+    if (with_drag) {
+        if (w.nw > 0)
+            k_adj_wall_obj<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, (const T *)c->f[c->cur], lamA,
+                                                            w.gtw, w.jwall);
+        if (w.ncv > 0)
+            k_adj_fuseT<T><<<dim3((unsigned)w.ncv, nba(2L * c->nvp, 256)), 256, 0, c->stream>>>(a, lamA);
+    }
+    // the public-layout staging buffer of the seed and of lambda^0
+    if ((seed || lam0) && !c->d_pub) AC(cudaMalloc(&c->d_pub, c->state_elems * c->elem));
+    if (seed) {
+        // a linear functional of F^N as the step leaves it (members of a
+        // merged control volume hold its value; no fusion transpose)
+        AC(cudaMemcpyAsync(c->d_pub, seed, c->state_elems * c->elem,
+                           seed_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+        k_adj_seed<T><<<dim3((unsigned)c->nc, nba(2L * c->nv, 256)), 256, 0, c->stream>>>(grid2d(c),
+                                                                                         (const T *)c->d_pub, lamA);
+    }
     // reverse sweep, segment by segment: recompute the segment onto the tape
     // (each step writes the next tape buffer), then apply the transposed steps
     // backwards
@@ -1673,6 +1705,12 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         if (c->bc[s] != DVM_BC_MAXWELLIAN) { std::memset(gbc[s], 0, sizeof(double) * 5 * nside[s]); continue; }
         AC(cudaMemcpyAsync(gbc[s], w.gbc + 5L * s * nmax, sizeof(double) * 5 * nside[s], cudaMemcpyDeviceToHost, c->stream));
     }
+    if (lam0) {
+        // dJ/dF^0 in the public layout
+        AC(unpack2d(c, w.lam[lin], c->d_pub));
+        AC(cudaMemcpyAsync(lam0, c->d_pub, c->state_elems * c->elem,
+                           lam0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    }
     if (gprim0) {
         if (!c->have_prim0) { set_error("dvm_drag_adjoint: gprim0 needs a state set by dvm_init_maxwellian"); return DVM_ERR_STATE; }
         k_adj_init<T><<<dim3(nba(c->nx, 32), nba(c->ny, 8)), dim3(32, 8), 0, c->stream>>>(
@@ -1706,10 +1744,13 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
 }  // namespace
 
 int drag_adjoint2d(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double *const *gbc, double *gprim0,
-                   double *ms_forward, double *ms_reverse)
+                   double *ms_forward, double *ms_reverse, int with_drag, const void *seed, int seed_dev, void *lam0,
+                   int lam0_dev)
 {
-    return c->prec == DVM_FP32 ? drag_adjoint_t<float>(c, nsteps, K, J, gTw, gbc, gprim0, ms_forward, ms_reverse)
-                               : drag_adjoint_t<double>(c, nsteps, K, J, gTw, gbc, gprim0, ms_forward, ms_reverse);
+    return c->prec == DVM_FP32 ? drag_adjoint_t<float>(c, nsteps, K, J, gTw, gbc, gprim0, ms_forward, ms_reverse,
+                                                       with_drag, seed, seed_dev, lam0, lam0_dev)
+                               : drag_adjoint_t<double>(c, nsteps, K, J, gTw, gbc, gprim0, ms_forward, ms_reverse,
+                                                        with_drag, seed, seed_dev, lam0, lam0_dev);
 }
 
 void free_adjoint2d(dvm_ctx *c)

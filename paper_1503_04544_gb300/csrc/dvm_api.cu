@@ -182,15 +182,19 @@ cudaError_t shakhov3d(dvm_ctx *c);   // the Shakhov term of the 3D step (dvm_sha
 static cudaError_t st_step(dvm_ctx *c)
 {
     cudaError_t e = c->dim == 2 ? step2d(c) : step3d(c);
-    if (e == cudaSuccess && c->model == DVM_SHAKHOV) e = c->dim == 2 ? shakhov2d(c) : shakhov3d(c);
+    // the explicit scheme adds the Shakhov term after the step; the
+    // semi-implicit one relaxes towards the Shakhov equilibrium in its
+    // relaxation kernel
+    if (e == cudaSuccess && c->model == DVM_SHAKHOV && c->time_scheme == DVM_EXPLICIT)
+        e = c->dim == 2 ? shakhov2d(c) : shakhov3d(c);
     return e;
 }
 
 // Why the Shakhov model cannot run on this context (nullptr: it can).
 static const char *shakhov_unsupported(const dvm_ctx *c)
 {
-    if (c->time_scheme != DVM_EXPLICIT) return "Shakhov model: the explicit time scheme only";
-    if (c->moving) return "Shakhov model: fixed obstacles only in this library version";
+    if (c->split) return "Shakhov model: not with a velocity split (the heat flux needs its own exchange)";
+    if (c->eq_mode != DVM_EQ_DIRECT) return "Shakhov model: the direct moments only (the conservative equilibrium is BGK)";
     return nullptr;
 }
 
@@ -299,6 +303,7 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     c->Kn = ph->Kn; c->Lref = ph->Lref; c->cfl = ph->cfl;
     // tau = sqrt(pi)/2 (rho0/rho) Kn L / sqrt(2 R T0), Sec. 5, R = T0 = rho0 = 1
     c->tau0 = std::sqrt(M_PI) / 2.0 * c->Kn * c->Lref / std::sqrt(2.0);
+    c->dt_given = ph->dt > 0;
     if (ph->dt > 0) c->dt = ph->dt;
     else {
         double s = axis_vmax(c->nvx, c->vxmin, c->vxmax) / c->dx + axis_vmax(c->nvy, c->vymin, c->vymax) / c->dy;
@@ -356,6 +361,10 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
         c->S = best;
     }
     const int nmom = dim == 2 ? 4 : 5;
+    // the whole velocity grid is this context's own until a velocity split
+    c->gnv[0] = c->nvx; c->gnv[1] = c->nvy; c->gnv[2] = dim == 3 ? c->nvz : 1;
+    c->gv0[0] = c->vxmin; c->gv0[1] = c->vymin; c->gv0[2] = c->vzmin;
+    c->gdv[0] = c->dvx; c->gdv[1] = c->dvy; c->gdv[2] = dim == 3 ? c->dvz : 1.0;
     {
         cudaError_t e = cudaStreamCreateWithFlags(&c->wstream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_wfork, cudaEventDisableTiming);
@@ -463,7 +472,7 @@ void dvm_destroy(dvm_ctx *c)
     cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->counts);
     cudaFree(c->wphi); cudaFree(c->wcontrib); cudaFree(c->cvinfo);
     cudaFree(c->d_body); cudaFree(c->d_hist); cudaFree(c->d_err);
-    cudaFree(c->d_scratch); cudaFree(c->d_out);
+    cudaFree(c->d_scratch); cudaFree(c->d_out); cudaFree(c->eqp); cudaFree(c->split_in); cudaFree(c->cv_ratio);
     cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
     for (int s = 0; s < 6; ++s) cudaFree(c->d_bcstate[s]);
     cudaFree(c->d_prim0);
@@ -587,6 +596,11 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
         CK(cudaMemcpy(c->d_segdir, b->seg_dir, sizeof(double) * 2 * b->nseg, cudaMemcpyHostToDevice));
     }
     c->moving = b->shape != DVM_SHAPE_NONE && b->movable;
+    // per-cell control-volume area ratios of a moving obstacle (the Shakhov
+    // term scales with them)
+    cudaFree(c->cv_ratio);
+    c->cv_ratio = nullptr;
+    if (c->moving) CK(cudaMalloc(&c->cv_ratio, sizeof(double) * (size_t)c->nc));
     // box of cells that can be non-gas or have a non-gas cell within reach
     if (b->shape == DVM_SHAPE_NONE) {
         c->i0 = c->i1 = c->j0 = c->j1 = 0;
@@ -749,6 +763,13 @@ static int problem_hash(dvm_ctx *c, uint64_t *out)
                           c->vymin, c->vymax, c->vzmin, c->vzmax, c->Kn, c->Lref, c->cfl, c->Pr};
     f.bytes(ext, sizeof(ext));
     f.val((int32_t)c->model);
+    f.val((int32_t)c->eq_mode);
+    f.val((int32_t)c->split);
+    for (int d = 0; d < 3; ++d) {
+        f.val((int32_t)c->gnv[d]);
+        f.bytes(&c->gv0[d], sizeof(double));
+        f.bytes(&c->gdv[d], sizeof(double));
+    }
     for (int side = 0; side < 2 * c->dim; ++side) {
         f.val((int32_t)c->bc[side]);
         if (c->bc[side] == DVM_BC_MAXWELLIAN && c->d_bcstate[side]) {
@@ -874,6 +895,10 @@ int dvm_step_async(dvm_ctx *c, int nsteps)
         }
     if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return DVM_ERR_ARG; }
+    if (c->split) {
+        set_error("a velocity-split context steps through dvm_split_begin and dvm_split_finish");
+        return DVM_ERR_STATE;
+    }
     if (c->model == DVM_SHAKHOV)
         if (const char *why = shakhov_unsupported(c)) { set_error(why); return DVM_ERR_UNSUPPORTED; }
     int s = 0;
@@ -902,8 +927,8 @@ int dvm_set_time_scheme(dvm_ctx *c, int scheme)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
     if (scheme != DVM_EXPLICIT && scheme != DVM_IMEX) { set_error("time scheme must be DVM_EXPLICIT or DVM_IMEX"); return DVM_ERR_ARG; }
-    if (scheme == DVM_IMEX && c->model == DVM_SHAKHOV) {
-        set_error("Shakhov model: the explicit time scheme only");
+    if (scheme == DVM_IMEX && c->split) {
+        set_error("velocity split: the explicit scheme only");
         return DVM_ERR_UNSUPPORTED;
     }
     c->time_scheme = scheme;
@@ -920,6 +945,29 @@ int dvm_set_collision_model(dvm_ctx *c, int model, double Pr)
     }
     c->model = model;
     c->Pr = model == DVM_SHAKHOV ? Pr : 1.0;
+    return DVM_OK;
+}
+
+int dvm_set_equilibrium(dvm_ctx *c, int mode)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (mode != DVM_EQ_DIRECT && mode != DVM_EQ_CONSERVATIVE) {
+        set_error("equilibrium mode must be DVM_EQ_DIRECT or DVM_EQ_CONSERVATIVE");
+        return DVM_ERR_ARG;
+    }
+    if (mode == DVM_EQ_CONSERVATIVE && c->model != DVM_BGK) {
+        set_error("the conservative equilibrium is implemented for the BGK model");
+        return DVM_ERR_UNSUPPORTED;
+    }
+    if (mode == DVM_EQ_CONSERVATIVE && !c->eqp) {
+        if (cudaMalloc(&c->eqp, (size_t)(c->dim + 2) * c->nc * c->elem) != cudaSuccess) {
+            cudaGetLastError();
+            c->eqp = nullptr;
+            set_error("dvm_set_equilibrium: out of device memory");
+            return DVM_ERR_OOM;
+        }
+    }
+    c->eq_mode = mode;
     return DVM_OK;
 }
 
@@ -1065,11 +1113,36 @@ int dvm_rollback(dvm_ctx *c, int enable)
     return DVM_OK;
 }
 
-int dvm_moments(dvm_ctx *c, double *rho, double *ux, double *uy, double *uz, double *T)
+// Scatter of the [cell][5] moment records into up to five device arrays.
+__global__ void k_scatter5(const double *src, long nc, double *a0, double *a1, double *a2, double *a3, double *a4)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const double *r = src + 5 * k;
+    if (a0) a0[k] = r[0];
+    if (a1) a1[k] = r[1];
+    if (a2) a2[k] = r[2];
+    if (a3) a3[k] = r[3];
+    if (a4) a4[k] = r[4];
+}
+
+int dvm_moments(dvm_ctx *c, double *rho, double *ux, double *uy, double *uz, double *T, int on_device)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (c->split) {
+        set_error("dvm_moments: a velocity-split context holds a slab of the velocity grid; "
+                  "the moments need the sums over every rank");
+        return DVM_ERR_STATE;
+    }
     const size_t nc = (size_t)c->nc;
     CK(st_moments(c, c->d_out));
+    if (on_device) {
+        k_scatter5<<<(unsigned)((nc + 255) / 256), 256, 0, c->stream>>>(c->d_out, (long)nc, rho, ux, uy, uz, T);
+        CK(cudaGetLastError());
+        c->launches += 1;
+        CK(cudaStreamSynchronize(c->stream));
+        return DVM_OK;
+    }
     std::vector<double> h(5 * nc);
     CK(cudaMemcpyAsync(h.data(), c->d_out, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1080,6 +1153,111 @@ int dvm_moments(dvm_ctx *c, double *rho, double *ux, double *uy, double *uz, dou
         if (uz) uz[k] = h[5 * k + 3];
         if (T) T[k] = h[5 * k + 4];
     }
+    return DVM_OK;
+}
+
+// ---- velocity split (Sec. 5.2)
+int dvm_set_velocity_split(dvm_ctx *c, const dvm_vgrid *gv)
+{
+    if (!c || !gv) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (c->have_state || c->body.shape != DVM_SHAPE_NONE) {
+        set_error("velocity split: set it right after dvm_create, before the body and the state");
+        return DVM_ERR_STATE;
+    }
+    if (c->time_scheme != DVM_EXPLICIT || c->model != DVM_BGK) {
+        set_error("velocity split: the explicit scheme and the BGK model only");
+        return DVM_ERR_UNSUPPORTED;
+    }
+    const bool d3 = c->dim == 3;
+    const int gn[3] = {gv->nvx, gv->nvy, d3 ? gv->nvz : 1};
+    const double glo[3] = {gv->vxmin, gv->vymin, gv->vzmin}, ghi[3] = {gv->vxmax, gv->vymax, gv->vzmax};
+    for (int d = 0; d < c->dim; ++d)
+        if (gn[d] < 1 || gn[d] > kMaxAxisNv || !(ghi[d] > glo[d])) {
+            set_error("velocity split: bad whole velocity grid (1 to 64 points per axis)");
+            return DVM_ERR_ARG;
+        }
+    // the split axis is the last one (v_y in 2D, v_z in 3D); this context's
+    // grid must be its rows [k0, k0 + n) with the other axes equal
+    const int ax = c->dim - 1;
+    const double gstep = (ghi[ax] - glo[ax]) / gn[ax];
+    double *lo = d3 ? &c->vzmin : &c->vymin, *hi = d3 ? &c->vzmax : &c->vymax, *step = d3 ? &c->dvz : &c->dvy;
+    const int nloc = d3 ? c->nvz : c->nvy;
+    const double k0d = (*lo - glo[ax]) / gstep;
+    const long k0 = std::lround(k0d);
+    bool ok = std::fabs(gstep - *step) <= 1e-12 * gstep && std::fabs(k0d - (double)k0) <= 1e-9 && k0 >= 0 &&
+              k0 + nloc <= gn[ax] && gv->nvx == c->nvx && gv->vxmin == c->vxmin && gv->vxmax == c->vxmax;
+    if (d3) ok = ok && gv->nvy == c->nvy && gv->vymin == c->vymin && gv->vymax == c->vymax;
+    if (!ok) {
+        set_error("velocity split: the context's velocity grid is not a slab of rows of the last axis of the whole "
+                  "grid (the other axes and the step equal, the first row an integer number of steps from the start)");
+        return DVM_ERR_ARG;
+    }
+    for (int d = 0; d < 3; ++d) {
+        c->gnv[d] = d < c->dim ? gn[d] : 1;
+        c->gv0[d] = d < c->dim ? glo[d] : 0.0;
+        c->gdv[d] = d < c->dim ? (ghi[d] - glo[d]) / gn[d] : 1.0;
+    }
+    // every rank takes the split axis' step of the whole grid and its first
+    // row from the same expression, so that the quantities the ranks share
+    // (the wall sums' dv, the force) are formed from bit-identical numbers
+    *step = gstep;
+    *lo = glo[ax] + (double)k0 * gstep;
+    *hi = *lo + nloc * gstep;
+    if (!c->dt_given) {
+        // every rank takes the CFL time step of the whole velocity grid
+        double sum = 0;
+        for (int d = 0; d < c->dim; ++d)
+            sum += axis_vmax(gn[d], glo[d], ghi[d]) / (d == 0 ? c->dx : d == 1 ? c->dy : c->dz);
+        c->dt = c->cfl / sum;
+    }
+    CK(d3 ? tables3d(c) : tables2d(c));
+    CK(cudaStreamSynchronize(c->stream));
+    const int nmom = c->dim + 2;
+    if (!c->split_in) {
+        if (cudaMalloc(&c->split_in, (size_t)nmom * c->nc * c->elem) != cudaSuccess) {
+            cudaGetLastError();
+            c->split_in = nullptr;
+            set_error("dvm_set_velocity_split: out of device memory");
+            return DVM_ERR_OOM;
+        }
+    }
+    c->split = true;
+    return DVM_OK;
+}
+
+int dvm_split_size(dvm_ctx *c, size_t *count)
+{
+    if (!c || !count) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (!c->split) { set_error("dvm_split_size: no velocity split set"); return DVM_ERR_STATE; }
+    const size_t nmom = c->dim + 2, nwall = c->dim == 2 ? 8 : 14;
+    *count = nmom * c->nc + nwall * (c->body.shape != DVM_SHAPE_NONE ? c->list_cap : 0);
+    return DVM_OK;
+}
+
+int dvm_split_begin(dvm_ctx *c, void *xbuf)
+{
+    if (!c || !xbuf) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (!c->split) { set_error("dvm_split_begin: no velocity split set"); return DVM_ERR_STATE; }
+    if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
+    if (c->split_begun) { set_error("dvm_split_begin: the previous step is not finished"); return DVM_ERR_STATE; }
+    for (int d = 0; d < c->dim; ++d)
+        if ((c->bc[2 * d] == DVM_BC_PERIODIC) != (c->bc[2 * d + 1] == DVM_BC_PERIODIC)) {
+            set_error("opposite sides must both be periodic or both not");
+            return DVM_ERR_ARG;
+        }
+    cudaError_t e = c->dim == 2 ? split_step2d(c, 1, xbuf) : split_step3d(c, 1, xbuf);
+    if (e != cudaSuccess) return cuda_fail(e, "dvm_split_begin");
+    c->split_begun = true;
+    return DVM_OK;
+}
+
+int dvm_split_finish(dvm_ctx *c, void *xbuf)
+{
+    if (!c || !xbuf) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (!c->split || !c->split_begun) { set_error("dvm_split_finish: no dvm_split_begin pending"); return DVM_ERR_STATE; }
+    cudaError_t e = c->dim == 2 ? split_step2d(c, 2, xbuf) : split_step3d(c, 2, xbuf);
+    c->split_begun = false;
+    if (e != cudaSuccess) return cuda_fail(e, "dvm_split_finish");
     return DVM_OK;
 }
 
@@ -1204,17 +1382,21 @@ int dvm_geometry3d(dvm_ctx *c, int8_t *type, int8_t *cgas, double *ax, double *a
     return DVM_OK;
 }
 
-int dvm_drag_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, double *J, double *gTw, double *gbc0,
-                     double *gbc1, double *gbc2, double *gbc3, double *gprim0, double *ms_forward,
-                     double *ms_reverse)
+// The checks every adjoint entry point makes.
+static int adjoint_checks(dvm_ctx *c, int nsteps, int checkpoint_every)
 {
-    if (!c || !J || !gTw) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (!c) { set_error("null argument"); return DVM_ERR_ARG; }
     if (c->dim != 2) { set_error("dvm_drag_adjoint: 2D contexts only"); return DVM_ERR_UNSUPPORTED; }
     if (c->time_scheme != DVM_EXPLICIT) {
         set_error("dvm_drag_adjoint: the explicit time scheme only");
         return DVM_ERR_UNSUPPORTED;
     }
     if (c->model != DVM_BGK) { set_error("dvm_drag_adjoint: the BGK model only"); return DVM_ERR_UNSUPPORTED; }
+    if (c->eq_mode != DVM_EQ_DIRECT) {
+        set_error("dvm_drag_adjoint: the direct moments only (not the conservative equilibrium)");
+        return DVM_ERR_UNSUPPORTED;
+    }
+    if (c->split) { set_error("dvm_drag_adjoint: not with a velocity split"); return DVM_ERR_UNSUPPORTED; }
     if (c->body.shape == DVM_SHAPE_NONE || c->moving) {
         set_error("dvm_drag_adjoint: needs a fixed obstacle"); return DVM_ERR_UNSUPPORTED;
     }
@@ -1225,10 +1407,44 @@ int dvm_drag_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, double *J, do
             set_error("opposite sides must both be periodic or both not");
             return DVM_ERR_ARG;
         }
+    return DVM_OK;
+}
+
+int dvm_drag_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, double *J, double *gTw, double *gbc0,
+                     double *gbc1, double *gbc2, double *gbc3, double *gprim0, double *ms_forward,
+                     double *ms_reverse)
+{
+    if (!c || !J || !gTw) { set_error("null argument"); return DVM_ERR_ARG; }
+    int rc = adjoint_checks(c, nsteps, checkpoint_every);
+    if (rc != DVM_OK) return rc;
     double *gbc[4] = {gbc0, gbc1, gbc2, gbc3};
-    int rc = drag_adjoint2d(c, nsteps, checkpoint_every, J, gTw, gbc, gprim0, ms_forward, ms_reverse);
+    rc = drag_adjoint2d(c, nsteps, checkpoint_every, J, gTw, gbc, gprim0, ms_forward, ms_reverse, 1, nullptr, 0,
+                        nullptr, 0);
     if (rc != DVM_OK) return rc;
     return check_flags(c);
+}
+
+int dvm_adjoint(dvm_ctx *c, int nsteps, int checkpoint_every, int with_drag, const void *seed, int seed_on_device,
+                void *lambda0, int lambda0_on_device, double *J, double *gTw, double *gbc0, double *gbc1,
+                double *gbc2, double *gbc3, double *gprim0)
+{
+    if (!c || !J || !gTw) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (!with_drag && !seed) { set_error("dvm_adjoint: no objective (with_drag = 0 and no seed)"); return DVM_ERR_ARG; }
+    int rc = adjoint_checks(c, nsteps, checkpoint_every);
+    if (rc != DVM_OK) return rc;
+    double *gbc[4] = {gbc0, gbc1, gbc2, gbc3};
+    rc = drag_adjoint2d(c, nsteps, checkpoint_every, J, gTw, gbc, gprim0, nullptr, nullptr, with_drag ? 1 : 0, seed,
+                        seed_on_device, lambda0, lambda0_on_device);
+    if (rc != DVM_OK) return rc;
+    return check_flags(c);
+}
+
+int dvm_step_vjp(dvm_ctx *c, const void *lambda_np1, void *lambda_n, int on_device, double *gTw)
+{
+    if (!c || !lambda_np1 || !lambda_n || !gTw) { set_error("null argument"); return DVM_ERR_ARG; }
+    double J = 0;
+    return dvm_adjoint(c, 1, 1, 0, lambda_np1, on_device, lambda_n, on_device, &J, gTw, nullptr, nullptr, nullptr,
+                       nullptr, nullptr);
 }
 
 int dvm_timing(dvm_ctx *c, int enable)

@@ -185,6 +185,16 @@ struct dvm_ctx {
     int time_scheme;              // DVM_EXPLICIT or DVM_IMEX (dvm_set_time_scheme)
     int model;                    // DVM_BGK or DVM_SHAKHOV (dvm_set_collision_model)
     double Pr;                    // Prandtl number of the Shakhov model
+    int eq_mode;                  // DVM_EQ_DIRECT or DVM_EQ_CONSERVATIVE (dvm_set_equilibrium)
+    int gnv[3];                   // the whole velocity grid: points, first velocity and step per axis
+    double gv0[3], gdv[3];        //   (this context's own grid unless a velocity split is set)
+    bool split;                   // dvm_set_velocity_split: steps through dvm_split_begin / _finish
+    bool split_begun;             // dvm_split_begin done, dvm_split_finish pending
+    void *split_in;               // [4 or 5][nc] summed moment sums in the state precision (velocity split)
+    double *cv_ratio;             // [nc] area ratio S^n / S^{n+1,*} of each special cell's control volume
+                                  //   (Shakhov with a moving obstacle)
+    bool dt_given;                // dt came from dvm_physics, not from the CFL rule
+    void *eqp;                    // [dim + 2][nc] conservative equilibrium parameters (state precision)
     void *snap_f, *snap_part;     // dvm_step: state and moment sums at the last checked step
     void *snap_scratch;           // dvm_step: moment sums of the state check
     void *snap_body;              // dvm_step: rigid-body record at the last checked step
@@ -212,6 +222,9 @@ cudaError_t partials_from_state2d(dvm_ctx *c);
 cudaError_t init_maxwellian2d(dvm_ctx *c, const double *d_prim);
 cudaError_t step2d(dvm_ctx *c);
 cudaError_t shakhov2d(dvm_ctx *c);                             // Eq. ShakhovDD term after a step (dvm_shakhov2d.cu)
+cudaError_t eqpar(dvm_ctx *c, const void *part, int S);         // conservative equilibrium parameters into c->eqp (dvm_equilibrium.cu)
+cudaError_t split_step2d(dvm_ctx *c, int phase, void *xbuf);    // velocity split: 1 begin, 2 finish (dvm_step2d.cu)
+cudaError_t split_step3d(dvm_ctx *c, int phase, void *xbuf);    // the same in 3D (dvm_step3d.cu)
 cudaError_t fusion2d(dvm_ctx *c, void *f, void *part);          // Eq. FusionDD on a buffer
 cudaError_t mass2d(dvm_ctx *c, double *d_scratch, double *d_out);
 cudaError_t moments_out2d(dvm_ctx *c, double *d_out);
@@ -228,7 +241,8 @@ int encode_tensor_map2d(dvm_ctx *c, void *buf, CUtensorMap *map);
 int encode_bits_map2d(dvm_ctx *c, void *buf, CUtensorMap *map);  // limiter-branch words (bits_pitch rows)
 // adjoint (dvm_adjoint2d.cu)
 int drag_adjoint2d(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double *const *gbc, double *gprim0,
-                   double *ms_forward, double *ms_reverse);
+                   double *ms_forward, double *ms_reverse, int with_drag, const void *seed, int seed_dev, void *lam0,
+                   int lam0_dev);
 void free_adjoint2d(dvm_ctx *c);
 
 // 3D (dvm_geometry3d.cu, dvm_step3d.cu)

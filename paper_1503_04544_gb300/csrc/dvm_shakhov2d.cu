@@ -5,12 +5,13 @@
 //   g_S = T/2 M [1 + (1 - Pr) c.q (|c|^2/T - 2) / (5 P T)],
 // c = v - u, P = rho T (R = 1), where q = sum c (|c|^2/2 f + g) dv is the heat
 // flux of the control volume at t^n (Eq. MacroscopicDDv).  The step kernels
-// relax towards M; with a fixed obstacle (area ratio S^n / S^{n+1,*} = 1) the
-// scheme's relaxation term differs from theirs by
-//   (dt/tau) (f_S - M) = (dt/tau) k c.q (|c|^2/T - 4) M,   k = (1 - Pr) / (5 rho T^2),
-// and the g counterpart, which k_shakhov adds to every gas cell after the
-// step, with the moments and heat flux of the cell's control volume at t^n.
-// It then rewrites the moment sums of the new state.
+// relax towards M; the scheme's relaxation term differs from theirs by
+//   a (dt/tau) (f_S - M) = a (dt/tau) k c.q (|c|^2/T - 4) M,   k = (1 - Pr) / (5 rho T^2),
+// and the g counterpart, with a = S^n / S^{n+1,*} the area ratio of the
+// control volume (1 for a fixed obstacle and for every plain cell), which
+// k_shakhov adds to every gas cell after the step, with the moments and heat
+// flux of the cell's control volume at t^n.  It then rewrites the moment sums
+// of the new state.
 #include "dvm_device.cuh"
 
 namespace dvm {
@@ -50,7 +51,8 @@ __device__ __forceinline__ double exp2_s(double x) { return exp2(x); }
 template <typename T>
 __global__ void __launch_bounds__(32 * kMomChunks)
     k_shakhov(Grid2D g, int S, T dt_tau0, T pr1, const T *fin, const T *pin, T *fout, T *pout,
-              const VCoef<T> *vt, const int32_t *master, const int8_t *type, int *err)
+              const VCoef<T> *vt, const int32_t *master, const int8_t *type, const uint8_t *flags,
+              const double *ratio, int *err)
 {
     constexpr int W = Vec<T>::W;
     using V = typename Vec<T>::type;
@@ -106,7 +108,9 @@ __global__ void __launch_bounds__(32 * kMomChunks)
     Acc<T> a4[4];
     if (gas) {
         const T A = rho / (T(2.0 * kPi) * tmp), c2 = T(kLog2e) / (T(2) * tmp);
-        const T kk = dt_tau0 * rho * pr1 / (T(5) * rho * tmp * tmp);     // (dt/tau) k
+        // a (dt/tau) k, a the area ratio of a moving obstacle's control volume
+        const T ar = ratio && (flags[cell] & kSpecial) ? (T)ratio[cell] : T(1);
+        const T kk = ar * dt_tau0 * rho * pr1 / (T(5) * rho * tmp * tmp);
         const T iT = T(1) / tmp, half = tmp / T(2);
         const long pc = nbr(g, i, j);
         long mir[4];
@@ -164,7 +168,7 @@ cudaError_t shakhov2d_t(dvm_ctx *c)
     if (e != cudaSuccess) return e;
     k_shakhov<T><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), T(1.0 - c->Pr), fin, pin, fout, pout,
                                                  (const VCoef<T> *)c->vtab, c->master, c->geo[c->gcur].type,
-                                                 c->d_err);
+                                                 c->flags, c->moving ? c->cv_ratio : nullptr, c->d_err);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return timing_mark_kernel(c, 2, 1);

@@ -58,6 +58,7 @@ __device__ __forceinline__ void gather_partials(const T *part, int S, long nc, l
 template <typename T> struct BulkArgs {
     Grid2D g;
     int S;
+    int Sin;                  // partial-sum slots of pin (S, or 1 for summed moments of a velocity split)
     const T *fin;
     T *fout;
     const T *pin;             // partial moments of f^n   [S][4][nc]
@@ -66,6 +67,7 @@ template <typename T> struct BulkArgs {
     const VCoef<T> *vt;       // [nvp]
     const ulonglong2 *pt;     // [ngrp][7] packed-pair coefficients (FP32 path)
     const int8_t *gsign;      // [ngrp][2]
+    const T *eqp;             // [4][nc] conservative equilibrium parameters, or null (direct moments)
     uint32_t *bits;           // [ngrp][bslab] limiter branches of the downwind faces (recording only)
     int bpitch;               // row pitch of the branch words
     long bslab;               // branch words per group
@@ -330,13 +332,18 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     T A = 0, c2 = 0, r = 0, gfac = 0, ux = 0, uy = 0, el0 = 0, e1x = 0, e1y = 0;
     if (plain) {
         T s[4];
-        gather_partials(a.pin, a.S, nc, cell, s);
+        gather_partials(a.pin, a.Sin, nc, cell, s);
         T rho, tmp;
         if (!primitives<T>(pick<T>(g.dv_f, g.dv), s[0], s[1], s[2], s[3], rho, ux, uy, tmp))
             atomicExch(&a.err[kErrNonphys], 1);
+        r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+        if (a.eqp) {
+            // conservative equilibrium (Sec. 3.1): tau from the direct
+            // density, the Maxwellian from the Newton parameters
+            rho = a.eqp[cell]; ux = a.eqp[nc + cell]; uy = a.eqp[2 * nc + cell]; tmp = a.eqp[3 * nc + cell];
+        }
         A = rho / (T(2.0 * kPi) * tmp);
         c2 = T(kLog2e) / (T(2) * tmp);
-        r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
         gfac = tmp / T(2);
         // log2 M(v) = el0 + e1x vx + e1y vy - c2 |v|^2 (packed path)
         if (!REC) {
@@ -534,9 +541,11 @@ struct CvArgs {
     const int32_t *counts;
     int cap;
     int S;
+    int Sin;                  // partial-sum slots of the moments read (S, or 1 for summed moments)
     int gps;                  // velocity groups per split
     const void *cvinfo;       // control-volume records
     const void *vt;           // per-velocity coefficients (state precision)
+    const void *eqp;          // [4][nc] conservative equilibrium parameters, or null
     int *err;
 };
 
@@ -589,8 +598,10 @@ __device__ int gather_members(const CvArgs &c, long m, int32_t *mem)
 
 // Control-volume records of every control volume in the list (once per
 // geometry): members from the master search, their slab indices, padding
-// mirrors, edge lengths, wall edges and the area ratios.
-__global__ void __launch_bounds__(256) k_members(CvArgs c, CvInfo *info)
+// mirrors, edge lengths, wall edges and the area ratios.  With ratio set,
+// every member also gets its control volume's area ratio S^n / S^{n+1,*}
+// (the Shakhov term of a moving obstacle scales with it).
+__global__ void __launch_bounds__(256) k_members(CvArgs c, CvInfo *info, double *ratio)
 {
     __shared__ int32_t mem[kMaxMembers];
     const Grid2D &g = c.g;
@@ -633,6 +644,8 @@ __global__ void __launch_bounds__(256) k_members(CvArgs c, CvInfo *info)
             I.bco = Sp > 0 ? g.dt / Sp : 0.0;
             if (!(Sp > 0)) atomicExch(&c.err[kErrGeometry], 1);
         }
+        __syncthreads();
+        if (ratio && threadIdx.x < nm) ratio[mem[threadIdx.x]] = I.a;
         __syncthreads();
     }
 }
@@ -755,66 +768,83 @@ __device__ __forceinline__ WallGeom wall_geom(const CvArgs &c, const BodyParams 
     return w;
 }
 
+// mode 0: the whole wall step.  A velocity split (Sec. 5.2) runs it in two
+// halves around the caller's sum over the ranks: mode 1 writes each wall
+// cell's eight sums over this context's velocities to xw[8 * slot] and stops;
+// mode 2 reads the summed eight values from xw and does the rest.
+// The wall sums are FP64 in both precisions (products of the state values,
+// exact in FP64 for an FP32 state, and FP64 sums), as are the wall density,
+// the stress, the force, the torque and the rotation.
 template <typename T>
 __global__ void __launch_bounds__(256) k_wall(CvArgs c, BodyParams b, BodyDev *body, const T *f,
                                               double *wdat, double *wcontrib, int *ticket,
-                                              double *hist, int moving)
+                                              double *hist, int moving, int mode, double *xw)
 {
     __shared__ double red[8 * 8];
-    __shared__ T ex[kMaxAxisNv], ey[kMaxAxisNv];
-    __shared__ T wsc[6];        // uwx, uwy, nwx, nwy, 1/(2 pi Tw), 2 Tw
-    __shared__ T wred[8 * 2];
+    __shared__ double ex[kMaxAxisNv], ey[kMaxAxisNv];
+    __shared__ double wsc[6];   // uwx, uwy, nwx, nwy, 1/(2 pi Tw), 2 Tw
+    __shared__ double wred[8 * 2];
     __shared__ bool last;
     const Grid2D &g = c.g;
-    const VCoef<T> *vt = reinterpret_cast<const VCoef<T> *>(c.vt);
     const int nw = min(c.counts[1], c.cap);
     const double omega = body->omega;
     const int tid = threadIdx.x;
     for (int idx = blockIdx.x; idx < nw; idx += gridDim.x) {
         const long k = c.wall_list[idx];
+        double r0, r1, r2, r3, r4, r5, r6, r7;
+        if (mode == 2) {
+            const double *x = xw + 8L * idx;
+            r0 = x[0]; r1 = x[1]; r2 = x[2]; r3 = x[3]; r4 = x[4]; r5 = x[5]; r6 = x[6]; r7 = x[7];
+        } else {
         if (tid == 0) {
             const WallGeom w = wall_geom(c, b, k, omega);
-            wsc[0] = (T)w.uwx; wsc[1] = (T)w.uwy; wsc[2] = (T)w.nwx; wsc[3] = (T)w.nwy;
-            wsc[4] = (T)(1.0 / (2.0 * kPi * w.Tw)); wsc[5] = (T)(2.0 * w.Tw);
+            wsc[0] = w.uwx; wsc[1] = w.uwy; wsc[2] = w.nwx; wsc[3] = w.nwy;
+            wsc[4] = 1.0 / (2.0 * kPi * w.Tw); wsc[5] = 2.0 * w.Tw;
         }
         __syncthreads();
-        const T uwx = wsc[0], uwy = wsc[1], nwx = wsc[2], nwy = wsc[3], cm = wsc[4], twoTw = wsc[5];
+        const double uwx = wsc[0], uwy = wsc[1], nwx = wsc[2], nwy = wsc[3], cm = wsc[4], twoTw = wsc[5];
         // separable Maxwellian M[1, u_w, T_w] = ex[p1] ey[p2] / (2 pi T_w)
         for (int q = tid; q < g.nvx + g.nvy; q += blockDim.x) {
-            if (q < g.nvx) { T d = vt[q].vx - uwx; ex[q] = dexp(-(d * d) / twoTw); }
-            else { int qq = q - g.nvx; T d = vt[qq * g.nvx].vy - uwy; ey[qq] = dexp(-(d * d) / twoTw); }
+            if (q < g.nvx) { const double d = g.vxmin + q * g.dvx - uwx; ex[q] = exp(-(d * d) / twoTw); }
+            else { const int qq = q - g.nvx; const double d = g.vymin + qq * g.dvy - uwy; ey[qq] = exp(-(d * d) / twoTw); }
         }
         __syncthreads();
-        // products and compensated sums in the state precision; the wall
-        // density, stress and force are formed from them in FP64
         const long pck = pcell(g, k) * Vec<T>::W;
-        Acc<T> a0, a1, a2, a3, a4, a5, a6, a7;
+        Acc<double> a0, a1, a2, a3, a4, a5, a6, a7;
         int p1 = tid % g.nvx, p2 = tid / g.nvx;
         const int dp1 = blockDim.x % g.nvx, dp2 = blockDim.x / g.nvx;
         for (int p = tid; p < g.nv; p += blockDim.x) {
-            const VCoef<T> vc = ld_coef(vt + p);
-            const T ax = vc.vx - uwx, ay = vc.vy - uwy;
-            const T cp = ax * nwx + ay * nwy;
-            if (cp > T(0)) {
-                const T fv = f[ebase<T>(g, 0, p) + pck];
+            const double ax = g.vxmin + p1 * g.dvx - uwx, ay = g.vymin + p2 * g.dvy - uwy;
+            const double cp = ax * nwx + ay * nwy;
+            if (cp > 0.0) {
+                const double fv = (double)f[ebase<T>(g, 0, p) + pck];
                 a0.add(cp * fv);
                 a5.add(ax * ax * fv); a6.add(ax * ay * fv); a7.add(ay * ay * fv);
-            } else if (cp < T(0)) {
-                const T m1 = cm * ex[p1] * ey[p2];
+            } else if (cp < 0.0) {
+                const double m1 = cm * ex[p1] * ey[p2];
                 a1.add(cp * m1);
                 a2.add(ax * ax * m1); a3.add(ax * ay * m1); a4.add(ay * ay * m1);
             }
             p1 += dp1; p2 += dp2;
             if (p1 >= g.nvx) { p1 -= g.nvx; p2 += 1; }
         }
-        const T r0 = block_acc(a0, wred), r1 = block_acc(a1, wred), r2 = block_acc(a2, wred);
-        const T r3 = block_acc(a3, wred), r4 = block_acc(a4, wred), r5 = block_acc(a5, wred);
-        const T r6 = block_acc(a6, wred), r7 = block_acc(a7, wred);
+        r0 = block_acc(a0, wred); r1 = block_acc(a1, wred); r2 = block_acc(a2, wred);
+        r3 = block_acc(a3, wred); r4 = block_acc(a4, wred); r5 = block_acc(a5, wred);
+        r6 = block_acc(a6, wred); r7 = block_acc(a7, wred);
+        if (mode == 1) {
+            if (tid == 0) {
+                double *x = xw + 8L * idx;
+                x[0] = r0; x[1] = r1; x[2] = r2; x[3] = r3; x[4] = r4; x[5] = r5; x[6] = r6; x[7] = r7;
+            }
+            __syncthreads();
+            continue;
+        }
+        }
         if (tid == 0) {
             const WallGeom w = wall_geom(c, b, k, omega);
-            const double phi = -((double)r0 * g.dv) / ((double)r1 * g.dv);
-            const double sxx = (phi * (double)r2 + (double)r5) * g.dv, sxy = (phi * (double)r3 + (double)r6) * g.dv;
-            const double syy = (phi * (double)r4 + (double)r7) * g.dv;
+            const double phi = -(r0 * g.dv) / (r1 * g.dv);
+            const double sxx = (phi * r2 + r5) * g.dv, sxy = (phi * r3 + r6) * g.dv;
+            const double syy = (phi * r4 + r7) * g.dv;
             const double fkx = (sxx * w.nwx + sxy * w.nwy) * w.lw, fky = (sxy * w.nwx + syy * w.nwy) * w.lw;
             wcontrib[3 * idx] = fkx;
             wcontrib[3 * idx + 1] = fky;
@@ -824,6 +854,7 @@ __global__ void __launch_bounds__(256) k_wall(CvArgs c, BodyParams b, BodyDev *b
         }
         __syncthreads();
     }
+    if (mode == 1) return;
     // the last block sums the contributions in list order
     __threadfence();
     __syncthreads();
@@ -897,11 +928,15 @@ __global__ void __launch_bounds__(256) k_special(CvArgs c, const T *fin, T *fout
         split_range(c, sp, W, v0, v1);
         const long m = c.spec_list[idx];
         T s[4];
-        gather_partials(pin, c.S, nc, m, s);
+        gather_partials(pin, c.Sin, nc, m, s);
         T rho, ux, uy, tmp;
         if (!primitives<T>(pick<T>(g.dv_f, g.dv), s[0], s[1], s[2], s[3], rho, ux, uy, tmp) && threadIdx.x == 0 && sp == 0)
             atomicExch(&c.err[kErrNonphys], 1);
         const T a = (T)I.a, bco = (T)I.bco, r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+        if (c.eqp) {
+            const T *e = static_cast<const T *>(c.eqp);
+            rho = e[m]; ux = e[nc + m]; uy = e[2 * nc + m]; tmp = e[3 * nc + m];
+        }
         const T A = rho / (T(2.0 * kPi) * tmp);
         const T i2T = T(1) / (T(2) * tmp);
         Acc<T> s0, s1, s2, s3;
@@ -1087,12 +1122,19 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_moments_out(Grid2D g, const
 __device__ __forceinline__ float exp2_relax(float x) { return ex2_fast(x); }
 __device__ __forceinline__ double exp2_relax(double x) { return exp2(x); }
 
-template <typename T>
+// With SHAK (the Shakhov model, Eq. ShakhovDD) the equilibrium carries the
+// heat flux at t^{n+1}, q = q_T / (1 + nu Pr), q_T that of the transported
+// values (the heat-flux moment of the scheme with the model's (1 - Pr) q):
+// a first pass over the cell's velocities sums q_T, the second relaxes
+// towards f_S = M [1 + k c.q (|c|^2/T - 4)], g_S = T/2 M [1 + k c.q (|c|^2/T - 2)],
+// k = (1 - Pr) / (5 rho T^2).
+template <typename T, bool SHAK>
 __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_tau0, T *f, const VCoef<T> *vt,
-                                                          T *part, const int8_t *type, int *err)
+                                                          T *part, const int8_t *type, const T *eqp, T Pr, int *err)
 {
     constexpr int W = Vec<T>::W;
     using V = typename Vec<T>::type;
+    __shared__ T qsh[2][32];
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y;
     const long nc = (long)g.nx * g.ny, cell = (long)j * g.nx + i;
     bool gas = i < g.nx && type[cell] != DVM_SOLID;
@@ -1104,15 +1146,53 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_
         gas = false;
     }
     Acc<T> a4[4];
+    const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
+    const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+    const long pc = nbr(g, i, j);
+    V *fv = reinterpret_cast<V *>(f);
+    T qx = 0, qy = 0;
+    if constexpr (SHAK) {
+        // heat flux of the transported values about their velocity
+        Acc<T> hq[2];
+        if (gas) {
+            for (int q = q0; q < q1; ++q) {
+                T a[W], b[W];
+                vld<T>(fv + (long)q * 2 * g.slab + pc, a);
+                vld<T>(fv + ((long)q * 2 + 1) * g.slab + pc, b);
+                T t0 = 0, t1 = 0;
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    if (q * W + e >= g.nv) continue;
+                    const VCoef<T> c = ld_coef(vt + q * W + e);
+                    const T dx = c.vx - ux, dy = c.vy - uy;
+                    const T w = T(0.5) * (dx * dx + dy * dy) * a[e] + b[e];
+                    t0 += dx * w;
+                    t1 += dy * w;
+                }
+                hq[0].add(t0);
+                hq[1].add(t1);
+            }
+        }
+        merge_chunks<T, 2>(hq);
+        if (threadIdx.y == 0) {
+            const T rel = T(1) / (T(1) + dt_tau0 * rho * Pr);
+            qsh[0][threadIdx.x] = hq[0].value() * pick<T>(g.dv_f, g.dv) * rel;
+            qsh[1][threadIdx.x] = hq[1].value() * pick<T>(g.dv_f, g.dv) * rel;
+        }
+        __syncthreads();
+        qx = qsh[0][threadIdx.x];
+        qy = qsh[1][threadIdx.x];
+    }
     if (gas) {
-        const T A = rho / (T(2.0 * kPi) * tmp), c2 = T(kLog2e) / (T(2) * tmp);
-        const T nu = dt_tau0 * rho, inv = T(1) / (T(1) + nu), half = tmp / T(2);
-        const long pc = nbr(g, i, j);
+        const T nu = dt_tau0 * rho, inv = T(1) / (T(1) + nu);
+        if (eqp) {
+            // conservative equilibrium of the transported state (Sec. 3.1)
+            rho = eqp[cell]; ux = eqp[nc + cell]; uy = eqp[2 * nc + cell]; tmp = eqp[3 * nc + cell];
+        }
+        const T A = rho / (T(2.0 * kPi) * tmp), c2 = T(kLog2e) / (T(2) * tmp), half = tmp / T(2);
+        const T kk = SHAK ? (T(1) - Pr) / (T(5) * rho * tmp * tmp) : T(0), iT = T(1) / tmp;
         long mir[4];
         mirrors(g, i, j, mir);
-        V *fv = reinterpret_cast<V *>(f);
-        const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
-        const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
 #pragma unroll 2
         for (int q = q0; q < q1; ++q) {
             V *pa = fv + (long)q * 2 * g.slab, *pb = pa + g.slab;
@@ -1126,8 +1206,14 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_
                 const VCoef<T> c = ld_coef(vt + q * W + e);
                 const T dx = c.vx - ux, dy = c.vy - uy;
                 const T M = A * exp2_relax(-(dx * dx + dy * dy) * c2);
-                a[e] = (a[e] + nu * M) * inv;
-                b[e] = (b[e] + nu * half * M) * inv;
+                T sf = T(1), sg = T(1);
+                if constexpr (SHAK) {
+                    const T h = kk * (dx * qx + dy * qy), d2 = (dx * dx + dy * dy) * iT;
+                    sf += h * (d2 - T(4));
+                    sg += h * (d2 - T(2));
+                }
+                a[e] = (a[e] + nu * M * sf) * inv;
+                b[e] = (b[e] + nu * half * M * sg) * inv;
                 t0 += a[e];
                 t1 += c.vx * a[e];
                 t2 += c.vy * a[e];
@@ -1355,8 +1441,36 @@ cudaError_t launch_bulk(dvm_ctx *c, const BulkArgs<T> &a)
     return cudaGetLastError();
 }
 
+// Moment sums of each cell over this context's velocities, folded over the
+// S velocity splits in fixed order: x[m][cell] = sum_s part[s][m][cell]
+// (the data a velocity split exchanges, Sec. 5.2), in FP64.
 template <typename T>
-cudaError_t step2d_t(dvm_ctx *c)
+__global__ void k_fold_partials(const T *part, int S, long nc, double *x)
+{
+    const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= nc) return;
+    T s[4];
+    gather_partials(part, S, nc, cell, s);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) x[(long)m * nc + cell] = (double)s[m];
+}
+
+// The summed moment sums back in the state precision, one slot.
+template <typename T>
+__global__ void k_unfold_partials(const double *x, long n, T *part)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) part[t] = (T)x[t];
+}
+
+// One step in phases.  phase 0: the whole step.  A velocity split (Sec. 5.2:
+// each rank holds every cell for a slab of the velocity grid) runs it as
+// phase 1, which ends with this context's contributions in xbuf (FP64: the
+// moment sums of F^n of every cell, [4][nc], then the eight wall sums of every
+// wall cell, [wall slot][8]), and phase 2, which takes xbuf summed over the
+// ranks and finishes the step.
+template <typename T>
+cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
 {
     Grid2D g = grid2d(c);
     // the semi-implicit scheme (Eq. ImpSchemeDD) transports without
@@ -1369,31 +1483,58 @@ cudaError_t step2d_t(dvm_ctx *c)
     BodyParams bp = body_params(c);
     const bool body = c->body.shape != DVM_SHAPE_NONE;
     const bool moving = c->moving;
+    const long nc = (long)c->nc;
     T *fin = (T *)c->f[c->cur], *fout = (T *)c->f[1 - c->cur];
     T *pin = (T *)c->part[c->cur], *pout = (T *)c->part[1 - c->cur];
     cudaError_t e = cudaSuccess;
-    if (moving) {
+    if (moving && phase != 2) {
         k_advance<<<1, 32, 0, c->stream>>>(c->d_body, c->dt, 1);
         if ((e = geometry2d_level(c, 1 - c->gcur, body_trig(c, 2))) != cudaSuccess) return e;
         if ((e = masters_flags2d(c, true)) != cudaSuccess) return e;
         c->launches += 9;
     }
-    CvArgs cv;
+    CvArgs cv{};
     cv.g = g;
     cv.Gn = c->geo[c->gcur];
     cv.Gp = moving ? c->geo[1 - c->gcur] : c->geo[c->gcur];
     cv.master = c->master; cv.flags = c->flags;
     cv.spec_list = c->spec_list; cv.wall_list = c->wall_list; cv.wslot = c->wslot;
     cv.counts = c->counts; cv.cap = c->list_cap; cv.S = c->S;
+    cv.Sin = phase == 2 ? 1 : c->S;
     cv.gps = (c->ngrp + c->S - 1) / c->S;
     cv.cvinfo = c->cvinfo; cv.vt = c->vtab;
+    const bool cons = c->eq_mode == DVM_EQ_CONSERVATIVE;
+    cv.eqp = cons && !imex ? c->eqp : nullptr;
     cv.err = c->d_err;
     const int cvgrid = 4 * 152;
-    if (body) {
-        if (moving || c->need_fusion) {
+    double *xw = xbuf ? xbuf + 4 * nc : nullptr;
+    if (phase != 2) {
+        if (body && (moving || c->need_fusion)) {
             k_fusion<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, pin);
             c->launches += 1;
         }
+        if (phase == 1) {
+            // this rank's moment sums of f_CV^n and wall sums, to be summed
+            // over the ranks by the caller
+            k_fold_partials<T><<<nblk(nc, 256), 256, 0, c->stream>>>(pin, c->S, nc, xbuf);
+            c->launches += 1;
+            if (body) {
+                k_wall<T><<<cvgrid, 256, 0, c->stream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
+                                                          c->d_hist, moving ? 1 : 0, 1, xw);
+                c->launches += 1;
+            }
+            return cudaGetLastError();
+        }
+    } else {
+        // the summed moments of f_CV^n, one slot in the state precision
+        pin = (T *)c->split_in;
+        k_unfold_partials<T><<<nblk(4 * nc, 256), 256, 0, c->stream>>>(xbuf, 4 * nc, pin);
+        c->launches += 1;
+    }
+    const int Sin = phase == 2 ? 1 : c->S;
+    // conservative equilibrium parameters of f_CV^n (after fusion)
+    if (cons && !imex && (e = eqpar(c, pin, Sin)) != cudaSuccess) return e;
+    if (body) {
         // the wall kernel (wall density, stress, force, rotation) and then the
         // control-volume kernel run on the side stream beside the bulk kernel:
         // both read F^n and write only the cut and merged control volumes,
@@ -1401,13 +1542,14 @@ cudaError_t step2d_t(dvm_ctx *c)
         if ((e = cudaEventRecord(c->ev_wfork, c->stream)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->wstream, c->ev_wfork, 0)) != cudaSuccess) return e;
         k_wall<T><<<cvgrid, 256, 0, c->wstream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
-                                                   c->d_hist, moving ? 1 : 0);
+                                                   c->d_hist, moving ? 1 : 0, phase == 2 ? 2 : 0, xw);
         c->launches += 1;
     }
-    BulkArgs<T> a;
-    a.g = g; a.S = c->S; a.fin = fin; a.fout = fout; a.pin = pin; a.pout = pout;
+    BulkArgs<T> a{};
+    a.g = g; a.S = c->S; a.Sin = Sin; a.fin = fin; a.fout = fout; a.pin = pin; a.pout = pout;
     a.flags = c->flags; a.vt = (const VCoef<T> *)c->vtab; a.gsign = c->gsign; a.err = c->d_err;
     a.pt = (const ulonglong2 *)c->ptab;
+    a.eqp = cons && !imex ? (const T *)c->eqp : nullptr;
     a.bits = c->rec_bits;
     a.bpitch = bits_pitch(c);
     a.bslab = bits_slab(c);
@@ -1427,8 +1569,16 @@ cudaError_t step2d_t(dvm_ctx *c)
     if (imex) {
         const dim3 grid(nblk(c->nx, 32), c->ny), block(32, kMomChunks);
         const int8_t *type1 = c->geo[moving ? 1 - c->gcur : c->gcur].type;    // cell types at t^{n+1}
-        k_imex<T><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, (const VCoef<T> *)c->vtab,
-                                                 pout, type1, c->d_err);
+        // conservative equilibrium parameters of the transported state
+        if (cons && (e = eqpar(c, pout, c->S)) != cudaSuccess) return e;
+        if (c->model == DVM_SHAKHOV)
+            k_imex<T, true><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
+                                                           (const VCoef<T> *)c->vtab, pout, type1, nullptr, T(c->Pr),
+                                                           c->d_err);
+        else
+            k_imex<T, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
+                                                            (const VCoef<T> *)c->vtab, pout, type1,
+                                                            cons ? (const T *)c->eqp : nullptr, T(1), c->d_err);
         c->launches += 1;
     }
     c->cur = 1 - c->cur;
@@ -1512,14 +1662,14 @@ size_t cvinfo_bytes() { return sizeof(CvInfo); }
 
 cudaError_t members2d(dvm_ctx *c, bool moving)
 {
-    CvArgs cv;
+    CvArgs cv{};
     cv.g = grid2d(c);
     cv.Gn = c->geo[c->gcur];
     cv.Gp = moving ? c->geo[1 - c->gcur] : c->geo[c->gcur];
     cv.master = c->master; cv.flags = c->flags; cv.wslot = c->wslot;
     cv.spec_list = c->spec_list; cv.counts = c->counts; cv.cap = c->list_cap;
     cv.err = c->d_err;
-    k_members<<<4 * 152, 256, 0, c->stream>>>(cv, (CvInfo *)c->cvinfo);
+    k_members<<<4 * 152, 256, 0, c->stream>>>(cv, (CvInfo *)c->cvinfo, c->cv_ratio);
     return cudaGetLastError();
 }
 
@@ -1527,7 +1677,7 @@ cudaError_t members2d(dvm_ctx *c, bool moving)
 // part (a scratch of S x 4 x nc elements).
 cudaError_t fusion2d(dvm_ctx *c, void *f, void *part)
 {
-    CvArgs cv;
+    CvArgs cv{};
     cv.g = grid2d(c);
     cv.Gn = c->geo[c->gcur];
     cv.Gp = c->geo[c->gcur];
@@ -1544,7 +1694,15 @@ cudaError_t fusion2d(dvm_ctx *c, void *f, void *part)
 
 cudaError_t step2d(dvm_ctx *c)
 {
-    return c->prec == DVM_FP32 ? step2d_t<float>(c) : step2d_t<double>(c);
+    return c->prec == DVM_FP32 ? step2d_t<float>(c, 0, nullptr) : step2d_t<double>(c, 0, nullptr);
+}
+
+// Velocity split: phase 1 (this rank's sums into xbuf) or phase 2 (finish
+// the step from xbuf summed over the ranks).
+cudaError_t split_step2d(dvm_ctx *c, int phase, void *xbuf)
+{
+    double *x = static_cast<double *>(xbuf);
+    return c->prec == DVM_FP32 ? step2d_t<float>(c, phase, x) : step2d_t<double>(c, phase, x);
 }
 
 cudaError_t tables2d(dvm_ctx *c)

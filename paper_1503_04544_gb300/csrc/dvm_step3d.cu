@@ -143,6 +143,7 @@ __device__ __forceinline__ T norm3(T tmp)
 template <typename T> struct Bulk3Args {
     Grid3D g;
     int S, nzc;
+    int Sin;                  // partial-sum slots of pin (S, or 1 for summed moments of a velocity split)
     const T *fin;
     T *fout;
     const T *pin;             // partial moments of F^n   [S][5][nc]
@@ -150,6 +151,7 @@ template <typename T> struct Bulk3Args {
     const uint16_t *flags;
     const VX3<T> *vxt;        // [nvxp]
     const VYZ3<T> *vyz;       // [nvy * nvz]
+    const T *eqp;             // [5][nc] conservative equilibrium parameters, or null (direct moments)
     int *err;
 };
 
@@ -283,16 +285,22 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
             if (fl & kPlain) {
                 plainm |= 1u << t;
                 T s[5];
-                gather_partials3(a.pin, a.S, nc, cell, s);
+                gather_partials3(a.pin, a.Sin, nc, cell, s);
                 T rho, ux, uy, uz, tmp;
                 if (!primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp)) atomicExch(&a.err[kErrNonphys], 1);
+                cz[5 * NT] = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+                if (a.eqp) {
+                    // conservative equilibrium (Sec. 3.1): tau from the direct
+                    // density, the Maxwellian from the Newton parameters
+                    rho = a.eqp[cell]; ux = a.eqp[nc + cell]; uy = a.eqp[2 * nc + cell];
+                    uz = a.eqp[3 * nc + cell]; tmp = a.eqp[4 * nc + cell];
+                }
                 const T c2 = T(kLog2e) / (T(2) * tmp);
                 cz[0] = log2(rho * norm3(tmp)) - c2 * ux * ux;
                 cz[NT] = T(2) * c2 * ux;
                 cz[2 * NT] = c2;
                 cz[3 * NT] = uy;
                 cz[4 * NT] = uz;
-                cz[5 * NT] = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
             }
             if (fl & kZero) zerom |= 1u << t;
             masks |= (uint32_t)((fl >> kMaskShift3) & 0x3F) << (8 * t);
@@ -551,10 +559,12 @@ struct Cv3Args {
     const int32_t *counts;
     int cap;
     int S;
+    int Sin;                  // partial-sum slots of the moments read (S, or 1 for summed moments)
     int gps;
     const void *cvinfo;
     const void *vxt;
     const void *vyz;
+    const void *eqp;          // [5][nc] conservative equilibrium parameters, or null
     int *err;
 };
 
@@ -762,8 +772,11 @@ __global__ void __launch_bounds__(256) k_fusion3(Cv3Args c, T *f, T *part)
 // record and the history.  (phi, u_w, T_w) of each wall cell are left for
 // the control-volume kernel.
 template <typename T>
+// mode 0: the whole wall step; a velocity split runs mode 1 (this rank's 14
+// sums of every wall cell into xw[14 * slot], FP64) and, after the caller's
+// sum over the ranks, mode 2 (the rest from the summed values).
 __global__ void __launch_bounds__(256) k_wall3(Cv3Args c, BodyParams b, BodyDev *body, const T *f, double *wdat,
-                                               double *wcontrib, int *ticket, double *hist)
+                                               double *wcontrib, int *ticket, double *hist, int mode, double *xw)
 {
     __shared__ double red[8 * 8];
     __shared__ T ex[kMaxAxisNv], ey[kMaxAxisNv], ez[kMaxAxisNv];
@@ -780,6 +793,11 @@ __global__ void __launch_bounds__(256) k_wall3(Cv3Args c, BodyParams b, BodyDev 
         const int q = c.wall_list[idx];
         const double rx = c.G.rwx[q] - b.cx, ry = c.G.rwy[q] - b.cy;
         const double uwx = b.vbx - ry * omega, uwy = b.vby + rx * omega, uwz = 0.0;
+        double rr[14];
+        if (mode == 2) {
+#pragma unroll
+            for (int t = 0; t < 14; ++t) rr[t] = xw[14L * idx + t];
+        } else {
         if (tid == 0) {
             wsc[0] = (T)uwx; wsc[1] = (T)uwy; wsc[2] = (T)uwz;
             wsc[3] = (T)c.G.nwx[q]; wsc[4] = (T)c.G.nwy[q]; wsc[5] = (T)c.G.nwz[q];
@@ -826,14 +844,21 @@ __global__ void __launch_bounds__(256) k_wall3(Cv3Args c, BodyParams b, BodyDev 
                 a[5].add(ay * ay * m1); a[6].add(ay * az * m1); a[7].add(az * az * m1);
             }
         }
-        T rr[14];
 #pragma unroll
-        for (int t = 0; t < 14; ++t) rr[t] = block_acc(a[t], wred);
+        for (int t = 0; t < 14; ++t) rr[t] = (double)block_acc(a[t], wred);
+        if (mode == 1) {
+            if (tid == 0)
+#pragma unroll
+                for (int t = 0; t < 14; ++t) xw[14L * idx + t] = rr[t];
+            __syncthreads();
+            continue;
+        }
+        }
         if (tid == 0) {
             const double dv = g.dv;
-            const double phi = -((double)rr[0] * dv) / ((double)rr[1] * dv);
+            const double phi = -(rr[0] * dv) / (rr[1] * dv);
             double S6[6];
-            for (int t = 0; t < 6; ++t) S6[t] = (phi * (double)rr[2 + t] + (double)rr[8 + t]) * dv;
+            for (int t = 0; t < 6; ++t) S6[t] = (phi * rr[2 + t] + rr[8 + t]) * dv;
             const double nxd = c.G.nwx[q], nyd = c.G.nwy[q], nzd = c.G.nwz[q], sw = c.G.sw[q];
             const double fx = (S6[0] * nxd + S6[1] * nyd + S6[2] * nzd) * sw;
             const double fy = (S6[1] * nxd + S6[3] * nyd + S6[4] * nzd) * sw;
@@ -845,6 +870,7 @@ __global__ void __launch_bounds__(256) k_wall3(Cv3Args c, BodyParams b, BodyDev 
         }
         __syncthreads();
     }
+    if (mode == 1) return;
     __threadfence();
     __syncthreads();
     if (tid == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
@@ -891,11 +917,15 @@ __global__ void __launch_bounds__(256) k_special3(Cv3Args c, const T *fin, T *fo
         const int v0 = sp * c.gps * g.W, v1 = min(g.nvp, v0 + c.gps * g.W);
         const int m = c.spec_list[idx];
         T s[5];
-        gather_partials3(pin, c.S, nc, m, s);
+        gather_partials3(pin, c.Sin, nc, m, s);
         T rho, ux, uy, uz, tmp;
         if (!primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp) && threadIdx.x == 0 && sp == 0)
             atomicExch(&c.err[kErrNonphys], 1);
         const T bco = (T)I.bco, r = pick<T>(g.dt_tau0_f, g.dt_tau0) * rho;
+        if (c.eqp) {
+            const T *e = static_cast<const T *>(c.eqp);
+            rho = e[m]; ux = e[nc + m]; uy = e[2 * nc + m]; uz = e[3 * nc + m]; tmp = e[4 * nc + m];
+        }
         const T A = rho * norm3(tmp);
         const T i2T = T(1) / (T(2) * tmp);
         Acc<T> acc[5];
@@ -1065,12 +1095,17 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_moments_out3(Grid3D g, cons
 // padding mirrors; the partial sums become those of the relaxed state.
 // Block = 32 consecutive cells of an x-row x kMomChunks warps, one chunk of
 // the velocity groups each.
-template <typename T>
+template <typename T, bool SHAK>
 __global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt_tau0, T *f, const VX3<T> *vxt,
-                                                           const VYZ3<T> *vyz, T *part, const int8_t *type, int *err)
+                                                           const VYZ3<T> *vyz, T *part, const int8_t *type,
+                                                           const T *eqp, T Pr, int *err)
 {
+    // SHAK: the Shakhov model (Sec. 2.1) with the heat flux at t^{n+1},
+    // q = q_T / (1 + nu Pr), q_T = sum c |c|^2/2 F dv of the transported
+    // values; F_S = M [1 + (1 - Pr) c.q (|c|^2/T - 5) / (5 rho T^2)]
     constexpr int W = Vec<T>::W;
     using V = typename Vec<T>::type;
+    __shared__ T qsh[3][32];
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const long nc = (long)g.nx * g.ny * g.nz, cell = ((long)k * g.ny + j) * g.nx + i;
     bool gas = i < g.nx && type[cell] != DVM_SOLID;
@@ -1084,13 +1119,58 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt
     Acc<T> a5[5];
     const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
     const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
+    const long pc = nbr3(g, i, j, k);
+    V *fv = reinterpret_cast<V *>(f);
+    T qx = 0, qy = 0, qz = 0;
+    if constexpr (SHAK) {
+        Acc<T> hq[3];
+        if (gas) {
+            int r = q0 / g.nxg, xg = q0 - r * g.nxg;
+            for (int q = q0; q < q1; ++q) {
+                T a[W];
+                vld<T>(fv + (long)q * g.slab + pc, a);
+                const VYZ3<T> cy = vyz[r];
+                const T dy = cy.vy - uy, dz = cy.vz - uz, dyz = dy * dy + dz * dz;
+                T t0 = 0, t1 = 0;
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    const int p1 = xg * W + e;
+                    if (p1 >= g.nvx) continue;
+                    const T dx = vxt[p1].vx - ux, w = T(0.5) * (dx * dx + dyz) * a[e];
+                    t0 += dx * w;
+                    t1 += w;
+                }
+                hq[0].add(t0);
+                hq[1].add(dy * t1);
+                hq[2].add(dz * t1);
+                if (++xg == g.nxg) {
+                    xg = 0;
+                    ++r;
+                }
+            }
+        }
+        merge_chunks<T, 3>(hq);
+        if (threadIdx.y == 0) {
+            const T rel = pick<T>(g.dv_f, g.dv) / (T(1) + dt_tau0 * rho * Pr);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) qsh[d][threadIdx.x] = hq[d].value() * rel;
+        }
+        __syncthreads();
+        qx = qsh[0][threadIdx.x];
+        qy = qsh[1][threadIdx.x];
+        qz = qsh[2][threadIdx.x];
+    }
     if (gas && q0 < q1) {
-        const T A = rho * norm3(tmp), c2 = T(kLog2e) / (T(2) * tmp);
         const T nu = dt_tau0 * rho, inv = T(1) / (T(1) + nu);
-        const long pc = nbr3(g, i, j, k);
+        if (eqp) {
+            // conservative equilibrium of the transported state (Sec. 3.1)
+            rho = eqp[cell]; ux = eqp[nc + cell]; uy = eqp[2 * nc + cell]; uz = eqp[3 * nc + cell];
+            tmp = eqp[4 * nc + cell];
+        }
+        const T A = rho * norm3(tmp), c2 = T(kLog2e) / (T(2) * tmp);
+        const T kk = SHAK ? (T(1) - Pr) / (T(5) * rho * tmp * tmp) : T(0), iT = T(1) / tmp;
         int mir[6];
         mirrors3(g, i, j, k, mir);
-        V *fv = reinterpret_cast<V *>(f);
         int r = q0 / g.nxg, xg = q0 - r * g.nxg;
 #pragma unroll 2
         for (int q = q0; q < q1; ++q) {
@@ -1099,13 +1179,15 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt
             vld<T>(pa + pc, a);
             const VYZ3<T> cy = vyz[r];
             const T dyz = (cy.vy - uy) * (cy.vy - uy) + (cy.vz - uz) * (cy.vz - uz);
+            const T hyz = kk * ((cy.vy - uy) * qy + (cy.vz - uz) * qz);
             T t0 = 0, t1 = 0, t2 = 0;
 #pragma unroll
             for (int e = 0; e < W; ++e) {
                 const int p1 = xg * W + e;
                 if (p1 >= g.nvx) continue;
                 const T vx = vxt[p1].vx, dx = vx - ux;
-                const T M = A * exp2_state(-(dx * dx + dyz) * c2);
+                T M = A * exp2_state(-(dx * dx + dyz) * c2);
+                if constexpr (SHAK) M *= T(1) + (kk * dx * qx + hyz) * ((dx * dx + dyz) * iT - T(5));
                 a[e] = (a[e] + nu * M) * inv;
                 t0 += a[e];
                 t1 += vx * a[e];
@@ -1331,12 +1413,12 @@ cudaError_t launch_bulk3(dvm_ctx *c, const Bulk3Args<T> &a)
 
 Cv3Args cv3_args(dvm_ctx *c)
 {
-    Cv3Args cv;
+    Cv3Args cv{};
     cv.g = grid3d(c);
     cv.G = c->geo3;
     cv.master = c->master; cv.flags = c->flags3;
     cv.spec_list = c->spec_list; cv.wall_list = c->wall_list; cv.wslot = c->wslot;
-    cv.counts = c->counts; cv.cap = c->list_cap; cv.S = c->S;
+    cv.counts = c->counts; cv.cap = c->list_cap; cv.S = c->S; cv.Sin = c->S;
     cv.gps = (c->ngrp + c->S - 1) / c->S;
     cv.cvinfo = c->cvinfo;
     cv.vxt = c->vtab;
@@ -1345,8 +1427,33 @@ Cv3Args cv3_args(dvm_ctx *c)
     return cv;
 }
 
+// Moment sums of each cell over this context's velocities, folded over the
+// S velocity splits in fixed order, in FP64 (the data a velocity split
+// exchanges, Sec. 5.2).
 template <typename T>
-cudaError_t step3d_t(dvm_ctx *c)
+__global__ void k_fold_partials3(const T *part, int S, long nc, double *x)
+{
+    const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= nc) return;
+    T s[5];
+    gather_partials3(part, S, nc, cell, s);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) x[(long)m * nc + cell] = (double)s[m];
+}
+
+template <typename T>
+__global__ void k_unfold_partials3(const double *x, long n, T *part)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) part[t] = (T)x[t];
+}
+
+// One step in phases, as in 2D: 0 the whole step; a velocity split runs
+// phase 1 (this rank's moment sums [5][nc] and wall sums [wall slot][14]
+// into the FP64 buffer xbuf) and phase 2 (the rest, from xbuf summed over
+// the ranks).
+template <typename T>
+cudaError_t step3d_t(dvm_ctx *c, int phase, double *xbuf)
 {
     Grid3D g = grid3d(c);
     // the semi-implicit scheme (Eq. ImpSchemeDD) transports without
@@ -1358,28 +1465,54 @@ cudaError_t step3d_t(dvm_ctx *c)
     }
     const BodyParams bp = body_params(c);
     const bool body = c->body.shape != DVM_SHAPE_NONE;
+    const long nc = (long)c->nc;
     T *fin = (T *)c->f[c->cur], *fout = (T *)c->f[1 - c->cur];
     T *pin = (T *)c->part[c->cur], *pout = (T *)c->part[1 - c->cur];
     cudaError_t e;
     Cv3Args cv = cv3_args(c);
     cv.g = g;                 // without the relaxation rate for the semi-implicit scheme
+    const bool cons = c->eq_mode == DVM_EQ_CONSERVATIVE;
+    cv.eqp = cons && !imex ? c->eqp : nullptr;
     const int cvgrid = 4 * 152;
-    if (body) {
-        if (c->need_fusion) {
+    double *xw = xbuf ? xbuf + 5 * nc : nullptr;
+    if (phase != 2) {
+        if (body && c->need_fusion) {
             k_fusion3<T><<<cvgrid, 256, 0, c->stream>>>(cv, fin, pin);
             c->launches += 1;
         }
+        if (phase == 1) {
+            k_fold_partials3<T><<<nb3(nc, 256), 256, 0, c->stream>>>(pin, c->S, nc, xbuf);
+            c->launches += 1;
+            if (body) {
+                k_wall3<T><<<cvgrid, 256, 0, c->stream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
+                                                           c->d_hist, 1, xw);
+                c->launches += 1;
+            }
+            return cudaGetLastError();
+        }
+    } else {
+        // the summed moments of F_CV^n, one slot in the state precision
+        pin = (T *)c->split_in;
+        k_unfold_partials3<T><<<nb3(5 * nc, 256), 256, 0, c->stream>>>(xbuf, 5 * nc, pin);
+        c->launches += 1;
+    }
+    const int Sin = phase == 2 ? 1 : c->S;
+    cv.Sin = Sin;
+    // conservative equilibrium parameters of F_CV^n (after fusion)
+    if (cons && !imex && (e = eqpar(c, pin, Sin)) != cudaSuccess) return e;
+    if (body) {
         // the wall kernel and then the control-volume kernel run on the side
         // stream beside the bulk kernel: both read F^n and write only the cut
         // and merged control volumes, the bulk kernel only the plain cells
         if ((e = cudaEventRecord(c->ev_wfork, c->stream)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->wstream, c->ev_wfork, 0)) != cudaSuccess) return e;
         k_wall3<T><<<cvgrid, 256, 0, c->wstream>>>(cv, bp, c->d_body, fin, c->wphi, c->wcontrib, c->ticket,
-                                                    c->d_hist);
+                                                    c->d_hist, phase == 2 ? 2 : 0, xw);
         c->launches += 1;
     }
-    Bulk3Args<T> a;
-    a.g = g; a.S = c->S; a.nzc = (c->nz + kZc3 - 1) / kZc3;
+    Bulk3Args<T> a{};
+    a.g = g; a.S = c->S; a.Sin = Sin; a.nzc = (c->nz + kZc3 - 1) / kZc3;
+    a.eqp = cons && !imex ? (const T *)c->eqp : nullptr;
     a.fin = fin; a.fout = fout; a.pin = pin; a.pout = pout;
     a.flags = c->flags3; a.vxt = vx_table<T>(c); a.vyz = vyz_table<T>(c); a.err = c->d_err;
     if ((e = timing_mark(c, 0)) != cudaSuccess) return e;
@@ -1396,8 +1529,16 @@ cudaError_t step3d_t(dvm_ctx *c)
     }
     if (imex) {
         const dim3 grid(nb3(c->nx, 32), c->ny, c->nz), block(32, kMomChunks);
-        k_imex3<T><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c), vyz_table<T>(c),
-                                                  pout, c->geo3.type, c->d_err);
+        // conservative equilibrium parameters of the transported state
+        if (cons && (e = eqpar(c, pout, c->S)) != cudaSuccess) return e;
+        if (c->model == DVM_SHAKHOV)
+            k_imex3<T, true><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c),
+                                                            vyz_table<T>(c), pout, c->geo3.type, nullptr, T(c->Pr),
+                                                            c->d_err);
+        else
+            k_imex3<T, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c),
+                                                             vyz_table<T>(c), pout, c->geo3.type,
+                                                             cons ? (const T *)c->eqp : nullptr, T(1), c->d_err);
         c->launches += 1;
     }
     c->cur = 1 - c->cur;
@@ -1455,7 +1596,18 @@ cudaError_t members3d(dvm_ctx *c)
     return cudaGetLastError();
 }
 
-cudaError_t step3d(dvm_ctx *c) { return c->prec == DVM_FP32 ? step3d_t<float>(c) : step3d_t<double>(c); }
+cudaError_t step3d(dvm_ctx *c)
+{
+    return c->prec == DVM_FP32 ? step3d_t<float>(c, 0, nullptr) : step3d_t<double>(c, 0, nullptr);
+}
+
+// Velocity split: phase 1 (this rank's sums into xbuf) or phase 2 (finish
+// the step from xbuf summed over the ranks).
+cudaError_t split_step3d(dvm_ctx *c, int phase, void *xbuf)
+{
+    double *x = static_cast<double *>(xbuf);
+    return c->prec == DVM_FP32 ? step3d_t<float>(c, phase, x) : step3d_t<double>(c, phase, x);
+}
 
 cudaError_t tables3d(dvm_ctx *c)
 {

@@ -82,8 +82,13 @@ SIGNATURES = {
     "dvm_load": [_P, C.c_char_p],
     "dvm_set_time_scheme": [_P, C.c_int],
     "dvm_set_collision_model": [_P, C.c_int, C.c_double],
+    "dvm_set_equilibrium": [_P, C.c_int],
     "dvm_check": [_P],
-    "dvm_moments": [_P, _PD, _PD, _PD, _PD, _PD],
+    "dvm_moments": [_P, _P, _P, _P, _P, _P, C.c_int],
+    "dvm_set_velocity_split": [_P, C.POINTER(VGrid)],
+    "dvm_split_size": [_P, C.POINTER(C.c_size_t)],
+    "dvm_split_begin": [_P, _P],
+    "dvm_split_finish": [_P, _P],
     "dvm_wall_force": [_P, _PD, _PD],
     "dvm_history": [_P, _PD, _PD, _PD, _PD, _PD, _PD, C.c_int, C.POINTER(C.c_int)],
     "dvm_body_state": [_P, _PD, _PD],
@@ -94,12 +99,15 @@ SIGNATURES = {
     "dvm_geometry2d_at": [_P, C.c_double, C.c_double],
     "dvm_geometry3d": [_P, _PI8, _PI8, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PI32],
     "dvm_drag_adjoint": [_P, C.c_int, C.c_int, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD],
+    "dvm_adjoint": [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, _PD, _PD, _PD, _PD, _PD, _PD, _PD],
+    "dvm_step_vjp": [_P, _P, _P, C.c_int, _PD],
     "dvm_timing": [_P, C.c_int],
     "dvm_kernel_time": [_P, _PD, C.POINTER(C.c_longlong)],
     "dvm_launches": [_P, C.POINTER(C.c_longlong)],
     "dvm_cell_counts": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                         C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
     "dvm_mass_noalloc": [_P, C.c_int, C.c_longlong, C.c_int, C.c_int, _P, C.c_double, _P, _P],
+    "dvm_fp64_peak": [_P, _PD],
     "dvm_last_error": [],
 }
 
@@ -121,6 +129,13 @@ def load():
             lib.dvm_last_error.restype = C.c_char_p
             _lib = lib
     return _lib
+
+
+def fp64_peak(stream: int | None = None) -> float:
+    """FP64 FMA throughput of the current device in GFLOP/s (dvm_fp64_peak)."""
+    out = C.c_double(0.0)
+    _check(load().dvm_fp64_peak(_P(stream) if stream else None, C.byref(out)))
+    return out.value
 
 
 def _ptr(a, t=_PD):
@@ -149,6 +164,11 @@ class Solver:
         _check(lib.dvm_create(C.byref(g), C.byref(v), C.byref(ph), int(precision),
                               int(cfg.get("scheme", 0)), _P(stream) if stream else None, C.byref(h)))
         self.h = h
+        if cfg.get("vsplit_global") is not None:
+            gv = cfg["vsplit_global"]
+            _check(lib.dvm_set_velocity_split(h, C.byref(VGrid(gv["nvx"], gv["nvy"], int(gv.get("nvz", 1)),
+                                                                gv["vxmin"], gv["vxmax"], gv["vymin"], gv["vymax"],
+                                                                gv.get("vzmin", 0.0), gv.get("vzmax", 1.0)))))
         dim = int(cfg.get("dim", 2))
         states = list(cfg.get("bc_state", [None] * 6)) + [None] * 6
         for side, kind in enumerate(list(cfg.get("bc", [0] * 6))[: 2 * dim]):
@@ -163,6 +183,8 @@ class Solver:
             self.set_time_scheme(int(cfg["time_scheme"]))
         if int(cfg.get("model", 0)):
             self.set_collision_model(int(cfg["model"]), float(cfg.get("Pr", 1.0)))
+        if int(cfg.get("conservative", 0)):
+            self.set_equilibrium(int(cfg["conservative"]))
         dt = C.c_double()
         tau0 = C.c_double()
         nc = C.c_longlong()
@@ -242,6 +264,11 @@ class Solver:
         """0: BGK (Eq. BGKDD), 1: Shakhov with Prandtl number Pr (Eq. ShakhovDD)."""
         _check(load().dvm_set_collision_model(self.h, int(model), float(Pr)))
 
+    def set_equilibrium(self, mode: int):
+        """0: the equilibrium takes the direct moments (Eq. MacroscopicDDv);
+        1: the conservative parameters found by Newton's method (Sec. 3.1)."""
+        _check(load().dvm_set_equilibrium(self.h, int(mode)))
+
     def rollback(self, enable: bool = True):
         """dvm_step leaves the state at the last good step on a failure (on by default)."""
         _check(load().dvm_rollback(self.h, int(bool(enable))))
@@ -254,10 +281,31 @@ class Solver:
         _check(load().dvm_check(self.h))
 
     # -------------------------------------------------------------- outputs
-    def moments(self) -> dict:
+    def moments(self, out: dict | None = None) -> dict:
+        """rho, ux, uy, uz, T per cell: numpy arrays, or the CUDA float64
+        tensors of ``out`` (written on the device, no host copy)."""
+        if out is not None:
+            keys = ("rho", "ux", "uy", "uz", "T")
+            _check(load().dvm_moments(self.h, *[_P(out[k].data_ptr()) if out.get(k) is not None else None
+                                                for k in keys], 1))
+            return out
         out = {k: np.zeros(self.ncell) for k in ("rho", "ux", "uy", "uz", "T")}
-        _check(load().dvm_moments(self.h, *[_ptr(out[k]) for k in ("rho", "ux", "uy", "uz", "T")]))
+        _check(load().dvm_moments(self.h, *[_P(out[k].ctypes.data) for k in ("rho", "ux", "uy", "uz", "T")], 0))
         return out
+
+    # -------------------------------------------------------------- velocity split
+    def split_size(self) -> int:
+        n = C.c_size_t()
+        _check(load().dvm_split_size(self.h, C.byref(n)))
+        return n.value
+
+    def split_begin(self, xbuf):
+        """This rank's moment and wall sums into the CUDA tensor ``xbuf``."""
+        _check(load().dvm_split_begin(self.h, _P(xbuf.data_ptr())))
+
+    def split_finish(self, xbuf):
+        """Finish the step from ``xbuf`` summed over the ranks."""
+        _check(load().dvm_split_finish(self.h, _P(xbuf.data_ptr())))
 
     def wall_force(self):
         F = np.zeros(3)
@@ -330,6 +378,55 @@ class Solver:
         return dict(J=float(J[0]), gTw=gtw, gbc=[g.reshape(-1, 5) for g in gbc],
                     gprim0=None if gp is None else gp.reshape(-1, 5), ms_forward=float(tf[0]),
                     ms_reverse=float(tr[0]))
+
+    def adjoint(self, nsteps: int, checkpoint_every: int = 20, with_drag: bool = False, seed=None,
+                want_lambda0: bool = True, want_init: bool = False) -> dict:
+        """Gradient of J = [with_drag] F_x(F^N) + <seed, F^N> (dvm_adjoint).
+        ``seed``: numpy array or CUDA tensor in the public layout; lambda0 is
+        returned the same way (a CUDA tensor if the seed is one)."""
+        ns = max(int(self.cfg.get("nseg", 0)), 1)
+        gtw = np.zeros(ns)
+        nside = [self.cfg["ny"], self.cfg["ny"], self.cfg["nx"], self.cfg["nx"]]
+        gbc = [np.zeros(5 * n) for n in nside]
+        gp = np.zeros(5 * self.ncell) if want_init else None
+        J = np.zeros(1)
+        dev = seed is not None and not isinstance(seed, np.ndarray)
+        if seed is None:
+            sp, sd = None, 0
+        elif dev:
+            sp, sd = _P(seed.data_ptr()), 1
+        else:
+            seed = np.ascontiguousarray(seed, dtype=self.dtype)
+            sp, sd = _P(seed.ctypes.data), 0
+        lam = None
+        lp = None
+        if want_lambda0:
+            if dev:
+                import torch
+                lam = torch.empty(self.state_size, dtype=seed.dtype, device=seed.device)
+                lp = _P(lam.data_ptr())
+            else:
+                lam = np.empty(self.state_size, self.dtype)
+                lp = _P(lam.ctypes.data)
+        _check(load().dvm_adjoint(self.h, int(nsteps), int(checkpoint_every), int(bool(with_drag)), sp, sd, lp,
+                                  1 if dev else 0, _ptr(J), _ptr(gtw), *[_ptr(g) for g in gbc], _ptr(gp)))
+        return dict(J=float(J[0]), gTw=gtw, lambda0=lam, gbc=[g.reshape(-1, 5) for g in gbc],
+                    gprim0=None if gp is None else gp.reshape(-1, 5))
+
+    def step_vjp(self, lam_np1) -> tuple:
+        """One transposed step around the current state (dvm_step_vjp): returns
+        (lambda_n, dJ/dT_w); the context advances one step."""
+        ns = max(int(self.cfg.get("nseg", 0)), 1)
+        gtw = np.zeros(ns)
+        if isinstance(lam_np1, np.ndarray):
+            lam_np1 = np.ascontiguousarray(lam_np1, dtype=self.dtype)
+            out = np.empty(self.state_size, self.dtype)
+            _check(load().dvm_step_vjp(self.h, _P(lam_np1.ctypes.data), _P(out.ctypes.data), 0, _ptr(gtw)))
+        else:
+            import torch
+            out = torch.empty_like(lam_np1)
+            _check(load().dvm_step_vjp(self.h, _P(lam_np1.data_ptr()), _P(out.data_ptr()), 1, _ptr(gtw)))
+        return out, gtw
 
     # -------------------------------------------------------------- instrumentation
     def timing(self, enable):

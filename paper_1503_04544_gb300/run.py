@@ -48,12 +48,16 @@ def main(argv=None):
     ap.add_argument("--time-scheme", choices=["explicit", "imex"], default="explicit")
     ap.add_argument("--model", choices=["bgk", "shakhov"], default="bgk",
                     help="collision model (Shakhov: Pr = 2/3)")
+    ap.add_argument("--equilibrium", choices=["direct", "conservative"], default="direct",
+                    help="BGK equilibrium from the direct moments or the conservative Newton parameters (Sec. 3.1)")
     args = ap.parse_args(argv)
     cfg = problem(args.workload, args.cells, args.nv, args.scheme)
     if args.time_scheme == "imex":
         cfg["time_scheme"] = 1
     if args.model == "shakhov":
         cfg.update(model=1, Pr=2.0 / 3.0)
+    if args.equilibrium == "conservative":
+        cfg["conservative"] = 1
     s = dvm.Solver(cfg, dvm.FP32 if args.precision == "fp32" else dvm.FP64)
     s.init_maxwellian()
     if args.workload == "adjoint":
