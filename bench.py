@@ -417,7 +417,9 @@ def measure(cfg, prec, args, world, local, stream, peak, peak_kind, fp64_peak=No
     s.timing(False)
     shak_ms, ns = 0.0, 0
     if cfg.get("model", 0) == 1:
-        # the Shakhov term's kernel, timed over a second run of the same steps
+        # the Shakhov model's own kernel (3D: k_shakhov3 every step; 2D:
+        # k_heatflux, every step in FP64, in FP32 only on a step that has no
+        # raw moments of its state), timed over a second run of the same steps
         s.timing(2)
         s.step_async(min(args.steps, 500))
         shak_ms, ns = s.kernel_time()
@@ -452,8 +454,10 @@ def measure(cfg, prec, args, world, local, stream, peak, peak_kind, fp64_peak=No
     achieved = bulk_pairs * bytes_per_pair / avg_bulk_s / 1e9
     dim3 = cfg.get("dim", 2) == 3
     wl = workload_key(cfg)
+    # the 2D explicit Shakhov step runs its own variant of k_bulk
+    shak_tag = "shakhov_" if (cfg.get("model", 0) == 1 and not dim3 and cfg.get("time_scheme", 0) == 0) else ""
     traffic = recorded_traffic(
-        f"k_bulk{'3' if dim3 else ''}_{wl}_{prec_name}.md",
+        f"k_bulk{'3' if dim3 else ''}_{shak_tag}{wl}_{prec_name}.md",
         os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step3d.cu" if dim3 else "dvm_step2d.cu"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": traffic,
@@ -463,25 +467,27 @@ def measure(cfg, prec, args, world, local, stream, peak, peak_kind, fp64_peak=No
                 "bulk_ms_per_launch": avg_bulk_s * 1e3,
                 "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)}
     if ns:
-        # Shakhov: k_shakhov reads F^n of every gas cell (heat flux) and
-        # reads and writes F^{n+1}: 3 x 2 components per pair
+        # Shakhov, 2D: k_heatflux reads F^n of every gas cell once (the
+        # step kernels form the Shakhov equilibrium themselves); 3D:
+        # k_shakhov3 reads F^n (heat flux) and reads and writes F^{n+1}
         avg_s = shak_ms / ns / 1e3
-        sb = 3 * s.ncomp * s.elem
+        sb = (3 if dim3 else 1) * s.ncomp * s.elem
         ach = pairs_per_step * sb / avg_s / 1e9
+        kname = "k_shakhov3" if dim3 else "k_heatflux"
         shak = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "frac_of_nominal": ach / NOMINAL_HBM_GBS,
-                "traffic": recorded_traffic(f"k_shakhov{'3' if dim3 else ''}_{wl}_{prec_name}.md",
+                "traffic": recorded_traffic(f"{kname}_{wl}_{prec_name}.md",
                                             os.path.join(ROOT, "paper_1503_04544_gb300", "csrc",
                                                          "dvm_shakhov3d.cu" if dim3 else "dvm_shakhov2d.cu")),
-                "kernel": ("k_shakhov3" if dim3 else "k_shakhov")
-                + " (heat flux of F^n + Shakhov term on F^{n+1} + moments)",
+                "kernel": kname + (" (heat flux of F^n + Shakhov term on F^{n+1} + moments)" if dim3
+                                   else " (heat flux of F^n for the Shakhov equilibrium)"),
                 "peak_source": f"{peak_kind} HBM copy bandwidth", "bytes_per_pair": sb,
                 "ms_per_launch": avg_s * 1e3, "share_of_step": avg_s * 1e3 / (ms / args.steps)}
         if avg_s > avg_bulk_s:
             shak["k_bulk"] = roofline
             roofline = shak
         else:
-            roofline["k_shakhov"] = shak
+            roofline[kname] = shak
     if prec == dvm.FP64 and not dim3 and cfg.get("scheme", 1) == 1 and roofline["kernel"].startswith("k_bulk"):
         # the FP64 step is bound by the FP64 pipe on this part: report that
         # ceiling (the measured FP64 FMA throughput), with the HBM view beside it

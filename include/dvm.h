@@ -142,10 +142,16 @@ int dvm_set_time_scheme(dvm_ctx *ctx, int scheme);
  * q = sum c (|c|^2/2 f + g) dv of the control volume at t^n (Eq.
  * MacroscopicDDv); in 3D F_S = M [1 + (1 - Pr) c.q (|c|^2/T - 5) / (5 P T)]
  * with q = sum c |c|^2/2 F dv (Sec. 2.1).  Pr = 1 is the BGK model.  The
- * Shakhov model is implemented with a fixed or no obstacle and the explicit
- * scheme; other combinations return DVM_ERR_UNSUPPORTED here, from
- * dvm_set_time_scheme or from dvm_step (a moving obstacle), and the drag
- * adjoint is BGK only.  Errors: DVM_ERR_ARG (model or Pr), DVM_ERR_UNSUPPORTED. */
+ * Shakhov model runs with a fixed, rotating (2D) or no obstacle and with
+ * both time schemes (the semi-implicit one relaxes towards the Shakhov
+ * equilibrium with the heat flux q_T / (1 + nu Pr) of the transported
+ * values, nu = dt/tau); the conservative equilibrium and the velocity split
+ * are BGK only (DVM_ERR_UNSUPPORTED here or there), and so is the drag
+ * adjoint.  The 2D explicit step takes q from moments that the previous
+ * step's kernels summed (raw third moments of the new state, shifted to each
+ * cell's velocity), so a step right after the state is set, and every FP64
+ * step, first reads F^n once for q.  Errors: DVM_ERR_ARG (model or Pr),
+ * DVM_ERR_UNSUPPORTED, DVM_ERR_OOM. */
 int dvm_set_collision_model(dvm_ctx *ctx, int model, double Pr);
 
 /* Moments that set the BGK equilibrium of each control volume (Sec. 3.1).
@@ -381,7 +387,8 @@ int dvm_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, int with_drag, c
 int dvm_step_vjp(dvm_ctx *ctx, const void *lambda_np1, void *lambda_n, int on_device, double *gTw);
 
 /* Live timing of one kernel: enable = 1 the fused bulk stream-and-relax
- * kernel, 2 the Shakhov term (dvm_set_collision_model), 0 off.  Every step
+ * kernel, 2 the Shakhov model's own kernel (dvm_set_collision_model: the 2D
+ * heat-flux pass where it runs, the 3D Shakhov term), 0 off.  Every step
  * records a CUDA event pair around that kernel's launch on the context's
  * stream.  dvm_kernel_time synchronises the stream, returns the summed
  * duration in milliseconds and the number of timed launches, and clears the

@@ -182,11 +182,11 @@ cudaError_t shakhov3d(dvm_ctx *c);   // the Shakhov term of the 3D step (dvm_sha
 static cudaError_t st_step(dvm_ctx *c)
 {
     cudaError_t e = c->dim == 2 ? step2d(c) : step3d(c);
-    // the explicit scheme adds the Shakhov term after the step; the
-    // semi-implicit one relaxes towards the Shakhov equilibrium in its
-    // relaxation kernel
-    if (e == cudaSuccess && c->model == DVM_SHAKHOV && c->time_scheme == DVM_EXPLICIT)
-        e = c->dim == 2 ? shakhov2d(c) : shakhov3d(c);
+    // the 2D step relaxes towards the Shakhov equilibrium itself; the 3D
+    // explicit step adds the Shakhov term after the step; the semi-implicit
+    // schemes relax towards it in their relaxation kernels
+    if (e == cudaSuccess && c->model == DVM_SHAKHOV && c->time_scheme == DVM_EXPLICIT && c->dim == 3)
+        e = shakhov3d(c);
     return e;
 }
 
@@ -220,6 +220,7 @@ static cudaError_t graph_steps(dvm_ctx *c, int pairs, int *done)
         destroy_retired(c);
     }
     const long long steps0 = c->steps_done, launches0 = c->launches;
+    const bool hvalid0 = c->hvalid;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return cudaSuccess;
@@ -237,6 +238,7 @@ static cudaError_t graph_steps(dvm_ctx *c, int pairs, int *done)
     if (graph) cudaGraphDestroy(graph);
     if (!ok) {
         // not capturable here: nothing was enqueued, step launch by launch
+        c->hvalid = hvalid0;
         cudaGetLastError();
         return cudaSuccess;
     }
@@ -283,6 +285,9 @@ int dvm_create(const dvm_grid *grid, const dvm_vgrid *vg, const dvm_physics *ph,
     }
     if (dim == 3 && (double)(grid->nx + 4) * (grid->ny + 4) * (grid->nz + 4) > 2.0e9) {
         set_error("3D grid too large for 32-bit slab indices"); return DVM_ERR_ARG;
+    }
+    if (dim == 2 && (double)(grid->nx + 4) * (grid->ny + 4) > 2.0e9) {
+        set_error("2D grid too large for 32-bit slab indices"); return DVM_ERR_ARG;
     }
     dvm_ctx *c = new (std::nothrow) dvm_ctx();
     if (!c) { set_error("host allocation"); return DVM_ERR_OOM; }
@@ -472,7 +477,8 @@ void dvm_destroy(dvm_ctx *c)
     cudaFree(c->spec_list); cudaFree(c->wall_list); cudaFree(c->counts);
     cudaFree(c->wphi); cudaFree(c->wcontrib); cudaFree(c->cvinfo);
     cudaFree(c->d_body); cudaFree(c->d_hist); cudaFree(c->d_err);
-    cudaFree(c->d_scratch); cudaFree(c->d_out); cudaFree(c->eqp); cudaFree(c->split_in); cudaFree(c->cv_ratio);
+    cudaFree(c->d_scratch); cudaFree(c->d_out); cudaFree(c->eqp); cudaFree(c->split_in); cudaFree(c->qheat);
+    cudaFree(c->hpart[0]); cudaFree(c->hpart[1]);
     cudaFree(c->d_Twseg); cudaFree(c->d_segdir);
     for (int s = 0; s < 6; ++s) cudaFree(c->d_bcstate[s]);
     cudaFree(c->d_prim0);
@@ -569,6 +575,7 @@ static int set_body3d(dvm_ctx *c, const dvm_body *b)
         CK(masters_flags3d(c));
     }
     c->need_fusion = true;
+    c->hvalid = false;
     c->steps_done = 0;
     return check_flags(c);
 }
@@ -596,11 +603,6 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
         CK(cudaMemcpy(c->d_segdir, b->seg_dir, sizeof(double) * 2 * b->nseg, cudaMemcpyHostToDevice));
     }
     c->moving = b->shape != DVM_SHAPE_NONE && b->movable;
-    // per-cell control-volume area ratios of a moving obstacle (the Shakhov
-    // term scales with them)
-    cudaFree(c->cv_ratio);
-    c->cv_ratio = nullptr;
-    if (c->moving) CK(cudaMalloc(&c->cv_ratio, sizeof(double) * (size_t)c->nc));
     // box of cells that can be non-gas or have a non-gas cell within reach
     if (b->shape == DVM_SHAPE_NONE) {
         c->i0 = c->i1 = c->j0 = c->j1 = 0;
@@ -640,6 +642,7 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
         CK(masters_flags2d(c, false));
     }
     c->need_fusion = true;
+    c->hvalid = false;
     c->steps_done = 0;
     return check_flags(c);
 }
@@ -654,6 +657,7 @@ int dvm_geometry2d_at(dvm_ctx *c, double cos_t, double sin_t)
     CK(geometry2d_level(c, c->gcur, body_trig(c, 0)));
     CK(masters_flags2d(c, false));
     c->need_fusion = true;
+    c->hvalid = false;
     return check_flags(c);
 }
 
@@ -681,6 +685,7 @@ int dvm_init_maxwellian(dvm_ctx *c, const double *rho, const double *ux, const d
     CK(st_partials(c));
     c->have_state = true;
     c->need_fusion = true;
+    c->hvalid = false;
     return check_flags(c);
 }
 
@@ -704,6 +709,7 @@ int dvm_set_state(dvm_ctx *c, const void *f, size_t bytes, int on_device)
     CK(st_partials(c));
     c->have_state = true;
     c->need_fusion = true;
+    c->hvalid = false;
     CK(cudaStreamSynchronize(c->stream));
     return DVM_OK;
 }
@@ -943,6 +949,18 @@ int dvm_set_collision_model(dvm_ctx *c, int model, double Pr)
         if (!(Pr >= 0) || !std::isfinite(Pr)) { set_error("Prandtl number must be finite and >= 0"); return DVM_ERR_ARG; }
         if (const char *why = shakhov_unsupported(c)) { set_error(why); return DVM_ERR_UNSUPPORTED; }
     }
+    if (model == DVM_SHAKHOV && c->dim == 2 && !c->qheat) {
+        const size_t hb = ((size_t)c->S * 5 + 2) * c->nc * c->elem;
+        if (cudaMalloc(&c->qheat, (size_t)2 * c->nc * c->elem) != cudaSuccess ||
+            cudaMalloc(&c->hpart[0], hb) != cudaSuccess || cudaMalloc(&c->hpart[1], hb) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->qheat); cudaFree(c->hpart[0]); cudaFree(c->hpart[1]);
+            c->qheat = c->hpart[0] = c->hpart[1] = nullptr;
+            set_error("dvm_set_collision_model: out of device memory");
+            return DVM_ERR_OOM;
+        }
+    }
+    c->hvalid = false;
     c->model = model;
     c->Pr = model == DVM_SHAKHOV ? Pr : 1.0;
     return DVM_OK;
@@ -1030,6 +1048,7 @@ static cudaError_t take_snapshot(dvm_ctx *c, StepMark *m)
 static cudaError_t restore_snapshot(dvm_ctx *c, const StepMark &m)
 {
     c->cur = m.cur; c->gcur = m.gcur; c->steps_done = m.steps; c->need_fusion = m.need_fusion;
+    c->hvalid = false;
     cudaError_t e = cudaMemcpyAsync(c->f[c->cur], c->snap_f, c->dev_elems * c->elem, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->part[c->cur], c->snap_part, part_bytes(c), cudaMemcpyDeviceToDevice, c->stream);

@@ -344,22 +344,23 @@ __device__ __forceinline__ long didx(const Grid2D &g, long k, int comp, int p)
 
 // Padding cells that mirror interior cell (i, j) on periodic and
 // zero-gradient sides (at most two along each axis); -1 where unused.
-__device__ __forceinline__ void mirrors(const Grid2D &g, int i, int j, long (&m)[4])
+template <typename I>
+__device__ __forceinline__ void mirrors(const Grid2D &g, int i, int j, I (&m)[4])
 {
     m[0] = m[1] = m[2] = m[3] = -1;
     if (g.bc[0] == DVM_BC_PERIODIC) {
-        if (i < 2) m[0] = nbr(g, i + g.nx, j);
-        else if (i >= g.nx - 2) m[0] = nbr(g, i - g.nx, j);
+        if (i < 2) m[0] = (I)nbr(g, i + g.nx, j);
+        else if (i >= g.nx - 2) m[0] = (I)nbr(g, i - g.nx, j);
     } else {
-        if (i == 0 && g.bc[0] == DVM_BC_ZEROGRAD) { m[0] = nbr(g, -1, j); m[1] = nbr(g, -2, j); }
-        if (i == g.nx - 1 && g.bc[1] == DVM_BC_ZEROGRAD) { m[0] = nbr(g, g.nx, j); m[1] = nbr(g, g.nx + 1, j); }
+        if (i == 0 && g.bc[0] == DVM_BC_ZEROGRAD) { m[0] = (I)nbr(g, -1, j); m[1] = (I)nbr(g, -2, j); }
+        if (i == g.nx - 1 && g.bc[1] == DVM_BC_ZEROGRAD) { m[0] = (I)nbr(g, g.nx, j); m[1] = (I)nbr(g, g.nx + 1, j); }
     }
     if (g.bc[2] == DVM_BC_PERIODIC) {
-        if (j < 2) m[2] = nbr(g, i, j + g.ny);
-        else if (j >= g.ny - 2) m[2] = nbr(g, i, j - g.ny);
+        if (j < 2) m[2] = (I)nbr(g, i, j + g.ny);
+        else if (j >= g.ny - 2) m[2] = (I)nbr(g, i, j - g.ny);
     } else {
-        if (j == 0 && g.bc[2] == DVM_BC_ZEROGRAD) { m[2] = nbr(g, i, -1); m[3] = nbr(g, i, -2); }
-        if (j == g.ny - 1 && g.bc[3] == DVM_BC_ZEROGRAD) { m[2] = nbr(g, i, g.ny); m[3] = nbr(g, i, g.ny + 1); }
+        if (j == 0 && g.bc[2] == DVM_BC_ZEROGRAD) { m[2] = (I)nbr(g, i, -1); m[3] = (I)nbr(g, i, -2); }
+        if (j == g.ny - 1 && g.bc[3] == DVM_BC_ZEROGRAD) { m[2] = (I)nbr(g, i, g.ny); m[3] = (I)nbr(g, i, g.ny + 1); }
     }
 }
 

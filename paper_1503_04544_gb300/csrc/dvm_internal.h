@@ -191,8 +191,10 @@ struct dvm_ctx {
     bool split;                   // dvm_set_velocity_split: steps through dvm_split_begin / _finish
     bool split_begun;             // dvm_split_begin done, dvm_split_finish pending
     void *split_in;               // [4 or 5][nc] summed moment sums in the state precision (velocity split)
-    double *cv_ratio;             // [nc] area ratio S^n / S^{n+1,*} of each special cell's control volume
-                                  //   (Shakhov with a moving obstacle)
+    void *qheat;                  // [2][nc] heat flux of each cell's control volume at t^n (2D Shakhov, state precision)
+    void *hpart[2];               // 2D Shakhov, paired with part[]: raw heat-flux moments [S][5][nc] of the state
+                                  // about a reference velocity [2][nc] per cell, written by the step that made it
+    bool hvalid;                  // hpart[cur] belongs to f[cur] (else the step starts with k_heatflux)
     bool dt_given;                // dt came from dvm_physics, not from the CFL rule
     void *eqp;                    // [dim + 2][nc] conservative equilibrium parameters (state precision)
     void *snap_f, *snap_part;     // dvm_step: state and moment sums at the last checked step
@@ -221,7 +223,7 @@ cudaError_t tables2d(dvm_ctx *c);
 cudaError_t partials_from_state2d(dvm_ctx *c);
 cudaError_t init_maxwellian2d(dvm_ctx *c, const double *d_prim);
 cudaError_t step2d(dvm_ctx *c);
-cudaError_t shakhov2d(dvm_ctx *c);                             // Eq. ShakhovDD term after a step (dvm_shakhov2d.cu)
+cudaError_t heatflux2d(dvm_ctx *c, const void *f, const void *part);   // heat flux of F^n for the Shakhov step (dvm_shakhov2d.cu)
 cudaError_t eqpar(dvm_ctx *c, const void *part, int S);         // conservative equilibrium parameters into c->eqp (dvm_equilibrium.cu)
 cudaError_t split_step2d(dvm_ctx *c, int phase, void *xbuf);    // velocity split: 1 begin, 2 finish (dvm_step2d.cu)
 cudaError_t split_step3d(dvm_ctx *c, int phase, void *xbuf);    // the same in 3D (dvm_step3d.cu)

@@ -68,6 +68,10 @@ template <typename T> struct BulkArgs {
     const ulonglong2 *pt;     // [ngrp][7] packed-pair coefficients (FP32 path)
     const int8_t *gsign;      // [ngrp][2]
     const T *eqp;             // [4][nc] conservative equilibrium parameters, or null (direct moments)
+    const T *qh;              // [2][nc] heat flux of the control volume at t^n (Shakhov model), used when hin is null
+    const T *hin;             // Shakhov: raw heat-flux moments of f^n [S][5][nc] and their reference velocity [2][nc]
+    T *hout;                  // Shakhov: the same for f^n+1
+    T pr1;                    // 1 - Pr (Shakhov model)
     uint32_t *bits;           // [ngrp][bslab] limiter branches of the downwind faces (recording only)
     int bpitch;               // row pitch of the branch words
     long bslab;               // branch words per group
@@ -265,10 +269,95 @@ __device__ __forceinline__ void fold_pairs(F2 (&Q)[4], T &q0, T &q1, T &q2, T &q
     for (int m = 0; m < 4; ++m) Q[m] = f2(0.f);
 }
 
+// Compensated sums of the FP32 Shakhov variant of the bulk kernel, kept in
+// shared memory (rows [m][sum, compensation], one column per thread) to
+// leave the registers to the update: the four moments and the five raw
+// heat-flux moments.
+constexpr int kSaccRows = 9;
+constexpr size_t kSaccBytes = (size_t)kSaccRows * 2 * 32 * kRows * sizeof(float);
+
+__device__ __forceinline__ void sacc_add(float *sa, int m, int tid, float x)
+{
+    constexpr int N = 32 * kRows;
+    Acc<float> a;
+    a.s = sa[(2 * m) * N + tid];
+    a.c = sa[(2 * m + 1) * N + tid];
+    a.add(x);
+    sa[(2 * m) * N + tid] = a.s;
+    sa[(2 * m + 1) * N + tid] = a.c;
+}
+
+__device__ __forceinline__ float sacc_value(const float *sa, int m, int tid)
+{
+    constexpr int N = 32 * kRows;
+    Acc<float> a;
+    a.s = sa[(2 * m) * N + tid];
+    a.c = sa[(2 * m + 1) * N + tid];
+    return a.value();
+}
+
+// Adds both lanes of the per-lane sums Q (n of them) to the shared
+// compensated sums from row m0 on and clears them.
+template <int n>
+__device__ __forceinline__ void fold_lanes(F2 (&Q)[n], int m0, float *sa, int tid)
+{
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+        float a, b;
+        f2_get(Q[m], a, b);
+        sacc_add(sa, m0 + m, tid, a + b);
+        Q[m] = f2(0.f);
+    }
+}
+
+// Compile-time choice between two variables.
+template <bool A, typename T>
+__device__ __forceinline__ T &sel(T &a, T &b)
+{
+    if constexpr (A) return a; else return b;
+}
+
+// Raw heat-flux moments (Shakhov model) of one component of a pair of
+// velocities about the origin, from the velocity table only: component 0
+// (f) adds vx ke f, vy ke f, vx^2 f, vx vy f, vy^2 f to H[0..4] (ke =
+// |v|^2/2), component 1 (g) adds vx g, vy g to H[0], H[1].  With the
+// moments of the cell, its heat flux about its own velocity u is
+//   q = H_(x,y) - u.P_(.,x|y) - u E + rho u |u|^2
+// (P the second moments, E = sum (ke f + g)); the same identity holds about
+// any reference velocity u_r with u - u_r in place of u.
+template <int COMP>
+__device__ __forceinline__ void hmom_x2(F2 O, F2 VX, F2 VY, F2 KE, F2 (&H)[5])
+{
+    if (COMP == 0) {
+        const F2 TX = mul2(VX, O), TY = mul2(VY, O);
+        H[2] = fma2(VX, TX, H[2]);
+        H[3] = fma2(VY, TX, H[3]);
+        H[4] = fma2(VY, TY, H[4]);
+        H[0] = fma2(KE, TX, H[0]);
+        H[1] = fma2(KE, TY, H[1]);
+    } else {
+        H[0] = fma2(VX, O, H[0]);
+        H[1] = fma2(VY, O, H[1]);
+    }
+}
+
+// The same over one FP32 velocity group (values o at velocities vx, vy).
+template <int COMP>
+__device__ __forceinline__ void hmom_group(const float (&o)[4], const float (&vx)[4], const float (&vy)[4],
+                                           F2 (&H)[5])
+{
+#pragma unroll
+    for (int e = 0; e < 4; e += 2) {
+        const F2 VX = f2(vx[e], vx[e + 1]), VY = f2(vy[e], vy[e + 1]);
+        const F2 KE = mul2(f2(0.5f), fma2(VX, VX, mul2(VY, VY)));
+        hmom_x2<COMP>(f2(o[e], o[e + 1]), VX, VY, KE, H);
+    }
+}
+
 // Store of one (group, component) vector of a cell and of its padding
 // mirrors (cells within two cells of a periodic or zero-gradient side).
 template <typename T>
-__device__ __forceinline__ void store_cell(typename Vec<T>::type *slab, long pc, const long (&mir)[4], bool anymir,
+__device__ __forceinline__ void store_cell(typename Vec<T>::type *slab, int pc, const int (&mir)[4], bool anymir,
                                            const T (&v)[Vec<T>::W])
 {
     vst<T>(slab + pc, v);
@@ -291,10 +380,21 @@ __device__ __forceinline__ void store_cell(typename Vec<T>::type *slab, long pc,
 // With REC (recomputation for the discrete adjoint) each plain cell also
 // writes the limiter branches of its downwind faces, one word per group at
 // its padded index (row pitch bpitch).
-template <typename T, bool MUSCL, bool REC>
+// With SHAK (the Shakhov model, Eq. ShakhovDD, explicit scheme) the cell
+// relaxes towards f_S = M [1 + k c.q (|c|^2/T - 4)], g_S = T/2 M [1 + k c.q
+// (|c|^2/T - 2)], k = (1 - Pr) / (5 rho T^2), with the heat flux q of the
+// cell at t^n: from the raw moments of f^n that the previous step left in
+// hin (shifted to the cell's velocity, see hmom_x2), or from k_heatflux when
+// hin is null.  The FP32 variant leaves the raw moments of f^{n+1} about the
+// origin in hout for the next step.
+template <typename T, bool MUSCL, bool REC, bool SHAK>
 __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int W = Vec<T>::W;
+    // raw heat-flux moments of the new state (FP32 only: an FP64 step is
+    // bound by the FP64 pipe, where one more read of f^n by k_heatflux costs
+    // less than these sums)
+    constexpr bool HRAW = SHAK && sizeof(T) == 4;
     using V = typename Vec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     V *ring = reinterpret_cast<V *>(smem);
@@ -307,7 +407,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     const bool inside = i < g.nx && j < g.ny;
     const long nc = (long)g.nx * g.ny;
     const long cell = inside ? (long)j * g.nx + i : 0;
-    const long pc = nbr(g, i, j);
+    const int pc = (int)nbr(g, i, j);
     const int split = blockIdx.z;
     const int gps = (g.ngrp + a.S - 1) / a.S;
     const int g0 = split * gps, g1 = min(g0 + gps, g.ngrp);
@@ -330,6 +430,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
 
     // equilibrium of the cell at t^n
     T A = 0, c2 = 0, r = 0, gfac = 0, ux = 0, uy = 0, el0 = 0, e1x = 0, e1y = 0;
+    T kqx = 0, kqy = 0, iT = 0, l2a4 = 0, nkuq = 0;  // Shakhov: k q_x, k q_y, 1/T, 2 log2(A)/log2(e) - 4, -k u.q
     if (plain) {
         T s[4];
         gather_partials(a.pin, a.Sin, nc, cell, s);
@@ -345,6 +446,37 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
         A = rho / (T(2.0 * kPi) * tmp);
         c2 = T(kLog2e) / (T(2) * tmp);
         gfac = tmp / T(2);
+        if constexpr (SHAK) {
+            T qx = 0, qy = 0;
+            if (HRAW && a.hin) {
+                // heat flux at t^n from the raw moments of f^n that the
+                // previous step wrote, about their reference velocity u_r
+                // (the origin, or the control volume's velocity at t^{n-1}
+                // for cells that k_special wrote): w = u - u_r and
+                // E' = sum (|v - u_r|^2/2 f + g)
+                Acc<T> h[5];
+                for (int sp = 0; sp < a.S; ++sp)
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) h[m].merge(a.hin[((long)sp * 5 + m) * nc + cell], T(0));
+                const long ur = (long)a.S * 5 * nc + cell;
+                const T urx = a.hin[ur], ury = a.hin[ur + nc];
+                const T wx = ux - urx, wy = uy - ury;
+                const T e1 = s[3] - urx * s[1] - ury * s[2] + T(0.5) * (urx * urx + ury * ury) * s[0];
+                const T rw2 = s[0] * (wx * wx + wy * wy);
+                const T dv = pick<T>(g.dv_f, g.dv);
+                qx = dv * (h[0].value() - wx * h[2].value() - wy * h[3].value() - wx * e1 + wx * rw2);
+                qy = dv * (h[1].value() - wx * h[3].value() - wy * h[4].value() - wy * e1 + wy * rw2);
+            } else {
+                qx = a.qh[cell];
+                qy = a.qh[nc + cell];
+            }
+            const T k = a.pr1 / (T(5) * rho * tmp * tmp);
+            kqx = k * qx;
+            kqy = k * qy;
+            iT = T(1) / tmp;
+            l2a4 = T(2.0 / kLog2e) * log2(A) - T(4);
+            nkuq = -(kqx * ux + kqy * uy);
+        }
         // log2 M(v) = el0 + e1x vx + e1y vy - c2 |v|^2 (packed path)
         if (!REC) {
             el0 = log2(A) - c2 * (ux * ux + uy * uy);
@@ -358,7 +490,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     const T wxm = (mask & 1) ? T(0.5) : T(0), wxp = (mask & 2) ? T(0.5) : T(0);
     const T wym = (mask & 4) ? T(0.5) : T(0), wyp = (mask & 8) ? T(0.5) : T(0);
     const int c0 = (ty + 2) * kTileX + tx + 2;
-    long mir[4];
+    int mir[4];               // padded indices fit in 32 bits (checked at context creation)
     mirrors(g, i, j, mir);
     const bool anymir = __any_sync(0xffffffffu, inside && (mir[0] >= 0 || mir[2] >= 0));
     __syncthreads();
@@ -380,6 +512,17 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     F2 Qp[4];                 // per-lane sums of the packed FP32 path
 #pragma unroll
     for (int m = 0; m < 4; ++m) Qp[m] = f2(0.f);
+    // FP32 Shakhov: raw heat-flux moments of f^{n+1} about the origin, per
+    // lane over 16 groups, then (with the four moments) into the shared
+    // compensated sums
+    F2 Hp[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) Hp[m] = f2(0.f);
+    float *sacc = reinterpret_cast<float *>(smem + kStages * kStageBytes + 2 * kStages * sizeof(uint64_t));
+    if constexpr (HRAW) {
+#pragma unroll
+        for (int m = 0; m < 2 * kSaccRows; ++m) sacc[m * 32 * kRows + tid] = 0;
+    }
     int fold = 0;
     for (int it = 0; it < ngr; ++it) {
         const int q = g0 + it, st = it % kStages;
@@ -397,6 +540,10 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
             const int sx = a.gsign[2 * q], sy = a.gsign[2 * q + 1];
             T vx[W], vy[W], nux[W], nuy[W], feq[W], out[W];
             uint32_t bw = 0;
+            // the FP32 Shakhov variant keeps every moment sum in the per-lane
+            // pairs: the scalar path's sums of this group go there at its end
+            T t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+            T &p0 = sel<HRAW>(t0, q0), &p1 = sel<HRAW>(t1, q1), &p2 = sel<HRAW>(t2, q2), &p3 = sel<HRAW>(t3, q3);
             if constexpr (sizeof(T) == 4 && MUSCL) {
                 if (sx != 0 && sy != 0) {
                     // packed FP32 path of the sign-uniform groups, coefficients
@@ -413,7 +560,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                             rows[k][1].v = v.y;
                         }
                     }
-                    F2 fq[2];
+                    F2 fq[2], fg[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         if (REC) {          // the recording variant keeps fewer per-cell registers
@@ -434,16 +581,39 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                             float x0, x1;
                             f2_get(X, x0, x1);
                             fq[h] = f2(ex2_fast(x0), ex2_fast(x1));
+                            if constexpr (SHAK) {
+                                // |c|^2/T - 4 = 2 (log2 A - log2 M) / log2 e - 4,
+                                // k c.q = kqx vx + kqy vy - (kqx ux + kqy uy);
+                                // f_S = M + M k c.q (|c|^2/T - 4) and
+                                // g_S = T/2 (f_S + 2 M k c.q)
+                                const F2 D4 = fma2(f2(float(-2.0 / kLog2e)), X, f2(l2a4));
+                                const F2 KCQ = fma2(P.vx[h], f2(kqx), fma2(P.vy[h], f2(kqy), f2(nkuq)));
+                                const F2 MK = mul2(fq[h], KCQ);
+                                fq[h] = fma2(MK, D4, fq[h]);
+                                fg[h] = mul2(f2(gfac), fma2(MK, f2(2.f), fq[h]));
+                            }
                         }
                     }
                     const F2 r2 = f2(r);
                     bulk_tile_x2<0, REC>(tile, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out, Qp, bw);
                     store_cell<T>(o0, pc, mir, anymir, out);
-                    const F2 gf = f2(gfac);
-                    fq[0] = mul2(fq[0], gf); fq[1] = mul2(fq[1], gf);
+                    if constexpr (SHAK) {
+                        hmom_x2<0>(f2(out[0], out[1]), P.vx[0], P.vy[0], P.ke[0], Hp);
+                        hmom_x2<0>(f2(out[2], out[3]), P.vx[1], P.vy[1], P.ke[1], Hp);
+                    }
+                    if constexpr (SHAK) {
+                        fq[0] = fg[0]; fq[1] = fg[1];
+                    } else {
+                        const F2 gf = f2(gfac);
+                        fq[0] = mul2(fq[0], gf); fq[1] = mul2(fq[1], gf);
+                    }
                     bulk_tile_x2<1, REC>(tile + kTileY * kTileX, c0, ux1, uy1, P, fq, wxm, wxp, wym, wyp, r2, out,
                                          Qp, bw);
                     store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
+                    if constexpr (SHAK) {
+                        hmom_x2<1>(f2(out[0], out[1]), P.vx[0], P.vy[0], P.ke[0], Hp);
+                        hmom_x2<1>(f2(out[2], out[3]), P.vx[1], P.vy[1], P.ke[1], Hp);
+                    }
                     goto stored;
                 }
             }
@@ -472,33 +642,63 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                     feq[e] = A * dexp2(-(dx * dx + dy * dy) * c2);
                 }
             }
+            // Shakhov: the equilibria of f and g (the BGK g equilibrium T/2 M
+            // is formed in place after the f update)
+            T feqg[W];
+            if constexpr (SHAK) {
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    const T dx = vx[e] - ux, dy = vy[e] - uy;
+                    const T kcq = kqx * dx + kqy * dy, d2 = (dx * dx + dy * dy) * iT;
+                    feqg[e] = gfac * feq[e] * fma(kcq, d2 - T(2), T(1));
+                    feq[e] *= fma(kcq, d2 - T(4), T(1));
+                }
+            }
             if (sx != 0 && sy != 0) {
                 const int ux1 = sx > 0 ? 1 : -1, uy1 = sy > 0 ? kTileX : -kTileX;
                 bulk_tile<T, MUSCL, 0, true, REC>(tile, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
-                                                  out, q0, q1, q2, q3, bw);
+                                                  out, p0, p1, p2, p3, bw);
                 store_cell<T>(o0, pc, mir, anymir, out);
+                if constexpr (HRAW) hmom_group<0>(out, vx, vy, Hp);
+                if constexpr (!SHAK) {
 #pragma unroll
-                for (int e = 0; e < W; ++e) feq[e] *= gfac;
-                bulk_tile<T, MUSCL, 1, true, REC>(tile + kTileY * kTileX, c0, ux1, uy1, vx, vy, nux, nuy, feq, wxm,
-                                                  wxp, wym, wyp, r, out, q0, q1, q2, q3, bw);
+                    for (int e = 0; e < W; ++e) feqg[e] = feq[e] * gfac;
+                }
+                bulk_tile<T, MUSCL, 1, true, REC>(tile + kTileY * kTileX, c0, ux1, uy1, vx, vy, nux, nuy, feqg, wxm,
+                                                  wxp, wym, wyp, r, out, p0, p1, p2, p3, bw);
                 store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
+                if constexpr (HRAW) hmom_group<1>(out, vx, vy, Hp);
             } else {
                 bulk_tile<T, MUSCL, 0, false, REC>(tile, c0, 1, kTileX, vx, vy, nux, nuy, feq, wxm, wxp, wym, wyp, r,
-                                                   out, q0, q1, q2, q3, bw);
+                                                   out, p0, p1, p2, p3, bw);
                 store_cell<T>(o0, pc, mir, anymir, out);
+                if constexpr (HRAW) hmom_group<0>(out, vx, vy, Hp);
+                if constexpr (!SHAK) {
 #pragma unroll
-                for (int e = 0; e < W; ++e) feq[e] *= gfac;
-                bulk_tile<T, MUSCL, 1, false, REC>(tile + kTileY * kTileX, c0, 1, kTileX, vx, vy, nux, nuy, feq,
-                                                   wxm, wxp, wym, wyp, r, out, q0, q1, q2, q3, bw);
+                    for (int e = 0; e < W; ++e) feqg[e] = feq[e] * gfac;
+                }
+                bulk_tile<T, MUSCL, 1, false, REC>(tile + kTileY * kTileX, c0, 1, kTileX, vx, vy, nux, nuy, feqg,
+                                                   wxm, wxp, wym, wyp, r, out, p0, p1, p2, p3, bw);
                 store_cell<T>(o0 + g.slab, pc, mir, anymir, out);
+                if constexpr (HRAW) hmom_group<1>(out, vx, vy, Hp);
+            }
+            if constexpr (HRAW) {
+                Qp[0] = add2(Qp[0], f2(t0, 0.f)); Qp[1] = add2(Qp[1], f2(t1, 0.f));
+                Qp[2] = add2(Qp[2], f2(t2, 0.f)); Qp[3] = add2(Qp[3], f2(t3, 0.f));
             }
         stored:
             if (REC) a.bits[(long)q * a.bslab + (long)(j + 2) * a.bpitch + i + 2] = bw;
-            // fold the plain sums of 8 groups into the compensated sums
-            if (++fold == 8) {
-                if constexpr (sizeof(T) == 4 && MUSCL) fold_pairs(Qp, q0, q1, q2, q3);
-                m0.add(q0); m1.add(q1); m2.add(q2); m3.add(q3);
-                q0 = q1 = q2 = q3 = 0;
+            // fold the plain sums of 8 groups (16 in the FP32 Shakhov variant)
+            // into the compensated sums
+            if (++fold == (HRAW ? 16 : 8)) {
+                if constexpr (HRAW) {
+                    fold_lanes<4>(Qp, 0, sacc, tid);
+                    fold_lanes<5>(Hp, 4, sacc, tid);
+                } else {
+                    if constexpr (sizeof(T) == 4 && MUSCL) fold_pairs(Qp, q0, q1, q2, q3);
+                    m0.add(q0); m1.add(q1); m2.add(q2); m3.add(q3);
+                    q0 = q1 = q2 = q3 = 0;
+                }
                 fold = 0;
             }
         } else if (zero) {
@@ -517,15 +717,37 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
         for (int k = max(ngr - kStages, 0); k < ngr; ++k) mbar_wait(&full[k % kStages], (uint32_t)((k / kStages) & 1));
     }
     if (plain) {
-        if constexpr (sizeof(T) == 4 && MUSCL) fold_pairs(Qp, q0, q1, q2, q3);
-        m0.add(q0); m1.add(q1); m2.add(q2); m3.add(q3);
-        a.pout[((long)split * 4 + 0) * nc + cell] = m0.value();
-        a.pout[((long)split * 4 + 1) * nc + cell] = m1.value();
-        a.pout[((long)split * 4 + 2) * nc + cell] = m2.value();
-        a.pout[((long)split * 4 + 3) * nc + cell] = m3.value();
+        if constexpr (HRAW) {
+            fold_lanes<4>(Qp, 0, sacc, tid);
+            fold_lanes<5>(Hp, 4, sacc, tid);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) a.pout[((long)split * 4 + m) * nc + cell] = sacc_value(sacc, m, tid);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) a.hout[((long)split * 5 + m) * nc + cell] = sacc_value(sacc, 4 + m, tid);
+            // the reference velocity of these sums: the origin
+            if (split == 0) {
+                a.hout[(long)a.S * 5 * nc + cell] = 0;
+                a.hout[((long)a.S * 5 + 1) * nc + cell] = 0;
+            }
+        } else {
+            if constexpr (sizeof(T) == 4 && MUSCL) fold_pairs(Qp, q0, q1, q2, q3);
+            m0.add(q0); m1.add(q1); m2.add(q2); m3.add(q3);
+            a.pout[((long)split * 4 + 0) * nc + cell] = m0.value();
+            a.pout[((long)split * 4 + 1) * nc + cell] = m1.value();
+            a.pout[((long)split * 4 + 2) * nc + cell] = m2.value();
+            a.pout[((long)split * 4 + 3) * nc + cell] = m3.value();
+        }
     } else if (zero) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) a.pout[((long)split * 4 + m) * nc + cell] = 0;
+        if constexpr (HRAW) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) a.hout[((long)split * 5 + m) * nc + cell] = 0;
+            if (split == 0) {
+                a.hout[(long)a.S * 5 * nc + cell] = 0;
+                a.hout[((long)a.S * 5 + 1) * nc + cell] = 0;
+            }
+        }
     }
 }
 
@@ -546,6 +768,9 @@ struct CvArgs {
     const void *cvinfo;       // control-volume records
     const void *vt;           // per-velocity coefficients (state precision)
     const void *eqp;          // [4][nc] conservative equilibrium parameters, or null
+    int shak;                 // the Shakhov model under the explicit scheme
+    void *hout;               // Shakhov: raw heat-flux moments of f^n+1 [S][5][nc] and reference velocity [2][nc]
+    double pr1;               // 1 - Pr (Shakhov model)
     int *err;
 };
 
@@ -598,10 +823,8 @@ __device__ int gather_members(const CvArgs &c, long m, int32_t *mem)
 
 // Control-volume records of every control volume in the list (once per
 // geometry): members from the master search, their slab indices, padding
-// mirrors, edge lengths, wall edges and the area ratios.  With ratio set,
-// every member also gets its control volume's area ratio S^n / S^{n+1,*}
-// (the Shakhov term of a moving obstacle scales with it).
-__global__ void __launch_bounds__(256) k_members(CvArgs c, CvInfo *info, double *ratio)
+// mirrors, edge lengths, wall edges and the area ratios.
+__global__ void __launch_bounds__(256) k_members(CvArgs c, CvInfo *info)
 {
     __shared__ int32_t mem[kMaxMembers];
     const Grid2D &g = c.g;
@@ -644,8 +867,6 @@ __global__ void __launch_bounds__(256) k_members(CvArgs c, CvInfo *info, double 
             I.bco = Sp > 0 ? g.dt / Sp : 0.0;
             if (!(Sp > 0)) atomicExch(&c.err[kErrGeometry], 1);
         }
-        __syncthreads();
-        if (ratio && threadIdx.x < nm) ratio[mem[threadIdx.x]] = I.a;
         __syncthreads();
     }
 }
@@ -939,12 +1160,38 @@ __global__ void __launch_bounds__(256) k_special(CvArgs c, const T *fin, T *fout
         }
         const T A = rho / (T(2.0 * kPi) * tmp);
         const T i2T = T(1) / (T(2) * tmp);
+        // Shakhov (Eq. ShakhovDD): k q with the heat flux of the control
+        // volume at t^n, summed here over every velocity of its (fused) state
+        T kqx = 0, kqy = 0;
+        if (c.shak) {
+            Acc<T> h0, h1;
+            for (int p = threadIdx.x; p < g.nv; p += blockDim.x) {
+                const VCoef<T> vc = ld_coef(vt + p);
+                const T dx = vc.vx - ux, dy = vc.vy - uy;
+                const T fa = fin[ebase<T>(g, 0, p) + I.pcm * W], fb = fin[ebase<T>(g, 1, p) + I.pcm * W];
+                const T w = T(0.5) * (dx * dx + dy * dy) * fa + fb;
+                h0.add(dx * w);
+                h1.add(dy * w);
+            }
+            const T dv = pick<T>(g.dv_f, g.dv);
+            const T qx = block_acc(h0, red) * dv, qy = block_acc(h1, red) * dv;
+            const T k = T(c.pr1) / (T(5) * rho * tmp * tmp);
+            kqx = k * qx;
+            kqy = k * qy;
+        }
         Acc<T> s0, s1, s2, s3;
+        Acc<T> hs[5];     // Shakhov: raw heat-flux moments of the new state about (ux, uy)
         for (int p = v0 + threadIdx.x; p < v1; p += blockDim.x) {
             const VCoef<T> vc = ld_coef(vt + p);
             const T vx = vc.vx, vy = vc.vy, nux = vc.nux, nuy = vc.nuy;
             const T dxu = vx - ux, dyu = vy - uy;
             const T feq0 = A * dexp(-(dxu * dxu + dyu * dyu) * i2T);
+            T sf = T(1), sg = T(1);
+            if (c.shak) {
+                const T kcq = kqx * dxu + kqy * dyu, d2 = (dxu * dxu + dyu * dyu) * T(2) * i2T;
+                sf = fma(kcq, d2 - T(4), T(1));
+                sg = fma(kcq, d2 - T(2), T(1));
+            }
             const long base0 = ebase<T>(g, 0, p), base1 = ebase<T>(g, 1, p);
             T R0 = 0, R1 = 0;
             for (int q = 0; q < nm; ++q) {
@@ -989,7 +1236,7 @@ __global__ void __launch_bounds__(256) k_special(CvArgs c, const T *fin, T *fout
             for (int comp = 0; comp < 2; ++comp) {
                 const long base = comp == 0 ? base0 : base1;
                 const T fcv = fin[base + I.pcm * W];
-                const T feq = comp == 0 ? feq0 : tmp / T(2) * feq0;
+                const T feq = comp == 0 ? feq0 * sf : tmp / T(2) * feq0 * sg;
                 const T fn = a * fcv - bco * (comp == 0 ? R0 : R1) + a * r * (feq - fcv);
                 for (int q = 0; q < nm; ++q) {
                     const CvMember &M = I.mem[q];
@@ -1004,6 +1251,15 @@ __global__ void __launch_bounds__(256) k_special(CvArgs c, const T *fin, T *fout
                 } else {
                     s3.add(fn);
                 }
+                if (c.hout) {
+                    if (comp == 0) {
+                        const T tx = dxu * fn, ty = dyu * fn, k2 = T(0.5) * (dxu * dxu + dyu * dyu);
+                        hs[0].add(k2 * tx); hs[1].add(k2 * ty);
+                        hs[2].add(dxu * tx); hs[3].add(dyu * tx); hs[4].add(dyu * ty);
+                    } else {
+                        hs[0].add(dxu * fn); hs[1].add(dyu * fn);
+                    }
+                }
             }
         }
         const T t0 = block_acc(s0, red), t1 = block_acc(s1, red);
@@ -1011,6 +1267,23 @@ __global__ void __launch_bounds__(256) k_special(CvArgs c, const T *fin, T *fout
         if (threadIdx.x < nm) {
             const CvMember &M = I.mem[threadIdx.x];
             write_split_partials<T>(pout, sp, nc, (long)M.j * g.nx + M.i, M.keep != 0, t0, t1, t2, t3);
+        }
+        if (c.hout) {
+            T hv[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) hv[q] = block_acc(hs[q], red);
+            if (threadIdx.x < nm) {
+                const CvMember &M = I.mem[threadIdx.x];
+                const long k = (long)M.j * g.nx + M.i;
+                const bool keep = M.keep != 0;
+                T *ho = static_cast<T *>(c.hout);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) ho[((long)sp * 5 + q) * nc + k] = keep ? hv[q] : T(0);
+                if (sp == 0) {
+                    ho[(long)c.S * 5 * nc + k] = keep ? ux : T(0);
+                    ho[((long)c.S * 5 + 1) * nc + k] = keep ? uy : T(0);
+                }
+            }
         }
         __syncthreads();
     }
@@ -1425,19 +1698,20 @@ __global__ void k_tables(Grid2D g, VCoef<T> *vt, int8_t *gsign, float4 *ptab)
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
-template <typename T, bool MUSCL, bool REC>
+template <typename T, bool MUSCL, bool REC, bool SHAK>
 cudaError_t launch_bulk(dvm_ctx *c, const BulkArgs<T> &a)
 {
-    const size_t smem = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t);
+    const size_t smem = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t) +
+                        (SHAK && sizeof(T) == 4 ? kSaccBytes : 0);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_bulk<T, MUSCL, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_bulk<T, MUSCL, REC, SHAK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(nblk(c->nx, 32), nblk(c->ny, kRows), c->S), block(32, kRows);
-    k_bulk<T, MUSCL, REC><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
+    k_bulk<T, MUSCL, REC, SHAK><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
     return cudaGetLastError();
 }
 
@@ -1505,6 +1779,15 @@ cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
     cv.cvinfo = c->cvinfo; cv.vt = c->vtab;
     const bool cons = c->eq_mode == DVM_EQ_CONSERVATIVE;
     cv.eqp = cons && !imex ? c->eqp : nullptr;
+    // the Shakhov model under the explicit scheme relaxes towards its
+    // equilibrium inside the step, with the heat flux of F^n from the raw
+    // moments the previous step left (k_heatflux when there are none)
+    const bool shak = c->model == DVM_SHAKHOV && !imex;
+    const bool hkeep = shak && c->prec == DVM_FP32;      // raw heat-flux moments kept (FP32)
+    const bool hraw = hkeep && c->hvalid;
+    cv.shak = shak ? 1 : 0;
+    cv.hout = hkeep ? c->hpart[1 - c->cur] : nullptr;
+    cv.pr1 = 1.0 - c->Pr;
     cv.err = c->d_err;
     const int cvgrid = 4 * 152;
     double *xw = xbuf ? xbuf + 4 * nc : nullptr;
@@ -1534,6 +1817,9 @@ cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
     const int Sin = phase == 2 ? 1 : c->S;
     // conservative equilibrium parameters of f_CV^n (after fusion)
     if (cons && !imex && (e = eqpar(c, pin, Sin)) != cudaSuccess) return e;
+    // heat flux of every control volume at t^n (after fusion) when no raw
+    // moments of F^n are at hand
+    if (shak && !hraw && (e = heatflux2d(c, fin, pin)) != cudaSuccess) return e;
     if (body) {
         // the wall kernel (wall density, stress, force, rotation) and then the
         // control-volume kernel run on the side stream beside the bulk kernel:
@@ -1550,12 +1836,17 @@ cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
     a.flags = c->flags; a.vt = (const VCoef<T> *)c->vtab; a.gsign = c->gsign; a.err = c->d_err;
     a.pt = (const ulonglong2 *)c->ptab;
     a.eqp = cons && !imex ? (const T *)c->eqp : nullptr;
+    a.qh = shak && !hraw ? (const T *)c->qheat : nullptr;
+    a.hin = hraw ? (const T *)c->hpart[c->cur] : nullptr;
+    a.hout = hkeep ? (T *)c->hpart[1 - c->cur] : nullptr;
+    a.pr1 = T(1.0 - c->Pr);
     a.bits = c->rec_bits;
     a.bpitch = bits_pitch(c);
     a.bslab = bits_slab(c);
     if ((e = timing_mark(c, 0)) != cudaSuccess) return e;
-    if (c->scheme != DVM_MUSCL) e = launch_bulk<T, false, false>(c, a);
-    else e = c->rec_bits ? launch_bulk<T, true, true>(c, a) : launch_bulk<T, true, false>(c, a);
+    if (shak) e = c->scheme != DVM_MUSCL ? launch_bulk<T, false, false, true>(c, a) : launch_bulk<T, true, false, true>(c, a);
+    else if (c->scheme != DVM_MUSCL) e = launch_bulk<T, false, false, false>(c, a);
+    else e = c->rec_bits ? launch_bulk<T, true, true, false>(c, a) : launch_bulk<T, true, false, false>(c, a);
     if (e != cudaSuccess) return e;
     if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
     c->launches += 1;
@@ -1584,6 +1875,7 @@ cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
     c->cur = 1 - c->cur;
     if (moving) c->gcur = 1 - c->gcur;
     c->need_fusion = false;
+    c->hvalid = hkeep;
     c->steps_done++;
     return cudaGetLastError();
 }
@@ -1669,7 +1961,7 @@ cudaError_t members2d(dvm_ctx *c, bool moving)
     cv.master = c->master; cv.flags = c->flags; cv.wslot = c->wslot;
     cv.spec_list = c->spec_list; cv.counts = c->counts; cv.cap = c->list_cap;
     cv.err = c->d_err;
-    k_members<<<4 * 152, 256, 0, c->stream>>>(cv, (CvInfo *)c->cvinfo, c->cv_ratio);
+    k_members<<<4 * 152, 256, 0, c->stream>>>(cv, (CvInfo *)c->cvinfo);
     return cudaGetLastError();
 }
 
