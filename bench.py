@@ -454,8 +454,10 @@ def measure(cfg, prec, args, world, local, stream, peak, peak_kind, fp64_peak=No
     achieved = bulk_pairs * bytes_per_pair / avg_bulk_s / 1e9
     dim3 = cfg.get("dim", 2) == 3
     wl = workload_key(cfg)
-    # the 2D explicit Shakhov step runs its own variant of k_bulk
-    shak_tag = "shakhov_" if (cfg.get("model", 0) == 1 and not dim3 and cfg.get("time_scheme", 0) == 0) else ""
+    # the explicit Shakhov step runs its own variant of the bulk kernel (2D;
+    # 3D in FP32)
+    shak_tag = "shakhov_" if (cfg.get("model", 0) == 1 and cfg.get("time_scheme", 0) == 0
+                              and (not dim3 or prec == dvm.FP32)) else ""
     traffic = recorded_traffic(
         f"k_bulk{'3' if dim3 else ''}_{shak_tag}{wl}_{prec_name}.md",
         os.path.join(ROOT, "paper_1503_04544_gb300", "csrc", "dvm_step3d.cu" if dim3 else "dvm_step2d.cu"))
@@ -467,19 +469,20 @@ def measure(cfg, prec, args, world, local, stream, peak, peak_kind, fp64_peak=No
                 "bulk_ms_per_launch": avg_bulk_s * 1e3,
                 "bulk_share_of_step": (bulk_ms / max(nb, 1)) / (ms / args.steps)}
     if ns:
-        # Shakhov, 2D: k_heatflux reads F^n of every gas cell once (the
-        # step kernels form the Shakhov equilibrium themselves); 3D:
-        # k_shakhov3 reads F^n (heat flux) and reads and writes F^{n+1}
+        # Shakhov: k_heatflux / k_heatflux3 read F^n of every gas cell once
+        # (the step kernels form the Shakhov equilibrium themselves); FP64
+        # 3D: k_shakhov3 reads F^n (heat flux) and reads and writes F^{n+1}
         avg_s = shak_ms / ns / 1e3
-        sb = (3 if dim3 else 1) * s.ncomp * s.elem
+        post = dim3 and prec == dvm.FP64
+        sb = (3 if post else 1) * s.ncomp * s.elem
         ach = pairs_per_step * sb / avg_s / 1e9
-        kname = "k_shakhov3" if dim3 else "k_heatflux"
+        kname = "k_shakhov3" if post else ("k_heatflux3" if dim3 else "k_heatflux")
         shak = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "frac_of_nominal": ach / NOMINAL_HBM_GBS,
                 "traffic": recorded_traffic(f"{kname}_{wl}_{prec_name}.md",
                                             os.path.join(ROOT, "paper_1503_04544_gb300", "csrc",
                                                          "dvm_shakhov3d.cu" if dim3 else "dvm_shakhov2d.cu")),
-                "kernel": kname + (" (heat flux of F^n + Shakhov term on F^{n+1} + moments)" if dim3
+                "kernel": kname + (" (heat flux of F^n + Shakhov term on F^{n+1} + moments)" if post
                                    else " (heat flux of F^n for the Shakhov equilibrium)"),
                 "peak_source": f"{peak_kind} HBM copy bandwidth", "bytes_per_pair": sb,
                 "ms_per_launch": avg_s * 1e3, "share_of_step": avg_s * 1e3 / (ms / args.steps)}

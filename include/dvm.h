@@ -150,8 +150,10 @@ int dvm_set_time_scheme(dvm_ctx *ctx, int scheme);
  * adjoint.  The 2D explicit step takes q from moments that the previous
  * step's kernels summed (raw third moments of the new state, shifted to each
  * cell's velocity), so a step right after the state is set, and every FP64
- * step, first reads F^n once for q.  Errors: DVM_ERR_ARG (model or Pr),
- * DVM_ERR_UNSUPPORTED, DVM_ERR_OOM. */
+ * step, first reads F^n once for q; the 3D explicit step reads F^n once for
+ * q before the step in FP32, and adds the Shakhov term after the BGK step in
+ * FP64.  Errors: DVM_ERR_ARG (model or Pr), DVM_ERR_UNSUPPORTED,
+ * DVM_ERR_OOM. */
 int dvm_set_collision_model(dvm_ctx *ctx, int model, double Pr);
 
 /* Moments that set the BGK equilibrium of each control volume (Sec. 3.1).
@@ -387,8 +389,8 @@ int dvm_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, int with_drag, c
 int dvm_step_vjp(dvm_ctx *ctx, const void *lambda_np1, void *lambda_n, int on_device, double *gTw);
 
 /* Live timing of one kernel: enable = 1 the fused bulk stream-and-relax
- * kernel, 2 the Shakhov model's own kernel (dvm_set_collision_model: the 2D
- * heat-flux pass where it runs, the 3D Shakhov term), 0 off.  Every step
+ * kernel, 2 the Shakhov model's own kernel (dvm_set_collision_model: the
+ * heat-flux pass where it runs, the FP64 3D Shakhov term), 0 off.  Every step
  * records a CUDA event pair around that kernel's launch on the context's
  * stream.  dvm_kernel_time synchronises the stream, returns the summed
  * duration in milliseconds and the number of timed launches, and clears the

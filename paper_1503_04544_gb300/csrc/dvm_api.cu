@@ -182,10 +182,12 @@ cudaError_t shakhov3d(dvm_ctx *c);   // the Shakhov term of the 3D step (dvm_sha
 static cudaError_t st_step(dvm_ctx *c)
 {
     cudaError_t e = c->dim == 2 ? step2d(c) : step3d(c);
-    // the 2D step relaxes towards the Shakhov equilibrium itself; the 3D
-    // explicit step adds the Shakhov term after the step; the semi-implicit
-    // schemes relax towards it in their relaxation kernels
-    if (e == cudaSuccess && c->model == DVM_SHAKHOV && c->time_scheme == DVM_EXPLICIT && c->dim == 3)
+    // the 2D step and the FP32 3D step relax towards the Shakhov equilibrium
+    // themselves; the FP64 3D explicit step adds the Shakhov term after the
+    // step; the semi-implicit schemes relax towards it in their relaxation
+    // kernels
+    if (e == cudaSuccess && c->model == DVM_SHAKHOV && c->time_scheme == DVM_EXPLICIT && c->dim == 3 &&
+        c->prec == DVM_FP64)
         e = shakhov3d(c);
     return e;
 }
@@ -949,10 +951,12 @@ int dvm_set_collision_model(dvm_ctx *c, int model, double Pr)
         if (!(Pr >= 0) || !std::isfinite(Pr)) { set_error("Prandtl number must be finite and >= 0"); return DVM_ERR_ARG; }
         if (const char *why = shakhov_unsupported(c)) { set_error(why); return DVM_ERR_UNSUPPORTED; }
     }
-    if (model == DVM_SHAKHOV && c->dim == 2 && !c->qheat) {
-        const size_t hb = ((size_t)c->S * 5 + 2) * c->nc * c->elem;
-        if (cudaMalloc(&c->qheat, (size_t)2 * c->nc * c->elem) != cudaSuccess ||
-            cudaMalloc(&c->hpart[0], hb) != cudaSuccess || cudaMalloc(&c->hpart[1], hb) != cudaSuccess) {
+    if (model == DVM_SHAKHOV && !c->qheat) {
+        // the heat flux of every cell [D][nc]; 2D also the raw heat-flux
+        // moments of the state, paired with the partial sums
+        const size_t hb = c->dim == 2 ? ((size_t)c->S * 5 + 2) * c->nc * c->elem : 0;
+        if (cudaMalloc(&c->qheat, (size_t)c->dim * c->nc * c->elem) != cudaSuccess ||
+            (hb && (cudaMalloc(&c->hpart[0], hb) != cudaSuccess || cudaMalloc(&c->hpart[1], hb) != cudaSuccess))) {
             cudaGetLastError();
             cudaFree(c->qheat); cudaFree(c->hpart[0]); cudaFree(c->hpart[1]);
             c->qheat = c->hpart[0] = c->hpart[1] = nullptr;

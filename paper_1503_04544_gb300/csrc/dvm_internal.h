@@ -191,7 +191,7 @@ struct dvm_ctx {
     bool split;                   // dvm_set_velocity_split: steps through dvm_split_begin / _finish
     bool split_begun;             // dvm_split_begin done, dvm_split_finish pending
     void *split_in;               // [4 or 5][nc] summed moment sums in the state precision (velocity split)
-    void *qheat;                  // [2][nc] heat flux of each cell's control volume at t^n (2D Shakhov, state precision)
+    void *qheat;                  // [D][nc] heat flux of each cell's control volume at t^n (Shakhov, state precision)
     void *hpart[2];               // 2D Shakhov, paired with part[]: raw heat-flux moments [S][5][nc] of the state
                                   // about a reference velocity [2][nc] per cell, written by the step that made it
     bool hvalid;                  // hpart[cur] belongs to f[cur] (else the step starts with k_heatflux)
@@ -223,7 +223,8 @@ cudaError_t tables2d(dvm_ctx *c);
 cudaError_t partials_from_state2d(dvm_ctx *c);
 cudaError_t init_maxwellian2d(dvm_ctx *c, const double *d_prim);
 cudaError_t step2d(dvm_ctx *c);
-cudaError_t heatflux2d(dvm_ctx *c, const void *f, const void *part);   // heat flux of F^n for the Shakhov step (dvm_shakhov2d.cu)
+cudaError_t heatflux2d(dvm_ctx *c, const void *f, const void *part);
+cudaError_t heatflux3d(dvm_ctx *c, const void *f, const void *part);   // [3][nc] heat flux into qheat (dvm_shakhov3d.cu)   // heat flux of F^n for the Shakhov step (dvm_shakhov2d.cu)
 cudaError_t eqpar(dvm_ctx *c, const void *part, int S);         // conservative equilibrium parameters into c->eqp (dvm_equilibrium.cu)
 cudaError_t split_step2d(dvm_ctx *c, int phase, void *xbuf);    // velocity split: 1 begin, 2 finish (dvm_step2d.cu)
 cudaError_t split_step3d(dvm_ctx *c, int phase, void *xbuf);    // the same in 3D (dvm_step3d.cu)

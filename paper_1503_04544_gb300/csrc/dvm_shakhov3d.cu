@@ -2,11 +2,16 @@
 // Sec. 2.1) under the explicit scheme (Eq. eq-schema3D): relaxation towards
 //   F_S = M [1 + (1 - Pr) c.q (|c|^2/T - 5) / (5 P T)],
 // c = v - u, P = rho T (R = 1), with the heat flux q = sum c |c|^2/2 F dv of
-// the control volume at t^n.  As in 2D, with a fixed obstacle the step
-// kernels' relaxation towards M differs from the scheme's by
+// the control volume at t^n.
+//
+// FP32: k_heatflux3 writes q of every cell's control volume before the step,
+// and the step kernels (k_bulk3, k_special3) relax towards F_S themselves.
+// FP64: the step kernels relax towards M, and k_shakhov3 adds the difference
 //   (dt/tau) k c.q (|c|^2/T - 5) M,   k = (1 - Pr) / (5 rho T^2),
-// which k_shakhov3 adds to every gas cell after the step; it then rewrites
-// the moment sums of the new state.
+// to every gas cell after the step (the obstacle is fixed, so the area ratio
+// of the scheme's relaxation term is 1); it then rewrites the moment sums of
+// the new state.  (The FP64 bulk kernel's shared memory has no room for the
+// Shakhov coefficients of its column cells.)
 #include "dvm_device.cuh"
 
 namespace dvm {
@@ -53,26 +58,26 @@ __device__ __forceinline__ void side_mirrors3(const Grid3D &g, int i, int j, int
 __device__ __forceinline__ float exp2_s3(float x) { return ex2_fast(x); }
 __device__ __forceinline__ double exp2_s3(double x) { return exp2(x); }
 
-// Block = 32 consecutive cells of an x-row x kMomChunks warps, each warp one
-// chunk of the velocity groups.  Pass 1 sums the heat flux of the cell's
-// control volume from F^n (its master's values after fusion), pass 2 adds the
-// Shakhov term to F^{n+1} of the cell and its padding mirrors and sums the
-// five moments of the result.  Solid cells keep their zero state and sums.
+// Heat flux of the control volume of cell (i, j, k) at t^n, for a block of 32
+// consecutive cells of an x-row x kMomChunks warps, each warp one chunk of
+// the velocity groups: the primitives from the partial sums of its master,
+// q from the master's F^n (after fusion), compensated sums merged over the
+// chunks in fixed order into qsh (every warp of the block reads them after
+// the barrier).  gas is false for solid cells and cells in no control volume.
 template <typename T>
-__global__ void __launch_bounds__(32 * kMomChunks)
-    k_shakhov3(Grid3D g, int S, T dt_tau0, T pr1, const T *fin, const T *pin, T *fout, T *pout,
-               const VxEntry<T> *vxt, const VyzEntry<T> *vyz, const int32_t *master, const int8_t *type, int *err)
+__device__ __forceinline__ void cv_heat_flux3(const Grid3D &g, int S, const T *fin, const T *pin,
+                                              const VxEntry<T> *vxt, const VyzEntry<T> *vyz, const int32_t *master,
+                                              const int8_t *type, int *err, int i, int j, int k, T (&qsh)[3][32],
+                                              bool &gas, T &rho, T &ux, T &uy, T &uz, T &tmp)
 {
     constexpr int W = Vec<T>::W;
     using V = typename Vec<T>::type;
-    __shared__ T qsh[3][32];
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const long nc = (long)g.nx * g.ny * g.nz, cell = ((long)k * g.ny + j) * g.nx + i;
     const T dv = pick<T>(g.dv_f, g.dv);
-    bool gas = i < g.nx && type[cell] != DVM_SOLID;
+    gas = i < g.nx && type[cell] != DVM_SOLID;
     const long m = gas ? (long)master[cell] : -1;
     gas = gas && m >= 0;
-    T rho = 0, ux = 0, uy = 0, uz = 0, tmp = 0;
+    rho = ux = uy = uz = tmp = 0;
     if (gas) {
         Acc<T> a[5];
         for (int q = 0; q < S; ++q)
@@ -91,7 +96,6 @@ __global__ void __launch_bounds__(32 * kMomChunks)
     }
     const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
     const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
-    // pass 1: heat flux of the control volume at t^n
     Acc<T> hq[3];
     if (gas && q0 < q1) {
         const int mk = (int)(m / ((long)g.nx * g.ny)), mr = (int)(m - (long)mk * g.nx * g.ny);
@@ -128,6 +132,44 @@ __global__ void __launch_bounds__(32 * kMomChunks)
         for (int d = 0; d < 3; ++d) qsh[d][threadIdx.x] = hq[d].value() * dv;
     }
     __syncthreads();
+}
+
+// The heat flux of every cell's control volume at t^n into q[3][nc] (0 for
+// solid cells and cells in no control volume).
+template <typename T>
+__global__ void __launch_bounds__(32 * kMomChunks)
+    k_heatflux3(Grid3D g, int S, const T *fin, const T *pin, const VxEntry<T> *vxt, const VyzEntry<T> *vyz,
+                const int32_t *master, const int8_t *type, T *q, int *err)
+{
+    __shared__ T qsh[3][32];
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    bool gas;
+    T rho, ux, uy, uz, tmp;
+    cv_heat_flux3(g, S, fin, pin, vxt, vyz, master, type, err, i, j, k, qsh, gas, rho, ux, uy, uz, tmp);
+    if (threadIdx.y != 0 || i >= g.nx) return;
+    const long nc = (long)g.nx * g.ny * g.nz, cell = ((long)k * g.ny + j) * g.nx + i;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) q[d * nc + cell] = gas ? qsh[d][threadIdx.x] : T(0);
+}
+
+// FP64: pass 1 (cv_heat_flux3), then pass 2 adds the Shakhov term to F^{n+1}
+// of the cell and its padding mirrors and sums the five moments of the
+// result.  Solid cells keep their zero state and sums.
+template <typename T>
+__global__ void __launch_bounds__(32 * kMomChunks)
+    k_shakhov3(Grid3D g, int S, T dt_tau0, T pr1, const T *fin, const T *pin, T *fout, T *pout,
+               const VxEntry<T> *vxt, const VyzEntry<T> *vyz, const int32_t *master, const int8_t *type, int *err)
+{
+    constexpr int W = Vec<T>::W;
+    using V = typename Vec<T>::type;
+    __shared__ T qsh[3][32];
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const long nc = (long)g.nx * g.ny * g.nz, cell = ((long)k * g.ny + j) * g.nx + i;
+    bool gas;
+    T rho, ux, uy, uz, tmp;
+    cv_heat_flux3(g, S, fin, pin, vxt, vyz, master, type, err, i, j, k, qsh, gas, rho, ux, uy, uz, tmp);
+    const int gps = (g.ngrp + kMomChunks - 1) / kMomChunks;
+    const int q0 = threadIdx.y * gps, q1 = min(q0 + gps, g.ngrp);
     const T qx = qsh[0][threadIdx.x], qy = qsh[1][threadIdx.x], qz = qsh[2][threadIdx.x];
     // pass 2: the Shakhov term on F^{n+1}
     Acc<T> a5[5];
@@ -205,7 +247,29 @@ cudaError_t shakhov3d_t(dvm_ctx *c)
     return timing_mark_kernel(c, 2, 1);
 }
 
+template <typename T>
+cudaError_t heatflux3d_t(dvm_ctx *c, const void *f, const void *part)
+{
+    const Grid3D g = grid3d(c);
+    const VxEntry<T> *vxt = reinterpret_cast<const VxEntry<T> *>(c->vtab);
+    const VyzEntry<T> *vyz = reinterpret_cast<const VyzEntry<T> *>(reinterpret_cast<const char *>(c->vtab) +
+                                                                   (size_t)c->nvxp * sizeof(VxEntry<T>));
+    const dim3 grid((unsigned)((c->nx + 31) / 32), (unsigned)c->ny, (unsigned)c->nz), block(32, kMomChunks);
+    cudaError_t e = timing_mark_kernel(c, 2, 0);
+    if (e != cudaSuccess) return e;
+    k_heatflux3<T><<<grid, block, 0, c->stream>>>(g, c->S, (const T *)f, (const T *)part, vxt, vyz, c->master,
+                                                   c->geo3.type, (T *)c->qheat, c->d_err);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return timing_mark_kernel(c, 2, 1);
+}
+
 }  // namespace
+
+cudaError_t heatflux3d(dvm_ctx *c, const void *f, const void *part)
+{
+    return c->prec == DVM_FP32 ? heatflux3d_t<float>(c, f, part) : heatflux3d_t<double>(c, f, part);
+}
 
 cudaError_t shakhov3d(dvm_ctx *c)
 {

@@ -33,6 +33,7 @@ namespace dvm {
 namespace {
 
 constexpr int kCoef3 = 6;            // per-cell coefficients of the bulk kernel
+constexpr int kCoef3S = 11;          // the same with the Shakhov model's five
 
 template <typename T> struct alignas(2 * sizeof(T)) VX3 { T vx, nux; };
 template <typename T> struct alignas(4 * sizeof(T)) VYZ3 { T vy, vz, nuy, nuz; };
@@ -152,6 +153,8 @@ template <typename T> struct Bulk3Args {
     const VX3<T> *vxt;        // [nvxp]
     const VYZ3<T> *vyz;       // [nvy * nvz]
     const T *eqp;             // [5][nc] conservative equilibrium parameters, or null (direct moments)
+    const T *qh;              // [3][nc] heat flux of the control volume at t^n (Shakhov model)
+    T pr1;                    // 1 - Pr (Shakhov model)
     int *err;
 };
 
@@ -174,10 +177,11 @@ template <typename T> __host__ __device__ constexpr int plane_stride3() { return
 // up to kVyzStage (v_y, v_z) pairs (more are read from global memory).
 constexpr int kVyzStage = 512;
 
-template <typename T>
+template <typename T, bool SHAK>
 size_t bulk3_smem()
 {
-    return (size_t)kRing3 * plane_stride3<T>() * 16 + (size_t)kZc3 * (kCoef3 + 10) * 32 * rows3<T>() * sizeof(T) +
+    const int ncoef = SHAK ? kCoef3S : kCoef3;
+    return (size_t)kRing3 * plane_stride3<T>() * 16 + (size_t)kZc3 * (ncoef + 10) * 32 * rows3<T>() * sizeof(T) +
            2 * kRing3 * sizeof(uint64_t) + (size_t)kMaxAxisNv * sizeof(VX3<T>) + (size_t)kVyzStage * sizeof(VYZ3<T>);
 }
 
@@ -224,18 +228,24 @@ __device__ __forceinline__ double exp2_state(double x) { return exp2(x); }
 // the group that contains v_x = 0).  Moments of the new state are summed per
 // cell in registers over 8 groups, then folded into compensated sums in
 // shared memory.
-template <typename T, bool MUSCL>
+// With SHAK (the Shakhov model, FP32) the cells relax towards F_S = M [1 +
+// k c.q (|c|^2/T - 5)], k = (1 - Pr) / (5 rho T^2), with the heat flux q of
+// the cell at t^n from k_heatflux3: |c|^2/T from the Maxwellian's base-2
+// exponent and k c.q linear in v, four operations per velocity.
+template <typename T, bool MUSCL, bool SHAK>
 __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
     k_bulk3(Bulk3Args<T> a, const __grid_constant__ CUtensorMap tmap)
 {
+    static_assert(!SHAK || sizeof(T) == 4, "the Shakhov variant of the bulk kernel is FP32");
     constexpr int W = Vec<T>::W, ZC = kZc3, R = rows3<T>(), NT = 32 * R, NP = ZC + 4;
+    constexpr int NCO = SHAK ? kCoef3S : kCoef3;
     constexpr int PC = plane_stride3<T>(), PB = plane_cells3<T>() * 16;
     static_assert((PC * 16) % 128 == 0, "tensor-copy destinations start on 128-byte boundaries");
     using V = typename Vec<T>::type;
     extern __shared__ __align__(128) unsigned char sm3[];
     V *ring = reinterpret_cast<V *>(sm3);
-    T *coef = reinterpret_cast<T *>(sm3 + kRing3 * PC * 16);        // [ZC][kCoef3][NT]
-    T *ksum = coef + ZC * kCoef3 * NT;                               // [ZC][5][2][NT]
+    T *coef = reinterpret_cast<T *>(sm3 + kRing3 * PC * 16);        // [ZC][NCO][NT]
+    T *ksum = coef + ZC * NCO * NT;                                  // [ZC][5][2][NT]
     uint64_t *full = reinterpret_cast<uint64_t *>(ksum + ZC * 10 * NT);
     uint64_t *empty = full + kRing3;
     VX3<T> *svx = reinterpret_cast<VX3<T> *>(empty + kRing3);          // [kMaxAxisNv]
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
             const bool in = inij && k < g.nz;
             const long cell = ((long)k * g.ny + j) * g.nx + i;
             const uint16_t fl = in ? a.flags[cell] : 0;
-            T *cz = coef + t * kCoef3 * NT + tid;
+            T *cz = coef + t * NCO * NT + tid;
             if (fl & kPlain) {
                 plainm |= 1u << t;
                 T s[5];
@@ -301,6 +311,16 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
                 cz[2 * NT] = c2;
                 cz[3 * NT] = uy;
                 cz[4 * NT] = uz;
+                if constexpr (SHAK) {
+                    // k q, -k u.q and 2 log2(A) / log2(e) - 5
+                    const T kk = a.pr1 / (T(5) * rho * tmp * tmp);
+                    const T kqx = kk * a.qh[cell], kqy = kk * a.qh[nc + cell], kqz = kk * a.qh[2 * nc + cell];
+                    cz[6 * NT] = kqx;
+                    cz[7 * NT] = kqy;
+                    cz[8 * NT] = kqz;
+                    cz[9 * NT] = -(kqx * ux + kqy * uy + kqz * uz);
+                    cz[10 * NT] = T(2.0 / kLog2e) * log2(rho * norm3(tmp)) - T(5);
+                }
             }
             if (fl & kZero) zerom |= 1u << t;
             masks |= (uint32_t)((fl >> kMaskShift3) & 0x3F) << (8 * t);
@@ -429,10 +449,17 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
             if (pl_t || ((zerom >> t) & 1u)) {
                 T out[W];
                 if (pl_t) {
-                    const T *cz = coef + t * kCoef3 * NT + tid;
+                    const T *cz = coef + t * NCO * NT + tid;
                     const T c0c = cz[0], c1 = cz[NT], c2 = cz[2 * NT], uy = cz[3 * NT], uz = cz[4 * NT], r = cz[5 * NT];
                     const T dyv = cyz.vy - uy, dzv = cyz.vz - uz;
                     const T cg = c0c - c2 * (dyv * dyv + dzv * dzv);
+                    // Shakhov: k c.q = kqx vx + (kqy vy + kqz vz - k u.q)
+                    T kqx = 0, kyz = 0, l5 = 0;
+                    if constexpr (SHAK) {
+                        kqx = cz[6 * NT];
+                        kyz = fma(cz[7 * NT], cyz.vy, fma(cz[8 * NT], cyz.vz, cz[9 * NT]));
+                        l5 = cz[10 * NT];
+                    }
                     const T omr = T(1) - r;
                     const T kyo = (mk & (py ? 8u : 4u)) ? ky : T(0), kyi = (mk & (py ? 4u : 8u)) ? ky : T(0);
                     T yu1[W], yu2[W], yd1[W];
@@ -475,7 +502,13 @@ __global__ void __launch_bounds__(32 * (rows3<T>() + 1), 1)
 #pragma unroll
                     for (int e = 0; e < W; ++e) {
                         const T dfy = dflux<T, MUSCL>(f0[e], yu1[e], MUSCL ? yu2[e] : T(0), MUSCL ? yd1[e] : T(0), kyo, kyi);
-                        const T feq = exp2_state(fma(fma(-c2, vx[e], c1), vx[e], cg));
+                        const T xe = fma(fma(-c2, vx[e], c1), vx[e], cg);
+                        T feq = exp2_state(xe);
+                        if constexpr (SHAK) {
+                            // |c|^2/T - 5 = 2 (log2 A - log2 M) / log2 e - 5
+                            const T mk5 = feq * fma(kqx, vx[e], kyz);
+                            feq = fma(mk5, fma(T(-2.0 / kLog2e), xe, l5), feq);
+                        }
                         T o = fma(r, feq, omr * f0[e]);
                         o = fma(-nux[e], dfx[e], o);
                         o = fma(-cyz.nuy, dfy, o);
@@ -565,6 +598,8 @@ struct Cv3Args {
     const void *vxt;
     const void *vyz;
     const void *eqp;          // [5][nc] conservative equilibrium parameters, or null
+    const void *qh;           // [3][nc] heat flux of the control volume at t^n (Shakhov model, FP32), or null
+    double pr1;               // 1 - Pr (Shakhov model)
     int *err;
 };
 
@@ -928,6 +963,15 @@ __global__ void __launch_bounds__(256) k_special3(Cv3Args c, const T *fin, T *fo
         }
         const T A = rho * norm3(tmp);
         const T i2T = T(1) / (T(2) * tmp);
+        // Shakhov (Sec. 2.1): k q with the heat flux of the control volume
+        T kqx = 0, kqy = 0, kqz = 0;
+        if (c.qh) {
+            const T *qh = static_cast<const T *>(c.qh);
+            const T kk = T(c.pr1) / (T(5) * rho * tmp * tmp);
+            kqx = kk * qh[m];
+            kqy = kk * qh[nc + m];
+            kqz = kk * qh[2 * nc + m];
+        }
         Acc<T> acc[5];
         for (int p = v0 + threadIdx.x; p < v1; p += blockDim.x) {
             T vx, vy, vz, nux, nuy, nuz;
@@ -971,7 +1015,9 @@ __global__ void __launch_bounds__(256) k_special3(Cv3Args c, const T *fin, T *fo
             }
             const T fcv = fg[(long)I.pcm * Wd];
             const T dxu = vx - ux, dyu = vy - uy, dzu = vz - uz;
-            const T feq = A * dexp(-(dxu * dxu + dyu * dyu + dzu * dzu) * i2T);
+            const T c2u = dxu * dxu + dyu * dyu + dzu * dzu;
+            T feq = A * dexp(-c2u * i2T);
+            if (c.qh) feq *= fma(kqx * dxu + kqy * dyu + kqz * dzu, c2u * T(2) * i2T - T(5), T(1));
             const T fn = fcv - bco * R + r * (feq - fcv);
             T *og = fout + (long)grp * g.slab * g.W + e;
             for (int t = 0; t < nm; ++t) {
@@ -1396,19 +1442,30 @@ const VYZ3<T> *vyz_table(const dvm_ctx *c)
     return reinterpret_cast<const VYZ3<T> *>(reinterpret_cast<const char *>(c->vtab) + (size_t)c->nvxp * sizeof(VX3<T>));
 }
 
-template <typename T, bool MUSCL>
+template <typename T, bool MUSCL, bool SHAK>
 cudaError_t launch_bulk3(dvm_ctx *c, const Bulk3Args<T> &a)
 {
-    const size_t smem = bulk3_smem<T>();
+    const size_t smem = bulk3_smem<T, SHAK>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_bulk3<T, MUSCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_bulk3<T, MUSCL, SHAK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(nb3(c->nx, 32), nb3(c->ny, rows3<T>()), (unsigned)(a.nzc * a.S)), block(32, rows3<T>() + 1);
-    k_bulk3<T, MUSCL><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
+    k_bulk3<T, MUSCL, SHAK><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
     return cudaGetLastError();
+}
+
+// The bulk kernel for the scheme, and its Shakhov variant in FP32.
+template <typename T>
+cudaError_t launch_bulk3_any(dvm_ctx *c, const Bulk3Args<T> &a, bool shak)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (shak) return c->scheme == DVM_MUSCL ? launch_bulk3<T, true, true>(c, a) : launch_bulk3<T, false, true>(c, a);
+    }
+    return c->scheme == DVM_MUSCL ? launch_bulk3<T, true, false>(c, a) : launch_bulk3<T, false, false>(c, a);
 }
 
 Cv3Args cv3_args(dvm_ctx *c)
@@ -1500,6 +1557,13 @@ cudaError_t step3d_t(dvm_ctx *c, int phase, double *xbuf)
     cv.Sin = Sin;
     // conservative equilibrium parameters of F_CV^n (after fusion)
     if (cons && !imex && (e = eqpar(c, pin, Sin)) != cudaSuccess) return e;
+    // the Shakhov model under the explicit scheme in FP32: the heat flux of
+    // every control volume at t^n (after fusion), and the step kernels relax
+    // towards its equilibrium (FP64: the post-pass k_shakhov3)
+    const bool shak = c->model == DVM_SHAKHOV && !imex && c->prec == DVM_FP32;
+    if (shak && (e = heatflux3d(c, fin, pin)) != cudaSuccess) return e;
+    cv.qh = shak ? c->qheat : nullptr;
+    cv.pr1 = 1.0 - c->Pr;
     if (body) {
         // the wall kernel and then the control-volume kernel run on the side
         // stream beside the bulk kernel: both read F^n and write only the cut
@@ -1513,10 +1577,12 @@ cudaError_t step3d_t(dvm_ctx *c, int phase, double *xbuf)
     Bulk3Args<T> a{};
     a.g = g; a.S = c->S; a.Sin = Sin; a.nzc = (c->nz + kZc3 - 1) / kZc3;
     a.eqp = cons && !imex ? (const T *)c->eqp : nullptr;
+    a.qh = shak ? (const T *)c->qheat : nullptr;
+    a.pr1 = T(1.0 - c->Pr);
     a.fin = fin; a.fout = fout; a.pin = pin; a.pout = pout;
     a.flags = c->flags3; a.vxt = vx_table<T>(c); a.vyz = vyz_table<T>(c); a.err = c->d_err;
     if ((e = timing_mark(c, 0)) != cudaSuccess) return e;
-    e = c->scheme == DVM_MUSCL ? launch_bulk3<T, true>(c, a) : launch_bulk3<T, false>(c, a);
+    e = launch_bulk3_any<T>(c, a, shak);
     if (e != cudaSuccess) return e;
     if ((e = timing_mark(c, 1)) != cudaSuccess) return e;
     c->launches += 1;
