@@ -247,6 +247,16 @@ def adjoint_cost(precision_fp32: bool = True):
     ms_fwd = e0.elapsed_time(e1)
     s.init_maxwellian()
     out = s.drag_adjoint(200, 20)
+    # the same with the forward run's tape kept in HBM (dvm_set_adjoint_tape):
+    # the checkpoint segments need no recomputation; a first call allocates
+    # the tape buffers, the second is timed
+    budget = 160 << 30
+    s.set_adjoint_tape(budget)
+    s.init_maxwellian()
+    s.drag_adjoint(200, 20)
+    s.init_maxwellian()
+    kt = s.drag_adjoint(200, 20)
+    s.set_adjoint_tape(0)
     s.close()
     return {"workload": cfg["name"], "steps": 200, "checkpoint_every": 20,
             "precision": "fp32" if precision_fp32 else "fp64",
@@ -254,8 +264,12 @@ def adjoint_cost(precision_fp32: bool = True):
             "ms_reverse": out["ms_reverse"],
             "reverse_over_forward": out["ms_reverse"] / ms_fwd,
             "gradient_over_forward": (out["ms_forward"] + out["ms_reverse"]) / ms_fwd,
+            "kept_tape": {"budget_bytes": budget, "ms_forward": kt["ms_forward"], "ms_reverse": kt["ms_reverse"],
+                          "gradient_over_forward": (kt["ms_forward"] + kt["ms_reverse"]) / ms_fwd,
+                          "drag_rel_diff": abs(kt["J"] - out["J"]) / max(abs(out["J"]), 1e-300)},
             "note": "reverse = recomputation from checkpoints + transposed steps; "
-                    "gradient = checkpointed forward + reverse"}
+                    "gradient = checkpointed forward + reverse; kept_tape: the forward run keeps "
+                    "every segment's states and limiter branches on the device (no recomputation)"}
 
 
 def max_over_ranks(values, device="cpu"):

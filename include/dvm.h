@@ -361,6 +361,21 @@ int dvm_drag_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, double *J, 
                      double *gbc0, double *gbc1, double *gbc2, double *gbc3, double *gprim0,
                      double *ms_forward, double *ms_reverse);
 
+/* Device memory the adjoint calls may use to keep the forward run's tape
+ * (default 0).  The reverse sweep needs, for every step, the state it
+ * linearises around and the limiter branches that step took; by default it
+ * recomputes each checkpoint segment from its checkpoint.  With a budget,
+ * the forward run writes whole segments (the last ones of the run, as many
+ * as fit: (checkpoint_every - 1) states, partial sums and branch words each)
+ * straight into device buffers and records every step's branches, and the
+ * reverse sweep reads them without recomputing.  The budget is capped by the
+ * free device memory less 4 GiB; buffers that cannot be allocated keep
+ * fewer segments.  Results are those of the recomputing sweep (a step that
+ * records its branches computes the same values as a plain step).  The
+ * buffers stay allocated until a smaller budget or dvm_destroy.  Errors:
+ * DVM_ERR_ARG (null context). */
+int dvm_set_adjoint_tape(dvm_ctx *ctx, size_t max_bytes);
+
 /* Discrete adjoint of nsteps steps for a general objective (the paper has
  * no adjoint; the step of Sec. 3.3.5 is differentiated as it stands, with
  * the same restrictions as dvm_drag_adjoint: 2D, fixed obstacle, explicit

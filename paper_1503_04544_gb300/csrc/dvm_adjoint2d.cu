@@ -1278,6 +1278,13 @@ struct AdjWork {
     std::vector<void *> ckpt, ckpt_part, tape, ptape;
     std::vector<CUtensorMap> tmaps;                  // TMA descriptors of the tape buffers
     std::vector<CUtensorMap> cmaps;                  // TMA descriptors of the checkpoints
+    // kept segments (written by the forward run, never recomputed): slots
+    // 1..K-1 of each, their partial moments and descriptors, and the branch
+    // words of steps 0..K-2
+    std::vector<void *> ktape, kptape;
+    std::vector<CUtensorMap> kmaps;
+    std::vector<uint32_t *> kbits;
+    std::vector<CUtensorMap> kbmaps;
     int cap = 0;
 };
 
@@ -1303,7 +1310,36 @@ void release(AdjWork &w)
     for (void *p : w.ckpt_part) cudaFree(p);
     for (void *p : w.tape) cudaFree(p);
     for (void *p : w.ptape) cudaFree(p);
+    for (void *p : w.ktape) cudaFree(p);
+    for (void *p : w.kptape) cudaFree(p);
+    for (uint32_t *p : w.kbits) cudaFree(p);
     w = AdjWork();
+}
+
+// Copy of the padding frame (two cells on every side: boundary ghosts and
+// mirrors) of every (group, component) slab of src into dst; a buffer that
+// the step writes takes the pads it does not write from the state.
+template <typename T>
+__global__ void k_adj_copy_pads(Grid2D g, const T *src, T *dst)
+{
+    using V = typename Vec<T>::type;
+    const int nxp = g.nx + 4;
+    const int nframe = 4 * nxp + 4 * g.ny;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nframe * 2 * g.ngrp) return;
+    const int q = (int)(t / nframe), f = (int)(t - (long)q * nframe);
+    int i, j;
+    if (f < 4 * nxp) {
+        const int r = f / nxp;
+        i = f - r * nxp;
+        j = r < 2 ? r : g.ny + r;          // padded rows 0, 1, ny + 2, ny + 3
+    } else {
+        const int u = f - 4 * nxp, cidx = u / g.ny;
+        j = 2 + (u - cidx * g.ny);
+        i = cidx < 2 ? cidx : g.nx + cidx; // padded columns 0, 1, nx + 2, nx + 3
+    }
+    const long o = (long)q * g.slab + (long)j * nxp + i;
+    reinterpret_cast<V *>(dst)[o] = reinterpret_cast<const V *>(src)[o];
 }
 
 AdjArgs adj_args(dvm_ctx *c, const AdjWork &w)
@@ -1450,6 +1486,10 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     const size_t partb = (size_t)c->S * 4 * c->nc * c->elem;
     const int nmax = c->nx > c->ny ? c->nx : c->ny;
     const int nseg = (nsteps + K - 1) / K;
+    const auto seglen = [&](int sgi) {
+        const int n0 = sgi * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
+        return n1 - n0;
+    };
     cudaError_t e = cudaSuccess;
 #define AC(call) do { e = (call); if (e != cudaSuccess) return cuda_fail(e, #call); } while (0)
     if (w.bytes_state != bytes || w.cap != c->list_cap) {
@@ -1502,9 +1542,64 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         if (rc != DVM_OK) return rc;
         w.cmaps.push_back(m);
     }
+    const bool rec = c->scheme == DVM_MUSCL;
+    const size_t bitsb = (size_t)c->ngrp * bits_slab(c) * sizeof(uint32_t);
+    // kept segments: the last nkeep of the run, whose tapes the forward run
+    // writes within the budget of dvm_set_adjoint_tape (and the device's free
+    // memory less a margin); a failed allocation keeps fewer
+    int nkeep = 0;
+    if (K > 1 && c->adj_tape > 0) {
+        const size_t kseg = (size_t)(K - 1) * (bytes + partb + (rec ? bitsb : 0));
+        size_t fr = 0, tot = 0;
+        AC(cudaMemGetInfo(&fr, &tot));
+        const size_t have = (size_t)w.ktape.size() / (K - 1) * kseg;      // already held
+        const size_t margin = (size_t)4 << 30;
+        const size_t avail = fr + have > margin ? fr + have - margin : 0;
+        const size_t budget = c->adj_tape < avail ? c->adj_tape : avail;
+        nkeep = (int)(budget / kseg < (size_t)nseg ? budget / kseg : (size_t)nseg);
+    }
+    {
+        const size_t nslots = (size_t)nkeep * (K - 1);
+        while (w.ktape.size() > nslots) {          // fewer than before: free the rest
+            cudaFree(w.ktape.back()); cudaFree(w.kptape.back());
+            w.ktape.pop_back(); w.kptape.pop_back(); w.kmaps.pop_back();
+            if (!w.kbits.empty()) { cudaFree(w.kbits.back()); w.kbits.pop_back(); w.kbmaps.pop_back(); }
+        }
+        while (w.ktape.size() < nslots) {
+            void *p = nullptr, *q = nullptr;
+            uint32_t *b = nullptr;
+            if (cudaMalloc(&p, bytes) != cudaSuccess || cudaMalloc(&q, partb) != cudaSuccess ||
+                (rec && cudaMalloc(&b, bitsb) != cudaSuccess)) {
+                cudaGetLastError();
+                cudaFree(p); cudaFree(q); cudaFree(b);
+                break;
+            }
+            CUtensorMap m;
+            int rc = encode_tensor_map2d(c, p, &m);
+            if (rc != DVM_OK) { cudaFree(p); cudaFree(q); cudaFree(b); return rc; }
+            w.ktape.push_back(p);
+            w.kptape.push_back(q);
+            w.kmaps.push_back(m);
+            if (rec) {
+                AC(cudaMemsetAsync(b, 0, bitsb, c->stream));
+                CUtensorMap bm;
+                rc = encode_bits_map2d(c, b, &bm);
+                if (rc != DVM_OK) { cudaFree(b); return rc; }
+                w.kbits.push_back(b);
+                w.kbmaps.push_back(bm);
+            }
+        }
+        nkeep = K > 1 ? (int)(w.ktape.size() / (K - 1)) : 0;
+    }
+    const int first_kept = nseg - nkeep;
+    // segment sgi's tape is kept (its interior slots come from the forward run)
+    const auto kept = [&](int sgi) { return sgi >= first_kept && seglen(sgi) > 1; };
+    const auto kidx = [&](int sgi, int t) { return (size_t)(sgi - first_kept) * (K - 1) + (t - 1); };
+    bool recompute_any = false;
+    for (int sgi = 0; sgi < first_kept; ++sgi) recompute_any = recompute_any || seglen(sgi) > 1;
     // two tape sets: the recomputation of one segment fills one while the
     // reverse sweep reads the other
-    while ((int)w.tape.size() < 2 * K) {
+    while (recompute_any && (int)w.tape.size() < 2 * K) {
         void *p = nullptr, *q = nullptr;
         AC(cudaMalloc(&p, bytes));
         AC(cudaMalloc(&q, partb));
@@ -1518,12 +1613,10 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     // limiter branches of the tape states (MUSCL): one buffer per tape slot but
     // the last, whose branches the checkpointed forward run records once per
     // segment; pad words that no cell writes stay 0
-    const bool rec = c->scheme == DVM_MUSCL;
-    const size_t bitsb = (size_t)c->ngrp * bits_slab(c) * sizeof(uint32_t);
     for (int pass = 0; pass < 2 && rec; ++pass) {
         std::vector<uint32_t *> &v = pass ? w.sbits : w.tbits;
         std::vector<CUtensorMap> &mv = pass ? w.sbmap : w.tbmap;
-        const int want = pass ? nseg : 2 * (K - 1);
+        const int want = pass ? nseg : (recompute_any ? 2 * (K - 1) : 0);
         while ((int)v.size() < want) {
             uint32_t *p = nullptr;
             AC(cudaMalloc(&p, bitsb));
@@ -1536,8 +1629,16 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         }
     }
     // the tape buffers take the boundary padding (Maxwellian ghosts) of the state
-    for (int t = 0; t < K; ++t)
-        AC(cudaMemcpyAsync(w.tape[t], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (recompute_any)
+        for (int t = 0; t < K; ++t)
+            AC(cudaMemcpyAsync(w.tape[t], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    {
+        const Grid2D g = grid2d(c);
+        const long nf = (long)(4 * (c->nx + 4) + 4 * c->ny) * 2 * c->ngrp;
+        for (size_t u = 0; u < w.ktape.size(); ++u)
+            k_adj_copy_pads<T><<<nba(nf, 256), 256, 0, c->stream>>>(g, (const T *)c->f[c->cur], (T *)w.ktape[u]);
+        AC(cudaGetLastError());
+    }
     AC(cudaMemsetAsync(w.gbc, 0, sizeof(double) * 5 * 4 * nmax, c->stream));
     AC(cudaMemsetAsync(w.gtw, 0, sizeof(double) * c->list_cap, c->stream));
     {
@@ -1577,17 +1678,46 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     for (int q = 0; q < 3; ++q) AC(cudaEventCreate(&ev[q]));
     const bool fuse0 = c->need_fusion;
     const long long steps0 = c->steps_done;
+    void *f_orig[2] = {c->f[0], c->f[1]}, *p_orig[2] = {c->part[0], c->part[1]};
+    const CUtensorMap tm_orig[2] = {c->tmap[0], c->tmap[1]};
     AC(cudaEventRecord(ev[0], c->stream));
-    // forward with checkpoints every K steps
+    // forward with checkpoints every K steps; a kept segment's steps write its
+    // tape (step t of the segment reads slot t, slot 0 being the live state,
+    // and writes slot t + 1; its last step writes the other live buffer) and
+    // record their limiter branches
     for (int n = 0; n < nsteps; ++n) {
-        if (n % K == 0) {
-            AC(cudaMemcpyAsync(w.ckpt[n / K], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
-            AC(cudaMemcpyAsync(w.ckpt_part[n / K], c->part[c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
+        const int sgi = n / K, t = n % K, len = seglen(sgi);
+        if (t == 0) {
+            AC(cudaMemcpyAsync(w.ckpt[sgi], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+            AC(cudaMemcpyAsync(w.ckpt_part[sgi], c->part[c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
         }
+        const bool last = t == len - 1;
         // the last step of each segment records its limiter branches
-        if (rec && (n % K == K - 1 || n == nsteps - 1)) c->rec_bits = w.sbits[n / K];
+        if (rec && last) c->rec_bits = w.sbits[sgi];
+        if (!kept(sgi)) {
+            const cudaError_t es = step2d(c);
+            c->rec_bits = nullptr;
+            AC(es);
+            continue;
+        }
+        const int L = c->cur;
+        if (t > 0) {
+            c->f[L] = w.ktape[kidx(sgi, t)];
+            c->part[L] = w.kptape[kidx(sgi, t)];
+            c->tmap[L] = w.kmaps[kidx(sgi, t)];
+        }
+        if (!last) {
+            c->f[1 - L] = w.ktape[kidx(sgi, t + 1)];
+            c->part[1 - L] = w.kptape[kidx(sgi, t + 1)];
+            c->tmap[1 - L] = w.kmaps[kidx(sgi, t + 1)];
+            if (rec) c->rec_bits = w.kbits[kidx(sgi, t + 1)];
+        }
         const cudaError_t es = step2d(c);
         c->rec_bits = nullptr;
+        c->f[0] = f_orig[0]; c->f[1] = f_orig[1];
+        c->part[0] = p_orig[0]; c->part[1] = p_orig[1];
+        c->tmap[0] = tm_orig[0]; c->tmap[1] = tm_orig[1];
+        if (!last) c->cur = L;      // the state is in the tape, the live buffers keep their parity
         AC(es);
     }
     AC(cudaEventRecord(ev[1], c->stream));
@@ -1621,22 +1751,21 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
                                                                                          (const T *)c->d_pub, lamA);
     }
     // reverse sweep, segment by segment: recompute the segment onto the tape
-    // (each step writes the next tape buffer), then apply the transposed steps
-    // backwards
-    void *f_orig[2] = {c->f[0], c->f[1]}, *p_orig[2] = {c->part[0], c->part[1]};
-    const CUtensorMap tm_orig[2] = {c->tmap[0], c->tmap[1]};
+    // (each step writes the next tape buffer) unless the forward run kept it,
+    // then apply the transposed steps backwards
     const int cur_orig = c->cur;
     cudaStream_t main_stream = c->stream;
     // tape slot 0 of segment sgi is its checkpoint; slot t > 0 is slot t of
-    // tape set sgi % 2; step t writes slot t + 1 (state and partial moments)
-    const auto fslot = [&](int sgi, int t) { return t == 0 ? w.ckpt[sgi] : w.tape[(sgi & 1) * K + t]; };
-    const auto pslot = [&](int sgi, int t) { return t == 0 ? w.ckpt_part[sgi] : w.ptape[(sgi & 1) * K + t]; };
+    // the kept tape or of tape set sgi % 2; step t writes slot t + 1 (state
+    // and partial moments)
+    const auto fslot = [&](int sgi, int t) {
+        return t == 0 ? w.ckpt[sgi] : (kept(sgi) ? w.ktape[kidx(sgi, t)] : w.tape[(sgi & 1) * K + t]);
+    };
+    const auto pslot = [&](int sgi, int t) {
+        return t == 0 ? w.ckpt_part[sgi] : (kept(sgi) ? w.kptape[kidx(sgi, t)] : w.ptape[(sgi & 1) * K + t]);
+    };
     const auto mslot = [&](int sgi, int t) { return t == 0 ? w.cmaps[sgi] : w.tmaps[(sgi & 1) * K + t]; };
     const auto bslot = [&](int sgi, int t) { return (sgi & 1) * (K - 1) + t; };
-    const auto seglen = [&](int sgi) {
-        const int n0 = sgi * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
-        return n1 - n0;
-    };
     bool used[2] = {false, false};
     // recomputation of segment sgi on the recomputation stream
     const auto recompute = [&](int sgi) -> cudaError_t {
@@ -1670,20 +1799,31 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     };
     // the checkpoints are written by the forward run on the main stream
     AC(cudaStreamWaitEvent(w.rstream, ev[1], 0));
-    AC(recompute(nseg - 1));
+    // a kept first segment linearises around the fused initial state as well
+    if (fuse0 && kept(0)) AC(fusion2d(c, fslot(0, 0), pslot(0, 0)));
+    if (!kept(nseg - 1)) AC(recompute(nseg - 1));
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int set = sgi & 1, len = seglen(sgi);
-        if (sgi > 0) AC(recompute(sgi - 1));           // the next segment, while this one is swept
-        AC(cudaStreamWaitEvent(c->stream, w.ev_rec[set], 0));
+        const bool kp = kept(sgi);
+        if (sgi > 0 && !kept(sgi - 1)) AC(recompute(sgi - 1));   // the next segment, while this one is swept
+        if (!kp) AC(cudaStreamWaitEvent(c->stream, w.ev_rec[set], 0));
         for (int t = len - 1; t >= 0; --t) {
-            const CUtensorMap *bm = !rec ? nullptr : (t == len - 1 ? &w.sbmap[sgi] : &w.tbmap[bslot(sgi, t)]);
-            const uint32_t *bits = !rec ? nullptr : (t == len - 1 ? w.sbits[sgi] : w.tbits[bslot(sgi, t)]);
+            // the branches of step t: recorded by the forward run for the last
+            // step and for every step of a kept segment (step t wrote slot t + 1)
+            const CUtensorMap *bm = !rec ? nullptr
+                                         : (t == len - 1 ? &w.sbmap[sgi]
+                                                         : (kp ? &w.kbmaps[kidx(sgi, t + 1)] : &w.tbmap[bslot(sgi, t)]));
+            const uint32_t *bits = !rec ? nullptr
+                                        : (t == len - 1 ? w.sbits[sgi]
+                                                        : (kp ? w.kbits[kidx(sgi, t + 1)] : w.tbits[bslot(sgi, t)]));
             AC(adjoint_step<T>(c, w, (const T *)fslot(sgi, t), (const T *)pslot(sgi, t), bits, bm, lin,
                                (T *)w.lam[1 - lin]));
             lin = 1 - lin;
         }
-        AC(cudaEventRecord(w.ev_used[set], c->stream));
-        used[set] = true;
+        if (!kp) {
+            AC(cudaEventRecord(w.ev_used[set], c->stream));
+            used[set] = true;
+        }
     }
     AC(cudaEventRecord(ev[2], c->stream));
     // J and dJ/dT_w per sector: ordered sums over the wall list on the host

@@ -943,6 +943,13 @@ int dvm_set_time_scheme(dvm_ctx *c, int scheme)
     return DVM_OK;
 }
 
+int dvm_set_adjoint_tape(dvm_ctx *c, size_t max_bytes)
+{
+    if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    c->adj_tape = max_bytes;
+    return DVM_OK;
+}
+
 int dvm_set_collision_model(dvm_ctx *c, int model, double Pr)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }

@@ -176,6 +176,7 @@ struct dvm_ctx {
     double *d_prim0;              // primitives of the last dvm_init_maxwellian (nc * 5)
     bool have_prim0;
     void *adj;                    // adjoint workspace (dvm_adjoint2d.cu)
+    size_t adj_tape;              // device bytes the adjoint may keep of the forward run's tape (dvm_set_adjoint_tape)
     uint32_t *rec_bits;           // if set, the 2D MUSCL bulk kernel records its limiter branches here
     bool have_state, have_geo, need_fusion, moving;
     int timing;                   // dvm_timing: 0 off, 1 the bulk kernel, 2 the Shakhov kernel

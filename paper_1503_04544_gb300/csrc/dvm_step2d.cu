@@ -478,11 +478,9 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
             nkuq = -(kqx * ux + kqy * uy);
         }
         // log2 M(v) = el0 + e1x vx + e1y vy - c2 |v|^2 (packed path)
-        if (!REC) {
-            el0 = log2(A) - c2 * (ux * ux + uy * uy);
-            e1x = T(2) * c2 * ux;
-            e1y = T(2) * c2 * uy;
-        }
+        el0 = log2(A) - c2 * (ux * ux + uy * uy);
+        e1x = T(2) * c2 * ux;
+        e1y = T(2) * c2 * uy;
     }
     const int mask = fl >> kMaskShift;
     // limiter weights of the faces x-, x+, y-, y+ (1/2 where the limited
@@ -504,7 +502,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
     if (sizeof(T) == 8 && plain) Qm = dexp2(T(-2) * c2 * T(g.dvx) * T(g.dvx));
     // the exponent's per-cell terms as pairs (packed path)
     F2 EL0, E1X, E1Y, NC2;
-    if constexpr (sizeof(T) == 4 && MUSCL && !REC) {
+    if constexpr (sizeof(T) == 4 && MUSCL) {
         EL0 = f2(el0); E1X = f2(e1x); E1Y = f2(e1y); NC2 = f2(-2.f * c2);
     }
     Acc<T> m0, m1, m2, m3;
@@ -563,17 +561,7 @@ __global__ void __launch_bounds__(32 * kRows, 2) k_bulk(BulkArgs<T> a, const __g
                     F2 fq[2], fg[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        if (REC) {          // the recording variant keeps fewer per-cell registers
-                            float pvx[2], pvy[2], fe[2];
-                            f2_get(P.vx[h], pvx[0], pvx[1]);
-                            f2_get(P.vy[h], pvy[0], pvy[1]);
-#pragma unroll
-                            for (int l = 0; l < 2; ++l) {
-                                const T dx = pvx[l] - ux, dy = pvy[l] - uy;
-                                fe[l] = A * dexp2(-(dx * dx + dy * dy) * c2);
-                            }
-                            fq[h] = f2(fe[0], fe[1]);
-                        } else {
+                        {
                             // log2 M = el0 - 2 c2 |v|^2/2 + e1x vx + e1y vy
                             F2 X = fma2(NC2, P.ke[h], EL0);
                             X = fma2(E1X, P.vx[h], X);

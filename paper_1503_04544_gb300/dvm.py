@@ -82,6 +82,7 @@ SIGNATURES = {
     "dvm_load": [_P, C.c_char_p],
     "dvm_set_time_scheme": [_P, C.c_int],
     "dvm_set_collision_model": [_P, C.c_int, C.c_double],
+    "dvm_set_adjoint_tape": [_P, C.c_size_t],
     "dvm_set_equilibrium": [_P, C.c_int],
     "dvm_check": [_P],
     "dvm_moments": [_P, _P, _P, _P, _P, _P, C.c_int],
@@ -259,6 +260,12 @@ class Solver:
     def set_time_scheme(self, scheme: int):
         """0: explicit (Eq. ExSchemeDD), 1: first-order semi-implicit (Eq. ImpSchemeDD)."""
         _check(load().dvm_set_time_scheme(self.h, int(scheme)))
+
+    def set_adjoint_tape(self, max_bytes: int):
+        """Device bytes the adjoint may use to keep the forward run's tape of
+        whole checkpoint segments, so that the reverse sweep does not
+        recompute them (0, the default: recompute every segment)."""
+        _check(load().dvm_set_adjoint_tape(self.h, int(max_bytes)))
 
     def set_collision_model(self, model: int, Pr: float = 1.0):
         """0: BGK (Eq. BGKDD), 1: Shakhov with Prandtl number Pr (Eq. ShakhovDD)."""
