@@ -200,6 +200,30 @@ __device__ __forceinline__ void minmod_pair(double b, double a, double c, double
     mi = minmod3(a, c);
 }
 
+// min(|a|, |b|) with the sign bit sign(a) XOR sign(b): non-negative exactly
+// when a and b have the same sign (one instruction on sm_86 and later).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b)
+{
+    float r;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// x with its sign flipped where s is negative (one bit operation).
+__device__ __forceinline__ float xorsign(float x, float s)
+{
+    return __int_as_float(__float_as_int(x) ^ (__float_as_int(s) & (int)0x80000000));
+}
+
+// Magnitudes of the two limiter values of minmod_pair: |minmod(b, a)| =
+// max(min_xorsign_abs(b, a), 0) and |minmod(a, c)| likewise.  Both limiter
+// values, where not zero, have the sign of a.
+__device__ __forceinline__ void minmod_mag_pair(float b, float a, float c, float &mo, float &mi)
+{
+    mo = fmaxf(min_xorsign_abs(b, a), 0.f);
+    mi = fmaxf(min_xorsign_abs(a, c), 0.f);
+}
+
 // 2^x by the hardware approximation (relative error a few ulp; results below
 // the smallest normal number flush to 0).
 __device__ __forceinline__ float ex2_fast(float x)

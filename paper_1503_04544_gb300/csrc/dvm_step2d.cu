@@ -190,9 +190,9 @@ __device__ __forceinline__ void bulk_tile(const typename Vec<T>::type *t, int c0
 // coefficient pairs -nux, -nuy, 1 - nux, 1 - nuy, vx, vy, |v|^2/2.
 struct PairCoef { F2 nnx[2], nny[2], onx[2], ony[2], vx[2], vy[2], ke[2]; };
 
-// Branch code of a minmod value m that is one of its arguments or 0 (b: the
-// second argument): 0 for zero, 2 for b (also on a tie), else 1.
-__device__ __forceinline__ uint32_t bcode(float m, float b) { return m == 0.f ? 0u : (m == b ? 2u : 1u); }
+// Branch code of a minmod value of magnitude m (b: its second argument): 0
+// for zero, 2 for b (also on a tie), else 1.
+__device__ __forceinline__ uint32_t bcode(float m, float b) { return m == 0.f ? 0u : (m == fabsf(b) ? 2u : 1u); }
 
 template <int COMP, bool REC>
 __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, int uy1, const PairCoef &P,
@@ -219,22 +219,28 @@ __device__ __forceinline__ void bulk_tile_x2(const float4 *t, int c0, int ux1, i
         const F2 AX = sub2(F, U1), AY = sub2(F, W1);
         const F2 BX = sub2(f2(d1[a0], d1[a1]), F), BY = sub2(f2(e1[a0], e1[a1]), F);
         const F2 CX = sub2(U1, f2(u2[a0], u2[a1])), CY = sub2(W1, f2(w2[a0], w2[a1]));
+        // the limited terms cxo mo - cxi mi from the magnitudes of the two
+        // limiter values, which (where not zero) share the sign of a: the same
+        // numbers as from the signed values, in fewer scalar min/max
         float ax[2], ay[2], bx[2], by[2], cx[2], cy[2], mxo[2], mxi[2], myo[2], myi[2];
         f2_get(AX, ax[0], ax[1]); f2_get(AY, ay[0], ay[1]);
         f2_get(BX, bx[0], bx[1]); f2_get(BY, by[0], by[1]);
         f2_get(CX, cx[0], cx[1]); f2_get(CY, cy[0], cy[1]);
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-            minmod_pair(bx[l], ax[l], cx[l], mxo[l], mxi[l]);
-            minmod_pair(by[l], ay[l], cy[l], myo[l], myi[l]);
+            minmod_mag_pair(bx[l], ax[l], cx[l], mxo[l], mxi[l]);
+            minmod_mag_pair(by[l], ay[l], cy[l], myo[l], myi[l]);
             if (REC) {
                 const int e = 2 * h + l;
                 lo |= bcode(mxo[l], ax[l]) << (((COMP * 2 + 0) * 4 + e) * 2);
                 lo |= bcode(myo[l], ay[l]) << (((COMP * 2 + 1) * 4 + e) * 2);
             }
         }
-        const F2 TX = fma2(NCXI, f2(mxi[0], mxi[1]), mul2(CXO, f2(mxo[0], mxo[1])));
-        const F2 TY = fma2(NCYI, f2(myi[0], myi[1]), mul2(CYO, f2(myo[0], myo[1])));
+        float tx[2], ty[2];
+        f2_get(fma2(NCXI, f2(mxi[0], mxi[1]), mul2(CXO, f2(mxo[0], mxo[1]))), tx[0], tx[1]);
+        f2_get(fma2(NCYI, f2(myi[0], myi[1]), mul2(CYO, f2(myo[0], myo[1]))), ty[0], ty[1]);
+        const F2 TX = f2(xorsign(tx[0], ax[0]), xorsign(tx[1], ax[1]));
+        const F2 TY = f2(xorsign(ty[0], ay[0]), xorsign(ty[1], ay[1]));
         const F2 DFX = fma2(P.onx[h], TX, AX), DFY = fma2(P.ony[h], TY, AY);
         F2 O = fma2(P.nnx[h], DFX, F);
         O = fma2(P.nny[h], DFY, O);
