@@ -162,6 +162,29 @@ __device__ __forceinline__ T minmod3(T a, T b)
     return fmax(fmin(a, b), fmin(fmax(a, b), T(0)));
 }
 
+// min(|a|, |b|) with the sign bit sign(a) XOR sign(b): non-negative exactly
+// when a and b have the same sign (one instruction on sm_86 and later).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b)
+{
+    float r;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// x with its sign flipped where s is negative (one bit operation).
+__device__ __forceinline__ float xorsign(float x, float s)
+{
+    return __int_as_float(__float_as_int(x) ^ (__float_as_int(s) & (int)0x80000000));
+}
+
+// FP32: the magnitude max(min_xorsign_abs(a, b), 0) with the sign of a,
+// which is the sign of the result where it is not zero (three operations;
+// the same number, up to the sign of a zero).
+__device__ __forceinline__ float minmod3(float a, float b)
+{
+    return xorsign(fmaxf(min_xorsign_abs(a, b), 0.f), a);
+}
+
 // The same for FP64 with integer operations on the bit patterns: the
 // magnitudes of IEEE-754 doubles order as their bits without the sign, and
 // the result is one of the arguments or zero, so it is exact (a zero result
@@ -176,43 +199,19 @@ __device__ __forceinline__ double minmod3(double a, double b)
     return (ia ^ ib) < 0 ? 0.0 : __longlong_as_double(r);
 }
 
-// Three-input minimum (one instruction on sm_100 and later).
-__device__ __forceinline__ float fmin3(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
 // The two limiter values of one axis that share the difference a: the
-// downwind face minmod(b, a) and the upwind face minmod(a, c), with
-// minmod(x, y) = median(x, y, 0) = min(max(x, y), max(x, 0), max(y, 0))
-// (exact: the median is one of its arguments); max(a, 0) serves both.
+// downwind face minmod(b, a) and the upwind face minmod(a, c) (exact: each
+// is one of its arguments or zero).
 __device__ __forceinline__ void minmod_pair(float b, float a, float c, float &mo, float &mi)
 {
-    const float za = fmaxf(a, 0.f);
-    mo = fmin3(fmaxf(b, a), fmaxf(b, 0.f), za);
-    mi = fmin3(fmaxf(a, c), za, fmaxf(c, 0.f));
+    // magnitudes (see minmod_mag_pair); both values carry the sign of a
+    mo = xorsign(fmaxf(min_xorsign_abs(b, a), 0.f), a);
+    mi = xorsign(fmaxf(min_xorsign_abs(a, c), 0.f), a);
 }
 __device__ __forceinline__ void minmod_pair(double b, double a, double c, double &mo, double &mi)
 {
     mo = minmod3(b, a);
     mi = minmod3(a, c);
-}
-
-// min(|a|, |b|) with the sign bit sign(a) XOR sign(b): non-negative exactly
-// when a and b have the same sign (one instruction on sm_86 and later).
-__device__ __forceinline__ float min_xorsign_abs(float a, float b)
-{
-    float r;
-    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
-    return r;
-}
-
-// x with its sign flipped where s is negative (one bit operation).
-__device__ __forceinline__ float xorsign(float x, float s)
-{
-    return __int_as_float(__float_as_int(x) ^ (__float_as_int(s) & (int)0x80000000));
 }
 
 // Magnitudes of the two limiter values of minmod_pair: |minmod(b, a)| =
