@@ -1395,7 +1395,10 @@ __device__ __forceinline__ double exp2_relax(double x) { return exp2(x); }
 // a first pass over the cell's velocities sums q_T, the second relaxes
 // towards f_S = M [1 + k c.q (|c|^2/T - 4)], g_S = T/2 M [1 + k c.q (|c|^2/T - 2)],
 // k = (1 - Pr) / (5 rho T^2).
-template <typename T, bool SHAK>
+// CONS: the equilibrium from the conservative parameters eqp (Sec. 3.1), a
+// variant of its own so that the plain one keeps its registers (the pass is
+// bound by memory latency, and 64 registers give four blocks per SM).
+template <typename T, bool SHAK, bool CONS>
 __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_tau0, T *f, const VCoef<T> *vt,
                                                           T *part, const int8_t *type, const T *eqp, T Pr, int *err)
 {
@@ -1452,7 +1455,7 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_
     }
     if (gas) {
         const T nu = dt_tau0 * rho, inv = T(1) / (T(1) + nu);
-        if (eqp) {
+        if constexpr (CONS) {
             // conservative equilibrium of the transported state (Sec. 3.1)
             rho = eqp[cell]; ux = eqp[nc + cell]; uy = eqp[2 * nc + cell]; tmp = eqp[3 * nc + cell];
         }
@@ -1857,13 +1860,17 @@ cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
         // conservative equilibrium parameters of the transported state
         if (cons && (e = eqpar(c, pout, c->S)) != cudaSuccess) return e;
         if (c->model == DVM_SHAKHOV)
-            k_imex<T, true><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
-                                                           (const VCoef<T> *)c->vtab, pout, type1, nullptr, T(c->Pr),
-                                                           c->d_err);
+            k_imex<T, true, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
+                                                                  (const VCoef<T> *)c->vtab, pout, type1, nullptr,
+                                                                  T(c->Pr), c->d_err);
+        else if (cons)
+            k_imex<T, false, true><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
+                                                                  (const VCoef<T> *)c->vtab, pout, type1,
+                                                                  (const T *)c->eqp, T(1), c->d_err);
         else
-            k_imex<T, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
-                                                            (const VCoef<T> *)c->vtab, pout, type1,
-                                                            cons ? (const T *)c->eqp : nullptr, T(1), c->d_err);
+            k_imex<T, false, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
+                                                                   (const VCoef<T> *)c->vtab, pout, type1, nullptr,
+                                                                   T(1), c->d_err);
         c->launches += 1;
     }
     c->cur = 1 - c->cur;
