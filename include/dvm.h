@@ -372,7 +372,8 @@ int dvm_drag_adjoint(dvm_ctx *ctx, int nsteps, int checkpoint_every, double *J, 
  * free device memory less 4 GiB; buffers that cannot be allocated keep
  * fewer segments.  Results are those of the recomputing sweep (a step that
  * records its branches computes the same values as a plain step).  The
- * buffers stay allocated until a smaller budget or dvm_destroy.  Errors:
+ * buffers stay allocated for later calls; a smaller budget frees what it no
+ * longer allows at once, and dvm_destroy frees the rest.  Errors:
  * DVM_ERR_ARG (null context). */
 int dvm_set_adjoint_tape(dvm_ctx *ctx, size_t max_bytes);
 

@@ -1893,6 +1893,22 @@ int drag_adjoint2d(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
                                                         with_drag, seed, seed_dev, lam0, lam0_dev);
 }
 
+// The kept tape buffers beyond what max_bytes allows go now (the adjoint
+// call re-allocates what its budget needs).
+void trim_adjoint_tape2d(dvm_ctx *c, size_t max_bytes)
+{
+    if (!c->adj) return;
+    AdjWork &w = *static_cast<AdjWork *>(c->adj);
+    if (w.ktape.empty()) return;
+    const size_t per = w.bytes_state + (size_t)c->S * 4 * c->nc * c->elem +
+                       (w.kbits.empty() ? 0 : (size_t)c->ngrp * bits_slab(c) * sizeof(uint32_t));
+    while (!w.ktape.empty() && w.ktape.size() * per > max_bytes) {
+        cudaFree(w.ktape.back()); cudaFree(w.kptape.back());
+        w.ktape.pop_back(); w.kptape.pop_back(); w.kmaps.pop_back();
+        if (!w.kbits.empty()) { cudaFree(w.kbits.back()); w.kbits.pop_back(); w.kbmaps.pop_back(); }
+    }
+}
+
 void free_adjoint2d(dvm_ctx *c)
 {
     if (!c->adj) return;

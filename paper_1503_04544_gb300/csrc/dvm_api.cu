@@ -947,6 +947,7 @@ int dvm_set_adjoint_tape(dvm_ctx *c, size_t max_bytes)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
     c->adj_tape = max_bytes;
+    if (c->dim == 2) trim_adjoint_tape2d(c, max_bytes);
     return DVM_OK;
 }
 

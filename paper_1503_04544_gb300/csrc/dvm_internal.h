@@ -248,6 +248,7 @@ int drag_adjoint2d(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
                    double *ms_forward, double *ms_reverse, int with_drag, const void *seed, int seed_dev, void *lam0,
                    int lam0_dev);
 void free_adjoint2d(dvm_ctx *c);
+void trim_adjoint_tape2d(dvm_ctx *c, size_t max_bytes);   // frees kept tape buffers beyond max_bytes
 
 // 3D (dvm_geometry3d.cu, dvm_step3d.cu)
 dvm::Grid3D grid3d(const dvm_ctx *c);

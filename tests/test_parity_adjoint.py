@@ -297,3 +297,20 @@ def test_adjoint_kept_tape_matches_recomputation(scheme, prec):
         for k in ("gTw", "lambda0", "gprim0", "F"):
             a, b = np.asarray(g[k]), np.asarray(ref[k])
             assert np.abs(a - b).max() <= tol * np.abs(b).max(), k
+
+
+def test_adjoint_tape_budget_change_on_one_context():
+    """A context that kept its tape, then drops the budget to 0 (which frees
+    the kept buffers), gives the same gradient from the recomputing sweep."""
+    cfg = small(1)
+    s = dvm.Solver(cfg, dvm.FP64)
+    s.init_maxwellian()
+    s.set_adjoint_tape(1 << 40)
+    g1 = s.adjoint(12, 5, with_drag=True)
+    s.set_adjoint_tape(0)
+    s.init_maxwellian()
+    g0 = s.adjoint(12, 5, with_drag=True)
+    s.close()
+    assert g1["J"] == g0["J"]
+    assert np.abs(g1["lambda0"] - g0["lambda0"]).max() <= 1e-13 * np.abs(g0["lambda0"]).max()
+    assert np.abs(g1["gTw"] - g0["gTw"]).max() <= 1e-13 * np.abs(g0["gTw"]).max()
