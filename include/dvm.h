@@ -256,9 +256,9 @@ int dvm_moments(dvm_ctx *ctx, double *rho, double *ux, double *uy, double *uz, d
 
 /* Velocity split (Sec. 5.2, "velocity parallelization"): each rank holds
  * every cell for a slab of the velocity grid, transports and relaxes its own
- * velocities, and the ranks exchange one sum per step.  2D and 3D, explicit
- * scheme, BGK (direct or conservative equilibrium), fixed or (2D) rotating
- * obstacle.
+ * velocities, and the ranks exchange one sum per step (two with the
+ * semi-implicit scheme).  2D and 3D, explicit or semi-implicit scheme, BGK
+ * (direct or conservative equilibrium), fixed or (2D) rotating obstacle.
  *
  * dvm_set_velocity_split declares that this context's velocity grid (given
  * to dvm_create) is the rows [k0, k0 + n) of the last axis (v_y in 2D, v_z in
@@ -285,14 +285,28 @@ int dvm_moments(dvm_ctx *ctx, double *rho, double *ux, double *uy, double *uz, d
  *   dvm_split_finish(ctx, xbuf)  finishes the step from the summed xbuf:
  *       wall density, force, torque and rotation (identical on every rank),
  *       fluxes, relaxation and the control volumes of this rank's velocities.
- * Both calls are asynchronous; dvm_check reads the error flags.  The ranks
- * must hold the same problem (grid, body, boundaries) and step in lockstep.
- * Errors: DVM_ERR_ARG (not a slab, null buffer), DVM_ERR_STATE (order),
- * DVM_ERR_UNSUPPORTED (semi-implicit, Shakhov), DVM_ERR_CUDA. */
+ * With the semi-implicit scheme (Eq. ImpSchemeDD) the relaxation needs the
+ * moments of the transported values over every velocity, so the step has a
+ * second exchange:
+ *   dvm_split_finish(ctx, xbuf)  transports (fluxes and control volumes, no
+ *       relaxation) and writes this rank's moment sums of the transported
+ *       values to xbuf ([D + 2][ncell], as in dvm_split_begin);
+ *   the caller sums xbuf over the ranks again;
+ *   dvm_split_relax(ctx, xbuf)  relaxes this rank's velocities towards the
+ *       equilibrium of the summed moments (conservative parameters included)
+ *       and ends the step.
+ * The calls are asynchronous; dvm_check reads the error flags.  The ranks
+ * must hold the same problem (grid, body, boundaries, time scheme) and step
+ * in lockstep.  Between the calls of one step, dvm_set_state,
+ * dvm_init_maxwellian, dvm_load, dvm_set_body, dvm_set_time_scheme and
+ * dvm_set_equilibrium return DVM_ERR_STATE.  Errors: DVM_ERR_ARG (not a slab,
+ * null buffer), DVM_ERR_STATE (order), DVM_ERR_UNSUPPORTED (Shakhov),
+ * DVM_ERR_CUDA. */
 int dvm_set_velocity_split(dvm_ctx *ctx, const dvm_vgrid *global);
 int dvm_split_size(dvm_ctx *ctx, size_t *count);
 int dvm_split_begin(dvm_ctx *ctx, void *xbuf);
 int dvm_split_finish(dvm_ctx *ctx, void *xbuf);
+int dvm_split_relax(dvm_ctx *ctx, void *xbuf);
 
 /* Force (F[0..2]) and torque about the z axis exerted by the gas on the body
  * at the start of the last step (Eqs. eq-force, eq-torque), FP64. */

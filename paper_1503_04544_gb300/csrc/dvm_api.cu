@@ -582,9 +582,19 @@ static int set_body3d(dvm_ctx *c, const dvm_body *b)
     return check_flags(c);
 }
 
+// A velocity-split step between its calls (dvm_split_begin ... finish, or
+// finish ... relax): the state, the body and the scheme must not change.
+static bool split_step_open(dvm_ctx *c, const char *fn)
+{
+    if (!c->split_begun && !c->split_relax) return false;
+    set_error(std::string(fn) + ": a velocity-split step is in progress");
+    return true;
+}
+
 int dvm_set_body(dvm_ctx *c, const dvm_body *b)
 {
     if (!c || !b) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (split_step_open(c, "dvm_set_body")) return DVM_ERR_STATE;
     if (c->dim == 3) return set_body3d(c, b);
     if (b->shape != DVM_SHAPE_NONE && b->shape != DVM_SHAPE_CIRCLE && b->shape != DVM_SHAPE_ELLIPSE) {
         set_error("2D shapes: none, circle, ellipse"); return DVM_ERR_UNSUPPORTED;
@@ -667,6 +677,7 @@ int dvm_init_maxwellian(dvm_ctx *c, const double *rho, const double *ux, const d
                         const double *uz, const double *T)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (split_step_open(c, "dvm_init_maxwellian")) return DVM_ERR_STATE;
     const size_t nc = (size_t)c->nc;
     std::vector<double> prim(5 * nc);
     for (size_t k = 0; k < nc; ++k) {
@@ -700,6 +711,7 @@ static int ensure_pub(dvm_ctx *c)
 int dvm_set_state(dvm_ctx *c, const void *f, size_t bytes, int on_device)
 {
     if (!c || !f) { set_error("null"); return DVM_ERR_ARG; }
+    if (split_step_open(c, "dvm_set_state")) return DVM_ERR_STATE;
     if (bytes != c->state_elems * c->elem) { set_error("state size mismatch"); return DVM_ERR_ARG; }
     int rc = ensure_pub(c);
     if (rc != DVM_OK) return rc;
@@ -845,6 +857,7 @@ int dvm_save(dvm_ctx *c, const char *path)
 int dvm_load(dvm_ctx *c, const char *path)
 {
     if (!c || !path) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (split_step_open(c, "dvm_load")) return DVM_ERR_STATE;
     FILE *fp = std::fopen(path, "rb");
     if (!fp) { set_error(std::string("dvm_load: cannot open ") + path); return DVM_ERR_ARG; }
     uint64_t mine = 0;
@@ -935,10 +948,7 @@ int dvm_set_time_scheme(dvm_ctx *c, int scheme)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
     if (scheme != DVM_EXPLICIT && scheme != DVM_IMEX) { set_error("time scheme must be DVM_EXPLICIT or DVM_IMEX"); return DVM_ERR_ARG; }
-    if (scheme == DVM_IMEX && c->split) {
-        set_error("velocity split: the explicit scheme only");
-        return DVM_ERR_UNSUPPORTED;
-    }
+    if (split_step_open(c, "dvm_set_time_scheme")) return DVM_ERR_STATE;
     c->time_scheme = scheme;
     return DVM_OK;
 }
@@ -981,6 +991,7 @@ int dvm_set_collision_model(dvm_ctx *c, int model, double Pr)
 int dvm_set_equilibrium(dvm_ctx *c, int mode)
 {
     if (!c) { set_error("null"); return DVM_ERR_ARG; }
+    if (split_step_open(c, "dvm_set_equilibrium")) return DVM_ERR_STATE;
     if (mode != DVM_EQ_DIRECT && mode != DVM_EQ_CONSERVATIVE) {
         set_error("equilibrium mode must be DVM_EQ_DIRECT or DVM_EQ_CONSERVATIVE");
         return DVM_ERR_ARG;
@@ -1195,8 +1206,8 @@ int dvm_set_velocity_split(dvm_ctx *c, const dvm_vgrid *gv)
         set_error("velocity split: set it right after dvm_create, before the body and the state");
         return DVM_ERR_STATE;
     }
-    if (c->time_scheme != DVM_EXPLICIT || c->model != DVM_BGK) {
-        set_error("velocity split: the explicit scheme and the BGK model only");
+    if (c->model != DVM_BGK) {
+        set_error("velocity split: the BGK model only");
         return DVM_ERR_UNSUPPORTED;
     }
     const bool d3 = c->dim == 3;
@@ -1270,7 +1281,10 @@ int dvm_split_begin(dvm_ctx *c, void *xbuf)
     if (!c || !xbuf) { set_error("null argument"); return DVM_ERR_ARG; }
     if (!c->split) { set_error("dvm_split_begin: no velocity split set"); return DVM_ERR_STATE; }
     if (!c->have_state) { set_error("no state: call dvm_init_maxwellian or dvm_set_state"); return DVM_ERR_STATE; }
-    if (c->split_begun) { set_error("dvm_split_begin: the previous step is not finished"); return DVM_ERR_STATE; }
+    if (c->split_begun || c->split_relax) {
+        set_error("dvm_split_begin: the previous step is not finished");
+        return DVM_ERR_STATE;
+    }
     for (int d = 0; d < c->dim; ++d)
         if ((c->bc[2 * d] == DVM_BC_PERIODIC) != (c->bc[2 * d + 1] == DVM_BC_PERIODIC)) {
             set_error("opposite sides must both be periodic or both not");
@@ -1288,7 +1302,22 @@ int dvm_split_finish(dvm_ctx *c, void *xbuf)
     if (!c->split || !c->split_begun) { set_error("dvm_split_finish: no dvm_split_begin pending"); return DVM_ERR_STATE; }
     cudaError_t e = c->dim == 2 ? split_step2d(c, 2, xbuf) : split_step3d(c, 2, xbuf);
     c->split_begun = false;
+    // the semi-implicit step waits for the second exchange
+    c->split_relax = e == cudaSuccess && c->time_scheme == DVM_IMEX;
     if (e != cudaSuccess) return cuda_fail(e, "dvm_split_finish");
+    return DVM_OK;
+}
+
+int dvm_split_relax(dvm_ctx *c, void *xbuf)
+{
+    if (!c || !xbuf) { set_error("null argument"); return DVM_ERR_ARG; }
+    if (!c->split || !c->split_relax) {
+        set_error("dvm_split_relax: no semi-implicit dvm_split_finish pending");
+        return DVM_ERR_STATE;
+    }
+    cudaError_t e = c->dim == 2 ? split_step2d(c, 3, xbuf) : split_step3d(c, 3, xbuf);
+    c->split_relax = false;
+    if (e != cudaSuccess) return cuda_fail(e, "dvm_split_relax");
     return DVM_OK;
 }
 

@@ -191,6 +191,7 @@ struct dvm_ctx {
     double gv0[3], gdv[3];        //   (this context's own grid unless a velocity split is set)
     bool split;                   // dvm_set_velocity_split: steps through dvm_split_begin / _finish
     bool split_begun;             // dvm_split_begin done, dvm_split_finish pending
+    bool split_relax;             // semi-implicit split step: transported, waiting for dvm_split_relax
     void *split_in;               // [4 or 5][nc] summed moment sums in the state precision (velocity split)
     void *qheat;                  // [D][nc] heat flux of each cell's control volume at t^n (Shakhov, state precision)
     void *hpart[2];               // 2D Shakhov, paired with part[]: raw heat-flux moments [S][5][nc] of the state

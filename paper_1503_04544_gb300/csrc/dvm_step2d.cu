@@ -1395,12 +1395,16 @@ __device__ __forceinline__ double exp2_relax(double x) { return exp2(x); }
 // a first pass over the cell's velocities sums q_T, the second relaxes
 // towards f_S = M [1 + k c.q (|c|^2/T - 4)], g_S = T/2 M [1 + k c.q (|c|^2/T - 2)],
 // k = (1 - Pr) / (5 rho T^2).
+// The moments of the transported values come from mom (Smom partial-sum
+// slots: this context's S, or 1 for the sums of a velocity split over the
+// ranks); the moment sums of the relaxed values go to part (S slots).
 // CONS: the equilibrium from the conservative parameters eqp (Sec. 3.1), a
 // variant of its own so that the plain one keeps its registers (the pass is
 // bound by memory latency, and 64 registers give four blocks per SM).
 template <typename T, bool SHAK, bool CONS>
 __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_tau0, T *f, const VCoef<T> *vt,
-                                                          T *part, const int8_t *type, const T *eqp, T Pr, int *err)
+                                                          const T *mom, int Smom, T *part, const int8_t *type,
+                                                          const T *eqp, T Pr, int *err)
 {
     constexpr int W = Vec<T>::W;
     using V = typename Vec<T>::type;
@@ -1409,7 +1413,7 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex(Grid2D g, int S, T dt_
     const long nc = (long)g.nx * g.ny, cell = (long)j * g.nx + i;
     bool gas = i < g.nx && type[cell] != DVM_SOLID;
     T s[4] = {T(0), T(0), T(0), T(0)};
-    if (gas) gather_partials(part, S, nc, cell, s);
+    if (gas) gather_partials(mom, Smom, nc, cell, s);
     T rho = 0, ux = 0, uy = 0, tmp = 0;
     if (gas && !primitives<T>(pick<T>(g.dv_f, g.dv), s[0], s[1], s[2], s[3], rho, ux, uy, tmp)) {
         if (threadIdx.y == 0) atomicExch(&err[kErrNonphys], 1);
@@ -1734,12 +1738,67 @@ __global__ void k_unfold_partials(const double *x, long n, T *part)
     if (t < n) part[t] = (T)x[t];
 }
 
+// The bookkeeping that ends a step: the new state is the current one.
+cudaError_t end_step2d(dvm_ctx *c, bool hkeep)
+{
+    c->cur = 1 - c->cur;
+    if (c->moving) c->gcur = 1 - c->gcur;
+    c->need_fusion = false;
+    c->hvalid = hkeep;
+    c->steps_done++;
+    return cudaGetLastError();
+}
+
+// The relaxation of the semi-implicit scheme (Eq. ImpSchemeDD) on the
+// transported values f[1 - cur], with their moments from mom (Smom slots).
+template <typename T>
+cudaError_t imex_relax2d(dvm_ctx *c, const T *mom, int Smom)
+{
+    const Grid2D g = grid2d(c);
+    T *fout = (T *)c->f[1 - c->cur], *pout = (T *)c->part[1 - c->cur];
+    const bool cons = c->eq_mode == DVM_EQ_CONSERVATIVE;
+    const dim3 grid(nblk(c->nx, 32), c->ny), block(32, kMomChunks);
+    const int8_t *type1 = c->geo[c->moving ? 1 - c->gcur : c->gcur].type;    // cell types at t^{n+1}
+    cudaError_t e;
+    // conservative equilibrium parameters of the transported state
+    if (cons && (e = eqpar(c, mom, Smom)) != cudaSuccess) return e;
+    const T r0 = T(c->dt / c->tau0);
+    const VCoef<T> *vt = (const VCoef<T> *)c->vtab;
+    if (c->model == DVM_SHAKHOV)
+        k_imex<T, true, false><<<grid, block, 0, c->stream>>>(g, c->S, r0, fout, vt, mom, Smom, pout, type1, nullptr,
+                                                              T(c->Pr), c->d_err);
+    else if (cons)
+        k_imex<T, false, true><<<grid, block, 0, c->stream>>>(g, c->S, r0, fout, vt, mom, Smom, pout, type1,
+                                                              (const T *)c->eqp, T(1), c->d_err);
+    else
+        k_imex<T, false, false><<<grid, block, 0, c->stream>>>(g, c->S, r0, fout, vt, mom, Smom, pout, type1,
+                                                               nullptr, T(1), c->d_err);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// Phase 3 of a semi-implicit step of a velocity split: the relaxation from
+// the moment sums of the transported values summed over the ranks (xbuf).
+template <typename T>
+cudaError_t split_relax2d_t(dvm_ctx *c, const double *xbuf)
+{
+    const long nc = (long)c->nc;
+    T *mom = (T *)c->split_in;
+    k_unfold_partials<T><<<nblk(4 * nc, 256), 256, 0, c->stream>>>(xbuf, 4 * nc, mom);
+    c->launches += 1;
+    cudaError_t e = imex_relax2d<T>(c, mom, 1);
+    if (e != cudaSuccess) return e;
+    return end_step2d(c, false);
+}
+
 // One step in phases.  phase 0: the whole step.  A velocity split (Sec. 5.2:
 // each rank holds every cell for a slab of the velocity grid) runs it as
 // phase 1, which ends with this context's contributions in xbuf (FP64: the
 // moment sums of F^n of every cell, [4][nc], then the eight wall sums of every
 // wall cell, [wall slot][8]), and phase 2, which takes xbuf summed over the
-// ranks and finishes the step.
+// ranks and finishes the step.  Under the semi-implicit scheme phase 2 ends
+// with this context's moment sums of the transported values in xbuf ([4][nc])
+// and phase 3 takes them summed over the ranks and relaxes.
 template <typename T>
 cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
 {
@@ -1855,30 +1914,16 @@ cudaError_t step2d_t(dvm_ctx *c, int phase, double *xbuf)
         c->launches += 1;
     }
     if (imex) {
-        const dim3 grid(nblk(c->nx, 32), c->ny), block(32, kMomChunks);
-        const int8_t *type1 = c->geo[moving ? 1 - c->gcur : c->gcur].type;    // cell types at t^{n+1}
-        // conservative equilibrium parameters of the transported state
-        if (cons && (e = eqpar(c, pout, c->S)) != cudaSuccess) return e;
-        if (c->model == DVM_SHAKHOV)
-            k_imex<T, true, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
-                                                                  (const VCoef<T> *)c->vtab, pout, type1, nullptr,
-                                                                  T(c->Pr), c->d_err);
-        else if (cons)
-            k_imex<T, false, true><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
-                                                                  (const VCoef<T> *)c->vtab, pout, type1,
-                                                                  (const T *)c->eqp, T(1), c->d_err);
-        else
-            k_imex<T, false, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout,
-                                                                   (const VCoef<T> *)c->vtab, pout, type1, nullptr,
-                                                                   T(1), c->d_err);
-        c->launches += 1;
+        if (phase == 2) {
+            // velocity split: this rank's moment sums of the transported
+            // values; the ranks sum them before dvm_split_relax (phase 3)
+            k_fold_partials<T><<<nblk(nc, 256), 256, 0, c->stream>>>(pout, c->S, nc, xbuf);
+            c->launches += 1;
+            return cudaGetLastError();
+        }
+        if ((e = imex_relax2d<T>(c, pout, c->S)) != cudaSuccess) return e;
     }
-    c->cur = 1 - c->cur;
-    if (moving) c->gcur = 1 - c->gcur;
-    c->need_fusion = false;
-    c->hvalid = hkeep;
-    c->steps_done++;
-    return cudaGetLastError();
+    return end_step2d(c, hkeep);
 }
 
 }  // namespace
@@ -1990,11 +2035,14 @@ cudaError_t step2d(dvm_ctx *c)
     return c->prec == DVM_FP32 ? step2d_t<float>(c, 0, nullptr) : step2d_t<double>(c, 0, nullptr);
 }
 
-// Velocity split: phase 1 (this rank's sums into xbuf) or phase 2 (finish
-// the step from xbuf summed over the ranks).
+// Velocity split: phase 1 (this rank's sums into xbuf), phase 2 (finish the
+// step from xbuf summed over the ranks; semi-implicit scheme: the transport,
+// and this rank's moment sums of the transported values into xbuf) or phase
+// 3 (semi-implicit scheme: the relaxation from xbuf summed over the ranks).
 cudaError_t split_step2d(dvm_ctx *c, int phase, void *xbuf)
 {
     double *x = static_cast<double *>(xbuf);
+    if (phase == 3) return c->prec == DVM_FP32 ? split_relax2d_t<float>(c, x) : split_relax2d_t<double>(c, x);
     return c->prec == DVM_FP32 ? step2d_t<float>(c, phase, x) : step2d_t<double>(c, phase, x);
 }
 

@@ -1136,15 +1136,17 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_moments_out3(Grid3D g, cons
 
 // Implicit relaxation of the semi-implicit scheme (Eq. ImpSchemeDD) in 3D,
 // after a transport pass without relaxation: every gas cell relaxes towards
-// the Maxwellian of the moments of its transported values (the partial sums),
-// F = (F* + nu M) / (1 + nu) with nu = (dt / tau0) rho, in place and in its
-// padding mirrors; the partial sums become those of the relaxed state.
+// the Maxwellian of the moments of its transported values (mom, Smom slots:
+// this context's partial sums, or those summed over the ranks of a velocity
+// split), F = (F* + nu M) / (1 + nu) with nu = (dt / tau0) rho, in place and
+// in its padding mirrors; the partial sums part become those of this
+// context's relaxed values.
 // Block = 32 consecutive cells of an x-row x kMomChunks warps, one chunk of
 // the velocity groups each.
 template <typename T, bool SHAK>
 __global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt_tau0, T *f, const VX3<T> *vxt,
-                                                           const VYZ3<T> *vyz, T *part, const int8_t *type,
-                                                           const T *eqp, T Pr, int *err)
+                                                           const VYZ3<T> *vyz, const T *mom, int Smom, T *part,
+                                                           const int8_t *type, const T *eqp, T Pr, int *err)
 {
     // SHAK: the Shakhov model (Sec. 2.1) with the heat flux at t^{n+1},
     // q = q_T / (1 + nu Pr), q_T = sum c |c|^2/2 F dv of the transported
@@ -1156,7 +1158,7 @@ __global__ void __launch_bounds__(32 * kMomChunks) k_imex3(Grid3D g, int S, T dt
     const long nc = (long)g.nx * g.ny * g.nz, cell = ((long)k * g.ny + j) * g.nx + i;
     bool gas = i < g.nx && type[cell] != DVM_SOLID;
     T s[5] = {T(0), T(0), T(0), T(0), T(0)};
-    if (gas) gather_partials3(part, S, nc, cell, s);
+    if (gas) gather_partials3(mom, Smom, nc, cell, s);
     T rho = 0, ux = 0, uy = 0, uz = 0, tmp = 0;
     if (gas && !primitives3<T>(pick<T>(g.dv_f, g.dv), s, rho, ux, uy, uz, tmp)) {
         if (threadIdx.y == 0) atomicExch(&err[kErrNonphys], 1);
@@ -1505,10 +1507,45 @@ __global__ void k_unfold_partials3(const double *x, long n, T *part)
     if (t < n) part[t] = (T)x[t];
 }
 
+// The bookkeeping that ends a step: the new state is the current one.
+cudaError_t end_step3d(dvm_ctx *c)
+{
+    c->cur = 1 - c->cur;
+    c->need_fusion = false;
+    c->steps_done++;
+    return cudaGetLastError();
+}
+
+// The relaxation of the semi-implicit scheme (Eq. ImpSchemeDD) on the
+// transported values f[1 - cur], with their moments from mom (Smom slots).
+template <typename T>
+cudaError_t imex_relax3d(dvm_ctx *c, const T *mom, int Smom)
+{
+    const Grid3D g = grid3d(c);
+    T *fout = (T *)c->f[1 - c->cur], *pout = (T *)c->part[1 - c->cur];
+    const bool cons = c->eq_mode == DVM_EQ_CONSERVATIVE;
+    const dim3 grid(nb3(c->nx, 32), c->ny, c->nz), block(32, kMomChunks);
+    cudaError_t e;
+    // conservative equilibrium parameters of the transported state
+    if (cons && (e = eqpar(c, mom, Smom)) != cudaSuccess) return e;
+    if (c->model == DVM_SHAKHOV)
+        k_imex3<T, true><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c),
+                                                        vyz_table<T>(c), mom, Smom, pout, c->geo3.type, nullptr,
+                                                        T(c->Pr), c->d_err);
+    else
+        k_imex3<T, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c),
+                                                         vyz_table<T>(c), mom, Smom, pout, c->geo3.type,
+                                                         cons ? (const T *)c->eqp : nullptr, T(1), c->d_err);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
 // One step in phases, as in 2D: 0 the whole step; a velocity split runs
 // phase 1 (this rank's moment sums [5][nc] and wall sums [wall slot][14]
 // into the FP64 buffer xbuf) and phase 2 (the rest, from xbuf summed over
-// the ranks).
+// the ranks).  Under the semi-implicit scheme phase 2 ends with this rank's
+// moment sums of the transported values in xbuf ([5][nc]) and phase 3 takes
+// them summed over the ranks and relaxes.
 template <typename T>
 cudaError_t step3d_t(dvm_ctx *c, int phase, double *xbuf)
 {
@@ -1594,23 +1631,30 @@ cudaError_t step3d_t(dvm_ctx *c, int phase, double *xbuf)
         c->launches += 1;
     }
     if (imex) {
-        const dim3 grid(nb3(c->nx, 32), c->ny, c->nz), block(32, kMomChunks);
-        // conservative equilibrium parameters of the transported state
-        if (cons && (e = eqpar(c, pout, c->S)) != cudaSuccess) return e;
-        if (c->model == DVM_SHAKHOV)
-            k_imex3<T, true><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c),
-                                                            vyz_table<T>(c), pout, c->geo3.type, nullptr, T(c->Pr),
-                                                            c->d_err);
-        else
-            k_imex3<T, false><<<grid, block, 0, c->stream>>>(g, c->S, T(c->dt / c->tau0), fout, vx_table<T>(c),
-                                                             vyz_table<T>(c), pout, c->geo3.type,
-                                                             cons ? (const T *)c->eqp : nullptr, T(1), c->d_err);
-        c->launches += 1;
+        if (phase == 2) {
+            // a velocity split relaxes in phase 3, from the moment sums of
+            // the transported values summed over the ranks
+            k_fold_partials3<T><<<nb3(nc, 256), 256, 0, c->stream>>>(pout, c->S, nc, xbuf);
+            c->launches += 1;
+            return cudaGetLastError();
+        }
+        if ((e = imex_relax3d<T>(c, pout, c->S)) != cudaSuccess) return e;
     }
-    c->cur = 1 - c->cur;
-    c->need_fusion = false;
-    c->steps_done++;
-    return cudaGetLastError();
+    return end_step3d(c);
+}
+
+// Phase 3 of a semi-implicit step of a velocity split: the relaxation from
+// the moment sums of the transported values summed over the ranks (xbuf).
+template <typename T>
+cudaError_t split_relax3d_t(dvm_ctx *c, const double *xbuf)
+{
+    const long nc = (long)c->nc;
+    T *mom = (T *)c->split_in;
+    k_unfold_partials3<T><<<nb3(5 * nc, 256), 256, 0, c->stream>>>(xbuf, 5 * nc, mom);
+    c->launches += 1;
+    cudaError_t e = imex_relax3d<T>(c, mom, 1);
+    if (e != cudaSuccess) return e;
+    return end_step3d(c);
 }
 
 }  // namespace
@@ -1672,6 +1716,7 @@ cudaError_t step3d(dvm_ctx *c)
 cudaError_t split_step3d(dvm_ctx *c, int phase, void *xbuf)
 {
     double *x = static_cast<double *>(xbuf);
+    if (phase == 3) return c->prec == DVM_FP32 ? split_relax3d_t<float>(c, x) : split_relax3d_t<double>(c, x);
     return c->prec == DVM_FP32 ? step3d_t<float>(c, phase, x) : step3d_t<double>(c, phase, x);
 }
 

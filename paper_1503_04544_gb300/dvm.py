@@ -90,6 +90,7 @@ SIGNATURES = {
     "dvm_split_size": [_P, C.POINTER(C.c_size_t)],
     "dvm_split_begin": [_P, _P],
     "dvm_split_finish": [_P, _P],
+    "dvm_split_relax": [_P, _P],
     "dvm_wall_force": [_P, _PD, _PD],
     "dvm_history": [_P, _PD, _PD, _PD, _PD, _PD, _PD, C.c_int, C.POINTER(C.c_int)],
     "dvm_body_state": [_P, _PD, _PD],
@@ -178,6 +179,7 @@ class Solver:
                 st = np.ascontiguousarray(states[side], dtype=np.float64)
             _check(lib.dvm_set_bc(h, side, int(kind), _ptr(st)))
         self._keep = []
+        self.time_scheme = EXPLICIT
         if cfg.get("shape", 0):
             self.set_body(cfg)
         if int(cfg.get("time_scheme", 0)):
@@ -260,6 +262,7 @@ class Solver:
     def set_time_scheme(self, scheme: int):
         """0: explicit (Eq. ExSchemeDD), 1: first-order semi-implicit (Eq. ImpSchemeDD)."""
         _check(load().dvm_set_time_scheme(self.h, int(scheme)))
+        self.time_scheme = int(scheme)
 
     def set_adjoint_tape(self, max_bytes: int):
         """Device bytes the adjoint may use to keep the forward run's tape of
@@ -311,8 +314,15 @@ class Solver:
         _check(load().dvm_split_begin(self.h, _P(xbuf.data_ptr())))
 
     def split_finish(self, xbuf):
-        """Finish the step from ``xbuf`` summed over the ranks."""
+        """Finish the step from ``xbuf`` summed over the ranks.  Under the
+        semi-implicit scheme: transport, and this rank's moment sums of the
+        transported values into ``xbuf`` for the second exchange."""
         _check(load().dvm_split_finish(self.h, _P(xbuf.data_ptr())))
+
+    def split_relax(self, xbuf):
+        """Semi-implicit scheme: relax from ``xbuf`` summed over the ranks
+        again, and end the step."""
+        _check(load().dvm_split_relax(self.h, _P(xbuf.data_ptr())))
 
     def wall_force(self):
         F = np.zeros(3)

@@ -3,7 +3,9 @@
 of the last velocity axis (v_y in 2D, v_z in 3D), transports and relaxes its
 own velocities, and the ranks sum one exchange buffer per step (the moment
 sums of every cell and the wall sums of every wall cell, dvm_split_begin /
-dvm_split_finish).
+dvm_split_finish).  The semi-implicit scheme sums it a second time: the
+moment sums of the transported values, from which every rank relaxes its own
+velocities (dvm_split_relax).
 
 The sum is the caller's collective: ``torch.distributed.all_reduce`` on the
 buffer (NCCL between GPUs), or ``local_allreduce`` for several contexts of
@@ -85,8 +87,14 @@ class SplitSolver:
         self.solver.split_begin(self.xbuf)
         return self.xbuf
 
-    def finish(self):
+    def finish(self) -> bool:
+        """Finish the step; True when it waits for the second exchange (the
+        semi-implicit scheme), with this rank's sums in the buffer."""
         self.solver.split_finish(self.xbuf)
+        return self.solver.time_scheme == dvm.IMEX
+
+    def relax(self):
+        self.solver.split_relax(self.xbuf)
 
     def close(self):
         self.solver.close()
@@ -99,8 +107,13 @@ def step(ranks: list[SplitSolver], allreduce, nsteps: int = 1):
     for _ in range(nsteps):
         bufs = [r.begin() for r in ranks]
         allreduce(bufs)
-        for r in ranks:
-            r.finish()
+        pending = [r.finish() for r in ranks]
+        if any(pending):
+            if not all(pending):
+                raise RuntimeError("velocity split: the ranks use different time schemes")
+            allreduce(bufs)
+            for r in ranks:
+                r.relax()
 
 
 def local_allreduce(bufs):
