@@ -235,8 +235,9 @@ static cudaError_t graph_steps(dvm_ctx *c, int pairs, int *done)
     c->steps_done = steps0;
     c->launches = launches0;
     cudaGraphExec_t exec = nullptr;
+    // the kernel nodes keep their own launch priorities (the bulk kernel's)
     const bool ok = es == cudaSuccess && ee == cudaSuccess && graph &&
-                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+                    cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
     if (graph) cudaGraphDestroy(graph);
     if (!ok) {
         // not capturable here: nothing was enqueued, step launch by launch

@@ -21,6 +21,7 @@
 
 #include <cstdio>
 #include <string>
+#include <type_traits>
 
 #include "dvm_device.cuh"
 
@@ -987,9 +988,12 @@ __device__ __forceinline__ WallGeom wall_geom(const CvArgs &c, const BodyParams 
 // halves around the caller's sum over the ranks: mode 1 writes each wall
 // cell's eight sums over this context's velocities to xw[8 * slot] and stops;
 // mode 2 reads the summed eight values from xw and does the rest.
-// The wall sums are FP64 in both precisions (products of the state values,
-// exact in FP64 for an FP32 state, and FP64 sums), as are the wall density,
-// the stress, the force, the torque and the rotation.
+// The velocities of the wall sums and their sign against the wall normal are
+// FP64 in both precisions (the split into incoming and outgoing velocities
+// is decided as in FP64); the products and the compensated sums are in the
+// state precision (for an FP32 state, FP32 products and compensated sums,
+// about 1e-7 relative); the wall density, the stress, the force, the torque
+// and the rotation are FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_wall(CvArgs c, BodyParams b, BodyDev *body, const T *f,
                                               double *wdat, double *wcontrib, int *ticket,
@@ -998,7 +1002,8 @@ __global__ void __launch_bounds__(256) k_wall(CvArgs c, BodyParams b, BodyDev *b
     __shared__ double red[8 * 8];
     __shared__ double ex[kMaxAxisNv], ey[kMaxAxisNv];
     __shared__ double wsc[6];   // uwx, uwy, nwx, nwy, 1/(2 pi Tw), 2 Tw
-    __shared__ double wred[8 * 2];
+    using WA = typename std::conditional<sizeof(T) == 4, float, double>::type;   // wall-sum type
+    __shared__ WA wred[8 * 2];
     __shared__ bool last;
     const Grid2D &g = c.g;
     const int nw = min(c.counts[1], c.cap);
@@ -1025,20 +1030,21 @@ __global__ void __launch_bounds__(256) k_wall(CvArgs c, BodyParams b, BodyDev *b
         }
         __syncthreads();
         const long pck = pcell(g, k) * Vec<T>::W;
-        Acc<double> a0, a1, a2, a3, a4, a5, a6, a7;
+        Acc<WA> a0, a1, a2, a3, a4, a5, a6, a7;
         int p1 = tid % g.nvx, p2 = tid / g.nvx;
         const int dp1 = blockDim.x % g.nvx, dp2 = blockDim.x / g.nvx;
         for (int p = tid; p < g.nv; p += blockDim.x) {
             const double ax = g.vxmin + p1 * g.dvx - uwx, ay = g.vymin + p2 * g.dvy - uwy;
             const double cp = ax * nwx + ay * nwy;
+            const WA cw = (WA)cp, axw = (WA)ax, ayw = (WA)ay;
             if (cp > 0.0) {
-                const double fv = (double)f[ebase<T>(g, 0, p) + pck];
-                a0.add(cp * fv);
-                a5.add(ax * ax * fv); a6.add(ax * ay * fv); a7.add(ay * ay * fv);
+                const WA fv = (WA)f[ebase<T>(g, 0, p) + pck];
+                a0.add(cw * fv);
+                a5.add(axw * axw * fv); a6.add(axw * ayw * fv); a7.add(ayw * ayw * fv);
             } else if (cp < 0.0) {
-                const double m1 = cm * ex[p1] * ey[p2];
-                a1.add(cp * m1);
-                a2.add(ax * ax * m1); a3.add(ax * ay * m1); a4.add(ay * ay * m1);
+                const WA m1 = (WA)(cm * ex[p1] * ey[p2]);
+                a1.add(cw * m1);
+                a2.add(axw * axw * m1); a3.add(axw * ayw * m1); a4.add(ayw * ayw * m1);
             }
             p1 += dp1; p2 += dp2;
             if (p1 >= g.nvx) { p1 -= g.nvx; p2 += 1; }
@@ -1711,9 +1717,27 @@ cudaError_t launch_bulk(dvm_ctx *c, const BulkArgs<T> &a)
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(nblk(c->nx, 32), nblk(c->ny, kRows), c->S), block(32, kRows);
-    k_bulk<T, MUSCL, REC, SHAK><<<grid, block, smem, c->stream>>>(a, c->tmap[c->cur]);
-    return cudaGetLastError();
+    // the device's greatest launch priority: the side-stream kernels beside
+    // it (wall and control volumes) take an SM's registers only when none of
+    // the bulk kernel's own blocks waits for them
+    static int prio = 0;
+    static bool have_prio = false;
+    if (!have_prio) {
+        int least = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &prio) != cudaSuccess) return cudaGetLastError();
+        have_prio = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblk(c->nx, 32), nblk(c->ny, kRows), c->S);
+    cfg.blockDim = dim3(32, kRows);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_bulk<T, MUSCL, REC, SHAK>, a, c->tmap[c->cur]);
 }
 
 // Moment sums of each cell over this context's velocities, folded over the
