@@ -25,7 +25,9 @@
 //                  cell's and folded back onto the cells they copy
 //                  (periodic, zero-gradient) or chained to (rho, u, T) of
 //                  the Maxwellian ghost state;
-//   k_adj_fuseT    transpose of the fusion of merged control volumes.
+//   k_adj_fuseT    transpose of the fusion of merged control volumes; it
+//                  also forms mu of the result for the next transposed
+//                  step, which then skips k_adj_mu.
 // The driver dvm_drag_adjoint checkpoints the forward run every K steps,
 // recomputes each segment onto a device tape and sweeps it backwards.
 #include <cstring>
@@ -758,28 +760,21 @@ __global__ void __launch_bounds__(256) k_adj_padwords(Grid2D g, const T *f, cons
 // folded onto the boundary cell (zero-gradient) or summed over the steps
 // into pacc (Maxwellian; a reduction without return, one adder per address
 // and step, so the sum is deterministic).
+// The term of one pad: side, side cell q, velocity group grp.
 template <typename T, bool MUSCL>
-__global__ void __launch_bounds__(256) k_adj_pads_fast(AdjArgs a, const T *lam, const uint32_t *bits, long bslab,
-                                                       int bpitch, int side0, int sides, int nside, int padmask,
-                                                       const uint8_t *fast, double *pacc, int nmax, T *lam_out)
+__device__ __forceinline__ void pad_fast_one(const AdjArgs &a, const T *lam, const uint32_t *bits, long bslab,
+                                             int bpitch, int side, int q, int grp, double *pacc, int nmax,
+                                             T *lam_out)
 {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     const Grid2D &g = a.g;
-    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long per = (long)nside * g.ngrp;
-    if (t >= per * sides) return;
-    const int side = side0 + (int)(t / per);
-    t %= per;
-    if (!((padmask >> side) & 1)) return;
     pacc += (long)side * nmax * 2 * g.nv;
-    const int q = (int)(t % nside), grp = (int)(t / nside), p = grp * W;
+    const int p = grp * W;
     const int axis = side >> 1;
     const int n = axis == 0 ? g.nx : g.ny;
     const int ib = (side & 1) ? n - 1 : 0;                  // boundary cell along the axis
     const int ci = axis == 0 ? ib : q, cj = axis == 0 ? q : ib;
-    const long k = (long)cj * g.nx + ci;
-    if (!fast[k]) return;
     const int di = axis == 0 ? ((side & 1) ? 1 : -1) : 0, dj = axis == 1 ? ((side & 1) ? 1 : -1) : 0;
     uint32_t bo = 0, bp1 = 0;
     if (MUSCL) {
@@ -819,6 +814,68 @@ __global__ void __launch_bounds__(256) k_adj_pads_fast(AdjArgs a, const T *lam, 
             vst<T>(o, cur);
         }
     }
+}
+
+// Pads of a zero-gradient or Maxwellian side whose boundary cell is a fast
+// cell (one thread per (side, side cell, velocity group), after the fast
+// gather; the two sides of one axis together, as they touch distinct cells):
+// folded onto the boundary cell (zero-gradient) or summed over the steps
+// into pacc (Maxwellian; a reduction without return, one adder per address
+// and step, so the sum is deterministic).
+template <typename T, bool MUSCL>
+__global__ void __launch_bounds__(256) k_adj_pads_fast(AdjArgs a, const T *lam, const uint32_t *bits, long bslab,
+                                                       int bpitch, int side0, int sides, int nside, int padmask,
+                                                       const uint8_t *fast, double *pacc, int nmax, T *lam_out)
+{
+    const Grid2D &g = a.g;
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long per = (long)nside * g.ngrp;
+    if (t >= per * sides) return;
+    const int side = side0 + (int)(t / per);
+    t %= per;
+    if (!((padmask >> side) & 1)) return;
+    const int q = (int)(t % nside), grp = (int)(t / nside);
+    const int axis = side >> 1;
+    const int ib = (side & 1) ? (axis == 0 ? g.nx : g.ny) - 1 : 0;
+    if (!fast[axis == 0 ? (long)q * g.nx + ib : (long)ib * g.nx + q]) return;
+    pad_fast_one<T, MUSCL>(a, lam, bits, bslab, bpitch, side, q, grp, pacc, nmax, lam_out);
+}
+
+// The same for the four sides in one launch (nx, ny > 1).  A corner cell's
+// x-side and y-side terms both land on it when both sides fold onto the
+// boundary cell: the x side's thread then adds the y side's term after its
+// own (the order of one launch per axis), so no two threads update one cell.
+template <typename T, bool MUSCL>
+__global__ void __launch_bounds__(256) k_adj_pads_fast4(AdjArgs a, const T *lam, const uint32_t *bits, long bslab,
+                                                        int bpitch, int padmask, const uint8_t *fast, double *pacc,
+                                                        int nmax, T *lam_out)
+{
+    const Grid2D &g = a.g;
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long perx = (long)g.ny * g.ngrp, pery = (long)g.nx * g.ngrp;
+    if (t >= 2 * (perx + pery)) return;
+    int side;
+    if (t < 2 * perx) {
+        side = (int)(t / perx);
+        t %= perx;
+    } else {
+        t -= 2 * perx;
+        side = 2 + (int)(t / pery);
+        t %= pery;
+    }
+    if (!((padmask >> side) & 1)) return;
+    const int nside = side < 2 ? g.ny : g.nx;
+    const int q = (int)(t % nside), grp = (int)(t / nside);
+    const auto folds = [&](int s) { return ((padmask >> s) & 1) && g.bc[s] != DVM_BC_MAXWELLIAN; };
+    const int axis = side >> 1;
+    const int ib = (side & 1) ? (axis == 0 ? g.nx : g.ny) - 1 : 0;
+    if (!fast[axis == 0 ? (long)q * g.nx + ib : (long)ib * g.nx + q]) return;
+    // a corner of a folding y side: left to the x side's thread when that folds too
+    if (axis == 1 && folds(side) && (q == 0 || q == g.nx - 1) && folds(q == 0 ? 0 : 1)) return;
+    pad_fast_one<T, MUSCL>(a, lam, bits, bslab, bpitch, side, q, grp, pacc, nmax, lam_out);
+    if (axis == 0 && folds(side) && (q == 0 || q == g.ny - 1) && folds(q == 0 ? 2 : 3))
+        pad_fast_one<T, MUSCL>(a, lam, bits, bslab, bpitch, q == 0 ? 2 : 3, side == 0 ? 0 : g.nx - 1, grp, pacc,
+                               nmax, lam_out);
 }
 
 // Cells eligible for the fast gather: plain gas cells whose neighbours within
@@ -1075,14 +1132,14 @@ __global__ void __launch_bounds__(256) k_adj_wall_obj(AdjArgs a, int nw, const W
 // Transpose of the fusion: lam_k = (sbar_k / S) sum_{j in CV} nu_j for merged
 // control volumes (one block per (control volume, chunk of velocities)).
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_fuseT(AdjArgs a, T *lam_out)
+__global__ void __launch_bounds__(256) k_adj_fuseT(AdjArgs a, T *lam_out, T *mucv)
 {
     __shared__ long pcs[kMaxMembers];
     __shared__ T ratio[kMaxMembers];
     const CvInfo &I = reinterpret_cast<const CvInfo *>(a.cvinfo)[blockIdx.x];
     constexpr int W = Vec<T>::W;
     const int nm = I.nm;
-    if (nm <= 1) return;
+    if (nm <= 1 && !mucv) return;
     if (threadIdx.x < nm) {
         pcs[threadIdx.x] = I.mem[threadIdx.x].pc * W;
         ratio[threadIdx.x] = (T)(I.mem[threadIdx.x].sb / I.Sn);
@@ -1094,7 +1151,15 @@ __global__ void __launch_bounds__(256) k_adj_fuseT(AdjArgs a, T *lam_out)
     const long base = ebase<T>(a.g, comp, p);
     T s = 0;
     for (int t = 0; t < nm; ++t) s += lam_out[base + pcs[t]];
-    for (int t = 0; t < nm; ++t) lam_out[base + pcs[t]] = ratio[t] * s;
+    if (nm > 1)
+        for (int t = 0; t < nm; ++t) lam_out[base + pcs[t]] = ratio[t] * s;
+    if (mucv) {
+        // the member sums of the next transposed step, summed as k_adj_mu
+        // sums them (the members' values in member order)
+        T m = 0;
+        for (int t = 0; t < nm; ++t) m += nm > 1 ? ratio[t] * s : lam_out[base + pcs[t]];
+        mucv[((long)blockIdx.x * 2 + comp) * a.g.nvp + p] = m;
+    }
 }
 
 // The two pad layers of one side: their sensitivities (the flux transposes
@@ -1257,7 +1322,8 @@ struct AdjWork {
     int padneed[4] = {0, 0, 0, 0};                   // side cells left to the generic pad kernel
     int ncv = 0;                                     // cut and merged control volumes
     cudaStream_t side = nullptr;                     // second stream of a transposed step
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_pw0 = nullptr, ev_pw = nullptr;
+    bool mu_ready = false;                           // mucv holds the member sums of the next lambda^{n+1}
     cudaStream_t rstream = nullptr;                  // recomputation, one segment ahead of the reverse sweep
     cudaEvent_t ev_rec[2] = {nullptr, nullptr};      // recomputation into tape set s done
     cudaEvent_t ev_used[2] = {nullptr, nullptr};     // transposed steps reading tape set s done
@@ -1298,6 +1364,8 @@ void release(AdjWork &w)
     cudaFree(w.wadj); cudaFree(w.wm); cudaFree(w.wt); cudaFree(w.wd); cudaFree(w.pacc); cudaFree(w.frec);
     if (w.ev_fork) cudaEventDestroy(w.ev_fork);
     if (w.ev_join) cudaEventDestroy(w.ev_join);
+    if (w.ev_pw0) cudaEventDestroy(w.ev_pw0);
+    if (w.ev_pw) cudaEventDestroy(w.ev_pw);
     if (w.side) cudaStreamDestroy(w.side);
     for (int q = 0; q < 2; ++q) {
         if (w.ev_rec[q]) cudaEventDestroy(w.ev_rec[q]);
@@ -1395,14 +1463,23 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
     const T *lam_in = (const T *)w.lam[lin];
     const AdjArgs a = adj_args(c, w);
     T *mucv = (T *)w.mucv, *aux = (T *)w.aux;
+    cudaError_t e;
     if (bits) {
+        // the pad words feed only the fast gather and the pads: on the side
+        // stream, beside the relaxation transpose
+        if ((e = cudaEventRecord(w.ev_pw0, c->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(w.side, w.ev_pw0, 0)) != cudaSuccess) return e;
         const int nmax = c->nx > c->ny ? c->nx : c->ny;
-        k_adj_padwords<T><<<nba(4L * nmax * c->ngrp, 256), 256, 0, c->stream>>>(
+        k_adj_padwords<T><<<nba(4L * nmax * c->ngrp, 256), 256, 0, w.side>>>(
             a.g, f, c->flags, c->gsign, (const VCoef<T> *)c->vtab, const_cast<uint32_t *>(bits), bits_slab(c),
             bits_pitch(c));
+        if ((e = cudaEventRecord(w.ev_pw, w.side)) != cudaSuccess) return e;
     }
     const dim3 cvg((unsigned)(w.ncv > 0 ? w.ncv : 1), nba(2L * c->nvp, 256));
-    if (w.ncv > 0) k_adj_mu<T><<<cvg, 256, 0, c->stream>>>(a, lam_in, mucv);
+    // the member sums of lambda^{n+1}, unless the previous transposed step's
+    // fusion transpose wrote them
+    if (w.ncv > 0 && !w.mu_ready) k_adj_mu<T><<<cvg, 256, 0, c->stream>>>(a, lam_in, mucv);
+    w.mu_ready = false;
     const dim3 cgrid(nba(c->nx, 32), nba(c->ny, 8)), cblock(32, 8);
     k_adj_relax<T><<<dim3(cgrid.x, cgrid.y, w.Z), cblock, 0, c->stream>>>(a, f, part, c->S, lam_in, mucv,
                                                                           (T *)w.rpart);
@@ -1410,7 +1487,7 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
     // the listed cells (record gather, then the wall terms of the wall cells
     // among them) on the side stream, concurrently with the fast cells and
     // their pads: the two write disjoint cells
-    cudaError_t e = cudaEventRecord(w.ev_fork, c->stream);
+    e = cudaEventRecord(w.ev_fork, c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.ev_fork, 0);
     if (e != cudaSuccess) return e;
     if (w.nslow > 0)
@@ -1420,6 +1497,7 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
         k_adj_wall_step<T><<<w.nw, 256, 0, w.side>>>(a, w.nw, w.wadj, (const WallVelT<T> *)w.wt, w.wd, f, lam_in,
                                                       mucv, lam_out, w.gtw);
     if ((e = cudaEventRecord(w.ev_join, w.side)) != cudaSuccess) return e;
+    if (bits && (e = cudaStreamWaitEvent(c->stream, w.ev_pw, 0)) != cudaSuccess) return e;
     e = c->scheme == DVM_MUSCL ? launch_gather_fast<T, true>(c, a, w, w.lmap[lin], bmap, lam_out)
                                : launch_gather_fast<T, false>(c, a, w, w.lmap[lin], nullptr, lam_out);
     if (e != cudaSuccess) return e;
@@ -1427,7 +1505,18 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
     const int nside[4] = {c->ny, c->ny, c->nx, c->nx};
     const int nmax = c->nx > c->ny ? c->nx : c->ny;
     const int ps = pad_sides(c);
-    for (int ax = 0; ax < 2; ++ax) {
+    if (c->nx > 1 && c->ny > 1 && ps) {
+        // the four sides in one launch
+        const unsigned nb = nba(2L * (c->nx + c->ny) * c->ngrp, 256);
+        if (c->scheme == DVM_MUSCL)
+            k_adj_pads_fast4<T, true><<<nb, 256, 0, c->stream>>>(a, lam_in, bits, bits_slab(c), bits_pitch(c), ps,
+                                                                 w.fast, w.pacc, nmax, lam_out);
+        else
+            k_adj_pads_fast4<T, false><<<nb, 256, 0, c->stream>>>(a, lam_in, nullptr, 0, 0, ps, w.fast, w.pacc, nmax,
+                                                                  lam_out);
+        ++launched;
+    }
+    for (int ax = 0; ax < 2 && !(c->nx > 1 && c->ny > 1); ++ax) {
         // both sides of the axis in one launch when they touch distinct cells
         const int n = ax == 0 ? c->nx : c->ny;
         for (int s = 2 * ax; s < 2 * ax + 2; s += n > 1 ? 2 : 1) {
@@ -1452,7 +1541,10 @@ cudaError_t adjoint_step(dvm_ctx *c, AdjWork &w, const T *f, const T *part, cons
             a, f, lam_in, mucv, s, nside[s], w.fast, ps, w.pacc + (long)s * nmax * 2 * c->nv, lam_out);
         ++launched;
     }
-    if (w.ncv > 0) k_adj_fuseT<T><<<cvg, 256, 0, c->stream>>>(a, lam_out);
+    if (w.ncv > 0) {
+        k_adj_fuseT<T><<<cvg, 256, 0, c->stream>>>(a, lam_out, mucv);
+        w.mu_ready = true;
+    }
     c->launches += launched;
     return cudaGetLastError();
 }
@@ -1524,6 +1616,8 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         }
         AC(cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming));
         AC(cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming));
+        AC(cudaEventCreateWithFlags(&w.ev_pw0, cudaEventDisableTiming));
+        AC(cudaEventCreateWithFlags(&w.ev_pw, cudaEventDisableTiming));
         w.Z = c->ngrp < 8 ? c->ngrp : 8;
         w.Zf = c->ngrp < 4 ? c->ngrp : 4;
         AC(cudaMalloc(&w.pacc, sizeof(double) * 4 * nmax * 2 * c->nv));
@@ -1595,6 +1689,9 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     // segment sgi's tape is kept (its interior slots come from the forward run)
     const auto kept = [&](int sgi) { return sgi >= first_kept && seglen(sgi) > 1; };
     const auto kidx = [&](int sgi, int t) { return (size_t)(sgi - first_kept) * (K - 1) + (t - 1); };
+    // a kept segment after a kept segment: the previous one's last step
+    // writes its checkpoint (no copy of the live state)
+    const auto direct = [&](int sgi) { return sgi >= 1 && kept(sgi - 1) && kept(sgi); };
     bool recompute_any = false;
     for (int sgi = 0; sgi < first_kept; ++sgi) recompute_any = recompute_any || seglen(sgi) > 1;
     // two tape sets: the recomputation of one segment fills one while the
@@ -1637,6 +1734,9 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
         const long nf = (long)(4 * (c->nx + 4) + 4 * c->ny) * 2 * c->ngrp;
         for (size_t u = 0; u < w.ktape.size(); ++u)
             k_adj_copy_pads<T><<<nba(nf, 256), 256, 0, c->stream>>>(g, (const T *)c->f[c->cur], (T *)w.ktape[u]);
+        for (int sgi = 1; sgi < nseg; ++sgi)
+            if (direct(sgi))
+                k_adj_copy_pads<T><<<nba(nf, 256), 256, 0, c->stream>>>(g, (const T *)c->f[c->cur], (T *)w.ckpt[sgi]);
         AC(cudaGetLastError());
     }
     AC(cudaMemsetAsync(w.gbc, 0, sizeof(double) * 5 * 4 * nmax, c->stream));
@@ -1682,12 +1782,13 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     const CUtensorMap tm_orig[2] = {c->tmap[0], c->tmap[1]};
     AC(cudaEventRecord(ev[0], c->stream));
     // forward with checkpoints every K steps; a kept segment's steps write its
-    // tape (step t of the segment reads slot t, slot 0 being the live state,
-    // and writes slot t + 1; its last step writes the other live buffer) and
-    // record their limiter branches
+    // tape (step t of the segment reads slot t, slot 0 being the live state or
+    // the checkpoint, and writes slot t + 1; its last step writes the next
+    // segment's checkpoint when that segment is kept, else the other live
+    // buffer) and record their limiter branches
     for (int n = 0; n < nsteps; ++n) {
         const int sgi = n / K, t = n % K, len = seglen(sgi);
-        if (t == 0) {
+        if (t == 0 && !direct(sgi)) {
             AC(cudaMemcpyAsync(w.ckpt[sgi], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
             AC(cudaMemcpyAsync(w.ckpt_part[sgi], c->part[c->cur], partb, cudaMemcpyDeviceToDevice, c->stream));
         }
@@ -1705,12 +1806,20 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
             c->f[L] = w.ktape[kidx(sgi, t)];
             c->part[L] = w.kptape[kidx(sgi, t)];
             c->tmap[L] = w.kmaps[kidx(sgi, t)];
+        } else if (direct(sgi)) {
+            c->f[L] = w.ckpt[sgi];
+            c->part[L] = w.ckpt_part[sgi];
+            c->tmap[L] = w.cmaps[sgi];
         }
         if (!last) {
             c->f[1 - L] = w.ktape[kidx(sgi, t + 1)];
             c->part[1 - L] = w.kptape[kidx(sgi, t + 1)];
             c->tmap[1 - L] = w.kmaps[kidx(sgi, t + 1)];
             if (rec) c->rec_bits = w.kbits[kidx(sgi, t + 1)];
+        } else if (sgi + 1 < nseg && direct(sgi + 1)) {
+            c->f[1 - L] = w.ckpt[sgi + 1];
+            c->part[1 - L] = w.ckpt_part[sgi + 1];
+            c->tmap[1 - L] = w.cmaps[sgi + 1];
         }
         const cudaError_t es = step2d(c);
         c->rec_bits = nullptr;
@@ -1738,7 +1847,8 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
             k_adj_wall_obj<T><<<w.nw, 256, 0, c->stream>>>(a, w.nw, w.wadj, w.wm, w.wd, (const T *)c->f[c->cur], lamA,
                                                             w.gtw, w.jwall);
         if (w.ncv > 0)
-            k_adj_fuseT<T><<<dim3((unsigned)w.ncv, nba(2L * c->nvp, 256)), 256, 0, c->stream>>>(a, lamA);
+            k_adj_fuseT<T><<<dim3((unsigned)w.ncv, nba(2L * c->nvp, 256)), 256, 0, c->stream>>>(a, lamA,
+                                                                                              (T *)nullptr);
     }
     // the public-layout staging buffer of the seed and of lambda^0
     if ((seed || lam0) && !c->d_pub) AC(cudaMalloc(&c->d_pub, c->state_elems * c->elem));
@@ -1754,6 +1864,7 @@ int drag_adjoint_t(dvm_ctx *c, int nsteps, int K, double *J, double *gTw, double
     // (each step writes the next tape buffer) unless the forward run kept it,
     // then apply the transposed steps backwards
     const int cur_orig = c->cur;
+    w.mu_ready = false;              // lambda^N took the objective and the seed after any fusion transpose
     cudaStream_t main_stream = c->stream;
     // tape slot 0 of segment sgi is its checkpoint; slot t > 0 is slot t of
     // the kept tape or of tape set sgi % 2; step t writes slot t + 1 (state
