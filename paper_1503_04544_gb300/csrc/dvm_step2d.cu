@@ -1720,13 +1720,14 @@ cudaError_t launch_bulk(dvm_ctx *c, const BulkArgs<T> &a)
     // the device's greatest launch priority: the side-stream kernels beside
     // it (wall and control volumes) take an SM's registers only when none of
     // the bulk kernel's own blocks waits for them
-    static int prio = 0;
-    static bool have_prio = false;
-    if (!have_prio) {
-        int least = 0;
-        if (cudaDeviceGetStreamPriorityRange(&least, &prio) != cudaSuccess) return cudaGetLastError();
-        have_prio = true;
-    }
+    static const int prio = [] {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return greatest;
+    }();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblk(c->nx, 32), nblk(c->ny, kRows), c->S);
     cfg.blockDim = dim3(32, kRows);
