@@ -56,7 +56,8 @@ enum { DVM_EXPLICIT = 0, DVM_IMEX = 1 };   /* time schemes, see dvm_set_time_sch
 enum { DVM_BGK = 0, DVM_SHAKHOV = 1 };     /* collision models, see dvm_set_collision_model */
 enum { DVM_EQ_DIRECT = 0, DVM_EQ_CONSERVATIVE = 1 };   /* equilibrium moments, see dvm_set_equilibrium */
 enum { DVM_BC_PERIODIC = 0, DVM_BC_MAXWELLIAN = 1, DVM_BC_ZEROGRAD = 2 };
-enum { DVM_SHAPE_NONE = 0, DVM_SHAPE_CIRCLE = 1, DVM_SHAPE_ELLIPSE = 2, DVM_SHAPE_SPHERE = 3 };
+enum { DVM_SHAPE_NONE = 0, DVM_SHAPE_CIRCLE = 1, DVM_SHAPE_ELLIPSE = 2, DVM_SHAPE_SPHERE = 3,
+       DVM_SHAPE_DISK_CONTAINER = 4, DVM_SHAPE_BOX_CONTAINER = 5 };
 enum { DVM_GAS = 0, DVM_CUT = 1, DVM_SOLID = 2 };
 
 /* Cartesian grid of Sec. 3.2.1: nx*ny (*nz) cells on the box. */
@@ -81,7 +82,10 @@ typedef struct {
 
 /* Obstacle (Sec. 3.3.4, Appendix A).  Level set: circle/sphere |x-c| - ra;
  * ellipse with semi-axes ra (along the body x axis) and rb, turned by theta,
- * first-order distance g/|grad g|.  movable = 1: free rotation about the
+ * first-order distance g/|grad g|.  Containers (2D; the gas is inside, the
+ * cells outside are solid; not movable): disk ra - |x-c|; box with
+ * half-widths ra along x and rb along y, min(x - (cx - ra), (cx + ra) - x,
+ * y - (cy - rb), (cy + rb) - y).  movable = 1: free rotation about the
  * centre with moment of inertia `inertia` (Eq. motionDD_vit); the centre and
  * (vbx, vby) stay fixed.  Wall temperature Tw, or per angular sector when
  * nseg > 0: sector s spans from direction seg_dir[2s..2s+1] counter-

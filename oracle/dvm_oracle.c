@@ -68,7 +68,8 @@ static double maxw3d(double rho, double ux, double uy, double uz, double T,
 /* ---------------------------------------------------------------- geometry */
 
 /* Level set of Appendix A: signed distance, negative inside the solid.
- * reading: the ellipse uses the first-order distance g/|grad g|. */
+ * reading: the ellipse uses the first-order distance g/|grad g|; a box
+ * container the least of the four signed distances to its sides. */
 static double levelset2d(const orc_cfg *c, double ct, double st, double x, double y)
 {
     double ddx = x - c->cx, ddy = y - c->cy;
@@ -83,6 +84,13 @@ static double levelset2d(const orc_cfg *c, double ct, double st, double x, doubl
         double nrm = sqrt(gx * gx + gy * gy);
         if (nrm > 0) return g / nrm;
         return -(c->ra < c->rb ? c->ra : c->rb);
+    } else if (c->shape == ORC_SHAPE_DISK_CONTAINER) {
+        /* the gas inside the disk */
+        return c->ra - sqrt(ddx * ddx + ddy * ddy);
+    } else if (c->shape == ORC_SHAPE_BOX_CONTAINER) {
+        /* the gas inside the box: the least distance to its four sides */
+        double x0 = c->cx - c->ra, x1 = c->cx + c->ra, y0 = c->cy - c->rb, y1 = c->cy + c->rb;
+        return fmin(fmin(x - x0, x1 - x), fmin(y - y0, y1 - y));
     }
     return 1.0;
 }

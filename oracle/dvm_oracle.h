@@ -26,7 +26,7 @@ enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_CFL = 2, ORC_ERR_GEOMETRY = 3,
 enum { ORC_GAS = 0, ORC_CUT = 1, ORC_SOLID = 2 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_MAXWELLIAN = 1, ORC_BC_ZEROGRAD = 2 };
 enum { ORC_SHAPE_NONE = 0, ORC_SHAPE_CIRCLE = 1, ORC_SHAPE_ELLIPSE = 2,
-       ORC_SHAPE_SPHERE = 3 };
+       ORC_SHAPE_SPHERE = 3, ORC_SHAPE_DISK_CONTAINER = 4, ORC_SHAPE_BOX_CONTAINER = 5 };
 enum { ORC_UPWIND = 0, ORC_MUSCL = 1 };
 enum { ORC_EXPLICIT = 0, ORC_IMEX = 1 };  /* Eq. ExSchemeDD | Eq. ImpSchemeDD */
 enum { ORC_BGK = 0, ORC_SHAKHOV = 1 };    /* Eq. BGKDD | Eq. ShakhovDD (Sec. 2.1) */

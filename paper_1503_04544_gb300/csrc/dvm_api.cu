@@ -597,12 +597,15 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
     if (!c || !b) { set_error("null argument"); return DVM_ERR_ARG; }
     if (split_step_open(c, "dvm_set_body")) return DVM_ERR_STATE;
     if (c->dim == 3) return set_body3d(c, b);
-    if (b->shape != DVM_SHAPE_NONE && b->shape != DVM_SHAPE_CIRCLE && b->shape != DVM_SHAPE_ELLIPSE) {
-        set_error("2D shapes: none, circle, ellipse"); return DVM_ERR_UNSUPPORTED;
+    const bool container = b->shape == DVM_SHAPE_DISK_CONTAINER || b->shape == DVM_SHAPE_BOX_CONTAINER;
+    if (b->shape != DVM_SHAPE_NONE && b->shape != DVM_SHAPE_CIRCLE && b->shape != DVM_SHAPE_ELLIPSE && !container) {
+        set_error("2D shapes: none, circle, ellipse, disk container, box container"); return DVM_ERR_UNSUPPORTED;
     }
-    if (b->shape != DVM_SHAPE_NONE && (!(b->ra > 0) || (b->shape == DVM_SHAPE_ELLIPSE && !(b->rb > 0)))) {
+    const bool two_sizes = b->shape == DVM_SHAPE_ELLIPSE || b->shape == DVM_SHAPE_BOX_CONTAINER;
+    if (b->shape != DVM_SHAPE_NONE && (!(b->ra > 0) || (two_sizes && !(b->rb > 0)))) {
         set_error("body size"); return DVM_ERR_ARG;
     }
+    if (container && b->movable) { set_error("a container is not movable"); return DVM_ERR_ARG; }
     if (b->movable && !(b->inertia > 0)) { set_error("movable body needs inertia > 0"); return DVM_ERR_ARG; }
     if (b->nseg > 0 && (!b->Tw_seg || !b->seg_dir)) { set_error("nseg > 0 needs Tw_seg and seg_dir"); return DVM_ERR_ARG; }
     c->body = *b;
@@ -619,6 +622,9 @@ int dvm_set_body(dvm_ctx *c, const dvm_body *b)
     // box of cells that can be non-gas or have a non-gas cell within reach
     if (b->shape == DVM_SHAPE_NONE) {
         c->i0 = c->i1 = c->j0 = c->j1 = 0;
+    } else if (container) {
+        // the cells outside the container are solid: the whole grid
+        c->i0 = 0; c->i1 = c->nx; c->j0 = 0; c->j1 = c->ny;
     } else {
         const double R = b->shape == DVM_SHAPE_ELLIPSE ? std::fmax(b->ra, b->rb) : b->ra;
         auto lo = [](double v, double h, int n) { int q = (int)std::floor(v / h) - kBoxMargin; return q < 0 ? 0 : (q > n ? n : q); };

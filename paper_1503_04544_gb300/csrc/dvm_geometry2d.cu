@@ -27,6 +27,12 @@ __device__ __forceinline__ double levelset(const BodyParams &b, double ct, doubl
         if (nrm > 0) return g / nrm;
         return -(b.ra < b.rb ? b.ra : b.rb);
     }
+    // containers: the gas inside
+    if (b.shape == DVM_SHAPE_DISK_CONTAINER) return b.ra - sqrt(ddx * ddx + ddy * ddy);
+    if (b.shape == DVM_SHAPE_BOX_CONTAINER) {
+        const double x0 = b.cx - b.ra, x1 = b.cx + b.ra, y0 = b.cy - b.rb, y1 = b.cy + b.rb;
+        return fmin(fmin(x - x0, x1 - x), fmin(y - y0, y1 - y));
+    }
     return 1.0;
 }
 

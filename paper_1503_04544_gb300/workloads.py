@@ -18,7 +18,8 @@ bc                  6 ints for the x-, x+, y-, y+, z-, z+ sides:
                     0 periodic, 1 Maxwellian ghost, 2 zero-gradient
 bc_state            per side: None or an array (n_side_cells, 5) of
                     (rho, ux, uy, uz, T) for Maxwellian sides
-shape               0 none, 1 circle, 2 ellipse, 3 sphere
+shape               0 none, 1 circle, 2 ellipse, 3 sphere, 4 disk container,
+                    5 box container (2D; the gas inside, half-widths ra, rb)
                     (in 3D, 1 is an infinite circular cylinder along ``axis``)
 axis                3D cylinder axis: 0 x, 1 y, 2 z
 cx, cy, cz, ra, rb  obstacle centre, radius (ra) or semi-axes (ra, rb)
@@ -120,6 +121,28 @@ def rotating_ellipse(nx=512, nv=40, scheme=0) -> dict:
                   mass=1.0, inertia=1e-3, movable=1, Tw=1.0,
                   init=dict(rho=1.0, ux=0.5 * (2.0 * Y - 1.0), uy=0.0, uz=0.0, T=1.0),
                   steps=5000, name=f"rotating_ellipse_{nx}x{nx}_v{nv}x{nv}")
+
+
+def disk_container(nx=64, nv=20, scheme=1, ra=0.45, Tw=1.3) -> dict:
+    """2D closed disk container of radius ra, diffuse wall at Tw, holding a
+    gas at rest (T = 1) with a density bump off the centre."""
+    X, Y = _cell_centres(nx, nx)
+    rho = 1.0 + 0.3 * np.exp(-((X - 0.42) ** 2 + (Y - 0.55) ** 2) / 0.01)
+    return base2d(nx, nx, nv, 8.0, Kn=0.1, Lref=1.0, cfl=0.5, scheme=scheme,
+                  shape=4, cx=0.5, cy=0.5, ra=ra, Tw=Tw,
+                  init=dict(rho=rho, ux=0.0, uy=0.0, uz=0.0, T=1.0), steps=200,
+                  name=f"disk_container_{nx}x{nx}_v{nv}x{nv}")
+
+
+def box_container(nx=64, nv=20, scheme=1, ra=0.41, rb=0.33, Tw=1.3) -> dict:
+    """2D closed box container with half-widths ra, rb about the centre of
+    the domain, diffuse wall at Tw, a drifting gas with a density bump."""
+    X, Y = _cell_centres(nx, nx)
+    rho = 1.0 + 0.3 * np.exp(-((X - 0.42) ** 2 + (Y - 0.55) ** 2) / 0.01)
+    return base2d(nx, nx, nv, 8.0, Kn=0.1, Lref=1.0, cfl=0.5, scheme=scheme,
+                  shape=5, cx=0.5013, cy=0.4987, ra=ra, rb=rb, Tw=Tw,
+                  init=dict(rho=rho, ux=0.3, uy=-0.2, uz=0.0, T=1.0), steps=200,
+                  name=f"box_container_{nx}x{nx}_v{nv}x{nv}")
 
 
 def sphere_mach15(n=96, nv=20, scheme=1) -> dict:
