@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {dvm.FP64: 1e-12, dvm.FP32: 1e-5}
 # Velocities are in units of sqrt(R T0) = 1: a velocity error is relative to
-# max(||u||_inf, 1), so that a flow near rest is not judged on the ratio of
+# max(||u||_inf, 1), so that a flow near rest is not measured by the ratio of
 # two round-off-sized numbers.
 GEO_KEYS = ("type", "cgas", "lx", "ly", "lw", "nwx", "nwy", "rwx", "rwy", "sbar")
 
