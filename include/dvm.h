@@ -178,8 +178,11 @@ int dvm_set_collision_model(dvm_ctx *ctx, int model, double Pr);
 int dvm_set_equilibrium(dvm_ctx *ctx, int mode);
 
 /* Place the obstacle and build the Appendix A geometry on the device (level
- * set, cell types, edge lengths, wall edges, areas, control volumes).
- * Errors: DVM_ERR_GEOMETRY, DVM_ERR_ARG. */
+ * set, cell types, edge lengths, wall edges, areas, control volumes).  2D:
+ * circle, ellipse, disk or box container; 3D: sphere.  Errors:
+ * DVM_ERR_GEOMETRY, DVM_ERR_ARG (sizes, a movable container, a movable body
+ * without inertia), DVM_ERR_UNSUPPORTED (a shape of the other dimension),
+ * DVM_ERR_STATE (between the calls of a velocity-split step). */
 int dvm_set_body(dvm_ctx *ctx, const dvm_body *body);
 
 /* Maxwellian initial state from host arrays of per-cell (rho, ux, uy, uz, T);
